@@ -1,0 +1,283 @@
+"""Seeded synthetic problem descriptions (bodies, motions, initial states).
+
+This module holds no arithmetic of the cut-cell method: it only lays out the
+inputs both the CUDA library and the CPU oracle consume -- grid extents,
+boundary conditions, body polygons at t = 0 (counter-clockwise, a union of
+polygons with disjoint interiors), the rigid motion, and cell-centre initial
+states in conserved variables.  The workloads are shaped like the paper's
+test cases (Sec. III): a density pulse in an inclined channel, a cylinder
+meeting a normal shock, a triangular wedge, a piston in a tube and a pitching
+NACA 0012 aerofoil.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field, replace
+from typing import List, Optional
+
+import numpy as np
+
+EULER, ADVECTION = 0, 1
+TRANSMISSIVE, REFLECTIVE, PERIODIC = 0, 1, 2
+UNCOVER_DONOR, UNCOVER_FLUX_GCL = 0, 1
+BASE_SEED = 1711113610
+GAMMA = 1.4
+
+
+@dataclass
+class Problem:
+    """One simulation instance."""
+    name: str
+    nx: int
+    ny: int
+    x0: float
+    y0: float
+    x1: float
+    y1: float
+    bc: tuple = (TRANSMISSIVE,) * 4          # x-low, x-high, y-low, y-high
+    equation: int = EULER
+    adv: tuple = (0.0, 0.0)
+    gamma: float = GAMMA
+    cfl: float = 0.5
+    uncover_mode: int = UNCOVER_DONOR
+    polygons: List[np.ndarray] = field(default_factory=list)   # each (n, 2), CCW
+    moving: List[int] = field(default_factory=list)
+    U: tuple = (0.0, 0.0)
+    pivot: tuple = (0.0, 0.0)
+    a0: float = 0.0
+    a1: float = 0.0
+    omega: float = 0.0
+    Q0: Optional[np.ndarray] = None           # (nc, ny, nx) conserved variables
+    steps: int = 0
+    t_end: float = 0.0
+
+    @property
+    def nc(self) -> int:
+        return 4 if self.equation == EULER else 1
+
+    @property
+    def dx(self) -> float:
+        return (self.x1 - self.x0) / self.nx
+
+    @property
+    def dy(self) -> float:
+        return (self.y1 - self.y0) / self.ny
+
+    def cell_centres(self):
+        xc = self.x0 + (np.arange(self.nx) + 0.5) * self.dx
+        yc = self.y0 + (np.arange(self.ny) + 0.5) * self.dy
+        return np.meshgrid(xc, yc)
+
+
+# --------------------------------------------------------------------------
+# bodies (counter-clockwise vertex lists)
+# --------------------------------------------------------------------------
+def cylinder_polygon(cx, cy, r, dx):
+    """Regular polygon inscribed in the circle, about two vertices per cell width."""
+    n = 4 * max(4, math.ceil(math.pi * r / dx))
+    th = 2.0 * math.pi * np.arange(n) / n
+    return np.stack([cx + r * np.cos(th), cy + r * np.sin(th)], axis=1)
+
+
+def triangle_polygon(cx, cy, side):
+    """Equilateral triangle with centroid (cx, cy), apex pointing to +x."""
+    R = side / math.sqrt(3.0)
+    th = np.array([0.0, 2.0 * math.pi / 3.0, 4.0 * math.pi / 3.0])
+    return np.stack([cx + R * np.cos(th), cy + R * np.sin(th)], axis=1)
+
+
+def naca00xx_polygon(t=0.12, chord=1.0, n_side=257, le=(-0.25, 0.0)):
+    """Symmetric NACA 4-digit section from the standard thickness formula,
+    cosine-spaced; the open trailing edge is closed by a straight segment."""
+    k = np.arange(n_side)
+    xs = 0.5 * chord * (1.0 - np.cos(np.pi * k / (n_side - 1)))
+    xi = xs / chord
+    yt = 5.0 * t * chord * (0.2969 * np.sqrt(xi) - 0.1260 * xi - 0.3516 * xi ** 2
+                            + 0.2843 * xi ** 3 - 0.1015 * xi ** 4)
+    lower = np.stack([xs, -yt], axis=1)                 # leading edge -> trailing edge
+    upper = np.stack([xs[::-1], yt[::-1]], axis=1)[:-1]  # trailing edge -> just before LE
+    pts = np.concatenate([lower, upper], axis=0)
+    pts[:, 0] += le[0]
+    pts[:, 1] += le[1]
+    return pts
+
+
+def rect_polygon(xa, ya, xb, yb):
+    return np.array([[xa, ya], [xb, ya], [xb, yb], [xa, yb]], dtype=np.float64)
+
+
+def channel_polygons(width=0.2, xlo=-0.3, xhi=1.3):
+    """Solid parts of the doubly periodic unit box around the slope-1/2 channel
+    whose axis copies are -x + 2y = 0.5 + k: the strips between channel copies,
+    extended past the box so that no polygon edge lies on a box side."""
+    h = 0.5 * width * math.sqrt(5.0)      # half-width in units of (-x + 2y)
+    polys = []
+    for k in range(-3, 3):
+        A = 0.5 + k + h
+        B = 1.5 + k - h
+        if (B + xhi) / 2.0 < -0.2 or (A + xlo) / 2.0 > 1.2:
+            continue
+        polys.append(np.array([[xlo, (A + xlo) / 2.0], [xhi, (A + xhi) / 2.0],
+                               [xhi, (B + xhi) / 2.0], [xlo, (B + xlo) / 2.0]], dtype=np.float64))
+    return polys
+
+
+# --------------------------------------------------------------------------
+# initial states
+# --------------------------------------------------------------------------
+def conserved(rho, u, v, p, gamma=GAMMA):
+    rho, u, v, p = np.broadcast_arrays(*[np.asarray(a, dtype=np.float64) for a in (rho, u, v, p)])
+    E = p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v)
+    return np.stack([rho, rho * u, rho * v, E])
+
+
+def post_shock(M, rho1=1.0, p1=1.0, gamma=GAMMA):
+    """Rankine-Hugoniot state behind a normal shock of Mach M running in -x
+    into gas at rest: (rho2, u2, p2)."""
+    c1 = math.sqrt(gamma * p1 / rho1)
+    rho2 = rho1 * (gamma + 1.0) * M * M / ((gamma - 1.0) * M * M + 2.0)
+    p2 = p1 * (1.0 + 2.0 * gamma / (gamma + 1.0) * (M * M - 1.0))
+    u2 = -2.0 / (gamma + 1.0) * (M - 1.0 / M) * c1
+    return rho2, u2, p2
+
+
+def shock_state(prob: Problem, M, x_shock, u_pre=0.0, gamma=GAMMA):
+    """Gas at rest relative to u_pre (rho = 1, p = 1) for x < x_shock and the
+    state behind a Mach-M shock running into it (toward -x) for x > x_shock."""
+    X, _ = prob.cell_centres()
+    r2, u2, p2 = post_shock(M, gamma=gamma)
+    right = X > x_shock
+    rho = np.where(right, r2, 1.0)
+    u = np.where(right, u_pre + u2, u_pre)
+    p = np.where(right, p2, 1.0)
+    return conserved(rho, u, 0.0 * rho, p, gamma)
+
+
+def piston_shock(u_p, rho1=1.0, p1=1.0, gamma=GAMMA):
+    """Planar piston at speed u_p into gas at rest: shock Mach number, shock
+    speed and the uniform state between piston and shock (rho2, u_p, p2)."""
+    c1 = math.sqrt(gamma * p1 / rho1)
+    a = (gamma + 1.0) * u_p / (4.0 * c1)
+    Ms = a + math.sqrt(a * a + 1.0)
+    rho2 = rho1 * (gamma + 1.0) * Ms * Ms / ((gamma - 1.0) * Ms * Ms + 2.0)
+    p2 = p1 * (1.0 + 2.0 * gamma / (gamma + 1.0) * (Ms * Ms - 1.0))
+    return Ms, Ms * c1, rho2, p2
+
+
+def channel_arclength(x, y):
+    """Arc length along the closed slope-1/2 channel loop from (0, 0.25)."""
+    L = math.sqrt(5.0)
+    k = np.rint(-x + 2.0 * y - 0.5)
+    s = (2.0 * (x + k) + y - 0.25) / L
+    return np.mod(s, L)
+
+
+def channel_pulse(s, t=0.0, s0=0.3, w=0.05):
+    """Exact transported profile u0(s - t) on the loop of length sqrt(5)."""
+    L = math.sqrt(5.0)
+    r = np.mod(s - t - s0 + 0.5 * L, L) - 0.5 * L
+    return np.exp(-(r / w) ** 2)
+
+
+# --------------------------------------------------------------------------
+# the five workloads
+# --------------------------------------------------------------------------
+def c1_advection(N=100, steps=200):
+    """Scalar advection along the inclined channel, doubly periodic unit box,
+    CFL 0.8 on regular cells, static walls."""
+    a = (2.0 / math.sqrt(5.0), 1.0 / math.sqrt(5.0))
+    prob = Problem("c1_channel_advection", N, N, 0.0, 0.0, 1.0, 1.0, bc=(PERIODIC,) * 4,
+                   equation=ADVECTION, adv=a, cfl=0.8, polygons=channel_polygons(),
+                   moving=[0] * len(channel_polygons()), steps=steps)
+    X, Y = prob.cell_centres()
+    prob.Q0 = channel_pulse(channel_arclength(X, Y))[None]
+    return prob
+
+
+def c2_cylinder(N=400, M=2.0, t_end=0.3, uncover_mode=UNCOVER_DONOR):
+    """Cylinder r = 0.1 from (0.15, 0.5) at (0.5 c, 0) meeting a Mach-M shock at
+    x = 0.3.  As in the paper's cylinder and wedge tests the body moves with
+    the pre-shock gas, which is at rest in the body's frame."""
+    dx = 1.0 / N
+    c_inf = math.sqrt(GAMMA)
+    prob = Problem("c2_cylinder_shock", N, N, 0.0, 0.0, 1.0, 1.0, cfl=0.5,
+                   polygons=[cylinder_polygon(0.15, 0.5, 0.1, dx)], moving=[1],
+                   U=(0.5 * c_inf, 0.0), pivot=(0.15, 0.5), t_end=t_end, uncover_mode=uncover_mode)
+    prob.Q0 = shock_state(prob, M, 0.3, u_pre=0.5 * c_inf)
+    return prob
+
+
+def c3_naca(N=1024, periods=1.0):
+    """NACA 0012, chord 1, pitching 2.5 deg sin(omega t) about the quarter chord,
+    Mach 0.6 free stream (rho = 1, p = 1/gamma, c = 1), reduced frequency 0.08."""
+    u_inf = 0.6
+    omega = 2.0 * 0.08 * u_inf / 1.0
+    prob = Problem("c3_naca0012_pitching", N, N, -2.0, -2.0, 2.0, 2.0, cfl=0.5,
+                   polygons=[naca00xx_polygon()], moving=[1], pivot=(0.0, 0.0),
+                   a0=0.0, a1=math.radians(2.5), omega=omega, t_end=periods * 2.0 * math.pi / omega)
+    X, _ = prob.cell_centres()
+    prob.Q0 = conserved(np.ones_like(X), u_inf, 0.0, 1.0 / GAMMA)
+    return prob
+
+
+def _body_instance(kind, N, M, uncover_mode=UNCOVER_DONOR, y_nudge=0.3183, x_nudge=0.2718):
+    """One C4/C5-style instance on the unit box with a body of `kind`.
+    Cylinder and triangle move with the pre-shock gas; the piston drives its
+    own shock and starts from the exact planar piston solution at the time
+    the shock is three cells ahead of the piston face."""
+    dx = 1.0 / N
+    c_inf = math.sqrt(GAMMA)
+    if kind == "cylinder":
+        polys, mov, U = [cylinder_polygon(0.15, 0.5, 0.1, dx)], [1], (0.5 * c_inf, 0.0)
+        pivot = (0.15, 0.5)
+    elif kind == "triangle":
+        polys, mov, U = [triangle_polygon(0.15, 0.5, 0.2)], [1], (0.5 * c_inf, 0.0)
+        pivot = (0.15, 0.5)
+    elif kind == "piston":
+        off, ox = y_nudge * dx, x_nudge * dx      # keep body sides off the grid lines
+        polys = [rect_polygon(-0.1, 0.36 + off, 0.6 + ox, 0.40 + off),
+                 rect_polygon(-0.1, 0.60 + off, 0.6 + ox, 0.64 + off),
+                 rect_polygon(0.05 + ox, 0.40 + off, 0.10 + ox, 0.60 + off)]
+        mov, U, pivot = [0, 0, 1], (0.3 * c_inf, 0.0), (0.075, 0.5)
+    else:
+        raise ValueError(kind)
+    prob = Problem(f"{kind}_N{N}", N, N, 0.0, 0.0, 1.0, 1.0, cfl=0.5, polygons=polys, moving=mov,
+                   U=U, pivot=pivot, uncover_mode=uncover_mode)
+    if kind == "piston":
+        X, Y = prob.cell_centres()
+        Ms, S, r2, p2 = piston_shock(U[0])
+        face = 0.10 + ox
+        shock = face + 3.0 * dx * S / (S - U[0])
+        inside = (X + 0.5 * dx > face) & (X < shock) & (Y > 0.40 + off) & (Y < 0.60 + off)
+        prob.Q0 = conserved(np.where(inside, r2, 1.0), np.where(inside, U[0], 0.0), 0.0,
+                            np.where(inside, p2, 1.0))
+    else:
+        prob.Q0 = shock_state(prob, M, 0.3, u_pre=U[0])
+    return prob
+
+
+def c4_batch(n=64, nmin=128, nmax=1024, steps=500, seed=None, kinds=("cylinder", "triangle", "piston")):
+    """64 independent instances on uneven grids, seeded."""
+    ss = np.random.SeedSequence(BASE_SEED).spawn(5)[3] if seed is None else np.random.SeedSequence(seed)
+    rng = np.random.default_rng(ss)
+    probs = []
+    for k in range(n):
+        N = int(rng.integers(nmin, nmax + 1))
+        kind = kinds[int(rng.integers(0, len(kinds)))]
+        M = float(rng.uniform(1.2, 3.0))
+        p = _body_instance(kind, N, M)
+        p.name = f"c4_{k:02d}_{kind}_N{N}_M{M:.3f}"
+        p.steps = steps
+        probs.append(p)
+    return probs
+
+
+def small_case(kind="cylinder", N=48, M=2.0, uncover_mode=UNCOVER_DONOR):
+    """Small single instance for parity tests (seconds on the oracle)."""
+    p = _body_instance(kind, N, M, uncover_mode=uncover_mode)
+    p.name = f"small_{kind}_N{N}"
+    return p
+
+
+def with_state(prob: Problem, Q) -> Problem:
+    return replace(prob, Q0=np.asarray(Q, dtype=np.float64))

@@ -1,0 +1,48 @@
+"""Pins for the oracle on the oblique-channel advection case: the profile is
+transported exactly along the closed channel loop, so the numerical solution
+is compared with u0(s - t) (Sec. III.A uses the same kind of test, a pulse
+travelling parallel to inclined walls), and the scalar content is conserved
+by the static stabilised walls."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1711_11361_gb300 import inputs
+
+
+def run(N, t_end):
+    prob = inputs.c1_advection(N)
+    o = oracle.Oracle(prob)
+    t = 0.0
+    c0 = o.contents().sum()
+    while t < t_end - 1e-14:
+        dt = min(o.cfl_dt(), t_end - t)
+        r, _ = o.step(dt)
+        assert r == 0
+        t += dt
+    X, Y = prob.cell_centres()
+    a = o.alpha()
+    u = o.state()[0]
+    ex = inputs.channel_pulse(inputs.channel_arclength(X, Y), t)
+    fl = a > 0
+    err = np.sum(a[fl] * np.abs(u[fl] - ex[fl])) / np.sum(a[fl] * np.abs(ex[fl]))
+    linf = np.max(np.abs(u[fl] - ex[fl]))
+    return err, linf, (o.contents().sum() - c0) / c0
+
+
+def test_c1_default_dt_is_cfl_on_regular_cells():
+    o = oracle.Oracle(inputs.c1_advection(100))
+    assert abs(o.cfl_dt() - 0.8 * 0.01 * math.sqrt(5.0) / 2.0) < 1e-17
+
+
+def test_c1_converges_to_exact_transport():
+    res = [run(N, 0.5) for N in (50, 100, 200)]
+    l1 = [r[0] for r in res]
+    for r in res:
+        assert abs(r[2]) < 1e-13            # conservation of the scalar
+    assert l1[1] < 0.25
+    o1 = math.log2(l1[0] / l1[1])
+    o2 = math.log2(l1[1] / l1[2])
+    assert o1 > 1.0 and o2 > 1.0
