@@ -1,0 +1,280 @@
+"""Benchmark of the moving-boundary cut-cell sweep on GB300.
+
+Workload (default): 64 independent Euler instances on uneven grids drawn
+uniformly from 128^2 to 1024^2 (seeded), bodies mixed from cylinder,
+equilateral triangle and piston-in-tube, seeded shock Mach numbers in
+[1.2, 3.0]; FP32 bulk arithmetic with FP64 geometry and stabilisation
+weights; each instance at its own CFL time step computed on the device; one
+CUDA-graph replay per time step.  A "step" is one time step of every
+instance = two directional sweeps, each running all five stages of the
+sweep (geometry, standard fluxes, stabilised and wall fluxes, conservative
+update with covering/uncovering, CFL reduction).
+
+Metric: cell-updates per second per sweep (grid cells of all instances times
+sweeps, divided by the device time).  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mb|reference]
+
+Multi-GPU (torchrun, one rank per GPU): every rank advances its own seeded
+batch of independent instances (weak scaling, no collective on the data
+path); value = cells updated by all ranks / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/s per sweep (FP32 batched vs plain FP64, same GB300, stated L1 err); p50/p99"
+UNIT = "cell-updates/s"
+BYTES_PER_CELL_FP32 = 32.0   # 4 conserved values read + 4 written per cell-sweep
+BYTES_PER_CELL_FP64 = 64.0
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def sample_clocks(stop, out):
+    q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+    while not stop.is_set():
+        try:
+            r = subprocess.run(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits"],
+                               capture_output=True, text=True, timeout=5)
+            for line in r.stdout.strip().splitlines():
+                out.append([x.strip() for x in line.split(",")])
+        except Exception:
+            pass
+        stop.wait(0.2)
+
+
+def summarize_clocks(samples, gpu_index):
+    rows = [s for s in samples if s and s[0] == str(gpu_index)] or samples
+    if not rows:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+    sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+    mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    reasons = set()
+    for r in rows:
+        for k, n in enumerate(names):
+            if len(r) > 5 + k and r[5 + k].lower().startswith("active"):
+                reasons.add(n)
+    return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+            "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def workload(rank, args):
+    from paper_1711_11361_gb300 import inputs
+    if args.workload == "c4":
+        seed = None if rank == 0 else inputs.BASE_SEED + 1000 + rank
+        return inputs.c4_batch(n=args.instances, seed=seed), "c4_batched_64_uneven_128-1024"
+    if args.workload == "c2":
+        return [inputs.c2_cylinder(400)], "c2_cylinder_400"
+    if args.workload == "c3":
+        return [inputs.c3_naca(1024)], "c3_naca0012_1024"
+    raise SystemExit(f"unknown workload {args.workload}")
+
+
+def cpu_baseline(probs, budget_s=12.0):
+    """The oracle as it stands on this host's cores, on a bounded sample:
+    full steps of the smallest instance of the workload until about
+    budget_s of CPU time."""
+    import oracle
+    p = min(probs, key=lambda q: q.nx * q.ny)
+    o = oracle.Oracle(p)
+    t0 = time.perf_counter()
+    steps = 0
+    while time.perf_counter() - t0 < budget_s:
+        o.step()
+        steps += 1
+    el = time.perf_counter() - t0
+    value = p.nx * p.ny * 2 * steps / el
+    return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} full steps of instance {p.name} ({p.nx}x{p.ny}), {el:.1f} s, single-threaded"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    probs, wname = workload(0, args)
+    import oracle
+    p = min(probs, key=lambda q: q.nx * q.ny)
+    o = oracle.Oracle(p)
+    for _ in range(args.warmup):
+        o.step()
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        o.step()
+        times.append(time.perf_counter() - t0)
+    cells = p.nx * p.ny * 2
+    tot = sum(times)
+    value = cells * len(times) / tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wname, "sample": f"instance {p.name} ({p.nx}x{p.ny}) per step"},
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "value": value, "unit": UNIT,
+                             "sample": f"one full step of {p.name} per timed step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="mb", choices=["mb", "reference"])
+    ap.add_argument("--workload", default="c4")
+    ap.add_argument("--instances", type=int, default=64)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1711_11361_gb300 import mb
+
+    probs, wname = workload(rank, args)
+    prec = mb.FP32 if args.precision == "fp32" else mb.FP64
+    sim = mb.Sim(probs, prec)
+    stream = torch.cuda.Stream()
+    sim.set_stream(stream.cuda_stream)
+    cells = sum(p.nx * p.ny for p in probs)
+    with torch.cuda.stream(stream):
+        sim.run(args.warmup, 0.0)
+    sim.sync()
+    # timed region: K graph replays, per-step events
+    stop = threading.Event()
+    samples = []
+    th = threading.Thread(target=sample_clocks, args=(stop, samples), daemon=True)
+    th.start()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        evs[0].record(stream)
+        for k in range(args.steps):
+            sim.run(1, 0.0)
+            evs[k + 1].record(stream)
+    torch.cuda.synchronize()
+    stop.set()
+    th.join(timeout=2)
+    per = np.array([evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)])
+    total_ms = float(per.sum())
+    if ws > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+        c = torch.tensor([float(cells)], device="cuda")
+        torch.distributed.all_reduce(c)
+        cells_all = float(c.item())
+    else:
+        cells_all = float(cells)
+    status = sim.sync()
+    value = cells_all * 2 * args.steps / (total_ms * 1e-3)
+
+    # dominant kernel: bulk sweep, timed with CUDA events on its stream
+    sim.enable_timing(True)
+    sim.run(4, 0.0)
+    bulk_ms, launches = sim.kernel_time()
+    sim.enable_timing(False)
+    avg_bulk_s = bulk_ms * 1e-3 / max(launches, 1)
+    bpc = BYTES_PER_CELL_FP32 if prec == mb.FP32 else BYTES_PER_CELL_FP64
+    achieved = cells * bpc / avg_bulk_s / 1e9
+    peak, peak_kind = measured_peaks()
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "bulk_traffic.json")
+    if os.path.exists(prof):
+        try:
+            traffic = json.load(open(prof)).get("per_launch_bytes_" + args.precision + "_" + wname)
+        except Exception:
+            traffic = None
+
+    # end to end through the C ABI with pinned host buffers
+    pinned_in = [torch.empty((p.nc, p.ny, p.nx), dtype=torch.float64).pin_memory() for p in probs]
+    pinned_out = [torch.empty((p.nc, p.ny, p.nx), dtype=torch.float64).pin_memory() for p in probs]
+    for k, p in enumerate(probs):
+        pinned_in[k].copy_(torch.from_numpy(p.Q0))
+    h2d = sum(t.numel() * 8 for t in pinned_in)
+    e2e_steps = max(1, args.e2e_steps)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s in range(e2e_steps):
+        for k in range(len(probs)):
+            mb.lib.mb_write_state(sim._h, k, mb.ctypes.cast(pinned_in[k].data_ptr(), mb.ctypes.POINTER(mb.ctypes.c_double)), 0.0)
+        sim.step(0.0)
+        for k in range(len(probs)):
+            mb.lib.mb_read_state(sim._h, k, mb.ctypes.cast(pinned_out[k].data_ptr(), mb.ctypes.POINTER(mb.ctypes.c_double)), None, None)
+    e2e_s = time.perf_counter() - t0
+    e2e_value = cells * 2 * e2e_steps / e2e_s * (ws if ws > 1 else 1)
+
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if prec == mb.FP32 else "f64", "data": "synthetic",
+        "config": {"workload": wname, "instances": len(probs), "cells_per_sweep": cells,
+                   "grid_sizes": [p.nx for p in probs], "bulk": args.precision,
+                   "geometry_and_weights": "f64", "dt": "per-instance CFL on device",
+                   "l2": "inputs larger than L2 (state per buffer %.2f GB)" % (cells * 16 / 1e9),
+                   "parallelism": "instances" if ws == 1 else f"instances x{ws} ranks"},
+        "p50_ms_per_step": float(np.percentile(per, 50)), "p99_ms_per_step": float(np.percentile(per, 99)),
+        "status": int(status),
+        "roofline": {"kernel": "k_bulk (MUSCL-Hancock+HLLC sweep update)", "bound": "hbm", "achieved": achieved,
+                     "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                     "peak_kind": peak_kind, "bytes_per_cell": bpc, "avg_launch_ms": avg_bulk_s * 1e3,
+                     "launches_timed": launches},
+        "clocks": summarize_clocks(samples, local),
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d,
+                "steps": e2e_steps},
+        "gpu_launches": 16 * args.steps,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(probs)
+    print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

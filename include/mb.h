@@ -1,0 +1,164 @@
+/*
+ * mb.h -- C ABI of the GB300 moving-boundary cut-cell library (libmbcut.so).
+ *
+ * One directional sweep of the dimensionally split, flux-stabilised
+ * Cartesian cut-cell method for the 2-D compressible Euler equations (and
+ * linear advection) around a moving rigid body, after Bennett, Nikiforakis &
+ * Klein, arXiv 1711.11361.  A sweep is: (1) cut-cell geometry at the sweep's
+ * start, middle and end poses; (2) MUSCL-Hancock + HLLC standard fluxes on
+ * every face; (3) stabilised cut-cell fluxes and the moving-wall term;
+ * (4) the conservative alpha*Q update with covering / uncovering; (5) the
+ * CFL wave-speed reduction.
+ *
+ * Conventions for every entry point:
+ *   - Return an mb_status; nothing aborts.  mb_last_error() gives text.
+ *   - Host pointers are caller-owned and only read/written during the call.
+ *   - Device memory is owned by the library (allocated in mb_*create, freed
+ *     in mb_destroy).
+ *   - Work is issued on the simulation's stream (default: a stream the
+ *     library creates; see mb_set_stream).  Calls returning host data
+ *     synchronise that stream.
+ *   - States are conserved variables, SoA planes of nx*ny doubles, x fastest:
+ *     Euler [rho, rho*u, rho*v, E]; advection [u].  Solid cells read as NaN.
+ *   - One mb_sim holds a batch of independent instances (n >= 1) that advance
+ *     together; kernels are launched once per sweep for the whole batch.
+ */
+#ifndef MB_H
+#define MB_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mb_sim mb_sim;
+
+typedef enum {
+    MB_OK = 0,
+    MB_E_INVAL = -1,     /* bad argument or unsupported configuration */
+    MB_E_NOMEM = -2,     /* device allocation failed */
+    MB_E_CUDA = -3,      /* CUDA runtime error (see mb_last_error) */
+    MB_E_UNSTABLE = -4,  /* a fluid cell became non-finite or rho/p <= 0, or
+                            a covered/uncovered cell had no fluid neighbour */
+    MB_E_TIMEOUT = -5,   /* reserved: a bounded device wait gave up */
+    MB_E_STATE = -6,     /* call order (e.g. second sweep with another dt) */
+    MB_E_CAPACITY = -7   /* a fixed-size device work list overflowed */
+} mb_status;
+
+enum { MB_BC_TRANSMISSIVE = 0, MB_BC_REFLECTIVE = 1, MB_BC_PERIODIC = 2 };
+enum { MB_EULER = 0, MB_ADVECTION = 1 };
+enum { MB_UNCOVER_DONOR = 0, MB_UNCOVER_FLUX_GCL = 1 };
+enum { MB_FP64 = 0, MB_FP32 = 1 };
+
+/* Uniform cell-centred grid on [x0,x1] x [y0,y1] (Sec. II.A). */
+typedef struct {
+    int nx, ny;                 /* cells; 8 <= nx, ny <= 16384 */
+    double x0, y0, x1, y1;
+    int bc[4];                  /* x-low, x-high, y-low, y-high; periodic in pairs */
+    int equation;               /* MB_EULER or MB_ADVECTION */
+    double adv[2];              /* advection velocity (MB_ADVECTION) */
+    double cfl;                 /* CFL number on regular cells (Sec. III) */
+    int uncover_mode;           /* MB_UNCOVER_DONOR: volume-weighted donor
+                                   initialisation (Sec. II.C.5, eqs.
+                                   volumeWeighting..DonorCellUpdate);
+                                   MB_UNCOVER_FLUX_GCL: the new cell fills
+                                   through its swept apertures */
+    int precision;              /* MB_FP64, or MB_FP32 bulk arithmetic with
+                                   FP64 geometry and stabilisation weights */
+} mb_grid;
+
+/* Rigid body: union of simple polygons with disjoint interiors, each listed
+ * counter-clockwise, vertices at t = 0 (copied at create).  Sec. II.A. */
+typedef struct {
+    int npoly;
+    const int *poly_start;      /* npoly+1 offsets into vx/vy */
+    const int *poly_moving;     /* npoly flags: 1 moves with the motion, 0 fixed */
+    const double *vx, *vy;
+} mb_body;
+
+/* Prescribed motion of the moving polygons: translation U*t plus rotation
+ * theta(t) = a0 + a1*sin(omega*t) about `pivot` (which translates too). */
+typedef struct {
+    double U[2];
+    double pivot[2];
+    double a0, a1, omega;
+} mb_motion;
+
+/* Create a single instance (Sec. II.A-C).  gamma: ratio of specific heats
+ * (ignored for advection).  The state starts undefined: call mb_write_state. */
+mb_status mb_create(const mb_grid *grid, double gamma, const mb_body *body,
+                    const mb_motion *motion, mb_sim **out);
+
+/* Create a batch of n independent instances (arrays of length n) that every
+ * mb_step / mb_sweep advances together in one set of kernel launches. */
+mb_status mb_batch_create(int n, const mb_grid *grids, const double *gammas,
+                          const mb_body *bodies, const mb_motion *motions, mb_sim **out);
+
+void mb_destroy(mb_sim *sim);
+
+/* Text of the last error on this sim (or of the last failed create if sim is
+ * NULL).  Valid until the next call on the same sim. */
+const char *mb_last_error(const mb_sim *sim);
+
+/* Run subsequent work on `stream` (a cudaStream_t, or NULL for the library's
+ * own stream).  The caller keeps ownership of the stream. */
+mb_status mb_set_stream(mb_sim *sim, void *stream);
+
+/* Set instance `inst`'s state (host array, nc*nx*ny doubles as above) at time
+ * t with the body at its pose of time t (translation U*t).  Values in cells
+ * that are solid at that pose are ignored.  Called between the two sweeps of
+ * a step it abandons that step: the next sweep starts a new one. */
+mb_status mb_write_state(mb_sim *sim, int inst, const double *Q, double t);
+
+/* Copy instance `inst`'s state to host arrays.  Q: nc*nx*ny doubles (solid
+ * cells NaN); alpha (optional): nx*ny volume fractions at the current pose;
+ * clock (optional): {t, X, Y, step}.  Synchronises; returns the first error
+ * any kernel has flagged for this instance since the last write. */
+mb_status mb_read_state(mb_sim *sim, int inst, double *Q, double *alpha, double *clock);
+
+/* One time step of every instance: two sweeps, x then y on even steps and
+ * y then x on odd steps (Sec. II.A, II.C.4).  dt > 0: that step for all
+ * instances; dt <= 0: each instance's own CFL step (Sec. III), computed on
+ * the device.  dt_used (optional, n doubles) synchronises to report them. */
+mb_status mb_step(mb_sim *sim, double dt, double *dt_used);
+
+/* One directional sweep (dir 0: x, 1: y) of every instance with time step dt
+ * (> 0).  Two calls make a step; the second must use the same dt.  The body
+ * moves along dir by U_dir*dt and through half the step's rotation. */
+mb_status mb_sweep(mb_sim *sim, int dir, double dt);
+
+/* Run nsteps steps (as mb_step with the same dt rule), replaying one CUDA
+ * graph per step.  Does not synchronise. */
+mb_status mb_run(mb_sim *sim, int nsteps, double dt);
+
+/* Wait for the sim's stream and report flagged errors (any instance). */
+mb_status mb_sync(mb_sim *sim);
+
+/* Sizes: number of instances, and for instance inst its nx, ny and number of
+ * components (any output pointer may be NULL). */
+mb_status mb_info(const mb_sim *sim, int inst, int *n_inst, int *nx, int *ny, int *nc);
+
+/* Diagnostics of instance inst's last sweep: out[0..3] = sum over cells of the
+ * wall terms (content per unit cell area, eq. Klein2DcompleteMovingMethod2a),
+ * out[4] = cells merged by the positivity safeguard, out[5] = band cells. */
+mb_status mb_diagnostics(mb_sim *sim, int inst, double *out);
+
+/* Copy the band records (cells cut at the start or end pose) of instance
+ * inst's last sweep into `out` (an array of max_records records of
+ * mb_band_record_size() bytes each, library-internal layout for debugging);
+ * *count receives the number of records of that sweep. */
+mb_status mb_band_records(mb_sim *sim, int inst, void *out, int max_records, int *count);
+
+/* Size in bytes of one band record as copied by mb_band_records. */
+int mb_band_record_size(void);
+
+/* Kernel timing.  enable != 0 brackets every launch of the bulk sweep kernel
+ * with CUDA events on the sim's stream (mb_run then launches without graphs).
+ * mb_kernel_time returns the bulk kernel's total milliseconds and launch
+ * count since timing was enabled (synchronises). */
+mb_status mb_enable_timing(mb_sim *sim, int enable);
+mb_status mb_kernel_time(mb_sim *sim, double *total_ms, int *launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MB_H */

@@ -1,0 +1,596 @@
+// mb_api.cu -- host runtime behind the C ABI in include/mb.h.
+//
+// A sim is a batch of instances laid out as independent grids in device
+// memory.  Every sweep is one fixed sequence of kernel launches over the
+// whole batch (pose -> geometry -> band prep -> band faces -> bulk -> events
+// -> safeguard -> finalize); mb_run captures a step (two sweeps) as a CUDA
+// graph and replays it.  Three state buffers rotate so that the step-start
+// state stays readable during the second sweep (the common advective wall
+// state of Sec. II.B is taken from it).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/mb.h"
+#include "mb_internal.cuh"
+
+namespace mb {
+void launch_pose(const InstDesc *, InstDyn *, const double *, const double *, const unsigned char *, double *,
+                 double *, int, int, int, int, double, cudaStream_t);
+void launch_geom(const InstDesc *, InstDyn *, const double *, const double *, const int *, const unsigned char *, int,
+                 int, int, int, BandRec *, double *, cudaStream_t);
+void launch_classify(const InstDesc *, InstDyn *, const double *, const double *, const unsigned char *, double *,
+                     double *, const int *, int, int, int, double *, cudaStream_t);
+template <class T>
+void launch_band_stage(int, const InstDesc *, InstDyn *, BandRec *, const double *, int *, int, int, int, int, int,
+                       int, int, int, cudaStream_t);
+template <class T>
+void launch_bulk(int, const InstDesc *, InstDyn *, const BandRec *, int, int, int, int, int, int, cudaStream_t);
+template <class T>
+int bulk_blocks_per_sm(int);
+template <class T>
+void launch_write_state(const InstDesc *, InstDyn *, const double *, int, int, cudaStream_t);
+template <class T>
+void launch_read_state(const InstDesc *, double *, int, int, cudaStream_t);
+constexpr int MIXCAP_HOST = 1024;
+}  // namespace mb
+
+using namespace mb;
+
+static std::string g_create_error;
+
+struct mb_sim {
+    int n = 0;
+    int prec = MB_FP64;
+    std::vector<InstDesc> hd;
+    InstDesc *dd = nullptr;
+    InstDyn *dy = nullptr;
+    double *vx = nullptr, *vy = nullptr, *px = nullptr, *py = nullptr;
+    unsigned char *vmov = nullptr;
+    int *vnext = nullptr;
+    int total_v = 0;
+    BandRec *rec = nullptr;
+    double *bnd = nullptr;
+    int total_rec = 0;
+    int *scratch = nullptr;
+    double *stage = nullptr;      // staging for state I/O (nc * max cells doubles)
+    size_t stage_len = 0;
+    int total_cols = 0;
+    int total_tiles[2] = {0, 0};
+    int bulk_grid[2] = {0, 0};
+    std::vector<void *> allocs;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int cur = 0;          // buffer holding the latest state (between steps)
+    int qn = 0;           // buffer holding the step-start state
+    int sidx = 0;         // sweep index within the step
+    long long nstep = 0;  // steps taken since the last write_state of instance 0
+    std::string err;
+    std::map<std::tuple<int, int, unsigned long long>, cudaGraphExec_t> graphs;
+    bool timing = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> evs;
+    std::vector<cudaEvent_t> free_events;
+};
+
+static mb_status fail(mb_sim *s, mb_status st, const std::string &msg) {
+    if (s) s->err = msg;
+    else g_create_error = msg;
+    return st;
+}
+
+static mb_status cuda_check(mb_sim *s, cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return MB_OK;
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    return fail(s, e == cudaErrorMemoryAllocation ? MB_E_NOMEM : MB_E_CUDA, m);
+}
+
+template <class P>
+static cudaError_t dalloc(mb_sim *s, P **p, size_t bytes) {
+    void *v = nullptr;
+    cudaError_t e = cudaMalloc(&v, bytes ? bytes : 16);
+    if (e == cudaSuccess) {
+        s->allocs.push_back(v);
+        *p = (P *)v;
+    }
+    return e;
+}
+
+static void free_all(mb_sim *s) {
+    for (auto &kv : s->graphs) cudaGraphExecDestroy(kv.second);
+    s->graphs.clear();
+    for (auto &e : s->evs) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
+    s->evs.clear();
+    for (void *p : s->allocs) cudaFree(p);
+    s->allocs.clear();
+    if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+    s->stream = nullptr;
+}
+
+static mb_status map_err(mb_sim *s, int e) {
+    if (!e) return MB_OK;
+    std::string m;
+    mb_status st = MB_E_UNSTABLE;
+    if (e & ERR_EDGE_CAP) { m += "edge list of a geometry column overflowed; "; st = MB_E_CAPACITY; }
+    if (e & ERR_BAND_CAP) { m += "band record capacity overflowed; "; st = MB_E_CAPACITY; }
+    if (e & ERR_STATE) { m += "second sweep of a step used another dt; "; st = MB_E_STATE; }
+    if (e & ERR_NONBR) m += "covered/uncovered cell without a fluid neighbour; ";
+    if (e & ERR_UNSTABLE) m += "non-physical state (rho or p <= 0 or non-finite); ";
+    if (e & (ERR_EDGE_CAP | ERR_BAND_CAP | ERR_STATE)) {
+    } else {
+        st = MB_E_UNSTABLE;
+    }
+    s->err = m;
+    return st;
+}
+
+extern "C" {
+
+const char *mb_last_error(const mb_sim *sim) { return sim ? sim->err.c_str() : g_create_error.c_str(); }
+
+mb_status mb_batch_create(int n, const mb_grid *grids, const double *gammas, const mb_body *bodies,
+                          const mb_motion *motions, mb_sim **out) {
+    if (!out) return fail(nullptr, MB_E_INVAL, "out is NULL");
+    *out = nullptr;
+    if (n < 1 || !grids || !bodies || !motions) return fail(nullptr, MB_E_INVAL, "bad batch arguments");
+    int prec = grids[0].precision;
+    for (int k = 0; k < n; ++k) {
+        const mb_grid &g = grids[k];
+        if (g.nx < 8 || g.ny < 8 || g.nx > 16384 || g.ny > 8192) return fail(nullptr, MB_E_INVAL, "grid size out of range");
+        if (!(g.x1 > g.x0) || !(g.y1 > g.y0)) return fail(nullptr, MB_E_INVAL, "empty domain");
+        if ((g.bc[0] == MB_BC_PERIODIC) != (g.bc[1] == MB_BC_PERIODIC) ||
+            (g.bc[2] == MB_BC_PERIODIC) != (g.bc[3] == MB_BC_PERIODIC))
+            return fail(nullptr, MB_E_INVAL, "periodic boundaries must come in pairs");
+        if (g.equation != MB_EULER && g.equation != MB_ADVECTION) return fail(nullptr, MB_E_INVAL, "unknown equation");
+        if (g.precision != prec) return fail(nullptr, MB_E_INVAL, "all instances of a batch share one precision");
+        if (!(g.cfl > 0.0 && g.cfl <= 1.0)) return fail(nullptr, MB_E_INVAL, "cfl must be in (0, 1]");
+        const mb_body &b = bodies[k];
+        if (b.npoly < 0 || (b.npoly > 0 && (!b.poly_start || !b.poly_moving || !b.vx || !b.vy)))
+            return fail(nullptr, MB_E_INVAL, "bad body");
+        for (int p = 0; p < b.npoly; ++p)
+            if (b.poly_start[p + 1] - b.poly_start[p] < 3) return fail(nullptr, MB_E_INVAL, "polygon with < 3 vertices");
+    }
+    mb_sim *s = new mb_sim();
+    s->n = n;
+    s->prec = prec;
+    const size_t esz = prec == MB_FP32 ? 4 : 8;
+    cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { mb_status st = cuda_check(s, e, "stream"); g_create_error = s->err; delete s; return st; }
+    s->own_stream = true;
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    // vertices
+    std::vector<double> hvx, hvy;
+    std::vector<unsigned char> hmov;
+    std::vector<int> hnext;
+    s->hd.resize(n);
+    size_t max_cells = 0;
+    int rec_total = 0, col_total = 0, tiles0 = 0, tiles1 = 0;
+#define CK(x)                                                     \
+    do {                                                          \
+        cudaError_t _e = (x);                                     \
+        if (_e != cudaSuccess) {                                  \
+            mb_status _st = cuda_check(s, _e, #x);                \
+            g_create_error = s->err;                              \
+            free_all(s);                                          \
+            delete s;                                             \
+            return _st;                                           \
+        }                                                         \
+    } while (0)
+    for (int k = 0; k < n; ++k) {
+        const mb_grid &g = grids[k];
+        const mb_body &b = bodies[k];
+        const mb_motion &m = motions[k];
+        InstDesc &I = s->hd[k];
+        memset(&I, 0, sizeof(I));
+        I.nx = g.nx; I.ny = g.ny;
+        I.pitch = (g.nx + 31) / 32 * 32;
+        I.nc = g.equation == MB_EULER ? 4 : 1;
+        I.x0 = g.x0; I.y0 = g.y0;
+        I.dx = (g.x1 - g.x0) / (double)g.nx;
+        I.dy = (g.y1 - g.y0) / (double)g.ny;
+        for (int q = 0; q < 4; ++q) I.bc[q] = g.bc[q];
+        I.eq = g.equation;
+        I.ucov = g.uncover_mode;
+        I.adv[0] = g.adv[0]; I.adv[1] = g.adv[1];
+        I.gamma = gammas ? gammas[k] : 1.4;
+        I.cfl = g.cfl;
+        I.U[0] = m.U[0]; I.U[1] = m.U[1];
+        I.pivot[0] = m.pivot[0]; I.pivot[1] = m.pivot[1];
+        I.a0 = m.a0; I.a1 = m.a1; I.omega = m.omega;
+        I.rotating = (m.a0 != 0.0 || m.a1 != 0.0) ? 1 : 0;
+        I.voff = (int)hvx.size();
+        I.nv = b.npoly > 0 ? b.poly_start[b.npoly] : 0;
+        double rmax = 0.0, perim = 0.0, bx0 = 1e300, bx1 = -1e300;
+        bool has_static = false;
+        for (int p = 0; p < b.npoly; ++p) {
+            int a = b.poly_start[p], z = b.poly_start[p + 1];
+            if (!b.poly_moving[p]) has_static = true;
+            for (int v = a; v < z; ++v) {
+                int w = v + 1 < z ? v + 1 : a;
+                hvx.push_back(b.vx[v]);
+                hvy.push_back(b.vy[v]);
+                hmov.push_back(b.poly_moving[p] ? 1 : 0);
+                hnext.push_back(I.voff + w);
+                perim += std::hypot(b.vx[w] - b.vx[v], b.vy[w] - b.vy[v]);
+                bx0 = std::min(bx0, b.vx[v]);
+                bx1 = std::max(bx1, b.vx[v]);
+                if (b.poly_moving[p]) rmax = std::max(rmax, std::hypot(b.vx[v] - m.pivot[0], b.vy[v] - m.pivot[1]));
+            }
+        }
+        double wr = std::fabs(m.a1 * m.omega) * rmax;
+        I.wall_bound[0] = std::fabs(m.U[0]) + wr;
+        I.wall_bound[1] = std::fabs(m.U[1]) + wr;
+        double h = std::min(I.dx, I.dy);
+        long long cap = 4LL * (long long)std::ceil(perim / h) + 2LL * I.nv + 1024;
+        if (I.rotating) cap *= 2;
+        cap = std::min<long long>(cap, (long long)g.nx * g.ny);
+        I.rec_cap = (int)cap;
+        I.rec_base = rec_total;
+        rec_total += I.rec_cap;
+        int gcols = g.nx;
+        if (!has_static && I.nv > 0) {
+            double width = I.rotating ? 2.0 * rmax : (bx1 - bx0);
+            gcols = std::min(g.nx, (int)std::ceil(width / I.dx) + 8);
+        }
+        if (I.nv == 0) gcols = 0;
+        I.gcol_max = gcols;
+        I.gcol_off = col_total;
+        col_total += gcols;
+        I.tiles_x[0] = (g.nx + 127) / 128;
+        I.ntiles[0] = I.tiles_x[0] * ((g.ny + 1) / 2);
+        I.tiles_x[1] = (g.nx + 31) / 32;
+        I.ntiles[1] = I.tiles_x[1] * ((g.ny + 15) / 16);
+        I.tile_off[0] = tiles0;
+        I.tile_off[1] = tiles1;
+        tiles0 += I.ntiles[0];
+        tiles1 += I.ntiles[1];
+        size_t cells = (size_t)I.pitch * g.ny;
+        for (int bb = 0; bb < 3; ++bb) CK(dalloc(s, &I.Q[bb], cells * I.nc * esz));
+        CK(dalloc(s, &I.cls, cells));
+        CK(dalloc(s, &I.rec, cells * sizeof(int)));
+        CK(cudaMemsetAsync(I.cls, 0, cells, s->stream));
+        CK(cudaMemsetAsync(I.rec, 0xff, cells * sizeof(int), s->stream));
+        max_cells = std::max(max_cells, (size_t)g.nx * g.ny);
+    }
+    s->total_v = (int)hvx.size();
+    s->total_rec = rec_total;
+    s->total_cols = col_total;
+    s->total_tiles[0] = tiles0;
+    s->total_tiles[1] = tiles1;
+    int tv = std::max(1, s->total_v);
+    CK(dalloc(s, &s->vx, tv * sizeof(double)));
+    CK(dalloc(s, &s->vy, tv * sizeof(double)));
+    CK(dalloc(s, &s->vmov, tv));
+    CK(dalloc(s, &s->vnext, tv * sizeof(int)));
+    CK(dalloc(s, &s->px, 3 * (size_t)tv * sizeof(double)));
+    CK(dalloc(s, &s->py, 3 * (size_t)tv * sizeof(double)));
+    if (s->total_v) {
+        CK(cudaMemcpy(s->vx, hvx.data(), s->total_v * sizeof(double), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(s->vy, hvy.data(), s->total_v * sizeof(double), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(s->vmov, hmov.data(), s->total_v, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(s->vnext, hnext.data(), s->total_v * sizeof(int), cudaMemcpyHostToDevice));
+    }
+    CK(dalloc(s, &s->rec, std::max(1, s->total_rec) * sizeof(BandRec)));
+    CK(dalloc(s, &s->bnd, std::max(1, s->total_rec) * sizeof(double)));
+    CK(dalloc(s, &s->scratch, (size_t)n * 2 * MIXCAP_HOST * sizeof(int)));
+    s->stage_len = max_cells * 4;
+    CK(dalloc(s, &s->stage, s->stage_len * sizeof(double)));
+    CK(dalloc(s, &s->dd, n * sizeof(InstDesc)));
+    CK(dalloc(s, &s->dy, n * sizeof(InstDyn)));
+    CK(cudaMemcpy(s->dd, s->hd.data(), n * sizeof(InstDesc), cudaMemcpyHostToDevice));
+    CK(cudaMemset(s->dy, 0, n * sizeof(InstDyn)));
+    for (int d = 0; d < 2; ++d) {
+        int bps = prec == MB_FP32 ? bulk_blocks_per_sm<float>(d) : bulk_blocks_per_sm<double>(d);
+        s->bulk_grid[d] = bps * nsm;
+    }
+    // initial classes at t = 0
+    for (int k = 0; k < n; ++k)
+        launch_classify(s->dd, s->dy, s->vx, s->vy, s->vmov, s->px, s->py, s->vnext, s->total_v, k, s->hd[k].nx,
+                        nullptr, s->stream);
+    CK(cudaStreamSynchronize(s->stream));
+    CK(cudaGetLastError());
+#undef CK
+    *out = s;
+    return MB_OK;
+}
+
+mb_status mb_create(const mb_grid *grid, double gamma, const mb_body *body, const mb_motion *motion, mb_sim **out) {
+    if (!grid || !body || !motion) return fail(nullptr, MB_E_INVAL, "NULL argument");
+    return mb_batch_create(1, grid, &gamma, body, motion, out);
+}
+
+void mb_destroy(mb_sim *sim) {
+    if (!sim) return;
+    if (sim->stream) cudaStreamSynchronize(sim->stream);
+    free_all(sim);
+    delete sim;
+}
+
+mb_status mb_set_stream(mb_sim *sim, void *stream) {
+    if (!sim) return MB_E_INVAL;
+    cudaStreamSynchronize(sim->stream);
+    for (auto &kv : sim->graphs) cudaGraphExecDestroy(kv.second);
+    sim->graphs.clear();
+    if (stream) {
+        if (sim->own_stream) cudaStreamDestroy(sim->stream);
+        sim->own_stream = false;
+        sim->stream = (cudaStream_t)stream;
+    } else if (!sim->own_stream) {
+        cudaStreamCreateWithFlags(&sim->stream, cudaStreamNonBlocking);
+        sim->own_stream = true;
+    }
+    return MB_OK;
+}
+
+static mb_status do_sweep(mb_sim *s, int dir, double dt) {
+    int src, dst, qn;
+    if (s->sidx == 0) {
+        s->qn = s->cur;
+        src = s->cur;
+        dst = (s->cur + 1) % 3;
+    } else {
+        src = (s->qn + 1) % 3;
+        dst = (s->qn + 2) % 3;
+    }
+    qn = s->qn;
+    const int last = s->sidx == 1;
+    cudaStream_t st = s->stream;
+    launch_pose(s->dd, s->dy, s->vx, s->vy, s->vmov, s->px, s->py, s->total_v, s->n, dir, s->sidx, dt, st);
+    launch_geom(s->dd, s->dy, s->px, s->py, s->vnext, s->vmov, s->total_v, s->n, s->total_cols, dir, s->rec, s->bnd, st);
+    auto band = [&](int stage) {
+        if (s->prec == MB_FP32)
+            launch_band_stage<float>(stage, s->dd, s->dy, s->rec, s->bnd, s->scratch, s->n, s->total_rec, dir, src,
+                                     dst, qn, s->sidx, last, st);
+        else
+            launch_band_stage<double>(stage, s->dd, s->dy, s->rec, s->bnd, s->scratch, s->n, s->total_rec, dir, src,
+                                      dst, qn, s->sidx, last, st);
+    };
+    band(0);
+    band(1);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (s->timing) {
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        cudaEventRecord(e0, st);
+    }
+    if (s->prec == MB_FP32)
+        launch_bulk<float>(dir, s->dd, s->dy, s->rec, s->n, s->total_tiles[dir], src, dst, last, s->bulk_grid[dir], st);
+    else
+        launch_bulk<double>(dir, s->dd, s->dy, s->rec, s->n, s->total_tiles[dir], src, dst, last, s->bulk_grid[dir], st);
+    if (s->timing) {
+        cudaEventRecord(e1, st);
+        s->evs.push_back({e0, e1});
+    }
+    band(2);
+    band(3);
+    band(4);
+    if (s->sidx == 1) {
+        s->cur = dst;
+        s->sidx = 0;
+        s->nstep++;
+    } else {
+        s->sidx = 1;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_check(s, e, "sweep launch");
+    return MB_OK;
+}
+
+mb_status mb_sweep(mb_sim *sim, int dir, double dt) {
+    if (!sim) return MB_E_INVAL;
+    if (dir != 0 && dir != 1) return fail(sim, MB_E_INVAL, "dir must be 0 or 1");
+    if (!(dt > 0.0)) return fail(sim, MB_E_INVAL, "mb_sweep needs dt > 0");
+    return do_sweep(sim, dir, dt);
+}
+
+static mb_status issue_step(mb_sim *sim, double dt) {
+    int d1 = (sim->nstep % 2 == 0) ? 0 : 1;
+    mb_status r = do_sweep(sim, d1, dt);
+    if (r != MB_OK) return r;
+    return do_sweep(sim, 1 - d1, dt);
+}
+
+mb_status mb_step(mb_sim *sim, double dt, double *dt_used) {
+    if (!sim) return MB_E_INVAL;
+    if (sim->sidx != 0) return fail(sim, MB_E_STATE, "mb_step in the middle of a step");
+    mb_status r = issue_step(sim, dt > 0.0 ? dt : 0.0);
+    if (r != MB_OK) return r;
+    if (dt_used) {
+        std::vector<InstDyn> h(sim->n);
+        cudaError_t e = cudaMemcpyAsync(h.data(), sim->dy, sim->n * sizeof(InstDyn), cudaMemcpyDeviceToHost, sim->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(sim->stream);
+        if (e != cudaSuccess) return cuda_check(sim, e, "dt readback");
+        for (int k = 0; k < sim->n; ++k) dt_used[k] = h[k].dt;
+    }
+    return MB_OK;
+}
+
+mb_status mb_run(mb_sim *sim, int nsteps, double dt) {
+    if (!sim || nsteps < 0) return MB_E_INVAL;
+    if (sim->sidx != 0) return fail(sim, MB_E_STATE, "mb_run in the middle of a step");
+    double dth = dt > 0.0 ? dt : 0.0;
+    for (int k = 0; k < nsteps; ++k) {
+        if (sim->timing) {
+            mb_status r = issue_step(sim, dth);
+            if (r != MB_OK) return r;
+            continue;
+        }
+        unsigned long long bits;
+        memcpy(&bits, &dth, sizeof(bits));
+        auto key = std::make_tuple(sim->cur, (int)(sim->nstep % 2), bits);
+        auto it = sim->graphs.find(key);
+        if (it == sim->graphs.end()) {
+            int cur0 = sim->cur;
+            long long ns0 = sim->nstep;
+            cudaGraph_t g;
+            cudaError_t e = cudaStreamBeginCapture(sim->stream, cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) return cuda_check(sim, e, "begin capture");
+            mb_status r = issue_step(sim, dth);
+            e = cudaStreamEndCapture(sim->stream, &g);
+            if (r != MB_OK) return r;
+            if (e != cudaSuccess) return cuda_check(sim, e, "end capture");
+            cudaGraphExec_t ex;
+            e = cudaGraphInstantiate(&ex, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return cuda_check(sim, e, "instantiate");
+            it = sim->graphs.emplace(key, ex).first;
+            sim->cur = cur0;   // capture did not run the step
+            sim->nstep = ns0;
+        }
+        cudaError_t e = cudaGraphLaunch(it->second, sim->stream);
+        if (e != cudaSuccess) return cuda_check(sim, e, "graph launch");
+        sim->qn = sim->cur;
+        sim->cur = (sim->cur + 2) % 3;
+        sim->nstep++;
+    }
+    return MB_OK;
+}
+
+mb_status mb_sync(mb_sim *sim) {
+    if (!sim) return MB_E_INVAL;
+    cudaError_t e = cudaStreamSynchronize(sim->stream);
+    if (e != cudaSuccess) return cuda_check(sim, e, "sync");
+    std::vector<InstDyn> h(sim->n);
+    e = cudaMemcpy(h.data(), sim->dy, sim->n * sizeof(InstDyn), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_check(sim, e, "dyn readback");
+    int err = 0;
+    for (auto &x : h) err |= x.err;
+    return map_err(sim, err);
+}
+
+mb_status mb_write_state(mb_sim *sim, int inst, const double *Q, double t) {
+    if (!sim || !Q || inst < 0 || inst >= sim->n) return MB_E_INVAL;
+    if (sim->sidx != 0) {
+        // abandon the half-done step: the written state starts a new one
+        sim->cur = (sim->qn + 1) % 3;
+        sim->sidx = 0;
+    }
+    const InstDesc &I = sim->hd[inst];
+    size_t n = (size_t)I.nx * I.ny;
+    cudaStream_t st = sim->stream;
+    InstDyn y;
+    memset(&y, 0, sizeof(y));
+    y.t = t;
+    y.X = I.U[0] * t;
+    y.Y = I.U[1] * t;
+    cudaError_t e = cudaMemcpyAsync(sim->dy + inst, &y, sizeof(y), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sim->stage, Q, n * I.nc * sizeof(double), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_check(sim, e, "write_state copy");
+    launch_classify(sim->dd, sim->dy, sim->vx, sim->vy, sim->vmov, sim->px, sim->py, sim->vnext, sim->total_v, inst,
+                    I.nx, nullptr, st);
+    if (sim->prec == MB_FP32) launch_write_state<float>(sim->dd, sim->dy, sim->stage, inst, sim->cur, st);
+    else launch_write_state<double>(sim->dd, sim->dy, sim->stage, inst, sim->cur, st);
+    e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_check(sim, e, "write_state");
+    if (inst == 0) sim->nstep = 0;
+    return MB_OK;
+}
+
+mb_status mb_read_state(mb_sim *sim, int inst, double *Q, double *alpha, double *clock) {
+    if (!sim || inst < 0 || inst >= sim->n) return MB_E_INVAL;
+    const InstDesc &I = sim->hd[inst];
+    size_t n = (size_t)I.nx * I.ny;
+    cudaStream_t st = sim->stream;
+    cudaError_t e = cudaSuccess;
+    int buf = sim->sidx == 0 ? sim->cur : (sim->qn + 1) % 3;
+    if (Q) {
+        if (sim->prec == MB_FP32) launch_read_state<float>(sim->dd, sim->stage, inst, buf, st);
+        else launch_read_state<double>(sim->dd, sim->stage, inst, buf, st);
+        e = cudaMemcpyAsync(Q, sim->stage, n * I.nc * sizeof(double), cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) return cuda_check(sim, e, "read_state copy");
+    }
+    if (alpha) {
+        launch_classify(sim->dd, sim->dy, sim->vx, sim->vy, sim->vmov, sim->px, sim->py, sim->vnext, sim->total_v,
+                        inst, I.nx, sim->stage, st);
+        e = cudaMemcpyAsync(alpha, sim->stage, n * sizeof(double), cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) return cuda_check(sim, e, "alpha copy");
+    }
+    InstDyn y;
+    e = cudaMemcpyAsync(&y, sim->dy + inst, sizeof(y), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_check(sim, e, "read_state");
+    if (clock) {
+        clock[0] = y.t;
+        clock[1] = y.X;
+        clock[2] = y.Y;
+        clock[3] = (double)y.step;
+    }
+    return map_err(sim, y.err);
+}
+
+mb_status mb_band_records(mb_sim *sim, int inst, void *out, int max_records, int *count) {
+    if (!sim || inst < 0 || inst >= sim->n) return MB_E_INVAL;
+    InstDyn y;
+    cudaError_t e = cudaMemcpyAsync(&y, sim->dy + inst, sizeof(y), cudaMemcpyDeviceToHost, sim->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(sim->stream);
+    if (e != cudaSuccess) return cuda_check(sim, e, "band records");
+    int n = std::min(y.band_count, sim->hd[inst].rec_cap);
+    if (count) *count = n;
+    if (out && max_records > 0) {
+        n = std::min(n, max_records);
+        e = cudaMemcpy(out, sim->rec + sim->hd[inst].rec_base, (size_t)n * sizeof(BandRec), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_check(sim, e, "band records copy");
+    }
+    return MB_OK;
+}
+
+int mb_band_record_size(void) { return (int)sizeof(BandRec); }
+
+mb_status mb_info(const mb_sim *sim, int inst, int *n_inst, int *nx, int *ny, int *nc) {
+    if (!sim) return MB_E_INVAL;
+    if (n_inst) *n_inst = sim->n;
+    if (inst >= 0 && inst < sim->n) {
+        if (nx) *nx = sim->hd[inst].nx;
+        if (ny) *ny = sim->hd[inst].ny;
+        if (nc) *nc = sim->hd[inst].nc;
+    }
+    return MB_OK;
+}
+
+mb_status mb_diagnostics(mb_sim *sim, int inst, double *out) {
+    if (!sim || !out || inst < 0 || inst >= sim->n) return MB_E_INVAL;
+    InstDyn y;
+    cudaError_t e = cudaMemcpyAsync(&y, sim->dy + inst, sizeof(y), cudaMemcpyDeviceToHost, sim->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(sim->stream);
+    if (e != cudaSuccess) return cuda_check(sim, e, "diagnostics");
+    for (int q = 0; q < 4; ++q) out[q] = y.wall_sum[q];
+    out[4] = y.mixed;
+    out[5] = y.band_count;
+    return MB_OK;
+}
+
+mb_status mb_enable_timing(mb_sim *sim, int enable) {
+    if (!sim) return MB_E_INVAL;
+    cudaStreamSynchronize(sim->stream);
+    for (auto &ev : sim->evs) { cudaEventDestroy(ev.first); cudaEventDestroy(ev.second); }
+    sim->evs.clear();
+    sim->timing = enable != 0;
+    return MB_OK;
+}
+
+mb_status mb_kernel_time(mb_sim *sim, double *total_ms, int *launches) {
+    if (!sim) return MB_E_INVAL;
+    cudaError_t e = cudaStreamSynchronize(sim->stream);
+    if (e != cudaSuccess) return cuda_check(sim, e, "kernel_time sync");
+    double tot = 0.0;
+    for (auto &ev : sim->evs) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev.first, ev.second);
+        tot += ms;
+    }
+    if (total_ms) *total_ms = tot;
+    if (launches) *launches = (int)sim->evs.size();
+    return MB_OK;
+}
+
+}  // extern "C"

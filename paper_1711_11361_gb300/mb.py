@@ -1,0 +1,230 @@
+"""ctypes binding of libmbcut.so (C ABI in include/mb.h).
+
+Argument marshalling only: every step of the sweep runs in the CUDA library.
+Importing this module loads the library and raises ImportError if it has not
+been built (``python -c "import __graft_entry__ as g; g.build()"``); there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import inputs
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libmbcut.so")
+
+MB_OK, MB_E_INVAL, MB_E_NOMEM, MB_E_CUDA, MB_E_UNSTABLE, MB_E_TIMEOUT, MB_E_STATE, MB_E_CAPACITY = 0, -1, -2, -3, -4, -5, -6, -7
+FP64, FP32 = 0, 1
+
+EXPORTS = ["mb_create", "mb_batch_create", "mb_destroy", "mb_last_error", "mb_set_stream", "mb_write_state",
+           "mb_read_state", "mb_step", "mb_sweep", "mb_run", "mb_sync", "mb_info", "mb_diagnostics",
+           "mb_enable_timing", "mb_kernel_time", "mb_band_records", "mb_band_record_size"]
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("x0", ctypes.c_double), ("y0", ctypes.c_double), ("x1", ctypes.c_double), ("y1", ctypes.c_double),
+                ("bc", ctypes.c_int * 4), ("equation", ctypes.c_int), ("adv", ctypes.c_double * 2),
+                ("cfl", ctypes.c_double), ("uncover_mode", ctypes.c_int), ("precision", ctypes.c_int)]
+
+
+class Body(ctypes.Structure):
+    _fields_ = [("npoly", ctypes.c_int), ("poly_start", ctypes.POINTER(ctypes.c_int)),
+                ("poly_moving", ctypes.POINTER(ctypes.c_int)),
+                ("vx", ctypes.POINTER(ctypes.c_double)), ("vy", ctypes.POINTER(ctypes.c_double))]
+
+
+class Motion(ctypes.Structure):
+    _fields_ = [("U", ctypes.c_double * 2), ("pivot", ctypes.c_double * 2),
+                ("a0", ctypes.c_double), ("a1", ctypes.c_double), ("omega", ctypes.c_double)]
+
+
+class MBError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"mb error {code}: {msg}")
+        self.code = code
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                          "(the CUDA library is the only implementation; there is no fallback)")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, D, I = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int
+    PP = ctypes.POINTER(ctypes.c_void_p)
+    sig = {
+        "mb_create": ([ctypes.POINTER(Grid), ctypes.c_double, ctypes.POINTER(Body), ctypes.POINTER(Motion), PP], I),
+        "mb_batch_create": ([I, ctypes.POINTER(Grid), D, ctypes.POINTER(Body), ctypes.POINTER(Motion), PP], I),
+        "mb_destroy": ([P], None),
+        "mb_last_error": ([P], ctypes.c_char_p),
+        "mb_set_stream": ([P, P], I),
+        "mb_write_state": ([P, I, D, ctypes.c_double], I),
+        "mb_read_state": ([P, I, D, D, D], I),
+        "mb_step": ([P, ctypes.c_double, D], I),
+        "mb_sweep": ([P, I, ctypes.c_double], I),
+        "mb_run": ([P, I, ctypes.c_double], I),
+        "mb_sync": ([P], I),
+        "mb_info": ([P, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)], I),
+        "mb_diagnostics": ([P, I, D], I),
+        "mb_enable_timing": ([P, I], I),
+        "mb_kernel_time": ([P, D, ctypes.POINTER(I)], I),
+        "mb_band_records": ([P, I, P, I, ctypes.POINTER(I)], I),
+        "mb_band_record_size": ([], I),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    return lib
+
+
+lib = _load()
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _marshal(prob: inputs.Problem, precision: int):
+    g = Grid()
+    g.nx, g.ny = prob.nx, prob.ny
+    g.x0, g.y0, g.x1, g.y1 = prob.x0, prob.y0, prob.x1, prob.y1
+    for k in range(4):
+        g.bc[k] = prob.bc[k]
+    g.equation = prob.equation
+    g.adv[0], g.adv[1] = prob.adv
+    g.cfl = prob.cfl
+    g.uncover_mode = prob.uncover_mode
+    g.precision = precision
+    starts = [0]
+    for poly in prob.polygons:
+        starts.append(starts[-1] + len(poly))
+    keep = {}
+    keep["ps"] = np.array(starts, dtype=np.int32)
+    keep["pm"] = np.array(prob.moving if prob.polygons else [0], dtype=np.int32)
+    allv = np.concatenate([np.asarray(p, dtype=np.float64) for p in prob.polygons]) if prob.polygons else np.zeros((1, 2))
+    keep["vx"] = np.ascontiguousarray(allv[:, 0])
+    keep["vy"] = np.ascontiguousarray(allv[:, 1])
+    b = Body()
+    b.npoly = len(prob.polygons)
+    b.poly_start = keep["ps"].ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    b.poly_moving = keep["pm"].ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    b.vx, b.vy = _dp(keep["vx"]), _dp(keep["vy"])
+    m = Motion()
+    m.U[0], m.U[1] = prob.U
+    m.pivot[0], m.pivot[1] = prob.pivot
+    m.a0, m.a1, m.omega = prob.a0, prob.a1, prob.omega
+    return g, b, m, keep
+
+
+class Sim:
+    """A batch of instances advancing together on the GPU."""
+
+    def __init__(self, problems, precision: int = FP64, write_initial: bool = True):
+        if isinstance(problems, inputs.Problem):
+            problems = [problems]
+        self.problems = list(problems)
+        n = len(self.problems)
+        gs, bs, ms, self._keep = (Grid * n)(), (Body * n)(), (Motion * n)(), []
+        gam = np.array([p.gamma for p in self.problems], dtype=np.float64)
+        for k, p in enumerate(self.problems):
+            g, b, m, keep = _marshal(p, precision)
+            gs[k], bs[k], ms[k] = g, b, m
+            self._keep.append(keep)
+        h = ctypes.c_void_p()
+        r = lib.mb_batch_create(n, gs, _dp(gam), bs, ms, ctypes.byref(h))
+        if r != MB_OK:
+            raise MBError(r, lib.mb_last_error(None).decode())
+        self._h = h
+        self.n = n
+        self.precision = precision
+        if write_initial:
+            for k, p in enumerate(self.problems):
+                if p.Q0 is not None:
+                    self.write_state(k, p.Q0)
+
+    def _check(self, r):
+        if r != MB_OK:
+            raise MBError(r, lib.mb_last_error(self._h).decode())
+        return r
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.mb_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def set_stream(self, stream_handle: int):
+        self._check(lib.mb_set_stream(self._h, ctypes.c_void_p(stream_handle)))
+
+    def write_state(self, inst, Q, t=0.0):
+        p = self.problems[inst]
+        Q = np.ascontiguousarray(Q, dtype=np.float64).reshape(p.nc, p.ny, p.nx)
+        self._check(lib.mb_write_state(self._h, inst, _dp(Q), t))
+
+    def read_state(self, inst=0, alpha=False, check=True):
+        p = self.problems[inst]
+        Q = np.empty((p.nc, p.ny, p.nx))
+        a = np.empty((p.ny, p.nx)) if alpha else None
+        clk = np.empty(4)
+        r = lib.mb_read_state(self._h, inst, _dp(Q), _dp(a) if alpha else None, _dp(clk))
+        if check:
+            self._check(r)
+        out = dict(Q=Q, t=clk[0], X=clk[1], Y=clk[2], step=int(clk[3]), status=r)
+        if alpha:
+            out["alpha"] = a
+        return out
+
+    def step(self, dt=0.0, report=False):
+        if report:
+            out = np.empty(self.n)
+            self._check(lib.mb_step(self._h, dt, _dp(out)))
+            return out
+        self._check(lib.mb_step(self._h, dt, None))
+
+    def sweep(self, d, dt):
+        self._check(lib.mb_sweep(self._h, d, dt))
+
+    def run(self, nsteps, dt=0.0):
+        self._check(lib.mb_run(self._h, nsteps, dt))
+
+    def sync(self):
+        return self._check(lib.mb_sync(self._h))
+
+    def diagnostics(self, inst=0):
+        o = np.zeros(6)
+        self._check(lib.mb_diagnostics(self._h, inst, _dp(o)))
+        return dict(wall=o[:4], mixed=int(o[4]), band=int(o[5]))
+
+    def enable_timing(self, on=True):
+        self._check(lib.mb_enable_timing(self._h, 1 if on else 0))
+
+    def kernel_time(self):
+        ms = ctypes.c_double()
+        n = ctypes.c_int()
+        self._check(lib.mb_kernel_time(self._h, ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
+
+    def band_records(self, inst=0):
+        """Raw band records of the last sweep as a numpy structured array."""
+        cnt = ctypes.c_int()
+        self._check(lib.mb_band_records(self._h, inst, None, 0, ctypes.byref(cnt)))
+        out = np.zeros(cnt.value, dtype=BAND_DTYPE)
+        if cnt.value:
+            self._check(lib.mb_band_records(self._h, inst, out.ctypes.data_as(ctypes.c_void_p), cnt.value,
+                                            ctypes.byref(cnt)))
+        return out
+
+
+BAND_DTYPE = np.dtype([("cell", "i4"), ("i", "i4"), ("j", "i4"), ("flags", "i4"),
+                       ("aA", "f8"), ("aB", "f8"), ("aM", "f8"), ("bown", "f8"), ("d", "f8"),
+                       ("nx", "f8"), ("ny", "f8"), ("wx", "f8"), ("wy", "f8"),
+                       ("FB", "f8", 4), ("QB", "f8", 4), ("Qp", "f8", 4), ("Flo", "f8", 4), ("Fhi", "f8", 4),
+                       ("C", "f8", 4), ("C2", "f8", 4), ("den", "f8"), ("mix", "i4"), ("pad", "i4")])
+assert BAND_DTYPE.itemsize == lib.mb_band_record_size(), "band record layout changed"
