@@ -22,12 +22,13 @@
 #include "mb_internal.cuh"
 
 namespace mb {
-void launch_pose(const InstDesc *, InstDyn *, const double *, const double *, const unsigned char *, double *,
-                 double *, int, int, int, int, double, cudaStream_t);
-void launch_geom(const InstDesc *, InstDyn *, const double *, const double *, const int *, const unsigned char *, int,
-                 int, int, int, BandRec *, double *, cudaStream_t);
+void geom_init();
+void launch_pose(const InstDesc *, InstDyn *, const double *, const double *, const unsigned char *, const int *,
+                 double *, double *, float *, int, int, int, int, double, cudaStream_t);
+void launch_geom(const InstDesc *, InstDyn *, const double *, const double *, const float *, const int *,
+                 const unsigned char *, int, int, int, int, BandRec *, double *, cudaStream_t);
 void launch_classify(const InstDesc *, InstDyn *, const double *, const double *, const unsigned char *, double *,
-                     double *, const int *, int, int, int, double *, cudaStream_t);
+                     double *, float *, const int *, int, int, int, double *, cudaStream_t);
 template <class T>
 void launch_band_stage(int, const InstDesc *, InstDyn *, BandRec *, const double *, int *, int, int, int, int, int,
                        int, int, int, cudaStream_t);
@@ -53,6 +54,7 @@ struct mb_sim {
     InstDesc *dd = nullptr;
     InstDyn *dy = nullptr;
     double *vx = nullptr, *vy = nullptr, *px = nullptr, *py = nullptr;
+    float *ebox = nullptr;        // FP32 x-bounds of every edge at the three poses
     unsigned char *vmov = nullptr;
     int *vnext = nullptr;
     int total_v = 0;
@@ -256,6 +258,7 @@ mb_status mb_batch_create(int n, const mb_grid *grids, const double *gammas, con
         for (int bb = 0; bb < 3; ++bb) CK(dalloc(s, &I.Q[bb], cells * I.nc * esz));
         CK(dalloc(s, &I.cls, cells));
         CK(dalloc(s, &I.rec, cells * sizeof(int)));
+        CK(dalloc(s, &I.alpha, cells * sizeof(double)));
         CK(cudaMemsetAsync(I.cls, 0, cells, s->stream));
         CK(cudaMemsetAsync(I.rec, 0xff, cells * sizeof(int), s->stream));
         max_cells = std::max(max_cells, (size_t)g.nx * g.ny);
@@ -272,6 +275,8 @@ mb_status mb_batch_create(int n, const mb_grid *grids, const double *gammas, con
     CK(dalloc(s, &s->vnext, tv * sizeof(int)));
     CK(dalloc(s, &s->px, 3 * (size_t)tv * sizeof(double)));
     CK(dalloc(s, &s->py, 3 * (size_t)tv * sizeof(double)));
+    CK(dalloc(s, &s->ebox, 3 * (size_t)tv * 2 * sizeof(float)));
+    geom_init();
     if (s->total_v) {
         CK(cudaMemcpy(s->vx, hvx.data(), s->total_v * sizeof(double), cudaMemcpyHostToDevice));
         CK(cudaMemcpy(s->vy, hvy.data(), s->total_v * sizeof(double), cudaMemcpyHostToDevice));
@@ -293,8 +298,8 @@ mb_status mb_batch_create(int n, const mb_grid *grids, const double *gammas, con
     }
     // initial classes at t = 0
     for (int k = 0; k < n; ++k)
-        launch_classify(s->dd, s->dy, s->vx, s->vy, s->vmov, s->px, s->py, s->vnext, s->total_v, k, s->hd[k].nx,
-                        nullptr, s->stream);
+        launch_classify(s->dd, s->dy, s->vx, s->vy, s->vmov, s->px, s->py, s->ebox, s->vnext, s->total_v, k,
+                        s->hd[k].nx, nullptr, s->stream);
     CK(cudaStreamSynchronize(s->stream));
     CK(cudaGetLastError());
 #undef CK
@@ -343,8 +348,10 @@ static mb_status do_sweep(mb_sim *s, int dir, double dt) {
     qn = s->qn;
     const int last = s->sidx == 1;
     cudaStream_t st = s->stream;
-    launch_pose(s->dd, s->dy, s->vx, s->vy, s->vmov, s->px, s->py, s->total_v, s->n, dir, s->sidx, dt, st);
-    launch_geom(s->dd, s->dy, s->px, s->py, s->vnext, s->vmov, s->total_v, s->n, s->total_cols, dir, s->rec, s->bnd, st);
+    launch_pose(s->dd, s->dy, s->vx, s->vy, s->vmov, s->vnext, s->px, s->py, s->ebox, s->total_v, s->n, dir, s->sidx,
+                dt, st);
+    launch_geom(s->dd, s->dy, s->px, s->py, s->ebox, s->vnext, s->vmov, s->total_v, s->n, s->total_cols, dir, s->rec,
+                s->bnd, st);
     auto band = [&](int stage) {
         if (s->prec == MB_FP32)
             launch_band_stage<float>(stage, s->dd, s->dy, s->rec, s->bnd, s->scratch, s->n, s->total_rec, dir, src,
@@ -481,11 +488,12 @@ mb_status mb_write_state(mb_sim *sim, int inst, const double *Q, double t) {
     y.t = t;
     y.X = I.U[0] * t;
     y.Y = I.U[1] * t;
+    y.th = I.rotating ? I.a0 + I.a1 * std::sin(I.omega * t) : 0.0;
     cudaError_t e = cudaMemcpyAsync(sim->dy + inst, &y, sizeof(y), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(sim->stage, Q, n * I.nc * sizeof(double), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_check(sim, e, "write_state copy");
-    launch_classify(sim->dd, sim->dy, sim->vx, sim->vy, sim->vmov, sim->px, sim->py, sim->vnext, sim->total_v, inst,
-                    I.nx, nullptr, st);
+    launch_classify(sim->dd, sim->dy, sim->vx, sim->vy, sim->vmov, sim->px, sim->py, sim->ebox, sim->vnext,
+                    sim->total_v, inst, I.nx, nullptr, st);
     if (sim->prec == MB_FP32) launch_write_state<float>(sim->dd, sim->dy, sim->stage, inst, sim->cur, st);
     else launch_write_state<double>(sim->dd, sim->dy, sim->stage, inst, sim->cur, st);
     e = cudaStreamSynchronize(st);
@@ -509,8 +517,8 @@ mb_status mb_read_state(mb_sim *sim, int inst, double *Q, double *alpha, double 
         if (e != cudaSuccess) return cuda_check(sim, e, "read_state copy");
     }
     if (alpha) {
-        launch_classify(sim->dd, sim->dy, sim->vx, sim->vy, sim->vmov, sim->px, sim->py, sim->vnext, sim->total_v,
-                        inst, I.nx, sim->stage, st);
+        launch_classify(sim->dd, sim->dy, sim->vx, sim->vy, sim->vmov, sim->px, sim->py, sim->ebox, sim->vnext,
+                        sim->total_v, inst, I.nx, sim->stage, st);
         e = cudaMemcpyAsync(alpha, sim->stage, n * sizeof(double), cudaMemcpyDeviceToHost, st);
         if (e != cudaSuccess) return cuda_check(sim, e, "alpha copy");
     }

@@ -16,12 +16,27 @@
 namespace mb {
 
 constexpr int GEOM_WARPS = 4;
-constexpr int EMAX = 256;           // edges per column and pose
+constexpr int EMAX = 192;           // edges per column and pose
+constexpr int LMAX = 32;            // crossings per grid line of a column
 constexpr int MAXROWWORDS = 256;    // ny <= 8192
 
-struct EdgeBuf {
+// edges of one column at one pose, in polygon order
+struct GeoBuf {
     double xa[EMAX], ya[EMAX], xb[EMAX], yb[EMAX];
+    double ovl[EMAX];                 // x-overlap with the column
+    short jlo[EMAX], jhi[EMAX];       // rows the edge may meet (widened x-range)
     unsigned char mov[EMAX];
+    double lyc[2][LMAX];              // crossings of the grid lines x_l (0) and x_r (1)
+    signed char ls[2][LMAX];          // +1 edge runs to +x (body above), -1 otherwise
+    unsigned char lf[2][LMAX];        // bit0: crossing from the left, bit1: from the right
+    int lcnt[2];
+    int cnt;
+};
+
+struct GeoWarp {
+    GeoBuf G;
+    unsigned bA[MAXROWWORDS], bB[MAXROWWORDS], bM[MAXROWWORDS];
+    int wpre[MAXROWWORDS + 1];
 };
 
 __device__ __forceinline__ double dmin(double a, double b) { return a < b ? a : b; }
@@ -29,11 +44,13 @@ __device__ __forceinline__ double dmax(double a, double b) { return a > b ? a : 
 __device__ __forceinline__ double clamp01(double a) { return a < 0.0 ? 0.0 : (a > 1.0 ? 1.0 : a); }
 
 // ---------------------------------------------------------------------------
-// K0: time step, poses of the sweep, posed vertices, column range
+// K0: time step, poses of the sweep, posed vertices, conservative FP32 x
+// bounds of every edge, column and row range of the body
 // ---------------------------------------------------------------------------
 __global__ void k_pose(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y, const double *__restrict__ vx,
-                       const double *__restrict__ vy, const unsigned char *__restrict__ vmov, double *__restrict__ px,
-                       double *__restrict__ py, int total_v, int dir, int sidx, double dt_host) {
+                       const double *__restrict__ vy, const unsigned char *__restrict__ vmov,
+                       const int *__restrict__ vnext, double *__restrict__ px, double *__restrict__ py,
+                       float *__restrict__ ebox, int total_v, int dir, int sidx, double dt_host) {
     const int inst = blockIdx.x;
     const InstDesc &I = D[inst];
     InstDyn &y = Y[inst];
@@ -60,6 +77,8 @@ __global__ void k_pose(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y, 
             dt = y.dt;
             if (dt_host > 0.0 && dt_host != dt) y.err |= ERR_STATE;
         }
+        y.lam = dt / (dir == 0 ? I.dx : I.dy);
+        y.lamf = (float)y.lam;
         double tA = y.t + (sidx == 0 ? 0.0 : 0.5 * dt);
         double tB = y.t + (sidx == 0 ? 0.5 * dt : dt);
         double tM = y.t + (sidx == 0 ? 0.25 * dt : 0.75 * dt);
@@ -84,13 +103,14 @@ __global__ void k_pose(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y, 
         y.Om = Om;
         y.band_count = 0;
         y.nbad = 0;
+        y.nbadlist = 0;
         y.mixed = 0;
         for (int q = 0; q < MAXC; ++q) y.wall_sum[q] = 0.0;
         sh[0] = y.XA; sh[1] = y.YA; sh[2] = y.XM; sh[3] = y.YM; sh[4] = y.XB; sh[5] = y.YB;
         sh[6] = y.cA; sh[7] = y.sA; sh[8] = y.cM; sh[9] = y.sM; sh[10] = y.cB; sh[11] = y.sB;
     }
     __syncthreads();
-    double xmin = 1e300, xmax = -1e300;
+    double xmin = 1e300, xmax = -1e300, ymin = 1e300, ymax = -1e300;
     for (int k = threadIdx.x; k < I.nv; k += blockDim.x) {
         int a = I.voff + k;
         double x0 = vx[a], y0 = vy[a];
@@ -111,69 +131,55 @@ __global__ void k_pose(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y, 
             }
             px[(size_t)P * total_v + a] = xo;
             py[(size_t)P * total_v + a] = yo;
-            xmin = dmin(xmin, xo);
-            xmax = dmax(xmax, xo);
+            xmin = dmin(xmin, xo); xmax = dmax(xmax, xo);
+            ymin = dmin(ymin, yo); ymax = dmax(ymax, yo);
         }
     }
-    // block reduction of the x extent
+    __syncthreads();
+    // conservative FP32 x-range of every edge (rounded outward)
+    for (int k = threadIdx.x; k < I.nv; k += blockDim.x) {
+        int a = I.voff + k, b = vnext[a];
+        for (int P = 0; P < 3; ++P) {
+            double xa = px[(size_t)P * total_v + a], xb = px[(size_t)P * total_v + b];
+            ebox[((size_t)P * total_v + a) * 2] = __double2float_rd(dmin(xa, xb));
+            ebox[((size_t)P * total_v + a) * 2 + 1] = __double2float_ru(dmax(xa, xb));
+        }
+    }
     for (int o = 16; o > 0; o >>= 1) {
         xmin = dmin(xmin, __shfl_xor_sync(0xffffffffu, xmin, o));
         xmax = dmax(xmax, __shfl_xor_sync(0xffffffffu, xmax, o));
+        ymin = dmin(ymin, __shfl_xor_sync(0xffffffffu, ymin, o));
+        ymax = dmax(ymax, __shfl_xor_sync(0xffffffffu, ymax, o));
     }
     int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (l == 0) { red[0][w] = xmin; red[1][w] = xmax; }
+    if (l == 0) { red[0][w] = xmin; red[1][w] = xmax; red[2][w] = ymin; red[3][w] = ymax; }
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (int k = 1; k < (int)(blockDim.x >> 5); ++k) { xmin = dmin(xmin, red[0][k]); xmax = dmax(xmax, red[1][k]); }
-        int c0 = (int)floor((xmin - I.x0) / I.dx) - 1;
-        int c1 = (int)floor((xmax - I.x0) / I.dx) + 1;
-        if (I.nv == 0) { c0 = 1; c1 = 0; }
+        for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
+            xmin = dmin(xmin, red[0][k]); xmax = dmax(xmax, red[1][k]);
+            ymin = dmin(ymin, red[2][k]); ymax = dmax(ymax, red[3][k]);
+        }
+        int c0 = (int)floor(fmax((xmin - I.x0) / I.dx, -4.0)) - 1;
+        int c1 = (int)floor(fmin((xmax - I.x0) / I.dx, (double)I.nx + 4.0)) + 1;
+        int r0 = (int)floor(fmax((ymin - I.y0) / I.dy, -4.0)) - 1;
+        int r1 = (int)floor(fmin((ymax - I.y0) / I.dy, (double)I.ny + 4.0)) + 1;
+        if (I.nv == 0) { c0 = 1; c1 = 0; r0 = 1; r1 = 0; }
         if (c0 < 0) c0 = 0;
         if (c1 > I.nx - 1) c1 = I.nx - 1;
+        if (r0 < 0) r0 = 0;
+        if (r1 > I.ny - 1) r1 = I.ny - 1;
         if (c1 - c0 + 1 > I.gcol_max) { c1 = c0 + I.gcol_max - 1; y.err |= ERR_EDGE_CAP; }
         y.col0 = c0;
         y.col1 = c1;
+        y.row0 = r0;
+        y.row1 = r1;
     }
 }
 
 // ---------------------------------------------------------------------------
-// warp-cooperative edge gather for one column and pose
+// rows of an edge inside the x-range [X0, X1]
 // ---------------------------------------------------------------------------
-__device__ int gather_edges(EdgeBuf &E, const InstDesc &I, const double *px, const double *py, const int *vnext,
-                            const unsigned char *vmov, int P, int total_v, double gxl, double gxr, int lane,
-                            int *err) {
-    int cnt = 0;
-    const double *PX = px + (size_t)P * total_v, *PY = py + (size_t)P * total_v;
-    for (int base = 0; base < I.nv; base += 32) {
-        int k = base + lane;
-        bool take = false;
-        double xa = 0, ya = 0, xb = 0, yb = 0;
-        int a = I.voff + k;
-        if (k < I.nv) {
-            int b = vnext[a];
-            xa = PX[a]; xb = PX[b];
-            take = dmax(xa, xb) >= gxl && dmin(xa, xb) <= gxr;
-            if (take) { ya = PY[a]; yb = PY[b]; }
-        }
-        unsigned m = __ballot_sync(0xffffffffu, take);
-        if (take) {
-            int pos = cnt + __popc(m & ((1u << lane) - 1u));
-            if (pos < EMAX) {
-                E.xa[pos] = xa; E.ya[pos] = ya; E.xb[pos] = xb; E.yb[pos] = yb;
-                E.mov[pos] = vmov[a];
-            }
-        }
-        cnt += __popc(m);
-    }
-    __syncwarp();
-    if (cnt > EMAX) {
-        if (lane == 0) *err |= ERR_EDGE_CAP;
-        cnt = EMAX;
-    }
-    return cnt;
-}
-
-// y-extent of an edge inside the closed column [xl, xr]; false if disjoint
+// y-extent of an edge inside the closed x-range [xl, xr]; false if disjoint
 __device__ __forceinline__ bool edge_yrange(double xa, double ya, double xb, double yb, double xl, double xr,
                                             double *elo, double *ehi) {
     double lo = dmin(xa, xb), hi = dmax(xa, xb);
@@ -193,55 +199,122 @@ __device__ __forceinline__ bool edge_yrange(double xa, double ya, double xb, dou
     return true;
 }
 
-// mark rows j whose closed cell [xl,xr]x[y_j,y_j+1] meets an edge
-__device__ void mark_rows(const EdgeBuf &E, int cnt, const InstDesc &I, double xl, double xr, unsigned *bits,
-                          int lane) {
-    for (int e = lane; e < cnt; e += 32) {
-        double elo, ehi;
-        if (!edge_yrange(E.xa[e], E.ya[e], E.xb[e], E.yb[e], xl, xr, &elo, &ehi)) continue;
-        double flo = (elo - I.y0) / I.dy, fhi = (ehi - I.y0) / I.dy;
-        flo = fmin(fmax(flo, -4.0), (double)I.ny + 4.0);
-        fhi = fmin(fmax(fhi, -4.0), (double)I.ny + 4.0);
-        int jlo = (int)floor(flo) - 1, jhi = (int)floor(fhi) + 1;
-        if (jlo < 0) jlo = 0;
-        if (jhi > I.ny - 1) jhi = I.ny - 1;
-        for (int j = jlo; j <= jhi; ++j) {
-            double yb = node_coord(I.y0, j, I.dy), yt = node_coord(I.y0, j + 1, I.dy);
-            if (ehi >= yb && elo <= yt) atomicOr(&bits[j >> 5], 1u << (j & 31));
+__device__ __forceinline__ int row_floor(const InstDesc &I, double yv) {
+    double f = (yv - I.y0) / I.dy;
+    f = fmin(fmax(f, -4.0), (double)I.ny + 4.0);
+    return (int)floor(f);
+}
+
+// ---------------------------------------------------------------------------
+// warp-cooperative gather of the edges overlapping [gxl, gxr] at pose P; marks
+// the rows whose closed cell of column [xl, xr] an edge meets (touch bits)
+// ---------------------------------------------------------------------------
+__device__ void gather(GeoBuf &G, const InstDesc &I, const double *__restrict__ px, const double *__restrict__ py,
+                       const float *__restrict__ ebox, const int *__restrict__ vnext,
+                       const unsigned char *__restrict__ vmov, int P, int total_v, double xl, double xr, double gxl,
+                       double gxr, unsigned *touch, int lane, int *err) {
+    const double *PX = px + (size_t)P * total_v, *PY = py + (size_t)P * total_v;
+    const float *EB = ebox + (size_t)P * total_v * 2;
+    const float fl = __double2float_rd(gxl), fr = __double2float_ru(gxr);
+    int cnt = 0, lc0 = 0, lc1 = 0;
+    for (int base = 0; base < I.nv; base += 32) {
+        const int k = base + lane;
+        const int a = I.voff + k;
+        bool take = false;
+        if (k < I.nv) take = EB[2 * a + 1] >= fl && EB[2 * a] <= fr;
+        const unsigned m = __ballot_sync(0xffffffffu, take);
+        double xa = 0, ya = 0, xb = 0, yb = 0;
+        bool c0 = false, c1 = false;
+        if (take) {
+            const int b = vnext[a];
+            xa = PX[a]; ya = PY[a]; xb = PX[b]; yb = PY[b];
+            const int pos = cnt + __popc(m & ((1u << lane) - 1u));
+            const double lo = dmin(xa, xb), hi = dmax(xa, xb);
+            if (pos < EMAX) {
+                G.xa[pos] = xa; G.ya[pos] = ya; G.xb[pos] = xb; G.yb[pos] = yb;
+                G.mov[pos] = vmov[a];
+                G.ovl[pos] = dmax(0.0, dmin(xr, hi) - dmax(xl, lo));
+                double elo, ehi;
+                if (edge_yrange(xa, ya, xb, yb, gxl, gxr, &elo, &ehi)) {
+                    G.jlo[pos] = (short)(row_floor(I, elo) - 1);
+                    G.jhi[pos] = (short)(row_floor(I, ehi) + 1);
+                } else {
+                    G.jlo[pos] = 1;
+                    G.jhi[pos] = 0;
+                }
+            }
+            if (touch) {
+                double elo, ehi;
+                if (edge_yrange(xa, ya, xb, yb, xl, xr, &elo, &ehi)) {
+                    int jl = row_floor(I, elo) - 1, jh = row_floor(I, ehi) + 1;
+                    if (jl < 0) jl = 0;
+                    if (jh > I.ny - 1) jh = I.ny - 1;
+                    for (int j = jl; j <= jh; ++j) {
+                        double ybj = node_coord(I.y0, j, I.dy), ytj = node_coord(I.y0, j + 1, I.dy);
+                        if (ehi >= ybj && elo <= ytj) atomicOr(&touch[j >> 5], 1u << (j & 31));
+                    }
+                }
+            }
+            c0 = xa != xb && lo <= xl && xl <= hi;
+            c1 = xa != xb && lo <= xr && xr <= hi;
         }
+        const unsigned m0 = __ballot_sync(0xffffffffu, c0), m1 = __ballot_sync(0xffffffffu, c1);
+        for (int L = 0; L < 2; ++L) {
+            const bool c = L == 0 ? c0 : c1;
+            const unsigned mm = L == 0 ? m0 : m1;
+            int &lc = L == 0 ? lc0 : lc1;
+            if (c) {
+                const int p = lc + __popc(mm & ((1u << lane) - 1u));
+                if (p < LMAX) {
+                    const double xs = L == 0 ? xl : xr;
+                    const double lo = dmin(xa, xb), hi = dmax(xa, xb);
+                    G.lyc[L][p] = ya + (xs - xa) * (yb - ya) / (xb - xa);
+                    G.ls[L][p] = xa < xb ? 1 : -1;
+                    G.lf[L][p] = (unsigned char)((lo < xs ? 1 : 0) | (xs < hi ? 2 : 0));
+                }
+            }
+            lc += __popc(mm);
+        }
+        cnt += __popc(m);
     }
+    if (cnt > EMAX || lc0 > LMAX || lc1 > LMAX) {
+        if (lane == 0) *err |= ERR_EDGE_CAP;
+    }
+    if (lane == 0) {
+        G.cnt = cnt < EMAX ? cnt : EMAX;
+        G.lcnt[0] = lc0 < LMAX ? lc0 : LMAX;
+        G.lcnt[1] = lc1 < LMAX ? lc1 : LMAX;
+    }
+    __syncwarp();
 }
 
-// solid length of the vertical segment {xs} x [y0r, y1r]; left_limit selects
-// the crossing convention min < xs <= max (limit from the left), otherwise
-// min <= xs < max
-__device__ double line_solid_v(const EdgeBuf &E, int cnt, double xs, double y0r, double y1r, bool left_limit) {
-    double L = 0.0;
-    for (int e = 0; e < cnt; ++e) {
-        double xa = E.xa[e], xb = E.xb[e];
-        double lo = dmin(xa, xb), hi = dmax(xa, xb);
-        bool cr = left_limit ? (lo < xs && xs <= hi) : (lo <= xs && xs < hi);
-        if (!cr) continue;
-        double ya = E.ya[e], yb = E.yb[e];
-        double yc = ya + (xs - xa) * (yb - ya) / (xb - xa);
-        double s = xa < xb ? 1.0 : -1.0;
+// solid length of {x_L} x [y0r, y1r] (L = 0: x_l, 1: x_r); left_limit takes
+// crossings as seen from the left of the line (min < x <= max)
+__device__ __forceinline__ double line_solid_v(const GeoBuf &G, int L, double y0r, double y1r, bool left_limit) {
+    double s = 0.0;
+    const unsigned char want = left_limit ? 1 : 2;
+    for (int e = 0; e < G.lcnt[L]; ++e) {
+        if (!(G.lf[L][e] & want)) continue;
+        double yc = G.lyc[L][e];
         double cl = yc < y0r ? y0r : (yc > y1r ? y1r : yc);
-        L += s * (y1r - cl);
+        s += (double)G.ls[L][e] * (y1r - cl);
     }
-    return L;
+    return s;
 }
 
-// solid length of the horizontal segment [xl, xr] x {yf} inside the column:
-// each edge contributes the x-measure over which it lies below yf
-__device__ double line_solid_h(const EdgeBuf &E, int cnt, double xl, double xr, double yf) {
+// solid length of [x_l, x_r] x {y_f} (y_f = y_jf): edges below the row
+// band contribute their whole overlap, the others the part below y_f
+__device__ double line_solid_h(const GeoBuf &G, double xl, double xr, double yf, int jf) {
     double L = 0.0;
-    for (int e = 0; e < cnt; ++e) {
-        double xa = E.xa[e], xb = E.xb[e], ya = E.ya[e], yb = E.yb[e];
-        double p = dmax(xl, dmin(xa, xb)), q = dmin(xr, dmax(xa, xb));
+    for (int e = 0; e < G.cnt; ++e) {
+        const double s = G.xa[e] < G.xb[e] ? 1.0 : -1.0;
+        if (G.jhi[e] < jf - 1) { L += s * G.ovl[e]; continue; }
+        if (G.jlo[e] > jf) continue;
+        const double xa = G.xa[e], xb = G.xb[e], ya = G.ya[e], yb = G.yb[e];
+        const double p = dmax(xl, dmin(xa, xb)), q = dmin(xr, dmax(xa, xb));
         if (!(q > p)) continue;
-        double s = xa < xb ? 1.0 : -1.0;
-        double k = (yb - ya) / (xb - xa);
-        double yp = ya + (p - xa) * k, yq = ya + (q - xa) * k;
+        const double k = (yb - ya) / (xb - xa);
+        const double yp = ya + (p - xa) * k, yq = ya + (q - xa) * k;
         double m;
         if (yp < yf && yq < yf) m = q - p;
         else if (!(yp < yf) && !(yq < yf)) m = 0.0;
@@ -255,113 +328,96 @@ __device__ double line_solid_h(const EdgeBuf &E, int cnt, double xl, double xr, 
     return L;
 }
 
-// area of body ∩ [rx0,rx1] x [ry0,ry1]; grid side on the right (x_s = rx1,
-// crossings taken from the left) or on the left (x_s = rx0, from the right)
-__device__ double solid_area(const EdgeBuf &E, int cnt, double rx0, double rx1, double ry0, double ry1,
-                             bool grid_right) {
-    double xo = grid_right ? rx0 : rx1;
-    double xs = grid_right ? rx1 : rx0;
-    double lx0 = rx0 - xo, lx1 = rx1 - xo, ly1 = ry1 - ry0;
+// sum over the edges meeting [rx0,rx1]x[ry0,ry1] (candidates: rows ja..jb) of
+// the integral of (x - xo) dy along the clipped edge; vertical edges on the
+// grid side xs are skipped.  Optionally accumulates the wall normal times
+// length (into the body: (-dy, dx) of the clipped pieces) and whether a
+// moving edge meets the closed rectangle.
+__device__ double rect_edges(const GeoBuf &G, int ja, int jb, double rx0, double rx1, double ry0, double ry1,
+                             double xo, double xs, double *nlx, double *nly, bool *mov) {
+    const double lx0 = rx0 - xo, lx1 = rx1 - xo, ly1 = ry1 - ry0;
     double A = 0.0;
-    for (int e = 0; e < cnt; ++e) {
-        double xa = E.xa[e], xb = E.xb[e], ya = E.ya[e], yb = E.yb[e];
+    for (int e = 0; e < G.cnt; ++e) {
+        if (G.jhi[e] < ja || G.jlo[e] > jb) continue;
+        const double xa = G.xa[e], xb = G.xb[e], ya = G.ya[e], yb = G.yb[e];
         if (dmax(ya, yb) < ry0 || dmin(ya, yb) > ry1 || dmax(xa, xb) < rx0 || dmin(xa, xb) > rx1) continue;
-        if (xa == xb && xa == xs) continue;   // vertical edge on the grid side
-        double ax = xa - xo, ay = ya - ry0, bx = xb - xo, by = yb - ry0;
-        double ddx = bx - ax, ddy = by - ay;
+        const double ax = xa - xo, ay = ya - ry0, bx = xb - xo, by = yb - ry0;
+        const double ddx = bx - ax, ddy = by - ay;
         double t0 = 0.0, t1 = 1.0;
         bool ok = true;
-        double pp[4] = {-ddx, ddx, -ddy, ddy};
-        double qq[4] = {ax - lx0, lx1 - ax, ay, ly1 - ay};
+        const double pp[4] = {-ddx, ddx, -ddy, ddy};
+        const double qq[4] = {ax - lx0, lx1 - ax, ay, ly1 - ay};
         for (int k = 0; k < 4; ++k) {
             if (pp[k] == 0.0) {
                 if (qq[k] < 0.0) ok = false;
                 continue;
             }
-            double r = qq[k] / pp[k];
+            const double r = qq[k] / pp[k];
             if (pp[k] < 0.0) t0 = dmax(t0, r);
             else t1 = dmin(t1, r);
         }
-        if (!ok || !(t1 > t0)) continue;
-        double xc0 = ax + t0 * ddx, xc1 = ax + t1 * ddx;
+        if (!ok || t1 < t0) continue;
+        if (mov && G.mov[e]) *mov = true;
+        if (xa == xb && xa == xs) continue;   // vertical edge on the grid side
+        if (!(t1 > t0)) continue;
+        const double xc0 = ax + t0 * ddx, xc1 = ax + t1 * ddx;
         A += ddy * (t1 - t0) * (0.5 * (xc0 + xc1));
+        if (nlx) {
+            *nlx -= ddy * (t1 - t0);
+            *nly += ddx * (t1 - t0);
+        }
     }
-    A += (rx1 - rx0) * line_solid_v(E, cnt, xs, ry0, ry1, grid_right);
     return A;
 }
 
-// touched-by-moving-edge test of a closed cell
-__device__ bool cell_moving(const EdgeBuf &E, int cnt, double xl, double xr, double yb, double yt) {
-    for (int e = 0; e < cnt; ++e) {
-        if (!E.mov[e]) continue;
-        double elo, ehi;
-        if (edge_yrange(E.xa[e], E.ya[e], E.xb[e], E.yb[e], xl, xr, &elo, &ehi) && ehi >= yb && elo <= yt)
-            return true;
-    }
-    return false;
-}
-
-__device__ __forceinline__ double cell_alpha(const EdgeBuf &E, int cnt, const InstDesc &I, double xl, double xr,
-                                             double yb, double yt) {
-    double A = solid_area(E, cnt, xl, xr, yb, yt, true);
+__device__ __forceinline__ double cell_alpha(const GeoBuf &G, const InstDesc &I, int j, double xl, double xr,
+                                             double yb, double yt, double *nlx, double *nly, bool *mov) {
+    double A = rect_edges(G, j, j, xl, xr, yb, yt, xl, xr, nlx, nly, mov) + (xr - xl) * line_solid_v(G, 1, yb, yt, true);
     double a = clamp01(1.0 - A / (I.dx * I.dy));
     return a < ALPHA_MIN ? 0.0 : a;
 }
 
-// time-averaged aperture of the face owned by cell (i,j) along dir at pose P
-// (P = 0 start, 1 middle, 2 end).  Translating sweeps use the exact swept strip
-// at the start pose; rotating sweeps Simpson's rule over the three poses; a
-// static direction the start-pose aperture.  Owner rule: delta >= 0 -> the
-// high face, delta < 0 -> the low face.
-__device__ double owned_face_part(const EdgeBuf &E, int cnt, const InstDesc &I, int dir, double delta, int P,
-                                  double xl, double xr, double yb, double yt) {
-    if (I.rotating) {
-        double w = P == 1 ? 4.0 / 6.0 : 1.0 / 6.0;
-        double ap = dir == 0 ? 1.0 - line_solid_v(E, cnt, xr, yb, yt, true) / I.dy
-                             : 1.0 - line_solid_h(E, cnt, xl, xr, yt) / I.dx;
-        return w * clamp01(ap);
+// fluid fraction of the strip between a grid line and its copy displaced by
+// w (>0: to the right / up); `line` is 0 (x_l) or 1 (x_r) for vertical strips
+__device__ double strip_beta_x(const GeoBuf &G, const InstDesc &I, int j, int line, double xs, double w, double yb,
+                               double yt) {
+    if (w > 0.0) {   // [xs, xs + w]: grid side on the left, crossings seen from the right
+        double x1 = xs + w;
+        double A = rect_edges(G, j, j, xs, x1, yb, yt, x1, xs, nullptr, nullptr, nullptr) +
+                   (x1 - xs) * line_solid_v(G, line, yb, yt, false);
+        return clamp01(1.0 - A / ((x1 - xs) * I.dy));
     }
-    if (P != 0) return 0.0;
-    if (delta == 0.0) {
-        double ap = dir == 0 ? 1.0 - line_solid_v(E, cnt, xr, yb, yt, true) / I.dy
-                             : 1.0 - line_solid_h(E, cnt, xl, xr, yt) / I.dx;
-        return clamp01(ap);
-    }
-    if (dir == 0) {
-        double sl = delta > 0 ? xr - delta : xl, sr = delta > 0 ? xr : xl - delta;
-        double A = solid_area(E, cnt, sl, sr, yb, yt, delta > 0);
-        return clamp01(1.0 - A / ((sr - sl) * I.dy));
-    }
-    double sl = delta > 0 ? yt - delta : yb, sr = delta > 0 ? yt : yb - delta;
-    double A = solid_area(E, cnt, xl, xr, sl, sr, true);
-    return clamp01(1.0 - A / ((sr - sl) * I.dx));
+    double x0 = xs + w;   // [xs - |w|, xs]: grid side on the right
+    double A = rect_edges(G, j, j, x0, xs, yb, yt, x0, xs, nullptr, nullptr, nullptr) +
+               (xs - x0) * line_solid_v(G, line, yb, yt, true);
+    return clamp01(1.0 - A / ((xs - x0) * I.dy));
 }
 
-// time-averaged aperture of the domain-boundary face that a boundary cell does
-// not own (x-low face when delta >= 0, x-high face when delta < 0, same for y)
-__device__ double boundary_face_part(const EdgeBuf &E, int cnt, const InstDesc &I, int dir, double delta, int P,
-                                     double xl, double xr, double yb, double yt) {
-    if (I.rotating) {
-        double w = P == 1 ? 4.0 / 6.0 : 1.0 / 6.0;
-        double ap = dir == 0 ? 1.0 - line_solid_v(E, cnt, xl, yb, yt, true) / I.dy
-                             : 1.0 - line_solid_h(E, cnt, xl, xr, yb) / I.dx;
-        return w * clamp01(ap);
-    }
-    if (P != 0) return 0.0;
-    if (delta == 0.0) {
-        double ap = dir == 0 ? 1.0 - line_solid_v(E, cnt, xl, yb, yt, true) / I.dy
-                             : 1.0 - line_solid_h(E, cnt, xl, xr, yb) / I.dx;
-        return clamp01(ap);
-    }
-    if (dir == 0) {
-        // delta > 0: strip left of the x-low face; delta < 0: right of the x-high face
-        double sl = delta > 0 ? xl - delta : xr, sr = delta > 0 ? xl : xr - delta;
-        double A = solid_area(E, cnt, sl, sr, yb, yt, delta > 0);
-        return clamp01(1.0 - A / ((sr - sl) * I.dy));
-    }
-    double sl = delta > 0 ? yb - delta : yt, sr = delta > 0 ? yb : yt - delta;
-    double A = solid_area(E, cnt, xl, xr, sl, sr, true);
-    return clamp01(1.0 - A / ((sr - sl) * I.dx));
+__device__ double strip_beta_y(const GeoBuf &G, const InstDesc &I, int j, double xl, double xr, double ys, double w) {
+    double y0 = w > 0.0 ? ys : ys + w, y1 = w > 0.0 ? ys + w : ys;
+    int ja = w > 0.0 ? j : j - 1, jb = w > 0.0 ? j + 1 : j;
+    double A = rect_edges(G, ja, jb, xl, xr, y0, y1, xl, xr, nullptr, nullptr, nullptr) +
+               (xr - xl) * line_solid_v(G, 1, y0, y1, true);
+    return clamp01(1.0 - A / ((y1 - y0) * I.dx));
+}
+
+// instantaneous aperture of a face of cell (i, j) along dir: hi != 0 -> the
+// high face (x_r or y_t), else the low face
+__device__ __forceinline__ double face_ap(const GeoBuf &G, const InstDesc &I, int dir, bool hi, int j, double xl,
+                                          double xr, double yb, double yt) {
+    if (dir == 0) return clamp01(1.0 - line_solid_v(G, hi ? 1 : 0, yb, yt, true) / I.dy);
+    return clamp01(1.0 - line_solid_h(G, xl, xr, hi ? yt : yb, hi ? j + 1 : j) / I.dx);
+}
+
+// time-averaged aperture (translation: exact swept strip, evaluated with the
+// body at the end pose B, where the strip of the start pose appears shifted
+// by the translation) of the face owned by the cell (own_hi: high face) or of
+// its domain-boundary face (boundary: the face it does not own)
+__device__ double swept_face_B(const GeoBuf &G, const InstDesc &I, int dir, double delta, bool hi, int j, double xl,
+                               double xr, double yb, double yt) {
+    if (delta == 0.0) return face_ap(G, I, dir, hi, j, xl, xr, yb, yt);
+    if (dir == 0) return strip_beta_x(G, I, j, hi ? 1 : 0, hi ? xr : xl, delta, yb, yt);
+    return strip_beta_y(G, I, j, xl, xr, hi ? yt : yb, delta);
 }
 
 // ---------------------------------------------------------------------------
@@ -370,207 +426,225 @@ __device__ double boundary_face_part(const EdgeBuf &E, int cnt, const InstDesc &
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(GEOM_WARPS * 32) k_geom(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y,
                                                         const double *__restrict__ px, const double *__restrict__ py,
+                                                        const float *__restrict__ ebox,
                                                         const int *__restrict__ vnext,
                                                         const unsigned char *__restrict__ vmov, int total_v,
                                                         int n_inst, int total_cols, int dir, BandRec *__restrict__ R,
                                                         double *__restrict__ bnd) {
-    __shared__ EdgeBuf Es[GEOM_WARPS];
-    __shared__ unsigned bitsA[GEOM_WARPS][MAXROWWORDS], bitsB[GEOM_WARPS][MAXROWWORDS];
+    extern __shared__ __align__(16) unsigned char gsm[];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    GeoWarp &W = ((GeoWarp *)gsm)[wib];
+    GeoBuf &G = W.G;
     const int gw = blockIdx.x * GEOM_WARPS + wib;
     if (gw >= total_cols) return;
-    // instance of this geometry column
     int lo = 0, hi = n_inst - 1;
     while (lo < hi) {
         int mid = (lo + hi + 1) >> 1;
         if (D[mid].gcol_off <= gw) lo = mid; else hi = mid - 1;
     }
-    const int inst = lo;
-    const InstDesc &I = D[inst];
-    InstDyn &y = Y[inst];
+    const InstDesc &I = D[lo];
+    InstDyn &y = Y[lo];
     const int i = y.col0 + (gw - I.gcol_off);
     if (i > y.col1 || i >= I.nx || I.nv == 0) return;
-    EdgeBuf &E = Es[wib];
-    unsigned *bA = bitsA[wib], *bB = bitsB[wib];
     const double xl = node_coord(I.x0, i, I.dx), xr = node_coord(I.x0, i + 1, I.dx);
     const double delta = y.delta;
-    const bool own_hi = I.rotating || delta >= 0.0;   // owner rule of the sweep-direction faces
-    const bool xbnd_lo = dir == 0 && I.bc[0] != 2 && i == 0;
-    const bool xbnd_hi = dir == 0 && I.bc[1] != 2 && i == I.nx - 1;
-    // gather range: the column, widened by |delta| at a non-periodic x boundary
-    double gxl = xl, gxr = xr;
-    if (xbnd_lo) gxl = xl - fabs(delta);
-    if (xbnd_hi) gxr = xr + fabs(delta);
+    const bool own_hi = I.rotating || delta >= 0.0;
+    const double gxl = xl - fabs(delta), gxr = xr + fabs(delta);
     const int nwords = (I.ny + 31) >> 5;
     int err = 0;
-    for (int w = lane; w < nwords; w += 32) { bA[w] = 0u; bB[w] = 0u; }
+    for (int w = lane; w < nwords; w += 32) { W.bA[w] = 0u; W.bB[w] = 0u; W.bM[w] = 0u; }
     __syncwarp();
-    // pass 1: touched rows at A, B (and M when rotating)
-    const int poses[3] = {0, 2, 1};
-    for (int pi = 0; pi < (I.rotating ? 3 : 2); ++pi) {
-        int P = poses[pi];
-        int cnt = gather_edges(E, I, px, py, vnext, vmov, P, total_v, gxl, gxr, lane, &err);
-        mark_rows(E, cnt, I, xl, xr, pi == 1 ? bB : bA, lane);   // M (rotating) is or-ed into the A map
-        __syncwarp();
+    // touched at the start pose: class bytes kept from the previous sweep
+    for (int j = y.row0 + lane; j <= y.row1; j += 32)
+        if (I.cls[j * I.pitch + i] & CLS_TOUCH) atomicOr(&W.bA[j >> 5], 1u << (j & 31));
+    if (I.rotating) gather(G, I, px, py, ebox, vnext, vmov, 1, total_v, xl, xr, gxl, gxr, W.bM, lane, &err);
+    gather(G, I, px, py, ebox, vnext, vmov, 2, total_v, xl, xr, gxl, gxr, W.bB, lane, &err);
+    // band rows in increasing order: per-word prefix counts
+    int running = 0;
+    for (int w0 = 0; w0 < nwords; w0 += 32) {
+        int w = w0 + lane;
+        int c = w < nwords ? __popc(W.bA[w] | W.bB[w] | W.bM[w]) : 0;
+        int incl = c;
+        for (int o = 1; o < 32; o <<= 1) {
+            int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        if (w < nwords) W.wpre[w] = running + incl - c;
+        running += __shfl_sync(0xffffffffu, incl, 31);
     }
-    __syncwarp();
-    // count band rows and reserve records (rows in increasing order)
+    const int T = running;
     int base = 0;
     if (lane == 0) {
-        int tot = 0;
-        for (int w = 0; w < nwords; ++w) tot += __popc(bA[w] | bB[w]);
-        base = tot ? atomicAdd(&y.band_count, tot) : 0;
-        if (base + tot > I.rec_cap) { err |= ERR_BAND_CAP; base = -1; }
+        base = T ? atomicAdd(&y.band_count, T) : 0;
+        if (base + T > I.rec_cap) { err |= ERR_BAND_CAP; base = -1; }
     }
     base = __shfl_sync(0xffffffffu, base, 0);
-    if (base < 0) { if (lane == 0) atomicOr(&y.err, err); return; }
-    // pass 2: per pose quantities for each band row
-    for (int pi = 0; pi < 3; ++pi) {
-        const int P = pi == 0 ? 0 : (pi == 1 ? 2 : 1);   // A, B, M
-        int cnt = gather_edges(E, I, px, py, vnext, vmov, P, total_v, gxl, gxr, lane, &err);
-        int running = 0;
-        for (int w0 = 0; w0 < nwords; w0 += 32) {
-            int w = w0 + lane;
-            unsigned m = w < nwords ? (bA[w] | bB[w]) : 0u;
-            int c = __popc(m);
-            int incl = c;
-            for (int o = 1; o < 32; o <<= 1) {
-                int v = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += v;
-            }
-            int idx = base + running + incl - c;
-            running += __shfl_sync(0xffffffffu, incl, 31);
-            while (m) {
-                int b = __ffs(m) - 1;
-                m &= m - 1;
-                const int j = w * 32 + b;
-                BandRec &r = R[I.rec_base + idx];
-                ++idx;
-                const double yb = node_coord(I.y0, j, I.dy), yt = node_coord(I.y0, j + 1, I.dy);
-                const bool tA = (bA[w] >> b) & 1u, tB = (bB[w] >> b) & 1u;
-                // the domain-boundary face this boundary cell does not own
-                const bool need_bnd =
-                    dir == 0 ? ((own_hi && i == 0 && I.bc[0] != 2) || (!own_hi && i == I.nx - 1 && I.bc[1] != 2))
-                             : ((own_hi && j == 0 && I.bc[2] != 2) || (!own_hi && j == I.ny - 1 && I.bc[3] != 2));
-                if (P == 0) {
-                    r.cell = j * I.pitch + i;
-                    r.i = i;
-                    r.j = j;
-                    r.aA = cell_alpha(E, cnt, I, xl, xr, yb, yt);
-                    r.bown = owned_face_part(E, cnt, I, dir, delta, 0, xl, xr, yb, yt);
-                    bnd[I.rec_base + idx - 1] =
-                        need_bnd ? boundary_face_part(E, cnt, I, dir, delta, 0, xl, xr, yb, yt) : 0.0;
-                    int fl = (tA ? RF_TOUCH_A : 0) | (tB ? RF_TOUCH_B : 0);
-                    if (cell_moving(E, cnt, xl, xr, yb, yt)) fl |= RF_MOVING;
-                    r.flags = fl;
-                } else if (P == 2) {
-                    r.aB = cell_alpha(E, cnt, I, xl, xr, yb, yt);
-                    if (I.rotating) {
-                        r.bown += owned_face_part(E, cnt, I, dir, delta, 2, xl, xr, yb, yt);
-                        if (need_bnd) bnd[I.rec_base + idx - 1] += boundary_face_part(E, cnt, I, dir, delta, 2, xl, xr, yb, yt);
-                    }
-                    if (cell_moving(E, cnt, xl, xr, yb, yt)) r.flags |= RF_MOVING;
-                } else {
-                    const double aM = cell_alpha(E, cnt, I, xl, xr, yb, yt);
-                    r.aM = aM;
-                    if (I.rotating) {
-                        r.bown += owned_face_part(E, cnt, I, dir, delta, 1, xl, xr, yb, yt);
-                        if (need_bnd) bnd[I.rec_base + idx - 1] += boundary_face_part(E, cnt, I, dir, delta, 1, xl, xr, yb, yt);
-                    }
-                    int fl = r.flags;
-                    if (cell_moving(E, cnt, xl, xr, yb, yt)) fl |= RF_MOVING;
-                    // instantaneous apertures at the mid pose
-                    const double bW = clamp01(1.0 - line_solid_v(E, cnt, xl, yb, yt, true) / I.dy);
-                    const double bE = clamp01(1.0 - line_solid_v(E, cnt, xr, yb, yt, true) / I.dy);
-                    const double bS = clamp01(1.0 - line_solid_h(E, cnt, xl, xr, yb) / I.dx);
-                    const double bN = clamp01(1.0 - line_solid_h(E, cnt, xl, xr, yt) / I.dx);
-                    // shielded distance d = alpha_hat / |delta beta| (eq. Klein2DalphaHat)
-                    const double blo = dir == 0 ? bW : bS, bhi = dir == 0 ? bE : bN;
-                    const double db = fabs(blo - bhi);
-                    const double ahat = aM - dmin(blo, bhi);
-                    r.d = db > 0.0 ? clamp01(ahat / db) : 1.0;
-                    // wall normal from aperture closure, into the body
-                    const double nLx = (bW - bE) * I.dy, nLy = (bS - bN) * I.dx;
-                    const double L = sqrt(nLx * nLx + nLy * nLy);
-                    r.nx = L > 0.0 ? nLx / L : 0.0;
-                    r.ny = L > 0.0 ? nLy / L : 0.0;
-                    // wall velocity at the cell centre
-                    double wx = 0.0, wy = 0.0;
-                    if (fl & RF_MOVING) {
-                        const double xc = I.x0 + ((double)i + 0.5) * I.dx, yc = I.y0 + ((double)j + 0.5) * I.dy;
-                        const double pcx = I.pivot[0] + y.XM, pcy = I.pivot[1] + y.YM;
-                        wx = I.U[0] - y.Om * (yc - pcy);
-                        wy = I.U[1] + y.Om * (xc - pcx);
-                    }
-                    r.wx = wx;
-                    r.wy = wy;
-                    // classes
-                    const bool unc = r.aA == 0.0 && r.aB > 0.0;
-                    const bool cov = r.aA > 0.0 && r.aB == 0.0;
-                    if (unc) fl |= RF_UNCOV;
-                    if (cov) fl |= RF_COVER;
-                    if (r.aA > 0.0 || (unc && I.ucov == 1)) fl |= RF_FLUID_A;
-                    if (r.aB > 0.0) fl |= RF_FLUID_B;
-                    r.flags = fl;
-                    r.mix = -1;
-                    // publish: class byte and record index of this cell
-                    I.rec[r.cell] = I.rec_base + idx - 1;
-                    I.cls[r.cell] |= CLS_BAND;
-                }
-            }
+    __syncwarp();
+    if (base < 0 || T == 0) {
+        if (lane == 0 && err) atomicOr(&y.err, err);
+        return;
+    }
+    auto locate = [&](int t, int *jrow, int *wrd, int *bit) {
+        int a = 0, b = nwords - 1;
+        while (a < b) {
+            int m = (a + b + 1) >> 1;
+            if (W.wpre[m] <= t) a = m; else b = m - 1;
         }
-        __syncwarp();
+        unsigned mask = W.bA[a] | W.bB[a] | W.bM[a];
+        int r = t - W.wpre[a];
+        int bpos = __fns(mask, 0, r + 1);
+        *wrd = a;
+        *bit = bpos;
+        *jrow = a * 32 + bpos;
+    };
+    const double wsimp_B = 1.0 / 6.0, wsimp_M = 4.0 / 6.0, wsimp_A = 1.0 / 6.0;
+    // pass B (edges of the end pose are in G)
+    for (int t = lane; t < T; t += 32) {
+        int j, wrd, bit;
+        locate(t, &j, &wrd, &bit);
+        BandRec &r = R[I.rec_base + base + t];
+        const double yb = node_coord(I.y0, j, I.dy), yt = node_coord(I.y0, j + 1, I.dy);
+        const bool tA = (W.bA[wrd] >> bit) & 1u, tB = (W.bB[wrd] >> bit) & 1u, tM = (W.bM[wrd] >> bit) & 1u;
+        const int cell = j * I.pitch + i;
+        r.cell = cell;
+        r.i = i;
+        r.j = j;
+        bool mov = false;
+        r.aB = cell_alpha(G, I, j, xl, xr, yb, yt, nullptr, nullptr, &mov);
+        r.aA = I.alpha[cell];
+        const bool need_bnd =
+            dir == 0 ? ((own_hi && i == 0 && I.bc[0] != 2) || (!own_hi && i == I.nx - 1 && I.bc[1] != 2))
+                     : ((own_hi && j == 0 && I.bc[2] != 2) || (!own_hi && j == I.ny - 1 && I.bc[3] != 2));
+        double bo, bb = 0.0;
+        if (I.rotating) {
+            bo = wsimp_B * face_ap(G, I, dir, true, j, xl, xr, yb, yt);
+            if (need_bnd) bb = wsimp_B * face_ap(G, I, dir, false, j, xl, xr, yb, yt);
+        } else {
+            bo = swept_face_B(G, I, dir, delta, own_hi, j, xl, xr, yb, yt);
+            if (need_bnd) bb = swept_face_B(G, I, dir, delta, !own_hi, j, xl, xr, yb, yt);
+        }
+        r.bown = bo;
+        bnd[I.rec_base + base + t] = bb;
+        const bool movA = (I.cls[cell] & CLS_MOVT) != 0;   // a moving edge met the cell at the start pose
+        r.flags = (tA ? RF_TOUCH_A : 0) | (tB ? RF_TOUCH_B : 0) | (tM ? RF_TOUCH_M : 0) |
+                  ((mov || movA) ? RF_MOVING : 0) | (mov ? RF_MOV_B : 0);
+    }
+    // pass M
+    gather(G, I, px, py, ebox, vnext, vmov, 1, total_v, xl, xr, gxl, gxr, nullptr, lane, &err);
+    for (int t = lane; t < T; t += 32) {
+        int j, wrd, bit;
+        locate(t, &j, &wrd, &bit);
+        const int ri = I.rec_base + base + t;
+        BandRec &r = R[ri];
+        const double yb = node_coord(I.y0, j, I.dy), yt = node_coord(I.y0, j + 1, I.dy);
+        bool mov = false;
+        double nlx = 0.0, nly = 0.0;
+        const double aM = cell_alpha(G, I, j, xl, xr, yb, yt, &nlx, &nly, &mov);
+        r.aM = aM;
+        int fl = r.flags | (mov ? RF_MOVING : 0);
+        if (I.rotating) {
+            r.bown += wsimp_M * face_ap(G, I, dir, true, j, xl, xr, yb, yt);
+            const bool need_bnd = dir == 0 ? (i == 0 && I.bc[0] != 2) : (j == 0 && I.bc[2] != 2);
+            if (need_bnd) bnd[ri] += wsimp_M * face_ap(G, I, dir, false, j, xl, xr, yb, yt);
+        }
+        // shielded distance d = alpha_hat / |delta beta| at the mid pose
+        const double blo = face_ap(G, I, dir, false, j, xl, xr, yb, yt);
+        const double bhi = face_ap(G, I, dir, true, j, xl, xr, yb, yt);
+        const double db = fabs(blo - bhi);
+        const double ahat = aM - dmin(blo, bhi);
+        r.d = db > 0.0 ? clamp01(ahat / db) : 1.0;
+        // wall normal (into the body) from the boundary pieces inside the cell
+        const double L = sqrt(nlx * nlx + nly * nly);
+        r.nx = L > 0.0 ? nlx / L : 0.0;
+        r.ny = L > 0.0 ? nly / L : 0.0;
+        double wx = 0.0, wy = 0.0;
+        if (fl & RF_MOVING) {
+            const double xc = I.x0 + ((double)i + 0.5) * I.dx, yc = I.y0 + ((double)j + 0.5) * I.dy;
+            const double pcx = I.pivot[0] + y.XM, pcy = I.pivot[1] + y.YM;
+            wx = I.U[0] - y.Om * (yc - pcy);
+            wy = I.U[1] + y.Om * (xc - pcx);
+        }
+        r.wx = wx;
+        r.wy = wy;
+        const bool unc = r.aA == 0.0 && r.aB > 0.0;
+        const bool cov = r.aA > 0.0 && r.aB == 0.0;
+        if (unc) fl |= RF_UNCOV;
+        if (cov) fl |= RF_COVER;
+        if (r.aA > 0.0 || (unc && I.ucov == 1)) fl |= RF_FLUID_A;
+        if (r.aB > 0.0) fl |= RF_FLUID_B;
+        r.flags = fl;
+        r.mix = -1;
+        I.rec[r.cell] = ri;
+        I.cls[r.cell] |= CLS_BAND;
+    }
+    if (I.rotating) {
+        gather(G, I, px, py, ebox, vnext, vmov, 0, total_v, xl, xr, gxl, gxr, nullptr, lane, &err);
+        for (int t = lane; t < T; t += 32) {
+            int j, wrd, bit;
+            locate(t, &j, &wrd, &bit);
+            const int ri = I.rec_base + base + t;
+            const double yb = node_coord(I.y0, j, I.dy), yt = node_coord(I.y0, j + 1, I.dy);
+            R[ri].bown += wsimp_A * face_ap(G, I, dir, true, j, xl, xr, yb, yt);
+            const bool need_bnd = dir == 0 ? (i == 0 && I.bc[0] != 2) : (j == 0 && I.bc[2] != 2);
+            if (need_bnd) bnd[ri] += wsimp_A * face_ap(G, I, dir, false, j, xl, xr, yb, yt);
+        }
     }
     if (lane == 0 && err) atomicOr(&y.err, err);
 }
 
 // ---------------------------------------------------------------------------
-// full classification at the current pose (create / write_state / alpha read)
+// full classification at the pose in slot 0 (create / write_state / alpha)
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(GEOM_WARPS * 32) k_classify(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y,
                                                             const double *__restrict__ px,
                                                             const double *__restrict__ py,
+                                                            const float *__restrict__ ebox,
                                                             const int *__restrict__ vnext,
                                                             const unsigned char *__restrict__ vmov, int total_v,
                                                             int inst, double *__restrict__ alpha_out) {
-    __shared__ EdgeBuf Es[GEOM_WARPS];
-    __shared__ unsigned bits[GEOM_WARPS][MAXROWWORDS];
+    extern __shared__ __align__(16) unsigned char gsm[];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    GeoWarp &W = ((GeoWarp *)gsm)[wib];
+    GeoBuf &G = W.G;
     const InstDesc &I = D[inst];
     const int i = blockIdx.x * GEOM_WARPS + wib;
     if (i >= I.nx) return;
-    EdgeBuf &E = Es[wib];
-    unsigned *bt = bits[wib];
     const double xl = node_coord(I.x0, i, I.dx), xr = node_coord(I.x0, i + 1, I.dx);
     const int nwords = (I.ny + 31) >> 5;
     int err = 0;
-    for (int w = lane; w < nwords; w += 32) bt[w] = 0u;
+    for (int w = lane; w < nwords; w += 32) W.bB[w] = 0u;
     __syncwarp();
-    int cnt = I.nv ? gather_edges(E, I, px, py, vnext, vmov, 0, total_v, xl, xr, lane, &err) : 0;
-    mark_rows(E, cnt, I, xl, xr, bt, lane);
+    if (I.nv) gather(G, I, px, py, ebox, vnext, vmov, 0, total_v, xl, xr, xl, xr, W.bB, lane, &err);
+    else if (lane == 0) { G.cnt = 0; G.lcnt[0] = G.lcnt[1] = 0; }
     __syncwarp();
     for (int j = lane; j < I.ny; j += 32) {
         const double yb = node_coord(I.y0, j, I.dy), yt = node_coord(I.y0, j + 1, I.dy);
-        const bool touched = (bt[j >> 5] >> (j & 31)) & 1u;
-        double a = cnt ? cell_alpha(E, cnt, I, xl, xr, yb, yt) : 1.0;
-        uint8_t c = 0;
-        if (a == 0.0) c = CLS_SOLID;
-        else if (touched) c = CLS_CUT;
-        I.cls[j * I.pitch + i] = c;
-        I.rec[j * I.pitch + i] = -1;
+        const bool touched = (W.bB[j >> 5] >> (j & 31)) & 1u;
+        bool mov = false;
+        const double a = cell_alpha(G, I, j, xl, xr, yb, yt, nullptr, nullptr, &mov);
+        uint8_t c = touched ? CLS_TOUCH : 0;
+        if (mov) c |= CLS_MOVT;
+        if (a == 0.0) c |= CLS_SOLID;
+        else if (touched) c |= CLS_CUT;
+        const int cell = j * I.pitch + i;
+        I.cls[cell] = c;
+        I.rec[cell] = -1;
+        I.alpha[cell] = a;
         if (alpha_out) alpha_out[(size_t)j * I.nx + i] = a;
     }
     if (lane == 0 && err) atomicOr(&Y[inst].err, err);
 }
 
-// pose of instance `inst` at its current (t, X, Y) into pose slot 0
+// pose of instance `inst` at its current (t, X, Y) into slot 0, with the
+// FP32 x-bounds of its edges
 __global__ void k_pose_current(const InstDesc *__restrict__ D, const InstDyn *__restrict__ Y,
                                const double *__restrict__ vx, const double *__restrict__ vy,
-                               const unsigned char *__restrict__ vmov, double *__restrict__ px,
-                               double *__restrict__ py, int inst) {
+                               const unsigned char *__restrict__ vmov, const int *__restrict__ vnext,
+                               double *__restrict__ px, double *__restrict__ py, float *__restrict__ ebox,
+                               int inst) {
     const InstDesc &I = D[inst];
     const InstDyn &y = Y[inst];
-    double th = I.rotating ? I.a0 + I.a1 * sin(I.omega * y.t) : 0.0;
+    double th = I.rotating ? y.th : 0.0;
     double c = cos(th), s = sin(th);
     for (int k = threadIdx.x; k < I.nv; k += blockDim.x) {
         int a = I.voff + k;
@@ -590,30 +664,46 @@ __global__ void k_pose_current(const InstDesc *__restrict__ D, const InstDyn *__
         px[a] = xo;
         py[a] = yo;
     }
+    __syncthreads();
+    for (int k = threadIdx.x; k < I.nv; k += blockDim.x) {
+        int a = I.voff + k, b = vnext[a];
+        ebox[2 * a] = __double2float_rd(dmin(px[a], px[b]));
+        ebox[2 * a + 1] = __double2float_ru(dmax(px[a], px[b]));
+    }
 }
 
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-void launch_pose(const InstDesc *D, InstDyn *Y, const double *vx, const double *vy, const unsigned char *vmov,
-                 double *px, double *py, int total_v, int n_inst, int dir, int sidx, double dt, cudaStream_t st) {
-    k_pose<<<n_inst, 256, 0, st>>>(D, Y, vx, vy, vmov, px, py, total_v, dir, sidx, dt);
+static size_t geom_smem() { return sizeof(GeoWarp) * GEOM_WARPS; }
+
+void geom_init() {
+    cudaFuncSetAttribute(k_geom, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)geom_smem());
+    cudaFuncSetAttribute(k_classify, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)geom_smem());
 }
 
-void launch_geom(const InstDesc *D, InstDyn *Y, const double *px, const double *py, const int *vnext,
-                 const unsigned char *vmov, int total_v, int n_inst, int total_cols, int dir, BandRec *R,
-                 double *bnd, cudaStream_t st) {
+void launch_pose(const InstDesc *D, InstDyn *Y, const double *vx, const double *vy, const unsigned char *vmov,
+                 const int *vnext, double *px, double *py, float *ebox, int total_v, int n_inst, int dir, int sidx,
+                 double dt, cudaStream_t st) {
+    k_pose<<<n_inst, 256, 0, st>>>(D, Y, vx, vy, vmov, vnext, px, py, ebox, total_v, dir, sidx, dt);
+}
+
+void launch_geom(const InstDesc *D, InstDyn *Y, const double *px, const double *py, const float *ebox,
+                 const int *vnext, const unsigned char *vmov, int total_v, int n_inst, int total_cols, int dir,
+                 BandRec *R, double *bnd, cudaStream_t st) {
     int blocks = (total_cols + GEOM_WARPS - 1) / GEOM_WARPS;
     if (blocks > 0)
-        k_geom<<<blocks, GEOM_WARPS * 32, 0, st>>>(D, Y, px, py, vnext, vmov, total_v, n_inst, total_cols, dir, R, bnd);
+        k_geom<<<blocks, GEOM_WARPS * 32, geom_smem(), st>>>(D, Y, px, py, ebox, vnext, vmov, total_v, n_inst,
+                                                           total_cols, dir, R, bnd);
 }
 
 void launch_classify(const InstDesc *D, InstDyn *Y, const double *vx, const double *vy, const unsigned char *vmov,
-                     double *px, double *py, const int *vnext, int total_v, int inst, int nx, double *alpha_out,
-                     cudaStream_t st) {
-    k_pose_current<<<1, 256, 0, st>>>(D, Y, vx, vy, vmov, px, py, inst);
+                     double *px, double *py, float *ebox, const int *vnext, int total_v, int inst, int nx,
+                     double *alpha_out, cudaStream_t st) {
+    k_pose_current<<<1, 256, 0, st>>>(D, Y, vx, vy, vmov, vnext, px, py, ebox, inst);
     int blocks = (nx + GEOM_WARPS - 1) / GEOM_WARPS;
-    k_classify<<<blocks, GEOM_WARPS * 32, 0, st>>>(D, Y, px, py, vnext, vmov, total_v, inst, alpha_out);
+    k_classify<<<blocks, GEOM_WARPS * 32, geom_smem(), st>>>(D, Y, px, py, ebox, vnext, vmov, total_v, inst,
+                                                           alpha_out);
 }
 
 }  // namespace mb

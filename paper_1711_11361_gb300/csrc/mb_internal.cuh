@@ -13,6 +13,8 @@ constexpr double ALPHA_MIN = 1e-10;   // smaller volume fractions count as solid
 constexpr uint8_t CLS_SOLID = 1;      // alpha == 0
 constexpr uint8_t CLS_CUT = 2;        // touched by the body boundary, alpha > 0
 constexpr uint8_t CLS_BAND = 4;       // has a band record this sweep
+constexpr uint8_t CLS_TOUCH = 8;      // touched by the body boundary (any alpha)
+constexpr uint8_t CLS_MOVT = 16;      // touched by an edge of a moving polygon
 
 // band record flags
 constexpr int RF_TOUCH_A = 1, RF_TOUCH_B = 2, RF_TOUCH_M = 4, RF_MOVING = 8;
@@ -24,6 +26,7 @@ constexpr int RF_WALL = 256;          // wall data valid
 constexpr int RF_USE8 = 512;          // event uses the 8-neighbourhood
 constexpr int RF_BAD = 1024;          // positivity safeguard triggered
 constexpr int RF_NONBR = 2048;        // event without fluid neighbour
+constexpr int RF_MOV_B = 4096;        // a moving edge meets the cell at the end pose
 
 // instance error flags
 constexpr int ERR_UNSTABLE = 1, ERR_EDGE_CAP = 2, ERR_BAND_CAP = 4, ERR_NONBR = 8, ERR_STATE = 16;
@@ -60,6 +63,7 @@ struct InstDesc {
     void *Q[3];          // state buffers (T*), plane stride pitch*ny
     uint8_t *cls;
     int *rec;
+    double *alpha;       // volume fraction at the current pose (pitch layout)
     int nv, voff;        // vertices [voff, voff+nv) of the global pools
     int rotating;
     double U[2], pivot[2], a0, a1, omega;
@@ -73,6 +77,7 @@ struct InstDesc {
 
 struct InstDyn {
     double t, X, Y, dt;
+    double th;                  // rotation angle of the current pose
     long long step;
     int sweep_in_step;
     int err;
@@ -84,10 +89,15 @@ struct InstDyn {
     double Om;                  // rotation rate at the mid time
     double delta;               // translation along the sweep (world units)
     int col0, col1;
+    int row0, row1;             // rows of the body's extent over the sweep's poses
+    float lamf;                 // dt / h along the sweep (FP32 kernels)
+    int pad2;
+    double lam;                 // dt / h along the sweep
     int band_count;
     int nbad;
     int mixed;
-    int pad;
+    int nbadlist;
+    int badlist[16];            // first records flagged by the positivity check
     double wall_sum[MAXC];
 };
 

@@ -263,8 +263,7 @@ __global__ void k_band_sweep(const InstDesc *__restrict__ D, InstDyn *__restrict
     if (r - I.rec_base >= y.band_count) return;
     BandRec &b = R[r];
     const int l = dir == 0 ? b.j : b.i, k = dir == 0 ? b.i : b.j;
-    const double h = dir == 0 ? I.dx : I.dy;
-    const double lam = y.dt / h;
+    const double lam = y.lam;
     const T g = (T)I.gamma, lamT = (T)lam, av0 = (T)I.adv[0], av1 = (T)I.adv[1];
     const bool own_hi = I.rotating || y.delta >= 0.0;
     CellW<T> w[5];
@@ -350,8 +349,7 @@ __global__ void __launch_bounds__(256) k_bulk(const InstDesc *__restrict__ D, In
         const int nal = DIR == 0 ? I.nx : I.ny, nln = DIR == 0 ? I.ny : I.nx;
         const int a0 = DIR == 0 ? tx * W : ty * W;
         const int l0 = DIR == 0 ? ty * NL : tx * NL;
-        const double dt = Y[lo].dt;
-        const T lam = (T)(dt / (DIR == 0 ? I.dx : I.dy));
+        const T lam = sizeof(T) == 4 ? (T)Y[lo].lamf : (T)Y[lo].lam;
         const T g = (T)I.gamma, av0 = (T)I.adv[0], av1 = (T)I.adv[1];
         const int nc = I.nc, eq = I.eq;
         const size_t plane = (size_t)I.pitch * I.ny;
@@ -442,7 +440,7 @@ __global__ void __launch_bounds__(256) k_bulk(const InstDesc *__restrict__ D, In
         }
         __syncthreads();
         // phase 4: update cells 0..W-1 of the tile
-        double smax0 = 0.0, smax1 = 0.0;
+        T smax0 = T(0), smax1 = T(0);
         int bad = 0;
         for (int e = tid; e < W * NL; e += 256) {
             int l = DIR == 0 ? e / W : e % NL;
@@ -469,13 +467,13 @@ __global__ void __launch_bounds__(256) k_bulk(const InstDesc *__restrict__ D, In
                 T p = (g - T(1)) * (qn[3] - T(0.5) * (qn[1] * qn[1] + qn[2] * qn[2]) * ir);
                 if (!(qn[0] > T(0)) || !(p > T(0))) bad = 1;
                 if (last) {
-                    double c = sqrt((double)(g * p * ir));
-                    smax0 = fmax(smax0, fabs((double)(qn[1] * ir)) + c);
-                    smax1 = fmax(smax1, fabs((double)(qn[2] * ir)) + c);
+                    T c = tsqrt(g * p * ir);
+                    smax0 = fmax(smax0, fabs(qn[1] * ir) + c);
+                    smax1 = fmax(smax1, fabs(qn[2] * ir) + c);
                 }
             } else if (last) {
-                smax0 = fabs((double)av0);
-                smax1 = fabs((double)av1);
+                smax0 = fabs(av0);
+                smax1 = fabs(av1);
             }
         }
         if (bad) atomicOr(&Y[lo].err, ERR_UNSTABLE);
@@ -484,12 +482,13 @@ __global__ void __launch_bounds__(256) k_bulk(const InstDesc *__restrict__ D, In
                 smax0 = fmax(smax0, __shfl_xor_sync(0xffffffffu, smax0, o));
                 smax1 = fmax(smax1, __shfl_xor_sync(0xffffffffu, smax1, o));
             }
-            if ((tid & 31) == 0) { red[0][tid >> 5] = smax0; red[1][tid >> 5] = smax1; }
+            if ((tid & 31) == 0) { red[0][tid >> 5] = (double)smax0; red[1][tid >> 5] = (double)smax1; }
             __syncthreads();
             if (tid == 0) {
-                for (int k = 1; k < 8; ++k) { smax0 = fmax(smax0, red[0][k]); smax1 = fmax(smax1, red[1][k]); }
-                atomic_max_pos(&Y[lo].S[0], smax0);
-                atomic_max_pos(&Y[lo].S[1], smax1);
+                double m0 = red[0][0], m1 = red[1][0];
+                for (int k = 1; k < 8; ++k) { m0 = fmax(m0, red[0][k]); m1 = fmax(m1, red[1][k]); }
+                atomic_max_pos(&Y[lo].S[0], m0);
+                atomic_max_pos(&Y[lo].S[1], m1);
             }
         }
         __syncthreads();
@@ -555,7 +554,8 @@ __global__ void k_events(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y
         bool ok = q0 > 0.0 && p > 0.0 && isfinite(q0) && isfinite(q1) && isfinite(q2) && isfinite(q3);
         if (!ok) {
             x.flags |= RF_BAD;
-            atomicAdd(&y.nbad, 1);
+            int k = atomicAdd(&y.nbad, 1);
+            if (k < 16) y.badlist[k] = r;
         }
     }
 }
@@ -578,6 +578,7 @@ __global__ void k_mix(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y, B
     // advance pose and clock
     y.X = y.XB;
     y.Y = y.YB;
+    y.th = y.thB;
     if (sidx == 1) {
         y.t += y.dt;
         y.step += 1;
@@ -598,7 +599,10 @@ __global__ void k_mix(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y, B
     };
     auto root = [&](int k) { while (par[k] != k) k = par[k]; return k; };
     bool overflow = false;
-    for (int r = I.rec_base; r < I.rec_base + y.band_count; ++r) {
+    const bool listed = y.nbad <= 16;
+    const int nscan = listed ? y.nbad : y.band_count;
+    for (int s = 0; s < nscan; ++s) {
+        const int r = listed ? y.badlist[s] : I.rec_base + s;
         const BandRec &b = R[r];
         if (!(b.flags & RF_BAD)) continue;
         int kb = find_node(b.cell);
@@ -691,7 +695,10 @@ __global__ void k_finalize(const InstDesc *__restrict__ D, InstDyn *__restrict__
     } else {
         for (int k = 0; k < I.nc; ++k) Qo[k * plane + b.cell] = T(NAN);
     }
-    I.cls[b.cell] = (uint8_t)((b.aB == 0.0 ? CLS_SOLID : 0) | ((b.flags & RF_TOUCH_B) && b.aB > 0.0 ? CLS_CUT : 0));
+    const bool tB = (b.flags & RF_TOUCH_B) != 0;
+    I.cls[b.cell] = (uint8_t)((b.aB == 0.0 ? CLS_SOLID : 0) | (tB && b.aB > 0.0 ? CLS_CUT : 0) | (tB ? CLS_TOUCH : 0) |
+                              ((b.flags & RF_MOV_B) ? CLS_MOVT : 0));
+    I.alpha[b.cell] = b.aB;
     I.rec[b.cell] = -1;
 }
 
