@@ -596,9 +596,11 @@ int or_swept(or_sim *s, int d, double X, double Y, double theta, double delta, d
     return OR_OK;
 }
 
-/* Current alpha (at the present pose). */
+/* Current alpha (at the present pose: after the first sweep of a step the
+ * body has turned through half of the step's rotation). */
 static void current_alpha(or_sim *s, double *alpha) {
-    double th = rotating(s) ? theta_at(s, s->t) : 0.0;
+    double tp = s->t + (s->sweep_in_step == 1 ? 0.5 * s->dt_step : 0.0);
+    double th = rotating(s) ? theta_at(s, tp) : 0.0;
     pose_vertices(s, s->X, s->Y, th, rotating(s));
     or_geom g;
     geom_alloc(s, &g);

@@ -33,7 +33,7 @@ template <class T>
 void launch_band_stage(int, const InstDesc *, InstDyn *, BandRec *, const double *, int *, int, int, int, int, int,
                        int, int, int, cudaStream_t);
 template <class T>
-void launch_bulk(int, const InstDesc *, InstDyn *, const BandRec *, int, int, int, int, int, int, cudaStream_t);
+void launch_bulk(int, int, const InstDesc *, InstDyn *, const BandRec *, int, int, int, int, int, cudaStream_t);
 template <class T>
 int bulk_blocks_per_sm(int);
 template <class T>
@@ -151,6 +151,7 @@ mb_status mb_batch_create(int n, const mb_grid *grids, const double *gammas, con
             return fail(nullptr, MB_E_INVAL, "periodic boundaries must come in pairs");
         if (g.equation != MB_EULER && g.equation != MB_ADVECTION) return fail(nullptr, MB_E_INVAL, "unknown equation");
         if (g.precision != prec) return fail(nullptr, MB_E_INVAL, "all instances of a batch share one precision");
+        if (g.equation != grids[0].equation) return fail(nullptr, MB_E_INVAL, "all instances of a batch share one equation");
         if (!(g.cfl > 0.0 && g.cfl <= 1.0)) return fail(nullptr, MB_E_INVAL, "cfl must be in (0, 1]");
         const mb_body &b = bodies[k];
         if (b.npoly < 0 || (b.npoly > 0 && (!b.poly_start || !b.poly_moving || !b.vx || !b.vy)))
@@ -246,10 +247,12 @@ mb_status mb_batch_create(int n, const mb_grid *grids, const double *gammas, con
         I.gcol_max = gcols;
         I.gcol_off = col_total;
         col_total += gcols;
-        I.tiles_x[0] = (g.nx + 127) / 128;
-        I.ntiles[0] = I.tiles_x[0] * ((g.ny + 1) / 2);
+        // bulk work items: x sweep one warp per row; y sweep one warp per 32
+        // columns and 64-row segment
+        I.tiles_x[0] = 1;
+        I.ntiles[0] = g.ny;
         I.tiles_x[1] = (g.nx + 31) / 32;
-        I.ntiles[1] = I.tiles_x[1] * ((g.ny + 15) / 16);
+        I.ntiles[1] = I.tiles_x[1] * ((g.ny + 63) / 64);
         I.tile_off[0] = tiles0;
         I.tile_off[1] = tiles1;
         tiles0 += I.ntiles[0];
@@ -368,10 +371,11 @@ static mb_status do_sweep(mb_sim *s, int dir, double dt) {
         cudaEventCreate(&e1);
         cudaEventRecord(e0, st);
     }
+    const int eq = s->hd[0].eq;
     if (s->prec == MB_FP32)
-        launch_bulk<float>(dir, s->dd, s->dy, s->rec, s->n, s->total_tiles[dir], src, dst, last, s->bulk_grid[dir], st);
+        launch_bulk<float>(dir, eq, s->dd, s->dy, s->rec, s->n, s->total_tiles[dir], src, dst, last, st);
     else
-        launch_bulk<double>(dir, s->dd, s->dy, s->rec, s->n, s->total_tiles[dir], src, dst, last, s->bulk_grid[dir], st);
+        launch_bulk<double>(dir, eq, s->dd, s->dy, s->rec, s->n, s->total_tiles[dir], src, dst, last, st);
     if (s->timing) {
         cudaEventRecord(e1, st);
         s->evs.push_back({e0, e1});

@@ -312,187 +312,307 @@ __global__ void k_band_sweep(const InstDesc *__restrict__ D, InstDyn *__restrict
 }
 
 // ---------------------------------------------------------------------------
-// k_bulk: standard update of every non-band cell (SMEM tiles, persistent)
+// bulk sweep kernels: standard MUSCL-Hancock + HLLC update of every non-band
+// cell.  Faces touching a band cell take the stabilised value its record
+// holds (computed once by k_band_sweep), so every face flux is computed once.
 // ---------------------------------------------------------------------------
-template <int DIR> struct Tile;
-template <> struct Tile<0> { static constexpr int W = 128, NL = 2; };
-template <> struct Tile<1> { static constexpr int W = 16, NL = 32; };
+constexpr int YSEG = 64;    // rows per thread in the y sweep
 
-template <class T, int DIR>
-constexpr size_t bulk_smem() {
-    constexpr int W = Tile<DIR>::W, NL = Tile<DIR>::NL;
-    return sizeof(T) * MAXC * ((W + 4) * NL + 2 * (W + 2) * NL + (W + 1) * NL) + (W + 4) * NL + 64;
+template <class T, int NC>
+struct QV { T q[NC]; };
+
+template <class T, int NC>
+__device__ __forceinline__ void load_cell(const T *__restrict__ Q, size_t plane, int ci, bool flip, int in,
+                                          QV<T, NC> &v) {
+#pragma unroll
+    for (int k = 0; k < NC; ++k) v.q[k] = __ldg(Q + k * plane + ci);
+    if (NC == 4 && flip) v.q[in] = -v.q[in];
 }
 
-template <class T, int DIR>
-__global__ void __launch_bounds__(256) k_bulk(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y,
-                                              const BandRec *__restrict__ R, int n_inst, int total_tiles, int src,
-                                              int dst, int last) {
-    constexpr int W = Tile<DIR>::W, NL = Tile<DIR>::NL, WH = W + 4;
-    extern __shared__ __align__(16) unsigned char smem[];
-    T *sq = (T *)smem;                       // [MAXC][WH*NL]
-    T *sl = sq + MAXC * WH * NL;             // [MAXC][(W+2)*NL]
-    T *sr = sl + MAXC * (W + 2) * NL;        // [MAXC][(W+2)*NL]
-    T *sf = sr + MAXC * (W + 2) * NL;        // [MAXC][(W+1)*NL]
-    uint8_t *sc = (uint8_t *)(sf + MAXC * (W + 1) * NL);
-    __shared__ double red[2][8];
-    const int tid = threadIdx.x;
-    for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
-        int lo = 0, hi = n_inst - 1;
-        while (lo < hi) {
-            int mid = (lo + hi + 1) >> 1;
-            if (D[mid].tile_off[DIR] <= tile) lo = mid; else hi = mid - 1;
+template <class T, int NC>
+__device__ __forceinline__ void shfl_up(QV<T, NC> &o, const QV<T, NC> &v) {
+#pragma unroll
+    for (int k = 0; k < NC; ++k) o.q[k] = __shfl_up_sync(0xffffffffu, v.q[k], 1);
+}
+template <class T, int NC>
+__device__ __forceinline__ void shfl_dn(QV<T, NC> &o, const QV<T, NC> &v) {
+#pragma unroll
+    for (int k = 0; k < NC; ++k) o.q[k] = __shfl_down_sync(0xffffffffu, v.q[k], 1);
+}
+template <class T, int NC>
+__device__ __forceinline__ void shfl_idx(QV<T, NC> &o, const QV<T, NC> &v, int src) {
+#pragma unroll
+    for (int k = 0; k < NC; ++k) o.q[k] = __shfl_sync(0xffffffffu, v.q[k], src);
+}
+
+// face flux between cells (a-1, a) of a line: stabilised record value if a
+// band cell is adjacent, zero next to a solid cell, HLLC otherwise
+template <class T, int NC, int EQ, int DIR>
+__device__ __forceinline__ void face_flux(const InstDesc &I, const BandRec *__restrict__ R, int line, int a, int n,
+                                          uint8_t cl, uint8_t cr, T g, T av0, T av1, const QV<T, NC> &QRl,
+                                          const QV<T, NC> &QLr, QV<T, NC> &F) {
+    if ((cl | cr) & CLS_BAND) {
+        bool fl;
+        const int bclo = I.bc[2 * DIR], bchi = I.bc[2 * DIR + 1];
+        const int pb = ghost_map(a, n, bclo, bchi, &fl), pa = ghost_map(a - 1, n, bclo, bchi, &fl);
+        const int cib = DIR == 0 ? line * I.pitch + pb : pb * I.pitch + line;
+        const int cia = DIR == 0 ? line * I.pitch + pa : pa * I.pitch + line;
+        const bool b_real = a < n || bchi == 2;
+        const bool a_real = a - 1 >= 0 || bclo == 2;
+        if ((cr & CLS_BAND) && (b_real || !a_real || !(cl & CLS_BAND))) {
+            const BandRec &rb = R[I.rec[cib]];
+#pragma unroll
+            for (int k = 0; k < NC; ++k) F.q[k] = (T)rb.Flo[k];
+        } else {
+            const BandRec &ra = R[I.rec[cia]];
+#pragma unroll
+            for (int k = 0; k < NC; ++k) F.q[k] = (T)ra.Fhi[k];
         }
-        const InstDesc &I = D[lo];
-        const int lt = tile - I.tile_off[DIR];
-        const int tx = lt % I.tiles_x[DIR], ty = lt / I.tiles_x[DIR];
-        const int nal = DIR == 0 ? I.nx : I.ny, nln = DIR == 0 ? I.ny : I.nx;
-        const int a0 = DIR == 0 ? tx * W : ty * W;
-        const int l0 = DIR == 0 ? ty * NL : tx * NL;
-        const T lam = sizeof(T) == 4 ? (T)Y[lo].lamf : (T)Y[lo].lam;
-        const T g = (T)I.gamma, av0 = (T)I.adv[0], av1 = (T)I.adv[1];
-        const int nc = I.nc, eq = I.eq;
-        const size_t plane = (size_t)I.pitch * I.ny;
-        const T *Q = buf<T>(I, src);
-        T *Qo = bufw<T>(I, dst);
-        auto sidx = [&](int l, int kk) { return DIR == 0 ? l * WH + kk : kk * NL + l; };
-        // phase 1: load states and classes (ghosts by boundary condition)
-        for (int e = tid; e < WH * NL; e += 256) {
-            int l = DIR == 0 ? e / WH : e % NL;
-            int kk = DIR == 0 ? e % WH : e / NL;
-            int line = l0 + l;
-            int s = sidx(l, kk);
-            if (line >= nln) { sc[s] = CLS_SOLID; continue; }
-            bool flip;
-            int pos = ghost_map(a0 + kk - 2, nal, I.bc[2 * DIR], I.bc[2 * DIR + 1], &flip);
-            int ci = DIR == 0 ? line * I.pitch + pos : pos * I.pitch + line;
-            sc[s] = I.cls[ci];
-            for (int q = 0; q < nc; ++q) {
-                T v = Q[q * plane + ci];
-                if (flip && q == 1 + DIR) v = -v;
-                sq[q * WH * NL + s] = v;
-            }
-        }
-        __syncthreads();
-        // phase 2: evolved boundary states of cells -1..W
-        for (int e = tid; e < (W + 2) * NL; e += 256) {
-            int l = DIR == 0 ? e / (W + 2) : e % NL;
-            int m = DIR == 0 ? e % (W + 2) : e / NL;
-            int kk = m + 1;
-            int s0 = sidx(l, kk);
-            int so = DIR == 0 ? l * (W + 2) + m : m * NL + l;
-            if (sc[s0] & CLS_SOLID) continue;
-            T qm[MAXC], q0[MAXC], qp[MAXC], QL[MAXC], QR[MAXC];
-            int sm = sidx(l, kk - 1), sp = sidx(l, kk + 1);
-            for (int q = 0; q < nc; ++q) {
-                qm[q] = sq[q * WH * NL + sm];
-                q0[q] = sq[q * WH * NL + s0];
-                qp[q] = sq[q * WH * NL + sp];
-            }
-            bool lim = !(sc[sm] & CLS_SOLID) && !(sc[sp] & CLS_SOLID);
-            evolve(eq, g, DIR, lam, av0, av1, qm, q0, qp, lim, QL, QR);
-            for (int q = 0; q < nc; ++q) {
-                sl[q * (W + 2) * NL + so] = QL[q];
-                sr[q * (W + 2) * NL + so] = QR[q];
-            }
-        }
-        __syncthreads();
-        // phase 3: face fluxes 0..W (face m between cells m-1 and m);
-        // faces touching a band cell take the stabilised value of its record
-        for (int e = tid; e < (W + 1) * NL; e += 256) {
-            int l = DIR == 0 ? e / (W + 1) : e % NL;
-            int m = DIR == 0 ? e % (W + 1) : e / NL;
-            int sa = sidx(l, m + 1), sb = sidx(l, m + 2);
-            int so = DIR == 0 ? l * (W + 1) + m : m * NL + l;
-            uint8_t ca = sc[sa], cb = sc[sb];
-            T F[MAXC] = {T(0), T(0), T(0), T(0)};
-            if ((ca | cb) & CLS_BAND) {
-                int line = l0 + l;
-                if (line < nln) {
-                    bool fl;
-                    int pb = ghost_map(a0 + m, nal, I.bc[2 * DIR], I.bc[2 * DIR + 1], &fl);
-                    int pa = ghost_map(a0 + m - 1, nal, I.bc[2 * DIR], I.bc[2 * DIR + 1], &fl);
-                    int cib = DIR == 0 ? line * I.pitch + pb : pb * I.pitch + line;
-                    int cia = DIR == 0 ? line * I.pitch + pa : pa * I.pitch + line;
-                    // a ghost beyond a non-periodic side mirrors a real cell:
-                    // take the record of the real cell on the other side
-                    const bool b_real = (a0 + m < nal) || I.bc[2 * DIR + 1] == 2;
-                    const bool a_real = (a0 + m - 1 >= 0) || I.bc[2 * DIR] == 2;
-                    if ((cb & CLS_BAND) && (b_real || !a_real || !(ca & CLS_BAND))) {
-                        const BandRec &rb = R[I.rec[cib]];
-                        for (int q = 0; q < nc; ++q) F[q] = (T)rb.Flo[q];
-                    } else {
-                        const BandRec &ra = R[I.rec[cia]];
-                        for (int q = 0; q < nc; ++q) F[q] = (T)ra.Fhi[q];
-                    }
-                }
-            } else if (!((ca | cb) & CLS_SOLID)) {
-                int ia = DIR == 0 ? l * (W + 2) + m : m * NL + l;
-                int ib = DIR == 0 ? l * (W + 2) + m + 1 : (m + 1) * NL + l;
-                T QRa[MAXC], QLb[MAXC];
-                for (int q = 0; q < nc; ++q) {
-                    QRa[q] = sr[q * (W + 2) * NL + ia];
-                    QLb[q] = sl[q * (W + 2) * NL + ib];
-                }
-                riemann_flux(eq, g, DIR, av0, av1, QRa, QLb, F);
-            }
-            for (int q = 0; q < nc; ++q) sf[q * (W + 1) * NL + so] = F[q];
-        }
-        __syncthreads();
-        // phase 4: update cells 0..W-1 of the tile
-        T smax0 = T(0), smax1 = T(0);
-        int bad = 0;
-        for (int e = tid; e < W * NL; e += 256) {
-            int l = DIR == 0 ? e / W : e % NL;
-            int m = DIR == 0 ? e % W : e / NL;
-            int a = a0 + m, line = l0 + l;
-            if (a >= nal || line >= nln) continue;
-            int s0 = sidx(l, m + 2);
-            uint8_t c0 = sc[s0];
-            if (c0 & CLS_BAND) continue;
-            int ci = DIR == 0 ? line * I.pitch + a : a * I.pitch + line;
-            if (c0 & CLS_SOLID) {
-                for (int q = 0; q < nc; ++q) Qo[q * plane + ci] = T(NAN);
-                continue;
-            }
-            int flo = DIR == 0 ? l * (W + 1) + m : m * NL + l;
-            int fhi = DIR == 0 ? l * (W + 1) + m + 1 : (m + 1) * NL + l;
-            T qn[MAXC];
-            for (int q = 0; q < nc; ++q) {
-                qn[q] = sq[q * WH * NL + s0] + lam * (sf[q * (W + 1) * NL + flo] - sf[q * (W + 1) * NL + fhi]);
-                Qo[q * plane + ci] = qn[q];
-            }
-            if (eq == 0) {
-                T ir = fdiv(T(1), qn[0]);
-                T p = (g - T(1)) * (qn[3] - T(0.5) * (qn[1] * qn[1] + qn[2] * qn[2]) * ir);
-                if (!(qn[0] > T(0)) || !(p > T(0))) bad = 1;
-                if (last) {
-                    T c = tsqrt(g * p * ir);
-                    smax0 = fmax(smax0, fabs(qn[1] * ir) + c);
-                    smax1 = fmax(smax1, fabs(qn[2] * ir) + c);
-                }
-            } else if (last) {
-                smax0 = fabs(av0);
-                smax1 = fabs(av1);
-            }
-        }
-        if (bad) atomicOr(&Y[lo].err, ERR_UNSTABLE);
-        if (last) {
-            for (int o = 16; o > 0; o >>= 1) {
-                smax0 = fmax(smax0, __shfl_xor_sync(0xffffffffu, smax0, o));
-                smax1 = fmax(smax1, __shfl_xor_sync(0xffffffffu, smax1, o));
-            }
-            if ((tid & 31) == 0) { red[0][tid >> 5] = (double)smax0; red[1][tid >> 5] = (double)smax1; }
-            __syncthreads();
-            if (tid == 0) {
-                double m0 = red[0][0], m1 = red[1][0];
-                for (int k = 1; k < 8; ++k) { m0 = fmax(m0, red[0][k]); m1 = fmax(m1, red[1][k]); }
-                atomic_max_pos(&Y[lo].S[0], m0);
-                atomic_max_pos(&Y[lo].S[1], m1);
-            }
-        }
-        __syncthreads();
+        return;
     }
+    if ((cl | cr) & CLS_SOLID) {
+#pragma unroll
+        for (int k = 0; k < NC; ++k) F.q[k] = T(0);
+        return;
+    }
+    riemann_flux(EQ, g, DIR, av0, av1, QRl.q, QLr.q, F.q);
+}
+
+// new state of a non-band cell; wave speeds and positivity for the CFL step
+template <class T, int NC, int EQ>
+__device__ __forceinline__ void update_cell(T *__restrict__ Qo, size_t plane, int ci, uint8_t c0, T lam, T g, T av0,
+                                            T av1, const QV<T, NC> &q, const QV<T, NC> &Flo, const QV<T, NC> &Fhi,
+                                            bool last, T &s0, T &s1, int &bad) {
+    if (c0 & CLS_BAND) return;
+    if (c0 & CLS_SOLID) {
+#pragma unroll
+        for (int k = 0; k < NC; ++k) Qo[k * plane + ci] = T(NAN);
+        return;
+    }
+    T qn[NC];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+        qn[k] = q.q[k] + lam * (Flo.q[k] - Fhi.q[k]);
+        Qo[k * plane + ci] = qn[k];
+    }
+    if (EQ == 0) {
+        T ir = fdiv(T(1), qn[0]);
+        T p = (g - T(1)) * (qn[NC - 1] - T(0.5) * (qn[1 % NC] * qn[1 % NC] + qn[2 % NC] * qn[2 % NC]) * ir);
+        if (!(qn[0] > T(0)) || !(p > T(0))) bad = 1;
+        if (last) {
+            T c = tsqrt(g * p * ir);
+            s0 = fmax(s0, fabs(qn[1 % NC] * ir) + c);
+            s1 = fmax(s1, fabs(qn[2 % NC] * ir) + c);
+        }
+    } else if (last) {
+        s0 = fabs(av0);
+        s1 = fabs(av1);
+    }
+}
+
+template <class T>
+__device__ __forceinline__ void finish_warp(InstDyn &y, bool last, T s0, T s1, int bad) {
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&y.err, ERR_UNSTABLE);
+    if (last) {
+        for (int o = 16; o > 0; o >>= 1) {
+            s0 = fmax(s0, __shfl_xor_sync(0xffffffffu, s0, o));
+            s1 = fmax(s1, __shfl_xor_sync(0xffffffffu, s1, o));
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomic_max_pos(&y.S[0], (double)s0);
+            atomic_max_pos(&y.S[1], (double)s1);
+        }
+    }
+}
+
+__device__ __forceinline__ int find_inst_warp(const InstDesc *D, int n_inst, int gw, int dir) {
+    int lo = 0, hi = n_inst - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (D[mid].tile_off[dir] <= gw) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// x sweep: one warp per row, lanes = 32 consecutive cells; the row is
+// processed chunk by chunk, the update trailing the flux computation by one
+// chunk so that the last lane finds its high face in the next chunk
+template <class T, int EQ>
+__global__ void __launch_bounds__(256) k_bulk_x(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y,
+                                                const BandRec *__restrict__ R, int n_inst, int total_warps, int src,
+                                                int dst, int last) {
+    constexpr int NC = EQ == 0 ? 4 : 1;
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (gw >= total_warps) return;
+    const int inst = find_inst_warp(D, n_inst, gw, 0);
+    const InstDesc &I = D[inst];
+    InstDyn &y = Y[inst];
+    const int j = gw - I.tile_off[0];
+    const int n = I.nx;
+    const T lam = sizeof(T) == 4 ? (T)y.lamf : (T)y.lam;
+    const T g = (T)I.gamma, av0 = (T)I.adv[0], av1 = (T)I.adv[1];
+    const size_t plane = (size_t)I.pitch * I.ny;
+    const T *__restrict__ Q = (const T *)I.Q[src];
+    T *__restrict__ Qo = (T *)I.Q[dst];
+    const int rowb = j * I.pitch;
+    const int bclo = I.bc[0], bchi = I.bc[1];
+    auto load = [&](int c, QV<T, NC> &v, uint8_t &cl) {
+        const int a = 32 * c + lane;
+        if (a < -2 || a > n + 1) {
+#pragma unroll
+            for (int k = 0; k < NC; ++k) v.q[k] = T(1);
+            cl = CLS_SOLID;
+            return;
+        }
+        bool fl;
+        const int p = ghost_map(a, n, bclo, bchi, &fl);
+        cl = I.cls[rowb + p];
+        load_cell<T, NC>(Q, plane, rowb + p, fl, 1, v);
+    };
+    const int c_last = (n + 1) >> 5;
+    QV<T, NC> Qm, Q0, Qp, QL, QR, F, Fprev, nb, nb2;
+    uint8_t cm, c0, cp;
+    load(-1, Qm, cm);
+    load(0, Q0, c0);
+    load(1, Qp, cp);
+    // evolved right state of cell -1 (lane 31 of chunk -1)
+    {
+        shfl_up(nb, Qm);
+        shfl_dn(nb2, Qm);
+        QV<T, NC> t;
+        shfl_idx(t, Q0, 0);
+        if (lane == 31) nb2 = t;
+        const int cmu = __shfl_up_sync(0xffffffffu, (int)cm, 1);
+        int cmd = __shfl_down_sync(0xffffffffu, (int)cm, 1);
+        const int c00 = __shfl_sync(0xffffffffu, (int)c0, 0);
+        if (lane == 31) cmd = c00;
+        const bool lim = !(cmu & CLS_SOLID) && !(cmd & CLS_SOLID);
+        evolve(EQ, g, 0, lam, av0, av1, nb.q, Qm.q, nb2.q, lim, QL.q, QR.q);
+    }
+    QV<T, NC> QRc;
+    shfl_idx(QRc, QR, 31);
+    int cRc = __shfl_sync(0xffffffffu, (int)cm, 31);
+    T s0 = T(0), s1 = T(0);
+    int bad = 0;
+    for (int c = 0; c <= c_last; ++c) {
+        // neighbours of chunk c
+        QV<T, NC> left, right, t;
+        shfl_up(left, Q0);
+        shfl_idx(t, Qm, 31);
+        if (lane == 0) left = t;
+        shfl_dn(right, Q0);
+        shfl_idx(t, Qp, 0);
+        if (lane == 31) right = t;
+        int cl_ = __shfl_up_sync(0xffffffffu, (int)c0, 1);
+        int cm31 = __shfl_sync(0xffffffffu, (int)cm, 31);
+        if (lane == 0) cl_ = cm31;
+        int cr_ = __shfl_down_sync(0xffffffffu, (int)c0, 1);
+        int cp0 = __shfl_sync(0xffffffffu, (int)cp, 0);
+        if (lane == 31) cr_ = cp0;
+        const bool lim = !(cl_ & CLS_SOLID) && !(cr_ & CLS_SOLID);
+        evolve(EQ, g, 0, lam, av0, av1, left.q, Q0.q, right.q, lim, QL.q, QR.q);
+        // face between cells a-1 and a
+        QV<T, NC> QRl;
+        shfl_up(QRl, QR);
+        if (lane == 0) QRl = QRc;
+        const int a = 32 * c + lane;
+        if (a >= 0 && a <= n) face_flux<T, NC, EQ, 0>(I, R, j, a, n, (uint8_t)cl_, c0, g, av0, av1, QRl, QL, F);
+        // update chunk c-1
+        if (c >= 1) {
+            QV<T, NC> Fhi;
+            shfl_dn(Fhi, Fprev);
+            shfl_idx(t, F, 0);
+            if (lane == 31) Fhi = t;
+            const int ap = a - 32;
+            if (ap >= 0 && ap < n)
+                update_cell<T, NC, EQ>(Qo, plane, rowb + ap, cm, lam, g, av0, av1, Qm, Fprev, Fhi, last, s0, s1, bad);
+        }
+        shfl_idx(QRc, QR, 31);
+        Fprev = F;
+        Qm = Q0; cm = c0;
+        Q0 = Qp; c0 = cp;
+        load(c + 2, Qp, cp);
+    }
+    // the last chunk (its high faces were computed in the final iteration)
+    {
+        QV<T, NC> Fhi;
+        shfl_dn(Fhi, Fprev);
+        const int ap = 32 * c_last + lane;
+        if (ap >= 0 && ap < n && lane < 31)
+            update_cell<T, NC, EQ>(Qo, plane, rowb + ap, cm, lam, g, av0, av1, Qm, Fprev, Fhi, last, s0, s1, bad);
+    }
+    (void)cRc;
+    finish_warp<T>(y, last != 0, s0, s1, bad);
+}
+
+// y sweep: one thread per column and segment of YSEG rows, marching upward
+// with a register window; 32 consecutive columns per warp keep every load
+// and store coalesced
+template <class T, int EQ>
+__global__ void __launch_bounds__(256) k_bulk_y(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y,
+                                                const BandRec *__restrict__ R, int n_inst, int total_warps, int src,
+                                                int dst, int last) {
+    constexpr int NC = EQ == 0 ? 4 : 1;
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (gw >= total_warps) return;
+    const int inst = find_inst_warp(D, n_inst, gw, 1);
+    const InstDesc &I = D[inst];
+    InstDyn &y = Y[inst];
+    const int local = gw - I.tile_off[1];
+    const int ncg = I.tiles_x[1];
+    const int cg = local % ncg, sg = local / ncg;
+    const int i_raw = cg * 32 + lane;
+    const bool active = i_raw < I.nx;
+    const int i = active ? i_raw : I.nx - 1;
+    const int n = I.ny;
+    const int j0 = sg * YSEG, j1 = min(n, j0 + YSEG);
+    const T lam = sizeof(T) == 4 ? (T)y.lamf : (T)y.lam;
+    const T g = (T)I.gamma, av0 = (T)I.adv[0], av1 = (T)I.adv[1];
+    const size_t plane = (size_t)I.pitch * I.ny;
+    const T *__restrict__ Q = (const T *)I.Q[src];
+    T *__restrict__ Qo = (T *)I.Q[dst];
+    const int bclo = I.bc[2], bchi = I.bc[3];
+    auto load = [&](int r, QV<T, NC> &v, uint8_t &cl) {
+        bool fl;
+        const int p = ghost_map(r, n, bclo, bchi, &fl);
+        const int ci = p * I.pitch + i;
+        cl = I.cls[ci];
+        load_cell<T, NC>(Q, plane, ci, fl, 2, v);
+    };
+    QV<T, NC> qa, qm, qc, qp, qq, QL, QR, QRc, F, Fprev;
+    uint8_t ca, cm, cc, cp, cq;
+    load(j0 - 2, qa, ca);
+    load(j0 - 1, qm, cm);
+    load(j0, qc, cc);
+    load(j0 + 1, qp, cp);
+    load(j0 + 2, qq, cq);
+    // evolved top state of row j0-1
+    evolve(EQ, g, 1, lam, av0, av1, qa.q, qm.q, qc.q, !(ca & CLS_SOLID) && !(cc & CLS_SOLID), QL.q, QRc.q);
+    T s0 = T(0), s1 = T(0);
+    int bad = 0;
+    for (int f = j0; f <= j1; ++f) {
+        // window: qm = row f-1, qc = row f, qp = row f+1, qq = row f+2
+        evolve(EQ, g, 1, lam, av0, av1, qm.q, qc.q, qp.q, !(cm & CLS_SOLID) && !(cp & CLS_SOLID), QL.q, QR.q);
+        face_flux<T, NC, EQ, 1>(I, R, i, f, n, cm, cc, g, av0, av1, QRc, QL, F);
+        if (f > j0 && active)
+            update_cell<T, NC, EQ>(Qo, plane, (f - 1) * I.pitch + i, cm, lam, g, av0, av1, qm, Fprev, F, last, s0,
+                                   s1, bad);
+        QRc = QR;
+        Fprev = F;
+        qm = qc; cm = cc;
+        qc = qp; cc = cp;
+        qp = qq; cp = cq;
+        if (f + 3 <= j1 + 1) load(f + 3, qq, cq);
+    }
+    finish_warp<T>(y, last != 0, s0, s1, bad);
+}
+
+template <class T, int EQ>
+void bulk_attr_t(int dir) {
+    if (dir == 0) cudaFuncSetAttribute(k_bulk_x<T, EQ>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+    else cudaFuncSetAttribute(k_bulk_y<T, EQ>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -772,34 +892,25 @@ void launch_band_stage(int stage, const InstDesc *D, InstDyn *Y, BandRec *R, con
     }
 }
 
-template <class T, int DIR>
-void launch_bulk_t(const InstDesc *D, InstDyn *Y, const BandRec *R, int n_inst, int total_tiles, int src, int dst,
-                   int last, int grid, cudaStream_t st) {
-    constexpr size_t sm = bulk_smem<T, DIR>();   // opt-in size set once by bulk_blocks_per_sm
-    int g = grid < total_tiles ? grid : total_tiles;
-    if (g > 0) k_bulk<T, DIR><<<g, 256, sm, st>>>(D, Y, R, n_inst, total_tiles, src, dst, last);
-}
-
 template <class T>
-void launch_bulk(int dir, const InstDesc *D, InstDyn *Y, const BandRec *R, int n_inst, int total_tiles, int src,
-                 int dst, int last, int grid, cudaStream_t st) {
-    if (dir == 0) launch_bulk_t<T, 0>(D, Y, R, n_inst, total_tiles, src, dst, last, grid, st);
-    else launch_bulk_t<T, 1>(D, Y, R, n_inst, total_tiles, src, dst, last, grid, st);
+void launch_bulk(int dir, int eq, const InstDesc *D, InstDyn *Y, const BandRec *R, int n_inst, int total_warps,
+                 int src, int dst, int last, cudaStream_t st) {
+    int blocks = (total_warps + 7) / 8;
+    if (blocks <= 0) return;
+    if (dir == 0) {
+        if (eq == 0) k_bulk_x<T, 0><<<blocks, 256, 0, st>>>(D, Y, R, n_inst, total_warps, src, dst, last);
+        else k_bulk_x<T, 1><<<blocks, 256, 0, st>>>(D, Y, R, n_inst, total_warps, src, dst, last);
+    } else {
+        if (eq == 0) k_bulk_y<T, 0><<<blocks, 256, 0, st>>>(D, Y, R, n_inst, total_warps, src, dst, last);
+        else k_bulk_y<T, 1><<<blocks, 256, 0, st>>>(D, Y, R, n_inst, total_warps, src, dst, last);
+    }
 }
 
 template <class T>
 int bulk_blocks_per_sm(int dir) {
-    int nb = 0;
-    if (dir == 0) {
-        constexpr size_t sm = bulk_smem<T, 0>();
-        cudaFuncSetAttribute(k_bulk<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bulk<T, 0>, 256, sm);
-    } else {
-        constexpr size_t sm = bulk_smem<T, 1>();
-        cudaFuncSetAttribute(k_bulk<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bulk<T, 1>, 256, sm);
-    }
-    return nb > 0 ? nb : 1;
+    bulk_attr_t<T, 0>(dir);
+    bulk_attr_t<T, 1>(dir);
+    return 1;
 }
 
 template <class T>
@@ -814,7 +925,7 @@ void launch_read_state(const InstDesc *D, double *out, int inst, int b, cudaStre
 #define MB_INST(T)                                                                                                \
     template void launch_band_stage<T>(int, const InstDesc *, InstDyn *, BandRec *, const double *, int *, int, int, \
                                        int, int, int, int, int, int, cudaStream_t);                                \
-    template void launch_bulk<T>(int, const InstDesc *, InstDyn *, const BandRec *, int, int, int, int, int, int,  \
+    template void launch_bulk<T>(int, int, const InstDesc *, InstDyn *, const BandRec *, int, int, int, int, int,  \
                                  cudaStream_t);                                                                    \
     template int bulk_blocks_per_sm<T>(int);                                                                       \
     template void launch_write_state<T>(const InstDesc *, InstDyn *, const double *, int, int, cudaStream_t);      \
