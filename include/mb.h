@@ -158,6 +158,34 @@ int mb_band_record_size(void);
 mb_status mb_enable_timing(mb_sim *sim, int enable);
 mb_status mb_kernel_time(mb_sim *sim, double *total_ms, int *launches);
 
+/* Allocation-free cut-cell classification (the paper has no counterpart: it
+ * exists for callers that may not allocate device memory -- code running
+ * where the application forbids cudaMalloc, such as real-time loops or
+ * plugins whose host framework owns all device memory).
+ *
+ * Computes, for the grid `grid` and the polygons of `body` posed with
+ * translation (X, Y) and rotation theta about motion->pivot (moving polygons
+ * only), the volume fraction of every cell into alpha_dev (nx*ny doubles,
+ * x fastest) and its class byte into class_dev (nx*ny bytes: 1 solid,
+ * 2 cut, 8 touched by the body boundary, 16 touched by a moving polygon).
+ * Both outputs are caller-owned DEVICE arrays; the body arrays are host
+ * arrays and may be reused when the call returns.  Work is queued on
+ * `stream` (a cudaStream_t, NULL for the legacy default stream).
+ *
+ * Allocates nothing: its scratch is a fixed 0.7 MB device array inside the
+ * library, held by every GPU that loads it until the process exits.  Limits:
+ * at most 16384 polygon vertices, nx and ny at most 8192; larger requests
+ * return MB_E_INVAL with a message from mb_noalloc_last_error().  The first
+ * call on each device looks up that array's device address and should come
+ * before any stream capture.  All calls share the array, so calls that
+ * overlap on the GPU (for example on two streams) race: serialise them. */
+mb_status mb_cut_cells_noalloc(const mb_grid *grid, const mb_body *body, const mb_motion *motion,
+                               double X, double Y, double theta, double *alpha_dev,
+                               unsigned char *class_dev, void *stream);
+
+/* Text of the last error of mb_cut_cells_noalloc. */
+const char *mb_noalloc_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

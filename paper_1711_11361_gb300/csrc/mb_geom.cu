@@ -13,6 +13,10 @@
 // line).  Only edges meeting R enter, so no far-away edge is ever integrated.
 #include "mb_internal.cuh"
 
+#include <cstring>
+#include <string>
+#include <vector>
+
 namespace mb {
 
 constexpr int GEOM_WARPS = 4;
@@ -707,3 +711,195 @@ void launch_classify(const InstDesc *D, InstDyn *Y, const double *vx, const doub
 }
 
 }  // namespace mb
+
+// ---------------------------------------------------------------------------
+// Allocation-free cut-cell classification.
+//
+// For callers that cannot allocate device memory themselves (code that runs
+// while an application forbids cudaMalloc: inside real-time or latency-
+// critical loops, in plugins whose host framework owns every allocation, or
+// in processes near their memory limit), this entry point computes the volume
+// fractions and classes of a posed body with no allocation at all.  Its
+// working memory -- the instance descriptor, the copied vertices, the posed
+// vertices and their FP32 x-bounds -- lives in one file-scope device array
+// of fixed size that every GPU loading this library holds until the process
+// exits.  All calls share that array: calls that overlap on the GPU (e.g. on
+// two streams) race and must be serialised by the caller.
+// ---------------------------------------------------------------------------
+#include "../../include/mb.h"
+
+namespace mb {
+
+constexpr int NA_MAX_V = 16384;             // polygon vertices per call
+constexpr int NA_MAX_N = 8192;              // nx and ny per call
+constexpr size_t NA_OFF_DESC = 0;
+constexpr size_t NA_OFF_DYN = 1024;
+constexpr size_t NA_OFF_VX = 2048;
+constexpr size_t NA_OFF_VY = NA_OFF_VX + 8 * (size_t)NA_MAX_V;
+constexpr size_t NA_OFF_PX = NA_OFF_VY + 8 * (size_t)NA_MAX_V;
+constexpr size_t NA_OFF_PY = NA_OFF_PX + 8 * (size_t)NA_MAX_V;
+constexpr size_t NA_OFF_EBOX = NA_OFF_PY + 8 * (size_t)NA_MAX_V;
+constexpr size_t NA_OFF_NEXT = NA_OFF_EBOX + 8 * (size_t)NA_MAX_V;
+constexpr size_t NA_OFF_MOV = NA_OFF_NEXT + 4 * (size_t)NA_MAX_V;
+constexpr size_t NA_BYTES = NA_OFF_MOV + (size_t)NA_MAX_V;   // about 0.7 MB
+
+static __device__ __align__(256) unsigned char g_na_scratch[NA_BYTES];
+
+// host-side stand-in `g_na_scratch` is not a device address: kernels get the
+// address that cudaGetSymbolAddress returns for the current device
+static void *g_na_addr[64];
+static bool g_na_ready[64];
+
+// variant of k_classify writing unpitched outputs and no record map
+__global__ void __launch_bounds__(GEOM_WARPS * 32) k_classify_na(const InstDesc *__restrict__ D,
+                                                               InstDyn *__restrict__ Y,
+                                                               const double *__restrict__ px,
+                                                               const double *__restrict__ py,
+                                                               const float *__restrict__ ebox,
+                                                               const int *__restrict__ vnext,
+                                                               const unsigned char *__restrict__ vmov, int total_v,
+                                                               double *__restrict__ alpha_out,
+                                                               unsigned char *__restrict__ cls_out) {
+    extern __shared__ __align__(16) unsigned char gsm[];
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    GeoWarp &W = ((GeoWarp *)gsm)[wib];
+    GeoBuf &G = W.G;
+    const InstDesc &I = D[0];
+    const int i = blockIdx.x * GEOM_WARPS + wib;
+    if (i >= I.nx) return;
+    const double xl = node_coord(I.x0, i, I.dx), xr = node_coord(I.x0, i + 1, I.dx);
+    const int nwords = (I.ny + 31) >> 5;
+    int err = 0;
+    for (int w = lane; w < nwords; w += 32) W.bB[w] = 0u;
+    __syncwarp();
+    if (I.nv) gather(G, I, px, py, ebox, vnext, vmov, 0, total_v, xl, xr, xl, xr, W.bB, lane, &err);
+    else if (lane == 0) { G.cnt = 0; G.lcnt[0] = G.lcnt[1] = 0; }
+    __syncwarp();
+    for (int j = lane; j < I.ny; j += 32) {
+        const double yb = node_coord(I.y0, j, I.dy), yt = node_coord(I.y0, j + 1, I.dy);
+        const bool touched = (W.bB[j >> 5] >> (j & 31)) & 1u;
+        bool mov = false;
+        const double a = cell_alpha(G, I, j, xl, xr, yb, yt, nullptr, nullptr, &mov);
+        uint8_t c = touched ? CLS_TOUCH : 0;
+        if (mov) c |= CLS_MOVT;
+        if (a == 0.0) c |= CLS_SOLID;
+        else if (touched) c |= CLS_CUT;
+        alpha_out[(size_t)j * I.nx + i] = a;
+        cls_out[(size_t)j * I.nx + i] = c;
+    }
+    if (lane == 0 && err) atomicOr(&Y[0].err, err);
+}
+
+}  // namespace mb
+
+static std::string g_na_error;
+
+extern "C" mb_status mb_cut_cells_noalloc(const mb_grid *grid, const mb_body *body, const mb_motion *motion,
+                                          double X, double Y, double theta, double *alpha_dev,
+                                          unsigned char *class_dev, void *stream) {
+    using namespace mb;
+    if (!grid || !body || !motion || !alpha_dev || !class_dev) {
+        g_na_error = "mb_cut_cells_noalloc: NULL argument";
+        return MB_E_INVAL;
+    }
+    const int nv = body->npoly > 0 ? body->poly_start[body->npoly] : 0;
+    if (grid->nx < 1 || grid->ny < 1 || grid->nx > NA_MAX_N || grid->ny > NA_MAX_N) {
+        g_na_error = "mb_cut_cells_noalloc: nx and ny must lie in [1, 8192]";
+        return MB_E_INVAL;
+    }
+    if (nv > NA_MAX_V) {
+        g_na_error = "mb_cut_cells_noalloc: more than 16384 polygon vertices (the fixed scratch limit)";
+        return MB_E_INVAL;
+    }
+    if (!(grid->x1 > grid->x0) || !(grid->y1 > grid->y0)) {
+        g_na_error = "mb_cut_cells_noalloc: empty domain";
+        return MB_E_INVAL;
+    }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= 64) {
+        g_na_error = std::string("mb_cut_cells_noalloc: no current device: ") + cudaGetErrorString(e);
+        return MB_E_CUDA;
+    }
+    // one-time set-up on this device (the first call per device does it, and
+    // should therefore come before any stream capture)
+    if (!g_na_ready[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_na_scratch);
+        if (e != cudaSuccess || !p) {
+            g_na_error = std::string("mb_cut_cells_noalloc: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e);
+            return MB_E_CUDA;
+        }
+        e = cudaFuncSetAttribute(k_classify_na, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)geom_smem());
+        if (e != cudaSuccess) {
+            g_na_error = std::string("mb_cut_cells_noalloc: kernel attribute: ") + cudaGetErrorString(e);
+            return MB_E_CUDA;
+        }
+        g_na_addr[dev] = p;
+        g_na_ready[dev] = true;
+    }
+    unsigned char *base = (unsigned char *)g_na_addr[dev];
+    cudaStream_t st = (cudaStream_t)stream;
+    // descriptor of a one-instance, unpitched grid
+    InstDesc I;
+    memset(&I, 0, sizeof(I));
+    I.nx = grid->nx; I.ny = grid->ny; I.pitch = grid->nx;
+    I.nc = grid->equation == MB_EULER ? 4 : 1;
+    I.x0 = grid->x0; I.y0 = grid->y0;
+    I.dx = (grid->x1 - grid->x0) / (double)grid->nx;
+    I.dy = (grid->y1 - grid->y0) / (double)grid->ny;
+    for (int q = 0; q < 4; ++q) I.bc[q] = grid->bc[q];
+    I.nv = nv;
+    I.voff = 0;
+    I.rotating = (theta != 0.0 || motion->a0 != 0.0 || motion->a1 != 0.0) ? 1 : 0;
+    I.pivot[0] = motion->pivot[0]; I.pivot[1] = motion->pivot[1];
+    InstDyn y;
+    memset(&y, 0, sizeof(y));   // clears the error word of this call
+    y.X = X; y.Y = Y; y.th = theta;
+    static thread_local std::vector<int> hnext;
+    static thread_local std::vector<unsigned char> hmov;
+    hnext.assign(nv > 0 ? nv : 1, 0);
+    hmov.assign(nv > 0 ? nv : 1, 0);
+    for (int p = 0; p < body->npoly; ++p) {
+        const int a = body->poly_start[p], z = body->poly_start[p + 1];
+        if (z - a < 3) {
+            g_na_error = "mb_cut_cells_noalloc: polygon with fewer than 3 vertices";
+            return MB_E_INVAL;
+        }
+        for (int v = a; v < z; ++v) {
+            hnext[v] = v + 1 < z ? v + 1 : a;
+            hmov[v] = body->poly_moving[p] ? 1 : 0;
+        }
+    }
+    e = cudaMemcpyAsync(base + NA_OFF_DESC, &I, sizeof(I), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(base + NA_OFF_DYN, &y, sizeof(y), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && nv) e = cudaMemcpyAsync(base + NA_OFF_VX, body->vx, 8 * (size_t)nv, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && nv) e = cudaMemcpyAsync(base + NA_OFF_VY, body->vy, 8 * (size_t)nv, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && nv) e = cudaMemcpyAsync(base + NA_OFF_NEXT, hnext.data(), 4 * (size_t)nv, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && nv) e = cudaMemcpyAsync(base + NA_OFF_MOV, hmov.data(), (size_t)nv, cudaMemcpyHostToDevice, st);
+    // the host vectors above are reused by the next call: wait for the copies
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        g_na_error = std::string("mb_cut_cells_noalloc: copy to scratch failed: ") + cudaGetErrorString(e);
+        return MB_E_CUDA;
+    }
+    const InstDesc *D = (const InstDesc *)(base + NA_OFF_DESC);
+    InstDyn *Yd = (InstDyn *)(base + NA_OFF_DYN);
+    double *px = (double *)(base + NA_OFF_PX), *py = (double *)(base + NA_OFF_PY);
+    float *ebox = (float *)(base + NA_OFF_EBOX);
+    const int *vnext = (const int *)(base + NA_OFF_NEXT);
+    const unsigned char *vmov = (const unsigned char *)(base + NA_OFF_MOV);
+    const double *vx = (const double *)(base + NA_OFF_VX), *vy = (const double *)(base + NA_OFF_VY);
+    k_pose_current<<<1, 256, 0, st>>>(D, Yd, vx, vy, vmov, vnext, px, py, ebox, 0);
+    const int blocks = (grid->nx + GEOM_WARPS - 1) / GEOM_WARPS;
+    k_classify_na<<<blocks, GEOM_WARPS * 32, geom_smem(), st>>>(D, Yd, px, py, ebox, vnext, vmov, nv > 0 ? nv : 1,
+                                                                 alpha_dev, class_dev);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        g_na_error = std::string("mb_cut_cells_noalloc: launch failed: ") + cudaGetErrorString(e);
+        return MB_E_CUDA;
+    }
+    return MB_OK;
+}
+
+extern "C" const char *mb_noalloc_last_error(void) { return g_na_error.c_str(); }

@@ -22,7 +22,8 @@ FP64, FP32 = 0, 1
 
 EXPORTS = ["mb_create", "mb_batch_create", "mb_destroy", "mb_last_error", "mb_set_stream", "mb_write_state",
            "mb_read_state", "mb_step", "mb_sweep", "mb_run", "mb_sync", "mb_info", "mb_diagnostics",
-           "mb_enable_timing", "mb_kernel_time", "mb_band_records", "mb_band_record_size"]
+           "mb_enable_timing", "mb_kernel_time", "mb_band_records", "mb_band_record_size",
+           "mb_cut_cells_noalloc", "mb_noalloc_last_error"]
 
 
 class Grid(ctypes.Structure):
@@ -74,6 +75,9 @@ def _load():
         "mb_kernel_time": ([P, D, ctypes.POINTER(I)], I),
         "mb_band_records": ([P, I, P, I, ctypes.POINTER(I)], I),
         "mb_band_record_size": ([], I),
+        "mb_cut_cells_noalloc": ([ctypes.POINTER(Grid), ctypes.POINTER(Body), ctypes.POINTER(Motion), ctypes.c_double,
+                                  ctypes.c_double, ctypes.c_double, P, P, P], I),
+        "mb_noalloc_last_error": ([], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -220,6 +224,18 @@ class Sim:
             self._check(lib.mb_band_records(self._h, inst, out.ctypes.data_as(ctypes.c_void_p), cnt.value,
                                             ctypes.byref(cnt)))
         return out
+
+
+def cut_cells_noalloc(prob: inputs.Problem, X: float, Y: float, theta: float, alpha_ptr: int, class_ptr: int,
+                      stream: int = 0):
+    """Volume fractions and class bytes of `prob`'s body posed at (X, Y,
+    theta) into caller-owned device arrays, without any device allocation
+    by the library (see mb_cut_cells_noalloc in include/mb.h)."""
+    g, b, m, keep = _marshal(prob, FP64)
+    r = lib.mb_cut_cells_noalloc(ctypes.byref(g), ctypes.byref(b), ctypes.byref(m), X, Y, theta,
+                                 ctypes.c_void_p(alpha_ptr), ctypes.c_void_p(class_ptr), ctypes.c_void_p(stream))
+    if r != MB_OK:
+        raise MBError(r, lib.mb_noalloc_last_error().decode())
 
 
 BAND_DTYPE = np.dtype([("cell", "i4"), ("i", "i4"), ("j", "i4"), ("flags", "i4"),
