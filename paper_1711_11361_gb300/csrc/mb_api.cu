@@ -245,8 +245,8 @@ mb_status mb_batch_create(int n, const mb_grid *grids, const double *gammas, con
         }
         if (I.nv == 0) gcols = 0;
         I.gcol_max = gcols;
-        I.gcol_off = col_total;
-        col_total += gcols;
+        I.gcol_off = col_total;          // in units of 4-column geometry groups
+        col_total += (gcols + 3) / 4;
         // bulk work items: x sweep one warp per row; y sweep one warp per 32
         // columns and 64-row segment
         I.tiles_x[0] = 1;

@@ -426,21 +426,310 @@ __device__ double swept_face_B(const GeoBuf &G, const InstDesc &I, int dir, doub
 
 // ---------------------------------------------------------------------------
 // K1: band records (cells touched by the body at the start or end pose, or
-// the middle pose when rotating) with their geometry
+// the middle pose when rotating) with their geometry.  One warp per group of
+// GC adjacent columns, band cells of the whole group spread over the lanes.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(GEOM_WARPS * 32) k_geom(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y,
-                                                        const double *__restrict__ px, const double *__restrict__ py,
-                                                        const float *__restrict__ ebox,
-                                                        const int *__restrict__ vnext,
-                                                        const unsigned char *__restrict__ vmov, int total_v,
-                                                        int n_inst, int total_cols, int dir, BandRec *__restrict__ R,
-                                                        double *__restrict__ bnd) {
+constexpr int GC = 4;               // columns per warp
+constexpr int EMAXG = 384;          // edges per group and pose
+constexpr int LMAXG = 32;           // crossings per grid line
+constexpr int NWB = 64;             // bitmap words per column (2048 rows of the body's extent)
+constexpr int GEOMG_WARPS = 2;
+
+struct GeoBufG {
+    double xa[EMAXG], ya[EMAXG], xb[EMAXG], yb[EMAXG];
+    double slope[EMAXG];            // (yb - ya) / (xb - xa)
+    short jlo[EMAXG], jhi[EMAXG];   // rows the edge may meet
+    short ilo[EMAXG], ihi[EMAXG];   // columns whose widened range the edge may meet
+    unsigned char mov[EMAXG];
+    double lyc[GC + 1][LMAXG];      // crossings of the grid lines x_{i0} .. x_{i0+GC}
+    signed char ls[GC + 1][LMAXG];
+    unsigned char lf[GC + 1][LMAXG];
+    int lcnt[GC + 1];
+    int cnt;
+};
+
+struct GeoWarpG {
+    GeoBufG G;
+    unsigned bA[GC][NWB], bB[GC][NWB], bM[GC][NWB];
+    int wpre[GC * NWB + 1];
+};
+
+__device__ __forceinline__ bool edge_yrange_s(double xa, double ya, double xb, double yb, double slope, double xl,
+                                              double xr, double *elo, double *ehi) {
+    double lo = dmin(xa, xb), hi = dmax(xa, xb);
+    if (hi < xl || lo > xr) return false;
+    double e0, e1;
+    if (xa == xb) {
+        e0 = ya; e1 = yb;
+    } else {
+        double xc0 = lo > xl ? lo : xl;
+        double xc1 = hi < xr ? hi : xr;
+        e0 = (xc0 == xa) ? ya : ((xc0 == xb) ? yb : ya + (xc0 - xa) * slope);
+        e1 = (xc1 == xa) ? ya : ((xc1 == xb) ? yb : ya + (xc1 - xa) * slope);
+    }
+    *elo = dmin(e0, e1);
+    *ehi = dmax(e0, e1);
+    return true;
+}
+
+__device__ __forceinline__ int col_floor(const InstDesc &I, double xv) {
+    double f = (xv - I.x0) / I.dx;
+    f = fmin(fmax(f, -4.0), (double)I.nx + 4.0);
+    return (int)floor(f);
+}
+
+// gather the edges overlapping the group's widened x-range at pose P; marks
+// touched rows per column (exact predicate) when bits != nullptr
+__device__ void gather_g(GeoBufG &G, const InstDesc &I, const double *__restrict__ px, const double *__restrict__ py,
+                         const float *__restrict__ ebox, const int *__restrict__ vnext,
+                         const unsigned char *__restrict__ vmov, int P, int total_v, int i0, int ncol, double ad,
+                         int row0, int nwb, unsigned (*bits)[NWB], int lane, int *err) {
+    const double *PX = px + (size_t)P * total_v, *PY = py + (size_t)P * total_v;
+    const float *EB = ebox + (size_t)P * total_v * 2;
+    const double gxl = node_coord(I.x0, i0, I.dx) - ad, gxr = node_coord(I.x0, i0 + ncol, I.dx) + ad;
+    const float fl = __double2float_rd(gxl), fr = __double2float_ru(gxr);
+    int cnt = 0;
+    int lc[GC + 1];
+    for (int L = 0; L <= GC; ++L) lc[L] = 0;
+    for (int base = 0; base < I.nv; base += 32) {
+        const int k = base + lane;
+        const int a = I.voff + k;
+        bool take = false;
+        if (k < I.nv) take = EB[2 * a + 1] >= fl && EB[2 * a] <= fr;
+        const unsigned m = __ballot_sync(0xffffffffu, take);
+        double xa = 0, ya = 0, xb = 0, yb = 0, sl = 0;
+        if (take) {
+            const int b = vnext[a];
+            xa = PX[a]; ya = PY[a]; xb = PX[b]; yb = PY[b];
+            sl = xa != xb ? (yb - ya) / (xb - xa) : 0.0;
+            const int pos = cnt + __popc(m & ((1u << lane) - 1u));
+            const double lo = dmin(xa, xb), hi = dmax(xa, xb);
+            if (pos < EMAXG) {
+                G.xa[pos] = xa; G.ya[pos] = ya; G.xb[pos] = xb; G.yb[pos] = yb;
+                G.slope[pos] = sl;
+                G.mov[pos] = vmov[a];
+                double elo, ehi;
+                if (edge_yrange_s(xa, ya, xb, yb, sl, gxl, gxr, &elo, &ehi)) {
+                    G.jlo[pos] = (short)(row_floor(I, elo) - 1);
+                    G.jhi[pos] = (short)(row_floor(I, ehi) + 1);
+                } else {
+                    G.jlo[pos] = 1;
+                    G.jhi[pos] = 0;
+                }
+                G.ilo[pos] = (short)(col_floor(I, lo - ad) - 1);
+                G.ihi[pos] = (short)(col_floor(I, hi + ad) + 1);
+            }
+            if (bits) {
+                for (int c = 0; c < ncol; ++c) {
+                    const double xl = node_coord(I.x0, i0 + c, I.dx), xr = node_coord(I.x0, i0 + c + 1, I.dx);
+                    double elo, ehi;
+                    if (!edge_yrange_s(xa, ya, xb, yb, sl, xl, xr, &elo, &ehi)) continue;
+                    int jl = row_floor(I, elo) - 1, jh = row_floor(I, ehi) + 1;
+                    if (jl < row0) jl = row0;
+                    if (jh > I.ny - 1) jh = I.ny - 1;
+                    if (jh > row0 + 32 * nwb - 1) jh = row0 + 32 * nwb - 1;
+                    for (int j = jl; j <= jh; ++j) {
+                        double ybj = node_coord(I.y0, j, I.dy), ytj = node_coord(I.y0, j + 1, I.dy);
+                        if (ehi >= ybj && elo <= ytj) atomicOr(&bits[c][(j - row0) >> 5], 1u << ((j - row0) & 31));
+                    }
+                }
+            }
+        }
+        // grid-line crossings
+        for (int L = 0; L <= ncol; ++L) {
+            const double xs = node_coord(I.x0, i0 + L, I.dx);
+            const double lo = dmin(xa, xb), hi = dmax(xa, xb);
+            const bool c = take && xa != xb && lo <= xs && xs <= hi;
+            const unsigned mm = __ballot_sync(0xffffffffu, c);
+            if (c) {
+                const int p = lc[L] + __popc(mm & ((1u << lane) - 1u));
+                if (p < LMAXG) {
+                    G.lyc[L][p] = ya + (xs - xa) * sl;
+                    G.ls[L][p] = xa < xb ? 1 : -1;
+                    G.lf[L][p] = (unsigned char)((lo < xs ? 1 : 0) | (xs < hi ? 2 : 0));
+                }
+            }
+            lc[L] += __popc(mm);
+        }
+        cnt += __popc(m);
+    }
+    bool over = cnt > EMAXG;
+    for (int L = 0; L <= ncol; ++L) over |= lc[L] > LMAXG;
+    if (over && lane == 0) *err |= ERR_EDGE_CAP;
+    if (lane == 0) {
+        G.cnt = cnt < EMAXG ? cnt : EMAXG;
+        for (int L = 0; L <= GC; ++L) G.lcnt[L] = L <= ncol ? (lc[L] < LMAXG ? lc[L] : LMAXG) : 0;
+    }
+    __syncwarp();
+}
+
+__device__ __forceinline__ double line_solid_vg(const GeoBufG &G, int L, double y0r, double y1r, bool left_limit) {
+    double s = 0.0;
+    const unsigned char want = left_limit ? 1 : 2;
+    for (int e = 0; e < G.lcnt[L]; ++e) {
+        if (!(G.lf[L][e] & want)) continue;
+        double yc = G.lyc[L][e];
+        double cl = yc < y0r ? y0r : (yc > y1r ? y1r : yc);
+        s += (double)G.ls[L][e] * (y1r - cl);
+    }
+    return s;
+}
+
+// solid length of [x_l, x_r] x {y_f} (column c of the group, y_f = y_jf): the
+// winding number just right of x_l from the crossings of that grid line,
+// then the crossings of y_f inside the column, in order along x
+__device__ double line_solid_hg(const GeoBufG &G, int c, int i, double xl, double xr, double yf, int jf) {
+    int w = 0;
+    for (int e = 0; e < G.lcnt[c]; ++e)
+        if ((G.lf[c][e] & 2) && G.lyc[c][e] < yf) w += G.ls[c][e];
+    double ex[8];
+    int ed[8], ne = 0;
+    bool overflow = false;
+    for (int e = 0; e < G.cnt; ++e) {
+        if (G.jhi[e] < jf - 1 || G.jlo[e] > jf || G.ihi[e] < i || G.ilo[e] > i) continue;
+        const double xa = G.xa[e], xb = G.xb[e], ya = G.ya[e], yb = G.yb[e];
+        if (ya == yb) continue;
+        if ((ya < yf) == (yb < yf)) continue;
+        const double xs = xa == xb ? xa : xa + (yf - ya) / G.slope[e];
+        if (!(xs > xl && xs < xr)) continue;
+        // crossing the boundary left to right: the interior of a
+        // counter-clockwise polygon lies left of its edges
+        const int dw = yb > ya ? -1 : 1;
+        if (ne < 8) {
+            int p = ne++;
+            while (p > 0 && ex[p - 1] > xs) { ex[p] = ex[p - 1]; ed[p] = ed[p - 1]; --p; }
+            ex[p] = xs;
+            ed[p] = dw;
+        } else {
+            overflow = true;
+        }
+    }
+    if (overflow) {   // many crossings inside one column: integrate edge by edge
+        double L = 0.0;
+        for (int e = 0; e < G.cnt; ++e) {
+            if (G.ihi[e] < i || G.ilo[e] > i) continue;
+            const double xa = G.xa[e], xb = G.xb[e], ya = G.ya[e], yb = G.yb[e];
+            const double p = dmax(xl, dmin(xa, xb)), q = dmin(xr, dmax(xa, xb));
+            if (!(q > p)) continue;
+            const double s = xa < xb ? 1.0 : -1.0;
+            const double k = G.slope[e];
+            const double yp = ya + (p - xa) * k, yq = ya + (q - xa) * k;
+            double m;
+            if (yp < yf && yq < yf) m = q - p;
+            else if (!(yp < yf) && !(yq < yf)) m = 0.0;
+            else {
+                double xs = p + (q - p) * ((yf - yp) / (yq - yp));
+                xs = xs < p ? p : (xs > q ? q : xs);
+                m = yp < yf ? xs - p : q - xs;
+            }
+            L += s * m;
+        }
+        return L;
+    }
+    double L = 0.0, pos = xl;
+    for (int k = 0; k < ne; ++k) {
+        if (w > 0) L += ex[k] - pos;
+        pos = ex[k];
+        w += ed[k];
+    }
+    if (w > 0) L += xr - pos;
+    return L;
+}
+
+__device__ double rect_edges_g(const GeoBufG &G, int i, int ja, int jb, double rx0, double rx1, double ry0,
+                               double ry1, double xo, double xs, double *nlx, double *nly, bool *mov) {
+    const double lx0 = rx0 - xo, lx1 = rx1 - xo, ly1 = ry1 - ry0;
+    double A = 0.0;
+    for (int e = 0; e < G.cnt; ++e) {
+        if (G.jhi[e] < ja || G.jlo[e] > jb || G.ihi[e] < i || G.ilo[e] > i) continue;
+        const double xa = G.xa[e], xb = G.xb[e], ya = G.ya[e], yb = G.yb[e];
+        if (dmax(ya, yb) < ry0 || dmin(ya, yb) > ry1 || dmax(xa, xb) < rx0 || dmin(xa, xb) > rx1) continue;
+        const double ax = xa - xo, ay = ya - ry0, bx = xb - xo, by = yb - ry0;
+        const double ddx = bx - ax, ddy = by - ay;
+        double t0 = 0.0, t1 = 1.0;
+        bool ok = true;
+        if (ddx == 0.0) {
+            if (ax < lx0 || ax > lx1) ok = false;
+        } else {
+            const double inv = 1.0 / ddx;
+            const double ra = (lx0 - ax) * inv, rb = (lx1 - ax) * inv;
+            t0 = dmax(t0, dmin(ra, rb));
+            t1 = dmin(t1, dmax(ra, rb));
+        }
+        if (ddy == 0.0) {
+            if (ay < 0.0 || ay > ly1) ok = false;
+        } else {
+            const double inv = 1.0 / ddy;
+            const double ra = (0.0 - ay) * inv, rb = (ly1 - ay) * inv;
+            t0 = dmax(t0, dmin(ra, rb));
+            t1 = dmin(t1, dmax(ra, rb));
+        }
+        if (!ok || t1 < t0) continue;
+        if (mov && G.mov[e]) *mov = true;
+        if (xa == xb && xa == xs) continue;   // vertical edge on the grid side
+        if (!(t1 > t0)) continue;
+        const double xc0 = ax + t0 * ddx, xc1 = ax + t1 * ddx;
+        A += ddy * (t1 - t0) * (0.5 * (xc0 + xc1));
+        if (nlx) {
+            *nlx -= ddy * (t1 - t0);
+            *nly += ddx * (t1 - t0);
+        }
+    }
+    return A;
+}
+
+__device__ __forceinline__ double cell_alpha_g(const GeoBufG &G, const InstDesc &I, int c, int i, int j, double xl,
+                                               double xr, double yb, double yt, double *nlx, double *nly, bool *mov) {
+    double A = rect_edges_g(G, i, j, j, xl, xr, yb, yt, xl, xr, nlx, nly, mov) +
+               (xr - xl) * line_solid_vg(G, c + 1, yb, yt, true);
+    double a = clamp01(1.0 - A / (I.dx * I.dy));
+    return a < ALPHA_MIN ? 0.0 : a;
+}
+
+__device__ double face_ap_g(const GeoBufG &G, const InstDesc &I, int dir, bool hi, int c, int i, int j, double xl,
+                            double xr, double yb, double yt) {
+    if (dir == 0) return clamp01(1.0 - line_solid_vg(G, hi ? c + 1 : c, yb, yt, true) / I.dy);
+    return clamp01(1.0 - line_solid_hg(G, c, i, xl, xr, hi ? yt : yb, hi ? j + 1 : j) / I.dx);
+}
+
+__device__ double swept_face_Bg(const GeoBufG &G, const InstDesc &I, int dir, double delta, bool hi, int c, int i,
+                                int j, double xl, double xr, double yb, double yt) {
+    if (delta == 0.0) return face_ap_g(G, I, dir, hi, c, i, j, xl, xr, yb, yt);
+    if (dir == 0) {
+        const int line = hi ? c + 1 : c;
+        const double xs = hi ? xr : xl;
+        if (delta > 0.0) {
+            const double x1 = xs + delta;
+            const double A = rect_edges_g(G, i, j, j, xs, x1, yb, yt, x1, xs, nullptr, nullptr, nullptr) +
+                             (x1 - xs) * line_solid_vg(G, line, yb, yt, false);
+            return clamp01(1.0 - A / ((x1 - xs) * I.dy));
+        }
+        const double x0 = xs + delta;
+        const double A = rect_edges_g(G, i, j, j, x0, xs, yb, yt, x0, xs, nullptr, nullptr, nullptr) +
+                         (xs - x0) * line_solid_vg(G, line, yb, yt, true);
+        return clamp01(1.0 - A / ((xs - x0) * I.dy));
+    }
+    const double ys = hi ? yt : yb;
+    const double y0 = delta > 0.0 ? ys : ys + delta, y1 = delta > 0.0 ? ys + delta : ys;
+    const int ja = delta > 0.0 ? j : j - 1, jb = delta > 0.0 ? j + 1 : j;
+    const double A = rect_edges_g(G, i, ja, jb, xl, xr, y0, y1, xl, xr, nullptr, nullptr, nullptr) +
+                     (xr - xl) * line_solid_vg(G, c + 1, y0, y1, true);
+    return clamp01(1.0 - A / ((y1 - y0) * I.dx));
+}
+
+__global__ void __launch_bounds__(GEOMG_WARPS * 32) k_geom(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y,
+                                                         const double *__restrict__ px, const double *__restrict__ py,
+                                                         const float *__restrict__ ebox,
+                                                         const int *__restrict__ vnext,
+                                                         const unsigned char *__restrict__ vmov, int total_v,
+                                                         int n_inst, int total_groups, int dir,
+                                                         BandRec *__restrict__ R, double *__restrict__ bnd) {
     extern __shared__ __align__(16) unsigned char gsm[];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    GeoWarp &W = ((GeoWarp *)gsm)[wib];
-    GeoBuf &G = W.G;
-    const int gw = blockIdx.x * GEOM_WARPS + wib;
-    if (gw >= total_cols) return;
+    GeoWarpG &W = ((GeoWarpG *)gsm)[wib];
+    GeoBufG &G = W.G;
+    const int gw = blockIdx.x * GEOMG_WARPS + wib;
+    if (gw >= total_groups) return;
     int lo = 0, hi = n_inst - 1;
     while (lo < hi) {
         int mid = (lo + hi + 1) >> 1;
@@ -448,32 +737,45 @@ __global__ void __launch_bounds__(GEOM_WARPS * 32) k_geom(const InstDesc *__rest
     }
     const InstDesc &I = D[lo];
     InstDyn &y = Y[lo];
-    const int i = y.col0 + (gw - I.gcol_off);
-    if (i > y.col1 || i >= I.nx || I.nv == 0) return;
-    const double xl = node_coord(I.x0, i, I.dx), xr = node_coord(I.x0, i + 1, I.dx);
+    const int i0 = y.col0 + GC * (gw - I.gcol_off);
+    if (i0 > y.col1 || i0 >= I.nx || I.nv == 0) return;
+    const int ncol = min(GC, min(y.col1, I.nx - 1) - i0 + 1);
     const double delta = y.delta;
     const bool own_hi = I.rotating || delta >= 0.0;
-    const double gxl = xl - fabs(delta), gxr = xr + fabs(delta);
-    const int nwords = (I.ny + 31) >> 5;
+    const double ad = fabs(delta);
+    const int row0 = y.row0;
+    const int nwb = (y.row1 - y.row0) / 32 + 1;
     int err = 0;
-    for (int w = lane; w < nwords; w += 32) { W.bA[w] = 0u; W.bB[w] = 0u; W.bM[w] = 0u; }
+    if (y.row1 < y.row0) return;
+    if (nwb > NWB) {
+        if (lane == 0) atomicOr(&y.err, ERR_BAND_CAP);
+        return;
+    }
+    for (int w = lane; w < GC * NWB; w += 32) {
+        (&W.bA[0][0])[w] = 0u;
+        (&W.bB[0][0])[w] = 0u;
+        (&W.bM[0][0])[w] = 0u;
+    }
     __syncwarp();
     // touched at the start pose: class bytes kept from the previous sweep
-    for (int j = y.row0 + lane; j <= y.row1; j += 32)
-        if (I.cls[j * I.pitch + i] & CLS_TOUCH) atomicOr(&W.bA[j >> 5], 1u << (j & 31));
-    if (I.rotating) gather(G, I, px, py, ebox, vnext, vmov, 1, total_v, xl, xr, gxl, gxr, W.bM, lane, &err);
-    gather(G, I, px, py, ebox, vnext, vmov, 2, total_v, xl, xr, gxl, gxr, W.bB, lane, &err);
-    // band rows in increasing order: per-word prefix counts
+    for (int c = 0; c < ncol; ++c)
+        for (int j = row0 + lane; j <= y.row1; j += 32)
+            if (I.cls[j * I.pitch + i0 + c] & CLS_TOUCH) atomicOr(&W.bA[c][(j - row0) >> 5], 1u << ((j - row0) & 31));
+    if (I.rotating) gather_g(G, I, px, py, ebox, vnext, vmov, 1, total_v, i0, ncol, ad, row0, nwb, W.bM, lane, &err);
+    gather_g(G, I, px, py, ebox, vnext, vmov, 2, total_v, i0, ncol, ad, row0, nwb, W.bB, lane, &err);
+    // band cells in (column, row) order: prefix counts over the words
+    const int nw = ncol * nwb;
     int running = 0;
-    for (int w0 = 0; w0 < nwords; w0 += 32) {
-        int w = w0 + lane;
-        int c = w < nwords ? __popc(W.bA[w] | W.bB[w] | W.bM[w]) : 0;
-        int incl = c;
+    for (int w0 = 0; w0 < nw; w0 += 32) {
+        const int w = w0 + lane;
+        const int c = w / nwb, k = w % nwb;
+        int cnt = w < nw ? __popc(W.bA[c][k] | W.bB[c][k] | W.bM[c][k]) : 0;
+        int incl = cnt;
         for (int o = 1; o < 32; o <<= 1) {
             int v = __shfl_up_sync(0xffffffffu, incl, o);
             if (lane >= o) incl += v;
         }
-        if (w < nwords) W.wpre[w] = running + incl - c;
+        if (w < nw) W.wpre[w] = running + incl - cnt;
         running += __shfl_sync(0xffffffffu, incl, 31);
     }
     const int T = running;
@@ -488,76 +790,77 @@ __global__ void __launch_bounds__(GEOM_WARPS * 32) k_geom(const InstDesc *__rest
         if (lane == 0 && err) atomicOr(&y.err, err);
         return;
     }
-    auto locate = [&](int t, int *jrow, int *wrd, int *bit) {
-        int a = 0, b = nwords - 1;
+    auto locate = [&](int t, int *c, int *j, int *k, int *bit) {
+        int a = 0, b = nw - 1;
         while (a < b) {
             int m = (a + b + 1) >> 1;
             if (W.wpre[m] <= t) a = m; else b = m - 1;
         }
-        unsigned mask = W.bA[a] | W.bB[a] | W.bM[a];
-        int r = t - W.wpre[a];
-        int bpos = __fns(mask, 0, r + 1);
-        *wrd = a;
-        *bit = bpos;
-        *jrow = a * 32 + bpos;
+        *c = a / nwb;
+        *k = a % nwb;
+        const unsigned mask = W.bA[*c][*k] | W.bB[*c][*k] | W.bM[*c][*k];
+        *bit = __fns(mask, 0, t - W.wpre[a] + 1);
+        *j = row0 + (*k) * 32 + *bit;
     };
     const double wsimp_B = 1.0 / 6.0, wsimp_M = 4.0 / 6.0, wsimp_A = 1.0 / 6.0;
     // pass B (edges of the end pose are in G)
     for (int t = lane; t < T; t += 32) {
-        int j, wrd, bit;
-        locate(t, &j, &wrd, &bit);
+        int c, j, k, bit;
+        locate(t, &c, &j, &k, &bit);
+        const int i = i0 + c;
         BandRec &r = R[I.rec_base + base + t];
+        const double xl = node_coord(I.x0, i, I.dx), xr = node_coord(I.x0, i + 1, I.dx);
         const double yb = node_coord(I.y0, j, I.dy), yt = node_coord(I.y0, j + 1, I.dy);
-        const bool tA = (W.bA[wrd] >> bit) & 1u, tB = (W.bB[wrd] >> bit) & 1u, tM = (W.bM[wrd] >> bit) & 1u;
+        const bool tA = (W.bA[c][k] >> bit) & 1u, tB = (W.bB[c][k] >> bit) & 1u, tM = (W.bM[c][k] >> bit) & 1u;
         const int cell = j * I.pitch + i;
         r.cell = cell;
         r.i = i;
         r.j = j;
         bool mov = false;
-        r.aB = cell_alpha(G, I, j, xl, xr, yb, yt, nullptr, nullptr, &mov);
+        r.aB = cell_alpha_g(G, I, c, i, j, xl, xr, yb, yt, nullptr, nullptr, &mov);
         r.aA = I.alpha[cell];
         const bool need_bnd =
             dir == 0 ? ((own_hi && i == 0 && I.bc[0] != 2) || (!own_hi && i == I.nx - 1 && I.bc[1] != 2))
                      : ((own_hi && j == 0 && I.bc[2] != 2) || (!own_hi && j == I.ny - 1 && I.bc[3] != 2));
         double bo, bb = 0.0;
         if (I.rotating) {
-            bo = wsimp_B * face_ap(G, I, dir, true, j, xl, xr, yb, yt);
-            if (need_bnd) bb = wsimp_B * face_ap(G, I, dir, false, j, xl, xr, yb, yt);
+            bo = wsimp_B * face_ap_g(G, I, dir, true, c, i, j, xl, xr, yb, yt);
+            if (need_bnd) bb = wsimp_B * face_ap_g(G, I, dir, false, c, i, j, xl, xr, yb, yt);
         } else {
-            bo = swept_face_B(G, I, dir, delta, own_hi, j, xl, xr, yb, yt);
-            if (need_bnd) bb = swept_face_B(G, I, dir, delta, !own_hi, j, xl, xr, yb, yt);
+            bo = swept_face_Bg(G, I, dir, delta, own_hi, c, i, j, xl, xr, yb, yt);
+            if (need_bnd) bb = swept_face_Bg(G, I, dir, delta, !own_hi, c, i, j, xl, xr, yb, yt);
         }
         r.bown = bo;
         bnd[I.rec_base + base + t] = bb;
-        const bool movA = (I.cls[cell] & CLS_MOVT) != 0;   // a moving edge met the cell at the start pose
+        const bool movA = (I.cls[cell] & CLS_MOVT) != 0;
         r.flags = (tA ? RF_TOUCH_A : 0) | (tB ? RF_TOUCH_B : 0) | (tM ? RF_TOUCH_M : 0) |
                   ((mov || movA) ? RF_MOVING : 0) | (mov ? RF_MOV_B : 0);
     }
     // pass M
-    gather(G, I, px, py, ebox, vnext, vmov, 1, total_v, xl, xr, gxl, gxr, nullptr, lane, &err);
+    gather_g(G, I, px, py, ebox, vnext, vmov, 1, total_v, i0, ncol, ad, row0, nwb, nullptr, lane, &err);
     for (int t = lane; t < T; t += 32) {
-        int j, wrd, bit;
-        locate(t, &j, &wrd, &bit);
+        int c, j, k, bit;
+        locate(t, &c, &j, &k, &bit);
+        const int i = i0 + c;
         const int ri = I.rec_base + base + t;
         BandRec &r = R[ri];
+        const double xl = node_coord(I.x0, i, I.dx), xr = node_coord(I.x0, i + 1, I.dx);
         const double yb = node_coord(I.y0, j, I.dy), yt = node_coord(I.y0, j + 1, I.dy);
         bool mov = false;
         double nlx = 0.0, nly = 0.0;
-        const double aM = cell_alpha(G, I, j, xl, xr, yb, yt, &nlx, &nly, &mov);
+        const double aM = cell_alpha_g(G, I, c, i, j, xl, xr, yb, yt, &nlx, &nly, &mov);
         r.aM = aM;
         int fl = r.flags | (mov ? RF_MOVING : 0);
         if (I.rotating) {
-            r.bown += wsimp_M * face_ap(G, I, dir, true, j, xl, xr, yb, yt);
+            r.bown += wsimp_M * face_ap_g(G, I, dir, true, c, i, j, xl, xr, yb, yt);
             const bool need_bnd = dir == 0 ? (i == 0 && I.bc[0] != 2) : (j == 0 && I.bc[2] != 2);
-            if (need_bnd) bnd[ri] += wsimp_M * face_ap(G, I, dir, false, j, xl, xr, yb, yt);
+            if (need_bnd) bnd[ri] += wsimp_M * face_ap_g(G, I, dir, false, c, i, j, xl, xr, yb, yt);
         }
-        // shielded distance d = alpha_hat / |delta beta| at the mid pose
-        const double blo = face_ap(G, I, dir, false, j, xl, xr, yb, yt);
-        const double bhi = face_ap(G, I, dir, true, j, xl, xr, yb, yt);
+        const double blo = face_ap_g(G, I, dir, false, c, i, j, xl, xr, yb, yt);
+        const double bhi = face_ap_g(G, I, dir, true, c, i, j, xl, xr, yb, yt);
         const double db = fabs(blo - bhi);
         const double ahat = aM - dmin(blo, bhi);
         r.d = db > 0.0 ? clamp01(ahat / db) : 1.0;
-        // wall normal (into the body) from the boundary pieces inside the cell
         const double L = sqrt(nlx * nlx + nly * nly);
         r.nx = L > 0.0 ? nlx / L : 0.0;
         r.ny = L > 0.0 ? nly / L : 0.0;
@@ -582,15 +885,17 @@ __global__ void __launch_bounds__(GEOM_WARPS * 32) k_geom(const InstDesc *__rest
         I.cls[r.cell] |= CLS_BAND;
     }
     if (I.rotating) {
-        gather(G, I, px, py, ebox, vnext, vmov, 0, total_v, xl, xr, gxl, gxr, nullptr, lane, &err);
+        gather_g(G, I, px, py, ebox, vnext, vmov, 0, total_v, i0, ncol, ad, row0, nwb, nullptr, lane, &err);
         for (int t = lane; t < T; t += 32) {
-            int j, wrd, bit;
-            locate(t, &j, &wrd, &bit);
+            int c, j, k, bit;
+            locate(t, &c, &j, &k, &bit);
+            const int i = i0 + c;
             const int ri = I.rec_base + base + t;
+            const double xl = node_coord(I.x0, i, I.dx), xr = node_coord(I.x0, i + 1, I.dx);
             const double yb = node_coord(I.y0, j, I.dy), yt = node_coord(I.y0, j + 1, I.dy);
-            R[ri].bown += wsimp_A * face_ap(G, I, dir, true, j, xl, xr, yb, yt);
+            R[ri].bown += wsimp_A * face_ap_g(G, I, dir, true, c, i, j, xl, xr, yb, yt);
             const bool need_bnd = dir == 0 ? (i == 0 && I.bc[0] != 2) : (j == 0 && I.bc[2] != 2);
-            if (need_bnd) bnd[ri] += wsimp_A * face_ap(G, I, dir, false, j, xl, xr, yb, yt);
+            if (need_bnd) bnd[ri] += wsimp_A * face_ap_g(G, I, dir, false, c, i, j, xl, xr, yb, yt);
         }
     }
     if (lane == 0 && err) atomicOr(&y.err, err);
@@ -680,9 +985,10 @@ __global__ void k_pose_current(const InstDesc *__restrict__ D, const InstDyn *__
 // launchers
 // ---------------------------------------------------------------------------
 static size_t geom_smem() { return sizeof(GeoWarp) * GEOM_WARPS; }
+static size_t geomg_smem() { return sizeof(GeoWarpG) * GEOMG_WARPS; }
 
 void geom_init() {
-    cudaFuncSetAttribute(k_geom, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)geom_smem());
+    cudaFuncSetAttribute(k_geom, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)geomg_smem());
     cudaFuncSetAttribute(k_classify, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)geom_smem());
 }
 
@@ -693,12 +999,12 @@ void launch_pose(const InstDesc *D, InstDyn *Y, const double *vx, const double *
 }
 
 void launch_geom(const InstDesc *D, InstDyn *Y, const double *px, const double *py, const float *ebox,
-                 const int *vnext, const unsigned char *vmov, int total_v, int n_inst, int total_cols, int dir,
+                 const int *vnext, const unsigned char *vmov, int total_v, int n_inst, int total_groups, int dir,
                  BandRec *R, double *bnd, cudaStream_t st) {
-    int blocks = (total_cols + GEOM_WARPS - 1) / GEOM_WARPS;
+    int blocks = (total_groups + GEOMG_WARPS - 1) / GEOMG_WARPS;
     if (blocks > 0)
-        k_geom<<<blocks, GEOM_WARPS * 32, geom_smem(), st>>>(D, Y, px, py, ebox, vnext, vmov, total_v, n_inst,
-                                                           total_cols, dir, R, bnd);
+        k_geom<<<blocks, GEOMG_WARPS * 32, geomg_smem(), st>>>(D, Y, px, py, ebox, vnext, vmov, total_v, n_inst,
+                                                             total_groups, dir, R, bnd);
 }
 
 void launch_classify(const InstDesc *D, InstDyn *Y, const double *vx, const double *vy, const unsigned char *vmov,
