@@ -88,6 +88,27 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+def combine_ranks(total_ms, cells, device):
+    """Whole-job figures over all ranks: the slowest rank's timed region (max)
+    and the cells all ranks updated per sweep (sum).  Works with any
+    torch.distributed backend; single-process runs pass through."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(total_ms), float(cells)
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor([float(cells)], dtype=torch.float64, device=device)
+    dist.all_reduce(c)
+    return float(t.item()), float(c.item())
+
+
+def job_value(cells_all, steps, total_ms):
+    """Cell-updates per second: every cell of every rank is updated twice per
+    step (one x and one y sweep)."""
+    return cells_all * 2 * steps / (total_ms * 1e-3)
+
+
 def workload(rank, args):
     from paper_1711_11361_gb300 import inputs
     if args.workload == "c4":
@@ -197,18 +218,9 @@ def main():
     stop.set()
     th.join(timeout=2)
     per = np.array([evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)])
-    total_ms = float(per.sum())
-    if ws > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-        c = torch.tensor([float(cells)], device="cuda")
-        torch.distributed.all_reduce(c)
-        cells_all = float(c.item())
-    else:
-        cells_all = float(cells)
+    total_ms, cells_all = combine_ranks(float(per.sum()), cells, "cuda")
     status = sim.sync()
-    value = cells_all * 2 * args.steps / (total_ms * 1e-3)
+    value = job_value(cells_all, args.steps, total_ms)
 
     # dominant kernel: bulk sweep, timed with CUDA events on its stream
     sim.enable_timing(True)
