@@ -199,6 +199,8 @@ mb_status mb_batch_create(int n, const mb_grid *grids, const double *gammas, con
         I.x0 = g.x0; I.y0 = g.y0;
         I.dx = (g.x1 - g.x0) / (double)g.nx;
         I.dy = (g.y1 - g.y0) / (double)g.ny;
+        I.rdx = 1.0 / I.dx;
+        I.rdy = 1.0 / I.dy;
         for (int q = 0; q < 4; ++q) I.bc[q] = g.bc[q];
         I.eq = g.equation;
         I.ucov = g.uncover_mode;
@@ -245,8 +247,8 @@ mb_status mb_batch_create(int n, const mb_grid *grids, const double *gammas, con
         }
         if (I.nv == 0) gcols = 0;
         I.gcol_max = gcols;
-        I.gcol_off = col_total;          // in units of 4-column geometry groups
-        col_total += (gcols + 3) / 4;
+        I.gcol_off = col_total;          // in units of GEO_GC-column geometry groups
+        col_total += (gcols + GEO_GC - 1) / GEO_GC;
         // bulk work items: x sweep one warp per row; y sweep one warp per 32
         // columns and 64-row segment
         I.tiles_x[0] = 1;

@@ -204,7 +204,7 @@ __device__ __forceinline__ bool edge_yrange(double xa, double ya, double xb, dou
 }
 
 __device__ __forceinline__ int row_floor(const InstDesc &I, double yv) {
-    double f = (yv - I.y0) / I.dy;
+    double f = (yv - I.y0) * I.rdy;
     f = fmin(fmax(f, -4.0), (double)I.ny + 4.0);
     return (int)floor(f);
 }
@@ -426,22 +426,33 @@ __device__ double swept_face_B(const GeoBuf &G, const InstDesc &I, int dir, doub
 
 // ---------------------------------------------------------------------------
 // K1: band records (cells touched by the body at the start or end pose, or
-// the middle pose when rotating) with their geometry.  One warp per group of
-// GC adjacent columns, band cells of the whole group spread over the lanes.
+// the middle pose when rotating) with their geometry.  One CTA per group of
+// GC adjacent columns: warp 0 gathers the edges near the group, every band
+// cell of the group gets a thread, and each column keeps a bit list of the
+// edges that can meet its cells.
 // ---------------------------------------------------------------------------
-constexpr int GC = 4;               // columns per warp
+constexpr int GC = GEO_GC;          // columns per group
 constexpr int EMAXG = 384;          // edges per group and pose
 constexpr int LMAXG = 32;           // crossings per grid line
 constexpr int NWB = 64;             // bitmap words per column (2048 rows of the body's extent)
-constexpr int GEOMG_WARPS = 2;
+constexpr int GEOMG_THREADS = 128;  // one CTA per group; its warps share the group's edges
+constexpr int EWORDS = EMAXG / 32;  // words of a column's edge bit list
 
 struct GeoBufG {
     double xa[EMAXG], ya[EMAXG], xb[EMAXG], yb[EMAXG];
     double slope[EMAXG];            // (yb - ya) / (xb - xa)
+    double idx[EMAXG], idy[EMAXG];  // 1 / (xb - xa), 1 / (yb - ya) (0 if the difference is 0)
+    float fx0[EMAXG], fx1[EMAXG], fy0[EMAXG], fy1[EMAXG];   // bounding box rounded outward
     short jlo[EMAXG], jhi[EMAXG];   // rows the edge may meet
     short ilo[EMAXG], ihi[EMAXG];   // columns whose widened range the edge may meet
     unsigned char mov[EMAXG];
-    double lyc[GC + 1][LMAXG];      // crossings of the grid lines x_{i0} .. x_{i0+GC}
+    unsigned char pc0[EMAXG];       // first group column the edge's x-range may meet
+    int pp[EMAXG + 1];              // prefix over edges of their (edge, column) pairs
+    int npair;
+    unsigned cm[GC][EWORDS];        // per column: edges whose candidate columns contain it
+    unsigned lm[GC + 1][EWORDS];    // per grid line: edges crossing it
+    double xln[GC + 1];             // x of the grid lines x_{i0} .. x_{i0+GC}
+    double lyc[GC + 1][LMAXG];      // crossings of those grid lines
     signed char ls[GC + 1][LMAXG];
     unsigned char lf[GC + 1][LMAXG];
     int lcnt[GC + 1];
@@ -473,94 +484,206 @@ __device__ __forceinline__ bool edge_yrange_s(double xa, double ya, double xb, d
 }
 
 __device__ __forceinline__ int col_floor(const InstDesc &I, double xv) {
-    double f = (xv - I.x0) / I.dx;
+    double f = (xv - I.x0) * I.rdx;
     f = fmin(fmax(f, -4.0), (double)I.nx + 4.0);
     return (int)floor(f);
 }
 
-// gather the edges overlapping the group's widened x-range at pose P; marks
-// touched rows per column (exact predicate) when bits != nullptr
+// warp 0: the edges whose x-range meets the group's widened x-range at pose
+// P, compacted into G in vertex order with their per-edge data
 __device__ void gather_g(GeoBufG &G, const InstDesc &I, const double *__restrict__ px, const double *__restrict__ py,
                          const float *__restrict__ ebox, const int *__restrict__ vnext,
                          const unsigned char *__restrict__ vmov, int P, int total_v, int i0, int ncol, double ad,
-                         int row0, int nwb, unsigned (*bits)[NWB], int lane, int *err) {
+                         int lane, int *err) {
     const double *PX = px + (size_t)P * total_v, *PY = py + (size_t)P * total_v;
     const float *EB = ebox + (size_t)P * total_v * 2;
-    const double gxl = node_coord(I.x0, i0, I.dx) - ad, gxr = node_coord(I.x0, i0 + ncol, I.dx) + ad;
+    if (lane <= GC) G.xln[lane] = node_coord(I.x0, i0 + lane, I.dx);
+    __syncwarp();
+    const double gxl = G.xln[0] - ad, gxr = G.xln[ncol] + ad;
     const float fl = __double2float_rd(gxl), fr = __double2float_ru(gxr);
-    int cnt = 0;
-    int lc[GC + 1];
-    for (int L = 0; L <= GC; ++L) lc[L] = 0;
+    int cnt = 0, npair = 0;
     for (int base = 0; base < I.nv; base += 32) {
         const int k = base + lane;
         const int a = I.voff + k;
         bool take = false;
         if (k < I.nv) take = EB[2 * a + 1] >= fl && EB[2 * a] <= fr;
         const unsigned m = __ballot_sync(0xffffffffu, take);
-        double xa = 0, ya = 0, xb = 0, yb = 0, sl = 0;
-        if (take) {
+        if (m == 0u) continue;
+        const int pos = cnt + __popc(m & ((1u << lane) - 1u));
+        int np = 0;
+        if (take && pos < EMAXG) {
             const int b = vnext[a];
-            xa = PX[a]; ya = PY[a]; xb = PX[b]; yb = PY[b];
-            sl = xa != xb ? (yb - ya) / (xb - xa) : 0.0;
-            const int pos = cnt + __popc(m & ((1u << lane) - 1u));
+            const double xa = PX[a], ya = PY[a], xb = PX[b], yb = PY[b];
+            const double rx = xa != xb ? 1.0 / (xb - xa) : 0.0;
+            const double sl = (yb - ya) * rx;
             const double lo = dmin(xa, xb), hi = dmax(xa, xb);
-            if (pos < EMAXG) {
-                G.xa[pos] = xa; G.ya[pos] = ya; G.xb[pos] = xb; G.yb[pos] = yb;
-                G.slope[pos] = sl;
-                G.mov[pos] = vmov[a];
-                double elo, ehi;
-                if (edge_yrange_s(xa, ya, xb, yb, sl, gxl, gxr, &elo, &ehi)) {
-                    G.jlo[pos] = (short)(row_floor(I, elo) - 1);
-                    G.jhi[pos] = (short)(row_floor(I, ehi) + 1);
-                } else {
-                    G.jlo[pos] = 1;
-                    G.jhi[pos] = 0;
-                }
-                G.ilo[pos] = (short)(col_floor(I, lo - ad) - 1);
-                G.ihi[pos] = (short)(col_floor(I, hi + ad) + 1);
+            G.xa[pos] = xa; G.ya[pos] = ya; G.xb[pos] = xb; G.yb[pos] = yb;
+            G.slope[pos] = sl;
+            G.idx[pos] = rx;
+            G.idy[pos] = ya != yb ? 1.0 / (yb - ya) : 0.0;
+            G.fx0[pos] = __double2float_rd(lo);
+            G.fx1[pos] = __double2float_ru(hi);
+            G.fy0[pos] = __double2float_rd(dmin(ya, yb));
+            G.fy1[pos] = __double2float_ru(dmax(ya, yb));
+            G.mov[pos] = vmov[a];
+            double elo, ehi;
+            if (edge_yrange_s(xa, ya, xb, yb, sl, gxl, gxr, &elo, &ehi)) {
+                G.jlo[pos] = (short)(row_floor(I, elo) - 1);
+                G.jhi[pos] = (short)(row_floor(I, ehi) + 1);
+            } else {
+                G.jlo[pos] = 1;
+                G.jhi[pos] = 0;
             }
-            if (bits) {
-                for (int c = 0; c < ncol; ++c) {
-                    const double xl = node_coord(I.x0, i0 + c, I.dx), xr = node_coord(I.x0, i0 + c + 1, I.dx);
-                    double elo, ehi;
-                    if (!edge_yrange_s(xa, ya, xb, yb, sl, xl, xr, &elo, &ehi)) continue;
-                    int jl = row_floor(I, elo) - 1, jh = row_floor(I, ehi) + 1;
-                    if (jl < row0) jl = row0;
-                    if (jh > I.ny - 1) jh = I.ny - 1;
-                    if (jh > row0 + 32 * nwb - 1) jh = row0 + 32 * nwb - 1;
-                    for (int j = jl; j <= jh; ++j) {
-                        double ybj = node_coord(I.y0, j, I.dy), ytj = node_coord(I.y0, j + 1, I.dy);
-                        if (ehi >= ybj && elo <= ytj) atomicOr(&bits[c][(j - row0) >> 5], 1u << ((j - row0) & 31));
-                    }
-                }
-            }
+            G.ilo[pos] = (short)(col_floor(I, lo - ad) - 1);
+            G.ihi[pos] = (short)(col_floor(I, hi + ad) + 1);
+            // group columns whose closed x-range the edge may meet
+            const int c0 = col_floor(I, lo) - 1 - i0, c1 = col_floor(I, hi) + 1 - i0;
+            const int ca = c0 < 0 ? 0 : c0, cb = c1 > ncol - 1 ? ncol - 1 : c1;
+            np = cb >= ca ? cb - ca + 1 : 0;
+            G.pc0[pos] = (unsigned char)(np ? ca : 0);
         }
-        // grid-line crossings
-        for (int L = 0; L <= ncol; ++L) {
-            const double xs = node_coord(I.x0, i0 + L, I.dx);
-            const double lo = dmin(xa, xb), hi = dmax(xa, xb);
-            const bool c = take && xa != xb && lo <= xs && xs <= hi;
-            const unsigned mm = __ballot_sync(0xffffffffu, c);
-            if (c) {
-                const int p = lc[L] + __popc(mm & ((1u << lane) - 1u));
-                if (p < LMAXG) {
-                    G.lyc[L][p] = ya + (xs - xa) * sl;
-                    G.ls[L][p] = xa < xb ? 1 : -1;
-                    G.lf[L][p] = (unsigned char)((lo < xs ? 1 : 0) | (xs < hi ? 2 : 0));
-                }
-            }
-            lc[L] += __popc(mm);
+        int incl = np;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
         }
+        if (take && pos < EMAXG) G.pp[pos] = npair + incl - np;
+        npair += __shfl_sync(0xffffffffu, incl, 31);
         cnt += __popc(m);
     }
-    bool over = cnt > EMAXG;
-    for (int L = 0; L <= ncol; ++L) over |= lc[L] > LMAXG;
-    if (over && lane == 0) *err |= ERR_EDGE_CAP;
+    if (cnt > EMAXG && lane == 0) *err |= ERR_EDGE_CAP;
     if (lane == 0) {
-        G.cnt = cnt < EMAXG ? cnt : EMAXG;
-        for (int L = 0; L <= GC; ++L) G.lcnt[L] = L <= ncol ? (lc[L] < LMAXG ? lc[L] : LMAXG) : 0;
+        const int n = cnt < EMAXG ? cnt : EMAXG;
+        G.cnt = n;
+        G.pp[n] = npair;
+        G.npair = npair;
     }
     __syncwarp();
+}
+
+// all threads, after gather_g: per column the bit list of the edges whose
+// candidate columns contain it, per grid line x_{i0+L} the bit list of the
+// edges crossing it, and (bits != nullptr) the rows of each column whose
+// closed cell an edge meets (exact predicate)
+__device__ void index_g(GeoBufG &G, const InstDesc &I, int i0, int ncol, int row0, int nwb, unsigned (*bits)[NWB],
+                        int tid) {
+    const int n = G.cnt, nwd = (n + 31) >> 5;
+    for (int p = tid; p < (2 * ncol + 1) * nwd; p += GEOMG_THREADS) {
+        const int r = p / nwd, w = p - r * nwd;
+        unsigned msk = 0u;
+        if (r < ncol) {
+            const int i = i0 + r;
+            for (int b = 0; b < 32; ++b) {
+                const int e = w * 32 + b;
+                if (e < n && G.ilo[e] <= i && i <= G.ihi[e]) msk |= 1u << b;
+            }
+            G.cm[r][w] = msk;
+        } else {
+            const int L = r - ncol;
+            const double xs = G.xln[L];
+            const float fxs = (float)xs;
+            unsigned cand = 0u;
+            for (int b = 0; b < 32; ++b) {
+                const int e = w * 32 + b;
+                if (e < n && G.fx1[e] >= fxs && G.fx0[e] <= fxs) cand |= 1u << b;
+            }
+            for (; cand; cand &= cand - 1u) {
+                const int b = __ffs(cand) - 1, e = w * 32 + b;
+                const double xa = G.xa[e], xb = G.xb[e];
+                if (xa != xb && dmin(xa, xb) <= xs && xs <= dmax(xa, xb)) msk |= 1u << b;
+            }
+            G.lm[L][w] = msk;
+        }
+    }
+    if (!bits) return;
+    // (edge, column) pairs whose x-ranges may meet, enumerated densely
+    const int npair = G.npair;
+    for (int p = tid; p < npair; p += GEOMG_THREADS) {
+        int a = 0, b = n - 1;
+        while (a < b) {
+            const int mid = (a + b + 1) >> 1;
+            if (G.pp[mid] <= p) a = mid; else b = mid - 1;
+        }
+        const int e = a, c = G.pc0[e] + (p - G.pp[e]);
+        const double xl = G.xln[c], xr = G.xln[c + 1];
+        double elo, ehi;
+        if (!edge_yrange_s(G.xa[e], G.ya[e], G.xb[e], G.yb[e], G.slope[e], xl, xr, &elo, &ehi)) continue;
+        const int jf0 = row_floor(I, elo), jf1 = row_floor(I, ehi);
+        int jl = jf0 - 1, jh = jf1 + 1;
+        if (jl < row0) jl = row0;
+        if (jh > I.ny - 1) jh = I.ny - 1;
+        if (jh > row0 + 32 * nwb - 1) jh = row0 + 32 * nwb - 1;
+        for (int j = jl; j <= jh; ++j) {
+            // rows jf0+1 .. jf1-1 lie strictly inside [elo, ehi] whatever the
+            // rounding of the floors; the exact predicate decides the rest
+            bool hit = j > jf0 && j < jf1;
+            if (!hit) {
+                const double ybj = node_coord(I.y0, j, I.dy), ytj = node_coord(I.y0, j + 1, I.dy);
+                hit = ehi >= ybj && elo <= ytj;
+            }
+            if (hit) atomicOr(&bits[c][(j - row0) >> 5], 1u << ((j - row0) & 31));
+        }
+    }
+}
+
+// lanes 0..ncol of one warp, after index_g: the crossing lists of the grid
+// lines in edge order (crossing y, direction, which side of the line the
+// edge extends to)
+__device__ void compact_lines_g(GeoBufG &G, int ncol, int lane, int *err) {
+    if (lane <= GC) {
+        int k = 0;
+        if (lane <= ncol) {
+            const int L = lane;
+            const double xs = G.xln[L];
+            const int nwd = (G.cnt + 31) >> 5;
+            for (int w = 0; w < nwd; ++w)
+                for (unsigned m = G.lm[L][w]; m; m &= m - 1u) {
+                    const int e = w * 32 + __ffs(m) - 1;
+                    if (k < LMAXG) {
+                        const double xa = G.xa[e], xb = G.xb[e], ya = G.ya[e];
+                        const double lo = dmin(xa, xb), hi = dmax(xa, xb);
+                        G.lyc[L][k] = ya + (xs - xa) * G.slope[e];
+                        G.ls[L][k] = xa < xb ? 1 : -1;
+                        G.lf[L][k] = (unsigned char)((lo < xs ? 1 : 0) | (xs < hi ? 2 : 0));
+                    }
+                    ++k;
+                }
+            if (k > LMAXG) *err |= ERR_EDGE_CAP;
+        }
+        G.lcnt[lane] = k < LMAXG ? k : LMAXG;
+    }
+}
+
+// loop over the edges on column c's bit list, in gather order; `continue` in
+// the body moves to the next edge
+#define FOR_COL_EDGES(G, c, e)                                                              \
+    for (int e##_w = 0, e##_n = ((G).cnt + 31) >> 5; e##_w < e##_n; ++e##_w)                 \
+        for (unsigned e##_m = (G).cm[c][e##_w]; e##_m; e##_m &= e##_m - 1u)                  \
+            if (const int e = e##_w * 32 + __ffs(e##_m) - 1; true)
+
+// resumable walk over column c's edge bit list.  The geometry queries first
+// collect a lane's candidate edges with integer / FP32 tests (divergent but
+// cheap), then run the FP64 arithmetic over the collected edges, so that the
+// lanes of a warp execute the FP64 block together instead of once per edge
+// any lane needs.
+constexpr int SVN = 8;              // candidate edges collected per round
+struct ColIter {
+    int w, n;
+    unsigned m;
+};
+__device__ __forceinline__ void col_iter_init(const GeoBufG &G, int c, ColIter &it) {
+    it.n = (G.cnt + 31) >> 5;
+    it.w = 0;
+    it.m = it.n ? G.cm[c][0] : 0u;
+}
+__device__ __forceinline__ int col_iter_next(const GeoBufG &G, int c, ColIter &it) {
+    while (it.m == 0u) {
+        if (++it.w >= it.n) return -1;
+        it.m = G.cm[c][it.w];
+    }
+    const int e = it.w * 32 + __ffs(it.m) - 1;
+    it.m &= it.m - 1u;
+    return e;
 }
 
 __device__ __forceinline__ double line_solid_vg(const GeoBufG &G, int L, double y0r, double y1r, bool left_limit) {
@@ -585,30 +708,41 @@ __device__ double line_solid_hg(const GeoBufG &G, int c, int i, double xl, doubl
     double ex[8];
     int ed[8], ne = 0;
     bool overflow = false;
-    for (int e = 0; e < G.cnt; ++e) {
-        if (G.jhi[e] < jf - 1 || G.jlo[e] > jf || G.ihi[e] < i || G.ilo[e] > i) continue;
-        const double xa = G.xa[e], xb = G.xb[e], ya = G.ya[e], yb = G.yb[e];
-        if (ya == yb) continue;
-        if ((ya < yf) == (yb < yf)) continue;
-        const double xs = xa == xb ? xa : xa + (yf - ya) / G.slope[e];
-        if (!(xs > xl && xs < xr)) continue;
-        // crossing the boundary left to right: the interior of a
-        // counter-clockwise polygon lies left of its edges
-        const int dw = yb > ya ? -1 : 1;
-        if (ne < 8) {
-            int p = ne++;
-            while (p > 0 && ex[p - 1] > xs) { ex[p] = ex[p - 1]; ed[p] = ed[p - 1]; --p; }
-            ex[p] = xs;
-            ed[p] = dw;
-        } else {
-            overflow = true;
+    const float fyf = (float)yf;
+    ColIter it;
+    col_iter_init(G, c, it);
+    for (;;) {
+        int sv[SVN], ns = 0, en;
+        while (ns < SVN && (en = col_iter_next(G, c, it)) >= 0) {
+            if (G.jhi[en] < jf - 1 || G.jlo[en] > jf) continue;
+            if (G.fy1[en] < fyf || G.fy0[en] > fyf) continue;
+            sv[ns++] = en;
         }
+        for (int q = 0; q < ns; ++q) {
+            const int e = sv[q];
+            const double xa = G.xa[e], xb = G.xb[e], ya = G.ya[e], yb = G.yb[e];
+            if (ya == yb) continue;
+            if ((ya < yf) == (yb < yf)) continue;
+            const double xs = xa == xb ? xa : xa + (yf - ya) * (xb - xa) * G.idy[e];
+            if (!(xs > xl && xs < xr)) continue;
+            // crossing the boundary left to right: the interior of a
+            // counter-clockwise polygon lies left of its edges
+            const int dw = yb > ya ? -1 : 1;
+            if (ne < 8) {
+                int p = ne++;
+                while (p > 0 && ex[p - 1] > xs) { ex[p] = ex[p - 1]; ed[p] = ed[p - 1]; --p; }
+                ex[p] = xs;
+                ed[p] = dw;
+            } else {
+                overflow = true;
+            }
+        }
+        if (ns < SVN) break;
     }
     if (overflow) {   // many crossings inside one column: integrate edge by edge
         double L = 0.0;
-        for (int e = 0; e < G.cnt; ++e) {
-            if (G.ihi[e] < i || G.ilo[e] > i) continue;
-            const double xa = G.xa[e], xb = G.xb[e], ya = G.ya[e], yb = G.yb[e];
+        FOR_COL_EDGES(G, c, e) {
+            const double xa = G.xa[e], xb = G.xb[e], ya = G.ya[e];
             const double p = dmax(xl, dmin(xa, xb)), q = dmin(xr, dmax(xa, xb));
             if (!(q > p)) continue;
             const double s = xa < xb ? 1.0 : -1.0;
@@ -636,51 +770,64 @@ __device__ double line_solid_hg(const GeoBufG &G, int c, int i, double xl, doubl
     return L;
 }
 
-__device__ double rect_edges_g(const GeoBufG &G, int i, int ja, int jb, double rx0, double rx1, double ry0,
+__device__ double rect_edges_g(const GeoBufG &G, int c, int ja, int jb, double rx0, double rx1, double ry0,
                                double ry1, double xo, double xs, double *nlx, double *nly, bool *mov) {
     const double lx0 = rx0 - xo, lx1 = rx1 - xo, ly1 = ry1 - ry0;
+    const float frx0 = __double2float_rd(rx0), frx1 = __double2float_ru(rx1);
+    const float fry0 = __double2float_rd(ry0), fry1 = __double2float_ru(ry1);
     double A = 0.0;
-    for (int e = 0; e < G.cnt; ++e) {
-        if (G.jhi[e] < ja || G.jlo[e] > jb || G.ihi[e] < i || G.ilo[e] > i) continue;
-        const double xa = G.xa[e], xb = G.xb[e], ya = G.ya[e], yb = G.yb[e];
-        if (dmax(ya, yb) < ry0 || dmin(ya, yb) > ry1 || dmax(xa, xb) < rx0 || dmin(xa, xb) > rx1) continue;
-        const double ax = xa - xo, ay = ya - ry0, bx = xb - xo, by = yb - ry0;
-        const double ddx = bx - ax, ddy = by - ay;
-        double t0 = 0.0, t1 = 1.0;
-        bool ok = true;
-        if (ddx == 0.0) {
-            if (ax < lx0 || ax > lx1) ok = false;
-        } else {
-            const double inv = 1.0 / ddx;
-            const double ra = (lx0 - ax) * inv, rb = (lx1 - ax) * inv;
-            t0 = dmax(t0, dmin(ra, rb));
-            t1 = dmin(t1, dmax(ra, rb));
+    ColIter it;
+    col_iter_init(G, c, it);
+    for (;;) {
+        int sv[SVN], ns = 0, en;
+        while (ns < SVN && (en = col_iter_next(G, c, it)) >= 0) {
+            if (G.jhi[en] < ja || G.jlo[en] > jb) continue;
+            if (G.fy1[en] < fry0 || G.fy0[en] > fry1 || G.fx1[en] < frx0 || G.fx0[en] > frx1) continue;
+            sv[ns++] = en;
         }
-        if (ddy == 0.0) {
-            if (ay < 0.0 || ay > ly1) ok = false;
-        } else {
-            const double inv = 1.0 / ddy;
-            const double ra = (0.0 - ay) * inv, rb = (ly1 - ay) * inv;
-            t0 = dmax(t0, dmin(ra, rb));
-            t1 = dmin(t1, dmax(ra, rb));
+        for (int k = 0; k < ns; ++k) {
+            const int e = sv[k];
+            const double xa = G.xa[e], xb = G.xb[e], ya = G.ya[e], yb = G.yb[e];
+            if (dmax(ya, yb) < ry0 || dmin(ya, yb) > ry1 || dmax(xa, xb) < rx0 || dmin(xa, xb) > rx1) continue;
+            const double ax = xa - xo, ay = ya - ry0, bx = xb - xo, by = yb - ry0;
+            const double ddx = bx - ax, ddy = by - ay;
+            double t0 = 0.0, t1 = 1.0;
+            bool ok = true;
+            if (ddx == 0.0) {
+                if (ax < lx0 || ax > lx1) ok = false;
+            } else {
+                const double inv = G.idx[e];
+                const double ra = (lx0 - ax) * inv, rb = (lx1 - ax) * inv;
+                t0 = dmax(t0, dmin(ra, rb));
+                t1 = dmin(t1, dmax(ra, rb));
+            }
+            if (ddy == 0.0) {
+                if (ay < 0.0 || ay > ly1) ok = false;
+            } else {
+                const double inv = G.idy[e];
+                const double ra = (0.0 - ay) * inv, rb = (ly1 - ay) * inv;
+                t0 = dmax(t0, dmin(ra, rb));
+                t1 = dmin(t1, dmax(ra, rb));
+            }
+            if (!ok || t1 < t0) continue;
+            if (mov && G.mov[e]) *mov = true;
+            if (xa == xb && xa == xs) continue;   // vertical edge on the grid side
+            if (!(t1 > t0)) continue;
+            const double xc0 = ax + t0 * ddx, xc1 = ax + t1 * ddx;
+            A += ddy * (t1 - t0) * (0.5 * (xc0 + xc1));
+            if (nlx) {
+                *nlx -= ddy * (t1 - t0);
+                *nly += ddx * (t1 - t0);
+            }
         }
-        if (!ok || t1 < t0) continue;
-        if (mov && G.mov[e]) *mov = true;
-        if (xa == xb && xa == xs) continue;   // vertical edge on the grid side
-        if (!(t1 > t0)) continue;
-        const double xc0 = ax + t0 * ddx, xc1 = ax + t1 * ddx;
-        A += ddy * (t1 - t0) * (0.5 * (xc0 + xc1));
-        if (nlx) {
-            *nlx -= ddy * (t1 - t0);
-            *nly += ddx * (t1 - t0);
-        }
+        if (ns < SVN) break;
     }
     return A;
 }
 
 __device__ __forceinline__ double cell_alpha_g(const GeoBufG &G, const InstDesc &I, int c, int i, int j, double xl,
                                                double xr, double yb, double yt, double *nlx, double *nly, bool *mov) {
-    double A = rect_edges_g(G, i, j, j, xl, xr, yb, yt, xl, xr, nlx, nly, mov) +
+    double A = rect_edges_g(G, c, j, j, xl, xr, yb, yt, xl, xr, nlx, nly, mov) +
                (xr - xl) * line_solid_vg(G, c + 1, yb, yt, true);
     double a = clamp01(1.0 - A / (I.dx * I.dy));
     return a < ALPHA_MIN ? 0.0 : a;
@@ -700,24 +847,24 @@ __device__ double swept_face_Bg(const GeoBufG &G, const InstDesc &I, int dir, do
         const double xs = hi ? xr : xl;
         if (delta > 0.0) {
             const double x1 = xs + delta;
-            const double A = rect_edges_g(G, i, j, j, xs, x1, yb, yt, x1, xs, nullptr, nullptr, nullptr) +
+            const double A = rect_edges_g(G, c, j, j, xs, x1, yb, yt, x1, xs, nullptr, nullptr, nullptr) +
                              (x1 - xs) * line_solid_vg(G, line, yb, yt, false);
             return clamp01(1.0 - A / ((x1 - xs) * I.dy));
         }
         const double x0 = xs + delta;
-        const double A = rect_edges_g(G, i, j, j, x0, xs, yb, yt, x0, xs, nullptr, nullptr, nullptr) +
+        const double A = rect_edges_g(G, c, j, j, x0, xs, yb, yt, x0, xs, nullptr, nullptr, nullptr) +
                          (xs - x0) * line_solid_vg(G, line, yb, yt, true);
         return clamp01(1.0 - A / ((xs - x0) * I.dy));
     }
     const double ys = hi ? yt : yb;
     const double y0 = delta > 0.0 ? ys : ys + delta, y1 = delta > 0.0 ? ys + delta : ys;
     const int ja = delta > 0.0 ? j : j - 1, jb = delta > 0.0 ? j + 1 : j;
-    const double A = rect_edges_g(G, i, ja, jb, xl, xr, y0, y1, xl, xr, nullptr, nullptr, nullptr) +
+    const double A = rect_edges_g(G, c, ja, jb, xl, xr, y0, y1, xl, xr, nullptr, nullptr, nullptr) +
                      (xr - xl) * line_solid_vg(G, c + 1, y0, y1, true);
     return clamp01(1.0 - A / ((y1 - y0) * I.dx));
 }
 
-__global__ void __launch_bounds__(GEOMG_WARPS * 32) k_geom(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y,
+__global__ void __launch_bounds__(GEOMG_THREADS) k_geom(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y,
                                                          const double *__restrict__ px, const double *__restrict__ py,
                                                          const float *__restrict__ ebox,
                                                          const int *__restrict__ vnext,
@@ -725,10 +872,11 @@ __global__ void __launch_bounds__(GEOMG_WARPS * 32) k_geom(const InstDesc *__res
                                                          int n_inst, int total_groups, int dir,
                                                          BandRec *__restrict__ R, double *__restrict__ bnd) {
     extern __shared__ __align__(16) unsigned char gsm[];
-    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    GeoWarpG &W = ((GeoWarpG *)gsm)[wib];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, tid = threadIdx.x;
+    GeoWarpG &W = *(GeoWarpG *)gsm;
     GeoBufG &G = W.G;
-    const int gw = blockIdx.x * GEOMG_WARPS + wib;
+    __shared__ int sh_base;
+    const int gw = blockIdx.x;
     if (gw >= total_groups) return;
     int lo = 0, hi = n_inst - 1;
     while (lo < hi) {
@@ -748,46 +896,60 @@ __global__ void __launch_bounds__(GEOMG_WARPS * 32) k_geom(const InstDesc *__res
     int err = 0;
     if (y.row1 < y.row0) return;
     if (nwb > NWB) {
-        if (lane == 0) atomicOr(&y.err, ERR_BAND_CAP);
+        if (tid == 0) atomicOr(&y.err, ERR_BAND_CAP);
         return;
     }
-    for (int w = lane; w < GC * NWB; w += 32) {
+    for (int w = tid; w < GC * NWB; w += GEOMG_THREADS) {
         (&W.bA[0][0])[w] = 0u;
         (&W.bB[0][0])[w] = 0u;
         (&W.bM[0][0])[w] = 0u;
     }
-    __syncwarp();
+    __syncthreads();
     // touched at the start pose: class bytes kept from the previous sweep
-    for (int c = 0; c < ncol; ++c)
-        for (int j = row0 + lane; j <= y.row1; j += 32)
-            if (I.cls[j * I.pitch + i0 + c] & CLS_TOUCH) atomicOr(&W.bA[c][(j - row0) >> 5], 1u << ((j - row0) & 31));
-    if (I.rotating) gather_g(G, I, px, py, ebox, vnext, vmov, 1, total_v, i0, ncol, ad, row0, nwb, W.bM, lane, &err);
-    gather_g(G, I, px, py, ebox, vnext, vmov, 2, total_v, i0, ncol, ad, row0, nwb, W.bB, lane, &err);
+    const int nrow = y.row1 - row0 + 1;
+    for (int p = tid; p < nrow * ncol; p += GEOMG_THREADS) {
+        const int jr = p / ncol, c = p - jr * ncol;
+        if (I.cls[(row0 + jr) * I.pitch + i0 + c] & CLS_TOUCH) atomicOr(&W.bA[c][jr >> 5], 1u << (jr & 31));
+    }
+    if (I.rotating) {   // touched at the middle pose
+        if (warp == 0) gather_g(G, I, px, py, ebox, vnext, vmov, 1, total_v, i0, ncol, ad, lane, &err);
+        __syncthreads();
+        index_g(G, I, i0, ncol, row0, nwb, W.bM, tid);
+        __syncthreads();
+    }
+    if (warp == 0) gather_g(G, I, px, py, ebox, vnext, vmov, 2, total_v, i0, ncol, ad, lane, &err);
+    __syncthreads();
+    index_g(G, I, i0, ncol, row0, nwb, W.bB, tid);
+    __syncthreads();
+    if (warp == 1) compact_lines_g(G, ncol, lane, &err);
     // band cells in (column, row) order: prefix counts over the words
     const int nw = ncol * nwb;
-    int running = 0;
-    for (int w0 = 0; w0 < nw; w0 += 32) {
-        const int w = w0 + lane;
-        const int c = w / nwb, k = w % nwb;
-        int cnt = w < nw ? __popc(W.bA[c][k] | W.bB[c][k] | W.bM[c][k]) : 0;
-        int incl = cnt;
-        for (int o = 1; o < 32; o <<= 1) {
-            int v = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += v;
+    if (warp == 0) {
+        int running = 0;
+        for (int w0 = 0; w0 < nw; w0 += 32) {
+            const int w = w0 + lane;
+            const int c = w / nwb, k = w % nwb;
+            int cnt = w < nw ? __popc(W.bA[c][k] | W.bB[c][k] | W.bM[c][k]) : 0;
+            int incl = cnt;
+            for (int o = 1; o < 32; o <<= 1) {
+                int v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            if (w < nw) W.wpre[w] = running + incl - cnt;
+            running += __shfl_sync(0xffffffffu, incl, 31);
         }
-        if (w < nw) W.wpre[w] = running + incl - cnt;
-        running += __shfl_sync(0xffffffffu, incl, 31);
+        if (lane == 0) {
+            W.wpre[GC * NWB] = running;
+            int b = running ? atomicAdd(&y.band_count, running) : 0;
+            if (b + running > I.rec_cap) { err |= ERR_BAND_CAP; b = -1; }
+            sh_base = b;
+        }
     }
-    const int T = running;
-    int base = 0;
-    if (lane == 0) {
-        base = T ? atomicAdd(&y.band_count, T) : 0;
-        if (base + T > I.rec_cap) { err |= ERR_BAND_CAP; base = -1; }
-    }
-    base = __shfl_sync(0xffffffffu, base, 0);
-    __syncwarp();
+    __syncthreads();
+    const int T = W.wpre[GC * NWB];
+    const int base = sh_base;
     if (base < 0 || T == 0) {
-        if (lane == 0 && err) atomicOr(&y.err, err);
+        if (err) atomicOr(&y.err, err);
         return;
     }
     auto locate = [&](int t, int *c, int *j, int *k, int *bit) {
@@ -804,12 +966,12 @@ __global__ void __launch_bounds__(GEOMG_WARPS * 32) k_geom(const InstDesc *__res
     };
     const double wsimp_B = 1.0 / 6.0, wsimp_M = 4.0 / 6.0, wsimp_A = 1.0 / 6.0;
     // pass B (edges of the end pose are in G)
-    for (int t = lane; t < T; t += 32) {
+    for (int t = tid; t < T; t += GEOMG_THREADS) {
         int c, j, k, bit;
         locate(t, &c, &j, &k, &bit);
         const int i = i0 + c;
         BandRec &r = R[I.rec_base + base + t];
-        const double xl = node_coord(I.x0, i, I.dx), xr = node_coord(I.x0, i + 1, I.dx);
+        const double xl = G.xln[c], xr = G.xln[c + 1];
         const double yb = node_coord(I.y0, j, I.dy), yt = node_coord(I.y0, j + 1, I.dy);
         const bool tA = (W.bA[c][k] >> bit) & 1u, tB = (W.bB[c][k] >> bit) & 1u, tM = (W.bM[c][k] >> bit) & 1u;
         const int cell = j * I.pitch + i;
@@ -837,14 +999,20 @@ __global__ void __launch_bounds__(GEOMG_WARPS * 32) k_geom(const InstDesc *__res
                   ((mov || movA) ? RF_MOVING : 0) | (mov ? RF_MOV_B : 0);
     }
     // pass M
-    gather_g(G, I, px, py, ebox, vnext, vmov, 1, total_v, i0, ncol, ad, row0, nwb, nullptr, lane, &err);
-    for (int t = lane; t < T; t += 32) {
+    __syncthreads();
+    if (warp == 0) gather_g(G, I, px, py, ebox, vnext, vmov, 1, total_v, i0, ncol, ad, lane, &err);
+    __syncthreads();
+    index_g(G, I, i0, ncol, row0, nwb, nullptr, tid);
+    __syncthreads();
+    if (warp == 1) compact_lines_g(G, ncol, lane, &err);
+    __syncthreads();
+    for (int t = tid; t < T; t += GEOMG_THREADS) {
         int c, j, k, bit;
         locate(t, &c, &j, &k, &bit);
         const int i = i0 + c;
         const int ri = I.rec_base + base + t;
         BandRec &r = R[ri];
-        const double xl = node_coord(I.x0, i, I.dx), xr = node_coord(I.x0, i + 1, I.dx);
+        const double xl = G.xln[c], xr = G.xln[c + 1];
         const double yb = node_coord(I.y0, j, I.dy), yt = node_coord(I.y0, j + 1, I.dy);
         bool mov = false;
         double nlx = 0.0, nly = 0.0;
@@ -885,20 +1053,26 @@ __global__ void __launch_bounds__(GEOMG_WARPS * 32) k_geom(const InstDesc *__res
         I.cls[r.cell] |= CLS_BAND;
     }
     if (I.rotating) {
-        gather_g(G, I, px, py, ebox, vnext, vmov, 0, total_v, i0, ncol, ad, row0, nwb, nullptr, lane, &err);
-        for (int t = lane; t < T; t += 32) {
+        __syncthreads();
+        if (warp == 0) gather_g(G, I, px, py, ebox, vnext, vmov, 0, total_v, i0, ncol, ad, lane, &err);
+        __syncthreads();
+        index_g(G, I, i0, ncol, row0, nwb, nullptr, tid);
+        __syncthreads();
+        if (warp == 1) compact_lines_g(G, ncol, lane, &err);
+        __syncthreads();
+        for (int t = tid; t < T; t += GEOMG_THREADS) {
             int c, j, k, bit;
             locate(t, &c, &j, &k, &bit);
             const int i = i0 + c;
             const int ri = I.rec_base + base + t;
-            const double xl = node_coord(I.x0, i, I.dx), xr = node_coord(I.x0, i + 1, I.dx);
+            const double xl = G.xln[c], xr = G.xln[c + 1];
             const double yb = node_coord(I.y0, j, I.dy), yt = node_coord(I.y0, j + 1, I.dy);
             R[ri].bown += wsimp_A * face_ap_g(G, I, dir, true, c, i, j, xl, xr, yb, yt);
             const bool need_bnd = dir == 0 ? (i == 0 && I.bc[0] != 2) : (j == 0 && I.bc[2] != 2);
             if (need_bnd) bnd[ri] += wsimp_A * face_ap_g(G, I, dir, false, c, i, j, xl, xr, yb, yt);
         }
     }
-    if (lane == 0 && err) atomicOr(&y.err, err);
+    if (err) atomicOr(&y.err, err);
 }
 
 // ---------------------------------------------------------------------------
@@ -985,7 +1159,7 @@ __global__ void k_pose_current(const InstDesc *__restrict__ D, const InstDyn *__
 // launchers
 // ---------------------------------------------------------------------------
 static size_t geom_smem() { return sizeof(GeoWarp) * GEOM_WARPS; }
-static size_t geomg_smem() { return sizeof(GeoWarpG) * GEOMG_WARPS; }
+static size_t geomg_smem() { return sizeof(GeoWarpG); }
 
 void geom_init() {
     cudaFuncSetAttribute(k_geom, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)geomg_smem());
@@ -1001,9 +1175,9 @@ void launch_pose(const InstDesc *D, InstDyn *Y, const double *vx, const double *
 void launch_geom(const InstDesc *D, InstDyn *Y, const double *px, const double *py, const float *ebox,
                  const int *vnext, const unsigned char *vmov, int total_v, int n_inst, int total_groups, int dir,
                  BandRec *R, double *bnd, cudaStream_t st) {
-    int blocks = (total_groups + GEOMG_WARPS - 1) / GEOMG_WARPS;
+    int blocks = total_groups;
     if (blocks > 0)
-        k_geom<<<blocks, GEOMG_WARPS * 32, geomg_smem(), st>>>(D, Y, px, py, ebox, vnext, vmov, total_v, n_inst,
+        k_geom<<<blocks, GEOMG_THREADS, geomg_smem(), st>>>(D, Y, px, py, ebox, vnext, vmov, total_v, n_inst,
                                                              total_groups, dir, R, bnd);
 }
 
@@ -1154,6 +1328,8 @@ extern "C" mb_status mb_cut_cells_noalloc(const mb_grid *grid, const mb_body *bo
     I.x0 = grid->x0; I.y0 = grid->y0;
     I.dx = (grid->x1 - grid->x0) / (double)grid->nx;
     I.dy = (grid->y1 - grid->y0) / (double)grid->ny;
+    I.rdx = 1.0 / I.dx;
+    I.rdy = 1.0 / I.dy;
     for (int q = 0; q < 4; ++q) I.bc[q] = grid->bc[q];
     I.nv = nv;
     I.voff = 0;

@@ -7,6 +7,7 @@
 namespace mb {
 
 constexpr int MAXC = 4;
+constexpr int GEO_GC = 16;            // grid columns per geometry group (one CTA each)
 constexpr double ALPHA_MIN = 1e-10;   // smaller volume fractions count as solid
 
 // cell class byte (state at the current pose A of the sweep)
@@ -55,6 +56,7 @@ struct BandRec {
 struct InstDesc {
     int nx, ny, pitch, nc;
     double x0, y0, dx, dy;
+    double rdx, rdy;            // 1/dx, 1/dy (candidate row and column ranges only)
     int bc[4];
     int eq;
     int ucov;

@@ -165,7 +165,10 @@ __global__ void k_band_prep(const InstDesc *__restrict__ D, InstDyn *__restrict_
             double g = I.gamma;
             double rs, ps_step, usx, usy, rs2, ps_sw, u2x, u2y;
             wall_state(g, qs, b.nx, b.ny, b.wx, b.wy, &rs, &ps_step, &usx, &usy);
-            wall_state(g, qc, b.nx, b.ny, b.wx, b.wy, &rs2, &ps_sw, &u2x, &u2y);
+            bool same = true;
+            for (int q = 0; q < 4; ++q) same = same && qs[q] == qc[q];
+            if (same) ps_sw = ps_step;   // first sweep of a step: one state
+            else wall_state(g, qc, b.nx, b.ny, b.wx, b.wy, &rs2, &ps_sw, &u2x, &u2y);
             double Eadv = ps_step / (g - 1.0) + 0.5 * rs * (usx * usx + usy * usy);
             double ud = dir == 0 ? usx : usy;
             b.QB[0] = rs; b.QB[1] = rs * usx; b.QB[2] = rs * usy; b.QB[3] = Eadv;
@@ -550,7 +553,7 @@ __global__ void __launch_bounds__(256) k_bulk_x(const InstDesc *__restrict__ D, 
 // with a register window; 32 consecutive columns per warp keep every load
 // and store coalesced
 template <class T, int EQ>
-__global__ void __launch_bounds__(256) k_bulk_y(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y,
+__global__ void __launch_bounds__(256, 3) k_bulk_y(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y,
                                                 const BandRec *__restrict__ R, int n_inst, int total_warps, int src,
                                                 int dst, int last) {
     constexpr int NC = EQ == 0 ? 4 : 1;
