@@ -23,9 +23,10 @@
 
 namespace mb {
 void geom_init();
+void launch_nodes(const InstDesc *, int, cudaStream_t);
 void launch_pose(const InstDesc *, InstDyn *, const double *, const double *, const unsigned char *, const int *,
                  double *, double *, float *, int, int, int, int, double, cudaStream_t);
-void launch_geom(const InstDesc *, InstDyn *, const double *, const double *, const float *, const int *,
+void launch_geom(const InstDesc *, InstDyn *, const int *, const double *, const double *, const float *, const int *,
                  const unsigned char *, int, int, int, int, BandRec *, double *, cudaStream_t);
 void launch_classify(const InstDesc *, InstDyn *, const double *, const double *, const unsigned char *, double *,
                      double *, float *, const int *, int, int, int, double *, cudaStream_t);
@@ -64,7 +65,8 @@ struct mb_sim {
     int *scratch = nullptr;
     double *stage = nullptr;      // staging for state I/O (nc * max cells doubles)
     size_t stage_len = 0;
-    int total_cols = 0;
+    int total_cols = 0;           // geometry groups
+    int *ginst = nullptr;         // instance of each geometry group
     int total_tiles[2] = {0, 0};
     int bulk_grid[2] = {0, 0};
     std::vector<void *> allocs;
@@ -201,6 +203,8 @@ mb_status mb_batch_create(int n, const mb_grid *grids, const double *gammas, con
         I.dy = (g.y1 - g.y0) / (double)g.ny;
         I.rdx = 1.0 / I.dx;
         I.rdy = 1.0 / I.dy;
+        I.rdxf = (float)I.rdx;
+        I.rdyf = (float)I.rdy;
         for (int q = 0; q < 4; ++q) I.bc[q] = g.bc[q];
         I.eq = g.equation;
         I.ucov = g.uncover_mode;
@@ -247,8 +251,6 @@ mb_status mb_batch_create(int n, const mb_grid *grids, const double *gammas, con
         }
         if (I.nv == 0) gcols = 0;
         I.gcol_max = gcols;
-        I.gcol_off = col_total;          // in units of GEO_GC-column geometry groups
-        col_total += (gcols + GEO_GC - 1) / GEO_GC;
         // bulk work items: x sweep one warp per row; y sweep one warp per 32
         // columns and 64-row segment
         I.tiles_x[0] = 1;
@@ -264,9 +266,36 @@ mb_status mb_batch_create(int n, const mb_grid *grids, const double *gammas, con
         CK(dalloc(s, &I.cls, cells));
         CK(dalloc(s, &I.rec, cells * sizeof(int)));
         CK(dalloc(s, &I.alpha, cells * sizeof(double)));
+        {
+            double *xn = nullptr, *yn = nullptr;
+            CK(dalloc(s, &xn, (g.nx + 1) * sizeof(double)));
+            CK(dalloc(s, &yn, (g.ny + 1) * sizeof(double)));
+            I.xn = xn;
+            I.yn = yn;
+        }
         CK(cudaMemsetAsync(I.cls, 0, cells, s->stream));
         CK(cudaMemsetAsync(I.rec, 0xff, cells * sizeof(int), s->stream));
         max_cells = std::max(max_cells, (size_t)g.nx * g.ny);
+    }
+    // geometry groups (GEO_GC columns, one CTA each): instances with more
+    // polygon vertices first, so that the groups with the most cut cells start
+    // in the first wave of CTAs
+    {
+        std::vector<int> order(n);
+        for (int k = 0; k < n; ++k) order[k] = k;
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int a, int b) { return s->hd[a].nv > s->hd[b].nv; });
+        std::vector<int> ginst;
+        for (int k : order) {
+            InstDesc &I = s->hd[k];
+            I.gcol_off = col_total;
+            const int ng = (I.gcol_max + GEO_GC - 1) / GEO_GC;
+            for (int q = 0; q < ng; ++q) ginst.push_back(k);
+            col_total += ng;
+        }
+        CK(dalloc(s, &s->ginst, std::max<size_t>(1, ginst.size()) * sizeof(int)));
+        if (!ginst.empty())
+            CK(cudaMemcpy(s->ginst, ginst.data(), ginst.size() * sizeof(int), cudaMemcpyHostToDevice));
     }
     s->total_v = (int)hvx.size();
     s->total_rec = rec_total;
@@ -297,6 +326,7 @@ mb_status mb_batch_create(int n, const mb_grid *grids, const double *gammas, con
     CK(dalloc(s, &s->dy, n * sizeof(InstDyn)));
     CK(cudaMemcpy(s->dd, s->hd.data(), n * sizeof(InstDesc), cudaMemcpyHostToDevice));
     CK(cudaMemset(s->dy, 0, n * sizeof(InstDyn)));
+    launch_nodes(s->dd, n, s->stream);
     for (int d = 0; d < 2; ++d) {
         int bps = prec == MB_FP32 ? bulk_blocks_per_sm<float>(d) : bulk_blocks_per_sm<double>(d);
         s->bulk_grid[d] = bps * nsm;
@@ -355,7 +385,7 @@ static mb_status do_sweep(mb_sim *s, int dir, double dt) {
     cudaStream_t st = s->stream;
     launch_pose(s->dd, s->dy, s->vx, s->vy, s->vmov, s->vnext, s->px, s->py, s->ebox, s->total_v, s->n, dir, s->sidx,
                 dt, st);
-    launch_geom(s->dd, s->dy, s->px, s->py, s->ebox, s->vnext, s->vmov, s->total_v, s->n, s->total_cols, dir, s->rec,
+    launch_geom(s->dd, s->dy, s->ginst, s->px, s->py, s->ebox, s->vnext, s->vmov, s->total_v, s->n, s->total_cols, dir, s->rec,
                 s->bnd, st);
     auto band = [&](int stage) {
         if (s->prec == MB_FP32)

@@ -435,7 +435,7 @@ constexpr int GC = GEO_GC;          // columns per group
 constexpr int EMAXG = 384;          // edges per group and pose
 constexpr int LMAXG = 32;           // crossings per grid line
 constexpr int NWB = 64;             // bitmap words per column (2048 rows of the body's extent)
-constexpr int GEOMG_THREADS = 128;  // one CTA per group; its warps share the group's edges
+constexpr int GEOMG_THREADS = 256;  // one CTA per group; its warps share the group's edges
 constexpr int EWORDS = EMAXG / 32;  // words of a column's edge bit list
 
 struct GeoBufG {
@@ -449,6 +449,8 @@ struct GeoBufG {
     unsigned char pc0[EMAXG];       // first group column the edge's x-range may meet
     int pp[EMAXG + 1];              // prefix over edges of their (edge, column) pairs
     int npair;
+    unsigned chm[GEOMG_THREADS / 4];      // gather: take masks of a batch of vertex chunks
+    int chp[GEOMG_THREADS / 4 + 1];       // gather: their exclusive prefix
     unsigned cm[GC][EWORDS];        // per column: edges whose candidate columns contain it
     unsigned lm[GC + 1][EWORDS];    // per grid line: edges crossing it
     double xln[GC + 1];             // x of the grid lines x_{i0} .. x_{i0+GC}
@@ -483,35 +485,84 @@ __device__ __forceinline__ bool edge_yrange_s(double xa, double ya, double xb, d
     return true;
 }
 
+// FP32 floors for candidate ranges (superset tests with a one-cell margin):
+// the FP64 offset rounded to FP32 and scaled is within 0.01 cell of the exact
+// position for grids up to 16384 cells
+__device__ __forceinline__ int row_floor_f(const InstDesc &I, double yv) {
+    float f = __double2float_rn(yv - I.y0) * I.rdyf;
+    f = fminf(fmaxf(f, -4.0f), (float)I.ny + 4.0f);
+    return (int)floorf(f);
+}
+__device__ __forceinline__ int col_floor_f(const InstDesc &I, double xv) {
+    float f = __double2float_rn(xv - I.x0) * I.rdxf;
+    f = fminf(fmaxf(f, -4.0f), (float)I.nx + 4.0f);
+    return (int)floorf(f);
+}
+
 __device__ __forceinline__ int col_floor(const InstDesc &I, double xv) {
     double f = (xv - I.x0) * I.rdx;
     f = fmin(fmax(f, -4.0), (double)I.nx + 4.0);
     return (int)floor(f);
 }
 
-// warp 0: the edges whose x-range meets the group's widened x-range at pose
-// P, compacted into G in vertex order with their per-edge data
+// all threads: the edges whose x-range meets the group's widened x-range at
+// pose P, compacted into G in vertex order with their per-edge data.  The
+// warps test batches of 32-vertex chunks against the FP32 x-bounds together;
+// a prefix over the chunks' counts keeps the vertex order.
+constexpr int GNW = GEOMG_THREADS / 32;     // warps per CTA
+constexpr int GCPW = 8;                     // chunks per warp and batch
+constexpr int GNCH = GNW * GCPW;            // chunks per batch
+static_assert(GNCH == GEOMG_THREADS / 4, "chunk batch arrays of GeoBufG");
 __device__ void gather_g(GeoBufG &G, const InstDesc &I, const double *__restrict__ px, const double *__restrict__ py,
                          const float *__restrict__ ebox, const int *__restrict__ vnext,
                          const unsigned char *__restrict__ vmov, int P, int total_v, int i0, int ncol, double ad,
-                         int lane, int *err) {
+                         int tid, int *err) {
+    const int lane = tid & 31, warp = tid >> 5;
     const double *PX = px + (size_t)P * total_v, *PY = py + (size_t)P * total_v;
-    const float *EB = ebox + (size_t)P * total_v * 2;
-    if (lane <= GC) G.xln[lane] = node_coord(I.x0, i0 + lane, I.dx);
-    __syncwarp();
+    const float2 *EB = (const float2 *)(ebox + (size_t)P * total_v * 2) + I.voff;
+    if (tid <= ncol) G.xln[tid] = I.xn[i0 + tid];
+    __syncthreads();
     const double gxl = G.xln[0] - ad, gxr = G.xln[ncol] + ad;
     const float fl = __double2float_rd(gxl), fr = __double2float_ru(gxr);
-    int cnt = 0, npair = 0;
-    for (int base = 0; base < I.nv; base += 32) {
-        const int k = base + lane;
-        const int a = I.voff + k;
-        bool take = false;
-        if (k < I.nv) take = EB[2 * a + 1] >= fl && EB[2 * a] <= fr;
-        const unsigned m = __ballot_sync(0xffffffffu, take);
-        if (m == 0u) continue;
-        const int pos = cnt + __popc(m & ((1u << lane) - 1u));
-        int np = 0;
-        if (take && pos < EMAXG) {
+    int cnt = 0;
+    for (int b0 = 0; b0 < I.nv; b0 += 32 * GNCH) {
+        float2 eb[GCPW];
+#pragma unroll
+        for (int u = 0; u < GCPW; ++u) {
+            const int k = b0 + (warp + u * GNW) * 32 + lane;
+            eb[u] = k < I.nv ? EB[k] : make_float2(1.0f, 0.0f);
+        }
+#pragma unroll
+        for (int u = 0; u < GCPW; ++u) {
+            const int k = b0 + (warp + u * GNW) * 32 + lane;
+            const bool take = k < I.nv && eb[u].y >= fl && eb[u].x <= fr;
+            const unsigned m = __ballot_sync(0xffffffffu, take);
+            if (lane == 0) G.chm[warp + u * GNW] = m;
+        }
+        __syncthreads();
+        if (warp == 0) {   // exclusive prefix of the chunks' counts
+            int run = 0;
+            for (int q0 = 0; q0 < GNCH; q0 += 32) {
+                const int c = __popc(G.chm[q0 + lane]);
+                int incl = c;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += v;
+                }
+                G.chp[q0 + lane] = run + incl - c;
+                run += __shfl_sync(0xffffffffu, incl, 31);
+            }
+            if (lane == 0) G.chp[GNCH] = run;
+        }
+        __syncthreads();
+        for (int u = 0; u < GCPW; ++u) {
+            const int q = warp + u * GNW;
+            const unsigned m = G.chm[q];
+            if (!((m >> lane) & 1u)) continue;
+            const int k = b0 + q * 32 + lane;
+            const int a = I.voff + k;
+            const int pos = cnt + G.chp[q] + __popc(m & ((1u << lane) - 1u));
+            if (pos >= EMAXG) continue;
             const int b = vnext[a];
             const double xa = PX[a], ya = PY[a], xb = PX[b], yb = PY[b];
             const double rx = xa != xb ? 1.0 / (xb - xa) : 0.0;
@@ -528,37 +579,46 @@ __device__ void gather_g(GeoBufG &G, const InstDesc &I, const double *__restrict
             G.mov[pos] = vmov[a];
             double elo, ehi;
             if (edge_yrange_s(xa, ya, xb, yb, sl, gxl, gxr, &elo, &ehi)) {
-                G.jlo[pos] = (short)(row_floor(I, elo) - 1);
-                G.jhi[pos] = (short)(row_floor(I, ehi) + 1);
+                G.jlo[pos] = (short)(row_floor_f(I, elo) - 1);
+                G.jhi[pos] = (short)(row_floor_f(I, ehi) + 1);
             } else {
                 G.jlo[pos] = 1;
                 G.jhi[pos] = 0;
             }
-            G.ilo[pos] = (short)(col_floor(I, lo - ad) - 1);
-            G.ihi[pos] = (short)(col_floor(I, hi + ad) + 1);
+            G.ilo[pos] = (short)(col_floor_f(I, lo - ad) - 1);
+            G.ihi[pos] = (short)(col_floor_f(I, hi + ad) + 1);
             // group columns whose closed x-range the edge may meet
-            const int c0 = col_floor(I, lo) - 1 - i0, c1 = col_floor(I, hi) + 1 - i0;
+            const int c0 = col_floor_f(I, lo) - 1 - i0, c1 = col_floor_f(I, hi) + 1 - i0;
             const int ca = c0 < 0 ? 0 : c0, cb = c1 > ncol - 1 ? ncol - 1 : c1;
-            np = cb >= ca ? cb - ca + 1 : 0;
+            const int np = cb >= ca ? cb - ca + 1 : 0;
             G.pc0[pos] = (unsigned char)(np ? ca : 0);
+            G.pp[pos] = np;
         }
-        int incl = np;
-        for (int o = 1; o < 32; o <<= 1) {
-            const int v = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += v;
+        cnt += G.chp[GNCH];
+        __syncthreads();
+    }
+    const int n = cnt < EMAXG ? cnt : EMAXG;
+    if (warp == 0) {   // pair counts -> exclusive prefix over the edges
+        int run = 0;
+        for (int e0 = 0; e0 < n; e0 += 32) {
+            const int e = e0 + lane;
+            const int c = e < n ? G.pp[e] : 0;
+            int incl = c;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            if (e < n) G.pp[e] = run + incl - c;
+            run += __shfl_sync(0xffffffffu, incl, 31);
         }
-        if (take && pos < EMAXG) G.pp[pos] = npair + incl - np;
-        npair += __shfl_sync(0xffffffffu, incl, 31);
-        cnt += __popc(m);
+        if (lane == 0) {
+            G.pp[n] = run;
+            G.npair = run;
+            G.cnt = n;
+            if (cnt > EMAXG) *err |= ERR_EDGE_CAP;
+        }
     }
-    if (cnt > EMAXG && lane == 0) *err |= ERR_EDGE_CAP;
-    if (lane == 0) {
-        const int n = cnt < EMAXG ? cnt : EMAXG;
-        G.cnt = n;
-        G.pp[n] = npair;
-        G.npair = npair;
-    }
-    __syncwarp();
+    __syncthreads();
 }
 
 // all threads, after gather_g: per column the bit list of the edges whose
@@ -608,7 +668,7 @@ __device__ void index_g(GeoBufG &G, const InstDesc &I, int i0, int ncol, int row
         const double xl = G.xln[c], xr = G.xln[c + 1];
         double elo, ehi;
         if (!edge_yrange_s(G.xa[e], G.ya[e], G.xb[e], G.yb[e], G.slope[e], xl, xr, &elo, &ehi)) continue;
-        const int jf0 = row_floor(I, elo), jf1 = row_floor(I, ehi);
+        const int jf0 = row_floor_f(I, elo), jf1 = row_floor_f(I, ehi);
         int jl = jf0 - 1, jh = jf1 + 1;
         if (jl < row0) jl = row0;
         if (jh > I.ny - 1) jh = I.ny - 1;
@@ -617,10 +677,7 @@ __device__ void index_g(GeoBufG &G, const InstDesc &I, int i0, int ncol, int row
             // rows jf0+1 .. jf1-1 lie strictly inside [elo, ehi] whatever the
             // rounding of the floors; the exact predicate decides the rest
             bool hit = j > jf0 && j < jf1;
-            if (!hit) {
-                const double ybj = node_coord(I.y0, j, I.dy), ytj = node_coord(I.y0, j + 1, I.dy);
-                hit = ehi >= ybj && elo <= ytj;
-            }
+            if (!hit) hit = ehi >= I.yn[j] && elo <= I.yn[j + 1];
             if (hit) atomicOr(&bits[c][(j - row0) >> 5], 1u << ((j - row0) & 31));
         }
     }
@@ -864,7 +921,8 @@ __device__ double swept_face_Bg(const GeoBufG &G, const InstDesc &I, int dir, do
     return clamp01(1.0 - A / ((y1 - y0) * I.dx));
 }
 
-__global__ void __launch_bounds__(GEOMG_THREADS) k_geom(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y,
+__global__ void __launch_bounds__(GEOMG_THREADS, 3) k_geom(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y,
+                                                            const int *__restrict__ ginst,
                                                          const double *__restrict__ px, const double *__restrict__ py,
                                                          const float *__restrict__ ebox,
                                                          const int *__restrict__ vnext,
@@ -878,11 +936,7 @@ __global__ void __launch_bounds__(GEOMG_THREADS) k_geom(const InstDesc *__restri
     __shared__ int sh_base;
     const int gw = blockIdx.x;
     if (gw >= total_groups) return;
-    int lo = 0, hi = n_inst - 1;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (D[mid].gcol_off <= gw) lo = mid; else hi = mid - 1;
-    }
+    const int lo = ginst[gw];
     const InstDesc &I = D[lo];
     InstDyn &y = Y[lo];
     const int i0 = y.col0 + GC * (gw - I.gcol_off);
@@ -912,13 +966,11 @@ __global__ void __launch_bounds__(GEOMG_THREADS) k_geom(const InstDesc *__restri
         if (I.cls[(row0 + jr) * I.pitch + i0 + c] & CLS_TOUCH) atomicOr(&W.bA[c][jr >> 5], 1u << (jr & 31));
     }
     if (I.rotating) {   // touched at the middle pose
-        if (warp == 0) gather_g(G, I, px, py, ebox, vnext, vmov, 1, total_v, i0, ncol, ad, lane, &err);
-        __syncthreads();
+        gather_g(G, I, px, py, ebox, vnext, vmov, 1, total_v, i0, ncol, ad, tid, &err);
         index_g(G, I, i0, ncol, row0, nwb, W.bM, tid);
         __syncthreads();
     }
-    if (warp == 0) gather_g(G, I, px, py, ebox, vnext, vmov, 2, total_v, i0, ncol, ad, lane, &err);
-    __syncthreads();
+    gather_g(G, I, px, py, ebox, vnext, vmov, 2, total_v, i0, ncol, ad, tid, &err);
     index_g(G, I, i0, ncol, row0, nwb, W.bB, tid);
     __syncthreads();
     if (warp == 1) compact_lines_g(G, ncol, lane, &err);
@@ -972,7 +1024,7 @@ __global__ void __launch_bounds__(GEOMG_THREADS) k_geom(const InstDesc *__restri
         const int i = i0 + c;
         BandRec &r = R[I.rec_base + base + t];
         const double xl = G.xln[c], xr = G.xln[c + 1];
-        const double yb = node_coord(I.y0, j, I.dy), yt = node_coord(I.y0, j + 1, I.dy);
+        const double yb = I.yn[j], yt = I.yn[j + 1];
         const bool tA = (W.bA[c][k] >> bit) & 1u, tB = (W.bB[c][k] >> bit) & 1u, tM = (W.bM[c][k] >> bit) & 1u;
         const int cell = j * I.pitch + i;
         r.cell = cell;
@@ -1000,8 +1052,7 @@ __global__ void __launch_bounds__(GEOMG_THREADS) k_geom(const InstDesc *__restri
     }
     // pass M
     __syncthreads();
-    if (warp == 0) gather_g(G, I, px, py, ebox, vnext, vmov, 1, total_v, i0, ncol, ad, lane, &err);
-    __syncthreads();
+    gather_g(G, I, px, py, ebox, vnext, vmov, 1, total_v, i0, ncol, ad, tid, &err);
     index_g(G, I, i0, ncol, row0, nwb, nullptr, tid);
     __syncthreads();
     if (warp == 1) compact_lines_g(G, ncol, lane, &err);
@@ -1013,7 +1064,7 @@ __global__ void __launch_bounds__(GEOMG_THREADS) k_geom(const InstDesc *__restri
         const int ri = I.rec_base + base + t;
         BandRec &r = R[ri];
         const double xl = G.xln[c], xr = G.xln[c + 1];
-        const double yb = node_coord(I.y0, j, I.dy), yt = node_coord(I.y0, j + 1, I.dy);
+        const double yb = I.yn[j], yt = I.yn[j + 1];
         bool mov = false;
         double nlx = 0.0, nly = 0.0;
         const double aM = cell_alpha_g(G, I, c, i, j, xl, xr, yb, yt, &nlx, &nly, &mov);
@@ -1054,8 +1105,7 @@ __global__ void __launch_bounds__(GEOMG_THREADS) k_geom(const InstDesc *__restri
     }
     if (I.rotating) {
         __syncthreads();
-        if (warp == 0) gather_g(G, I, px, py, ebox, vnext, vmov, 0, total_v, i0, ncol, ad, lane, &err);
-        __syncthreads();
+        gather_g(G, I, px, py, ebox, vnext, vmov, 0, total_v, i0, ncol, ad, tid, &err);
         index_g(G, I, i0, ncol, row0, nwb, nullptr, tid);
         __syncthreads();
         if (warp == 1) compact_lines_g(G, ncol, lane, &err);
@@ -1066,7 +1116,7 @@ __global__ void __launch_bounds__(GEOMG_THREADS) k_geom(const InstDesc *__restri
             const int i = i0 + c;
             const int ri = I.rec_base + base + t;
             const double xl = G.xln[c], xr = G.xln[c + 1];
-            const double yb = node_coord(I.y0, j, I.dy), yt = node_coord(I.y0, j + 1, I.dy);
+            const double yb = I.yn[j], yt = I.yn[j + 1];
             R[ri].bown += wsimp_A * face_ap_g(G, I, dir, true, c, i, j, xl, xr, yb, yt);
             const bool need_bnd = dir == 0 ? (i == 0 && I.bc[0] != 2) : (j == 0 && I.bc[2] != 2);
             if (need_bnd) bnd[ri] += wsimp_A * face_ap_g(G, I, dir, false, c, i, j, xl, xr, yb, yt);
@@ -1155,6 +1205,14 @@ __global__ void k_pose_current(const InstDesc *__restrict__ D, const InstDyn *__
     }
 }
 
+// grid-line coordinates of every instance (one block per instance)
+__global__ void k_nodes(const InstDesc *__restrict__ D) {
+    const InstDesc &I = D[blockIdx.x];
+    double *xn = const_cast<double *>(I.xn), *yn = const_cast<double *>(I.yn);
+    for (int i = threadIdx.x; i <= I.nx; i += blockDim.x) xn[i] = node_coord(I.x0, i, I.dx);
+    for (int j = threadIdx.x; j <= I.ny; j += blockDim.x) yn[j] = node_coord(I.y0, j, I.dy);
+}
+
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
@@ -1166,18 +1224,22 @@ void geom_init() {
     cudaFuncSetAttribute(k_classify, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)geom_smem());
 }
 
+void launch_nodes(const InstDesc *D, int n_inst, cudaStream_t st) {
+    if (n_inst > 0) k_nodes<<<n_inst, 256, 0, st>>>(D);
+}
+
 void launch_pose(const InstDesc *D, InstDyn *Y, const double *vx, const double *vy, const unsigned char *vmov,
                  const int *vnext, double *px, double *py, float *ebox, int total_v, int n_inst, int dir, int sidx,
                  double dt, cudaStream_t st) {
     k_pose<<<n_inst, 256, 0, st>>>(D, Y, vx, vy, vmov, vnext, px, py, ebox, total_v, dir, sidx, dt);
 }
 
-void launch_geom(const InstDesc *D, InstDyn *Y, const double *px, const double *py, const float *ebox,
+void launch_geom(const InstDesc *D, InstDyn *Y, const int *ginst, const double *px, const double *py, const float *ebox,
                  const int *vnext, const unsigned char *vmov, int total_v, int n_inst, int total_groups, int dir,
                  BandRec *R, double *bnd, cudaStream_t st) {
     int blocks = total_groups;
     if (blocks > 0)
-        k_geom<<<blocks, GEOMG_THREADS, geomg_smem(), st>>>(D, Y, px, py, ebox, vnext, vmov, total_v, n_inst,
+        k_geom<<<blocks, GEOMG_THREADS, geomg_smem(), st>>>(D, Y, ginst, px, py, ebox, vnext, vmov, total_v, n_inst,
                                                              total_groups, dir, R, bnd);
 }
 

@@ -57,6 +57,8 @@ struct InstDesc {
     int nx, ny, pitch, nc;
     double x0, y0, dx, dy;
     double rdx, rdy;            // 1/dx, 1/dy (candidate row and column ranges only)
+    float rdxf, rdyf;           // the same in FP32
+    const double *xn, *yn;      // grid-line coordinates x_0..x_nx, y_0..y_ny (device)
     int bc[4];
     int eq;
     int ucov;
