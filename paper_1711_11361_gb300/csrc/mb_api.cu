@@ -255,7 +255,9 @@ mb_status mb_batch_create(int n, const mb_grid *grids, const double *gammas, con
         // columns and 64-row segment
         I.tiles_x[0] = 1;
         I.ntiles[0] = g.ny;
-        I.tiles_x[1] = (g.nx + 31) / 32;
+        // y sweep: 32 columns per warp
+        const int ycols = 32;
+        I.tiles_x[1] = (g.nx + ycols - 1) / ycols;
         I.ntiles[1] = I.tiles_x[1] * ((g.ny + 63) / 64);
         I.tile_off[0] = tiles0;
         I.tile_off[1] = tiles1;

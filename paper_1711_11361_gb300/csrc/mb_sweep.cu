@@ -612,6 +612,476 @@ __global__ void __launch_bounds__(256, 3) k_bulk_y(const InstDesc *__restrict__ 
     finish_warp<T>(y, last != 0, s0, s1, bad);
 }
 
+// ---------------------------------------------------------------------------
+// packed FP32 Euler bulk kernels.  Every thread carries two cells (x sweep:
+// two neighbours along the row; y sweep: two neighbouring columns) and runs
+// the MUSCL-Hancock + HLLC arithmetic of both on FP32x2 instructions, the .x
+// half for the first cell and the .y half for the second.  Same scheme and
+// face ownership as the scalar kernels above; HLLC is written without
+// branches (one physical flux is evaluated, then the case is selected).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 P2(float s) { return make_float2(s, s); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 rcp2(float2 a) { return make_float2(__fdividef(1.0f, a.x), __fdividef(1.0f, a.y)); }
+__device__ __forceinline__ float2 sqrt2(float2 a) { return make_float2(sqrtf(a.x), sqrtf(a.y)); }
+__device__ __forceinline__ float2 min2(float2 a, float2 b) { return make_float2(fminf(a.x, b.x), fminf(a.y, b.y)); }
+__device__ __forceinline__ float2 max2(float2 a, float2 b) { return make_float2(fmaxf(a.x, b.x), fmaxf(a.y, b.y)); }
+__device__ __forceinline__ float2 sel2(bool cx, bool cy, float2 a, float2 b) {
+    return make_float2(cx ? a.x : b.x, cy ? a.y : b.y);
+}
+
+// a pair of conserved states with 1/rho and p of each
+struct S2 {
+    float2 q[4];
+};
+struct E2 {
+    float2 q[4];
+    float2 ir, p;
+};
+
+__device__ __forceinline__ void prim2(float g1, const float2 *q, float2 &ir, float2 &p) {
+    ir = rcp2(q[0]);
+    const float2 ke = fma2(q[1], q[1], mul2(q[2], q[2]));
+    p = mul2(P2(g1), fma2(mul2(P2(-0.5f), ke), ir, q[3]));
+}
+
+// physical flux along D of states q with normal velocity un and pressure p
+template <int D>
+__device__ __forceinline__ void flux2(const float2 *q, float2 un, float2 p, float2 *f) {
+    f[0] = mul2(q[0], un);
+    f[1] = D == 0 ? fma2(q[1], un, p) : mul2(q[1], un);
+    f[2] = D == 1 ? fma2(q[2], un, p) : mul2(q[2], un);
+    f[3] = mul2(un, add2(q[3], p));
+}
+
+__device__ __forceinline__ float2 vanleer2(float2 dm, float2 dp) {
+    const float2 pr = mul2(dm, dp);
+    const float2 r = mul2(add2(pr, pr), rcp2(add2(dm, dp)));
+    return sel2(pr.x > 0.0f, pr.y > 0.0f, r, P2(0.0f));
+}
+
+// MUSCL-Hancock boundary states of the two cells (as evolve(): van Leer
+// slopes, zero slope when lim is false, first order if an evolved state is
+// not physical); also returns 1/rho and p of the evolved states
+template <int D>
+__device__ __forceinline__ void evolve2(float g1, float lam, const float2 *qm, const float2 *q0, const float2 *qp,
+                                        bool limx, bool limy, E2 &QL, E2 &QR) {
+    constexpr int in = D == 0 ? 1 : 2;
+    float2 qL[4], qR[4], fL[4], fR[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        float2 sl = vanleer2(sub2(q0[k], qm[k]), sub2(qp[k], q0[k]));
+        sl = sel2(limx, limy, sl, P2(0.0f));
+        qL[k] = fma2(P2(-0.5f), sl, q0[k]);
+        qR[k] = fma2(P2(0.5f), sl, q0[k]);
+    }
+    float2 ir, p;
+    prim2(g1, qL, ir, p);
+    flux2<D>(qL, mul2(qL[in], ir), p, fL);
+    prim2(g1, qR, ir, p);
+    flux2<D>(qR, mul2(qR[in], ir), p, fR);
+    const float2 hl = P2(0.5f * lam);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float2 dfl = mul2(hl, sub2(fL[k], fR[k]));
+        QL.q[k] = add2(qL[k], dfl);
+        QR.q[k] = add2(qR[k], dfl);
+    }
+    prim2(g1, QL.q, QL.ir, QL.p);
+    prim2(g1, QR.q, QR.ir, QR.p);
+    const bool okx = QL.q[0].x > 0.0f && QR.q[0].x > 0.0f && QL.p.x > 0.0f && QR.p.x > 0.0f;
+    const bool oky = QL.q[0].y > 0.0f && QR.q[0].y > 0.0f && QL.p.y > 0.0f && QR.p.y > 0.0f;
+    if (!(okx && oky)) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            QL.q[k] = sel2(okx, oky, QL.q[k], q0[k]);
+            QR.q[k] = sel2(okx, oky, QR.q[k], q0[k]);
+        }
+        prim2(g1, QL.q, QL.ir, QL.p);
+        prim2(g1, QR.q, QR.ir, QR.p);
+    }
+}
+
+// HLLC (Davis wave speeds) for two faces: left states L, right states R
+template <int D>
+__device__ __forceinline__ void hllc2(float g, const E2 &L, const E2 &R, float2 *F) {
+    constexpr int in = D == 0 ? 1 : 2, it = 3 - in;
+    const float2 uL = mul2(L.q[in], L.ir), uR = mul2(R.q[in], R.ir);
+    const float2 cL = sqrt2(mul2(mul2(P2(g), L.p), L.ir)), cR = sqrt2(mul2(mul2(P2(g), R.p), R.ir));
+    const float2 SL = min2(sub2(uL, cL), sub2(uR, cR)), SR = max2(add2(uL, cL), add2(uR, cR));
+    const float2 aL = mul2(L.q[0], sub2(SL, uL)), aR = mul2(R.q[0], sub2(SR, uR));
+    const float2 num = add2(sub2(R.p, L.p), sub2(mul2(aL, uL), mul2(aR, uR)));
+    const float2 Ss = mul2(num, rcp2(sub2(aL, aR)));
+    // side whose flux is used: L when supersonic to the right or Ss >= 0
+    const bool kx = SL.x >= 0.0f || (SR.x > 0.0f && Ss.x >= 0.0f);
+    const bool ky = SL.y >= 0.0f || (SR.y > 0.0f && Ss.y >= 0.0f);
+    float2 q[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) q[k] = sel2(kx, ky, L.q[k], R.q[k]);
+    const float2 iv = sel2(kx, ky, L.ir, R.ir), u = sel2(kx, ky, uL, uR), p = sel2(kx, ky, L.p, R.p);
+    const float2 S = sel2(kx, ky, SL, SR), a = sel2(kx, ky, aL, aR);
+    float2 f[4];
+    flux2<D>(q, u, p, f);
+    const float2 fac = mul2(a, rcp2(sub2(S, Ss)));
+    float2 qs[4];
+    qs[0] = fac;
+    qs[in] = mul2(fac, Ss);
+    qs[it] = mul2(fac, mul2(q[it], iv));
+    qs[3] = mul2(fac, fma2(sub2(Ss, u), fma2(p, rcp2(a), Ss), mul2(q[3], iv)));
+    const bool sx = SL.x >= 0.0f || SR.x <= 0.0f, sy = SL.y >= 0.0f || SR.y <= 0.0f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) F[k] = sel2(sx, sy, f[k], fma2(S, sub2(qs[k], q[k]), f[k]));
+}
+
+// flux of one face (half h of F) replaced by the band record value or zero
+template <int DIR>
+__device__ __forceinline__ void face_override(const InstDesc &I, const BandRec *__restrict__ R, int line, int a,
+                                              int n, uint8_t cl, uint8_t cr, float2 *F, int h) {
+    if (!((cl | cr) & (CLS_BAND | CLS_SOLID))) return;
+    float v[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    if ((cl | cr) & CLS_BAND) {
+        bool fl;
+        const int bclo = I.bc[2 * DIR], bchi = I.bc[2 * DIR + 1];
+        const int pb = ghost_map(a, n, bclo, bchi, &fl), pa = ghost_map(a - 1, n, bclo, bchi, &fl);
+        const int cib = DIR == 0 ? line * I.pitch + pb : pb * I.pitch + line;
+        const int cia = DIR == 0 ? line * I.pitch + pa : pa * I.pitch + line;
+        const bool b_real = a < n || bchi == 2;
+        const bool a_real = a - 1 >= 0 || bclo == 2;
+        if ((cr & CLS_BAND) && (b_real || !a_real || !(cl & CLS_BAND))) {
+            const BandRec &rb = R[I.rec[cib]];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) v[k] = (float)rb.Flo[k];
+        } else {
+            const BandRec &ra = R[I.rec[cia]];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) v[k] = (float)ra.Fhi[k];
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (h == 0) F[k].x = v[k];
+        else F[k].y = v[k];
+    }
+}
+
+// new states of the two cells (q, fluxes Flo / Fhi through their low / high
+// faces); stores the cells flagged in st (bit 0: first, bit 1: second);
+// wave speeds and positivity for the CFL step
+__device__ __forceinline__ void update2(float *__restrict__ Qo, size_t plane, int ci, int st, bool vec, float g1,
+                                        float g, float lam, const float2 *q, const float2 *Flo, const float2 *Fhi,
+                                        bool last, float &s0, float &s1, int &bad) {
+    float2 qn[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) qn[k] = fma2(P2(lam), sub2(Flo[k], Fhi[k]), q[k]);
+    if (vec) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) *(float2 *)(Qo + k * plane + ci) = qn[k];
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (st & 1) Qo[k * plane + ci] = qn[k].x;
+            if (st & 2) Qo[k * plane + ci + 1] = qn[k].y;
+        }
+    }
+    float2 ir, p;
+    prim2(g1, qn, ir, p);
+    if (((st & 1) && !(qn[0].x > 0.0f && p.x > 0.0f)) || ((st & 2) && !(qn[0].y > 0.0f && p.y > 0.0f))) bad = 1;
+    if (last) {
+        const float2 c = sqrt2(mul2(mul2(P2(g), p), ir));
+        const float2 w0 = add2(make_float2(fabsf(qn[1].x * ir.x), fabsf(qn[1].y * ir.y)), c);
+        const float2 w1 = add2(make_float2(fabsf(qn[2].x * ir.x), fabsf(qn[2].y * ir.y)), c);
+        if (st & 1) { s0 = fmaxf(s0, w0.x); s1 = fmaxf(s1, w1.x); }
+        if (st & 2) { s0 = fmaxf(s0, w0.y); s1 = fmaxf(s1, w1.y); }
+    }
+}
+
+__device__ __forceinline__ void shfl_up4(float2 *o, const float2 *v, int comp) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) o[k].x = __shfl_up_sync(0xffffffffu, comp ? v[k].y : v[k].x, 1);
+}
+
+// x sweep, packed: one warp per row, lane l holds cells 64c + 2l and
+// 64c + 2l + 1 of chunk c; the update trails the fluxes by one chunk
+__global__ void __launch_bounds__(256) k_bulk_x_p(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y,
+                                                  const BandRec *__restrict__ R, int n_inst, int total_warps, int src,
+                                                  int dst, int last) {
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (gw >= total_warps) return;
+    const int inst = find_inst_warp(D, n_inst, gw, 0);
+    const InstDesc &I = D[inst];
+    InstDyn &y = Y[inst];
+    const int j = gw - I.tile_off[0];
+    const int n = I.nx;
+    const float lam = y.lamf;
+    const float g = (float)I.gamma, g1 = g - 1.0f;
+    const size_t plane = (size_t)I.pitch * I.ny;
+    const float *__restrict__ Q = (const float *)I.Q[src];
+    float *__restrict__ Qo = (float *)I.Q[dst];
+    const int rowb = j * I.pitch;
+    const int bclo = I.bc[0], bchi = I.bc[1];
+    // the pair of chunk c (classes packed as first | second << 8)
+    auto load = [&](int c, S2 &v, int &cls) {
+        const int a = 64 * c + 2 * lane;
+        if (a >= 0 && a + 1 < n) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) v.q[k] = __ldg((const float2 *)(Q + k * plane + rowb + a));
+            cls = __ldg((const unsigned short *)(I.cls + rowb + a));
+            return;
+        }
+        cls = 0;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int b = a + h;
+            float w[4];
+            int cb;
+            if (b < -2 || b > n + 1) {
+                w[0] = w[1] = w[2] = w[3] = 1.0f;
+                cb = CLS_SOLID;
+            } else {
+                bool fl;
+                const int pidx = ghost_map(b, n, bclo, bchi, &fl);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) w[k] = __ldg(Q + k * plane + rowb + pidx);
+                if (fl) w[1] = -w[1];
+                cb = I.cls[rowb + pidx];
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (h == 0) v.q[k].x = w[k];
+                else v.q[k].y = w[k];
+            }
+            cls |= cb << (8 * h);
+        }
+    };
+    const int c_last = (n + 1) >> 6;   // chunk holding face n
+    S2 Qm, Q0, Qp;
+    int cm, c0, cp;
+    load(-1, Qm, cm);
+    load(0, Q0, c0);
+    load(1, Qp, cp);
+    // evolved right state of cell -1 (second cell of lane 31, chunk -1)
+    E2 QRc;
+    {
+        float2 qm[4], qp[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float up = __shfl_up_sync(0xffffffffu, Qm.q[k].y, 1);
+            const float dn = __shfl_down_sync(0xffffffffu, Qm.q[k].x, 1);
+            const float nx0 = __shfl_sync(0xffffffffu, Q0.q[k].x, 0);
+            qm[k] = make_float2(up, Qm.q[k].x);
+            qp[k] = make_float2(Qm.q[k].y, lane == 31 ? nx0 : dn);
+        }
+        const int cu = __shfl_up_sync(0xffffffffu, cm, 1), cd0 = __shfl_down_sync(0xffffffffu, cm, 1);
+        const int cn = __shfl_sync(0xffffffffu, c0, 0);
+        const int cd = lane == 31 ? cn : cd0;
+        const bool lx = !((cu >> 8) & CLS_SOLID) && !((cm >> 8) & CLS_SOLID);
+        const bool ly = !(cm & CLS_SOLID) && !(cd & CLS_SOLID);
+        E2 QL, QR;
+        evolve2<0>(g1, lam, qm, Qm.q, qp, lx, ly, QL, QR);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) QRc.q[k].x = __shfl_sync(0xffffffffu, QR.q[k].y, 31);
+        QRc.ir.x = __shfl_sync(0xffffffffu, QR.ir.y, 31);
+        QRc.p.x = __shfl_sync(0xffffffffu, QR.p.y, 31);
+    }
+    float s0 = 0.0f, s1 = 0.0f;
+    int bad = 0;
+    float2 Fprev[4];
+    for (int c = 0; c <= c_last; ++c) {
+        const int a = 64 * c + 2 * lane;
+        // neighbours: the cell before the pair and the cell after it
+        float2 qm[4], qp[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float up = __shfl_up_sync(0xffffffffu, Q0.q[k].y, 1);
+            const float pv = __shfl_sync(0xffffffffu, Qm.q[k].y, 31);
+            const float dn = __shfl_down_sync(0xffffffffu, Q0.q[k].x, 1);
+            const float nx0 = __shfl_sync(0xffffffffu, Qp.q[k].x, 0);
+            qm[k] = make_float2(lane == 0 ? pv : up, Q0.q[k].x);
+            qp[k] = make_float2(Q0.q[k].y, lane == 31 ? nx0 : dn);
+        }
+        const int cu0 = __shfl_up_sync(0xffffffffu, c0, 1), cpv = __shfl_sync(0xffffffffu, cm, 31);
+        const int cd0 = __shfl_down_sync(0xffffffffu, c0, 1), cnx = __shfl_sync(0xffffffffu, cp, 0);
+        const int cu = lane == 0 ? cpv : cu0, cd = lane == 31 ? cnx : cd0;
+        const int clA = (cu >> 8) & 0xff, cA = c0 & 0xff, cB = (c0 >> 8) & 0xff, crB = cd & 0xff;
+        const bool lx = !(clA & CLS_SOLID) && !(cB & CLS_SOLID);
+        const bool ly = !(cA & CLS_SOLID) && !(crB & CLS_SOLID);
+        E2 QL, QR;
+        evolve2<0>(g1, lam, qm, Q0.q, qp, lx, ly, QL, QR);
+        // faces a (cells a-1 | a) and a+1 (cells a | a+1)
+        E2 Lf;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float up = __shfl_up_sync(0xffffffffu, QR.q[k].y, 1);
+            Lf.q[k] = make_float2(lane == 0 ? QRc.q[k].x : up, QR.q[k].x);
+        }
+        {
+            const float ui = __shfl_up_sync(0xffffffffu, QR.ir.y, 1), up = __shfl_up_sync(0xffffffffu, QR.p.y, 1);
+            Lf.ir = make_float2(lane == 0 ? QRc.ir.x : ui, QR.ir.x);
+            Lf.p = make_float2(lane == 0 ? QRc.p.x : up, QR.p.x);
+        }
+        float2 F[4];
+        hllc2<0>(g, Lf, QL, F);
+        if (a <= n) face_override<0>(I, R, j, a, n, (uint8_t)clA, (uint8_t)cA, F, 0);
+        if (a + 1 <= n) face_override<0>(I, R, j, a + 1, n, (uint8_t)cA, (uint8_t)cB, F, 1);
+        // update of chunk c-1: high faces are the second half of Fprev and
+        // the first half of the next lane's (lane 31: this chunk's lane 0)
+        if (c >= 1) {
+            float2 Fhi[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float dn = __shfl_down_sync(0xffffffffu, Fprev[k].x, 1);
+                const float nx0 = __shfl_sync(0xffffffffu, F[k].x, 0);
+                Fhi[k] = make_float2(Fprev[k].y, lane == 31 ? nx0 : dn);
+            }
+            const int ap = a - 64;
+            int st = 0;
+            if (ap < n && !((cm & 0xff) & (CLS_BAND | CLS_SOLID))) st |= 1;
+            if (ap + 1 < n && !(((cm >> 8) & 0xff) & (CLS_BAND | CLS_SOLID))) st |= 2;
+            if (st) update2(Qo, plane, rowb + ap, st, st == 3, g1, g, lam, Qm.q, Fprev, Fhi, last, s0, s1, bad);
+            if ((cm & CLS_SOLID) && ap < n) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) Qo[k * plane + rowb + ap] = NAN;
+            }
+            if (((cm >> 8) & CLS_SOLID) && ap + 1 < n) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) Qo[k * plane + rowb + ap + 1] = NAN;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) QRc.q[k].x = __shfl_sync(0xffffffffu, QR.q[k].y, 31);
+        QRc.ir.x = __shfl_sync(0xffffffffu, QR.ir.y, 31);
+        QRc.p.x = __shfl_sync(0xffffffffu, QR.p.y, 31);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) Fprev[k] = F[k];
+        Qm = Q0; cm = c0;
+        Q0 = Qp; c0 = cp;
+        load(c + 2, Qp, cp);
+    }
+    // the last chunk (its high faces were computed in the final iteration,
+    // except the one past lane 31 which lies beyond face n)
+    {
+        float2 Fhi[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float dn = __shfl_down_sync(0xffffffffu, Fprev[k].x, 1);
+            Fhi[k] = make_float2(Fprev[k].y, dn);
+        }
+        const int ap = 64 * c_last + 2 * lane;
+        int st = 0;
+        if (ap < n && !((cm & 0xff) & (CLS_BAND | CLS_SOLID))) st |= 1;
+        if (ap + 1 < n && lane < 31 && !(((cm >> 8) & 0xff) & (CLS_BAND | CLS_SOLID))) st |= 2;
+        if (st) update2(Qo, plane, rowb + ap, st, st == 3, g1, g, lam, Qm.q, Fprev, Fhi, last, s0, s1, bad);
+        if ((cm & CLS_SOLID) && ap < n) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) Qo[k * plane + rowb + ap] = NAN;
+        }
+        if (((cm >> 8) & CLS_SOLID) && ap + 1 < n && lane < 31) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) Qo[k * plane + rowb + ap + 1] = NAN;
+        }
+    }
+    finish_warp<float>(y, last != 0, s0, s1, bad);
+}
+
+// y sweep, packed: one thread per pair of neighbouring columns and segment of
+// YSEG rows, marching upward with a register window; a warp covers 64
+// consecutive columns
+constexpr int YCOLS_P = 64;
+__global__ void __launch_bounds__(256) k_bulk_y_p(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y,
+                                                  const BandRec *__restrict__ R, int n_inst, int total_warps, int src,
+                                                  int dst, int last) {
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (gw >= total_warps) return;
+    const int inst = find_inst_warp(D, n_inst, gw, 1);
+    const InstDesc &I = D[inst];
+    InstDyn &y = Y[inst];
+    const int local = gw - I.tile_off[1];
+    const int ncg = I.tiles_x[1];
+    const int cg = local % ncg, sg = local / ncg;
+    const int i_raw = cg * YCOLS_P + 2 * lane;
+    // columns i, i+1 (a pair past the last column repeats column nx-1)
+    const int st0 = (i_raw < I.nx ? 1 : 0) | (i_raw + 1 < I.nx ? 2 : 0);
+    const int i = i_raw < I.nx ? i_raw : I.nx - 1;
+    const bool pair_ok = st0 == 3;
+    const int n = I.ny;
+    const int j0 = sg * YSEG, j1 = min(n, j0 + YSEG);
+    const float lam = y.lamf;
+    const float g = (float)I.gamma, g1 = g - 1.0f;
+    const size_t plane = (size_t)I.pitch * I.ny;
+    const float *__restrict__ Q = (const float *)I.Q[src];
+    float *__restrict__ Qo = (float *)I.Q[dst];
+    const int bclo = I.bc[2], bchi = I.bc[3];
+    auto load = [&](int r, S2 &v, int &cls) {
+        bool fl;
+        const int p = ghost_map(r, n, bclo, bchi, &fl);
+        const int ci = p * I.pitch + i;
+        if (pair_ok) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) v.q[k] = __ldg((const float2 *)(Q + k * plane + ci));
+            cls = __ldg((const unsigned short *)(I.cls + ci));
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) v.q[k] = P2(__ldg(Q + k * plane + ci));
+            const int cc = I.cls[ci];
+            cls = cc | cc << 8;
+        }
+        if (fl) {
+            v.q[2].x = -v.q[2].x;
+            v.q[2].y = -v.q[2].y;
+        }
+    };
+    S2 qa, qm, qc, qp, qq;
+    int ca, cm, cc, cp, cq;
+    load(j0 - 2, qa, ca);
+    load(j0 - 1, qm, cm);
+    load(j0, qc, cc);
+    load(j0 + 1, qp, cp);
+    load(j0 + 2, qq, cq);
+    E2 QL, QR, QRc;
+    evolve2<1>(g1, lam, qa.q, qm.q, qc.q, !(ca & CLS_SOLID) && !(cc & CLS_SOLID),
+               !((ca >> 8) & CLS_SOLID) && !((cc >> 8) & CLS_SOLID), QL, QRc);
+    float s0 = 0.0f, s1 = 0.0f;
+    int bad = 0;
+    float2 Fprev[4];
+    for (int f = j0; f <= j1; ++f) {
+        // window: qm = row f-1, qc = row f, qp = row f+1, qq = row f+2
+        evolve2<1>(g1, lam, qm.q, qc.q, qp.q, !(cm & CLS_SOLID) && !(cp & CLS_SOLID),
+                   !((cm >> 8) & CLS_SOLID) && !((cp >> 8) & CLS_SOLID), QL, QR);
+        float2 F[4];
+        hllc2<1>(g, QRc, QL, F);
+        face_override<1>(I, R, i, f, n, (uint8_t)(cm & 0xff), (uint8_t)(cc & 0xff), F, 0);
+        if (pair_ok) face_override<1>(I, R, i + 1, f, n, (uint8_t)(cm >> 8), (uint8_t)(cc >> 8), F, 1);
+        if (f > j0) {
+            int st = 0;
+            if ((st0 & 1) && !((cm & 0xff) & (CLS_BAND | CLS_SOLID))) st |= 1;
+            if ((st0 & 2) && !(((cm >> 8) & 0xff) & (CLS_BAND | CLS_SOLID))) st |= 2;
+            const int ci = (f - 1) * I.pitch + i;
+            if (st) update2(Qo, plane, ci, st, st == 3, g1, g, lam, qm.q, Fprev, F, last, s0, s1, bad);
+            if ((st0 & 1) && (cm & CLS_SOLID)) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) Qo[k * plane + ci] = NAN;
+            }
+            if ((st0 & 2) && ((cm >> 8) & CLS_SOLID)) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) Qo[k * plane + ci + 1] = NAN;
+            }
+        }
+        QRc = QR;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) Fprev[k] = F[k];
+        qm = qc; cm = cc;
+        qc = qp; cc = cp;
+        qp = qq; cp = cq;
+        if (f + 3 <= j1 + 1) load(f + 3, qq, cq);
+    }
+    finish_warp<float>(y, last != 0, s0, s1, bad);
+}
+
 template <class T, int EQ>
 void bulk_attr_t(int dir) {
     if (dir == 0) cudaFuncSetAttribute(k_bulk_x<T, EQ>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
@@ -900,8 +1370,10 @@ void launch_bulk(int dir, int eq, const InstDesc *D, InstDyn *Y, const BandRec *
                  int src, int dst, int last, cudaStream_t st) {
     int blocks = (total_warps + 7) / 8;
     if (blocks <= 0) return;
+    const bool packed = sizeof(T) == 4 && eq == 0;   // FP32 Euler x sweep: the FP32x2 kernel
     if (dir == 0) {
-        if (eq == 0) k_bulk_x<T, 0><<<blocks, 256, 0, st>>>(D, Y, R, n_inst, total_warps, src, dst, last);
+        if (packed) k_bulk_x_p<<<blocks, 256, 0, st>>>(D, Y, R, n_inst, total_warps, src, dst, last);
+        else if (eq == 0) k_bulk_x<T, 0><<<blocks, 256, 0, st>>>(D, Y, R, n_inst, total_warps, src, dst, last);
         else k_bulk_x<T, 1><<<blocks, 256, 0, st>>>(D, Y, R, n_inst, total_warps, src, dst, last);
     } else {
         if (eq == 0) k_bulk_y<T, 0><<<blocks, 256, 0, st>>>(D, Y, R, n_inst, total_warps, src, dst, last);
