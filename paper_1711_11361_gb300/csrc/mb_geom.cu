@@ -108,6 +108,7 @@ __global__ void k_pose(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y, 
         y.band_count = 0;
         y.nbad = 0;
         y.nbadlist = 0;
+        y.nbulk = 0;
         y.mixed = 0;
         for (int q = 0; q < MAXC; ++q) y.wall_sum[q] = 0.0;
         sh[0] = y.XA; sh[1] = y.YA; sh[2] = y.XM; sh[3] = y.YM; sh[4] = y.XB; sh[5] = y.YB;

@@ -7,6 +7,7 @@
 namespace mb {
 
 constexpr int MAXC = 4;
+constexpr int NBULK = 32;              // non-physical bulk cells listed per sweep
 constexpr int GEO_GC = 16;            // grid columns per geometry group (one CTA each)
 constexpr double ALPHA_MIN = 1e-10;   // smaller volume fractions count as solid
 
@@ -102,6 +103,8 @@ struct InstDyn {
     int mixed;
     int nbadlist;
     int badlist[16];            // first records flagged by the positivity check
+    int nbulk;                  // non-band cells found non-physical by the bulk update
+    int bulkbad[NBULK];         // their cell indices (first NBULK)
     double wall_sum[MAXC];
 };
 

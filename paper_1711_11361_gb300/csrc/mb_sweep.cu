@@ -381,11 +381,18 @@ __device__ __forceinline__ void face_flux(const InstDesc &I, const BandRec *__re
     riemann_flux(EQ, g, DIR, av0, av1, QRl.q, QLr.q, F.q);
 }
 
+// a non-band cell whose updated state is not physical: listed for the
+// positivity safeguard (k_mix)
+__device__ __forceinline__ void list_bulk_bad(InstDyn &y, int cell) {
+    const int k = atomicAdd(&y.nbulk, 1);
+    if (k < NBULK) y.bulkbad[k] = cell;
+}
+
 // new state of a non-band cell; wave speeds and positivity for the CFL step
 template <class T, int NC, int EQ>
 __device__ __forceinline__ void update_cell(T *__restrict__ Qo, size_t plane, int ci, uint8_t c0, T lam, T g, T av0,
                                             T av1, const QV<T, NC> &q, const QV<T, NC> &Flo, const QV<T, NC> &Fhi,
-                                            bool last, T &s0, T &s1, int &bad) {
+                                            bool last, T &s0, T &s1, InstDyn &y) {
     if (c0 & CLS_BAND) return;
     if (c0 & CLS_SOLID) {
 #pragma unroll
@@ -401,7 +408,7 @@ __device__ __forceinline__ void update_cell(T *__restrict__ Qo, size_t plane, in
     if (EQ == 0) {
         T ir = fdiv(T(1), qn[0]);
         T p = (g - T(1)) * (qn[NC - 1] - T(0.5) * (qn[1 % NC] * qn[1 % NC] + qn[2 % NC] * qn[2 % NC]) * ir);
-        if (!(qn[0] > T(0)) || !(p > T(0))) bad = 1;
+        if (!(qn[0] > T(0)) || !(p > T(0))) list_bulk_bad(y, ci);
         if (last) {
             T c = tsqrt(g * p * ir);
             s0 = fmax(s0, fabs(qn[1 % NC] * ir) + c);
@@ -414,8 +421,7 @@ __device__ __forceinline__ void update_cell(T *__restrict__ Qo, size_t plane, in
 }
 
 template <class T>
-__device__ __forceinline__ void finish_warp(InstDyn &y, bool last, T s0, T s1, int bad) {
-    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&y.err, ERR_UNSTABLE);
+__device__ __forceinline__ void finish_warp(InstDyn &y, bool last, T s0, T s1) {
     if (last) {
         for (int o = 16; o > 0; o >>= 1) {
             s0 = fmax(s0, __shfl_xor_sync(0xffffffffu, s0, o));
@@ -497,7 +503,6 @@ __global__ void __launch_bounds__(256) k_bulk_x(const InstDesc *__restrict__ D, 
     shfl_idx(QRc, QR, 31);
     int cRc = __shfl_sync(0xffffffffu, (int)cm, 31);
     T s0 = T(0), s1 = T(0);
-    int bad = 0;
     for (int c = 0; c <= c_last; ++c) {
         // neighbours of chunk c
         QV<T, NC> left, right, t;
@@ -529,7 +534,7 @@ __global__ void __launch_bounds__(256) k_bulk_x(const InstDesc *__restrict__ D, 
             if (lane == 31) Fhi = t;
             const int ap = a - 32;
             if (ap >= 0 && ap < n)
-                update_cell<T, NC, EQ>(Qo, plane, rowb + ap, cm, lam, g, av0, av1, Qm, Fprev, Fhi, last, s0, s1, bad);
+                update_cell<T, NC, EQ>(Qo, plane, rowb + ap, cm, lam, g, av0, av1, Qm, Fprev, Fhi, last, s0, s1, y);
         }
         shfl_idx(QRc, QR, 31);
         Fprev = F;
@@ -543,10 +548,10 @@ __global__ void __launch_bounds__(256) k_bulk_x(const InstDesc *__restrict__ D, 
         shfl_dn(Fhi, Fprev);
         const int ap = 32 * c_last + lane;
         if (ap >= 0 && ap < n && lane < 31)
-            update_cell<T, NC, EQ>(Qo, plane, rowb + ap, cm, lam, g, av0, av1, Qm, Fprev, Fhi, last, s0, s1, bad);
+            update_cell<T, NC, EQ>(Qo, plane, rowb + ap, cm, lam, g, av0, av1, Qm, Fprev, Fhi, last, s0, s1, y);
     }
     (void)cRc;
-    finish_warp<T>(y, last != 0, s0, s1, bad);
+    finish_warp<T>(y, last != 0, s0, s1);
 }
 
 // y sweep: one thread per column and segment of YSEG rows, marching upward
@@ -594,14 +599,13 @@ __global__ void __launch_bounds__(256, 3) k_bulk_y(const InstDesc *__restrict__ 
     // evolved top state of row j0-1
     evolve(EQ, g, 1, lam, av0, av1, qa.q, qm.q, qc.q, !(ca & CLS_SOLID) && !(cc & CLS_SOLID), QL.q, QRc.q);
     T s0 = T(0), s1 = T(0);
-    int bad = 0;
     for (int f = j0; f <= j1; ++f) {
         // window: qm = row f-1, qc = row f, qp = row f+1, qq = row f+2
         evolve(EQ, g, 1, lam, av0, av1, qm.q, qc.q, qp.q, !(cm & CLS_SOLID) && !(cp & CLS_SOLID), QL.q, QR.q);
         face_flux<T, NC, EQ, 1>(I, R, i, f, n, cm, cc, g, av0, av1, QRc, QL, F);
         if (f > j0 && active)
             update_cell<T, NC, EQ>(Qo, plane, (f - 1) * I.pitch + i, cm, lam, g, av0, av1, qm, Fprev, F, last, s0,
-                                   s1, bad);
+                                   s1, y);
         QRc = QR;
         Fprev = F;
         qm = qc; cm = cc;
@@ -609,7 +613,7 @@ __global__ void __launch_bounds__(256, 3) k_bulk_y(const InstDesc *__restrict__ 
         qp = qq; cp = cq;
         if (f + 3 <= j1 + 1) load(f + 3, qq, cq);
     }
-    finish_warp<T>(y, last != 0, s0, s1, bad);
+    finish_warp<T>(y, last != 0, s0, s1);
 }
 
 // ---------------------------------------------------------------------------
@@ -772,7 +776,7 @@ __device__ __forceinline__ void face_override(const InstDesc &I, const BandRec *
 // wave speeds and positivity for the CFL step
 __device__ __forceinline__ void update2(float *__restrict__ Qo, size_t plane, int ci, int st, bool vec, float g1,
                                         float g, float lam, const float2 *q, const float2 *Flo, const float2 *Fhi,
-                                        bool last, float &s0, float &s1, int &bad) {
+                                        bool last, float &s0, float &s1, InstDyn &y) {
     float2 qn[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) qn[k] = fma2(P2(lam), sub2(Flo[k], Fhi[k]), q[k]);
@@ -788,7 +792,8 @@ __device__ __forceinline__ void update2(float *__restrict__ Qo, size_t plane, in
     }
     float2 ir, p;
     prim2(g1, qn, ir, p);
-    if (((st & 1) && !(qn[0].x > 0.0f && p.x > 0.0f)) || ((st & 2) && !(qn[0].y > 0.0f && p.y > 0.0f))) bad = 1;
+    if ((st & 1) && !(qn[0].x > 0.0f && p.x > 0.0f)) list_bulk_bad(y, ci);
+    if ((st & 2) && !(qn[0].y > 0.0f && p.y > 0.0f)) list_bulk_bad(y, ci + 1);
     if (last) {
         const float2 c = sqrt2(mul2(mul2(P2(g), p), ir));
         const float2 w0 = add2(make_float2(fabsf(qn[1].x * ir.x), fabsf(qn[1].y * ir.y)), c);
@@ -798,17 +803,38 @@ __device__ __forceinline__ void update2(float *__restrict__ Qo, size_t plane, in
     }
 }
 
-__device__ __forceinline__ void shfl_up4(float2 *o, const float2 *v, int comp) {
-#pragma unroll
-    for (int k = 0; k < 4; ++k) o[k].x = __shfl_up_sync(0xffffffffu, comp ? v[k].y : v[k].x, 1);
+// asynchronous global -> shared copies of 4 or 8 bytes (completion through
+// cp.async.wait_group, issued and waited for by the same thread)
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
 }
+__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// per-warp ring of row chunks for the x sweep: chunk c of the row sits in
+// slot c % XR, prefetched XR - 2 chunks ahead
+constexpr int XR = 4;
+struct XRing {
+    float q[XR][4][64];
+    unsigned char cls[XR][64];
+};
 
 // x sweep, packed: one warp per row, lane l holds cells 64c + 2l and
 // 64c + 2l + 1 of chunk c; the update trails the fluxes by one chunk
-__global__ void __launch_bounds__(256) k_bulk_x_p(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y,
+__global__ void __launch_bounds__(128, 5) k_bulk_x_p(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y,
                                                   const BandRec *__restrict__ R, int n_inst, int total_warps, int src,
                                                   int dst, int last) {
+    extern __shared__ __align__(16) unsigned char xsm[];
     const int lane = threadIdx.x & 31;
+    XRing &rg = ((XRing *)xsm)[threadIdx.x >> 5];
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (gw >= total_warps) return;
     const int inst = find_inst_warp(D, n_inst, gw, 0);
@@ -823,90 +849,111 @@ __global__ void __launch_bounds__(256) k_bulk_x_p(const InstDesc *__restrict__ D
     float *__restrict__ Qo = (float *)I.Q[dst];
     const int rowb = j * I.pitch;
     const int bclo = I.bc[0], bchi = I.bc[1];
-    // the pair of chunk c (classes packed as first | second << 8)
-    auto load = [&](int c, S2 &v, int &cls) {
-        const int a = 64 * c + 2 * lane;
-        if (a >= 0 && a + 1 < n) {
-#pragma unroll
-            for (int k = 0; k < 4; ++k) v.q[k] = __ldg((const float2 *)(Q + k * plane + rowb + a));
-            cls = __ldg((const unsigned short *)(I.cls + rowb + a));
-            return;
-        }
-        cls = 0;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int b = a + h;
-            float w[4];
-            int cb;
-            if (b < -2 || b > n + 1) {
-                w[0] = w[1] = w[2] = w[3] = 1.0f;
-                cb = CLS_SOLID;
-            } else {
-                bool fl;
-                const int pidx = ghost_map(b, n, bclo, bchi, &fl);
-#pragma unroll
-                for (int k = 0; k < 4; ++k) w[k] = __ldg(Q + k * plane + rowb + pidx);
-                if (fl) w[1] = -w[1];
-                cb = I.cls[rowb + pidx];
-            }
+    // copies of chunk c's real cells into its slot (one commit group per call)
+    auto prefetch = [&](int c) {
+        if (c >= 0 && 64 * c < n) {
+            const int s = c & (XR - 1);
+            const int a = 64 * c + 2 * lane;
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                if (h == 0) v.q[k].x = w[k];
-                else v.q[k].y = w[k];
+                if (a + 1 < n) cp_async8(&rg.q[s][k][2 * lane], Q + k * plane + rowb + a);
+                else if (a < n) cp_async4(&rg.q[s][k][2 * lane], Q + k * plane + rowb + a);
             }
-            cls |= cb << (8 * h);
+            if (lane < 16 && 64 * c + 4 * lane < n) cp_async4(&rg.cls[s][4 * lane], I.cls + rowb + 64 * c + 4 * lane);
+        }
+        cp_async_commit();
+    };
+    // state and class of cell b: from the ring inside the row, a ghost cell
+    // of the boundary condition next to it, filler beyond
+    auto cell = [&](int b, float *w, int &cb) {
+        if (b >= 0 && b < n) {
+            const int s = (b >> 6) & (XR - 1), o = b & 63;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) w[k] = rg.q[s][k][o];
+            cb = rg.cls[s][o];
+        } else if (b >= -2 && b <= n + 1) {
+            bool fl;
+            const int p = ghost_map(b, n, bclo, bchi, &fl);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) w[k] = __ldg(Q + k * plane + rowb + p);
+            if (fl) w[1] = -w[1];
+            cb = I.cls[rowb + p];
+        } else {
+            w[0] = w[1] = w[2] = w[3] = 1.0f;
+            cb = CLS_SOLID;
         }
     };
+    // the pair of chunk c (classes packed as first | second << 8)
+    auto pair = [&](int c, S2 &v, int &cls) {
+        const int a = 64 * c + 2 * lane;
+        if (a >= 0 && a + 1 < n) {
+            const int s = c & (XR - 1);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) v.q[k] = *(const float2 *)&rg.q[s][k][2 * lane];
+            cls = *(const unsigned short *)&rg.cls[s][2 * lane];
+            return;
+        }
+        float w0[4], w1[4];
+        int c0, c1;
+        cell(a, w0, c0);
+        cell(a + 1, w1, c1);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v.q[k] = make_float2(w0[k], w1[k]);
+        cls = c0 | c1 << 8;
+    };
     const int c_last = (n + 1) >> 6;   // chunk holding face n
-    S2 Qm, Q0, Qp;
-    int cm, c0, cp;
-    load(-1, Qm, cm);
-    load(0, Q0, c0);
-    load(1, Qp, cp);
-    // evolved right state of cell -1 (second cell of lane 31, chunk -1)
+    prefetch(0);
+    prefetch(1);
+    cp_async_wait<0>();
+    __syncwarp();
+    // evolved right state of cell -1
     E2 QRc;
     {
-        float2 qm[4], qp[4];
+        float w[4], wm[4], wp[4];
+        int cb, cbm, cbp;
+        cell(-1, w, cb);
+        cell(-2, wm, cbm);
+        cell(0, wp, cbp);
+        float2 qm[4], q0[4], qp[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const float up = __shfl_up_sync(0xffffffffu, Qm.q[k].y, 1);
-            const float dn = __shfl_down_sync(0xffffffffu, Qm.q[k].x, 1);
-            const float nx0 = __shfl_sync(0xffffffffu, Q0.q[k].x, 0);
-            qm[k] = make_float2(up, Qm.q[k].x);
-            qp[k] = make_float2(Qm.q[k].y, lane == 31 ? nx0 : dn);
+            qm[k] = make_float2(wm[k], wm[k]);
+            q0[k] = make_float2(w[k], w[k]);
+            qp[k] = make_float2(wp[k], wp[k]);
         }
-        const int cu = __shfl_up_sync(0xffffffffu, cm, 1), cd0 = __shfl_down_sync(0xffffffffu, cm, 1);
-        const int cn = __shfl_sync(0xffffffffu, c0, 0);
-        const int cd = lane == 31 ? cn : cd0;
-        const bool lx = !((cu >> 8) & CLS_SOLID) && !((cm >> 8) & CLS_SOLID);
-        const bool ly = !(cm & CLS_SOLID) && !(cd & CLS_SOLID);
-        E2 QL, QR;
-        evolve2<0>(g1, lam, qm, Qm.q, qp, lx, ly, QL, QR);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) QRc.q[k].x = __shfl_sync(0xffffffffu, QR.q[k].y, 31);
-        QRc.ir.x = __shfl_sync(0xffffffffu, QR.ir.y, 31);
-        QRc.p.x = __shfl_sync(0xffffffffu, QR.p.y, 31);
+        const bool lim = !(cbm & CLS_SOLID) && !(cbp & CLS_SOLID);
+        E2 QL;
+        evolve2<0>(g1, lam, qm, q0, qp, lim, lim, QL, QRc);
     }
     float s0 = 0.0f, s1 = 0.0f;
-    int bad = 0;
     float2 Fprev[4];
     for (int c = 0; c <= c_last; ++c) {
+        __syncwarp();
+        prefetch(c + XR - 2);
+        cp_async_wait<XR - 3>();
+        __syncwarp();
         const int a = 64 * c + 2 * lane;
-        // neighbours: the cell before the pair and the cell after it
+        S2 Q0;
+        int c0;
+        pair(c, Q0, c0);
+        float wl[4], wr[4];
+        int clA, crB;
+        if (lane > 0 && a + 1 < n) {
+            const int s = c & (XR - 1);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) wl[k] = rg.q[s][k][2 * lane - 1];
+            clA = rg.cls[s][2 * lane - 1];
+        } else {
+            cell(a - 1, wl, clA);
+        }
+        cell(a + 2, wr, crB);
         float2 qm[4], qp[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const float up = __shfl_up_sync(0xffffffffu, Q0.q[k].y, 1);
-            const float pv = __shfl_sync(0xffffffffu, Qm.q[k].y, 31);
-            const float dn = __shfl_down_sync(0xffffffffu, Q0.q[k].x, 1);
-            const float nx0 = __shfl_sync(0xffffffffu, Qp.q[k].x, 0);
-            qm[k] = make_float2(lane == 0 ? pv : up, Q0.q[k].x);
-            qp[k] = make_float2(Q0.q[k].y, lane == 31 ? nx0 : dn);
+            qm[k] = make_float2(wl[k], Q0.q[k].x);
+            qp[k] = make_float2(Q0.q[k].y, wr[k]);
         }
-        const int cu0 = __shfl_up_sync(0xffffffffu, c0, 1), cpv = __shfl_sync(0xffffffffu, cm, 31);
-        const int cd0 = __shfl_down_sync(0xffffffffu, c0, 1), cnx = __shfl_sync(0xffffffffu, cp, 0);
-        const int cu = lane == 0 ? cpv : cu0, cd = lane == 31 ? cnx : cd0;
-        const int clA = (cu >> 8) & 0xff, cA = c0 & 0xff, cB = (c0 >> 8) & 0xff, crB = cd & 0xff;
+        const int cA = c0 & 0xff, cB = (c0 >> 8) & 0xff;
         const bool lx = !(clA & CLS_SOLID) && !(cB & CLS_SOLID);
         const bool ly = !(cA & CLS_SOLID) && !(crB & CLS_SOLID);
         E2 QL, QR;
@@ -937,11 +984,14 @@ __global__ void __launch_bounds__(256) k_bulk_x_p(const InstDesc *__restrict__ D
                 const float nx0 = __shfl_sync(0xffffffffu, F[k].x, 0);
                 Fhi[k] = make_float2(Fprev[k].y, lane == 31 ? nx0 : dn);
             }
+            S2 Qm;
+            int cm;
+            pair(c - 1, Qm, cm);
             const int ap = a - 64;
             int st = 0;
             if (ap < n && !((cm & 0xff) & (CLS_BAND | CLS_SOLID))) st |= 1;
             if (ap + 1 < n && !(((cm >> 8) & 0xff) & (CLS_BAND | CLS_SOLID))) st |= 2;
-            if (st) update2(Qo, plane, rowb + ap, st, st == 3, g1, g, lam, Qm.q, Fprev, Fhi, last, s0, s1, bad);
+            if (st) update2(Qo, plane, rowb + ap, st, st == 3, g1, g, lam, Qm.q, Fprev, Fhi, last, s0, s1, y);
             if ((cm & CLS_SOLID) && ap < n) {
 #pragma unroll
                 for (int k = 0; k < 4; ++k) Qo[k * plane + rowb + ap] = NAN;
@@ -957,9 +1007,6 @@ __global__ void __launch_bounds__(256) k_bulk_x_p(const InstDesc *__restrict__ D
         QRc.p.x = __shfl_sync(0xffffffffu, QR.p.y, 31);
 #pragma unroll
         for (int k = 0; k < 4; ++k) Fprev[k] = F[k];
-        Qm = Q0; cm = c0;
-        Q0 = Qp; c0 = cp;
-        load(c + 2, Qp, cp);
     }
     // the last chunk (its high faces were computed in the final iteration,
     // except the one past lane 31 which lies beyond face n)
@@ -970,11 +1017,14 @@ __global__ void __launch_bounds__(256) k_bulk_x_p(const InstDesc *__restrict__ D
             const float dn = __shfl_down_sync(0xffffffffu, Fprev[k].x, 1);
             Fhi[k] = make_float2(Fprev[k].y, dn);
         }
+        S2 Qm;
+        int cm;
+        pair(c_last, Qm, cm);
         const int ap = 64 * c_last + 2 * lane;
         int st = 0;
         if (ap < n && !((cm & 0xff) & (CLS_BAND | CLS_SOLID))) st |= 1;
         if (ap + 1 < n && lane < 31 && !(((cm >> 8) & 0xff) & (CLS_BAND | CLS_SOLID))) st |= 2;
-        if (st) update2(Qo, plane, rowb + ap, st, st == 3, g1, g, lam, Qm.q, Fprev, Fhi, last, s0, s1, bad);
+        if (st) update2(Qo, plane, rowb + ap, st, st == 3, g1, g, lam, Qm.q, Fprev, Fhi, last, s0, s1, y);
         if ((cm & CLS_SOLID) && ap < n) {
 #pragma unroll
             for (int k = 0; k < 4; ++k) Qo[k * plane + rowb + ap] = NAN;
@@ -984,7 +1034,7 @@ __global__ void __launch_bounds__(256) k_bulk_x_p(const InstDesc *__restrict__ D
             for (int k = 0; k < 4; ++k) Qo[k * plane + rowb + ap + 1] = NAN;
         }
     }
-    finish_warp<float>(y, last != 0, s0, s1, bad);
+    finish_warp<float>(y, last != 0, s0, s1);
 }
 
 // y sweep, packed: one thread per pair of neighbouring columns and segment of
@@ -1046,7 +1096,6 @@ __global__ void __launch_bounds__(256) k_bulk_y_p(const InstDesc *__restrict__ D
     evolve2<1>(g1, lam, qa.q, qm.q, qc.q, !(ca & CLS_SOLID) && !(cc & CLS_SOLID),
                !((ca >> 8) & CLS_SOLID) && !((cc >> 8) & CLS_SOLID), QL, QRc);
     float s0 = 0.0f, s1 = 0.0f;
-    int bad = 0;
     float2 Fprev[4];
     for (int f = j0; f <= j1; ++f) {
         // window: qm = row f-1, qc = row f, qp = row f+1, qq = row f+2
@@ -1061,7 +1110,7 @@ __global__ void __launch_bounds__(256) k_bulk_y_p(const InstDesc *__restrict__ D
             if ((st0 & 1) && !((cm & 0xff) & (CLS_BAND | CLS_SOLID))) st |= 1;
             if ((st0 & 2) && !(((cm >> 8) & 0xff) & (CLS_BAND | CLS_SOLID))) st |= 2;
             const int ci = (f - 1) * I.pitch + i;
-            if (st) update2(Qo, plane, ci, st, st == 3, g1, g, lam, qm.q, Fprev, F, last, s0, s1, bad);
+            if (st) update2(Qo, plane, ci, st, st == 3, g1, g, lam, qm.q, Fprev, F, last, s0, s1, y);
             if ((st0 & 1) && (cm & CLS_SOLID)) {
 #pragma unroll
                 for (int k = 0; k < 4; ++k) Qo[k * plane + ci] = NAN;
@@ -1079,7 +1128,7 @@ __global__ void __launch_bounds__(256) k_bulk_y_p(const InstDesc *__restrict__ D
         qp = qq; cp = cq;
         if (f + 3 <= j1 + 1) load(f + 3, qq, cq);
     }
-    finish_warp<float>(y, last != 0, s0, s1, bad);
+    finish_warp<float>(y, last != 0, s0, s1);
 }
 
 template <class T, int EQ>
@@ -1176,7 +1225,8 @@ __global__ void k_mix(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y, B
         y.t += y.dt;
         y.step += 1;
     }
-    if (y.nbad == 0) return;
+    if (y.nbad == 0 && y.nbulk == 0) return;
+    if (y.nbulk > NBULK) { y.err |= ERR_UNSTABLE; return; }
     int *node = scratch + (size_t)inst * 2 * MIXCAP;     // cell index of node
     int *par = node + MIXCAP;
     int nn = 0;
@@ -1191,43 +1241,84 @@ __global__ void k_mix(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y, B
         return nn++;
     };
     auto root = [&](int k) { while (par[k] != k) k = par[k]; return k; };
-    bool overflow = false;
-    const bool listed = y.nbad <= 16;
-    const int nscan = listed ? y.nbad : y.band_count;
-    for (int s = 0; s < nscan; ++s) {
-        const int r = listed ? y.badlist[s] : I.rec_base + s;
-        const BandRec &b = R[r];
-        if (!(b.flags & RF_BAD)) continue;
-        int kb = find_node(b.cell);
-        if (kb < 0) { overflow = true; break; }
+    auto alpha_B = [&](int c) -> double {
+        const uint8_t cl = I.cls[c];
+        return (cl & CLS_BAND) ? R[I.rec[c]].aB : ((cl & CLS_SOLID) ? 0.0 : 1.0);
+    };
+    // a non-physical cell joins the clusters of its fluid face neighbours
+    auto seed = [&](int cell, int i, int j) -> bool {
+        const int kb = find_node(cell);
+        if (kb < 0) return false;
         const int dd[4][2] = {{-1, 0}, {1, 0}, {0, -1}, {0, 1}};
         for (int m = 0; m < 4; ++m) {
-            int ii = b.i + dd[m][0], jj = b.j + dd[m][1];
+            int ii = i + dd[m][0], jj = j + dd[m][1];
             if (I.bc[0] == 2) { ii %= I.nx; if (ii < 0) ii += I.nx; }
             if (I.bc[2] == 2) { jj %= I.ny; if (jj < 0) jj += I.ny; }
             if (ii < 0 || ii >= I.nx || jj < 0 || jj >= I.ny) continue;
-            int c = jj * I.pitch + ii;
-            uint8_t cl = I.cls[c];
-            double aB = (cl & CLS_BAND) ? R[I.rec[c]].aB : ((cl & CLS_SOLID) ? 0.0 : 1.0);
-            if (!(aB > 0.0)) continue;
-            int kn = find_node(c);
-            if (kn < 0) { overflow = true; break; }
-            int ra = root(kb), rb = root(kn);
+            const int c = jj * I.pitch + ii;
+            if (!(alpha_B(c) > 0.0)) continue;
+            const int kn = find_node(c);
+            if (kn < 0) return false;
+            const int ra = root(kb), rb = root(kn);
             if (ra != rb) { if (ra < rb) par[rb] = ra; else par[ra] = rb; }
         }
-        if (overflow) break;
+        return true;
+    };
+    auto sort_int = [](int *v, int m) {
+        for (int x = 1; x < m; ++x) {
+            const int t = v[x];
+            int z = x;
+            while (z > 0 && v[z - 1] > t) { v[z] = v[z - 1]; --z; }
+            v[z] = t;
+        }
+    };
+    bool overflow = false;
+    // seeds in a fixed order: flagged band records by cell, then listed bulk cells
+    {
+        int seeds[16 + NBULK];
+        int ns = 0;
+        const bool listed = y.nbad <= 16;
+        if (listed) {
+            for (int q = 0; q < y.nbad; ++q) seeds[ns++] = R[y.badlist[q]].cell;
+            sort_int(seeds, ns);
+            for (int q = 0; q < ns && !overflow; ++q) {
+                const int c = seeds[q];
+                overflow = !seed(c, c % I.pitch, c / I.pitch);
+            }
+        } else {
+            for (int q = 0; q < y.band_count && !overflow; ++q) {
+                const BandRec &b = R[I.rec_base + q];
+                if (b.flags & RF_BAD) overflow = !seed(b.cell, b.i, b.j);
+            }
+        }
+        ns = 0;
+        for (int q = 0; q < y.nbulk; ++q) seeds[ns++] = y.bulkbad[q];
+        sort_int(seeds, ns);
+        for (int q = 0; q < ns && !overflow; ++q) {
+            const int c = seeds[q];
+            overflow = !seed(c, c % I.pitch, c / I.pitch);
+        }
     }
     if (overflow) { y.err |= ERR_UNSTABLE; return; }
-    // cluster sums
+    // nodes in cell order with the cell of their cluster root, so that the
+    // cluster sums run in a fixed order
+    for (int k = 0; k < nn; ++k) par[k] = root(k);        // node indices of the roots
+    for (int k = 0; k < nn; ++k) par[k] = node[par[k]];   // then their cells
+    for (int x = 1; x < nn; ++x) {
+        const int c = node[x], r = par[x];
+        int z = x;
+        while (z > 0 && node[z - 1] > c) { node[z] = node[z - 1]; par[z] = par[z - 1]; --z; }
+        node[z] = c;
+        par[z] = r;
+    }
     for (int k = 0; k < nn; ++k) {
-        int rk = root(k);
-        if (rk != k) continue;
+        const int rc = par[k];
+        if (node[k] != rc) continue;   // one pass per cluster, at its root cell
         double tot[MAXC] = {0, 0, 0, 0}, vol = 0.0;
         for (int m = 0; m < nn; ++m) {
-            if (root(m) != k) continue;
-            int c = node[m];
-            uint8_t cl = I.cls[c];
-            if (cl & CLS_BAND) {
+            if (par[m] != rc) continue;
+            const int c = node[m];
+            if (I.cls[c] & CLS_BAND) {
                 const BandRec &b = R[I.rec[c]];
                 vol += b.aB;
                 for (int q = 0; q < I.nc; ++q) tot[q] += b.C2[q];
@@ -1237,14 +1328,23 @@ __global__ void k_mix(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y, B
             }
         }
         for (int m = 0; m < nn; ++m) {
-            if (root(m) != k) continue;
-            int c = node[m];
-            uint8_t cl = I.cls[c];
-            if (cl & CLS_BAND) {
+            if (par[m] != rc) continue;
+            const int c = node[m];
+            if (I.cls[c] & CLS_BAND) {
                 BandRec &b = R[I.rec[c]];
                 for (int q = 0; q < I.nc; ++q) b.C2[q] = b.aB * (tot[q] / vol);
             } else {
-                for (int q = 0; q < I.nc; ++q) Qo[q * plane + c] = (T)(tot[q] / vol);
+                double qn[MAXC];
+                for (int q = 0; q < I.nc; ++q) {
+                    qn[q] = tot[q] / vol;
+                    Qo[q * plane + c] = (T)qn[q];
+                }
+                // a merged bulk cell that is still not physical ends the run
+                // (band cells are checked when their state is formed)
+                if (I.nc == 4) {
+                    const double pm = (I.gamma - 1.0) * (qn[3] - 0.5 * (qn[1] * qn[1] + qn[2] * qn[2]) / qn[0]);
+                    if (!(qn[0] > 0.0 && pm > 0.0)) y.err |= ERR_UNSTABLE;
+                }
             }
         }
     }
@@ -1372,7 +1472,7 @@ void launch_bulk(int dir, int eq, const InstDesc *D, InstDyn *Y, const BandRec *
     if (blocks <= 0) return;
     const bool packed = sizeof(T) == 4 && eq == 0;   // FP32 Euler x sweep: the FP32x2 kernel
     if (dir == 0) {
-        if (packed) k_bulk_x_p<<<blocks, 256, 0, st>>>(D, Y, R, n_inst, total_warps, src, dst, last);
+        if (packed) k_bulk_x_p<<<(total_warps + 3) / 4, 128, 4 * sizeof(XRing), st>>>(D, Y, R, n_inst, total_warps, src, dst, last);
         else if (eq == 0) k_bulk_x<T, 0><<<blocks, 256, 0, st>>>(D, Y, R, n_inst, total_warps, src, dst, last);
         else k_bulk_x<T, 1><<<blocks, 256, 0, st>>>(D, Y, R, n_inst, total_warps, src, dst, last);
     } else {
