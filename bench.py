@@ -109,6 +109,27 @@ def job_value(cells_all, steps, total_ms):
     return cells_all * 2 * steps / (total_ms * 1e-3)
 
 
+def bulk_traffic(precision, wname):
+    """DRAM bytes per bulk-kernel launch (mean over the x and y kernels) from
+    the ncu capture summarised in profiles/bulk_traffic.json, or None when
+    that capture is of another workload or precision or the kernel sources
+    have changed since it was taken."""
+    import hashlib
+    prof = os.path.join(ROOT, "profiles", "bulk_traffic.json")
+    try:
+        d = json.load(open(prof))
+        if d["workload"] != wname or d["precision"] != precision:
+            return None
+        for f, sha in d["sources_sha256"].items():
+            with open(os.path.join(ROOT, "paper_1711_11361_gb300", "csrc", f), "rb") as fh:
+                if hashlib.sha256(fh.read()).hexdigest() != sha:
+                    return None
+        v = list(d["per_launch_bytes"].values())
+        return float(sum(v) / len(v))
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def workload(rank, args):
     from paper_1711_11361_gb300 import inputs
     if args.workload == "c4":
@@ -231,13 +252,7 @@ def main():
     bpc = BYTES_PER_CELL_FP32 if prec == mb.FP32 else BYTES_PER_CELL_FP64
     achieved = cells * bpc / avg_bulk_s / 1e9
     peak, peak_kind = measured_peaks()
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "bulk_traffic.json")
-    if os.path.exists(prof):
-        try:
-            traffic = json.load(open(prof)).get("per_launch_bytes_" + args.precision + "_" + wname)
-        except Exception:
-            traffic = None
+    traffic = bulk_traffic(args.precision, wname)
 
     # end to end through the C ABI with pinned host buffers
     pinned_in = [torch.empty((p.nc, p.ny, p.nx), dtype=torch.float64).pin_memory() for p in probs]
@@ -272,7 +287,7 @@ def main():
                    "parallelism": "instances" if ws == 1 else f"instances x{ws} ranks"},
         "p50_ms_per_step": float(np.percentile(per, 50)), "p99_ms_per_step": float(np.percentile(per, 99)),
         "status": int(status),
-        "roofline": {"kernel": "k_bulk (MUSCL-Hancock+HLLC sweep update)", "bound": "hbm", "achieved": achieved,
+        "roofline": {"kernel": "bulk sweep update (MUSCL-Hancock + HLLC), x and y kernels", "bound": "hbm", "achieved": achieved,
                      "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "peak_kind": peak_kind, "bytes_per_cell": bpc, "avg_launch_ms": avg_bulk_s * 1e3,
                      "launches_timed": launches},
