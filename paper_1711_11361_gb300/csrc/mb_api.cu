@@ -255,8 +255,9 @@ mb_status mb_batch_create(int n, const mb_grid *grids, const double *gammas, con
         // columns and 64-row segment
         I.tiles_x[0] = 1;
         I.ntiles[0] = g.ny;
-        // y sweep: 32 columns per warp
-        const int ycols = 32;
+        // y sweep: 32 columns per warp, 64 for the FP32 Euler kernel that
+        // carries two columns per thread
+        const int ycols = (prec == MB_FP32 && g.equation == MB_EULER) ? 64 : 32;
         I.tiles_x[1] = (g.nx + ycols - 1) / ycols;
         I.ntiles[1] = I.tiles_x[1] * ((g.ny + 63) / 64);
         I.tile_off[0] = tiles0;

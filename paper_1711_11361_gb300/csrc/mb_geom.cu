@@ -101,9 +101,14 @@ __global__ void k_pose(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y, 
         y.XM = dir == 0 ? y.X + 0.5 * delta : y.X;
         y.YM = dir == 1 ? y.Y + 0.5 * delta : y.Y;
         y.thA = thA; y.thB = thB; y.thM = thM;
-        y.cA = cos(thA); y.sA = sin(thA);
-        y.cB = cos(thB); y.sB = sin(thB);
-        y.cM = cos(thM); y.sM = sin(thM);
+        if (I.rotating) {
+            sincos(thA, &y.sA, &y.cA);
+            sincos(thB, &y.sB, &y.cB);
+            sincos(thM, &y.sM, &y.cM);
+        } else {   // the rotation of a translating body is the identity
+            y.cA = y.cB = y.cM = 1.0;
+            y.sA = y.sB = y.sM = 0.0;
+        }
         y.Om = Om;
         y.band_count = 0;
         y.nbad = 0;

@@ -1037,14 +1037,24 @@ __global__ void __launch_bounds__(128, 5) k_bulk_x_p(const InstDesc *__restrict_
     finish_warp<float>(y, last != 0, s0, s1);
 }
 
+// per-warp ring of rows for the y sweep: row r of the warp's 64 columns sits
+// in slot (r - j0 + 2) % YR, prefetched YR - 2 rows ahead
+constexpr int YR = 8;
+struct YRing {
+    float q[YR][4][64];
+    unsigned char cls[YR][64];
+};
+
 // y sweep, packed: one thread per pair of neighbouring columns and segment of
-// YSEG rows, marching upward with a register window; a warp covers 64
-// consecutive columns
+// YSEG rows, marching upward; a warp covers 64 consecutive columns and
+// streams its rows through a shared-memory ring filled by cp.async
 constexpr int YCOLS_P = 64;
-__global__ void __launch_bounds__(256) k_bulk_y_p(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y,
-                                                  const BandRec *__restrict__ R, int n_inst, int total_warps, int src,
-                                                  int dst, int last) {
+__global__ void __launch_bounds__(128, 5) k_bulk_y_p(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y,
+                                                     const BandRec *__restrict__ R, int n_inst, int total_warps,
+                                                     int src, int dst, int last) {
+    extern __shared__ __align__(16) unsigned char ysm[];
     const int lane = threadIdx.x & 31;
+    YRing &rg = ((YRing *)ysm)[threadIdx.x >> 5];
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (gw >= total_warps) return;
     const int inst = find_inst_warp(D, n_inst, gw, 1);
@@ -1053,11 +1063,9 @@ __global__ void __launch_bounds__(256) k_bulk_y_p(const InstDesc *__restrict__ D
     const int local = gw - I.tile_off[1];
     const int ncg = I.tiles_x[1];
     const int cg = local % ncg, sg = local / ncg;
-    const int i_raw = cg * YCOLS_P + 2 * lane;
-    // columns i, i+1 (a pair past the last column repeats column nx-1)
-    const int st0 = (i_raw < I.nx ? 1 : 0) | (i_raw + 1 < I.nx ? 2 : 0);
-    const int i = i_raw < I.nx ? i_raw : I.nx - 1;
-    const bool pair_ok = st0 == 3;
+    const int col0 = cg * YCOLS_P;
+    const int i = col0 + 2 * lane;     // columns i, i+1 of this thread
+    const int st0 = (i < I.nx ? 1 : 0) | (i + 1 < I.nx ? 2 : 0);
     const int n = I.ny;
     const int j0 = sg * YSEG, j1 = min(n, j0 + YSEG);
     const float lam = y.lamf;
@@ -1066,45 +1074,79 @@ __global__ void __launch_bounds__(256) k_bulk_y_p(const InstDesc *__restrict__ D
     const float *__restrict__ Q = (const float *)I.Q[src];
     float *__restrict__ Qo = (float *)I.Q[dst];
     const int bclo = I.bc[2], bchi = I.bc[3];
-    auto load = [&](int r, S2 &v, int &cls) {
-        bool fl;
-        const int p = ghost_map(r, n, bclo, bchi, &fl);
-        const int ci = p * I.pitch + i;
-        if (pair_ok) {
+    // copies of row r (a ghost row of the boundary condition outside [0, n))
+    // into its slot; rows past j1 + 1 are not needed (one commit group per call)
+    auto prefetch = [&](int r) {
+        if (r <= j1 + 1) {
+            const int s = (r - j0 + 2) & (YR - 1);
+            bool fl;
+            const int p = ghost_map(r, n, bclo, bchi, &fl);
+            const int ci = p * I.pitch + i;
 #pragma unroll
-            for (int k = 0; k < 4; ++k) v.q[k] = __ldg((const float2 *)(Q + k * plane + ci));
-            cls = __ldg((const unsigned short *)(I.cls + ci));
-        } else {
-#pragma unroll
-            for (int k = 0; k < 4; ++k) v.q[k] = P2(__ldg(Q + k * plane + ci));
-            const int cc = I.cls[ci];
-            cls = cc | cc << 8;
+            for (int k = 0; k < 4; ++k) {
+                if (st0 == 3) cp_async8(&rg.q[s][k][2 * lane], Q + k * plane + ci);
+                else if (st0 == 1) cp_async4(&rg.q[s][k][2 * lane], Q + k * plane + ci);
+            }
+            if (lane < 16 && col0 + 4 * lane < I.pitch)
+                cp_async4(&rg.cls[s][4 * lane], I.cls + p * I.pitch + col0 + 4 * lane);
         }
-        if (fl) {
+        cp_async_commit();
+    };
+    // the pair of row r from the ring; columns past the grid read as solid
+    auto row = [&](int r, S2 &v, int &cls) {
+        const int s = (r - j0 + 2) & (YR - 1);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v.q[k] = *(const float2 *)&rg.q[s][k][2 * lane];
+        cls = *(const unsigned short *)&rg.cls[s][2 * lane];
+        if (st0 != 3) {
+            if (!(st0 & 1)) {
+                cls = (cls & 0xff00) | CLS_SOLID;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) v.q[k].x = 1.0f;
+            }
+            cls = (cls & 0xff) | (CLS_SOLID << 8);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) v.q[k].y = 1.0f;
+        }
+        if ((r < 0 && bclo == 1) || (r >= n && bchi == 1)) {
             v.q[2].x = -v.q[2].x;
             v.q[2].y = -v.q[2].y;
         }
     };
-    S2 qa, qm, qc, qp, qq;
-    int ca, cm, cc, cp, cq;
-    load(j0 - 2, qa, ca);
-    load(j0 - 1, qm, cm);
-    load(j0, qc, cc);
-    load(j0 + 1, qp, cp);
-    load(j0 + 2, qq, cq);
-    E2 QL, QR, QRc;
-    evolve2<1>(g1, lam, qa.q, qm.q, qc.q, !(ca & CLS_SOLID) && !(cc & CLS_SOLID),
-               !((ca >> 8) & CLS_SOLID) && !((cc >> 8) & CLS_SOLID), QL, QRc);
+    for (int r = j0 - 2; r < j0 - 2 + YR; ++r) prefetch(r);
+    cp_async_wait<YR - 3>();
+    __syncwarp();
+    E2 QRc;
+    {
+        S2 qa, qm, qc;
+        int ca, cm, cc;
+        row(j0 - 2, qa, ca);
+        row(j0 - 1, qm, cm);
+        row(j0, qc, cc);
+        E2 QL;
+        evolve2<1>(g1, lam, qa.q, qm.q, qc.q, !(ca & CLS_SOLID) && !(cc & CLS_SOLID),
+                   !((ca >> 8) & CLS_SOLID) && !((cc >> 8) & CLS_SOLID), QL, QRc);
+    }
     float s0 = 0.0f, s1 = 0.0f;
     float2 Fprev[4];
     for (int f = j0; f <= j1; ++f) {
-        // window: qm = row f-1, qc = row f, qp = row f+1, qq = row f+2
+        __syncwarp();
+        prefetch(f + YR - 2);
+        cp_async_wait<YR - 3>();
+        __syncwarp();
+        // rows f-1, f, f+1
+        S2 qm, qc, qp;
+        int cm, cc, cp;
+        row(f - 1, qm, cm);
+        row(f, qc, cc);
+        row(f + 1, qp, cp);
+        E2 QL, QR;
         evolve2<1>(g1, lam, qm.q, qc.q, qp.q, !(cm & CLS_SOLID) && !(cp & CLS_SOLID),
                    !((cm >> 8) & CLS_SOLID) && !((cp >> 8) & CLS_SOLID), QL, QR);
         float2 F[4];
         hllc2<1>(g, QRc, QL, F);
-        face_override<1>(I, R, i, f, n, (uint8_t)(cm & 0xff), (uint8_t)(cc & 0xff), F, 0);
-        if (pair_ok) face_override<1>(I, R, i + 1, f, n, (uint8_t)(cm >> 8), (uint8_t)(cc >> 8), F, 1);
+        if (st0 & 1) face_override<1>(I, R, i, f, n, (uint8_t)(cm & 0xff), (uint8_t)(cc & 0xff), F, 0);
+        if (st0 & 2) face_override<1>(I, R, i + 1, f, n, (uint8_t)(cm >> 8), (uint8_t)(cc >> 8), F, 1);
         if (f > j0) {
             int st = 0;
             if ((st0 & 1) && !((cm & 0xff) & (CLS_BAND | CLS_SOLID))) st |= 1;
@@ -1123,10 +1165,6 @@ __global__ void __launch_bounds__(256) k_bulk_y_p(const InstDesc *__restrict__ D
         QRc = QR;
 #pragma unroll
         for (int k = 0; k < 4; ++k) Fprev[k] = F[k];
-        qm = qc; cm = cc;
-        qc = qp; cc = cp;
-        qp = qq; cp = cq;
-        if (f + 3 <= j1 + 1) load(f + 3, qq, cq);
     }
     finish_warp<float>(y, last != 0, s0, s1);
 }
@@ -1470,13 +1508,14 @@ void launch_bulk(int dir, int eq, const InstDesc *D, InstDyn *Y, const BandRec *
                  int src, int dst, int last, cudaStream_t st) {
     int blocks = (total_warps + 7) / 8;
     if (blocks <= 0) return;
-    const bool packed = sizeof(T) == 4 && eq == 0;   // FP32 Euler x sweep: the FP32x2 kernel
+    const bool packed = sizeof(T) == 4 && eq == 0;   // FP32 Euler: the FP32x2 kernels
     if (dir == 0) {
         if (packed) k_bulk_x_p<<<(total_warps + 3) / 4, 128, 4 * sizeof(XRing), st>>>(D, Y, R, n_inst, total_warps, src, dst, last);
         else if (eq == 0) k_bulk_x<T, 0><<<blocks, 256, 0, st>>>(D, Y, R, n_inst, total_warps, src, dst, last);
         else k_bulk_x<T, 1><<<blocks, 256, 0, st>>>(D, Y, R, n_inst, total_warps, src, dst, last);
     } else {
-        if (eq == 0) k_bulk_y<T, 0><<<blocks, 256, 0, st>>>(D, Y, R, n_inst, total_warps, src, dst, last);
+        if (packed) k_bulk_y_p<<<(total_warps + 3) / 4, 128, 4 * sizeof(YRing), st>>>(D, Y, R, n_inst, total_warps, src, dst, last);
+        else if (eq == 0) k_bulk_y<T, 0><<<blocks, 256, 0, st>>>(D, Y, R, n_inst, total_warps, src, dst, last);
         else k_bulk_y<T, 1><<<blocks, 256, 0, st>>>(D, Y, R, n_inst, total_warps, src, dst, last);
     }
 }
@@ -1485,6 +1524,12 @@ template <class T>
 int bulk_blocks_per_sm(int dir) {
     bulk_attr_t<T, 0>(dir);
     bulk_attr_t<T, 1>(dir);
+    if (sizeof(T) == 4) {   // the FP32x2 kernels' shared-memory rings
+        if (dir == 0)
+            cudaFuncSetAttribute(k_bulk_x_p, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(4 * sizeof(XRing)));
+        else
+            cudaFuncSetAttribute(k_bulk_y_p, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(4 * sizeof(YRing)));
+    }
     return 1;
 }
 
