@@ -130,6 +130,72 @@ def bulk_traffic(precision, wname):
         return None
 
 
+def accuracy_leg(mb, probs, steps=20):
+    """FP32 batch against the FP64 GPU path (itself held to the oracle at
+    1e-12 per step by the parity tests) on the same instances, the same
+    initial states and a common fixed dt (the smallest CFL step of the
+    instances): the relative L1 density error, alpha-weighted over fluid
+    cells, and the drift of the conserved totals (rho, rho u, rho v, E)
+    relative to the exactly conservative FP64 path, as maxima over
+    instances."""
+    s64 = mb.Sim(probs, mb.FP64)
+    dts = s64.step(0.0, report=True)
+    s64.close()
+    dt = float(np.min(dts))
+    s64 = mb.Sim(probs, mb.FP64)
+    s32 = mb.Sim(probs, mb.FP32)
+    for _ in range(steps):
+        s64.step(dt)
+        s32.step(dt)
+    s64.sync()
+    s32.sync()
+    l1, drift = [], np.zeros(4)
+    for k in range(len(probs)):
+        a = s64.read_state(k, alpha=True)
+        b = s32.read_state(k)
+        al = a["alpha"]
+        fl = al > 0
+        r64, r32 = a["Q"][0][fl], b["Q"][0][fl]
+        w = al[fl]
+        l1.append(float(np.sum(w * np.abs(r32 - r64)) / np.sum(w * np.abs(r64))))
+        for q in range(4):
+            t64 = np.sum(w * a["Q"][q][fl])
+            t32 = np.sum(w * b["Q"][q][fl])
+            scale = np.sum(w * np.abs(a["Q"][q][fl]))
+            drift[q] = max(drift[q], abs(t32 - t64) / scale if scale > 0 else 0.0)
+    s64.close()
+    s32.close()
+    return {"l1_density_rel_max": max(l1), "l1_density_rel_mean": float(np.mean(l1)),
+            "conservation_drift_rel_max": {"rho": drift[0], "rho_u": drift[1], "rho_v": drift[2], "E": drift[3]},
+            "against": "FP64 GPU path, same instances and states", "steps": steps, "dt": dt}
+
+
+def fp64_single_leg(mb, probs, steps=6):
+    """The plain FP64 path one instance at a time (largest, median and
+    smallest grid of the workload): cell-updates/s, for the speedup of the
+    FP32 batched form."""
+    import torch
+    pick = sorted(probs, key=lambda q: q.nx * q.ny)
+    pick = [pick[-1], pick[len(pick) // 2], pick[0]]
+    cells, ms = 0, 0.0
+    for p in pick:
+        sim = mb.Sim([p], mb.FP64)
+        st = torch.cuda.Stream()
+        sim.set_stream(st.cuda_stream)
+        sim.run(2, 0.0)
+        sim.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        sim.run(steps, 0.0)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms += e0.elapsed_time(e1)
+        cells += p.nx * p.ny * 2 * steps
+        sim.close()
+    return {"value": cells / (ms * 1e-3), "unit": UNIT,
+            "sample": "%d steps each of %s, one instance per sim, FP64 throughout" % (steps, ", ".join(p.name for p in pick))}
+
+
 def workload(rank, args):
     from paper_1711_11361_gb300 import inputs
     if args.workload == "c4":
@@ -199,6 +265,7 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true", help="skip the FP32-vs-FP64 and FP64 single-instance legs")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -296,6 +363,11 @@ def main():
                 "steps": e2e_steps},
         "gpu_launches": 16 * args.steps,
     }
+    if args.workload == "c4" and not args.no_accuracy:
+        line["accuracy"] = accuracy_leg(mb, probs)
+        f64 = fp64_single_leg(mb, probs)
+        line["fp64_single_instance"] = f64
+        line["speedup_vs_fp64_single_instance"] = value / f64["value"]
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(probs)
     print(json.dumps(line))

@@ -26,6 +26,8 @@
 #ifndef MB_H
 #define MB_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -157,6 +159,62 @@ int mb_band_record_size(void);
  * count since timing was enabled (synchronises). */
 mb_status mb_enable_timing(mb_sim *sim, int enable);
 mb_status mb_kernel_time(mb_sim *sim, double *total_ms, int *launches);
+
+/* Add one instance to a batch between steps (not between the two sweeps of
+ * a step); it gets the next index, with state undefined until mb_write_state.
+ * It takes the batch's current sweep order (x first when the batch has taken
+ * an even number of steps since its last mb_write_state of instance 0).
+ * Same checks as mb_batch_create; precision and equation must be the batch's.
+ * The other instances keep their device-resident state. */
+mb_status mb_batch_add(mb_sim *sim, const mb_grid *grid, double gamma, const mb_body *body,
+                       const mb_motion *motion, int *inst);
+
+/* Remove instance inst between steps, releasing its device memory; the
+ * instances after it move down one index. */
+mb_status mb_batch_remove(mb_sim *sim, int inst);
+
+/* Device bytes instance inst holds (its buffers and its share of the batch's
+ * shared arrays); 0 for a bad index. */
+size_t mb_instance_bytes(const mb_sim *sim, int inst);
+
+/* The same figure for an instance not yet created (0 if the description is
+ * invalid); allocates nothing. */
+size_t mb_request_bytes(const mb_grid *grid, const mb_body *body, const mb_motion *motion);
+
+/* ---- request loop (continuous batching; not a construct of the paper) ----
+ * A server keeps one batch.  Submitted requests queue; mb_server_tick admits
+ * queued requests (first come, first served) while the device-memory budget
+ * and the slot limit allow, advances every admitted simulation by one CFL
+ * step in the batch's shared launches, and retires those that reached their
+ * step count: the final state goes to the request's Qout and the memory is
+ * released for the next requests.  Admission waits for an even batch step so
+ * that each simulation alternates its sweep order exactly as it would alone;
+ * a request's result is therefore the same alone and in any mix. */
+typedef struct mb_server mb_server;
+
+typedef struct {
+    mb_grid grid;               /* precision and equation must be the server's */
+    double gamma;
+    mb_body body;               /* copied at submit */
+    mb_motion motion;
+    const double *Q0;           /* initial state, nc*nx*ny host doubles (copied at submit) */
+    double t0;                  /* time of Q0 (body posed at t0) */
+    int nsteps;                 /* CFL steps to take */
+    double *Qout;               /* final state, nc*nx*ny host doubles, caller-owned,
+                                   written by the tick that retires the request; may be NULL */
+} mb_request;
+
+mb_status mb_server_create(int precision, int equation, double budget_bytes, int max_active, mb_server **out);
+void mb_server_destroy(mb_server *srv);
+const char *mb_server_last_error(const mb_server *srv);
+mb_status mb_server_submit(mb_server *srv, const mb_request *req, int *id);
+/* One tick (admit, step, retire).  Outputs (optional): simulations on the
+ * device, requests waiting, requests finished (including failed ones). */
+mb_status mb_server_tick(mb_server *srv, int *n_active, int *n_queued, int *n_done);
+/* state: 0 queued, 1 running, 2 done, < 0 the mb_status it failed with;
+ * info (optional, 5 doubles): submit, admit and completion times (seconds,
+ * host steady clock), steps taken, device bytes held while running. */
+mb_status mb_server_query(mb_server *srv, int id, int *state, double *info);
 
 /* Allocation-free cut-cell classification (the paper has no counterpart: it
  * exists for callers that may not allocate device memory -- code running

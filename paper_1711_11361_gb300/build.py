@@ -24,6 +24,7 @@ UNITS = {
     "mb_geom.cu": ["-fmad=false"],
     "mb_sweep.cu": ["--ftz=true", "--prec-div=false", "--prec-sqrt=false"],
     "mb_api.cu": [],
+    "mb_server.cu": [],
 }
 
 

@@ -48,10 +48,24 @@ using namespace mb;
 
 static std::string g_create_error;
 
+// host copy of an instance's body and the device buffers it owns
+struct InstHost {
+    std::vector<double> vx, vy;
+    std::vector<unsigned char> mov;
+    std::vector<int> next;        // next vertex of each edge, instance-local
+    std::vector<void *> allocs;   // state buffers, classes, record index, alpha, grid lines
+};
+
 struct mb_sim {
     int n = 0;
     int prec = MB_FP64;
+    int eq = MB_EULER;
+    int nsm = 0;
     std::vector<InstDesc> hd;
+    std::vector<InstHost> ih;
+    // capacities (elements) of the shared arrays below
+    size_t cap_vx = 0, cap_vy = 0, cap_mov = 0, cap_next = 0, cap_px = 0, cap_py = 0, cap_ebox = 0;
+    size_t cap_rec = 0, cap_bnd = 0, cap_scr = 0, cap_dd = 0, cap_dy = 0, cap_ginst = 0;
     InstDesc *dd = nullptr;
     InstDyn *dy = nullptr;
     double *vx = nullptr, *vy = nullptr, *px = nullptr, *py = nullptr;
@@ -69,7 +83,6 @@ struct mb_sim {
     int *ginst = nullptr;         // instance of each geometry group
     int total_tiles[2] = {0, 0};
     int bulk_grid[2] = {0, 0};
-    std::vector<void *> allocs;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int cur = 0;          // buffer holding the latest state (between steps)
@@ -95,24 +108,49 @@ static mb_status cuda_check(mb_sim *s, cudaError_t e, const char *what) {
     return fail(s, e == cudaErrorMemoryAllocation ? MB_E_NOMEM : MB_E_CUDA, m);
 }
 
+// device buffer owned by one instance (freed with it)
 template <class P>
-static cudaError_t dalloc(mb_sim *s, P **p, size_t bytes) {
+static cudaError_t ialloc(InstHost &h, P **p, size_t bytes) {
     void *v = nullptr;
     cudaError_t e = cudaMalloc(&v, bytes ? bytes : 16);
     if (e == cudaSuccess) {
-        s->allocs.push_back(v);
+        h.allocs.push_back(v);
         *p = (P *)v;
     }
     return e;
 }
 
-static void free_all(mb_sim *s) {
+// shared array: reallocated (contents dropped) when it must grow
+template <class P>
+static cudaError_t ensure(P **p, size_t &cap, size_t need, size_t elem) {
+    if (*p && cap >= need) return cudaSuccess;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    size_t n = std::max<size_t>(need + need / 4, 1);
+    void *v = nullptr;
+    cudaError_t e = cudaMalloc(&v, n * elem);
+    if (e != cudaSuccess) { cap = 0; return e; }
+    *p = (P *)v;
+    cap = n;
+    return cudaSuccess;
+}
+
+static void drop_graphs(mb_sim *s) {
     for (auto &kv : s->graphs) cudaGraphExecDestroy(kv.second);
     s->graphs.clear();
+}
+
+static void free_all(mb_sim *s) {
+    drop_graphs(s);
     for (auto &e : s->evs) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
     s->evs.clear();
-    for (void *p : s->allocs) cudaFree(p);
-    s->allocs.clear();
+    for (auto &h : s->ih)
+        for (void *p : h.allocs) cudaFree(p);
+    s->ih.clear();
+    void *shared[] = {s->dd, s->dy, s->vx, s->vy, s->px, s->py, s->ebox, s->vmov, s->vnext,
+                      s->rec, s->bnd, s->scratch, s->stage, s->ginst};
+    for (void *p : shared)
+        if (p) cudaFree(p);
     if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
     s->stream = nullptr;
 }
@@ -138,46 +176,228 @@ extern "C" {
 
 const char *mb_last_error(const mb_sim *sim) { return sim ? sim->err.c_str() : g_create_error.c_str(); }
 
+// checks of one instance against the batch's precision and equation
+static const char *check_instance(const mb_grid &g, const mb_body &b, int prec, int eq) {
+    if (g.nx < 8 || g.ny < 8 || g.nx > 16384 || g.ny > 8192) return "grid size out of range";
+    if (!(g.x1 > g.x0) || !(g.y1 > g.y0)) return "empty domain";
+    if ((g.bc[0] == MB_BC_PERIODIC) != (g.bc[1] == MB_BC_PERIODIC) ||
+        (g.bc[2] == MB_BC_PERIODIC) != (g.bc[3] == MB_BC_PERIODIC))
+        return "periodic boundaries must come in pairs";
+    if (g.equation != MB_EULER && g.equation != MB_ADVECTION) return "unknown equation";
+    if (g.precision != prec) return "all instances of a batch share one precision";
+    if (g.equation != eq) return "all instances of a batch share one equation";
+    if (!(g.cfl > 0.0 && g.cfl <= 1.0)) return "cfl must be in (0, 1]";
+    if (b.npoly < 0 || (b.npoly > 0 && (!b.poly_start || !b.poly_moving || !b.vx || !b.vy))) return "bad body";
+    for (int p = 0; p < b.npoly; ++p)
+        if (b.poly_start[p + 1] - b.poly_start[p] < 3) return "polygon with < 3 vertices";
+    return nullptr;
+}
+
+// descriptor of one instance (device pointers and offsets into the shared
+// arrays are set by make_instance and relayout)
+static void describe_instance(int prec, const mb_grid &g, double gamma, const mb_body &b, const mb_motion &m,
+                              InstDesc &I, InstHost &h) {
+    memset(&I, 0, sizeof(I));
+    I.nx = g.nx; I.ny = g.ny;
+    I.pitch = (g.nx + 31) / 32 * 32;
+    I.nc = g.equation == MB_EULER ? 4 : 1;
+    I.x0 = g.x0; I.y0 = g.y0;
+    I.dx = (g.x1 - g.x0) / (double)g.nx;
+    I.dy = (g.y1 - g.y0) / (double)g.ny;
+    I.rdx = 1.0 / I.dx;
+    I.rdy = 1.0 / I.dy;
+    I.rdxf = (float)I.rdx;
+    I.rdyf = (float)I.rdy;
+    for (int q = 0; q < 4; ++q) I.bc[q] = g.bc[q];
+    I.eq = g.equation;
+    I.ucov = g.uncover_mode;
+    I.adv[0] = g.adv[0]; I.adv[1] = g.adv[1];
+    I.gamma = gamma;
+    I.cfl = g.cfl;
+    I.U[0] = m.U[0]; I.U[1] = m.U[1];
+    I.pivot[0] = m.pivot[0]; I.pivot[1] = m.pivot[1];
+    I.a0 = m.a0; I.a1 = m.a1; I.omega = m.omega;
+    I.rotating = (m.a0 != 0.0 || m.a1 != 0.0) ? 1 : 0;
+    I.nv = b.npoly > 0 ? b.poly_start[b.npoly] : 0;
+    double rmax = 0.0, perim = 0.0, bx0 = 1e300, bx1 = -1e300;
+    bool has_static = false;
+    for (int p = 0; p < b.npoly; ++p) {
+        int a = b.poly_start[p], z = b.poly_start[p + 1];
+        if (!b.poly_moving[p]) has_static = true;
+        for (int v = a; v < z; ++v) {
+            int w = v + 1 < z ? v + 1 : a;
+            h.vx.push_back(b.vx[v]);
+            h.vy.push_back(b.vy[v]);
+            h.mov.push_back(b.poly_moving[p] ? 1 : 0);
+            h.next.push_back(w);
+            perim += std::hypot(b.vx[w] - b.vx[v], b.vy[w] - b.vy[v]);
+            bx0 = std::min(bx0, b.vx[v]);
+            bx1 = std::max(bx1, b.vx[v]);
+            if (b.poly_moving[p]) rmax = std::max(rmax, std::hypot(b.vx[v] - m.pivot[0], b.vy[v] - m.pivot[1]));
+        }
+    }
+    double wr = std::fabs(m.a1 * m.omega) * rmax;
+    I.wall_bound[0] = std::fabs(m.U[0]) + wr;
+    I.wall_bound[1] = std::fabs(m.U[1]) + wr;
+    double hh = std::min(I.dx, I.dy);
+    long long cap = 4LL * (long long)std::ceil(perim / hh) + 2LL * I.nv + 1024;
+    if (I.rotating) cap *= 2;
+    cap = std::min<long long>(cap, (long long)g.nx * g.ny);
+    I.rec_cap = (int)cap;
+    int gcols = g.nx;
+    if (!has_static && I.nv > 0) {
+        double width = I.rotating ? 2.0 * rmax : (bx1 - bx0);
+        gcols = std::min(g.nx, (int)std::ceil(width / I.dx) + 8);
+    }
+    if (I.nv == 0) gcols = 0;
+    I.gcol_max = gcols;
+    // bulk work items: x sweep one warp per row; y sweep one warp per 32
+    // columns (64 for the FP32 Euler kernel that carries two columns per
+    // thread) and 64-row segment
+    I.tiles_x[0] = 1;
+    I.ntiles[0] = g.ny;
+    const int ycols = (prec == MB_FP32 && g.equation == MB_EULER) ? 64 : 32;
+    I.tiles_x[1] = (g.nx + ycols - 1) / ycols;
+    I.ntiles[1] = I.tiles_x[1] * ((g.ny + 63) / 64);
+}
+
+// descriptor and device buffers of one instance
+static cudaError_t make_instance(mb_sim *s, const mb_grid &g, double gamma, const mb_body &b, const mb_motion &m,
+                                 InstDesc &I, InstHost &h) {
+    describe_instance(s->prec, g, gamma, b, m, I, h);
+    const size_t esz = s->prec == MB_FP32 ? 4 : 8;
+    const size_t cells = (size_t)I.pitch * g.ny;
+    cudaError_t e = cudaSuccess;
+    for (int bb = 0; bb < 3 && e == cudaSuccess; ++bb) e = ialloc(h, &I.Q[bb], cells * I.nc * esz);
+    if (e == cudaSuccess) e = ialloc(h, &I.cls, cells);
+    if (e == cudaSuccess) e = ialloc(h, &I.rec, cells * sizeof(int));
+    if (e == cudaSuccess) e = ialloc(h, &I.alpha, cells * sizeof(double));
+    double *xn = nullptr, *yn = nullptr;
+    if (e == cudaSuccess) e = ialloc(h, &xn, (g.nx + 1) * sizeof(double));
+    if (e == cudaSuccess) e = ialloc(h, &yn, (g.ny + 1) * sizeof(double));
+    I.xn = xn;
+    I.yn = yn;
+    if (e == cudaSuccess) e = cudaMemsetAsync(I.cls, 0, cells, s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(I.rec, 0xff, cells * sizeof(int), s->stream);
+    return e;
+}
+
+// device bytes an instance holds (its own buffers and its share of the
+// shared arrays), for admission by memory budget
+static size_t instance_bytes(const InstDesc &I, int prec) {
+    const size_t esz = prec == MB_FP32 ? 4 : 8;
+    const size_t cells = (size_t)I.pitch * I.ny;
+    return 3 * cells * I.nc * esz + cells * (1 + 4 + 8) + (size_t)(I.nx + I.ny + 2) * 8 +
+           (size_t)I.rec_cap * (sizeof(BandRec) + 8) + (size_t)I.nv * 100 + sizeof(InstDesc) + sizeof(InstDyn) +
+           2 * MIXCAP_HOST * sizeof(int) + (size_t)I.nx * I.ny * I.nc * 8;
+}
+
+// offsets of every instance in the shared arrays, those arrays, the
+// descriptors and the instance of every geometry group; the dynamic state of
+// new instance k is the old instance from[k]'s (zero when from[k] < 0).  The
+// stream must be idle.
+static cudaError_t relayout(mb_sim *s, int old_n, const std::vector<int> &from) {
+    const int n = (int)s->hd.size();
+    std::vector<InstDyn> old(old_n), dyn(n);
+    cudaError_t e = cudaSuccess;
+    if (old_n > 0) e = cudaMemcpy(old.data(), s->dy, old_n * sizeof(InstDyn), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return e;
+    for (int k = 0; k < n; ++k) {
+        if (from[k] >= 0) dyn[k] = old[from[k]];
+        else memset(&dyn[k], 0, sizeof(InstDyn));
+    }
+    std::vector<double> hvx, hvy;
+    std::vector<unsigned char> hmov;
+    std::vector<int> hnext;
+    int rec_total = 0, tiles0 = 0, tiles1 = 0;
+    size_t max_cells = 1;
+    for (int k = 0; k < n; ++k) {
+        InstDesc &I = s->hd[k];
+        const InstHost &h = s->ih[k];
+        I.voff = (int)hvx.size();
+        hvx.insert(hvx.end(), h.vx.begin(), h.vx.end());
+        hvy.insert(hvy.end(), h.vy.begin(), h.vy.end());
+        hmov.insert(hmov.end(), h.mov.begin(), h.mov.end());
+        for (int w : h.next) hnext.push_back(I.voff + w);
+        I.rec_base = rec_total;
+        rec_total += I.rec_cap;
+        I.tile_off[0] = tiles0;
+        I.tile_off[1] = tiles1;
+        tiles0 += I.ntiles[0];
+        tiles1 += I.ntiles[1];
+        max_cells = std::max(max_cells, (size_t)I.nx * I.ny);
+    }
+    // geometry groups (GEO_GC columns, one CTA each): instances with more
+    // polygon vertices first, so that the groups with the most cut cells start
+    // in the first wave of CTAs
+    std::vector<int> order(n), ginst;
+    for (int k = 0; k < n; ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return s->hd[a].nv > s->hd[b].nv; });
+    int col_total = 0;
+    for (int k : order) {
+        InstDesc &I = s->hd[k];
+        I.gcol_off = col_total;
+        const int ng = (I.gcol_max + GEO_GC - 1) / GEO_GC;
+        for (int q = 0; q < ng; ++q) ginst.push_back(k);
+        col_total += ng;
+    }
+    const size_t tv = std::max<size_t>(1, hvx.size());
+    if (e == cudaSuccess) e = ensure(&s->vx, s->cap_vx, tv, sizeof(double));
+    if (e == cudaSuccess) e = ensure(&s->vy, s->cap_vy, tv, sizeof(double));
+    if (e == cudaSuccess) e = ensure(&s->vmov, s->cap_mov, tv, 1);
+    if (e == cudaSuccess) e = ensure(&s->vnext, s->cap_next, tv, sizeof(int));
+    if (e == cudaSuccess) e = ensure(&s->px, s->cap_px, 3 * tv, sizeof(double));
+    if (e == cudaSuccess) e = ensure(&s->py, s->cap_py, 3 * tv, sizeof(double));
+    if (e == cudaSuccess) e = ensure(&s->ebox, s->cap_ebox, 3 * tv * 2, sizeof(float));
+    if (e == cudaSuccess) e = ensure(&s->rec, s->cap_rec, std::max(1, rec_total), sizeof(BandRec));
+    if (e == cudaSuccess) e = ensure(&s->bnd, s->cap_bnd, std::max(1, rec_total), sizeof(double));
+    if (e == cudaSuccess) e = ensure(&s->scratch, s->cap_scr, (size_t)std::max(1, n) * 2 * MIXCAP_HOST, sizeof(int));
+    if (e == cudaSuccess) e = ensure(&s->stage, s->stage_len, max_cells * 4, sizeof(double));
+    if (e == cudaSuccess) e = ensure(&s->dd, s->cap_dd, std::max(1, n), sizeof(InstDesc));
+    if (e == cudaSuccess) e = ensure(&s->dy, s->cap_dy, std::max(1, n), sizeof(InstDyn));
+    if (e == cudaSuccess) e = ensure(&s->ginst, s->cap_ginst, std::max<size_t>(1, ginst.size()), sizeof(int));
+    if (e != cudaSuccess) return e;
+    // the posed vertices of pose slot 0 are refreshed by every classification;
+    // the other slots by every sweep
+    if (!hvx.empty()) {
+        e = cudaMemcpy(s->vx, hvx.data(), hvx.size() * sizeof(double), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(s->vy, hvy.data(), hvy.size() * sizeof(double), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(s->vmov, hmov.data(), hmov.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(s->vnext, hnext.data(), hnext.size() * sizeof(int), cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess && n > 0) e = cudaMemcpy(s->dd, s->hd.data(), n * sizeof(InstDesc), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && n > 0) e = cudaMemcpy(s->dy, dyn.data(), n * sizeof(InstDyn), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !ginst.empty())
+        e = cudaMemcpy(s->ginst, ginst.data(), ginst.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return e;
+    s->n = n;
+    s->total_v = (int)hvx.size();
+    s->total_rec = rec_total;
+    s->total_cols = col_total;
+    s->total_tiles[0] = tiles0;
+    s->total_tiles[1] = tiles1;
+    drop_graphs(s);
+    return cudaSuccess;
+}
+
+// classes and volume fractions of instance k at its current pose
+static void classify_instance(mb_sim *s, int k, double *alpha_out) {
+    launch_classify(s->dd, s->dy, s->vx, s->vy, s->vmov, s->px, s->py, s->ebox, s->vnext, s->total_v, k, s->hd[k].nx,
+                    alpha_out, s->stream);
+}
+
 mb_status mb_batch_create(int n, const mb_grid *grids, const double *gammas, const mb_body *bodies,
                           const mb_motion *motions, mb_sim **out) {
     if (!out) return fail(nullptr, MB_E_INVAL, "out is NULL");
     *out = nullptr;
     if (n < 1 || !grids || !bodies || !motions) return fail(nullptr, MB_E_INVAL, "bad batch arguments");
-    int prec = grids[0].precision;
     for (int k = 0; k < n; ++k) {
-        const mb_grid &g = grids[k];
-        if (g.nx < 8 || g.ny < 8 || g.nx > 16384 || g.ny > 8192) return fail(nullptr, MB_E_INVAL, "grid size out of range");
-        if (!(g.x1 > g.x0) || !(g.y1 > g.y0)) return fail(nullptr, MB_E_INVAL, "empty domain");
-        if ((g.bc[0] == MB_BC_PERIODIC) != (g.bc[1] == MB_BC_PERIODIC) ||
-            (g.bc[2] == MB_BC_PERIODIC) != (g.bc[3] == MB_BC_PERIODIC))
-            return fail(nullptr, MB_E_INVAL, "periodic boundaries must come in pairs");
-        if (g.equation != MB_EULER && g.equation != MB_ADVECTION) return fail(nullptr, MB_E_INVAL, "unknown equation");
-        if (g.precision != prec) return fail(nullptr, MB_E_INVAL, "all instances of a batch share one precision");
-        if (g.equation != grids[0].equation) return fail(nullptr, MB_E_INVAL, "all instances of a batch share one equation");
-        if (!(g.cfl > 0.0 && g.cfl <= 1.0)) return fail(nullptr, MB_E_INVAL, "cfl must be in (0, 1]");
-        const mb_body &b = bodies[k];
-        if (b.npoly < 0 || (b.npoly > 0 && (!b.poly_start || !b.poly_moving || !b.vx || !b.vy)))
-            return fail(nullptr, MB_E_INVAL, "bad body");
-        for (int p = 0; p < b.npoly; ++p)
-            if (b.poly_start[p + 1] - b.poly_start[p] < 3) return fail(nullptr, MB_E_INVAL, "polygon with < 3 vertices");
+        const char *msg = check_instance(grids[k], bodies[k], grids[0].precision, grids[0].equation);
+        if (msg) return fail(nullptr, MB_E_INVAL, msg);
     }
     mb_sim *s = new mb_sim();
-    s->n = n;
-    s->prec = prec;
-    const size_t esz = prec == MB_FP32 ? 4 : 8;
-    cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
-    if (e != cudaSuccess) { mb_status st = cuda_check(s, e, "stream"); g_create_error = s->err; delete s; return st; }
-    s->own_stream = true;
-    int dev = 0, nsm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    // vertices
-    std::vector<double> hvx, hvy;
-    std::vector<unsigned char> hmov;
-    std::vector<int> hnext;
-    s->hd.resize(n);
-    size_t max_cells = 0;
-    int rec_total = 0, col_total = 0, tiles0 = 0, tiles1 = 0;
+    s->prec = grids[0].precision;
+    s->eq = grids[0].equation;
 #define CK(x)                                                     \
     do {                                                          \
         cudaError_t _e = (x);                                     \
@@ -189,160 +409,95 @@ mb_status mb_batch_create(int n, const mb_grid *grids, const double *gammas, con
             return _st;                                           \
         }                                                         \
     } while (0)
-    for (int k = 0; k < n; ++k) {
-        const mb_grid &g = grids[k];
-        const mb_body &b = bodies[k];
-        const mb_motion &m = motions[k];
-        InstDesc &I = s->hd[k];
-        memset(&I, 0, sizeof(I));
-        I.nx = g.nx; I.ny = g.ny;
-        I.pitch = (g.nx + 31) / 32 * 32;
-        I.nc = g.equation == MB_EULER ? 4 : 1;
-        I.x0 = g.x0; I.y0 = g.y0;
-        I.dx = (g.x1 - g.x0) / (double)g.nx;
-        I.dy = (g.y1 - g.y0) / (double)g.ny;
-        I.rdx = 1.0 / I.dx;
-        I.rdy = 1.0 / I.dy;
-        I.rdxf = (float)I.rdx;
-        I.rdyf = (float)I.rdy;
-        for (int q = 0; q < 4; ++q) I.bc[q] = g.bc[q];
-        I.eq = g.equation;
-        I.ucov = g.uncover_mode;
-        I.adv[0] = g.adv[0]; I.adv[1] = g.adv[1];
-        I.gamma = gammas ? gammas[k] : 1.4;
-        I.cfl = g.cfl;
-        I.U[0] = m.U[0]; I.U[1] = m.U[1];
-        I.pivot[0] = m.pivot[0]; I.pivot[1] = m.pivot[1];
-        I.a0 = m.a0; I.a1 = m.a1; I.omega = m.omega;
-        I.rotating = (m.a0 != 0.0 || m.a1 != 0.0) ? 1 : 0;
-        I.voff = (int)hvx.size();
-        I.nv = b.npoly > 0 ? b.poly_start[b.npoly] : 0;
-        double rmax = 0.0, perim = 0.0, bx0 = 1e300, bx1 = -1e300;
-        bool has_static = false;
-        for (int p = 0; p < b.npoly; ++p) {
-            int a = b.poly_start[p], z = b.poly_start[p + 1];
-            if (!b.poly_moving[p]) has_static = true;
-            for (int v = a; v < z; ++v) {
-                int w = v + 1 < z ? v + 1 : a;
-                hvx.push_back(b.vx[v]);
-                hvy.push_back(b.vy[v]);
-                hmov.push_back(b.poly_moving[p] ? 1 : 0);
-                hnext.push_back(I.voff + w);
-                perim += std::hypot(b.vx[w] - b.vx[v], b.vy[w] - b.vy[v]);
-                bx0 = std::min(bx0, b.vx[v]);
-                bx1 = std::max(bx1, b.vx[v]);
-                if (b.poly_moving[p]) rmax = std::max(rmax, std::hypot(b.vx[v] - m.pivot[0], b.vy[v] - m.pivot[1]));
-            }
-        }
-        double wr = std::fabs(m.a1 * m.omega) * rmax;
-        I.wall_bound[0] = std::fabs(m.U[0]) + wr;
-        I.wall_bound[1] = std::fabs(m.U[1]) + wr;
-        double h = std::min(I.dx, I.dy);
-        long long cap = 4LL * (long long)std::ceil(perim / h) + 2LL * I.nv + 1024;
-        if (I.rotating) cap *= 2;
-        cap = std::min<long long>(cap, (long long)g.nx * g.ny);
-        I.rec_cap = (int)cap;
-        I.rec_base = rec_total;
-        rec_total += I.rec_cap;
-        int gcols = g.nx;
-        if (!has_static && I.nv > 0) {
-            double width = I.rotating ? 2.0 * rmax : (bx1 - bx0);
-            gcols = std::min(g.nx, (int)std::ceil(width / I.dx) + 8);
-        }
-        if (I.nv == 0) gcols = 0;
-        I.gcol_max = gcols;
-        // bulk work items: x sweep one warp per row; y sweep one warp per 32
-        // columns and 64-row segment
-        I.tiles_x[0] = 1;
-        I.ntiles[0] = g.ny;
-        // y sweep: 32 columns per warp, 64 for the FP32 Euler kernel that
-        // carries two columns per thread
-        const int ycols = (prec == MB_FP32 && g.equation == MB_EULER) ? 64 : 32;
-        I.tiles_x[1] = (g.nx + ycols - 1) / ycols;
-        I.ntiles[1] = I.tiles_x[1] * ((g.ny + 63) / 64);
-        I.tile_off[0] = tiles0;
-        I.tile_off[1] = tiles1;
-        tiles0 += I.ntiles[0];
-        tiles1 += I.ntiles[1];
-        size_t cells = (size_t)I.pitch * g.ny;
-        for (int bb = 0; bb < 3; ++bb) CK(dalloc(s, &I.Q[bb], cells * I.nc * esz));
-        CK(dalloc(s, &I.cls, cells));
-        CK(dalloc(s, &I.rec, cells * sizeof(int)));
-        CK(dalloc(s, &I.alpha, cells * sizeof(double)));
-        {
-            double *xn = nullptr, *yn = nullptr;
-            CK(dalloc(s, &xn, (g.nx + 1) * sizeof(double)));
-            CK(dalloc(s, &yn, (g.ny + 1) * sizeof(double)));
-            I.xn = xn;
-            I.yn = yn;
-        }
-        CK(cudaMemsetAsync(I.cls, 0, cells, s->stream));
-        CK(cudaMemsetAsync(I.rec, 0xff, cells * sizeof(int), s->stream));
-        max_cells = std::max(max_cells, (size_t)g.nx * g.ny);
-    }
-    // geometry groups (GEO_GC columns, one CTA each): instances with more
-    // polygon vertices first, so that the groups with the most cut cells start
-    // in the first wave of CTAs
-    {
-        std::vector<int> order(n);
-        for (int k = 0; k < n; ++k) order[k] = k;
-        std::stable_sort(order.begin(), order.end(),
-                         [&](int a, int b) { return s->hd[a].nv > s->hd[b].nv; });
-        std::vector<int> ginst;
-        for (int k : order) {
-            InstDesc &I = s->hd[k];
-            I.gcol_off = col_total;
-            const int ng = (I.gcol_max + GEO_GC - 1) / GEO_GC;
-            for (int q = 0; q < ng; ++q) ginst.push_back(k);
-            col_total += ng;
-        }
-        CK(dalloc(s, &s->ginst, std::max<size_t>(1, ginst.size()) * sizeof(int)));
-        if (!ginst.empty())
-            CK(cudaMemcpy(s->ginst, ginst.data(), ginst.size() * sizeof(int), cudaMemcpyHostToDevice));
-    }
-    s->total_v = (int)hvx.size();
-    s->total_rec = rec_total;
-    s->total_cols = col_total;
-    s->total_tiles[0] = tiles0;
-    s->total_tiles[1] = tiles1;
-    int tv = std::max(1, s->total_v);
-    CK(dalloc(s, &s->vx, tv * sizeof(double)));
-    CK(dalloc(s, &s->vy, tv * sizeof(double)));
-    CK(dalloc(s, &s->vmov, tv));
-    CK(dalloc(s, &s->vnext, tv * sizeof(int)));
-    CK(dalloc(s, &s->px, 3 * (size_t)tv * sizeof(double)));
-    CK(dalloc(s, &s->py, 3 * (size_t)tv * sizeof(double)));
-    CK(dalloc(s, &s->ebox, 3 * (size_t)tv * 2 * sizeof(float)));
+    CK(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
+    s->own_stream = true;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&s->nsm, cudaDevAttrMultiProcessorCount, dev);
+    s->hd.resize(n);
+    s->ih.resize(n);
+    for (int k = 0; k < n; ++k)
+        CK(make_instance(s, grids[k], gammas ? gammas[k] : 1.4, bodies[k], motions[k], s->hd[k], s->ih[k]));
+    CK(cudaStreamSynchronize(s->stream));
     geom_init();
-    if (s->total_v) {
-        CK(cudaMemcpy(s->vx, hvx.data(), s->total_v * sizeof(double), cudaMemcpyHostToDevice));
-        CK(cudaMemcpy(s->vy, hvy.data(), s->total_v * sizeof(double), cudaMemcpyHostToDevice));
-        CK(cudaMemcpy(s->vmov, hmov.data(), s->total_v, cudaMemcpyHostToDevice));
-        CK(cudaMemcpy(s->vnext, hnext.data(), s->total_v * sizeof(int), cudaMemcpyHostToDevice));
-    }
-    CK(dalloc(s, &s->rec, std::max(1, s->total_rec) * sizeof(BandRec)));
-    CK(dalloc(s, &s->bnd, std::max(1, s->total_rec) * sizeof(double)));
-    CK(dalloc(s, &s->scratch, (size_t)n * 2 * MIXCAP_HOST * sizeof(int)));
-    s->stage_len = max_cells * 4;
-    CK(dalloc(s, &s->stage, s->stage_len * sizeof(double)));
-    CK(dalloc(s, &s->dd, n * sizeof(InstDesc)));
-    CK(dalloc(s, &s->dy, n * sizeof(InstDyn)));
-    CK(cudaMemcpy(s->dd, s->hd.data(), n * sizeof(InstDesc), cudaMemcpyHostToDevice));
-    CK(cudaMemset(s->dy, 0, n * sizeof(InstDyn)));
+    CK(relayout(s, 0, std::vector<int>(n, -1)));
     launch_nodes(s->dd, n, s->stream);
     for (int d = 0; d < 2; ++d) {
-        int bps = prec == MB_FP32 ? bulk_blocks_per_sm<float>(d) : bulk_blocks_per_sm<double>(d);
-        s->bulk_grid[d] = bps * nsm;
+        int bps = s->prec == MB_FP32 ? bulk_blocks_per_sm<float>(d) : bulk_blocks_per_sm<double>(d);
+        s->bulk_grid[d] = bps * s->nsm;
     }
     // initial classes at t = 0
-    for (int k = 0; k < n; ++k)
-        launch_classify(s->dd, s->dy, s->vx, s->vy, s->vmov, s->px, s->py, s->ebox, s->vnext, s->total_v, k,
-                        s->hd[k].nx, nullptr, s->stream);
+    for (int k = 0; k < n; ++k) classify_instance(s, k, nullptr);
     CK(cudaStreamSynchronize(s->stream));
     CK(cudaGetLastError());
 #undef CK
     *out = s;
     return MB_OK;
+}
+
+mb_status mb_batch_add(mb_sim *sim, const mb_grid *grid, double gamma, const mb_body *body, const mb_motion *motion,
+                       int *inst) {
+    if (!sim || !grid || !body || !motion) return MB_E_INVAL;
+    if (sim->sidx != 0) return fail(sim, MB_E_STATE, "mb_batch_add in the middle of a step");
+    const char *msg = check_instance(*grid, *body, sim->prec, sim->eq);
+    if (msg) return fail(sim, MB_E_INVAL, msg);
+    cudaError_t e = cudaStreamSynchronize(sim->stream);
+    if (e != cudaSuccess) return cuda_check(sim, e, "batch_add sync");
+    const int old_n = sim->n;
+    InstDesc I;
+    InstHost h;
+    e = make_instance(sim, *grid, gamma, *body, *motion, I, h);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(sim->stream);
+    if (e != cudaSuccess) {
+        for (void *p : h.allocs) cudaFree(p);
+        return cuda_check(sim, e, "batch_add buffers");
+    }
+    sim->hd.push_back(I);
+    sim->ih.push_back(std::move(h));
+    std::vector<int> from(old_n + 1);
+    for (int k = 0; k < old_n; ++k) from[k] = k;
+    from[old_n] = -1;
+    e = relayout(sim, old_n, from);
+    if (e == cudaSuccess) {
+        launch_nodes(sim->dd, sim->n, sim->stream);
+        classify_instance(sim, old_n, nullptr);
+        e = cudaStreamSynchronize(sim->stream);
+        if (e == cudaSuccess) e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return cuda_check(sim, e, "batch_add");
+    if (inst) *inst = old_n;
+    return MB_OK;
+}
+
+mb_status mb_batch_remove(mb_sim *sim, int inst) {
+    if (!sim || inst < 0 || inst >= sim->n) return MB_E_INVAL;
+    if (sim->sidx != 0) return fail(sim, MB_E_STATE, "mb_batch_remove in the middle of a step");
+    cudaError_t e = cudaStreamSynchronize(sim->stream);
+    if (e != cudaSuccess) return cuda_check(sim, e, "batch_remove sync");
+    const int old_n = sim->n;
+    for (void *p : sim->ih[inst].allocs) cudaFree(p);
+    sim->hd.erase(sim->hd.begin() + inst);
+    sim->ih.erase(sim->ih.begin() + inst);
+    std::vector<int> from(old_n - 1);
+    for (int k = 0; k < old_n - 1; ++k) from[k] = k < inst ? k : k + 1;
+    e = relayout(sim, old_n, from);
+    if (e != cudaSuccess) return cuda_check(sim, e, "batch_remove");
+    if (sim->n == 0) sim->nstep = 0;
+    return MB_OK;
+}
+
+size_t mb_instance_bytes(const mb_sim *sim, int inst) {
+    if (!sim || inst < 0 || inst >= sim->n) return 0;
+    return instance_bytes(sim->hd[inst], sim->prec);
+}
+
+size_t mb_request_bytes(const mb_grid *grid, const mb_body *body, const mb_motion *motion) {
+    if (!grid || !body || !motion) return 0;
+    if (check_instance(*grid, *body, grid->precision, grid->equation)) return 0;
+    InstDesc I;
+    InstHost h;
+    describe_instance(grid->precision, *grid, 1.4, *body, *motion, I, h);
+    return instance_bytes(I, grid->precision);
 }
 
 mb_status mb_create(const mb_grid *grid, double gamma, const mb_body *body, const mb_motion *motion, mb_sim **out) {
@@ -406,7 +561,7 @@ static mb_status do_sweep(mb_sim *s, int dir, double dt) {
         cudaEventCreate(&e1);
         cudaEventRecord(e0, st);
     }
-    const int eq = s->hd[0].eq;
+    const int eq = s->eq;
     if (s->prec == MB_FP32)
         launch_bulk<float>(dir, eq, s->dd, s->dy, s->rec, s->n, s->total_tiles[dir], src, dst, last, st);
     else
@@ -432,12 +587,14 @@ static mb_status do_sweep(mb_sim *s, int dir, double dt) {
 
 mb_status mb_sweep(mb_sim *sim, int dir, double dt) {
     if (!sim) return MB_E_INVAL;
+    if (sim->n == 0) return MB_OK;
     if (dir != 0 && dir != 1) return fail(sim, MB_E_INVAL, "dir must be 0 or 1");
     if (!(dt > 0.0)) return fail(sim, MB_E_INVAL, "mb_sweep needs dt > 0");
     return do_sweep(sim, dir, dt);
 }
 
 static mb_status issue_step(mb_sim *sim, double dt) {
+    if (sim->n == 0) return MB_OK;   // an empty batch (all instances removed)
     int d1 = (sim->nstep % 2 == 0) ? 0 : 1;
     mb_status r = do_sweep(sim, d1, dt);
     if (r != MB_OK) return r;
@@ -461,6 +618,7 @@ mb_status mb_step(mb_sim *sim, double dt, double *dt_used) {
 
 mb_status mb_run(mb_sim *sim, int nsteps, double dt) {
     if (!sim || nsteps < 0) return MB_E_INVAL;
+    if (sim->n == 0) return MB_OK;
     if (sim->sidx != 0) return fail(sim, MB_E_STATE, "mb_run in the middle of a step");
     double dth = dt > 0.0 ? dt : 0.0;
     for (int k = 0; k < nsteps; ++k) {

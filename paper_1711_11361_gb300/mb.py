@@ -23,7 +23,9 @@ FP64, FP32 = 0, 1
 EXPORTS = ["mb_create", "mb_batch_create", "mb_destroy", "mb_last_error", "mb_set_stream", "mb_write_state",
            "mb_read_state", "mb_step", "mb_sweep", "mb_run", "mb_sync", "mb_info", "mb_diagnostics",
            "mb_enable_timing", "mb_kernel_time", "mb_band_records", "mb_band_record_size",
-           "mb_cut_cells_noalloc", "mb_noalloc_last_error"]
+           "mb_cut_cells_noalloc", "mb_noalloc_last_error", "mb_batch_add", "mb_batch_remove", "mb_instance_bytes",
+           "mb_request_bytes", "mb_server_create", "mb_server_destroy", "mb_server_last_error", "mb_server_submit",
+           "mb_server_tick", "mb_server_query"]
 
 
 class Grid(ctypes.Structure):
@@ -42,6 +44,12 @@ class Body(ctypes.Structure):
 class Motion(ctypes.Structure):
     _fields_ = [("U", ctypes.c_double * 2), ("pivot", ctypes.c_double * 2),
                 ("a0", ctypes.c_double), ("a1", ctypes.c_double), ("omega", ctypes.c_double)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("grid", Grid), ("gamma", ctypes.c_double), ("body", Body), ("motion", Motion),
+                ("Q0", ctypes.POINTER(ctypes.c_double)), ("t0", ctypes.c_double), ("nsteps", ctypes.c_int),
+                ("Qout", ctypes.POINTER(ctypes.c_double))]
 
 
 class MBError(RuntimeError):
@@ -78,6 +86,17 @@ def _load():
         "mb_cut_cells_noalloc": ([ctypes.POINTER(Grid), ctypes.POINTER(Body), ctypes.POINTER(Motion), ctypes.c_double,
                                   ctypes.c_double, ctypes.c_double, P, P, P], I),
         "mb_noalloc_last_error": ([], ctypes.c_char_p),
+        "mb_batch_add": ([P, ctypes.POINTER(Grid), ctypes.c_double, ctypes.POINTER(Body), ctypes.POINTER(Motion),
+                          ctypes.POINTER(I)], I),
+        "mb_batch_remove": ([P, I], I),
+        "mb_instance_bytes": ([P, I], ctypes.c_size_t),
+        "mb_request_bytes": ([ctypes.POINTER(Grid), ctypes.POINTER(Body), ctypes.POINTER(Motion)], ctypes.c_size_t),
+        "mb_server_create": ([I, I, ctypes.c_double, I, PP], I),
+        "mb_server_destroy": ([P], None),
+        "mb_server_last_error": ([P], ctypes.c_char_p),
+        "mb_server_submit": ([P, ctypes.POINTER(Request), ctypes.POINTER(I)], I),
+        "mb_server_tick": ([P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)], I),
+        "mb_server_query": ([P, I, ctypes.POINTER(I), D], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -215,6 +234,26 @@ class Sim:
         self._check(lib.mb_kernel_time(self._h, ctypes.byref(ms), ctypes.byref(n)))
         return ms.value, n.value
 
+    def add(self, prob: inputs.Problem, write_initial: bool = True) -> int:
+        """Append an instance between steps (mb_batch_add); returns its index."""
+        g, b, m, keep = _marshal(prob, self.precision)
+        k = ctypes.c_int()
+        self._check(lib.mb_batch_add(self._h, ctypes.byref(g), prob.gamma, ctypes.byref(b), ctypes.byref(m),
+                                     ctypes.byref(k)))
+        self.problems.append(prob)
+        self._keep.append(keep)
+        self.n += 1
+        if write_initial and prob.Q0 is not None:
+            self.write_state(k.value, prob.Q0)
+        return k.value
+
+    def remove(self, inst: int):
+        """Remove an instance between steps (mb_batch_remove); later indices move down."""
+        self._check(lib.mb_batch_remove(self._h, inst))
+        del self.problems[inst]
+        del self._keep[inst]
+        self.n -= 1
+
     def band_records(self, inst=0):
         """Raw band records of the last sweep as a numpy structured array."""
         cnt = ctypes.c_int()
@@ -236,6 +275,64 @@ def cut_cells_noalloc(prob: inputs.Problem, X: float, Y: float, theta: float, al
                                  ctypes.c_void_p(alpha_ptr), ctypes.c_void_p(class_ptr), ctypes.c_void_p(stream))
     if r != MB_OK:
         raise MBError(r, lib.mb_noalloc_last_error().decode())
+
+
+class Server:
+    """Continuous-batching request loop (mb_server_* in include/mb.h)."""
+
+    QUEUED, RUNNING, DONE = 0, 1, 2
+
+    def __init__(self, precision=FP32, equation=0, budget_bytes=32 * 2 ** 30, max_active=64):
+        h = ctypes.c_void_p()
+        r = lib.mb_server_create(precision, equation, float(budget_bytes), max_active, ctypes.byref(h))
+        if r != MB_OK:
+            raise MBError(r, "bad server arguments")
+        self._h = h
+        self.precision = precision
+        self._keep = {}
+        self.out = {}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.mb_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def _check(self, r):
+        if r != MB_OK:
+            raise MBError(r, lib.mb_server_last_error(self._h).decode())
+
+    def submit(self, prob: inputs.Problem, nsteps: int, Q0=None, t0=0.0) -> int:
+        g, b, m, keep = _marshal(prob, self.precision)
+        Q0 = np.ascontiguousarray(prob.Q0 if Q0 is None else Q0, dtype=np.float64)
+        out = np.full((prob.nc, prob.ny, prob.nx), np.nan)
+        req = Request(g, prob.gamma, b, m, _dp(Q0), t0, nsteps, _dp(out))
+        k = ctypes.c_int()
+        self._check(lib.mb_server_submit(self._h, ctypes.byref(req), ctypes.byref(k)))
+        self.out[k.value] = out
+        return k.value
+
+    def tick(self):
+        a, q, d = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self._check(lib.mb_server_tick(self._h, ctypes.byref(a), ctypes.byref(q), ctypes.byref(d)))
+        return a.value, q.value, d.value
+
+    def query(self, rid: int):
+        st = ctypes.c_int()
+        info = np.zeros(5)
+        self._check(lib.mb_server_query(self._h, rid, ctypes.byref(st), _dp(info)))
+        return dict(state=st.value, t_submit=info[0], t_admit=info[1], t_done=info[2], steps=int(info[3]),
+                    bytes=int(info[4]))
+
+    def result(self, rid: int):
+        return self.out[rid]
+
+
+def request_bytes(prob: inputs.Problem, precision=FP32) -> int:
+    g, b, m, keep = _marshal(prob, precision)
+    return int(lib.mb_request_bytes(ctypes.byref(g), ctypes.byref(b), ctypes.byref(m)))
 
 
 BAND_DTYPE = np.dtype([("cell", "i4"), ("i", "i4"), ("j", "i4"), ("flags", "i4"),

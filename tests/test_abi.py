@@ -11,7 +11,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def declared():
     src = open(os.path.join(ROOT, "include", "mb.h")).read()
-    return sorted(set(re.findall(r"^\s*(?:mb_status|void|int|const char \*)\s*(mb_\w+)\s*\(", src, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:mb_status|void|int|size_t|const char \*)\s*(mb_\w+)\s*\(", src, re.M)))
 
 
 def test_header_declares_the_north_star_calls():
