@@ -158,10 +158,13 @@ def accuracy_leg(mb, probs, steps=20):
         r64, r32 = a["Q"][0][fl], b["Q"][0][fl]
         w = al[fl]
         l1.append(float(np.sum(w * np.abs(r32 - r64)) / np.sum(w * np.abs(r64))))
+        # momentum components against the momentum magnitude (one of them
+        # vanishes by symmetry in most instances)
+        mom = np.sum(w * np.hypot(a["Q"][1][fl], a["Q"][2][fl]))
         for q in range(4):
             t64 = np.sum(w * a["Q"][q][fl])
             t32 = np.sum(w * b["Q"][q][fl])
-            scale = np.sum(w * np.abs(a["Q"][q][fl]))
+            scale = mom if q in (1, 2) else np.sum(w * np.abs(a["Q"][q][fl]))
             drift[q] = max(drift[q], abs(t32 - t64) / scale if scale > 0 else 0.0)
     s64.close()
     s32.close()
@@ -196,6 +199,109 @@ def fp64_single_leg(mb, probs, steps=6):
             "sample": "%d steps each of %s, one instance per sim, FP64 throughout" % (steps, ", ".join(p.name for p in pick))}
 
 
+def run_served(args):
+    """Served stream (continuous batching through mb_server_*): a bounded
+    prefix of the seeded request stream (grid sizes, step counts and count
+    set by the --c5-* options), Poisson arrivals at an offered load of
+    --c5-load times the batched throughput measured on the stream's own first
+    requests.  Reports aggregate cell-updates/s over the run, p50/p99
+    completion latency (submission to result on the host), and the serial
+    plain-FP64 time of the same stream extrapolated from a sample."""
+    import torch
+    from paper_1711_11361_gb300 import inputs, mb
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    specs = inputs.c5_requests(n=args.c5_requests, nmin=args.c5_nmin, nmax=args.c5_nmax, smin=args.c5_smin,
+                               smax=args.c5_smax)
+    work = np.array([sp["N"] ** 2 * 2.0 * sp["steps"] for sp in specs])
+    probs = [inputs.make_request(sp) for sp in specs]
+    # batched throughput of the stream's own instances sets the offered rate
+    probe = probs[:16]
+    sim = mb.Sim(probe, mb.FP32)
+    st = torch.cuda.Stream()
+    sim.set_stream(st.cuda_stream)
+    sim.run(3, 0.0)
+    sim.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    sim.run(5, 0.0)
+    e1.record(st)
+    torch.cuda.synchronize()
+    thr = sum(p.nx * p.ny for p in probe) * 2 * 5 / (e0.elapsed_time(e1) * 1e-3)
+    sim.close()
+    mean_gap = float(np.mean(work)) / (args.c5_load * thr)
+    arr = inputs.c5_arrivals(len(specs), mean_gap)
+    srv = mb.Server(mb.FP32, 0, budget_bytes=args.c5_budget_gib * 2 ** 30, max_active=args.c5_max_active)
+    stop = threading.Event()
+    samples = []
+    th = threading.Thread(target=sample_clocks, args=(stop, samples), daemon=True)
+    th.start()
+    ids, k, n = [], 0, len(specs)
+    t0 = time.perf_counter()
+    peak = 0
+    while True:
+        now = time.perf_counter() - t0
+        while k < n and arr[k] <= now:
+            ids.append(srv.submit(probs[k], specs[k]["steps"]))
+            k += 1
+        a, q, d = srv.tick()
+        peak = max(peak, a)
+        if d == n:
+            break
+        if a == 0 and q == 0 and k < n:
+            time.sleep(max(0.0, min(arr[k] - (time.perf_counter() - t0), 0.01)))
+    stop.set()
+    th.join(timeout=2)
+    info = [srv.query(i) for i in ids]
+    failed = sum(1 for x in info if x["state"] != mb.Server.DONE)
+    lat = np.array([x["t_done"] - x["t_submit"] for x in info])
+    span = max(x["t_done"] for x in info) - min(x["t_submit"] for x in info)
+    value = float(work.sum() / span)
+    srv.close()
+    # serial plain FP64: one request at a time, FP64 throughout (sample)
+    sample = sorted(range(n), key=lambda i: specs[i]["N"])
+    sample = [sample[0], sample[n // 2], sample[-1]]
+    cells, ms = 0.0, 0.0
+    for i in sample:
+        s64 = mb.Sim(probs[i], mb.FP64)
+        s64.set_stream(st.cuda_stream)
+        s64.run(1, 0.0)
+        s64.sync()
+        e0.record(st)
+        s64.run(4, 0.0)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms += e0.elapsed_time(e1)
+        cells += probs[i].nx * probs[i].ny * 2 * 4
+        s64.close()
+    rate64 = cells / (ms * 1e-3)
+    serial_s = float(work.sum() / rate64)
+    if rank != 0:
+        return
+    line = {
+        "metric": "cell-updates/s aggregate over a served request stream (continuous batching, FP32 bulk); "
+                  "p50/p99 completion latency",
+        "value": value, "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "c5_served_%d_req_N%d-%d_steps%d-%d" % (n, args.c5_nmin, args.c5_nmax, args.c5_smin,
+                                                                      args.c5_smax),
+                   "arrivals": "Poisson, mean gap %.4g s = %.2f x batched throughput %.3g cell-updates/s"
+                               % (mean_gap, args.c5_load, thr),
+                   "budget_gib": args.c5_budget_gib, "max_active": args.c5_max_active,
+                   "full_stream": "2000 requests, N 256-2048, 500-5000 steps (this run: the bounded prefix above)"},
+        "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                      "mean": float(lat.mean())},
+        "requests": n, "failed": failed, "peak_active": peak, "makespan_s": span,
+        "failures": [{"request": probs[i].name, "state": info[i]["state"], "error": info[i]["error"]}
+                     for i in range(n) if info[i]["state"] != mb.Server.DONE][:10],
+        "clocks": summarize_clocks(samples, local),
+        "serial_fp64": {"value": rate64, "unit": UNIT, "seconds_for_stream": serial_s,
+                        "extrapolated": "from %d-request sample (4 steps each), one instance at a time" % len(sample)},
+        "speedup_vs_serial_fp64": serial_s / span,
+    }
+    print(json.dumps(line))
+
+
 def workload(rank, args):
     from paper_1711_11361_gb300 import inputs
     if args.workload == "c4":
@@ -205,6 +311,9 @@ def workload(rank, args):
         return [inputs.c2_cylinder(400)], "c2_cylinder_400"
     if args.workload == "c3":
         return [inputs.c3_naca(1024)], "c3_naca0012_1024"
+    if args.workload == "c5":
+        specs = inputs.c5_requests(n=16, nmin=args.c5_nmin, nmax=args.c5_nmax, smin=args.c5_smin, smax=args.c5_smax)
+        return [inputs.make_request(sp) for sp in specs], "c5_served_first16"
     raise SystemExit(f"unknown workload {args.workload}")
 
 
@@ -266,10 +375,20 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true", help="skip the FP32-vs-FP64 and FP64 single-instance legs")
+    ap.add_argument("--c5-requests", type=int, default=200)
+    ap.add_argument("--c5-nmin", type=int, default=256)
+    ap.add_argument("--c5-nmax", type=int, default=1024)
+    ap.add_argument("--c5-smin", type=int, default=50)
+    ap.add_argument("--c5-smax", type=int, default=200)
+    ap.add_argument("--c5-load", type=float, default=0.9)
+    ap.add_argument("--c5-budget-gib", type=float, default=32.0)
+    ap.add_argument("--c5-max-active", type=int, default=64)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "c5":
+        return run_served(args)
 
     import torch
     ws, rank, local = dist_env()

@@ -215,6 +215,8 @@ mb_status mb_server_tick(mb_server *srv, int *n_active, int *n_queued, int *n_do
  * info (optional, 5 doubles): submit, admit and completion times (seconds,
  * host steady clock), steps taken, device bytes held while running. */
 mb_status mb_server_query(mb_server *srv, int id, int *state, double *info);
+/* Text of the error a failed request ended with ("" otherwise). */
+const char *mb_server_request_error(const mb_server *srv, int id);
 
 /* Allocation-free cut-cell classification (the paper has no counterpart: it
  * exists for callers that may not allocate device memory -- code running

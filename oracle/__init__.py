@@ -25,7 +25,6 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "mbref.c")
 _LIB = os.path.join(_HERE, "libmbref.so")
-_LIB_OMP = os.path.join(_HERE, "libmbref_omp.so")
 _lock = threading.Lock()
 
 EULER, ADVECTION = 0, 1

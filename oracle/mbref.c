@@ -37,6 +37,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#define OR_MIX_LAYERS 8   /* merges of the positivity safeguard per sweep */
 #define OR_EULER 0
 #define OR_ADVECTION 1
 #define OR_BC_TRANSMISSIVE 0
@@ -977,8 +978,10 @@ int or_sweep(or_sim *s, int d, double dt) {
     /* positivity safeguard (a reading; the paper gives none): a cell whose
      * content is non-physical after the update is merged with its fluid face
      * neighbours; every connected cluster of such cells and their neighbours
-     * shares its total content in proportion to volume.  Exactly conservative. */
-    if (s->c.equation == OR_EULER) {
+     * shares its total content in proportion to volume.  Cells still
+     * non-physical after a merge seed the next one, which reaches one layer of
+     * neighbours further, up to OR_MIX_LAYERS merges.  Exactly conservative. */
+    for (int layer = 0; layer < OR_MIX_LAYERS && s->c.equation == OR_EULER; ++layer) {
         int *lab = (int *)malloc(sizeof(int) * n);
         unsigned char *bad = (unsigned char *)calloc((size_t)n, 1);
         int nbad = 0;
@@ -1031,6 +1034,7 @@ int or_sweep(or_sim *s, int d, double dt) {
             free(tot); free(par);
         }
         free(lab); free(bad);
+        if (!nbad) break;
     }
 
     /* new state Q' = content / alpha^B */

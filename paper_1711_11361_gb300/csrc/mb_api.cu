@@ -164,6 +164,9 @@ static mb_status map_err(mb_sim *s, int e) {
     if (e & ERR_STATE) { m += "second sweep of a step used another dt; "; st = MB_E_STATE; }
     if (e & ERR_NONBR) m += "covered/uncovered cell without a fluid neighbour; ";
     if (e & ERR_UNSTABLE) m += "non-physical state (rho or p <= 0 or non-finite); ";
+    if (e & ERR_MIX_CAP) m += "more non-physical cells in one sweep than the positivity safeguard lists; ";
+    if (e & ERR_MIX_BULK) m += "a merged cluster is still non-physical; ";
+    if (e & ERR_MIX_BAND) m += "a cut cell is still non-physical after the safeguard; ";
     if (e & (ERR_EDGE_CAP | ERR_BAND_CAP | ERR_STATE)) {
     } else {
         st = MB_E_UNSTABLE;
@@ -289,7 +292,7 @@ static size_t instance_bytes(const InstDesc &I, int prec) {
     const size_t cells = (size_t)I.pitch * I.ny;
     return 3 * cells * I.nc * esz + cells * (1 + 4 + 8) + (size_t)(I.nx + I.ny + 2) * 8 +
            (size_t)I.rec_cap * (sizeof(BandRec) + 8) + (size_t)I.nv * 100 + sizeof(InstDesc) + sizeof(InstDyn) +
-           2 * MIXCAP_HOST * sizeof(int) + (size_t)I.nx * I.ny * I.nc * 8;
+           3 * MIXCAP_HOST * sizeof(int) + (size_t)I.nx * I.ny * I.nc * 8;
 }
 
 // offsets of every instance in the shared arrays, those arrays, the
@@ -351,7 +354,7 @@ static cudaError_t relayout(mb_sim *s, int old_n, const std::vector<int> &from) 
     if (e == cudaSuccess) e = ensure(&s->ebox, s->cap_ebox, 3 * tv * 2, sizeof(float));
     if (e == cudaSuccess) e = ensure(&s->rec, s->cap_rec, std::max(1, rec_total), sizeof(BandRec));
     if (e == cudaSuccess) e = ensure(&s->bnd, s->cap_bnd, std::max(1, rec_total), sizeof(double));
-    if (e == cudaSuccess) e = ensure(&s->scratch, s->cap_scr, (size_t)std::max(1, n) * 2 * MIXCAP_HOST, sizeof(int));
+    if (e == cudaSuccess) e = ensure(&s->scratch, s->cap_scr, (size_t)std::max(1, n) * 3 * MIXCAP_HOST, sizeof(int));
     if (e == cudaSuccess) e = ensure(&s->stage, s->stage_len, max_cells * 4, sizeof(double));
     if (e == cudaSuccess) e = ensure(&s->dd, s->cap_dd, std::max(1, n), sizeof(InstDesc));
     if (e == cudaSuccess) e = ensure(&s->dy, s->cap_dy, std::max(1, n), sizeof(InstDyn));

@@ -32,6 +32,9 @@ constexpr int RF_MOV_B = 4096;        // a moving edge meets the cell at the end
 
 // instance error flags
 constexpr int ERR_UNSTABLE = 1, ERR_EDGE_CAP = 2, ERR_BAND_CAP = 4, ERR_NONBR = 8, ERR_STATE = 16;
+constexpr int ERR_MIX_CAP = 32;     // more non-physical cells than the safeguard's lists hold
+constexpr int ERR_MIX_BULK = 64;    // a merged cluster still non-physical (non-band cell)
+constexpr int ERR_MIX_BAND = 128;   // a band cell still non-physical after merging
 
 struct BandRec {
     int cell;            // j*pitch + i

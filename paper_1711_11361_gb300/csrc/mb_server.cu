@@ -40,6 +40,7 @@ struct Request {
     double t_submit = 0, t_admit = 0, t_done = 0;
     int steps_done = 0;
     size_t bytes = 0;
+    std::string error;        // why it failed
     mb_body body() const {
         mb_body b;
         b.npoly = npoly;
@@ -153,6 +154,7 @@ static bool admit_one(mb_server *srv, mb_status *st) {
             q.state = r;
             srv->queue.pop_front();
             srv->err = mb_last_error(nullptr);
+            q.error = srv->err;
             ++srv->n_done;
             return true;
         }
@@ -162,6 +164,7 @@ static bool admit_one(mb_server *srv, mb_status *st) {
             q.state = r;
             srv->queue.pop_front();
             srv->err = mb_last_error(srv->sim);
+            q.error = srv->err;
             ++srv->n_done;
             return true;
         }
@@ -207,6 +210,7 @@ mb_status mb_server_tick(mb_server *srv, int *n_active, int *n_queued, int *n_do
         if (q.steps_done < q.nsteps) continue;
         st = mb_read_state(srv->sim, pos, q.Qout, nullptr, nullptr);
         q.state = st == MB_OK ? 2 : st;
+        if (st != MB_OK) q.error = mb_last_error(srv->sim);
         q.t_done = now_s();
         mb_status r = mb_batch_remove(srv->sim, pos);
         if (r != MB_OK) return srv_fail(srv, r, mb_last_error(srv->sim));
@@ -219,6 +223,11 @@ mb_status mb_server_tick(mb_server *srv, int *n_active, int *n_queued, int *n_do
     if (n_queued) *n_queued = (int)srv->queue.size();
     if (n_done) *n_done = srv->n_done;
     return MB_OK;
+}
+
+const char *mb_server_request_error(const mb_server *srv, int id) {
+    if (!srv || id < 0 || id >= (int)srv->req.size()) return "";
+    return srv->req[id].error.c_str();
 }
 
 mb_status mb_server_query(mb_server *srv, int id, int *state, double *info) {

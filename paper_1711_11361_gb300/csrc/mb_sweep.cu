@@ -1247,6 +1247,7 @@ __global__ void k_events(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y
 // the instance flagged a bad cell.  Also advances the instance's clock.
 // ---------------------------------------------------------------------------
 constexpr int MIXCAP = 1024;
+constexpr int MIX_LAYERS = 8;   // merges per sweep (cells still non-physical seed the next)
 
 template <class T>
 __global__ void k_mix(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y, BandRec *__restrict__ R,
@@ -1264,8 +1265,8 @@ __global__ void k_mix(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y, B
         y.step += 1;
     }
     if (y.nbad == 0 && y.nbulk == 0) return;
-    if (y.nbulk > NBULK) { y.err |= ERR_UNSTABLE; return; }
-    int *node = scratch + (size_t)inst * 2 * MIXCAP;     // cell index of node
+    if (y.nbulk > NBULK) { y.err |= ERR_UNSTABLE | ERR_MIX_CAP; return; }
+    int *node = scratch + (size_t)inst * 3 * MIXCAP;     // cell index of node
     int *par = node + MIXCAP;
     int nn = 0;
     const size_t plane = (size_t)I.pitch * I.ny;
@@ -1310,83 +1311,103 @@ __global__ void k_mix(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y, B
             v[z] = t;
         }
     };
+    // physical state of a cell's content after the update (or a merge)
+    auto physical = [&](int c) -> bool {
+        double q[MAXC];
+        if (I.cls[c] & CLS_BAND) {
+            const BandRec &bb = R[I.rec[c]];
+            if (!(bb.aB > 0.0)) return true;
+            for (int k = 0; k < I.nc; ++k) q[k] = bb.C2[k] / bb.aB;
+        } else {
+            for (int k = 0; k < I.nc; ++k) q[k] = (double)Qo[k * plane + c];
+        }
+        const double pm = (I.gamma - 1.0) * (q[3] - 0.5 * (q[1] * q[1] + q[2] * q[2]) / q[0]);
+        return q[0] > 0.0 && pm > 0.0 && isfinite(q[1]) && isfinite(q[2]) && isfinite(q[3]);
+    };
+    int *next = par + MIXCAP;   // seeds of the next merge
+    int nnext = 0;
     bool overflow = false;
-    // seeds in a fixed order: flagged band records by cell, then listed bulk cells
-    {
-        int seeds[16 + NBULK];
-        int ns = 0;
-        const bool listed = y.nbad <= 16;
-        if (listed) {
-            for (int q = 0; q < y.nbad; ++q) seeds[ns++] = R[y.badlist[q]].cell;
+    for (int layer = 0; layer < MIX_LAYERS; ++layer) {
+        nn = 0;
+        if (layer == 0) {
+            // flagged band records by cell, then listed bulk cells
+            int seeds[16 + NBULK];
+            int ns = 0;
+            const bool listed = y.nbad <= 16;
+            if (listed) {
+                for (int q = 0; q < y.nbad; ++q) seeds[ns++] = R[y.badlist[q]].cell;
+                sort_int(seeds, ns);
+                for (int q = 0; q < ns && !overflow; ++q) {
+                    const int c = seeds[q];
+                    overflow = !seed(c, c % I.pitch, c / I.pitch);
+                }
+            } else {
+                for (int q = 0; q < y.band_count && !overflow; ++q) {
+                    const BandRec &bb = R[I.rec_base + q];
+                    if (bb.flags & RF_BAD) overflow = !seed(bb.cell, bb.i, bb.j);
+                }
+            }
+            ns = 0;
+            for (int q = 0; q < y.nbulk; ++q) seeds[ns++] = y.bulkbad[q];
             sort_int(seeds, ns);
             for (int q = 0; q < ns && !overflow; ++q) {
                 const int c = seeds[q];
                 overflow = !seed(c, c % I.pitch, c / I.pitch);
             }
         } else {
-            for (int q = 0; q < y.band_count && !overflow; ++q) {
-                const BandRec &b = R[I.rec_base + q];
-                if (b.flags & RF_BAD) overflow = !seed(b.cell, b.i, b.j);
+            // cells still non-physical after the last merge (in cell order)
+            for (int q = 0; q < nnext && !overflow; ++q) {
+                const int c = next[q];
+                overflow = !seed(c, c % I.pitch, c / I.pitch);
             }
         }
-        ns = 0;
-        for (int q = 0; q < y.nbulk; ++q) seeds[ns++] = y.bulkbad[q];
-        sort_int(seeds, ns);
-        for (int q = 0; q < ns && !overflow; ++q) {
-            const int c = seeds[q];
-            overflow = !seed(c, c % I.pitch, c / I.pitch);
+        if (overflow) { y.err |= ERR_UNSTABLE | ERR_MIX_CAP; return; }
+        // nodes in cell order with the cell of their cluster root, so that the
+        // cluster sums run in a fixed order
+        for (int k = 0; k < nn; ++k) par[k] = root(k);        // node indices of the roots
+        for (int k = 0; k < nn; ++k) par[k] = node[par[k]];   // then their cells
+        for (int x = 1; x < nn; ++x) {
+            const int c = node[x], r = par[x];
+            int z = x;
+            while (z > 0 && node[z - 1] > c) { node[z] = node[z - 1]; par[z] = par[z - 1]; --z; }
+            node[z] = c;
+            par[z] = r;
         }
-    }
-    if (overflow) { y.err |= ERR_UNSTABLE; return; }
-    // nodes in cell order with the cell of their cluster root, so that the
-    // cluster sums run in a fixed order
-    for (int k = 0; k < nn; ++k) par[k] = root(k);        // node indices of the roots
-    for (int k = 0; k < nn; ++k) par[k] = node[par[k]];   // then their cells
-    for (int x = 1; x < nn; ++x) {
-        const int c = node[x], r = par[x];
-        int z = x;
-        while (z > 0 && node[z - 1] > c) { node[z] = node[z - 1]; par[z] = par[z - 1]; --z; }
-        node[z] = c;
-        par[z] = r;
-    }
-    for (int k = 0; k < nn; ++k) {
-        const int rc = par[k];
-        if (node[k] != rc) continue;   // one pass per cluster, at its root cell
-        double tot[MAXC] = {0, 0, 0, 0}, vol = 0.0;
-        for (int m = 0; m < nn; ++m) {
-            if (par[m] != rc) continue;
-            const int c = node[m];
-            if (I.cls[c] & CLS_BAND) {
-                const BandRec &b = R[I.rec[c]];
-                vol += b.aB;
-                for (int q = 0; q < I.nc; ++q) tot[q] += b.C2[q];
-            } else {
-                vol += 1.0;
-                for (int q = 0; q < I.nc; ++q) tot[q] += (double)Qo[q * plane + c];
-            }
-        }
-        for (int m = 0; m < nn; ++m) {
-            if (par[m] != rc) continue;
-            const int c = node[m];
-            if (I.cls[c] & CLS_BAND) {
-                BandRec &b = R[I.rec[c]];
-                for (int q = 0; q < I.nc; ++q) b.C2[q] = b.aB * (tot[q] / vol);
-            } else {
-                double qn[MAXC];
-                for (int q = 0; q < I.nc; ++q) {
-                    qn[q] = tot[q] / vol;
-                    Qo[q * plane + c] = (T)qn[q];
+        for (int k = 0; k < nn; ++k) {
+            const int rc = par[k];
+            if (node[k] != rc) continue;   // one pass per cluster, at its root cell
+            double tot[MAXC] = {0, 0, 0, 0}, vol = 0.0;
+            for (int m = 0; m < nn; ++m) {
+                if (par[m] != rc) continue;
+                const int c = node[m];
+                if (I.cls[c] & CLS_BAND) {
+                    const BandRec &bb = R[I.rec[c]];
+                    vol += bb.aB;
+                    for (int q = 0; q < I.nc; ++q) tot[q] += bb.C2[q];
+                } else {
+                    vol += 1.0;
+                    for (int q = 0; q < I.nc; ++q) tot[q] += (double)Qo[q * plane + c];
                 }
-                // a merged bulk cell that is still not physical ends the run
-                // (band cells are checked when their state is formed)
-                if (I.nc == 4) {
-                    const double pm = (I.gamma - 1.0) * (qn[3] - 0.5 * (qn[1] * qn[1] + qn[2] * qn[2]) / qn[0]);
-                    if (!(qn[0] > 0.0 && pm > 0.0)) y.err |= ERR_UNSTABLE;
+            }
+            for (int m = 0; m < nn; ++m) {
+                if (par[m] != rc) continue;
+                const int c = node[m];
+                if (I.cls[c] & CLS_BAND) {
+                    BandRec &bb = R[I.rec[c]];
+                    for (int q = 0; q < I.nc; ++q) bb.C2[q] = bb.aB * (tot[q] / vol);
+                } else {
+                    for (int q = 0; q < I.nc; ++q) Qo[q * plane + c] = (T)(tot[q] / vol);
                 }
             }
         }
+        y.mixed += nn;
+        nnext = 0;
+        for (int k = 0; k < nn; ++k)
+            if (!physical(node[k])) next[nnext++] = node[k];
+        if (nnext == 0) return;
     }
-    y.mixed += nn;
+    // still non-physical after the last merge
+    y.err |= ERR_UNSTABLE | ERR_MIX_BULK;
 }
 
 // ---------------------------------------------------------------------------
@@ -1413,7 +1434,7 @@ __global__ void k_finalize(const InstDesc *__restrict__ D, InstDyn *__restrict__
         if (I.eq == 0) {
             double p = (I.gamma - 1.0) * (q[3] - 0.5 * (q[1] * q[1] + q[2] * q[2]) / q[0]);
             bool ok = q[0] > 0.0 && p > 0.0 && isfinite(q[1]) && isfinite(q[2]) && isfinite(q[3]);
-            if (!ok) atomicOr(&y.err, ERR_UNSTABLE);
+            if (!ok) atomicOr(&y.err, ERR_UNSTABLE | ERR_MIX_BAND);
             if (last) {
                 double c = sqrt(I.gamma * p / q[0]);
                 atomic_max_pos(&y.S[0], fabs(q[1] / q[0]) + c);

@@ -272,6 +272,44 @@ def c4_batch(n=64, nmin=128, nmax=1024, steps=500, seed=None, kinds=("cylinder",
     return probs
 
 
+def c5_requests(n=2000, nmin=256, nmax=2048, smin=500, smax=5000, seed=None,
+                kinds=("cylinder", "triangle", "piston", "naca")):
+    """Served stream: n request specs (kind, N, shock Mach, steps), grid size
+    log-uniform in [nmin, nmax], steps uniform in [smin, smax], body uniform
+    over the kinds (the pitching NACA 0012 of c3_naca; the others as in the
+    batch), seeded (child 4 of the base seed).  Specs are light; make_request
+    builds the problem when it is submitted."""
+    ss = np.random.SeedSequence(BASE_SEED).spawn(5)[4] if seed is None else np.random.SeedSequence(seed)
+    rng = np.random.default_rng(ss)
+    out = []
+    for k in range(n):
+        N = int(round(math.exp(rng.uniform(math.log(nmin), math.log(nmax)))))
+        kind = kinds[int(rng.integers(0, len(kinds)))]
+        M = float(rng.uniform(1.2, 3.0))
+        steps = int(rng.integers(smin, smax + 1))
+        out.append(dict(k=k, kind=kind, N=N, M=M, steps=steps))
+    return out
+
+
+def make_request(spec) -> Problem:
+    """The problem of a served-stream spec (c5_requests)."""
+    if spec["kind"] == "naca":
+        p = c3_naca(spec["N"])
+    else:
+        p = _body_instance(spec["kind"], spec["N"], spec["M"])
+    p.name = f"c5_{spec['k']:04d}_{spec['kind']}_N{spec['N']}"
+    p.steps = spec["steps"]
+    return p
+
+
+def c5_arrivals(n, mean_gap, seed=None):
+    """Poisson arrival times (exponential gaps of the given mean, seconds)
+    for a served stream of n requests, seeded (child 0 of the stream's seed)."""
+    base = np.random.SeedSequence(BASE_SEED).spawn(5)[4] if seed is None else np.random.SeedSequence(seed)
+    rng = np.random.default_rng(base.spawn(1)[0])
+    return np.cumsum(rng.exponential(mean_gap, size=n))
+
+
 def small_case(kind="cylinder", N=48, M=2.0, uncover_mode=UNCOVER_DONOR):
     """Small single instance for parity tests (seconds on the oracle)."""
     p = _body_instance(kind, N, M, uncover_mode=uncover_mode)

@@ -25,7 +25,7 @@ EXPORTS = ["mb_create", "mb_batch_create", "mb_destroy", "mb_last_error", "mb_se
            "mb_enable_timing", "mb_kernel_time", "mb_band_records", "mb_band_record_size",
            "mb_cut_cells_noalloc", "mb_noalloc_last_error", "mb_batch_add", "mb_batch_remove", "mb_instance_bytes",
            "mb_request_bytes", "mb_server_create", "mb_server_destroy", "mb_server_last_error", "mb_server_submit",
-           "mb_server_tick", "mb_server_query"]
+           "mb_server_tick", "mb_server_query", "mb_server_request_error"]
 
 
 class Grid(ctypes.Structure):
@@ -97,6 +97,7 @@ def _load():
         "mb_server_submit": ([P, ctypes.POINTER(Request), ctypes.POINTER(I)], I),
         "mb_server_tick": ([P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)], I),
         "mb_server_query": ([P, I, ctypes.POINTER(I), D], I),
+        "mb_server_request_error": ([P, I], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -324,7 +325,7 @@ class Server:
         info = np.zeros(5)
         self._check(lib.mb_server_query(self._h, rid, ctypes.byref(st), _dp(info)))
         return dict(state=st.value, t_submit=info[0], t_admit=info[1], t_done=info[2], steps=int(info[3]),
-                    bytes=int(info[4]))
+                    bytes=int(info[4]), error=lib.mb_server_request_error(self._h, rid).decode())
 
     def result(self, rid: int):
         return self.out[rid]
