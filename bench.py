@@ -403,6 +403,7 @@ def main():
     sim = mb.Sim(probs, prec)
     stream = torch.cuda.Stream()
     sim.set_stream(stream.cuda_stream)
+    tune = sim.autotune()
     cells = sum(p.nx * p.ny for p in probs)
     with torch.cuda.stream(stream):
         sim.run(args.warmup, 0.0)
@@ -470,7 +471,8 @@ def main():
                    "grid_sizes": [p.nx for p in probs], "bulk": args.precision,
                    "geometry_and_weights": "f64", "dt": "per-instance CFL on device",
                    "l2": "inputs larger than L2 (state per buffer %.2f GB)" % (cells * 16 / 1e9),
-                   "parallelism": "instances" if ws == 1 else f"instances x{ws} ranks"},
+                   "parallelism": "instances" if ws == 1 else f"instances x{ws} ranks",
+                   "autotuned": {"x_cta": tune["x_cta"], "y_cta": tune["y_cta"], "y_rows_per_thread": tune["y_rows"]}},
         "p50_ms_per_step": float(np.percentile(per, 50)), "p99_ms_per_step": float(np.percentile(per, 99)),
         "status": int(status),
         "roofline": {"kernel": "bulk sweep update (MUSCL-Hancock + HLLC), x and y kernels", "bound": "hbm", "achieved": achieved,

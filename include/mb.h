@@ -153,6 +153,14 @@ mb_status mb_band_records(mb_sim *sim, int inst, void *out, int max_records, int
 /* Size in bytes of one band record as copied by mb_band_records. */
 int mb_band_record_size(void);
 
+/* Pick the bulk kernels' launch shapes for this batch by timing candidates
+ * on the device (between steps; the simulation is not changed): the CTA size
+ * of each sweep direction's kernel and the rows per thread of the y sweep.
+ * report (optional, 5 doubles): x CTA size, y CTA size, y rows per thread,
+ * and the best x and y kernel times in ms.  Later mb_batch_add calls use the
+ * chosen shapes. */
+mb_status mb_autotune(mb_sim *sim, double *report);
+
 /* Kernel timing.  enable != 0 brackets every launch of the bulk sweep kernel
  * with CUDA events on the sim's stream (mb_run then launches without graphs).
  * mb_kernel_time returns the bulk kernel's total milliseconds and launch

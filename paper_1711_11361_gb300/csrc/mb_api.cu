@@ -34,7 +34,7 @@ template <class T>
 void launch_band_stage(int, const InstDesc *, InstDyn *, BandRec *, const double *, int *, int, int, int, int, int,
                        int, int, int, cudaStream_t);
 template <class T>
-void launch_bulk(int, int, const InstDesc *, InstDyn *, const BandRec *, int, int, int, int, int, cudaStream_t);
+void launch_bulk(int, int, const InstDesc *, InstDyn *, const BandRec *, int, int, int, int, int, int, cudaStream_t);
 template <class T>
 int bulk_blocks_per_sm(int);
 template <class T>
@@ -83,6 +83,10 @@ struct mb_sim {
     int *ginst = nullptr;         // instance of each geometry group
     int total_tiles[2] = {0, 0};
     int bulk_grid[2] = {0, 0};
+    // launch shapes of the bulk kernels (mb_autotune): CTA size per direction
+    // of the FP32x2 kernels, rows per thread of the y sweep
+    int tune_cta[2] = {128, 128};
+    int tune_yseg = 64;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int cur = 0;          // buffer holding the latest state (between steps)
@@ -198,8 +202,8 @@ static const char *check_instance(const mb_grid &g, const mb_body &b, int prec, 
 
 // descriptor of one instance (device pointers and offsets into the shared
 // arrays are set by make_instance and relayout)
-static void describe_instance(int prec, const mb_grid &g, double gamma, const mb_body &b, const mb_motion &m,
-                              InstDesc &I, InstHost &h) {
+static void describe_instance(int prec, int yseg, const mb_grid &g, double gamma, const mb_body &b,
+                              const mb_motion &m, InstDesc &I, InstHost &h) {
     memset(&I, 0, sizeof(I));
     I.nx = g.nx; I.ny = g.ny;
     I.pitch = (g.nx + 31) / 32 * 32;
@@ -261,13 +265,14 @@ static void describe_instance(int prec, const mb_grid &g, double gamma, const mb
     I.ntiles[0] = g.ny;
     const int ycols = (prec == MB_FP32 && g.equation == MB_EULER) ? 64 : 32;
     I.tiles_x[1] = (g.nx + ycols - 1) / ycols;
-    I.ntiles[1] = I.tiles_x[1] * ((g.ny + 63) / 64);
+    I.yseg = yseg;
+    I.ntiles[1] = I.tiles_x[1] * ((g.ny + yseg - 1) / yseg);
 }
 
 // descriptor and device buffers of one instance
 static cudaError_t make_instance(mb_sim *s, const mb_grid &g, double gamma, const mb_body &b, const mb_motion &m,
                                  InstDesc &I, InstHost &h) {
-    describe_instance(s->prec, g, gamma, b, m, I, h);
+    describe_instance(s->prec, s->tune_yseg, g, gamma, b, m, I, h);
     const size_t esz = s->prec == MB_FP32 ? 4 : 8;
     const size_t cells = (size_t)I.pitch * g.ny;
     cudaError_t e = cudaSuccess;
@@ -499,7 +504,7 @@ size_t mb_request_bytes(const mb_grid *grid, const mb_body *body, const mb_motio
     if (check_instance(*grid, *body, grid->precision, grid->equation)) return 0;
     InstDesc I;
     InstHost h;
-    describe_instance(grid->precision, *grid, 1.4, *body, *motion, I, h);
+    describe_instance(grid->precision, 64, *grid, 1.4, *body, *motion, I, h);
     return instance_bytes(I, grid->precision);
 }
 
@@ -566,9 +571,9 @@ static mb_status do_sweep(mb_sim *s, int dir, double dt) {
     }
     const int eq = s->eq;
     if (s->prec == MB_FP32)
-        launch_bulk<float>(dir, eq, s->dd, s->dy, s->rec, s->n, s->total_tiles[dir], src, dst, last, st);
+        launch_bulk<float>(dir, eq, s->dd, s->dy, s->rec, s->n, s->total_tiles[dir], src, dst, last, s->tune_cta[dir], st);
     else
-        launch_bulk<double>(dir, eq, s->dd, s->dy, s->rec, s->n, s->total_tiles[dir], src, dst, last, st);
+        launch_bulk<double>(dir, eq, s->dd, s->dy, s->rec, s->n, s->total_tiles[dir], src, dst, last, s->tune_cta[dir], st);
     if (s->timing) {
         cudaEventRecord(e1, st);
         s->evs.push_back({e0, e1});
@@ -774,6 +779,87 @@ mb_status mb_diagnostics(mb_sim *sim, int inst, double *out) {
     for (int q = 0; q < 4; ++q) out[q] = y.wall_sum[q];
     out[4] = y.mixed;
     out[5] = y.band_count;
+    return MB_OK;
+}
+
+// rows per thread of the y sweep for every instance (tile counts follow)
+static cudaError_t set_yseg(mb_sim *s, int yseg) {
+    if (yseg == s->tune_yseg) return cudaSuccess;
+    s->tune_yseg = yseg;
+    for (auto &I : s->hd) {
+        I.yseg = yseg;
+        I.ntiles[1] = I.tiles_x[1] * ((I.ny + yseg - 1) / yseg);
+    }
+    std::vector<int> from(s->n);
+    for (int k = 0; k < s->n; ++k) from[k] = k;
+    return relayout(s, s->n, from);
+}
+
+mb_status mb_autotune(mb_sim *sim, double *report) {
+    if (!sim) return MB_E_INVAL;
+    if (sim->sidx != 0) return fail(sim, MB_E_STATE, "mb_autotune in the middle of a step");
+    if (sim->n == 0) return MB_OK;
+    cudaError_t e = cudaStreamSynchronize(sim->stream);
+    if (e != cudaSuccess) return cuda_check(sim, e, "autotune sync");
+    // the bulk kernels alone, from the current state into a free buffer,
+    // outside a step (no band cells are marked then; the last-sweep outputs
+    // stay off), so the simulation is not changed
+    const int src = sim->cur, dst = (sim->cur + 1) % 3;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    auto time_bulk = [&](int dir, int cta) -> double {
+        auto go = [&]() {
+            if (sim->prec == MB_FP32)
+                launch_bulk<float>(dir, sim->eq, sim->dd, sim->dy, sim->rec, sim->n, sim->total_tiles[dir], src, dst,
+                                   0, cta, sim->stream);
+            else
+                launch_bulk<double>(dir, sim->eq, sim->dd, sim->dy, sim->rec, sim->n, sim->total_tiles[dir], src,
+                                    dst, 0, cta, sim->stream);
+        };
+        go();
+        cudaEventRecord(e0, sim->stream);
+        for (int r = 0; r < 3; ++r) go();
+        cudaEventRecord(e1, sim->stream);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        return ms / 3.0;
+    };
+    const bool packed = sim->prec == MB_FP32 && sim->eq == MB_EULER;
+    const int ctas[2] = {64, 128};
+    const int ysegs[3] = {32, 64, 128};
+    double best_x = 1e30, best_y = 1e30;
+    int bx = sim->tune_cta[0], by = sim->tune_cta[1], bs = sim->tune_yseg;
+    for (int c = 0; c < (packed ? 2 : 1); ++c) {
+        const int cta = packed ? ctas[c] : 256;
+        double t = time_bulk(0, cta);
+        if (t < best_x) { best_x = t; bx = cta; }
+    }
+    for (int ys = 0; ys < 3; ++ys) {
+        e = set_yseg(sim, ysegs[ys]);
+        if (e != cudaSuccess) break;
+        for (int c = 0; c < (packed ? 2 : 1); ++c) {
+            const int cta = packed ? ctas[c] : 256;
+            double t = time_bulk(1, cta);
+            if (t < best_y) { best_y = t; by = cta; bs = ysegs[ys]; }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e == cudaSuccess) e = set_yseg(sim, bs);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_check(sim, e, "autotune");
+    sim->tune_cta[0] = bx;
+    sim->tune_cta[1] = by;
+    drop_graphs(sim);
+    if (report) {
+        report[0] = bx;
+        report[1] = by;
+        report[2] = bs;
+        report[3] = best_x;
+        report[4] = best_y;
+    }
     return MB_OK;
 }
 

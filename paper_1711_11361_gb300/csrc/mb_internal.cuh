@@ -78,6 +78,7 @@ struct InstDesc {
     double wall_bound[2];
     int rec_base, rec_cap;
     int gcol_max, gcol_off;     // geometry columns reserved for this instance
+    int yseg;                   // rows per thread of the y sweep (tuned)
     int tile_off[2];            // first bulk tile (per direction)
     int ntiles[2];
     int tiles_x[2];             // tiles along x per direction

@@ -319,7 +319,6 @@ __global__ void k_band_sweep(const InstDesc *__restrict__ D, InstDyn *__restrict
 // cell.  Faces touching a band cell take the stabilised value its record
 // holds (computed once by k_band_sweep), so every face flux is computed once.
 // ---------------------------------------------------------------------------
-constexpr int YSEG = 64;    // rows per thread in the y sweep
 
 template <class T, int NC>
 struct QV { T q[NC]; };
@@ -554,7 +553,7 @@ __global__ void __launch_bounds__(256) k_bulk_x(const InstDesc *__restrict__ D, 
     finish_warp<T>(y, last != 0, s0, s1);
 }
 
-// y sweep: one thread per column and segment of YSEG rows, marching upward
+// y sweep: one thread per column and segment of I.yseg rows, marching upward
 // with a register window; 32 consecutive columns per warp keep every load
 // and store coalesced
 template <class T, int EQ>
@@ -575,7 +574,7 @@ __global__ void __launch_bounds__(256, 3) k_bulk_y(const InstDesc *__restrict__ 
     const bool active = i_raw < I.nx;
     const int i = active ? i_raw : I.nx - 1;
     const int n = I.ny;
-    const int j0 = sg * YSEG, j1 = min(n, j0 + YSEG);
+    const int j0 = sg * I.yseg, j1 = min(n, j0 + I.yseg);
     const T lam = sizeof(T) == 4 ? (T)y.lamf : (T)y.lam;
     const T g = (T)I.gamma, av0 = (T)I.adv[0], av1 = (T)I.adv[1];
     const size_t plane = (size_t)I.pitch * I.ny;
@@ -1046,7 +1045,7 @@ struct YRing {
 };
 
 // y sweep, packed: one thread per pair of neighbouring columns and segment of
-// YSEG rows, marching upward; a warp covers 64 consecutive columns and
+// I.yseg rows, marching upward; a warp covers 64 consecutive columns and
 // streams its rows through a shared-memory ring filled by cp.async
 constexpr int YCOLS_P = 64;
 __global__ void __launch_bounds__(128, 5) k_bulk_y_p(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y,
@@ -1067,7 +1066,7 @@ __global__ void __launch_bounds__(128, 5) k_bulk_y_p(const InstDesc *__restrict_
     const int i = col0 + 2 * lane;     // columns i, i+1 of this thread
     const int st0 = (i < I.nx ? 1 : 0) | (i + 1 < I.nx ? 2 : 0);
     const int n = I.ny;
-    const int j0 = sg * YSEG, j1 = min(n, j0 + YSEG);
+    const int j0 = sg * I.yseg, j1 = min(n, j0 + I.yseg);
     const float lam = y.lamf;
     const float g = (float)I.gamma, g1 = g - 1.0f;
     const size_t plane = (size_t)I.pitch * I.ny;
@@ -1526,16 +1525,17 @@ void launch_band_stage(int stage, const InstDesc *D, InstDyn *Y, BandRec *R, con
 
 template <class T>
 void launch_bulk(int dir, int eq, const InstDesc *D, InstDyn *Y, const BandRec *R, int n_inst, int total_warps,
-                 int src, int dst, int last, cudaStream_t st) {
+                 int src, int dst, int last, int cta, cudaStream_t st) {
+    const int wpc = cta / 32;   // warps per CTA of the FP32x2 kernels
     int blocks = (total_warps + 7) / 8;
     if (blocks <= 0) return;
     const bool packed = sizeof(T) == 4 && eq == 0;   // FP32 Euler: the FP32x2 kernels
     if (dir == 0) {
-        if (packed) k_bulk_x_p<<<(total_warps + 3) / 4, 128, 4 * sizeof(XRing), st>>>(D, Y, R, n_inst, total_warps, src, dst, last);
+        if (packed) k_bulk_x_p<<<(total_warps + wpc - 1) / wpc, cta, wpc * sizeof(XRing), st>>>(D, Y, R, n_inst, total_warps, src, dst, last);
         else if (eq == 0) k_bulk_x<T, 0><<<blocks, 256, 0, st>>>(D, Y, R, n_inst, total_warps, src, dst, last);
         else k_bulk_x<T, 1><<<blocks, 256, 0, st>>>(D, Y, R, n_inst, total_warps, src, dst, last);
     } else {
-        if (packed) k_bulk_y_p<<<(total_warps + 3) / 4, 128, 4 * sizeof(YRing), st>>>(D, Y, R, n_inst, total_warps, src, dst, last);
+        if (packed) k_bulk_y_p<<<(total_warps + wpc - 1) / wpc, cta, wpc * sizeof(YRing), st>>>(D, Y, R, n_inst, total_warps, src, dst, last);
         else if (eq == 0) k_bulk_y<T, 0><<<blocks, 256, 0, st>>>(D, Y, R, n_inst, total_warps, src, dst, last);
         else k_bulk_y<T, 1><<<blocks, 256, 0, st>>>(D, Y, R, n_inst, total_warps, src, dst, last);
     }
@@ -1567,7 +1567,7 @@ void launch_read_state(const InstDesc *D, double *out, int inst, int b, cudaStre
     template void launch_band_stage<T>(int, const InstDesc *, InstDyn *, BandRec *, const double *, int *, int, int, \
                                        int, int, int, int, int, int, cudaStream_t);                                \
     template void launch_bulk<T>(int, int, const InstDesc *, InstDyn *, const BandRec *, int, int, int, int, int,  \
-                                 cudaStream_t);                                                                    \
+                                 int, cudaStream_t);                                                                    \
     template int bulk_blocks_per_sm<T>(int);                                                                       \
     template void launch_write_state<T>(const InstDesc *, InstDyn *, const double *, int, int, cudaStream_t);      \
     template void launch_read_state<T>(const InstDesc *, double *, int, int, cudaStream_t);

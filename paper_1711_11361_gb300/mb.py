@@ -25,7 +25,7 @@ EXPORTS = ["mb_create", "mb_batch_create", "mb_destroy", "mb_last_error", "mb_se
            "mb_enable_timing", "mb_kernel_time", "mb_band_records", "mb_band_record_size",
            "mb_cut_cells_noalloc", "mb_noalloc_last_error", "mb_batch_add", "mb_batch_remove", "mb_instance_bytes",
            "mb_request_bytes", "mb_server_create", "mb_server_destroy", "mb_server_last_error", "mb_server_submit",
-           "mb_server_tick", "mb_server_query", "mb_server_request_error"]
+           "mb_server_tick", "mb_server_query", "mb_server_request_error", "mb_autotune"]
 
 
 class Grid(ctypes.Structure):
@@ -98,6 +98,7 @@ def _load():
         "mb_server_tick": ([P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)], I),
         "mb_server_query": ([P, I, ctypes.POINTER(I), D], I),
         "mb_server_request_error": ([P, I], ctypes.c_char_p),
+        "mb_autotune": ([P, D], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -225,6 +226,12 @@ class Sim:
         o = np.zeros(6)
         self._check(lib.mb_diagnostics(self._h, inst, _dp(o)))
         return dict(wall=o[:4], mixed=int(o[4]), band=int(o[5]))
+
+    def autotune(self):
+        """Tune the bulk kernels' launch shapes (mb_autotune); returns the choice."""
+        r = np.zeros(5)
+        self._check(lib.mb_autotune(self._h, _dp(r)))
+        return dict(x_cta=int(r[0]), y_cta=int(r[1]), y_rows=int(r[2]), x_ms=r[3], y_ms=r[4])
 
     def enable_timing(self, on=True):
         self._check(lib.mb_enable_timing(self._h, 1 if on else 0))

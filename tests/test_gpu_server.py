@@ -108,3 +108,21 @@ def test_server_admits_by_memory_budget(mb):
         assert srv.query(rid)["state"] == mb.Server.DONE
         assert np.array_equal(srv.result(rid), _solo(mb, p, 5, mb.FP32)["Q"], equal_nan=True)
     srv.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_autotune_changes_no_result(mb, precision):
+    """Launch shapes picked by mb_autotune (CTA sizes, rows per thread of
+    the y sweep) move work between threads only: the state is bit-identical
+    to an untuned run, and tuning in mid-run changes nothing."""
+    prec = mb.FP64 if precision == "fp64" else mb.FP32
+    probs = _mix()[:3]
+    a = mb.Sim(probs, prec)
+    a.run(3, 0.0)
+    choice = a.autotune()
+    assert choice["x_cta"] in (64, 128, 256) and choice["y_rows"] in (32, 64, 128)
+    a.run(3, 0.0)
+    b = mb.Sim(probs, prec)
+    b.run(6, 0.0)
+    for k in range(len(probs)):
+        assert np.array_equal(a.read_state(k)["Q"], b.read_state(k)["Q"], equal_nan=True), k
