@@ -366,7 +366,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="mb", choices=["mb", "reference"])
     ap.add_argument("--workload", default="c4")
@@ -374,6 +374,7 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes of the bulk kernels")
     ap.add_argument("--no-accuracy", action="store_true", help="skip the FP32-vs-FP64 and FP64 single-instance legs")
     ap.add_argument("--c5-requests", type=int, default=200)
     ap.add_argument("--c5-nmin", type=int, default=256)
@@ -403,7 +404,7 @@ def main():
     sim = mb.Sim(probs, prec)
     stream = torch.cuda.Stream()
     sim.set_stream(stream.cuda_stream)
-    tune = sim.autotune()
+    tune = sim.autotune() if not args.no_autotune else {"x_cta": None, "y_cta": None, "y_rows": None}
     cells = sum(p.nx * p.ny for p in probs)
     with torch.cuda.stream(stream):
         sim.run(args.warmup, 0.0)
@@ -472,7 +473,8 @@ def main():
                    "geometry_and_weights": "f64", "dt": "per-instance CFL on device",
                    "l2": "inputs larger than L2 (state per buffer %.2f GB)" % (cells * 16 / 1e9),
                    "parallelism": "instances" if ws == 1 else f"instances x{ws} ranks",
-                   "autotuned": {"x_cta": tune["x_cta"], "y_cta": tune["y_cta"], "y_rows_per_thread": tune["y_rows"]}},
+                   "autotuned": {k: tune.get(k) for k in ("x_cta", "y_cta", "y_rows", "x_min_ctas", "y_min_ctas",
+                                                          "x_ring_chunks")}},
         "p50_ms_per_step": float(np.percentile(per, 50)), "p99_ms_per_step": float(np.percentile(per, 99)),
         "status": int(status),
         "roofline": {"kernel": "bulk sweep update (MUSCL-Hancock + HLLC), x and y kernels", "bound": "hbm", "achieved": achieved,

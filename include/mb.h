@@ -155,10 +155,12 @@ int mb_band_record_size(void);
 
 /* Pick the bulk kernels' launch shapes for this batch by timing candidates
  * on the device (between steps; the simulation is not changed): the CTA size
- * of each sweep direction's kernel and the rows per thread of the y sweep.
- * report (optional, 5 doubles): x CTA size, y CTA size, y rows per thread,
- * and the best x and y kernel times in ms.  Later mb_batch_add calls use the
- * chosen shapes. */
+ * of each sweep direction's kernel, its register budget (registers for 4 or
+ * 5 resident CTAs per SM), the depth of the x sweep's row ring and the rows
+ * per thread of the y sweep.  report (optional, 8 doubles): x CTA size, y CTA
+ * size, y rows per thread, the best x and y kernel times in ms, the x and y
+ * register budgets (resident CTAs per SM) and the x ring depth (chunks of 64
+ * cells).  Later mb_batch_add calls use the chosen shapes. */
 mb_status mb_autotune(mb_sim *sim, double *report);
 
 /* Kernel timing.  enable != 0 brackets every launch of the bulk sweep kernel

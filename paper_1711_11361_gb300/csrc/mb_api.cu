@@ -83,9 +83,10 @@ struct mb_sim {
     int *ginst = nullptr;         // instance of each geometry group
     int total_tiles[2] = {0, 0};
     int bulk_grid[2] = {0, 0};
-    // launch shapes of the bulk kernels (mb_autotune): CTA size per direction
-    // of the FP32x2 kernels, rows per thread of the y sweep
-    int tune_cta[2] = {128, 128};
+    // launch shapes of the bulk kernels (mb_autotune): CTA size, register
+    // budget and ring depth per direction of the FP32x2 kernels, rows per
+    // thread of the y sweep
+    int tune_cta[2] = {64 | SHAPE_MINB4 | SHAPE_RING8, 64 | SHAPE_MINB4};
     int tune_yseg = 64;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
@@ -827,22 +828,32 @@ mb_status mb_autotune(mb_sim *sim, double *report) {
         return ms / 3.0;
     };
     const bool packed = sim->prec == MB_FP32 && sim->eq == MB_EULER;
-    const int ctas[2] = {64, 128};
+    // candidate shapes of the FP32x2 kernels: CTA size x register budget
+    // (x: also the ring depth); the other kernels have one shape
+    std::vector<int> xs, ys;
+    if (packed) {
+        for (int cta : {64, 128})
+            for (int m4 = 0; m4 < 2; ++m4) {
+                ys.push_back(cta | (m4 ? SHAPE_MINB4 : 0));
+                for (int r8 = 0; r8 < 2; ++r8) xs.push_back(cta | (m4 ? SHAPE_MINB4 : 0) | (r8 ? SHAPE_RING8 : 0));
+            }
+    } else {
+        xs.push_back(256);
+        ys.push_back(256);
+    }
     const int ysegs[3] = {32, 64, 128};
     double best_x = 1e30, best_y = 1e30;
     int bx = sim->tune_cta[0], by = sim->tune_cta[1], bs = sim->tune_yseg;
-    for (int c = 0; c < (packed ? 2 : 1); ++c) {
-        const int cta = packed ? ctas[c] : 256;
-        double t = time_bulk(0, cta);
-        if (t < best_x) { best_x = t; bx = cta; }
+    for (int shape : xs) {
+        double t = time_bulk(0, shape);
+        if (t < best_x) { best_x = t; bx = shape; }
     }
-    for (int ys = 0; ys < 3; ++ys) {
-        e = set_yseg(sim, ysegs[ys]);
+    for (int ys_ = 0; ys_ < 3; ++ys_) {
+        e = set_yseg(sim, ysegs[ys_]);
         if (e != cudaSuccess) break;
-        for (int c = 0; c < (packed ? 2 : 1); ++c) {
-            const int cta = packed ? ctas[c] : 256;
-            double t = time_bulk(1, cta);
-            if (t < best_y) { best_y = t; by = cta; bs = ysegs[ys]; }
+        for (int shape : ys) {
+            double t = time_bulk(1, shape);
+            if (t < best_y) { best_y = t; by = shape; bs = ysegs[ys_]; }
         }
     }
     cudaEventDestroy(e0);
@@ -854,11 +865,14 @@ mb_status mb_autotune(mb_sim *sim, double *report) {
     sim->tune_cta[1] = by;
     drop_graphs(sim);
     if (report) {
-        report[0] = bx;
-        report[1] = by;
+        report[0] = bx & 1023;
+        report[1] = by & 1023;
         report[2] = bs;
         report[3] = best_x;
         report[4] = best_y;
+        report[5] = (bx & SHAPE_MINB4) ? 4 : 5;
+        report[6] = (by & SHAPE_MINB4) ? 4 : 5;
+        report[7] = (bx & SHAPE_RING8) ? 8 : 4;
     }
     return MB_OK;
 }

@@ -10,6 +10,10 @@ constexpr int MAXC = 4;
 constexpr int NBULK = 32;              // non-physical bulk cells listed per sweep
 constexpr int GEO_GC = 16;            // grid columns per geometry group (one CTA each)
 constexpr double ALPHA_MIN = 1e-10;   // smaller volume fractions count as solid
+// launch shape of the FP32x2 bulk kernels: bits 0-9 CTA threads (64 or 128),
+// bit 10 registers budgeted for 4 resident CTAs per SM (else 5), bit 11 an
+// x-sweep ring of 8 chunks (else 4)
+constexpr int SHAPE_MINB4 = 1024, SHAPE_RING8 = 2048;
 
 // cell class byte (state at the current pose A of the sweep)
 constexpr uint8_t CLS_SOLID = 1;      // alpha == 0
@@ -223,34 +227,36 @@ __device__ __forceinline__ void riemann_flux(int eq, T g, int d, T a0, T a1, con
 
 // Exact solution of the moving-wall Riemann problem (eq. riemann_wallvel):
 // the ghost mirrors the normal velocity about the wall's; the contact moves
-// with the wall; shock branch in closed form, rarefaction isentropic.
-__device__ __forceinline__ void wall_state(double g, const double *q, double nx, double ny, double wx, double wy,
-                                           double *rs, double *ps, double *usx, double *usy) {
-    double rho = q[0], u = q[1] / rho, v = q[2] / rho;
-    double p = (g - 1.0) * (q[3] - 0.5 * (q[1] * q[1] + q[2] * q[2]) / rho);
-    double un = u * nx + v * ny, wn = wx * nx + wy * ny;
-    double du = un - wn;
-    double mu = (g - 1.0) / (g + 1.0);
-    double pst, rst;
-    if (du > 0.0) {
-        double A = 2.0 / ((g + 1.0) * rho), B = mu * p;
-        pst = p + du / (2.0 * A) * (du + sqrt(du * du + 4.0 * A * (p + B)));
-        double pr = pst / p;
-        rst = rho * (pr + mu) / (mu * pr + 1.0);
+// with the wall; shock branch in closed form, rarefaction isentropic.  R is
+// the arithmetic type: double on the FP64 path; the FP32-bulk path solves the
+// wall problem in float (it is flux arithmetic, like the bulk fluxes).
+template <class R>
+__device__ __forceinline__ void wall_state(R g, const R *q, R nx, R ny, R wx, R wy, R *rs, R *ps, R *usx, R *usy) {
+    R rho = q[0], u = q[1] / rho, v = q[2] / rho;
+    R p = (g - R(1)) * (q[3] - R(0.5) * (q[1] * q[1] + q[2] * q[2]) / rho);
+    R un = u * nx + v * ny, wn = wx * nx + wy * ny;
+    R du = un - wn;
+    R mu = (g - R(1)) / (g + R(1));
+    R pst, rst;
+    if (du > R(0)) {
+        R A = R(2) / ((g + R(1)) * rho), B = mu * p;
+        pst = p + du / (R(2) * A) * (du + sqrt(du * du + R(4) * A * (p + B)));
+        R pr = pst / p;
+        rst = rho * (pr + mu) / (mu * pr + R(1));
     } else {
-        double c = sqrt(g * p / rho);
-        double x = 1.0 + 0.5 * (g - 1.0) * du / c;
-        if (x > 0.0) {
-            pst = p * pow(x, 2.0 * g / (g - 1.0));
-            rst = rho * pow(pst / p, 1.0 / g);
+        R c = sqrt(g * p / rho);
+        R x = R(1) + R(0.5) * (g - R(1)) * du / c;
+        if (x > R(0)) {
+            pst = p * pow(x, R(2) * g / (g - R(1)));
+            rst = rho * pow(pst / p, R(1) / g);
         } else {
-            pst = 0.0;
-            rst = 0.0;
+            pst = R(0);
+            rst = R(0);
         }
     }
-    double fp = 1e-12 * p;
+    R fp = R(1e-12) * p;
     *ps = pst > fp ? pst : fp;
-    *rs = rst > 1e-12 * rho ? rst : 1e-12 * rho;
+    *rs = rst > R(1e-12) * rho ? rst : R(1e-12) * rho;
     *usx = u - du * nx;
     *usy = v - du * ny;
 }

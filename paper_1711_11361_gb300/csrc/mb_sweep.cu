@@ -141,15 +141,19 @@ __global__ void k_band_prep(const InstDesc *__restrict__ D, InstDyn *__restrict_
                     double a = (cl & CLS_BAND) ? R[I.rec[c]].aA : ((cl & CLS_SOLID) ? 0.0 : 1.0);
                     if (!(a > 0.0)) continue;
                     ws += a;
-                    for (int q = 0; q < I.nc; ++q) acc[q] += a * (double)QA[q * plane + c];
+                    
+#pragma unroll
+                    for (int q = 0; q < MAXC; ++q)
+                        if (q < I.nc) acc[q] += a * (double)QA[q * plane + c];
                 }
         }
         if (ws == 0.0) {
             atomicOr(&y.err, ERR_NONBR);
-            for (int q = 0; q < I.nc; ++q) b.Qp[q] = 0.0;
+            for (int q = 0; q < MAXC; ++q) b.Qp[q] = 0.0;
             b.flags &= ~RF_FLUID_A;
         } else {
-            for (int q = 0; q < I.nc; ++q) b.Qp[q] = acc[q] / ws;
+            for (int q = 0; q < MAXC; ++q)
+                if (q < I.nc) b.Qp[q] = acc[q] / ws;
         }
     }
     // moving-wall boundary state: advective part from the step-start state,
@@ -157,24 +161,32 @@ __global__ void k_band_prep(const InstDesc *__restrict__ D, InstDyn *__restrict_
     if (b.flags & RF_FLUID_A) {
         double qc[MAXC], qs[MAXC];
         bool unc = (b.flags & RF_UNCOV) != 0;
-        for (int q = 0; q < I.nc; ++q) qc[q] = unc ? b.Qp[q] : (double)QA[q * plane + b.cell];
+        
+#pragma unroll
+        for (int q = 0; q < MAXC; ++q) qc[q] = q >= I.nc ? 0.0 : unc ? b.Qp[q] : (double)QA[q * plane + b.cell];
         double n0 = (double)QN[b.cell];
         bool fresh = n0 != n0;
-        for (int q = 0; q < I.nc; ++q) qs[q] = fresh ? qc[q] : (double)QN[q * plane + b.cell];
+        
+#pragma unroll
+        for (int q = 0; q < MAXC; ++q) qs[q] = q >= I.nc ? 0.0 : fresh ? qc[q] : (double)QN[q * plane + b.cell];
         if (I.eq == 0) {
-            double g = I.gamma;
-            double rs, ps_step, usx, usy, rs2, ps_sw, u2x, u2y;
-            wall_state(g, qs, b.nx, b.ny, b.wx, b.wy, &rs, &ps_step, &usx, &usy);
+            // wall problem in the path's arithmetic type (FP64 path: double)
+            T qsT[4], qcT[4];
+            for (int q = 0; q < 4; ++q) { qsT[q] = (T)qs[q]; qcT[q] = (T)qc[q]; }
+            const T g = (T)I.gamma;
+            const T nx = (T)b.nx, ny = (T)b.ny, wx = (T)b.wx, wy = (T)b.wy;
+            T rs, ps_step, usx, usy, rs2, ps_sw, u2x, u2y;
+            wall_state<T>(g, qsT, nx, ny, wx, wy, &rs, &ps_step, &usx, &usy);
             bool same = true;
             for (int q = 0; q < 4; ++q) same = same && qs[q] == qc[q];
             if (same) ps_sw = ps_step;   // first sweep of a step: one state
-            else wall_state(g, qc, b.nx, b.ny, b.wx, b.wy, &rs2, &ps_sw, &u2x, &u2y);
-            double Eadv = ps_step / (g - 1.0) + 0.5 * rs * (usx * usx + usy * usy);
-            double ud = dir == 0 ? usx : usy;
+            else wall_state<T>(g, qcT, nx, ny, wx, wy, &rs2, &ps_sw, &u2x, &u2y);
+            T Eadv = ps_step / (g - T(1)) + T(0.5) * rs * (usx * usx + usy * usy);
+            T ud = dir == 0 ? usx : usy;
             b.QB[0] = rs; b.QB[1] = rs * usx; b.QB[2] = rs * usy; b.QB[3] = Eadv;
             b.FB[0] = rs * ud;
-            b.FB[1] = rs * ud * usx + (dir == 0 ? ps_sw : 0.0);
-            b.FB[2] = rs * ud * usy + (dir == 1 ? ps_sw : 0.0);
+            b.FB[1] = rs * ud * usx + (dir == 0 ? ps_sw : T(0));
+            b.FB[2] = rs * ud * usy + (dir == 1 ? ps_sw : T(0));
             b.FB[3] = ud * (Eadv + ps_step);
         } else {
             b.QB[0] = qs[0];
@@ -818,22 +830,33 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-// per-warp ring of row chunks for the x sweep: chunk c of the row sits in
-// slot c % XR, prefetched XR - 2 chunks ahead
-constexpr int XR = 4;
+// per-warp ring of the x sweep: cell b of the row (the ghost cells -2, -1,
+// n, n+1 of the boundary conditions included) sits at position b mod 64 XC;
+// chunks of 64 cells arrive by cp.async XC - 2 chunks ahead of their use
+template <int XC>
 struct XRing {
-    float q[XR][4][64];
-    unsigned char cls[XR][64];
+    float q[4][64 * XC];
+    unsigned char cls[64 * XC];
 };
 
+// class bits that take a cell off the plain path (solid, or a band cell whose
+// faces carry stabilised fluxes)
+constexpr unsigned CLS_OFF = CLS_SOLID | CLS_BAND;
+
 // x sweep, packed: one warp per row, lane l holds cells 64c + 2l and
-// 64c + 2l + 1 of chunk c; the update trails the fluxes by one chunk
-__global__ void __launch_bounds__(128, 5) k_bulk_x_p(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y,
+// 64c + 2l + 1 of chunk c; the update trails the fluxes by one chunk.  A
+// chunk whose cells and stencil halo are all plain fluid cells takes the
+// plain path (no limiter switches, no face replacement, whole-pair stores);
+// the decision is warp-uniform, from a ballot over the class bytes.
+// MINB: resident CTAs per SM the registers are budgeted for; XC: ring chunks.
+template <int MINB, int XC>
+__global__ void __launch_bounds__(128, MINB) k_bulk_x_p(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y,
                                                   const BandRec *__restrict__ R, int n_inst, int total_warps, int src,
                                                   int dst, int last) {
     extern __shared__ __align__(16) unsigned char xsm[];
     const int lane = threadIdx.x & 31;
-    XRing &rg = ((XRing *)xsm)[threadIdx.x >> 5];
+    constexpr int XRN = 64 * XC;
+    XRing<XC> &rg = ((XRing<XC> *)xsm)[threadIdx.x >> 5];
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (gw >= total_warps) return;
     const int inst = find_inst_warp(D, n_inst, gw, 0);
@@ -844,119 +867,145 @@ __global__ void __launch_bounds__(128, 5) k_bulk_x_p(const InstDesc *__restrict_
     const float lam = y.lamf;
     const float g = (float)I.gamma, g1 = g - 1.0f;
     const size_t plane = (size_t)I.pitch * I.ny;
-    const float *__restrict__ Q = (const float *)I.Q[src];
-    float *__restrict__ Qo = (float *)I.Q[dst];
     const int rowb = j * I.pitch;
-    const int bclo = I.bc[0], bchi = I.bc[1];
-    // copies of chunk c's real cells into its slot (one commit group per call)
-    auto prefetch = [&](int c) {
-        if (c >= 0 && 64 * c < n) {
-            const int s = c & (XR - 1);
-            const int a = 64 * c + 2 * lane;
+    const float *__restrict__ Q = (const float *)I.Q[src] + rowb;
+    float *__restrict__ Qb = (float *)I.Q[dst];
+    float *__restrict__ Qo = Qb + rowb;
+    const unsigned char *__restrict__ cl = I.cls + rowb;
+    // ghost cells of the boundary conditions: lane 0: -2, 1: -1, 2: n, 3: n+1
+    float gq[4] = {1.0f, 1.0f, 1.0f, 1.0f};
+    int gc = CLS_SOLID, gb = -1000000;
+    if (lane < 4) {
+        gb = lane < 2 ? lane - 2 : n + lane - 2;
+        bool fl;
+        const int p = ghost_map(gb, n, I.bc[0], I.bc[1], &fl);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                if (a + 1 < n) cp_async8(&rg.q[s][k][2 * lane], Q + k * plane + rowb + a);
-                else if (a < n) cp_async4(&rg.q[s][k][2 * lane], Q + k * plane + rowb + a);
+        for (int k = 0; k < 4; ++k) gq[k] = __ldg(Q + k * plane + p);
+        if (fl) gq[1] = -gq[1];
+        gc = cl[p];
+    }
+    // ghosts that belong to chunk c or c+1 into the ring (after those chunks'
+    // copies have completed, so that a copied class word cannot overwrite them)
+    auto put_ghost = [&](int c) {
+        const int gk = gb >> 6;
+        if (lane < 4 && (gk == c || gk == c + 1)) {
+            const int pos = gb & (XRN - 1);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) rg.q[k][pos] = gq[k];
+            rg.cls[pos] = (unsigned char)gc;
+        }
+    };
+    // copies of chunk c's real cells into the ring (one commit group per call)
+    auto prefetch = [&](int c) {
+        const int a0 = 64 * c;
+        if (c >= 0 && a0 < n) {
+            const int s = a0 & (XRN - 1);
+            const int a = a0 + 2 * lane;
+            if (a + 1 < n) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) cp_async8(&rg.q[k][s + 2 * lane], Q + k * plane + a);
+            } else if (a < n) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) cp_async4(&rg.q[k][s + 2 * lane], Q + k * plane + a);
             }
-            if (lane < 16 && 64 * c + 4 * lane < n) cp_async4(&rg.cls[s][4 * lane], I.cls + rowb + 64 * c + 4 * lane);
+            if (lane < 16 && a0 + 4 * lane < n) cp_async4(&rg.cls[s + 4 * lane], cl + a0 + 4 * lane);
         }
         cp_async_commit();
     };
-    // state and class of cell b: from the ring inside the row, a ghost cell
-    // of the boundary condition next to it, filler beyond
-    auto cell = [&](int b, float *w, int &cb) {
-        if (b >= 0 && b < n) {
-            const int s = (b >> 6) & (XR - 1), o = b & 63;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) w[k] = rg.q[s][k][o];
-            cb = rg.cls[s][o];
-        } else if (b >= -2 && b <= n + 1) {
-            bool fl;
-            const int p = ghost_map(b, n, bclo, bchi, &fl);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) w[k] = __ldg(Q + k * plane + rowb + p);
-            if (fl) w[1] = -w[1];
-            cb = I.cls[rowb + p];
-        } else {
-            w[0] = w[1] = w[2] = w[3] = 1.0f;
-            cb = CLS_SOLID;
-        }
-    };
-    // the pair of chunk c (classes packed as first | second << 8)
-    auto pair = [&](int c, S2 &v, int &cls) {
-        const int a = 64 * c + 2 * lane;
-        if (a >= 0 && a + 1 < n) {
-            const int s = c & (XR - 1);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) v.q[k] = *(const float2 *)&rg.q[s][k][2 * lane];
-            cls = *(const unsigned short *)&rg.cls[s][2 * lane];
-            return;
-        }
-        float w0[4], w1[4];
-        int c0, c1;
-        cell(a, w0, c0);
-        cell(a + 1, w1, c1);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) v.q[k] = make_float2(w0[k], w1[k]);
-        cls = c0 | c1 << 8;
-    };
     const int c_last = (n + 1) >> 6;   // chunk holding face n
-    prefetch(0);
-    prefetch(1);
-    cp_async_wait<0>();
+#pragma unroll
+    for (int c = 0; c < XC - 2; ++c) prefetch(c);
+    cp_async_wait<XC - 4>();   // chunks 0 and 1 complete
     __syncwarp();
-    // evolved right state of cell -1
+    put_ghost(-1);
+    __syncwarp();
+    // evolved right state of cell -1 (all lanes alike)
     E2 QRc;
     {
-        float w[4], wm[4], wp[4];
-        int cb, cbm, cbp;
-        cell(-1, w, cb);
-        cell(-2, wm, cbm);
-        cell(0, wp, cbp);
         float2 qm[4], q0[4], qp[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            qm[k] = make_float2(wm[k], wm[k]);
-            q0[k] = make_float2(w[k], w[k]);
-            qp[k] = make_float2(wp[k], wp[k]);
+            qm[k] = P2(rg.q[k][XRN - 2]);
+            q0[k] = P2(rg.q[k][XRN - 1]);
+            qp[k] = P2(rg.q[k][0]);
         }
-        const bool lim = !(cbm & CLS_SOLID) && !(cbp & CLS_SOLID);
+        const bool lim = !(rg.cls[XRN - 2] & CLS_SOLID) && !(rg.cls[0] & CLS_SOLID);
         E2 QL;
         evolve2<0>(g1, lam, qm, q0, qp, lim, lim, QL, QRc);
     }
+    // cells -2 and -1 plain (ghost classes), previous chunk entirely plain
+    bool prev_hi = !((rg.cls[XRN - 2] | rg.cls[XRN - 1]) & CLS_OFF);
+    bool prev_all = false;
+    // validity of this lane's pair for the plain-path test: positions past
+    // n + 1 hold stale ring contents and are never used for a real cell
+    const int rem = n + 1 - 2 * lane;
     float s0 = 0.0f, s1 = 0.0f;
     float2 Fprev[4];
+    // update of the chunk before c (faces Fprev, high face of lane 31 from
+    // this chunk's lane 0), with class checks; tail: no chunk c
+    auto update_general = [&](int c, const float2 *F, bool tail) {
+        float2 Fhi[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float dn = __shfl_down_sync(0xffffffffu, Fprev[k].x, 1);
+            const float nx0 = tail ? 0.0f : __shfl_sync(0xffffffffu, F[k].x, 0);
+            Fhi[k] = make_float2(Fprev[k].y, lane == 31 ? nx0 : dn);
+        }
+        const int ap = 64 * (c - 1) + 2 * lane;
+        const int pp = ap & (XRN - 1);
+        S2 Qm;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) Qm.q[k] = *(const float2 *)&rg.q[k][pp];
+        const int cm = *(const unsigned short *)&rg.cls[pp];
+        const bool in1 = tail ? lane < 31 : true;
+        int st = 0;
+        if (ap < n && !((cm & 0xff) & CLS_OFF)) st |= 1;
+        if (ap + 1 < n && in1 && !(((cm >> 8) & 0xff) & CLS_OFF)) st |= 2;
+        if (st) update2(Qb, plane, rowb + ap, st, st == 3, g1, g, lam, Qm.q, Fprev, Fhi, last, s0, s1, y);
+        if ((cm & CLS_SOLID) && ap < n) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) Qo[k * plane + ap] = NAN;
+        }
+        if (((cm >> 8) & CLS_SOLID) && ap + 1 < n && in1) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) Qo[k * plane + ap + 1] = NAN;
+        }
+    };
     for (int c = 0; c <= c_last; ++c) {
         __syncwarp();
-        prefetch(c + XR - 2);
-        cp_async_wait<XR - 3>();
+        prefetch(c + XC - 2);
+        cp_async_wait<XC - 3>();   // chunks up to c + 1 complete
+        __syncwarp();
+        put_ghost(c);
         __syncwarp();
         const int a = 64 * c + 2 * lane;
+        const int pa = a & (XRN - 1), pl = (a - 1) & (XRN - 1), pr = (a + 2) & (XRN - 1);
+        const int c0 = *(const unsigned short *)&rg.cls[pa];
+        // plain-path test over cells 64c-2 .. 64c+64 (those up to n+1)
+        const int lim = rem - 64 * c;
+        const int vm = lim >= 1 ? 0x0505 : (lim == 0 ? 0x0005 : 0);
+        const unsigned bal = __ballot_sync(0xffffffffu, !(c0 & vm));
+        const int ah = 64 * c + 64;
+        const bool hclean = ah > n + 1 || !(rg.cls[ah & (XRN - 1)] & CLS_OFF);
+        const bool plain = bal == 0xffffffffu && prev_hi && hclean;
         S2 Q0;
-        int c0;
-        pair(c, Q0, c0);
-        float wl[4], wr[4];
-        int clA, crB;
-        if (lane > 0 && a + 1 < n) {
-            const int s = c & (XR - 1);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) wl[k] = rg.q[s][k][2 * lane - 1];
-            clA = rg.cls[s][2 * lane - 1];
-        } else {
-            cell(a - 1, wl, clA);
-        }
-        cell(a + 2, wr, crB);
         float2 qm[4], qp[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            qm[k] = make_float2(wl[k], Q0.q[k].x);
-            qp[k] = make_float2(Q0.q[k].y, wr[k]);
+            Q0.q[k] = *(const float2 *)&rg.q[k][pa];
+            qm[k] = make_float2(rg.q[k][pl], Q0.q[k].x);
+            qp[k] = make_float2(Q0.q[k].y, rg.q[k][pr]);
         }
-        const int cA = c0 & 0xff, cB = (c0 >> 8) & 0xff;
-        const bool lx = !(clA & CLS_SOLID) && !(cB & CLS_SOLID);
-        const bool ly = !(cA & CLS_SOLID) && !(crB & CLS_SOLID);
         E2 QL, QR;
-        evolve2<0>(g1, lam, qm, Q0.q, qp, lx, ly, QL, QR);
+        if (plain) {
+            evolve2<0>(g1, lam, qm, Q0.q, qp, true, true, QL, QR);
+        } else {
+            const int clA = rg.cls[pl], crB = rg.cls[pr];
+            const int cA = c0 & 0xff, cB = (c0 >> 8) & 0xff;
+            const bool lx = !(clA & CLS_SOLID) && !(cB & CLS_SOLID);
+            const bool ly = !(cA & CLS_SOLID) && !(crB & CLS_SOLID);
+            evolve2<0>(g1, lam, qm, Q0.q, qp, lx, ly, QL, QR);
+        }
         // faces a (cells a-1 | a) and a+1 (cells a | a+1)
         E2 Lf;
 #pragma unroll
@@ -971,33 +1020,44 @@ __global__ void __launch_bounds__(128, 5) k_bulk_x_p(const InstDesc *__restrict_
         }
         float2 F[4];
         hllc2<0>(g, Lf, QL, F);
-        if (a <= n) face_override<0>(I, R, j, a, n, (uint8_t)clA, (uint8_t)cA, F, 0);
-        if (a + 1 <= n) face_override<0>(I, R, j, a + 1, n, (uint8_t)cA, (uint8_t)cB, F, 1);
-        // update of chunk c-1: high faces are the second half of Fprev and
-        // the first half of the next lane's (lane 31: this chunk's lane 0)
+        if (!plain) {
+            const int clA = rg.cls[pl];
+            const int cA = c0 & 0xff, cB = (c0 >> 8) & 0xff;
+            if (a <= n) face_override<0>(I, R, j, a, n, (uint8_t)clA, (uint8_t)cA, F, 0);
+            if (a + 1 <= n) face_override<0>(I, R, j, a + 1, n, (uint8_t)cA, (uint8_t)cB, F, 1);
+        }
         if (c >= 1) {
-            float2 Fhi[4];
+            if (prev_all && 64 * c <= n) {
+                // chunk c-1: 64 real plain cells
+                float2 Fhi[4];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const float dn = __shfl_down_sync(0xffffffffu, Fprev[k].x, 1);
-                const float nx0 = __shfl_sync(0xffffffffu, F[k].x, 0);
-                Fhi[k] = make_float2(Fprev[k].y, lane == 31 ? nx0 : dn);
-            }
-            S2 Qm;
-            int cm;
-            pair(c - 1, Qm, cm);
-            const int ap = a - 64;
-            int st = 0;
-            if (ap < n && !((cm & 0xff) & (CLS_BAND | CLS_SOLID))) st |= 1;
-            if (ap + 1 < n && !(((cm >> 8) & 0xff) & (CLS_BAND | CLS_SOLID))) st |= 2;
-            if (st) update2(Qo, plane, rowb + ap, st, st == 3, g1, g, lam, Qm.q, Fprev, Fhi, last, s0, s1, y);
-            if ((cm & CLS_SOLID) && ap < n) {
+                for (int k = 0; k < 4; ++k) {
+                    const float dn = __shfl_down_sync(0xffffffffu, Fprev[k].x, 1);
+                    const float nx0 = __shfl_sync(0xffffffffu, F[k].x, 0);
+                    Fhi[k] = make_float2(Fprev[k].y, lane == 31 ? nx0 : dn);
+                }
+                const int ap = a - 64;
+                const int pp = ap & (XRN - 1);
+                float2 qn[4];
 #pragma unroll
-                for (int k = 0; k < 4; ++k) Qo[k * plane + rowb + ap] = NAN;
-            }
-            if (((cm >> 8) & CLS_SOLID) && ap + 1 < n) {
-#pragma unroll
-                for (int k = 0; k < 4; ++k) Qo[k * plane + rowb + ap + 1] = NAN;
+                for (int k = 0; k < 4; ++k) {
+                    const float2 qo = *(const float2 *)&rg.q[k][pp];
+                    qn[k] = fma2(P2(lam), sub2(Fprev[k], Fhi[k]), qo);
+                    *(float2 *)(Qo + k * plane + ap) = qn[k];
+                }
+                float2 ir, p;
+                prim2(g1, qn, ir, p);
+                if (!(qn[0].x > 0.0f && p.x > 0.0f)) list_bulk_bad(y, rowb + ap);
+                if (!(qn[0].y > 0.0f && p.y > 0.0f)) list_bulk_bad(y, rowb + ap + 1);
+                if (last) {
+                    const float2 cs = sqrt2(mul2(mul2(P2(g), p), ir));
+                    const float2 w0 = add2(make_float2(fabsf(qn[1].x * ir.x), fabsf(qn[1].y * ir.y)), cs);
+                    const float2 w1 = add2(make_float2(fabsf(qn[2].x * ir.x), fabsf(qn[2].y * ir.y)), cs);
+                    s0 = fmaxf(s0, fmaxf(w0.x, w0.y));
+                    s1 = fmaxf(s1, fmaxf(w1.x, w1.y));
+                }
+            } else {
+                update_general(c, F, false);
             }
         }
 #pragma unroll
@@ -1006,33 +1066,12 @@ __global__ void __launch_bounds__(128, 5) k_bulk_x_p(const InstDesc *__restrict_
         QRc.p.x = __shfl_sync(0xffffffffu, QR.p.y, 31);
 #pragma unroll
         for (int k = 0; k < 4; ++k) Fprev[k] = F[k];
+        prev_hi = (bal >> 31) != 0;
+        prev_all = bal == 0xffffffffu;
     }
     // the last chunk (its high faces were computed in the final iteration,
     // except the one past lane 31 which lies beyond face n)
-    {
-        float2 Fhi[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const float dn = __shfl_down_sync(0xffffffffu, Fprev[k].x, 1);
-            Fhi[k] = make_float2(Fprev[k].y, dn);
-        }
-        S2 Qm;
-        int cm;
-        pair(c_last, Qm, cm);
-        const int ap = 64 * c_last + 2 * lane;
-        int st = 0;
-        if (ap < n && !((cm & 0xff) & (CLS_BAND | CLS_SOLID))) st |= 1;
-        if (ap + 1 < n && lane < 31 && !(((cm >> 8) & 0xff) & (CLS_BAND | CLS_SOLID))) st |= 2;
-        if (st) update2(Qo, plane, rowb + ap, st, st == 3, g1, g, lam, Qm.q, Fprev, Fhi, last, s0, s1, y);
-        if ((cm & CLS_SOLID) && ap < n) {
-#pragma unroll
-            for (int k = 0; k < 4; ++k) Qo[k * plane + rowb + ap] = NAN;
-        }
-        if (((cm >> 8) & CLS_SOLID) && ap + 1 < n && lane < 31) {
-#pragma unroll
-            for (int k = 0; k < 4; ++k) Qo[k * plane + rowb + ap + 1] = NAN;
-        }
-    }
+    update_general(c_last + 1, Fprev, true);
     finish_warp<float>(y, last != 0, s0, s1);
 }
 
@@ -1046,9 +1085,12 @@ struct YRing {
 
 // y sweep, packed: one thread per pair of neighbouring columns and segment of
 // I.yseg rows, marching upward; a warp covers 64 consecutive columns and
-// streams its rows through a shared-memory ring filled by cp.async
+// streams its rows through a shared-memory ring filled by cp.async.  A row
+// step whose three rows lie inside the grid and hold only plain fluid cells
+// (warp-uniform ballot) takes the plain path.
 constexpr int YCOLS_P = 64;
-__global__ void __launch_bounds__(128, 5) k_bulk_y_p(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y,
+template <int MINB>
+__global__ void __launch_bounds__(128, MINB) k_bulk_y_p(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y,
                                                      const BandRec *__restrict__ R, int n_inst, int total_warps,
                                                      int src, int dst, int last) {
     extern __shared__ __align__(16) unsigned char ysm[];
@@ -1064,34 +1106,42 @@ __global__ void __launch_bounds__(128, 5) k_bulk_y_p(const InstDesc *__restrict_
     const int cg = local % ncg, sg = local / ncg;
     const int col0 = cg * YCOLS_P;
     const int i = col0 + 2 * lane;     // columns i, i+1 of this thread
-    const int st0 = (i < I.nx ? 1 : 0) | (i + 1 < I.nx ? 2 : 0);
+    const int nx = I.nx, pitch = I.pitch;
+    const int st0 = (i < nx ? 1 : 0) | (i + 1 < nx ? 2 : 0);
     const int n = I.ny;
     const int j0 = sg * I.yseg, j1 = min(n, j0 + I.yseg);
     const float lam = y.lamf;
     const float g = (float)I.gamma, g1 = g - 1.0f;
-    const size_t plane = (size_t)I.pitch * I.ny;
+    const size_t plane = (size_t)pitch * n;
     const float *__restrict__ Q = (const float *)I.Q[src];
     float *__restrict__ Qo = (float *)I.Q[dst];
+    const unsigned char *__restrict__ cl = I.cls;
     const int bclo = I.bc[2], bchi = I.bc[3];
+    const bool cls_lane = lane < 16 && col0 + 4 * lane < pitch;
+    // validity mask of this lane's class pair for the plain-path test
+    const int vm = st0 == 3 ? 0x0505 : (st0 == 1 ? 0x0005 : 0);
     // copies of row r (a ghost row of the boundary condition outside [0, n))
     // into its slot; rows past j1 + 1 are not needed (one commit group per call)
     auto prefetch = [&](int r) {
         if (r <= j1 + 1) {
             const int s = (r - j0 + 2) & (YR - 1);
-            bool fl;
-            const int p = ghost_map(r, n, bclo, bchi, &fl);
-            const int ci = p * I.pitch + i;
+            int p = r;
+            if (r < 0 || r >= n) {
+                bool fl;
+                p = ghost_map(r, n, bclo, bchi, &fl);
+            }
+            const float *src_q = Q + (size_t)p * pitch + i;
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                if (st0 == 3) cp_async8(&rg.q[s][k][2 * lane], Q + k * plane + ci);
-                else if (st0 == 1) cp_async4(&rg.q[s][k][2 * lane], Q + k * plane + ci);
+                if (st0 == 3) cp_async8(&rg.q[s][k][2 * lane], src_q + k * plane);
+                else if (st0 == 1) cp_async4(&rg.q[s][k][2 * lane], src_q + k * plane);
             }
-            if (lane < 16 && col0 + 4 * lane < I.pitch)
-                cp_async4(&rg.cls[s][4 * lane], I.cls + p * I.pitch + col0 + 4 * lane);
+            if (cls_lane) cp_async4(&rg.cls[s][4 * lane], cl + (size_t)p * pitch + col0 + 4 * lane);
         }
         cp_async_commit();
     };
-    // the pair of row r from the ring; columns past the grid read as solid
+    // the pair of row r from the ring; columns past the grid read as solid,
+    // ghost rows of a reflective side flip the normal momentum
     auto row = [&](int r, S2 &v, int &cls) {
         const int s = (r - j0 + 2) & (YR - 1);
 #pragma unroll
@@ -1128,37 +1178,84 @@ __global__ void __launch_bounds__(128, 5) k_bulk_y_p(const InstDesc *__restrict_
     }
     float s0 = 0.0f, s1 = 0.0f;
     float2 Fprev[4];
-    for (int f = j0; f <= j1; ++f) {
+    float *__restrict__ wp = Qo + (size_t)(j0 - 1) * pitch + i;   // row f-1 of this lane's columns
+    for (int f = j0; f <= j1; ++f, wp += pitch) {
         __syncwarp();
         prefetch(f + YR - 2);
         cp_async_wait<YR - 3>();
         __syncwarp();
-        // rows f-1, f, f+1
-        S2 qm, qc, qp;
-        int cm, cc, cp;
-        row(f - 1, qm, cm);
-        row(f, qc, cc);
-        row(f + 1, qp, cp);
-        E2 QL, QR;
-        evolve2<1>(g1, lam, qm.q, qc.q, qp.q, !(cm & CLS_SOLID) && !(cp & CLS_SOLID),
-                   !((cm >> 8) & CLS_SOLID) && !((cp >> 8) & CLS_SOLID), QL, QR);
+        const int sm_ = (f - j0 + 1) & (YR - 1), sc = (f - j0 + 2) & (YR - 1), sp = (f - j0 + 3) & (YR - 1);
+        const int cm = *(const unsigned short *)&rg.cls[sm_][2 * lane];
+        const int cc = *(const unsigned short *)&rg.cls[sc][2 * lane];
+        const int cp = *(const unsigned short *)&rg.cls[sp][2 * lane];
+        const bool inside = f >= 1 && f + 1 < n;
+        const bool plain = __all_sync(0xffffffffu, !((cm | cc | cp) & vm)) && inside;
         float2 F[4];
-        hllc2<1>(g, QRc, QL, F);
-        if (st0 & 1) face_override<1>(I, R, i, f, n, (uint8_t)(cm & 0xff), (uint8_t)(cc & 0xff), F, 0);
-        if (st0 & 2) face_override<1>(I, R, i + 1, f, n, (uint8_t)(cm >> 8), (uint8_t)(cc >> 8), F, 1);
-        if (f > j0) {
-            int st = 0;
-            if ((st0 & 1) && !((cm & 0xff) & (CLS_BAND | CLS_SOLID))) st |= 1;
-            if ((st0 & 2) && !(((cm >> 8) & 0xff) & (CLS_BAND | CLS_SOLID))) st |= 2;
-            const int ci = (f - 1) * I.pitch + i;
-            if (st) update2(Qo, plane, ci, st, st == 3, g1, g, lam, qm.q, Fprev, F, last, s0, s1, y);
-            if ((st0 & 1) && (cm & CLS_SOLID)) {
+        E2 QR;
+        if (plain) {
+            // rows f-1, f, f+1 straight from the ring (lanes past the grid
+            // compute on stale values that are never stored)
+            float2 qm[4], qc[4], qp[4];
 #pragma unroll
-                for (int k = 0; k < 4; ++k) Qo[k * plane + ci] = NAN;
+            for (int k = 0; k < 4; ++k) {
+                qm[k] = *(const float2 *)&rg.q[sm_][k][2 * lane];
+                qc[k] = *(const float2 *)&rg.q[sc][k][2 * lane];
+                qp[k] = *(const float2 *)&rg.q[sp][k][2 * lane];
             }
-            if ((st0 & 2) && ((cm >> 8) & CLS_SOLID)) {
+            E2 QL;
+            evolve2<1>(g1, lam, qm, qc, qp, true, true, QL, QR);
+            hllc2<1>(g, QRc, QL, F);
+            if (f > j0) {
+                float2 qn[4];
 #pragma unroll
-                for (int k = 0; k < 4; ++k) Qo[k * plane + ci + 1] = NAN;
+                for (int k = 0; k < 4; ++k) qn[k] = fma2(P2(lam), sub2(Fprev[k], F[k]), qm[k]);
+                if (st0 == 3) {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) *(float2 *)(wp + k * plane) = qn[k];
+                } else if (st0 == 1) {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) wp[k * plane] = qn[k].x;
+                }
+                float2 ir, p;
+                prim2(g1, qn, ir, p);
+                const int ci = (f - 1) * pitch + i;
+                if ((st0 & 1) && !(qn[0].x > 0.0f && p.x > 0.0f)) list_bulk_bad(y, ci);
+                if ((st0 & 2) && !(qn[0].y > 0.0f && p.y > 0.0f)) list_bulk_bad(y, ci + 1);
+                if (last) {
+                    const float2 cs = sqrt2(mul2(mul2(P2(g), p), ir));
+                    const float2 w0 = add2(make_float2(fabsf(qn[1].x * ir.x), fabsf(qn[1].y * ir.y)), cs);
+                    const float2 w1 = add2(make_float2(fabsf(qn[2].x * ir.x), fabsf(qn[2].y * ir.y)), cs);
+                    if (st0 & 1) { s0 = fmaxf(s0, w0.x); s1 = fmaxf(s1, w1.x); }
+                    if (st0 & 2) { s0 = fmaxf(s0, w0.y); s1 = fmaxf(s1, w1.y); }
+                }
+            }
+        } else {
+            // rows f-1, f, f+1
+            S2 qm, qc, qp;
+            int cm2, cc2, cp2;
+            row(f - 1, qm, cm2);
+            row(f, qc, cc2);
+            row(f + 1, qp, cp2);
+            E2 QL;
+            evolve2<1>(g1, lam, qm.q, qc.q, qp.q, !(cm2 & CLS_SOLID) && !(cp2 & CLS_SOLID),
+                       !((cm2 >> 8) & CLS_SOLID) && !((cp2 >> 8) & CLS_SOLID), QL, QR);
+            hllc2<1>(g, QRc, QL, F);
+            if (st0 & 1) face_override<1>(I, R, i, f, n, (uint8_t)(cm2 & 0xff), (uint8_t)(cc2 & 0xff), F, 0);
+            if (st0 & 2) face_override<1>(I, R, i + 1, f, n, (uint8_t)(cm2 >> 8), (uint8_t)(cc2 >> 8), F, 1);
+            if (f > j0) {
+                int st = 0;
+                if ((st0 & 1) && !((cm2 & 0xff) & CLS_OFF)) st |= 1;
+                if ((st0 & 2) && !(((cm2 >> 8) & 0xff) & CLS_OFF)) st |= 2;
+                const int ci = (f - 1) * pitch + i;
+                if (st) update2(Qo, plane, ci, st, st == 3, g1, g, lam, qm.q, Fprev, F, last, s0, s1, y);
+                if ((st0 & 1) && (cm2 & CLS_SOLID)) {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) Qo[k * plane + ci] = NAN;
+                }
+                if ((st0 & 2) && ((cm2 >> 8) & CLS_SOLID)) {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) Qo[k * plane + ci + 1] = NAN;
+                }
             }
         }
         QRc = QR;
@@ -1525,18 +1622,29 @@ void launch_band_stage(int stage, const InstDesc *D, InstDyn *Y, BandRec *R, con
 
 template <class T>
 void launch_bulk(int dir, int eq, const InstDesc *D, InstDyn *Y, const BandRec *R, int n_inst, int total_warps,
-                 int src, int dst, int last, int cta, cudaStream_t st) {
+                 int src, int dst, int last, int shape, cudaStream_t st) {
+    const int cta = shape & 1023;
     const int wpc = cta / 32;   // warps per CTA of the FP32x2 kernels
     int blocks = (total_warps + 7) / 8;
     if (blocks <= 0) return;
     const bool packed = sizeof(T) == 4 && eq == 0;   // FP32 Euler: the FP32x2 kernels
+    const int pg = (total_warps + wpc - 1) / wpc;
+    const bool m4 = (shape & SHAPE_MINB4) != 0, r8 = (shape & SHAPE_RING8) != 0;
     if (dir == 0) {
-        if (packed) k_bulk_x_p<<<(total_warps + wpc - 1) / wpc, cta, wpc * sizeof(XRing), st>>>(D, Y, R, n_inst, total_warps, src, dst, last);
-        else if (eq == 0) k_bulk_x<T, 0><<<blocks, 256, 0, st>>>(D, Y, R, n_inst, total_warps, src, dst, last);
+        if (packed) {
+            const size_t sm = wpc * (r8 ? sizeof(XRing<8>) : sizeof(XRing<4>));
+            if (m4 && r8) k_bulk_x_p<4, 8><<<pg, cta, sm, st>>>(D, Y, R, n_inst, total_warps, src, dst, last);
+            else if (m4) k_bulk_x_p<4, 4><<<pg, cta, sm, st>>>(D, Y, R, n_inst, total_warps, src, dst, last);
+            else if (r8) k_bulk_x_p<5, 8><<<pg, cta, sm, st>>>(D, Y, R, n_inst, total_warps, src, dst, last);
+            else k_bulk_x_p<5, 4><<<pg, cta, sm, st>>>(D, Y, R, n_inst, total_warps, src, dst, last);
+        } else if (eq == 0) k_bulk_x<T, 0><<<blocks, 256, 0, st>>>(D, Y, R, n_inst, total_warps, src, dst, last);
         else k_bulk_x<T, 1><<<blocks, 256, 0, st>>>(D, Y, R, n_inst, total_warps, src, dst, last);
     } else {
-        if (packed) k_bulk_y_p<<<(total_warps + wpc - 1) / wpc, cta, wpc * sizeof(YRing), st>>>(D, Y, R, n_inst, total_warps, src, dst, last);
-        else if (eq == 0) k_bulk_y<T, 0><<<blocks, 256, 0, st>>>(D, Y, R, n_inst, total_warps, src, dst, last);
+        if (packed) {
+            const size_t sm = wpc * sizeof(YRing);
+            if (m4) k_bulk_y_p<4><<<pg, cta, sm, st>>>(D, Y, R, n_inst, total_warps, src, dst, last);
+            else k_bulk_y_p<5><<<pg, cta, sm, st>>>(D, Y, R, n_inst, total_warps, src, dst, last);
+        } else if (eq == 0) k_bulk_y<T, 0><<<blocks, 256, 0, st>>>(D, Y, R, n_inst, total_warps, src, dst, last);
         else k_bulk_y<T, 1><<<blocks, 256, 0, st>>>(D, Y, R, n_inst, total_warps, src, dst, last);
     }
 }
@@ -1545,11 +1653,16 @@ template <class T>
 int bulk_blocks_per_sm(int dir) {
     bulk_attr_t<T, 0>(dir);
     bulk_attr_t<T, 1>(dir);
-    if (sizeof(T) == 4) {   // the FP32x2 kernels' shared-memory rings
-        if (dir == 0)
-            cudaFuncSetAttribute(k_bulk_x_p, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(4 * sizeof(XRing)));
-        else
-            cudaFuncSetAttribute(k_bulk_y_p, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(4 * sizeof(YRing)));
+    if (sizeof(T) == 4) {   // the FP32x2 kernels' shared-memory rings (4 warps per CTA at most)
+        if (dir == 0) {
+            cudaFuncSetAttribute(k_bulk_x_p<5, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(4 * sizeof(XRing<4>)));
+            cudaFuncSetAttribute(k_bulk_x_p<4, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(4 * sizeof(XRing<4>)));
+            cudaFuncSetAttribute(k_bulk_x_p<5, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(4 * sizeof(XRing<8>)));
+            cudaFuncSetAttribute(k_bulk_x_p<4, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(4 * sizeof(XRing<8>)));
+        } else {
+            cudaFuncSetAttribute(k_bulk_y_p<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(4 * sizeof(YRing)));
+            cudaFuncSetAttribute(k_bulk_y_p<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(4 * sizeof(YRing)));
+        }
     }
     return 1;
 }

@@ -229,9 +229,10 @@ class Sim:
 
     def autotune(self):
         """Tune the bulk kernels' launch shapes (mb_autotune); returns the choice."""
-        r = np.zeros(5)
+        r = np.zeros(8)
         self._check(lib.mb_autotune(self._h, _dp(r)))
-        return dict(x_cta=int(r[0]), y_cta=int(r[1]), y_rows=int(r[2]), x_ms=r[3], y_ms=r[4])
+        return dict(x_cta=int(r[0]), y_cta=int(r[1]), y_rows=int(r[2]), x_ms=r[3], y_ms=r[4],
+                    x_min_ctas=int(r[5]), y_min_ctas=int(r[6]), x_ring_chunks=int(r[7]))
 
     def enable_timing(self, on=True):
         self._check(lib.mb_enable_timing(self._h, 1 if on else 0))
