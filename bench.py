@@ -431,6 +431,21 @@ def main():
     status = sim.sync()
     value = job_value(cells_all, args.steps, total_ms)
 
+    # the same steps with every bulk cell waiting for the band fluxes (no
+    # overlap of the bulk pass with the geometry), for comparison
+    serial_ms = None
+    if prec == mb.FP32:
+        sim.set_overlap(False)
+        with torch.cuda.stream(stream):
+            sim.run(2, 0.0)
+            e_a, e_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e_a.record(stream)
+            sim.run(10, 0.0)
+            e_b.record(stream)
+        torch.cuda.synchronize()
+        serial_ms = e_a.elapsed_time(e_b) / 10
+        sim.set_overlap(True)
+
     # dominant kernel: bulk sweep, timed with CUDA events on its stream
     sim.enable_timing(True)
     sim.run(4, 0.0)
@@ -476,6 +491,7 @@ def main():
                    "autotuned": {k: tune.get(k) for k in ("x_cta", "y_cta", "y_rows", "x_min_ctas", "y_min_ctas",
                                                           "x_ring_chunks")}},
         "p50_ms_per_step": float(np.percentile(per, 50)), "p99_ms_per_step": float(np.percentile(per, 99)),
+        "ms_per_step_without_overlap": serial_ms,
         "status": int(status),
         "roofline": {"kernel": "bulk sweep update (MUSCL-Hancock + HLLC), x and y kernels", "bound": "hbm", "achieved": achieved,
                      "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,

@@ -27,14 +27,15 @@ void launch_nodes(const InstDesc *, int, cudaStream_t);
 void launch_pose(const InstDesc *, InstDyn *, const double *, const double *, const unsigned char *, const int *,
                  double *, double *, float *, int, int, int, int, double, cudaStream_t);
 void launch_geom(const InstDesc *, InstDyn *, const int *, const double *, const double *, const float *, const int *,
-                 const unsigned char *, int, int, int, int, BandRec *, double *, cudaStream_t);
+                 const unsigned char *, int, int, int, int, BandRec *, double *, int, cudaStream_t);
 void launch_classify(const InstDesc *, InstDyn *, const double *, const double *, const unsigned char *, double *,
                      double *, float *, const int *, int, int, int, double *, cudaStream_t);
 template <class T>
 void launch_band_stage(int, const InstDesc *, InstDyn *, BandRec *, const double *, int *, int, int, int, int, int,
                        int, int, int, cudaStream_t);
 template <class T>
-void launch_bulk(int, int, const InstDesc *, InstDyn *, const BandRec *, int, int, int, int, int, int, cudaStream_t);
+void launch_bulk(int, int, const InstDesc *, InstDyn *, const BandRec *, int, int, int, int, int, int, int, DeferList,
+                 int, cudaStream_t);
 template <class T>
 int bulk_blocks_per_sm(int);
 template <class T>
@@ -83,6 +84,18 @@ struct mb_sim {
     int *ginst = nullptr;         // instance of each geometry group
     int total_tiles[2] = {0, 0};
     int bulk_grid[2] = {0, 0};
+    // cell pairs whose bulk update waits for the band fluxes (FP32 Euler)
+    int2 *ditem = nullptr;
+    int *dcount = nullptr;
+    size_t cap_ditem = 0, cap_dcount = 0;
+    // the geometry and band-flux kernels of a sweep run on this stream,
+    // concurrently with the bulk pass on the sim's stream (FP32 Euler)
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    bool overlap = true;          // mb_set_overlap
+    // geometry CTAs per SM while the bulk pass runs beside them (they loop
+    // over the geometry groups; the rest of each SM holds bulk CTAs)
+    int geom_ctas_per_sm = 3;
     // launch shapes of the bulk kernels (mb_autotune): CTA size, register
     // budget and ring depth per direction of the FP32x2 kernels, rows per
     // thread of the y sweep
@@ -153,11 +166,16 @@ static void free_all(mb_sim *s) {
         for (void *p : h.allocs) cudaFree(p);
     s->ih.clear();
     void *shared[] = {s->dd, s->dy, s->vx, s->vy, s->px, s->py, s->ebox, s->vmov, s->vnext,
-                      s->rec, s->bnd, s->scratch, s->stage, s->ginst};
+                      s->rec, s->bnd, s->scratch, s->stage, s->ginst, s->ditem, s->dcount};
     for (void *p : shared)
         if (p) cudaFree(p);
     if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
     s->stream = nullptr;
+    if (s->side) cudaStreamDestroy(s->side);
+    if (s->ev_fork) cudaEventDestroy(s->ev_fork);
+    if (s->ev_join) cudaEventDestroy(s->ev_join);
+    s->side = nullptr;
+    s->ev_fork = s->ev_join = nullptr;
 }
 
 static mb_status map_err(mb_sim *s, int e) {
@@ -166,13 +184,14 @@ static mb_status map_err(mb_sim *s, int e) {
     mb_status st = MB_E_UNSTABLE;
     if (e & ERR_EDGE_CAP) { m += "edge list of a geometry column overflowed; "; st = MB_E_CAPACITY; }
     if (e & ERR_BAND_CAP) { m += "band record capacity overflowed; "; st = MB_E_CAPACITY; }
+    if (e & ERR_DEFER_CAP) { m += "list of bulk cells deferred to the band fluxes overflowed; "; st = MB_E_CAPACITY; }
     if (e & ERR_STATE) { m += "second sweep of a step used another dt; "; st = MB_E_STATE; }
     if (e & ERR_NONBR) m += "covered/uncovered cell without a fluid neighbour; ";
     if (e & ERR_UNSTABLE) m += "non-physical state (rho or p <= 0 or non-finite); ";
     if (e & ERR_MIX_CAP) m += "more non-physical cells in one sweep than the positivity safeguard lists; ";
     if (e & ERR_MIX_BULK) m += "a merged cluster is still non-physical; ";
     if (e & ERR_MIX_BAND) m += "a cut cell is still non-physical after the safeguard; ";
-    if (e & (ERR_EDGE_CAP | ERR_BAND_CAP | ERR_STATE)) {
+    if (e & (ERR_EDGE_CAP | ERR_BAND_CAP | ERR_STATE | ERR_DEFER_CAP)) {
     } else {
         st = MB_E_UNSTABLE;
     }
@@ -274,6 +293,7 @@ static void describe_instance(int prec, int yseg, const mb_grid &g, double gamma
 static cudaError_t make_instance(mb_sim *s, const mb_grid &g, double gamma, const mb_body &b, const mb_motion &m,
                                  InstDesc &I, InstHost &h) {
     describe_instance(s->prec, s->tune_yseg, g, gamma, b, m, I, h);
+    I.serial_bulk = s->overlap ? 0 : 1;
     const size_t esz = s->prec == MB_FP32 ? 4 : 8;
     const size_t cells = (size_t)I.pitch * g.ny;
     cudaError_t e = cudaSuccess;
@@ -365,6 +385,10 @@ static cudaError_t relayout(mb_sim *s, int old_n, const std::vector<int> &from) 
     if (e == cudaSuccess) e = ensure(&s->dd, s->cap_dd, std::max(1, n), sizeof(InstDesc));
     if (e == cudaSuccess) e = ensure(&s->dy, s->cap_dy, std::max(1, n), sizeof(InstDyn));
     if (e == cudaSuccess) e = ensure(&s->ginst, s->cap_ginst, std::max<size_t>(1, ginst.size()), sizeof(int));
+    // a touched cell defers at most 4 cell pairs of its line; the cells
+    // touched at a sweep's start pose are band cells of the sweep before
+    if (e == cudaSuccess) e = ensure(&s->ditem, s->cap_ditem, 4 * (size_t)rec_total + 4096, sizeof(int2));
+    if (e == cudaSuccess) e = ensure(&s->dcount, s->cap_dcount, 1, sizeof(int));
     if (e != cudaSuccess) return e;
     // the posed vertices of pose slot 0 are refreshed by every classification;
     // the other slots by every sweep
@@ -420,6 +444,13 @@ mb_status mb_batch_create(int n, const mb_grid *grids, const double *gammas, con
     } while (0)
     CK(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
     s->own_stream = true;
+    {
+        int lo = 0, hi = 0;
+        CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+        CK(cudaStreamCreateWithPriority(&s->side, cudaStreamNonBlocking, hi));
+        CK(cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming));
+    }
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&s->nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -537,6 +568,20 @@ mb_status mb_set_stream(mb_sim *sim, void *stream) {
     return MB_OK;
 }
 
+mb_status mb_set_overlap(mb_sim *sim, int enable) {
+    if (!sim) return MB_E_INVAL;
+    if (sim->sidx != 0) return fail(sim, MB_E_STATE, "mb_set_overlap in the middle of a step");
+    cudaError_t e = cudaStreamSynchronize(sim->stream);
+    sim->overlap = enable > 0;
+    if (enable > 0) sim->geom_ctas_per_sm = std::min(enable, 8);
+    drop_graphs(sim);   // captured steps hold the launch sequence of the old setting
+    for (auto &I : sim->hd) I.serial_bulk = sim->overlap ? 0 : 1;
+    if (e == cudaSuccess && sim->n > 0)
+        e = cudaMemcpy(sim->dd, sim->hd.data(), sim->n * sizeof(InstDesc), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_check(sim, e, "set overlap");
+    return MB_OK;
+}
+
 static mb_status do_sweep(mb_sim *s, int dir, double dt) {
     int src, dst, qn;
     if (s->sidx == 0) {
@@ -552,36 +597,66 @@ static mb_status do_sweep(mb_sim *s, int dir, double dt) {
     cudaStream_t st = s->stream;
     launch_pose(s->dd, s->dy, s->vx, s->vy, s->vmov, s->vnext, s->px, s->py, s->ebox, s->total_v, s->n, dir, s->sidx,
                 dt, st);
-    launch_geom(s->dd, s->dy, s->ginst, s->px, s->py, s->ebox, s->vnext, s->vmov, s->total_v, s->n, s->total_cols, dir, s->rec,
-                s->bnd, st);
-    auto band = [&](int stage) {
+    auto band = [&](int stage, cudaStream_t sx) {
         if (s->prec == MB_FP32)
             launch_band_stage<float>(stage, s->dd, s->dy, s->rec, s->bnd, s->scratch, s->n, s->total_rec, dir, src,
-                                     dst, qn, s->sidx, last, st);
+                                     dst, qn, s->sidx, last, sx);
         else
             launch_band_stage<double>(stage, s->dd, s->dy, s->rec, s->bnd, s->scratch, s->n, s->total_rec, dir, src,
-                                      dst, qn, s->sidx, last, st);
+                                      dst, qn, s->sidx, last, sx);
     };
-    band(0);
-    band(1);
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (s->timing) {
-        cudaEventCreate(&e0);
-        cudaEventCreate(&e1);
-        cudaEventRecord(e0, st);
-    }
+    auto geom_band = [&](cudaStream_t sx, int ctas) {
+        launch_geom(s->dd, s->dy, s->ginst, s->px, s->py, s->ebox, s->vnext, s->vmov, s->total_v, s->n, s->total_cols,
+                    dir, s->rec, s->bnd, ctas, sx);
+        band(0, sx);
+        band(1, sx);
+    };
     const int eq = s->eq;
-    if (s->prec == MB_FP32)
-        launch_bulk<float>(dir, eq, s->dd, s->dy, s->rec, s->n, s->total_tiles[dir], src, dst, last, s->tune_cta[dir], st);
-    else
-        launch_bulk<double>(dir, eq, s->dd, s->dy, s->rec, s->n, s->total_tiles[dir], src, dst, last, s->tune_cta[dir], st);
-    if (s->timing) {
-        cudaEventRecord(e1, st);
-        s->evs.push_back({e0, e1});
+    // whether an instance may take the deferred pass whole this sweep (a
+    // rotating body, a host time step, or a CFL number that lets a body move
+    // 0.9 cells per sweep)
+    bool any_dall = dt > 0.0;
+    for (const auto &I : s->hd) any_dall = any_dall || I.rotating || I.cfl >= 0.9 || I.serial_bulk;
+    const DeferList dl{s->ditem, s->dcount, (int)std::min<size_t>(s->cap_ditem, 0x7fffffff)};
+    auto bulk = [&](int mode) {
+        if (mode == 0 && s->prec == MB_FP32 && eq == MB_EULER) cudaMemsetAsync(s->dcount, 0, sizeof(int), st);
+        if (s->prec == MB_FP32)
+            launch_bulk<float>(dir, eq, s->dd, s->dy, s->rec, s->n, s->total_tiles[dir], src, dst, last,
+                               s->tune_cta[dir], mode, dl, any_dall ? 1 : 0, st);
+        else
+            launch_bulk<double>(dir, eq, s->dd, s->dy, s->rec, s->n, s->total_tiles[dir], src, dst, last,
+                                s->tune_cta[dir], mode, dl, any_dall ? 1 : 0, st);
+    };
+    const bool two_pass = s->prec == MB_FP32 && eq == MB_EULER;
+    if (two_pass && !s->timing) {
+        // geometry and band fluxes (FP64 pipe, latency) on the side stream
+        // while the bulk pass that needs no band data (FP32 pipe, HBM) runs
+        // on the sim's stream; the deferred cells after both
+        cudaEventRecord(s->ev_fork, st);
+        cudaStreamWaitEvent(s->side, s->ev_fork, 0);
+        geom_band(s->side, s->geom_ctas_per_sm * s->nsm);
+        cudaEventRecord(s->ev_join, s->side);
+        bulk(0);
+        cudaStreamWaitEvent(st, s->ev_join, 0);
+        bulk(1);
+    } else {
+        geom_band(st, 0);
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (s->timing) {
+            cudaEventCreate(&e0);
+            cudaEventCreate(&e1);
+            cudaEventRecord(e0, st);
+        }
+        bulk(0);
+        bulk(1);
+        if (s->timing) {
+            cudaEventRecord(e1, st);
+            s->evs.push_back({e0, e1});
+        }
     }
-    band(2);
-    band(3);
-    band(4);
+    band(2, st);
+    band(3, st);
+    band(4, st);
     if (s->sidx == 1) {
         s->cur = dst;
         s->sidx = 0;
@@ -811,12 +886,16 @@ mb_status mb_autotune(mb_sim *sim, double *report) {
     cudaEventCreate(&e1);
     auto time_bulk = [&](int dir, int cta) -> double {
         auto go = [&]() {
-            if (sim->prec == MB_FP32)
-                launch_bulk<float>(dir, sim->eq, sim->dd, sim->dy, sim->rec, sim->n, sim->total_tiles[dir], src, dst,
-                                   0, cta, sim->stream);
-            else
-                launch_bulk<double>(dir, sim->eq, sim->dd, sim->dy, sim->rec, sim->n, sim->total_tiles[dir], src,
-                                    dst, 0, cta, sim->stream);
+            const DeferList dl{sim->ditem, sim->dcount, (int)std::min<size_t>(sim->cap_ditem, 0x7fffffff)};
+            for (int mode = 0; mode < 2; ++mode) {
+                if (mode == 0) cudaMemsetAsync(sim->dcount, 0, sizeof(int), sim->stream);
+                if (sim->prec == MB_FP32)
+                    launch_bulk<float>(dir, sim->eq, sim->dd, sim->dy, sim->rec, sim->n, sim->total_tiles[dir], src,
+                                       dst, 0, cta, mode, dl, 0, sim->stream);
+                else
+                    launch_bulk<double>(dir, sim->eq, sim->dd, sim->dy, sim->rec, sim->n, sim->total_tiles[dir], src,
+                                        dst, 0, cta, mode, dl, 0, sim->stream);
+            }
         };
         go();
         cudaEventRecord(e0, sim->stream);

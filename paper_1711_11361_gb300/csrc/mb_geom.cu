@@ -95,6 +95,11 @@ __global__ void k_pose(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y, 
         }
         double delta = I.U[dir] * dt;
         y.delta = delta;
+        // the concurrent bulk pass may update a cell before this sweep's
+        // geometry is known only when the body moves by less than a cell
+        // along the sweep and does not rotate (its band then lies within one
+        // cell, along the sweep, of the cells touched at the start pose)
+        y.defer_all = (I.serial_bulk || I.rotating || fabs(delta) >= 0.9 * (dir == 0 ? I.dx : I.dy)) ? 1 : 0;
         y.XA = y.X; y.YA = y.Y;
         y.XB = dir == 0 ? y.X + delta : y.X;
         y.YB = dir == 1 ? y.Y + delta : y.Y;
@@ -927,20 +932,17 @@ __device__ double swept_face_Bg(const GeoBufG &G, const InstDesc &I, int dir, do
     return clamp01(1.0 - A / ((y1 - y0) * I.dx));
 }
 
-__global__ void __launch_bounds__(GEOMG_THREADS, 3) k_geom(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y,
-                                                            const int *__restrict__ ginst,
-                                                         const double *__restrict__ px, const double *__restrict__ py,
-                                                         const float *__restrict__ ebox,
-                                                         const int *__restrict__ vnext,
-                                                         const unsigned char *__restrict__ vmov, int total_v,
-                                                         int n_inst, int total_groups, int dir,
-                                                         BandRec *__restrict__ R, double *__restrict__ bnd) {
+// the band cells of geometry group gw (one CTA)
+__device__ __forceinline__ void geom_group(int gw, const InstDesc *__restrict__ D, InstDyn *__restrict__ Y,
+                                           const int *__restrict__ ginst, const double *__restrict__ px,
+                                           const double *__restrict__ py, const float *__restrict__ ebox,
+                                           const int *__restrict__ vnext, const unsigned char *__restrict__ vmov,
+                                           int total_v, int n_inst, int total_groups, int dir,
+                                           BandRec *__restrict__ R, double *__restrict__ bnd, int &sh_base) {
     extern __shared__ __align__(16) unsigned char gsm[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, tid = threadIdx.x;
     GeoWarpG &W = *(GeoWarpG *)gsm;
     GeoBufG &G = W.G;
-    __shared__ int sh_base;
-    const int gw = blockIdx.x;
     if (gw >= total_groups) return;
     const int lo = ginst[gw];
     const InstDesc &I = D[lo];
@@ -1131,6 +1133,24 @@ __global__ void __launch_bounds__(GEOMG_THREADS, 3) k_geom(const InstDesc *__res
     if (err) atomicOr(&y.err, err);
 }
 
+// One CTA per geometry group, or (when the bulk pass runs concurrently) a
+// grid of fewer CTAs that loop over the groups, so that every SM keeps room
+// for bulk CTAs beside its geometry CTA.
+__global__ void __launch_bounds__(GEOMG_THREADS, 3) k_geom(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y,
+                                                            const int *__restrict__ ginst,
+                                                            const double *__restrict__ px, const double *__restrict__ py,
+                                                            const float *__restrict__ ebox,
+                                                            const int *__restrict__ vnext,
+                                                            const unsigned char *__restrict__ vmov, int total_v,
+                                                            int n_inst, int total_groups, int dir,
+                                                            BandRec *__restrict__ R, double *__restrict__ bnd) {
+    __shared__ int sh_base;
+    for (int gw = blockIdx.x; gw < total_groups; gw += gridDim.x) {
+        geom_group(gw, D, Y, ginst, px, py, ebox, vnext, vmov, total_v, n_inst, total_groups, dir, R, bnd, sh_base);
+        __syncthreads();
+    }
+}
+
 // ---------------------------------------------------------------------------
 // full classification at the pose in slot 0 (create / write_state / alpha)
 // ---------------------------------------------------------------------------
@@ -1242,8 +1262,8 @@ void launch_pose(const InstDesc *D, InstDyn *Y, const double *vx, const double *
 
 void launch_geom(const InstDesc *D, InstDyn *Y, const int *ginst, const double *px, const double *py, const float *ebox,
                  const int *vnext, const unsigned char *vmov, int total_v, int n_inst, int total_groups, int dir,
-                 BandRec *R, double *bnd, cudaStream_t st) {
-    int blocks = total_groups;
+                 BandRec *R, double *bnd, int ctas, cudaStream_t st) {
+    int blocks = (ctas > 0 && ctas < total_groups) ? ctas : total_groups;
     if (blocks > 0)
         k_geom<<<blocks, GEOMG_THREADS, geomg_smem(), st>>>(D, Y, ginst, px, py, ebox, vnext, vmov, total_v, n_inst,
                                                              total_groups, dir, R, bnd);

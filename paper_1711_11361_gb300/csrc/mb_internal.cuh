@@ -39,6 +39,7 @@ constexpr int ERR_UNSTABLE = 1, ERR_EDGE_CAP = 2, ERR_BAND_CAP = 4, ERR_NONBR = 
 constexpr int ERR_MIX_CAP = 32;     // more non-physical cells than the safeguard's lists hold
 constexpr int ERR_MIX_BULK = 64;    // a merged cluster still non-physical (non-band cell)
 constexpr int ERR_MIX_BAND = 128;   // a band cell still non-physical after merging
+constexpr int ERR_DEFER_CAP = 256;  // the list of deferred bulk cells overflowed
 
 struct BandRec {
     int cell;            // j*pitch + i
@@ -59,6 +60,14 @@ struct BandRec {
     double den;          // event weight denominator
     int mix;             // safeguard cluster root (record index) or -1
     int pad;
+};
+
+// list of the cell pairs whose bulk update waits for the band fluxes (FP32
+// Euler sweeps; written by the concurrent bulk pass, read by k_bulk_def_*)
+struct DeferList {
+    int2 *item;     // (instance, first cell of the pair | cells to store << 28)
+    int *count;
+    int cap;
 };
 
 struct InstDesc {
@@ -82,6 +91,7 @@ struct InstDesc {
     double wall_bound[2];
     int rec_base, rec_cap;
     int gcol_max, gcol_off;     // geometry columns reserved for this instance
+    int serial_bulk;            // 1: no bulk cell is updated before the sweep's band fluxes
     int yseg;                   // rows per thread of the y sweep (tuned)
     int tile_off[2];            // first bulk tile (per direction)
     int ntiles[2];
@@ -104,7 +114,7 @@ struct InstDyn {
     int col0, col1;
     int row0, row1;             // rows of the body's extent over the sweep's poses
     float lamf;                 // dt / h along the sweep (FP32 kernels)
-    int pad2;
+    int defer_all;              // every bulk cell waits for the band fluxes (see k_pose)
     double lam;                 // dt / h along the sweep
     int band_count;
     int nbad;

@@ -102,6 +102,50 @@ __device__ double face_beta(const InstDesc &I, const BandRec *R, const double *b
     return (cl & CLS_SOLID) ? 0.0 : 1.0;
 }
 
+// Per-instance accumulations of the band kernels (wall terms, wave speeds):
+// the records a warp holds usually belong to one instance (records are
+// grouped by instance), so the warp combines its threads' values and issues
+// one atomic; otherwise every thread issues its own.  All 32 lanes call.
+__device__ __forceinline__ bool warp_one_inst(bool act, int inst, int &i0) {
+    const unsigned m = __ballot_sync(0xffffffffu, act);
+    i0 = m ? __shfl_sync(0xffffffffu, inst, __ffs(m) - 1) : -1;
+    return __all_sync(0xffffffffu, !act || inst == i0);
+}
+
+__device__ __forceinline__ void warp_add_to(InstDyn *Y, bool act, int inst, const double *v) {
+    int i0;
+    if (warp_one_inst(act, inst, i0)) {
+        if (i0 < 0) return;
+        for (int q = 0; q < MAXC; ++q) {
+            double s = act ? v[q] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if ((threadIdx.x & 31) == 0 && s != 0.0) atomicAdd(&Y[i0].wall_sum[q], s);
+        }
+    } else if (act) {
+        for (int q = 0; q < MAXC; ++q)
+            if (v[q] != 0.0) atomicAdd(&Y[inst].wall_sum[q], v[q]);
+    }
+}
+
+__device__ __forceinline__ void warp_max_to(InstDyn *Y, bool act, int inst, double s0, double s1) {
+    int i0;
+    if (warp_one_inst(act, inst, i0)) {
+        if (i0 < 0) return;
+        if (!act) s0 = s1 = 0.0;
+        for (int o = 16; o > 0; o >>= 1) {
+            s0 = fmax(s0, __shfl_xor_sync(0xffffffffu, s0, o));
+            s1 = fmax(s1, __shfl_xor_sync(0xffffffffu, s1, o));
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomic_max_pos(&Y[i0].S[0], s0);
+            atomic_max_pos(&Y[i0].S[1], s1);
+        }
+    } else if (act) {
+        atomic_max_pos(&Y[inst].S[0], s0);
+        atomic_max_pos(&Y[inst].S[1], s1);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // k_band_prep
 // ---------------------------------------------------------------------------
@@ -268,14 +312,14 @@ __device__ __noinline__ void face_stab(int eq, T g, int dir, T lamT, T av0, T av
 // k_band_sweep: both sweep-direction faces of each band cell and its content
 // ---------------------------------------------------------------------------
 template <class T>
-__global__ void k_band_sweep(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y, BandRec *__restrict__ R,
-                             const double *__restrict__ bnd, int n_inst, int total_rec, int dir, int src) {
-    int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= total_rec) return;
+__device__ __forceinline__ bool band_sweep_rec(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y,
+                                               BandRec *__restrict__ R, const double *__restrict__ bnd, int n_inst,
+                                               int r, int dir, int src, double *wsum, int &inst_out) {
     int inst = find_inst_rec(D, n_inst, r);
+    inst_out = inst;
     const InstDesc &I = D[inst];
     InstDyn &y = Y[inst];
-    if (r - I.rec_base >= y.band_count) return;
+    if (r - I.rec_base >= y.band_count) return false;
     BandRec &b = R[r];
     const int l = dir == 0 ? b.j : b.i, k = dir == 0 ? b.i : b.j;
     const double lam = y.lam;
@@ -318,12 +362,23 @@ __global__ void k_band_sweep(const InstDesc *__restrict__ D, InstDyn *__restrict
             if (blo != bhi && (b.flags & RF_WALL)) {
                 double wt = lam * (bhi - blo) * (b.FB[q] - wd * b.QB[q]);
                 v += wt;
-                atomicAdd(&y.wall_sum[q], wt);
+                wsum[q] += wt;
             }
             C[q] = v;
         }
     }
     for (int q = 0; q < MAXC; ++q) b.C[q] = C[q];
+    return true;
+}
+
+template <class T>
+__global__ void k_band_sweep(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y, BandRec *__restrict__ R,
+                             const double *__restrict__ bnd, int n_inst, int total_rec, int dir, int src) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    double ws[MAXC] = {0.0, 0.0, 0.0, 0.0};
+    int inst = -1;
+    const bool act = r < total_rec && band_sweep_rec<T>(D, Y, R, bnd, n_inst, r, dir, src, ws, inst);
+    warp_add_to(Y, act, inst, ws);
 }
 
 // ---------------------------------------------------------------------------
@@ -843,27 +898,84 @@ struct XRing {
 // faces carry stabilised fluxes)
 constexpr unsigned CLS_OFF = CLS_SOLID | CLS_BAND;
 
-// x sweep, packed: one warp per row, lane l holds cells 64c + 2l and
-// 64c + 2l + 1 of chunk c; the update trails the fluxes by one chunk.  A
-// chunk whose cells and stencil halo are all plain fluid cells takes the
-// plain path (no limiter switches, no face replacement, whole-pair stores);
-// the decision is warp-uniform, from a ballot over the class bytes.
-// MINB: resident CTAs per SM the registers are budgeted for; XC: ring chunks.
-template <int MINB, int XC>
-__global__ void __launch_bounds__(128, MINB) k_bulk_x_p(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y,
-                                                  const BandRec *__restrict__ R, int n_inst, int total_warps, int src,
-                                                  int dst, int last) {
-    extern __shared__ __align__(16) unsigned char xsm[];
+// Deferred cells of a sweep (FP32 Euler).  A cell is deferred when a cell
+// within three positions of it along the sweep was touched by the body
+// boundary at the start pose.  The body moves by less than a cell per sweep
+// and only along the sweep (k_pose sets defer_all otherwise, and for a
+// rotating body), so every band cell of the sweep lies within one position
+// of a touched cell, and so does every fluid cell next to a solid cell.  A
+// cell that is not deferred therefore has a five-cell stencil of plain
+// fluid cells (its update is the plain MUSCL-Hancock + HLLC update), or is
+// solid at both poses (its state is NaN).  Neither needs the sweep's
+// geometry, so the pass that stores them (mode 0) runs concurrently with the
+// geometry and band-flux kernels.  The deferred cells are appended, as cell
+// pairs, to a list that k_bulk_def_* work through after the band fluxes, on
+// the general path; an instance with defer_all is updated by a second
+// streaming pass (mode 1) instead.  The arithmetic of every cell is that of
+// a single general pass.
+
+// append this lane's pair (cell index ci of its first cell) when bits != 0;
+// one atomic per warp
+__device__ __forceinline__ void defer_push(const DeferList &L, InstDyn &y, int inst, int ci, int bits) {
+    const unsigned m = __ballot_sync(0xffffffffu, bits != 0);
+    if (!m) return;
     const int lane = threadIdx.x & 31;
+    int base = 0;
+    if (lane == __ffs(m) - 1) base = atomicAdd(L.count, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
+    if (bits) {
+        const int k = base + __popc(m & ((1u << lane) - 1u));
+        if (k < L.cap) L.item[k] = make_int2(inst, ci | (bits << 28));
+        else atomicOr(&y.err, ERR_DEFER_CAP);
+    }
+}
+
+// deferred bits of a lane's two cells in the chunk before the current one,
+// from the lane masks (bit l: lane l's pair, t0 its first cell, t1 its
+// second) of touched cells in the chunks before it (p2), itself (p1) and
+// after it (c)
+__device__ __forceinline__ int deferred_pair(int lane, unsigned p2_0, unsigned p2_1, unsigned p1_0, unsigned p1_1,
+                                             unsigned c_0, unsigned c_1) {
+    // window over lanes -2 .. 33 of the chunk: bit l + 2 holds lane l
+    const unsigned long long P = (unsigned long long)((p2_0 | p2_1) >> 30) |
+                                 ((unsigned long long)(p1_0 | p1_1) << 2) |
+                                 ((unsigned long long)(c_0 | c_1) << 34);
+    const unsigned long long W1 = (unsigned long long)(p2_1 >> 30) | ((unsigned long long)p1_1 << 2) |
+                                  ((unsigned long long)c_1 << 34);
+    const unsigned long long W0 = (unsigned long long)(p2_0 >> 30) | ((unsigned long long)p1_0 << 2) |
+                                  ((unsigned long long)c_0 << 34);
+    const bool mid = ((P >> (lane + 1)) & 7ull) != 0;        // lanes l-1, l, l+1
+    const bool d0 = mid || ((W1 >> lane) & 1ull);            // cell 2l-3 (lane l-2, second)
+    const bool d1 = mid || ((W0 >> (lane + 4)) & 1ull);      // cell 2l+4 (lane l+2, first)
+    return (d0 ? 1 : 0) | (d1 ? 2 : 0);
+}
+
+// x sweep, packed: one warp per row, lane l holds cells 64c + 2l and
+// 64c + 2l + 1 of chunk c; the update trails the fluxes by one chunk.
+// MODE 0: the cells that are not deferred (plain arithmetic throughout);
+// MODE 1: every cell of the instances with defer_all, on the general path
+// (a chunk whose cells and stencil halo are all plain fluid cells still takes
+// the plain arithmetic, decided by a warp-uniform ballot over the class
+// bytes).  MINB: resident CTAs per SM the registers are budgeted for; XC:
+// ring chunks.
+template <int MINB, int XC, int MODE>
+__global__ void __launch_bounds__(128, MINB) k_bulk_x_p(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y,
+                                                     const BandRec *__restrict__ R, int n_inst, int total_warps,
+                                                     int src, int dst, int last, DeferList dl) {
+    extern __shared__ __align__(16) unsigned char xsm[];
     constexpr int XRN = 64 * XC;
+    constexpr bool gen = MODE != 0;
+    const int lane = threadIdx.x & 31;
     XRing<XC> &rg = ((XRing<XC> *)xsm)[threadIdx.x >> 5];
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (gw >= total_warps) return;
     const int inst = find_inst_warp(D, n_inst, gw, 0);
     const InstDesc &I = D[inst];
     InstDyn &y = Y[inst];
+    if ((MODE == 0) == (y.defer_all != 0)) return;
     const int j = gw - I.tile_off[0];
     const int n = I.nx;
+    const int c_last = (n + 1) >> 6;   // chunk holding face n
     const float lam = y.lamf;
     const float g = (float)I.gamma, g1 = g - 1.0f;
     const size_t plane = (size_t)I.pitch * I.ny;
@@ -912,7 +1024,14 @@ __global__ void __launch_bounds__(128, MINB) k_bulk_x_p(const InstDesc *__restri
         }
         cp_async_commit();
     };
-    const int c_last = (n + 1) >> 6;   // chunk holding face n
+    // lane masks of chunk c's cells touched at the start pose (positions
+    // outside -2 .. n + 1 hold stale ring contents and count as clear)
+    auto touch_masks = [&](int c, unsigned &m0, unsigned &m1) {
+        const int a = 64 * c + 2 * lane;
+        const int cc = *(const unsigned short *)&rg.cls[a & (XRN - 1)];
+        m0 = __ballot_sync(0xffffffffu, a >= -2 && a <= n + 1 && (cc & CLS_TOUCH));
+        m1 = __ballot_sync(0xffffffffu, a + 1 >= -2 && a + 1 <= n + 1 && ((cc >> 8) & CLS_TOUCH));
+    };
 #pragma unroll
     for (int c = 0; c < XC - 2; ++c) prefetch(c);
     cp_async_wait<XC - 4>();   // chunks 0 and 1 complete
@@ -929,21 +1048,34 @@ __global__ void __launch_bounds__(128, MINB) k_bulk_x_p(const InstDesc *__restri
             q0[k] = P2(rg.q[k][XRN - 1]);
             qp[k] = P2(rg.q[k][0]);
         }
-        const bool lim = !(rg.cls[XRN - 2] & CLS_SOLID) && !(rg.cls[0] & CLS_SOLID);
+        const bool lim = !gen || (!(rg.cls[XRN - 2] & CLS_SOLID) && !(rg.cls[0] & CLS_SOLID));
         E2 QL;
         evolve2<0>(g1, lam, qm, q0, qp, lim, lim, QL, QRc);
     }
-    // cells -2 and -1 plain (ghost classes), previous chunk entirely plain
+    // plain-path state of the general path: cells 64c-2, 64c-1 plain, and
+    // the previous chunk entirely plain
     bool prev_hi = !((rg.cls[XRN - 2] | rg.cls[XRN - 1]) & CLS_OFF);
     bool prev_all = false;
-    // validity of this lane's pair for the plain-path test: positions past
-    // n + 1 hold stale ring contents and are never used for a real cell
+    // touch masks of the two chunks before the current one
+    unsigned tp2_0 = 0u, tp2_1 = 0u, tp1_0 = 0u, tp1_1 = 0u;
+    if (!gen) touch_masks(-1, tp1_0, tp1_1);
     const int rem = n + 1 - 2 * lane;
     float s0 = 0.0f, s1 = 0.0f;
     float2 Fprev[4];
+    // cells of the chunk before c that this pass stores and that are solid
+    // at the start pose; mode 0 lists the deferred pairs
+    auto store_bits = [&](int c, unsigned tc_0, unsigned tc_1, int cm, int &sol) {
+        const int ap = 64 * (c - 1) + 2 * lane;
+        const int real = (ap < n ? 1 : 0) | (ap + 1 < n ? 2 : 0);
+        sol = ((cm & CLS_SOLID) ? 1 : 0) | (((cm >> 8) & CLS_SOLID) ? 2 : 0);
+        if (gen) return real;
+        const int dp = deferred_pair(lane, tp2_0, tp2_1, tp1_0, tp1_1, tc_0, tc_1) & real;
+        defer_push(dl, y, inst, rowb + ap, dp);
+        return real & ~dp;
+    };
     // update of the chunk before c (faces Fprev, high face of lane 31 from
-    // this chunk's lane 0), with class checks; tail: no chunk c
-    auto update_general = [&](int c, const float2 *F, bool tail) {
+    // this chunk's lane 0; tail: the row's last chunk) on the general path
+    auto update_general = [&](int c, const float2 *F, bool tail, int sm, int cm) {
         float2 Fhi[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -956,17 +1088,16 @@ __global__ void __launch_bounds__(128, MINB) k_bulk_x_p(const InstDesc *__restri
         S2 Qm;
 #pragma unroll
         for (int k = 0; k < 4; ++k) Qm.q[k] = *(const float2 *)&rg.q[k][pp];
-        const int cm = *(const unsigned short *)&rg.cls[pp];
-        const bool in1 = tail ? lane < 31 : true;
+        const bool w0 = (sm & 1) != 0, w1 = (sm & 2) && (tail ? lane < 31 : true);
         int st = 0;
-        if (ap < n && !((cm & 0xff) & CLS_OFF)) st |= 1;
-        if (ap + 1 < n && in1 && !(((cm >> 8) & 0xff) & CLS_OFF)) st |= 2;
+        if (w0 && !((cm & 0xff) & CLS_OFF)) st |= 1;
+        if (w1 && !(((cm >> 8) & 0xff) & CLS_OFF)) st |= 2;
         if (st) update2(Qb, plane, rowb + ap, st, st == 3, g1, g, lam, Qm.q, Fprev, Fhi, last, s0, s1, y);
-        if ((cm & CLS_SOLID) && ap < n) {
+        if ((cm & CLS_SOLID) && w0) {
 #pragma unroll
             for (int k = 0; k < 4; ++k) Qo[k * plane + ap] = NAN;
         }
-        if (((cm >> 8) & CLS_SOLID) && ap + 1 < n && in1) {
+        if (((cm >> 8) & CLS_SOLID) && w1) {
 #pragma unroll
             for (int k = 0; k < 4; ++k) Qo[k * plane + ap + 1] = NAN;
         }
@@ -981,13 +1112,19 @@ __global__ void __launch_bounds__(128, MINB) k_bulk_x_p(const InstDesc *__restri
         const int a = 64 * c + 2 * lane;
         const int pa = a & (XRN - 1), pl = (a - 1) & (XRN - 1), pr = (a + 2) & (XRN - 1);
         const int c0 = *(const unsigned short *)&rg.cls[pa];
-        // plain-path test over cells 64c-2 .. 64c+64 (those up to n+1)
-        const int lim = rem - 64 * c;
-        const int vm = lim >= 1 ? 0x0505 : (lim == 0 ? 0x0005 : 0);
-        const unsigned bal = __ballot_sync(0xffffffffu, !(c0 & vm));
-        const int ah = 64 * c + 64;
-        const bool hclean = ah > n + 1 || !(rg.cls[ah & (XRN - 1)] & CLS_OFF);
-        const bool plain = bal == 0xffffffffu && prev_hi && hclean;
+        bool plain = true;
+        unsigned bal = 0xffffffffu;
+        if (gen) {
+            // plain-path test over cells 64c-2 .. 64c+64 (those up to n+1)
+            const int lim = rem - 64 * c;
+            const int vm = lim >= 1 ? 0x0505 : (lim == 0 ? 0x0005 : 0);
+            bal = __ballot_sync(0xffffffffu, !(c0 & vm));
+            const int ah = 64 * c + 64;
+            const bool hclean = ah > n + 1 || !(rg.cls[ah & (XRN - 1)] & CLS_OFF);
+            plain = bal == 0xffffffffu && prev_hi && hclean;
+        }
+        unsigned tc_0 = 0u, tc_1 = 0u;
+        if (!gen) touch_masks(c, tc_0, tc_1);
         S2 Q0;
         float2 qm[4], qp[4];
 #pragma unroll
@@ -1027,8 +1164,14 @@ __global__ void __launch_bounds__(128, MINB) k_bulk_x_p(const InstDesc *__restri
             if (a + 1 <= n) face_override<0>(I, R, j, a + 1, n, (uint8_t)cA, (uint8_t)cB, F, 1);
         }
         if (c >= 1) {
-            if (prev_all && 64 * c <= n) {
-                // chunk c-1: 64 real plain cells
+            const int ap = a - 64;
+            const int pp = ap & (XRN - 1);
+            const int cm = *(const unsigned short *)&rg.cls[pp];
+            int sol;
+            const int sm = store_bits(c, tc_0, tc_1, cm, sol);
+            if (!gen || (prev_all && 64 * c <= n)) {
+                // chunk c-1 on the plain path: the stored cells are plain, or
+                // (mode 0) solid at both poses
                 float2 Fhi[4];
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
@@ -1036,28 +1179,41 @@ __global__ void __launch_bounds__(128, MINB) k_bulk_x_p(const InstDesc *__restri
                     const float nx0 = __shfl_sync(0xffffffffu, F[k].x, 0);
                     Fhi[k] = make_float2(Fprev[k].y, lane == 31 ? nx0 : dn);
                 }
-                const int ap = a - 64;
-                const int pp = ap & (XRN - 1);
                 float2 qn[4];
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     const float2 qo = *(const float2 *)&rg.q[k][pp];
                     qn[k] = fma2(P2(lam), sub2(Fprev[k], Fhi[k]), qo);
-                    *(float2 *)(Qo + k * plane + ap) = qn[k];
                 }
+                const int sq = sm & sol;   // solid at both poses: NaN
+                if (sq) {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) qn[k] = make_float2((sq & 1) ? NAN : qn[k].x, (sq & 2) ? NAN : qn[k].y);
+                }
+                if (sm == 3) {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) *(float2 *)(Qo + k * plane + ap) = qn[k];
+                } else if (sm) {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        if (sm & 1) Qo[k * plane + ap] = qn[k].x;
+                        if (sm & 2) Qo[k * plane + ap + 1] = qn[k].y;
+                    }
+                }
+                const int st = sm & ~sol;
                 float2 ir, p;
                 prim2(g1, qn, ir, p);
-                if (!(qn[0].x > 0.0f && p.x > 0.0f)) list_bulk_bad(y, rowb + ap);
-                if (!(qn[0].y > 0.0f && p.y > 0.0f)) list_bulk_bad(y, rowb + ap + 1);
+                if ((st & 1) && !(qn[0].x > 0.0f && p.x > 0.0f)) list_bulk_bad(y, rowb + ap);
+                if ((st & 2) && !(qn[0].y > 0.0f && p.y > 0.0f)) list_bulk_bad(y, rowb + ap + 1);
                 if (last) {
                     const float2 cs = sqrt2(mul2(mul2(P2(g), p), ir));
                     const float2 w0 = add2(make_float2(fabsf(qn[1].x * ir.x), fabsf(qn[1].y * ir.y)), cs);
                     const float2 w1 = add2(make_float2(fabsf(qn[2].x * ir.x), fabsf(qn[2].y * ir.y)), cs);
-                    s0 = fmaxf(s0, fmaxf(w0.x, w0.y));
-                    s1 = fmaxf(s1, fmaxf(w1.x, w1.y));
+                    if (st & 1) { s0 = fmaxf(s0, w0.x); s1 = fmaxf(s1, w1.x); }
+                    if (st & 2) { s0 = fmaxf(s0, w0.y); s1 = fmaxf(s1, w1.y); }
                 }
             } else {
-                update_general(c, F, false);
+                update_general(c, F, false, sm, cm);
             }
         }
 #pragma unroll
@@ -1068,10 +1224,18 @@ __global__ void __launch_bounds__(128, MINB) k_bulk_x_p(const InstDesc *__restri
         for (int k = 0; k < 4; ++k) Fprev[k] = F[k];
         prev_hi = (bal >> 31) != 0;
         prev_all = bal == 0xffffffffu;
+        tp2_0 = tp1_0; tp2_1 = tp1_1;
+        tp1_0 = tc_0; tp1_1 = tc_1;
     }
-    // the last chunk (its high faces were computed in the final iteration,
-    // except the one past lane 31 which lies beyond face n)
-    update_general(c_last + 1, Fprev, true);
+    // the row's last chunk (its high faces were computed in the final
+    // iteration, except the one past lane 31 which lies beyond face n)
+    {
+        const int ap = 64 * c_last + 2 * lane;
+        const int cm = *(const unsigned short *)&rg.cls[ap & (XRN - 1)];
+        int sol;
+        const int sm = store_bits(c_last + 1, 0u, 0u, cm, sol);
+        update_general(c_last + 1, Fprev, true, sm, cm);
+    }
     finish_warp<float>(y, last != 0, s0, s1);
 }
 
@@ -1085,15 +1249,19 @@ struct YRing {
 
 // y sweep, packed: one thread per pair of neighbouring columns and segment of
 // I.yseg rows, marching upward; a warp covers 64 consecutive columns and
-// streams its rows through a shared-memory ring filled by cp.async.  A row
-// step whose three rows lie inside the grid and hold only plain fluid cells
-// (warp-uniform ballot) takes the plain path.
+// streams its rows through a shared-memory ring filled by cp.async.  Passes
+// as for the x sweep: MODE 0 stores the cells that are not deferred (no cell
+// within three rows touched at the start pose) and lists the deferred pairs;
+// MODE 1 updates every cell of the instances with defer_all on the general
+// path, where a row step whose three rows lie inside the grid and hold only
+// plain fluid cells (warp-uniform ballot) still takes the plain arithmetic.
 constexpr int YCOLS_P = 64;
-template <int MINB>
+template <int MINB, int MODE>
 __global__ void __launch_bounds__(128, MINB) k_bulk_y_p(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y,
                                                      const BandRec *__restrict__ R, int n_inst, int total_warps,
-                                                     int src, int dst, int last) {
+                                                     int src, int dst, int last, DeferList dl) {
     extern __shared__ __align__(16) unsigned char ysm[];
+    constexpr bool gen = MODE != 0;
     const int lane = threadIdx.x & 31;
     YRing &rg = ((YRing *)ysm)[threadIdx.x >> 5];
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -1101,6 +1269,7 @@ __global__ void __launch_bounds__(128, MINB) k_bulk_y_p(const InstDesc *__restri
     const int inst = find_inst_warp(D, n_inst, gw, 1);
     const InstDesc &I = D[inst];
     InstDyn &y = Y[inst];
+    if ((MODE == 0) == (y.defer_all != 0)) return;
     const int local = gw - I.tile_off[1];
     const int ncg = I.tiles_x[1];
     const int cg = local % ncg, sg = local / ncg;
@@ -1121,9 +1290,9 @@ __global__ void __launch_bounds__(128, MINB) k_bulk_y_p(const InstDesc *__restri
     // validity mask of this lane's class pair for the plain-path test
     const int vm = st0 == 3 ? 0x0505 : (st0 == 1 ? 0x0005 : 0);
     // copies of row r (a ghost row of the boundary condition outside [0, n))
-    // into its slot; rows past j1 + 1 are not needed (one commit group per call)
+    // into its slot; rows past j1 + 2 are not needed (one commit group per call)
     auto prefetch = [&](int r) {
-        if (r <= j1 + 1) {
+        if (r <= j1 + 2) {
             const int s = (r - j0 + 2) & (YR - 1);
             int p = r;
             if (r < 0 || r >= n) {
@@ -1162,9 +1331,34 @@ __global__ void __launch_bounds__(128, MINB) k_bulk_y_p(const InstDesc *__restri
             v.q[2].y = -v.q[2].y;
         }
     };
+    // touched bits (start pose) of row r's two cells, from the ring; rows
+    // outside -2 .. n + 1 count as clear
+    auto touch_bits = [&](int r) {
+        if (r < -2 || r > n + 1) return 0;
+        const int c = *(const unsigned short *)&rg.cls[(r - j0 + 2) & (YR - 1)][2 * lane];
+        return ((st0 & 1) && (c & CLS_TOUCH) ? 1 : 0) | ((st0 & 2) && ((c >> 8) & CLS_TOUCH) ? 2 : 0);
+    };
     for (int r = j0 - 2; r < j0 - 2 + YR; ++r) prefetch(r);
-    cp_async_wait<YR - 3>();
+    cp_async_wait<YR - 4>();   // rows j0-2 .. j0+1 complete
     __syncwarp();
+    // history of touched bits per column (bit 0: the newest row); row j0-3
+    // comes straight from global memory
+    unsigned h0 = 0u, h1 = 0u;
+    if (!gen) {
+        const int r = j0 - 3;
+        if (r >= -2) {
+            bool fl;
+            const int p = (r < 0 || r >= n) ? ghost_map(r, n, bclo, bchi, &fl) : r;
+            const unsigned char *cp = cl + (size_t)p * pitch + i;
+            h0 = (st0 & 1) && (cp[0] & CLS_TOUCH) ? 1u : 0u;
+            h1 = (st0 & 2) && (cp[1] & CLS_TOUCH) ? 1u : 0u;
+        }
+        for (int q = j0 - 2; q <= j0 + 1; ++q) {
+            const int b = touch_bits(q);
+            h0 = (h0 << 1) | (b & 1);
+            h1 = (h1 << 1) | (b >> 1);
+        }
+    }
     E2 QRc;
     {
         S2 qa, qm, qc;
@@ -1172,9 +1366,10 @@ __global__ void __launch_bounds__(128, MINB) k_bulk_y_p(const InstDesc *__restri
         row(j0 - 2, qa, ca);
         row(j0 - 1, qm, cm);
         row(j0, qc, cc);
+        const bool lx = !gen || (!(ca & CLS_SOLID) && !(cc & CLS_SOLID));
+        const bool ly = !gen || (!((ca >> 8) & CLS_SOLID) && !((cc >> 8) & CLS_SOLID));
         E2 QL;
-        evolve2<1>(g1, lam, qa.q, qm.q, qc.q, !(ca & CLS_SOLID) && !(cc & CLS_SOLID),
-                   !((ca >> 8) & CLS_SOLID) && !((cc >> 8) & CLS_SOLID), QL, QRc);
+        evolve2<1>(g1, lam, qa.q, qm.q, qc.q, lx, ly, QL, QRc);
     }
     float s0 = 0.0f, s1 = 0.0f;
     float2 Fprev[4];
@@ -1182,51 +1377,91 @@ __global__ void __launch_bounds__(128, MINB) k_bulk_y_p(const InstDesc *__restri
     for (int f = j0; f <= j1; ++f, wp += pitch) {
         __syncwarp();
         prefetch(f + YR - 2);
-        cp_async_wait<YR - 3>();
+        cp_async_wait<YR - 4>();   // rows up to f + 2 complete
         __syncwarp();
         const int sm_ = (f - j0 + 1) & (YR - 1), sc = (f - j0 + 2) & (YR - 1), sp = (f - j0 + 3) & (YR - 1);
         const int cm = *(const unsigned short *)&rg.cls[sm_][2 * lane];
-        const int cc = *(const unsigned short *)&rg.cls[sc][2 * lane];
-        const int cp = *(const unsigned short *)&rg.cls[sp][2 * lane];
+        // cells of row f-1 this pass stores; mode 0 lists the deferred pairs
+        // (touched cells in rows f-4 .. f+2) and keeps the others
+        int sm = st0;
+        if (!gen) {
+            const int b = touch_bits(f + 2);
+            h0 = (h0 << 1) | (b & 1);
+            h1 = (h1 << 1) | (b >> 1);
+            if (f > j0) {
+                const int dp = (((h0 & 0x7Fu) ? 1 : 0) | ((h1 & 0x7Fu) ? 2 : 0)) & st0;
+                defer_push(dl, y, inst, (f - 1) * pitch + i, dp);
+                sm = st0 & ~dp;
+            }
+        }
+        const int sol = ((cm & CLS_SOLID) ? 1 : 0) | (((cm >> 8) & CLS_SOLID) ? 2 : 0);
         const bool inside = f >= 1 && f + 1 < n;
-        const bool plain = __all_sync(0xffffffffu, !((cm | cc | cp) & vm)) && inside;
+        bool plain = true;
+        if (gen) {
+            const int cc = *(const unsigned short *)&rg.cls[sc][2 * lane];
+            const int cp = *(const unsigned short *)&rg.cls[sp][2 * lane];
+            plain = __all_sync(0xffffffffu, !((cm | cc | cp) & vm)) && inside;
+        }
         float2 F[4];
         E2 QR;
         if (plain) {
-            // rows f-1, f, f+1 straight from the ring (lanes past the grid
-            // compute on stale values that are never stored)
+            // rows f-1, f, f+1 (lanes past the grid compute on values that
+            // are never stored)
             float2 qm[4], qc[4], qp[4];
+            if (inside) {
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                qm[k] = *(const float2 *)&rg.q[sm_][k][2 * lane];
-                qc[k] = *(const float2 *)&rg.q[sc][k][2 * lane];
-                qp[k] = *(const float2 *)&rg.q[sp][k][2 * lane];
+                for (int k = 0; k < 4; ++k) {
+                    qm[k] = *(const float2 *)&rg.q[sm_][k][2 * lane];
+                    qc[k] = *(const float2 *)&rg.q[sc][k][2 * lane];
+                    qp[k] = *(const float2 *)&rg.q[sp][k][2 * lane];
+                }
+            } else {
+                S2 vm_, vc, vp;
+                int c_;
+                row(f - 1, vm_, c_);
+                row(f, vc, c_);
+                row(f + 1, vp, c_);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    qm[k] = vm_.q[k];
+                    qc[k] = vc.q[k];
+                    qp[k] = vp.q[k];
+                }
             }
             E2 QL;
             evolve2<1>(g1, lam, qm, qc, qp, true, true, QL, QR);
             hllc2<1>(g, QRc, QL, F);
-            if (f > j0) {
+            if (f > j0 && __any_sync(0xffffffffu, sm != 0)) {
                 float2 qn[4];
 #pragma unroll
                 for (int k = 0; k < 4; ++k) qn[k] = fma2(P2(lam), sub2(Fprev[k], F[k]), qm[k]);
-                if (st0 == 3) {
+                const int sq = sm & sol;   // (mode 0) solid at both poses: NaN
+                if (sq) {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) qn[k] = make_float2((sq & 1) ? NAN : qn[k].x, (sq & 2) ? NAN : qn[k].y);
+                }
+                if (sm == 3) {
 #pragma unroll
                     for (int k = 0; k < 4; ++k) *(float2 *)(wp + k * plane) = qn[k];
-                } else if (st0 == 1) {
+                } else if (sm) {
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) wp[k * plane] = qn[k].x;
+                    for (int k = 0; k < 4; ++k) {
+                        if (sm & 1) wp[k * plane] = qn[k].x;
+                        if (sm & 2) wp[k * plane + 1] = qn[k].y;
+                    }
                 }
+                const int st = sm & ~sol;
                 float2 ir, p;
                 prim2(g1, qn, ir, p);
                 const int ci = (f - 1) * pitch + i;
-                if ((st0 & 1) && !(qn[0].x > 0.0f && p.x > 0.0f)) list_bulk_bad(y, ci);
-                if ((st0 & 2) && !(qn[0].y > 0.0f && p.y > 0.0f)) list_bulk_bad(y, ci + 1);
+                if ((st & 1) && !(qn[0].x > 0.0f && p.x > 0.0f)) list_bulk_bad(y, ci);
+                if ((st & 2) && !(qn[0].y > 0.0f && p.y > 0.0f)) list_bulk_bad(y, ci + 1);
                 if (last) {
                     const float2 cs = sqrt2(mul2(mul2(P2(g), p), ir));
                     const float2 w0 = add2(make_float2(fabsf(qn[1].x * ir.x), fabsf(qn[1].y * ir.y)), cs);
                     const float2 w1 = add2(make_float2(fabsf(qn[2].x * ir.x), fabsf(qn[2].y * ir.y)), cs);
-                    if (st0 & 1) { s0 = fmaxf(s0, w0.x); s1 = fmaxf(s1, w1.x); }
-                    if (st0 & 2) { s0 = fmaxf(s0, w0.y); s1 = fmaxf(s1, w1.y); }
+                    if (st & 1) { s0 = fmaxf(s0, w0.x); s1 = fmaxf(s1, w1.x); }
+                    if (st & 2) { s0 = fmaxf(s0, w0.y); s1 = fmaxf(s1, w1.y); }
                 }
             }
         } else {
@@ -1244,15 +1479,15 @@ __global__ void __launch_bounds__(128, MINB) k_bulk_y_p(const InstDesc *__restri
             if (st0 & 2) face_override<1>(I, R, i + 1, f, n, (uint8_t)(cm2 >> 8), (uint8_t)(cc2 >> 8), F, 1);
             if (f > j0) {
                 int st = 0;
-                if ((st0 & 1) && !((cm2 & 0xff) & CLS_OFF)) st |= 1;
-                if ((st0 & 2) && !(((cm2 >> 8) & 0xff) & CLS_OFF)) st |= 2;
+                if ((sm & 1) && !((cm2 & 0xff) & CLS_OFF)) st |= 1;
+                if ((sm & 2) && !(((cm2 >> 8) & 0xff) & CLS_OFF)) st |= 2;
                 const int ci = (f - 1) * pitch + i;
                 if (st) update2(Qo, plane, ci, st, st == 3, g1, g, lam, qm.q, Fprev, F, last, s0, s1, y);
-                if ((st0 & 1) && (cm2 & CLS_SOLID)) {
+                if ((sm & 1) && (cm2 & CLS_SOLID)) {
 #pragma unroll
                     for (int k = 0; k < 4; ++k) Qo[k * plane + ci] = NAN;
                 }
-                if ((st0 & 2) && ((cm2 >> 8) & CLS_SOLID)) {
+                if ((sm & 2) && ((cm2 >> 8) & CLS_SOLID)) {
 #pragma unroll
                     for (int k = 0; k < 4; ++k) Qo[k * plane + ci + 1] = NAN;
                 }
@@ -1263,6 +1498,216 @@ __global__ void __launch_bounds__(128, MINB) k_bulk_y_p(const InstDesc *__restri
         for (int k = 0; k < 4; ++k) Fprev[k] = F[k];
     }
     finish_warp<float>(y, last != 0, s0, s1);
+}
+
+// ---------------------------------------------------------------------------
+// deferred bulk cells (FP32 Euler, after the band fluxes): one thread per
+// listed cell pair, the general path of the streaming kernels for its two
+// cells (same functions on the same inputs, so the same bits): MUSCL-Hancock
+// states of the cells around the pair, their HLLC fluxes, stabilised fluxes of
+// faces touching a band cell, the update of the listed cells
+// ---------------------------------------------------------------------------
+
+// state and class of cell b of a line through the ring-free path: real and
+// ghost cells (-2 .. n+1) from global memory, filler beyond
+__device__ __forceinline__ void def_cell(const float *__restrict__ Q, const unsigned char *__restrict__ cl,
+                                         size_t plane, int n, int stride, int comp_flip, int bclo, int bchi, int b,
+                                         float *w, int &cb) {
+    if (b >= -2 && b <= n + 1) {
+        bool fl;
+        const int p = ghost_map(b, n, bclo, bchi, &fl);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) w[k] = __ldg(Q + k * plane + (size_t)p * stride);
+        if (fl) w[comp_flip] = -w[comp_flip];
+        cb = cl[(size_t)p * stride];
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) w[k] = 1.0f;
+        cb = CLS_SOLID;
+    }
+}
+
+// wave speeds of a thread into its instance: one atomic per warp when the
+// warp's threads share the instance
+__device__ __forceinline__ void def_wave_speeds(InstDyn *__restrict__ Y, int inst, bool act, float s0, float s1) {
+    const unsigned am = __activemask();
+    const int i0 = __shfl_sync(am, inst, __ffs(am) - 1);
+    if (__all_sync(am, inst == i0)) {
+        for (int o = 16; o > 0; o >>= 1) {
+            s0 = fmaxf(s0, __shfl_xor_sync(am, s0, o));
+            s1 = fmaxf(s1, __shfl_xor_sync(am, s1, o));
+        }
+        if ((threadIdx.x & 31) == __ffs(am) - 1) {
+            atomic_max_pos(&Y[i0].S[0], (double)s0);
+            atomic_max_pos(&Y[i0].S[1], (double)s1);
+        }
+    } else if (act) {
+        atomic_max_pos(&Y[inst].S[0], (double)s0);
+        atomic_max_pos(&Y[inst].S[1], (double)s1);
+    }
+}
+
+__global__ void __launch_bounds__(128) k_bulk_def_x(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y,
+                                                    const BandRec *__restrict__ R, int src, int dst, int last,
+                                                    DeferList dl) {
+    const int cnt = min(*dl.count, dl.cap);
+    const int stride = gridDim.x * blockDim.x;
+    // whole warps iterate together (the wave-speed reduction is warp-wide)
+    for (int base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31; base < cnt; base += stride) {
+        const int t = base + (threadIdx.x & 31);
+        const bool act = t < cnt;
+        const int2 it = act ? dl.item[t] : dl.item[base];
+        const int inst = it.x, ci = it.y & 0x0fffffff, bits = act ? (it.y >> 28) & 3 : 0;
+        const InstDesc &I = D[inst];
+        InstDyn &y = Y[inst];
+        const int n = I.nx, j = ci / I.pitch, a = ci - j * I.pitch;
+        const float lam = y.lamf;
+        const float g = (float)I.gamma, g1 = g - 1.0f;
+        const size_t plane = (size_t)I.pitch * I.ny;
+        const int rowb = j * I.pitch;
+        const float *Q = (const float *)I.Q[src] + rowb;
+        float *Qb = (float *)I.Q[dst];
+        const unsigned char *cl = I.cls + rowb;
+        // cells a-2 .. a+3
+        float w[6][4];
+        int c[6];
+#pragma unroll
+        for (int m = 0; m < 6; ++m) def_cell(Q, cl, plane, n, 1, 1, I.bc[0], I.bc[1], a - 2 + m, w[m], c[m]);
+        // MUSCL-Hancock states of cells (a-1, a) and (a+1, a+2)
+        float2 qm[4], q0[4], qp[4];
+        E2 QLA, QRA, QLB, QRB;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            qm[k] = make_float2(w[0][k], w[1][k]);
+            q0[k] = make_float2(w[1][k], w[2][k]);
+            qp[k] = make_float2(w[2][k], w[3][k]);
+        }
+        evolve2<0>(g1, lam, qm, q0, qp, !(c[0] & CLS_SOLID) && !(c[2] & CLS_SOLID),
+                   !(c[1] & CLS_SOLID) && !(c[3] & CLS_SOLID), QLA, QRA);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            qm[k] = make_float2(w[2][k], w[3][k]);
+            q0[k] = make_float2(w[3][k], w[4][k]);
+            qp[k] = make_float2(w[4][k], w[5][k]);
+        }
+        evolve2<0>(g1, lam, qm, q0, qp, !(c[2] & CLS_SOLID) && !(c[4] & CLS_SOLID),
+                   !(c[3] & CLS_SOLID) && !(c[5] & CLS_SOLID), QLB, QRB);
+        // faces a (cells a-1 | a), a+1 (a | a+1), a+2 (a+1 | a+2)
+        E2 Rf, L2, R2;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            Rf.q[k] = make_float2(QLA.q[k].y, QLB.q[k].x);
+            L2.q[k] = P2(QRB.q[k].x);
+            R2.q[k] = P2(QLB.q[k].y);
+        }
+        Rf.ir = make_float2(QLA.ir.y, QLB.ir.x);
+        Rf.p = make_float2(QLA.p.y, QLB.p.x);
+        L2.ir = P2(QRB.ir.x);
+        L2.p = P2(QRB.p.x);
+        R2.ir = P2(QLB.ir.y);
+        R2.p = P2(QLB.p.y);
+        float2 F[4], F2[4];
+        hllc2<0>(g, QRA, Rf, F);
+        hllc2<0>(g, L2, R2, F2);
+        if (a <= n) face_override<0>(I, R, j, a, n, (uint8_t)c[1], (uint8_t)c[2], F, 0);
+        if (a + 1 <= n) face_override<0>(I, R, j, a + 1, n, (uint8_t)c[2], (uint8_t)c[3], F, 1);
+        if (a + 2 <= n) face_override<0>(I, R, j, a + 2, n, (uint8_t)c[3], (uint8_t)c[4], F2, 0);
+        float2 Fhi[4], qc[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            Fhi[k] = make_float2(F[k].y, F2[k].x);
+            qc[k] = make_float2(w[2][k], w[3][k]);
+        }
+        int st = 0;
+        if ((bits & 1) && !(c[2] & CLS_OFF)) st |= 1;
+        if ((bits & 2) && !(c[3] & CLS_OFF)) st |= 2;
+        float s0 = 0.0f, s1 = 0.0f;
+        if (st) update2(Qb, plane, rowb + a, st, st == 3, g1, g, lam, qc, F, Fhi, last, s0, s1, y);
+        if ((bits & 1) && (c[2] & CLS_SOLID)) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) Qb[k * plane + rowb + a] = NAN;
+        }
+        if ((bits & 2) && (c[3] & CLS_SOLID)) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) Qb[k * plane + rowb + a + 1] = NAN;
+        }
+        if (last) def_wave_speeds(Y, inst, st != 0, s0, s1);
+    }
+}
+
+__global__ void __launch_bounds__(128) k_bulk_def_y(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y,
+                                                    const BandRec *__restrict__ R, int src, int dst, int last,
+                                                    DeferList dl) {
+    const int cnt = min(*dl.count, dl.cap);
+    const int stride = gridDim.x * blockDim.x;
+    for (int base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31; base < cnt; base += stride) {
+        const int t = base + (threadIdx.x & 31);
+        const bool act = t < cnt;
+        const int2 it = act ? dl.item[t] : dl.item[base];
+        const int inst = it.x, ci = it.y & 0x0fffffff, bits = act ? (it.y >> 28) & 3 : 0;
+        const InstDesc &I = D[inst];
+        InstDyn &y = Y[inst];
+        const int n = I.ny, nx = I.nx, r = ci / I.pitch, i = ci - r * I.pitch;
+        const int st0 = (i < nx ? 1 : 0) | (i + 1 < nx ? 2 : 0);
+        const float lam = y.lamf;
+        const float g = (float)I.gamma, g1 = g - 1.0f;
+        const size_t plane = (size_t)I.pitch * n;
+        const float *Q = (const float *)I.Q[src];
+        float *Qo = (float *)I.Q[dst];
+        // rows r-2 .. r+2 of columns i, i+1 (columns past the grid: filler)
+        float2 w[5][4];
+        int c[5];
+#pragma unroll
+        for (int m = 0; m < 5; ++m) {
+            float a0[4], a1[4];
+            int c0, c1;
+            if (st0 & 1) def_cell(Q + i, I.cls + i, plane, n, I.pitch, 2, I.bc[2], I.bc[3], r - 2 + m, a0, c0);
+            else { a0[0] = a0[1] = a0[2] = a0[3] = 1.0f; c0 = CLS_SOLID; }
+            if (st0 & 2) def_cell(Q + i + 1, I.cls + i + 1, plane, n, I.pitch, 2, I.bc[2], I.bc[3], r - 2 + m, a1, c1);
+            else { a1[0] = a1[1] = a1[2] = a1[3] = 1.0f; c1 = CLS_SOLID; }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) w[m][k] = make_float2(a0[k], a1[k]);
+            c[m] = c0 | (c1 << 8);
+        }
+        auto lims = [&](int m, bool &lx, bool &ly) {
+            lx = !(c[m - 1] & CLS_SOLID) && !(c[m + 1] & CLS_SOLID);
+            ly = !((c[m - 1] >> 8) & CLS_SOLID) && !((c[m + 1] >> 8) & CLS_SOLID);
+        };
+        E2 QL1, QR1, QL2, QR2, QL3, QR3;
+        bool lx, ly;
+        lims(1, lx, ly);
+        evolve2<1>(g1, lam, w[0], w[1], w[2], lx, ly, QL1, QR1);
+        lims(2, lx, ly);
+        evolve2<1>(g1, lam, w[1], w[2], w[3], lx, ly, QL2, QR2);
+        lims(3, lx, ly);
+        evolve2<1>(g1, lam, w[2], w[3], w[4], lx, ly, QL3, QR3);
+        float2 Flo[4], Fhi[4];
+        hllc2<1>(g, QR1, QL2, Flo);
+        hllc2<1>(g, QR2, QL3, Fhi);
+        if (st0 & 1) {
+            face_override<1>(I, R, i, r, n, (uint8_t)(c[1] & 0xff), (uint8_t)(c[2] & 0xff), Flo, 0);
+            face_override<1>(I, R, i, r + 1, n, (uint8_t)(c[2] & 0xff), (uint8_t)(c[3] & 0xff), Fhi, 0);
+        }
+        if (st0 & 2) {
+            face_override<1>(I, R, i + 1, r, n, (uint8_t)(c[1] >> 8), (uint8_t)(c[2] >> 8), Flo, 1);
+            face_override<1>(I, R, i + 1, r + 1, n, (uint8_t)(c[2] >> 8), (uint8_t)(c[3] >> 8), Fhi, 1);
+        }
+        const int sm = bits & st0;
+        int st = 0;
+        if ((sm & 1) && !((c[2] & 0xff) & CLS_OFF)) st |= 1;
+        if ((sm & 2) && !(((c[2] >> 8) & 0xff) & CLS_OFF)) st |= 2;
+        float s0 = 0.0f, s1 = 0.0f;
+        if (st) update2(Qo, plane, ci, st, st == 3, g1, g, lam, w[2], Flo, Fhi, last, s0, s1, y);
+        if ((sm & 1) && (c[2] & CLS_SOLID)) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) Qo[k * plane + ci] = NAN;
+        }
+        if ((sm & 2) && ((c[2] >> 8) & CLS_SOLID)) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) Qo[k * plane + ci + 1] = NAN;
+        }
+        if (last) def_wave_speeds(Y, inst, st != 0, s0, s1);
+    }
 }
 
 template <class T, int EQ>
@@ -1510,14 +1955,14 @@ __global__ void k_mix(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y, B
 // k_finalize: new state of band cells, class bytes of the end pose
 // ---------------------------------------------------------------------------
 template <class T>
-__global__ void k_finalize(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y, BandRec *__restrict__ R,
-                           int n_inst, int total_rec, int dst, int last) {
-    int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= total_rec) return;
+__device__ __forceinline__ bool finalize_rec(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y,
+                                             BandRec *__restrict__ R, int n_inst, int r, int dst, int last,
+                                             double &s0, double &s1, int &inst_out) {
     int inst = find_inst_rec(D, n_inst, r);
+    inst_out = inst;
     const InstDesc &I = D[inst];
     InstDyn &y = Y[inst];
-    if (r - I.rec_base >= y.band_count) return;
+    if (r - I.rec_base >= y.band_count) return false;
     BandRec &b = R[r];
     const size_t plane = (size_t)I.pitch * I.ny;
     T *Qo = bufw<T>(I, dst);
@@ -1533,12 +1978,15 @@ __global__ void k_finalize(const InstDesc *__restrict__ D, InstDyn *__restrict__
             if (!ok) atomicOr(&y.err, ERR_UNSTABLE | ERR_MIX_BAND);
             if (last) {
                 double c = sqrt(I.gamma * p / q[0]);
-                atomic_max_pos(&y.S[0], fabs(q[1] / q[0]) + c);
-                atomic_max_pos(&y.S[1], fabs(q[2] / q[0]) + c);
+                s0 = fabs(q[1] / q[0]) + c;
+                s1 = fabs(q[2] / q[0]) + c;
+                // non-finite or negative speeds force the smallest step
+                if (!(s0 >= 0.0)) s0 = 1e300;
+                if (!(s1 >= 0.0)) s1 = 1e300;
             }
         } else if (last) {
-            atomic_max_pos(&y.S[0], fabs(I.adv[0]));
-            atomic_max_pos(&y.S[1], fabs(I.adv[1]));
+            s0 = fabs(I.adv[0]);
+            s1 = fabs(I.adv[1]);
         }
     } else {
         for (int k = 0; k < I.nc; ++k) Qo[k * plane + b.cell] = T(NAN);
@@ -1548,6 +1996,17 @@ __global__ void k_finalize(const InstDesc *__restrict__ D, InstDyn *__restrict__
                               ((b.flags & RF_MOV_B) ? CLS_MOVT : 0));
     I.alpha[b.cell] = b.aB;
     I.rec[b.cell] = -1;
+    return true;
+}
+
+template <class T>
+__global__ void k_finalize(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y, BandRec *__restrict__ R,
+                           int n_inst, int total_rec, int dst, int last) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    double s0 = 0.0, s1 = 0.0;
+    int inst = -1;
+    const bool act = r < total_rec && finalize_rec<T>(D, Y, R, n_inst, r, dst, last, s0, s1, inst);
+    if (last) warp_max_to(Y, act, inst, s0, s1);
 }
 
 // ---------------------------------------------------------------------------
@@ -1620,30 +2079,45 @@ void launch_band_stage(int stage, const InstDesc *D, InstDyn *Y, BandRec *R, con
     }
 }
 
+// bulk passes of one sweep.  FP32 Euler (the FP32x2 kernels): mode 0 is the
+// pass over the cells that need no band data (it lists the deferred cell
+// pairs in dl), mode 1 the deferred pairs and, when any instance may have
+// defer_all (any_defer_all), the streaming pass over those instances.  Other
+// kernels: one pass, launched for mode 0 only.
 template <class T>
 void launch_bulk(int dir, int eq, const InstDesc *D, InstDyn *Y, const BandRec *R, int n_inst, int total_warps,
-                 int src, int dst, int last, int shape, cudaStream_t st) {
+                 int src, int dst, int last, int shape, int mode, DeferList dl, int any_defer_all, cudaStream_t st) {
     const int cta = shape & 1023;
     const int wpc = cta / 32;   // warps per CTA of the FP32x2 kernels
     int blocks = (total_warps + 7) / 8;
     if (blocks <= 0) return;
     const bool packed = sizeof(T) == 4 && eq == 0;   // FP32 Euler: the FP32x2 kernels
+    if (!packed && mode != 0) return;
     const int pg = (total_warps + wpc - 1) / wpc;
     const bool m4 = (shape & SHAPE_MINB4) != 0, r8 = (shape & SHAPE_RING8) != 0;
+    constexpr int DEF_BLOCKS = 1216;   // 8 CTAs of 128 threads per SM, grid-stride over the list
     if (dir == 0) {
         if (packed) {
             const size_t sm = wpc * (r8 ? sizeof(XRing<8>) : sizeof(XRing<4>));
-            if (m4 && r8) k_bulk_x_p<4, 8><<<pg, cta, sm, st>>>(D, Y, R, n_inst, total_warps, src, dst, last);
-            else if (m4) k_bulk_x_p<4, 4><<<pg, cta, sm, st>>>(D, Y, R, n_inst, total_warps, src, dst, last);
-            else if (r8) k_bulk_x_p<5, 8><<<pg, cta, sm, st>>>(D, Y, R, n_inst, total_warps, src, dst, last);
-            else k_bulk_x_p<5, 4><<<pg, cta, sm, st>>>(D, Y, R, n_inst, total_warps, src, dst, last);
+            if (mode == 1) {
+                k_bulk_def_x<<<DEF_BLOCKS, 128, 0, st>>>(D, Y, R, src, dst, last, dl);
+                if (any_defer_all)
+                    k_bulk_x_p<4, 4, 1><<<pg, cta, wpc * sizeof(XRing<4>), st>>>(D, Y, R, n_inst, total_warps, src, dst, last, dl);
+            } else if (m4 && r8) k_bulk_x_p<4, 8, 0><<<pg, cta, sm, st>>>(D, Y, R, n_inst, total_warps, src, dst, last, dl);
+            else if (m4) k_bulk_x_p<4, 4, 0><<<pg, cta, sm, st>>>(D, Y, R, n_inst, total_warps, src, dst, last, dl);
+            else if (r8) k_bulk_x_p<5, 8, 0><<<pg, cta, sm, st>>>(D, Y, R, n_inst, total_warps, src, dst, last, dl);
+            else k_bulk_x_p<5, 4, 0><<<pg, cta, sm, st>>>(D, Y, R, n_inst, total_warps, src, dst, last, dl);
         } else if (eq == 0) k_bulk_x<T, 0><<<blocks, 256, 0, st>>>(D, Y, R, n_inst, total_warps, src, dst, last);
         else k_bulk_x<T, 1><<<blocks, 256, 0, st>>>(D, Y, R, n_inst, total_warps, src, dst, last);
     } else {
         if (packed) {
             const size_t sm = wpc * sizeof(YRing);
-            if (m4) k_bulk_y_p<4><<<pg, cta, sm, st>>>(D, Y, R, n_inst, total_warps, src, dst, last);
-            else k_bulk_y_p<5><<<pg, cta, sm, st>>>(D, Y, R, n_inst, total_warps, src, dst, last);
+            if (mode == 1) {
+                k_bulk_def_y<<<DEF_BLOCKS, 128, 0, st>>>(D, Y, R, src, dst, last, dl);
+                if (any_defer_all)
+                    k_bulk_y_p<4, 1><<<pg, cta, sm, st>>>(D, Y, R, n_inst, total_warps, src, dst, last, dl);
+            } else if (m4) k_bulk_y_p<4, 0><<<pg, cta, sm, st>>>(D, Y, R, n_inst, total_warps, src, dst, last, dl);
+            else k_bulk_y_p<5, 0><<<pg, cta, sm, st>>>(D, Y, R, n_inst, total_warps, src, dst, last, dl);
         } else if (eq == 0) k_bulk_y<T, 0><<<blocks, 256, 0, st>>>(D, Y, R, n_inst, total_warps, src, dst, last);
         else k_bulk_y<T, 1><<<blocks, 256, 0, st>>>(D, Y, R, n_inst, total_warps, src, dst, last);
     }
@@ -1655,13 +2129,17 @@ int bulk_blocks_per_sm(int dir) {
     bulk_attr_t<T, 1>(dir);
     if (sizeof(T) == 4) {   // the FP32x2 kernels' shared-memory rings (4 warps per CTA at most)
         if (dir == 0) {
-            cudaFuncSetAttribute(k_bulk_x_p<5, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(4 * sizeof(XRing<4>)));
-            cudaFuncSetAttribute(k_bulk_x_p<4, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(4 * sizeof(XRing<4>)));
-            cudaFuncSetAttribute(k_bulk_x_p<5, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(4 * sizeof(XRing<8>)));
-            cudaFuncSetAttribute(k_bulk_x_p<4, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(4 * sizeof(XRing<8>)));
+            const int s4 = (int)(4 * sizeof(XRing<4>)), s8 = (int)(4 * sizeof(XRing<8>));
+            cudaFuncSetAttribute(k_bulk_x_p<5, 4, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, s4);
+            cudaFuncSetAttribute(k_bulk_x_p<4, 4, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, s4);
+            cudaFuncSetAttribute(k_bulk_x_p<5, 8, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, s8);
+            cudaFuncSetAttribute(k_bulk_x_p<4, 8, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, s8);
+            cudaFuncSetAttribute(k_bulk_x_p<4, 4, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, s4);
         } else {
-            cudaFuncSetAttribute(k_bulk_y_p<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(4 * sizeof(YRing)));
-            cudaFuncSetAttribute(k_bulk_y_p<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(4 * sizeof(YRing)));
+            const int sy = (int)(4 * sizeof(YRing));
+            cudaFuncSetAttribute(k_bulk_y_p<5, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sy);
+            cudaFuncSetAttribute(k_bulk_y_p<4, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sy);
+            cudaFuncSetAttribute(k_bulk_y_p<4, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sy);
         }
     }
     return 1;
@@ -1680,7 +2158,7 @@ void launch_read_state(const InstDesc *D, double *out, int inst, int b, cudaStre
     template void launch_band_stage<T>(int, const InstDesc *, InstDyn *, BandRec *, const double *, int *, int, int, \
                                        int, int, int, int, int, int, cudaStream_t);                                \
     template void launch_bulk<T>(int, int, const InstDesc *, InstDyn *, const BandRec *, int, int, int, int, int,  \
-                                 int, cudaStream_t);                                                                    \
+                                 int, int, DeferList, int, cudaStream_t);                                               \
     template int bulk_blocks_per_sm<T>(int);                                                                       \
     template void launch_write_state<T>(const InstDesc *, InstDyn *, const double *, int, int, cudaStream_t);      \
     template void launch_read_state<T>(const InstDesc *, double *, int, int, cudaStream_t);

@@ -25,7 +25,7 @@ EXPORTS = ["mb_create", "mb_batch_create", "mb_destroy", "mb_last_error", "mb_se
            "mb_enable_timing", "mb_kernel_time", "mb_band_records", "mb_band_record_size",
            "mb_cut_cells_noalloc", "mb_noalloc_last_error", "mb_batch_add", "mb_batch_remove", "mb_instance_bytes",
            "mb_request_bytes", "mb_server_create", "mb_server_destroy", "mb_server_last_error", "mb_server_submit",
-           "mb_server_tick", "mb_server_query", "mb_server_request_error", "mb_autotune"]
+           "mb_server_tick", "mb_server_query", "mb_server_request_error", "mb_autotune", "mb_set_overlap"]
 
 
 class Grid(ctypes.Structure):
@@ -99,6 +99,7 @@ def _load():
         "mb_server_query": ([P, I, ctypes.POINTER(I), D], I),
         "mb_server_request_error": ([P, I], ctypes.c_char_p),
         "mb_autotune": ([P, D], I),
+        "mb_set_overlap": ([P, I], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -233,6 +234,11 @@ class Sim:
         self._check(lib.mb_autotune(self._h, _dp(r)))
         return dict(x_cta=int(r[0]), y_cta=int(r[1]), y_rows=int(r[2]), x_ms=r[3], y_ms=r[4],
                     x_min_ctas=int(r[5]), y_min_ctas=int(r[6]), x_ring_chunks=int(r[7]))
+
+    def set_overlap(self, on=True):
+        """Overlap of the bulk pass with the geometry and band fluxes
+        (mb_set_overlap): False, True, or the geometry CTAs per SM."""
+        self._check(lib.mb_set_overlap(self._h, int(on) if not isinstance(on, bool) else (1 if on else 0)))
 
     def enable_timing(self, on=True):
         self._check(lib.mb_enable_timing(self._h, 1 if on else 0))
