@@ -998,6 +998,7 @@ __global__ void __launch_bounds__(128, MINB) k_bulk_x_p(const InstDesc *__restri
     }
     // ghosts that belong to chunk c or c+1 into the ring (after those chunks'
     // copies have completed, so that a copied class word cannot overwrite them)
+    const int c_hi_ghost = (n >> 6) - 1;   // first chunk c whose chunks c, c+1 may hold ghost n or n+1
     auto put_ghost = [&](int c) {
         const int gk = gb >> 6;
         if (lane < 4 && (gk == c || gk == c + 1)) {
@@ -1069,6 +1070,8 @@ __global__ void __launch_bounds__(128, MINB) k_bulk_x_p(const InstDesc *__restri
         const int real = (ap < n ? 1 : 0) | (ap + 1 < n ? 2 : 0);
         sol = ((cm & CLS_SOLID) ? 1 : 0) | (((cm >> 8) & CLS_SOLID) ? 2 : 0);
         if (gen) return real;
+        // no touched cell within reach of chunk c-1 (the usual case): nothing deferred
+        if (!(((tp2_0 | tp2_1) >> 30) | tp1_0 | tp1_1 | tc_0 | tc_1)) return real;
         const int dp = deferred_pair(lane, tp2_0, tp2_1, tp1_0, tp1_1, tc_0, tc_1) & real;
         defer_push(dl, y, inst, rowb + ap, dp);
         return real & ~dp;
@@ -1107,8 +1110,10 @@ __global__ void __launch_bounds__(128, MINB) k_bulk_x_p(const InstDesc *__restri
         prefetch(c + XC - 2);
         cp_async_wait<XC - 3>();   // chunks up to c + 1 complete
         __syncwarp();
-        put_ghost(c);
-        __syncwarp();
+        if (c >= c_hi_ghost) {
+            put_ghost(c);
+            __syncwarp();
+        }
         const int a = 64 * c + 2 * lane;
         const int pa = a & (XRN - 1), pl = (a - 1) & (XRN - 1), pr = (a + 2) & (XRN - 1);
         const int c0 = *(const unsigned short *)&rg.cls[pa];
@@ -1568,11 +1573,26 @@ __global__ void __launch_bounds__(128) k_bulk_def_x(const InstDesc *__restrict__
         const float *Q = (const float *)I.Q[src] + rowb;
         float *Qb = (float *)I.Q[dst];
         const unsigned char *cl = I.cls + rowb;
-        // cells a-2 .. a+3
+        // cells a-2 .. a+3 (pairs of real cells as 8-byte loads)
         float w[6][4];
         int c[6];
+        if (a >= 2 && a + 3 < n) {
 #pragma unroll
-        for (int m = 0; m < 6; ++m) def_cell(Q, cl, plane, n, 1, 1, I.bc[0], I.bc[1], a - 2 + m, w[m], c[m]);
+            for (int m = 0; m < 6; m += 2) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float2 v = __ldg((const float2 *)(Q + k * plane + a - 2 + m));
+                    w[m][k] = v.x;
+                    w[m + 1][k] = v.y;
+                }
+                const unsigned short cc = __ldg((const unsigned short *)(cl + a - 2 + m));
+                c[m] = cc & 0xff;
+                c[m + 1] = cc >> 8;
+            }
+        } else {
+#pragma unroll
+            for (int m = 0; m < 6; ++m) def_cell(Q, cl, plane, n, 1, 1, I.bc[0], I.bc[1], a - 2 + m, w[m], c[m]);
+        }
         // MUSCL-Hancock states of cells (a-1, a) and (a+1, a+2)
         float2 qm[4], q0[4], qp[4];
         E2 QLA, QRA, QLB, QRB;
@@ -1659,6 +1679,14 @@ __global__ void __launch_bounds__(128) k_bulk_def_y(const InstDesc *__restrict__
         int c[5];
 #pragma unroll
         for (int m = 0; m < 5; ++m) {
+            const int rr = r - 2 + m;
+            if (st0 == 3 && rr >= 0 && rr < n) {   // both columns real, a real row: 8-byte loads
+                const size_t o = (size_t)rr * I.pitch + i;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) w[m][k] = __ldg((const float2 *)(Q + k * plane + o));
+                c[m] = __ldg((const unsigned short *)(I.cls + o));
+                continue;
+            }
             float a0[4], a1[4];
             int c0, c1;
             if (st0 & 1) def_cell(Q + i, I.cls + i, plane, n, I.pitch, 2, I.bc[2], I.bc[3], r - 2 + m, a0, c0);
