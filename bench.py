@@ -110,10 +110,11 @@ def job_value(cells_all, steps, total_ms):
 
 
 def bulk_traffic(precision, wname):
-    """DRAM bytes per bulk-kernel launch (mean over the x and y kernels) from
-    the ncu capture summarised in profiles/bulk_traffic.json, or None when
-    that capture is of another workload or precision or the kernel sources
-    have changed since it was taken."""
+    """DRAM bytes of the bulk update per sweep (mean over the x and y sweeps;
+    each the concurrent pass plus the deferred-pair kernel) from the ncu
+    capture summarised in profiles/bulk_traffic.json, or None when that
+    capture is of another workload or precision or the kernel sources have
+    changed since it was taken."""
     import hashlib
     prof = os.path.join(ROOT, "profiles", "bulk_traffic.json")
     try:
@@ -124,7 +125,7 @@ def bulk_traffic(precision, wname):
             with open(os.path.join(ROOT, "paper_1711_11361_gb300", "csrc", f), "rb") as fh:
                 if hashlib.sha256(fh.read()).hexdigest() != sha:
                     return None
-        v = list(d["per_launch_bytes"].values())
+        v = list(d["per_sweep_bytes"].values())
         return float(sum(v) / len(v))
     except (OSError, KeyError, ValueError):
         return None
@@ -493,7 +494,8 @@ def main():
         "p50_ms_per_step": float(np.percentile(per, 50)), "p99_ms_per_step": float(np.percentile(per, 99)),
         "ms_per_step_without_overlap": serial_ms,
         "status": int(status),
-        "roofline": {"kernel": "bulk sweep update (MUSCL-Hancock + HLLC), x and y kernels", "bound": "hbm", "achieved": achieved,
+        "roofline": {"kernel": "bulk sweep update (MUSCL-Hancock + HLLC), x and y: the pass concurrent with the "
+                               "geometry plus the deferred cell pairs, per sweep", "bound": "hbm", "achieved": achieved,
                      "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "peak_kind": peak_kind, "bytes_per_cell": bpc, "avg_launch_ms": avg_bulk_s * 1e3,
                      "launches_timed": launches},

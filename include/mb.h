@@ -106,16 +106,15 @@ const char *mb_last_error(const mb_sim *sim);
 mb_status mb_set_stream(mb_sim *sim, void *stream);
 
 /* Overlap of a sweep's bulk update with its geometry and band fluxes (FP32
- * Euler batches; on by default, with 3 geometry CTAs per SM).  With overlap on, the cells
- * whose update needs no band data (no cell within three positions along the
- * sweep touched by the body at the sweep's start pose) are updated by a pass
- * that runs concurrently with the geometry and band-flux kernels on a
- * second, higher-priority stream; the remaining cells are listed and updated
- * after the band fluxes.  Rotating bodies and sweeps that move a body by 0.9
- * cells or more take the second pass whole.  enable > 0 also sets how many
- * geometry CTAs each SM holds beside the bulk pass (at most 8).  enable = 0:
- * every cell waits for the band fluxes.  Results are the same bits either
- * way.  Not in the middle of a step. */
+ * Euler batches; on by default).  With overlap on, the cells whose update
+ * needs no band data (no cell within three positions along the sweep touched
+ * by the body at the sweep's start pose) are updated by a pass that runs
+ * concurrently with the geometry and band-flux kernels on a second,
+ * higher-priority stream; the remaining cells are listed and updated after
+ * the band fluxes.  Rotating bodies and sweeps that move a body by 0.9 cells
+ * or more take the second pass whole.  enable = 0: every cell waits for the
+ * band fluxes.  Results are the same bits either way.  Not in the middle of a
+ * step. */
 mb_status mb_set_overlap(mb_sim *sim, int enable);
 
 /* Set instance `inst`'s state (host array, nc*nx*ny doubles as above) at time

@@ -93,9 +93,10 @@ struct mb_sim {
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     bool overlap = true;          // mb_set_overlap
-    // geometry CTAs per SM while the bulk pass runs beside them (they loop
-    // over the geometry groups; the rest of each SM holds bulk CTAs)
-    int geom_ctas_per_sm = 3;
+    // geometry CTAs per SM while the bulk pass runs beside them (0: one CTA
+    // per geometry group, the fastest measured; n > 0: n CTAs per SM looping
+    // over the groups)
+    int geom_ctas_per_sm = 0;
     // launch shapes of the bulk kernels (mb_autotune): CTA size, register
     // budget and ring depth per direction of the FP32x2 kernels, rows per
     // thread of the y sweep
@@ -572,8 +573,7 @@ mb_status mb_set_overlap(mb_sim *sim, int enable) {
     if (!sim) return MB_E_INVAL;
     if (sim->sidx != 0) return fail(sim, MB_E_STATE, "mb_set_overlap in the middle of a step");
     cudaError_t e = cudaStreamSynchronize(sim->stream);
-    sim->overlap = enable > 0;
-    if (enable > 0) sim->geom_ctas_per_sm = std::min(enable, 8);
+    sim->overlap = enable != 0;
     drop_graphs(sim);   // captured steps hold the launch sequence of the old setting
     for (auto &I : sim->hd) I.serial_bulk = sim->overlap ? 0 : 1;
     if (e == cudaSuccess && sim->n > 0)

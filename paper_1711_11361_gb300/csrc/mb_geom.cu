@@ -1025,47 +1025,59 @@ __device__ __forceinline__ void geom_group(int gw, const InstDesc *__restrict__ 
         *j = row0 + (*k) * 32 + *bit;
     };
     const double wsimp_B = 1.0 / 6.0, wsimp_M = 4.0 / 6.0, wsimp_A = 1.0 / 6.0;
-    // pass B (edges of the end pose are in G)
-    for (int t = tid; t < T; t += GEOMG_THREADS) {
+    // Each band cell's geometric queries run on separate threads (two in
+    // pass B, three in pass M), so that the CTA's threads share the FP64
+    // clipping work evenly; the pass-M partial results wait in the record
+    // (aM, nx, ny, d, wx, pad) for the per-cell step that combines them.
+    // pass B (edges of the end pose are in G): 0: alpha_B and flags, 1: the
+    // owned face's time-averaged aperture
+    for (int u = tid; u < 2 * T; u += GEOMG_THREADS) {
+        const int part = u >= T ? 1 : 0, t = u - part * T;   // parts in contiguous blocks: warps stay uniform
         int c, j, k, bit;
         locate(t, &c, &j, &k, &bit);
         const int i = i0 + c;
         BandRec &r = R[I.rec_base + base + t];
         const double xl = G.xln[c], xr = G.xln[c + 1];
         const double yb = I.yn[j], yt = I.yn[j + 1];
-        const bool tA = (W.bA[c][k] >> bit) & 1u, tB = (W.bB[c][k] >> bit) & 1u, tM = (W.bM[c][k] >> bit) & 1u;
         const int cell = j * I.pitch + i;
-        r.cell = cell;
-        r.i = i;
-        r.j = j;
-        bool mov = false;
-        r.aB = cell_alpha_g(G, I, c, i, j, xl, xr, yb, yt, nullptr, nullptr, &mov);
-        r.aA = I.alpha[cell];
-        const bool need_bnd =
-            dir == 0 ? ((own_hi && i == 0 && I.bc[0] != 2) || (!own_hi && i == I.nx - 1 && I.bc[1] != 2))
-                     : ((own_hi && j == 0 && I.bc[2] != 2) || (!own_hi && j == I.ny - 1 && I.bc[3] != 2));
-        double bo, bb = 0.0;
-        if (I.rotating) {
-            bo = wsimp_B * face_ap_g(G, I, dir, true, c, i, j, xl, xr, yb, yt);
-            if (need_bnd) bb = wsimp_B * face_ap_g(G, I, dir, false, c, i, j, xl, xr, yb, yt);
+        if (part == 0) {
+            const bool tA = (W.bA[c][k] >> bit) & 1u, tB = (W.bB[c][k] >> bit) & 1u, tM = (W.bM[c][k] >> bit) & 1u;
+            r.cell = cell;
+            r.i = i;
+            r.j = j;
+            bool mov = false;
+            r.aB = cell_alpha_g(G, I, c, i, j, xl, xr, yb, yt, nullptr, nullptr, &mov);
+            r.aA = I.alpha[cell];
+            const bool movA = (I.cls[cell] & CLS_MOVT) != 0;
+            r.flags = (tA ? RF_TOUCH_A : 0) | (tB ? RF_TOUCH_B : 0) | (tM ? RF_TOUCH_M : 0) |
+                      ((mov || movA) ? RF_MOVING : 0) | (mov ? RF_MOV_B : 0);
         } else {
-            bo = swept_face_Bg(G, I, dir, delta, own_hi, c, i, j, xl, xr, yb, yt);
-            if (need_bnd) bb = swept_face_Bg(G, I, dir, delta, !own_hi, c, i, j, xl, xr, yb, yt);
+            const bool need_bnd =
+                dir == 0 ? ((own_hi && i == 0 && I.bc[0] != 2) || (!own_hi && i == I.nx - 1 && I.bc[1] != 2))
+                         : ((own_hi && j == 0 && I.bc[2] != 2) || (!own_hi && j == I.ny - 1 && I.bc[3] != 2));
+            double bo, bb = 0.0;
+            if (I.rotating) {
+                bo = wsimp_B * face_ap_g(G, I, dir, true, c, i, j, xl, xr, yb, yt);
+                if (need_bnd) bb = wsimp_B * face_ap_g(G, I, dir, false, c, i, j, xl, xr, yb, yt);
+            } else {
+                bo = swept_face_Bg(G, I, dir, delta, own_hi, c, i, j, xl, xr, yb, yt);
+                if (need_bnd) bb = swept_face_Bg(G, I, dir, delta, !own_hi, c, i, j, xl, xr, yb, yt);
+            }
+            r.bown = bo;
+            bnd[I.rec_base + base + t] = bb;
         }
-        r.bown = bo;
-        bnd[I.rec_base + base + t] = bb;
-        const bool movA = (I.cls[cell] & CLS_MOVT) != 0;
-        r.flags = (tA ? RF_TOUCH_A : 0) | (tB ? RF_TOUCH_B : 0) | (tM ? RF_TOUCH_M : 0) |
-                  ((mov || movA) ? RF_MOVING : 0) | (mov ? RF_MOV_B : 0);
     }
-    // pass M
+    // pass M: 0: alpha_M, the aperture-closure normal and the moving flag,
+    // 1: low face aperture (and the rotating body's Simpson term), 2: high
+    // face aperture
     __syncthreads();
     gather_g(G, I, px, py, ebox, vnext, vmov, 1, total_v, i0, ncol, ad, tid, &err);
     index_g(G, I, i0, ncol, row0, nwb, nullptr, tid);
     __syncthreads();
     if (warp == 1) compact_lines_g(G, ncol, lane, &err);
     __syncthreads();
-    for (int t = tid; t < T; t += GEOMG_THREADS) {
+    for (int u = tid; u < 3 * T; u += GEOMG_THREADS) {
+        const int part = u / T, t = u - part * T;
         int c, j, k, bit;
         locate(t, &c, &j, &k, &bit);
         const int i = i0 + c;
@@ -1073,18 +1085,34 @@ __device__ __forceinline__ void geom_group(int gw, const InstDesc *__restrict__ 
         BandRec &r = R[ri];
         const double xl = G.xln[c], xr = G.xln[c + 1];
         const double yb = I.yn[j], yt = I.yn[j + 1];
-        bool mov = false;
-        double nlx = 0.0, nly = 0.0;
-        const double aM = cell_alpha_g(G, I, c, i, j, xl, xr, yb, yt, &nlx, &nly, &mov);
-        r.aM = aM;
-        int fl = r.flags | (mov ? RF_MOVING : 0);
-        if (I.rotating) {
-            r.bown += wsimp_M * face_ap_g(G, I, dir, true, c, i, j, xl, xr, yb, yt);
-            const bool need_bnd = dir == 0 ? (i == 0 && I.bc[0] != 2) : (j == 0 && I.bc[2] != 2);
-            if (need_bnd) bnd[ri] += wsimp_M * face_ap_g(G, I, dir, false, c, i, j, xl, xr, yb, yt);
+        if (part == 0) {
+            bool mov = false;
+            double nlx = 0.0, nly = 0.0;
+            r.aM = cell_alpha_g(G, I, c, i, j, xl, xr, yb, yt, &nlx, &nly, &mov);
+            r.nx = nlx;
+            r.ny = nly;
+            r.pad = mov ? 1 : 0;
+        } else if (part == 1) {
+            if (I.rotating) {
+                r.bown += wsimp_M * face_ap_g(G, I, dir, true, c, i, j, xl, xr, yb, yt);
+                const bool need_bnd = dir == 0 ? (i == 0 && I.bc[0] != 2) : (j == 0 && I.bc[2] != 2);
+                if (need_bnd) bnd[ri] += wsimp_M * face_ap_g(G, I, dir, false, c, i, j, xl, xr, yb, yt);
+            }
+            r.d = face_ap_g(G, I, dir, false, c, i, j, xl, xr, yb, yt);
+        } else {
+            r.wx = face_ap_g(G, I, dir, true, c, i, j, xl, xr, yb, yt);
         }
-        const double blo = face_ap_g(G, I, dir, false, c, i, j, xl, xr, yb, yt);
-        const double bhi = face_ap_g(G, I, dir, true, c, i, j, xl, xr, yb, yt);
+    }
+    __syncthreads();
+    for (int t = tid; t < T; t += GEOMG_THREADS) {
+        int c, j, k, bit;
+        locate(t, &c, &j, &k, &bit);
+        const int i = i0 + c;
+        const int ri = I.rec_base + base + t;
+        BandRec &r = R[ri];
+        const double aM = r.aM, blo = r.d, bhi = r.wx, nlx = r.nx, nly = r.ny;
+        int fl = r.flags | (r.pad ? RF_MOVING : 0);
+        r.pad = 0;
         const double db = fabs(blo - bhi);
         const double ahat = aM - dmin(blo, bhi);
         r.d = db > 0.0 ? clamp01(ahat / db) : 1.0;

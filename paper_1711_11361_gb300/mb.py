@@ -236,9 +236,8 @@ class Sim:
                     x_min_ctas=int(r[5]), y_min_ctas=int(r[6]), x_ring_chunks=int(r[7]))
 
     def set_overlap(self, on=True):
-        """Overlap of the bulk pass with the geometry and band fluxes
-        (mb_set_overlap): False, True, or the geometry CTAs per SM."""
-        self._check(lib.mb_set_overlap(self._h, int(on) if not isinstance(on, bool) else (1 if on else 0)))
+        """Overlap of the bulk pass with the geometry and band fluxes (mb_set_overlap)."""
+        self._check(lib.mb_set_overlap(self._h, 1 if on else 0))
 
     def enable_timing(self, on=True):
         self._check(lib.mb_enable_timing(self._h, 1 if on else 0))
