@@ -49,17 +49,32 @@ __device__ __forceinline__ double clamp01(double a) { return a < 0.0 ? 0.0 : (a 
 
 // ---------------------------------------------------------------------------
 // K0: time step, poses of the sweep, posed vertices, conservative FP32 x
-// bounds of every edge, column and row range of the body
+// bounds of every edge, column and row range of the body.  POSE_PARTS CTAs
+// per instance share its vertices; each computes the time step and poses
+// (the same arithmetic), CTA 0 stores them, and the last CTA to finish turns
+// the merged extent into the column and row ranges.
 // ---------------------------------------------------------------------------
+constexpr int POSE_PARTS = 8;
+
+// order-preserving 64-bit key of a double (and back)
+__device__ __forceinline__ unsigned long long dkey(double v) {
+    const long long b = __double_as_longlong(v);
+    return (unsigned long long)(b ^ ((b >> 63) & 0x7fffffffffffffffLL)) ^ 0x8000000000000000ull;
+}
+__device__ __forceinline__ double dkey_inv(unsigned long long k) {
+    const unsigned long long u = k ^ 0x8000000000000000ull;
+    return __longlong_as_double((long long)(u ^ (((long long)u >> 63) & 0x7fffffffffffffffLL)));
+}
+
 __global__ void k_pose(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y, const double *__restrict__ vx,
                        const double *__restrict__ vy, const unsigned char *__restrict__ vmov,
                        const int *__restrict__ vnext, double *__restrict__ px, double *__restrict__ py,
                        float *__restrict__ ebox, int total_v, int dir, int sidx, double dt_host) {
-    const int inst = blockIdx.x;
+    const int inst = blockIdx.x / POSE_PARTS, part = blockIdx.x % POSE_PARTS;
     const InstDesc &I = D[inst];
     InstDyn &y = Y[inst];
     __shared__ double sh[16];
-    __shared__ double red[4][32];
+    __shared__ int last_cta;
     if (threadIdx.x == 0) {
         double dt;
         if (sidx == 0) {
@@ -74,18 +89,12 @@ __global__ void k_pose(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y, 
                 if (Sy <= 0.0) Sy = 1e-300;
                 dt = I.cfl * fmin(I.dx / Sx, I.dy / Sy);
             }
-            y.dt = dt;
-            y.S[0] = 0ull;
-            y.S[1] = 0ull;
         } else {
             dt = y.dt;
-            if (dt_host > 0.0 && dt_host != dt) y.err |= ERR_STATE;
         }
-        y.lam = dt / (dir == 0 ? I.dx : I.dy);
-        y.lamf = (float)y.lam;
-        double tA = y.t + (sidx == 0 ? 0.0 : 0.5 * dt);
-        double tB = y.t + (sidx == 0 ? 0.5 * dt : dt);
-        double tM = y.t + (sidx == 0 ? 0.25 * dt : 0.75 * dt);
+        const double tA = y.t + (sidx == 0 ? 0.0 : 0.5 * dt);
+        const double tB = y.t + (sidx == 0 ? 0.5 * dt : dt);
+        const double tM = y.t + (sidx == 0 ? 0.25 * dt : 0.75 * dt);
         double thA = 0.0, thB = 0.0, thM = 0.0, Om = 0.0;
         if (I.rotating) {
             thA = I.a0 + I.a1 * sin(I.omega * tA);
@@ -93,87 +102,117 @@ __global__ void k_pose(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y, 
             thM = I.a0 + I.a1 * sin(I.omega * tM);
             Om = I.a1 * I.omega * cos(I.omega * tM);
         }
-        double delta = I.U[dir] * dt;
-        y.delta = delta;
-        // the concurrent bulk pass may update a cell before this sweep's
-        // geometry is known only when the body moves by less than a cell
-        // along the sweep and does not rotate (its band then lies within one
-        // cell, along the sweep, of the cells touched at the start pose)
-        y.defer_all = (I.serial_bulk || I.rotating || fabs(delta) >= 0.9 * (dir == 0 ? I.dx : I.dy)) ? 1 : 0;
-        y.XA = y.X; y.YA = y.Y;
-        y.XB = dir == 0 ? y.X + delta : y.X;
-        y.YB = dir == 1 ? y.Y + delta : y.Y;
-        y.XM = dir == 0 ? y.X + 0.5 * delta : y.X;
-        y.YM = dir == 1 ? y.Y + 0.5 * delta : y.Y;
-        y.thA = thA; y.thB = thB; y.thM = thM;
+        const double delta = I.U[dir] * dt;
+        double cA = 1.0, sA = 0.0, cB = 1.0, sB = 0.0, cM = 1.0, sM = 0.0;   // identity for a translating body
         if (I.rotating) {
-            sincos(thA, &y.sA, &y.cA);
-            sincos(thB, &y.sB, &y.cB);
-            sincos(thM, &y.sM, &y.cM);
-        } else {   // the rotation of a translating body is the identity
-            y.cA = y.cB = y.cM = 1.0;
-            y.sA = y.sB = y.sM = 0.0;
+            sincos(thA, &sA, &cA);
+            sincos(thB, &sB, &cB);
+            sincos(thM, &sM, &cM);
         }
-        y.Om = Om;
-        y.band_count = 0;
-        y.nbad = 0;
-        y.nbadlist = 0;
-        y.nbulk = 0;
-        y.mixed = 0;
-        for (int q = 0; q < MAXC; ++q) y.wall_sum[q] = 0.0;
-        sh[0] = y.XA; sh[1] = y.YA; sh[2] = y.XM; sh[3] = y.YM; sh[4] = y.XB; sh[5] = y.YB;
-        sh[6] = y.cA; sh[7] = y.sA; sh[8] = y.cM; sh[9] = y.sM; sh[10] = y.cB; sh[11] = y.sB;
+        const double XA = y.X, YA = y.Y;
+        const double XB = dir == 0 ? y.X + delta : y.X, YB = dir == 1 ? y.Y + delta : y.Y;
+        const double XM = dir == 0 ? y.X + 0.5 * delta : y.X, YM = dir == 1 ? y.Y + 0.5 * delta : y.Y;
+        if (part == 0) {
+            if (sidx == 0) {
+                y.dt = dt;
+            } else {
+                if (dt_host > 0.0 && dt_host != dt) y.err |= ERR_STATE;
+                // the last sweep of the step gathers the wave speeds of the next step's dt
+                y.S[0] = 0ull;
+                y.S[1] = 0ull;
+            }
+            y.lam = dt / (dir == 0 ? I.dx : I.dy);
+            y.lamf = (float)y.lam;
+            y.delta = delta;
+            // the concurrent bulk pass may update a cell before this sweep's
+            // geometry is known only when the body moves by less than a cell
+            // along the sweep and does not rotate (its band then lies within one
+            // cell, along the sweep, of the cells touched at the start pose)
+            y.defer_all = (I.serial_bulk || I.rotating || fabs(delta) >= 0.9 * (dir == 0 ? I.dx : I.dy)) ? 1 : 0;
+            y.XA = XA; y.YA = YA; y.XB = XB; y.YB = YB; y.XM = XM; y.YM = YM;
+            y.thA = thA; y.thB = thB; y.thM = thM;
+            y.cA = cA; y.sA = sA; y.cB = cB; y.sB = sB; y.cM = cM; y.sM = sM;
+            y.Om = Om;
+            y.band_count = 0;
+            y.nbad = 0;
+            y.nbadlist = 0;
+            y.nbulk = 0;
+            y.mixed = 0;
+            for (int q = 0; q < MAXC; ++q) y.wall_sum[q] = 0.0;
+        }
+        sh[0] = XA; sh[1] = YA; sh[2] = XM; sh[3] = YM; sh[4] = XB; sh[5] = YB;
+        sh[6] = cA; sh[7] = sA; sh[8] = cM; sh[9] = sM; sh[10] = cB; sh[11] = sB;
     }
     __syncthreads();
-    double xmin = 1e300, xmax = -1e300, ymin = 1e300, ymax = -1e300;
-    for (int k = threadIdx.x; k < I.nv; k += blockDim.x) {
-        int a = I.voff + k;
-        double x0 = vx[a], y0 = vy[a];
-        for (int P = 0; P < 3; ++P) {   // 0: A, 1: M, 2: B
-            double X = sh[2 * P], Yy = sh[2 * P + 1], c = sh[6 + 2 * P], s = sh[7 + 2 * P];
-            double xo, yo;
-            if (!vmov[a]) {
-                xo = x0; yo = y0;
-            } else if (I.rotating) {
-                double ddx = x0 - I.pivot[0], ddy = y0 - I.pivot[1];
-                double rx = c * ddx - s * ddy;
-                double ry = s * ddx + c * ddy;
-                xo = (I.pivot[0] + rx) + X;
-                yo = (I.pivot[1] + ry) + Yy;
-            } else {
-                xo = x0 + X;
-                yo = y0 + Yy;
-            }
+    // posed position of vertex a at pose P (0: A, 1: M, 2: B)
+    auto posed = [&](int a, int P, double &xo, double &yo) {
+        const double x0 = vx[a], y0 = vy[a];
+        const double X = sh[2 * P], Yy = sh[2 * P + 1], c = sh[6 + 2 * P], s = sh[7 + 2 * P];
+        if (!vmov[a]) {
+            xo = x0; yo = y0;
+        } else if (I.rotating) {
+            double ddx = x0 - I.pivot[0], ddy = y0 - I.pivot[1];
+            double rx = c * ddx - s * ddy;
+            double ry = s * ddx + c * ddy;
+            xo = (I.pivot[0] + rx) + X;
+            yo = (I.pivot[1] + ry) + Yy;
+        } else {
+            xo = x0 + X;
+            yo = y0 + Yy;
+        }
+    };
+    // extent as order-preserving integer keys (minima complemented): integer
+    // compares and shuffles instead of FP64 ones
+    unsigned long long kx0 = 0ull, kx1 = 0ull, ky0 = 0ull, ky1 = 0ull;
+    for (int k = part * blockDim.x + threadIdx.x; k < I.nv; k += POSE_PARTS * blockDim.x) {
+        const int a = I.voff + k, b = vnext[a];
+        for (int P = 0; P < 3; ++P) {
+            double xo, yo, xb, yb;
+            posed(a, P, xo, yo);
+            posed(b, P, xb, yb);
             px[(size_t)P * total_v + a] = xo;
             py[(size_t)P * total_v + a] = yo;
-            xmin = dmin(xmin, xo); xmax = dmax(xmax, xo);
-            ymin = dmin(ymin, yo); ymax = dmax(ymax, yo);
+            const unsigned long long kxa = dkey(xo), kya = dkey(yo), kxb = dkey(xb);
+            kx0 = max(kx0, ~kxa); kx1 = max(kx1, kxa);
+            ky0 = max(ky0, ~kya); ky1 = max(ky1, kya);
+            // conservative FP32 x-range of edge a -> b (rounded outward)
+            const bool alo = kxa <= kxb;
+            ebox[((size_t)P * total_v + a) * 2] = __double2float_rd(alo ? xo : xb);
+            ebox[((size_t)P * total_v + a) * 2 + 1] = __double2float_ru(alo ? xb : xo);
         }
     }
-    __syncthreads();
-    // conservative FP32 x-range of every edge (rounded outward)
-    for (int k = threadIdx.x; k < I.nv; k += blockDim.x) {
-        int a = I.voff + k, b = vnext[a];
-        for (int P = 0; P < 3; ++P) {
-            double xa = px[(size_t)P * total_v + a], xb = px[(size_t)P * total_v + b];
-            ebox[((size_t)P * total_v + a) * 2] = __double2float_rd(dmin(xa, xb));
-            ebox[((size_t)P * total_v + a) * 2 + 1] = __double2float_ru(dmax(xa, xb));
-        }
-    }
+    __shared__ unsigned long long kred[4][32];
     for (int o = 16; o > 0; o >>= 1) {
-        xmin = dmin(xmin, __shfl_xor_sync(0xffffffffu, xmin, o));
-        xmax = dmax(xmax, __shfl_xor_sync(0xffffffffu, xmax, o));
-        ymin = dmin(ymin, __shfl_xor_sync(0xffffffffu, ymin, o));
-        ymax = dmax(ymax, __shfl_xor_sync(0xffffffffu, ymax, o));
+        kx0 = max(kx0, __shfl_xor_sync(0xffffffffu, kx0, o));
+        kx1 = max(kx1, __shfl_xor_sync(0xffffffffu, kx1, o));
+        ky0 = max(ky0, __shfl_xor_sync(0xffffffffu, ky0, o));
+        ky1 = max(ky1, __shfl_xor_sync(0xffffffffu, ky1, o));
     }
     int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (l == 0) { red[0][w] = xmin; red[1][w] = xmax; red[2][w] = ymin; red[3][w] = ymax; }
+    if (l == 0) { kred[0][w] = kx0; kred[1][w] = kx1; kred[2][w] = ky0; kred[3][w] = ky1; }
     __syncthreads();
     if (threadIdx.x == 0) {
         for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
-            xmin = dmin(xmin, red[0][k]); xmax = dmax(xmax, red[1][k]);
-            ymin = dmin(ymin, red[2][k]); ymax = dmax(ymax, red[3][k]);
+            kx0 = max(kx0, kred[0][k]); kx1 = max(kx1, kred[1][k]);
+            ky0 = max(ky0, kred[2][k]); ky1 = max(ky1, kred[3][k]);
         }
+        if (kx1) {   // this CTA posed vertices
+            atomicMax(&y.bbkey[0], kx0);
+            atomicMax(&y.bbkey[1], kx1);
+            atomicMax(&y.bbkey[2], ky0);
+            atomicMax(&y.bbkey[3], ky1);
+        }
+        __threadfence();
+        last_cta = atomicAdd(&y.pose_done, 1) == POSE_PARTS - 1;
+    }
+    __syncthreads();
+    if (last_cta && threadIdx.x == 0) {
+        __threadfence();
+        const unsigned long long k0 = atomicExch(&y.bbkey[0], 0ull), k1 = atomicExch(&y.bbkey[1], 0ull);
+        const unsigned long long k2 = atomicExch(&y.bbkey[2], 0ull), k3 = atomicExch(&y.bbkey[3], 0ull);
+        y.pose_done = 0;
+        const double xmin = dkey_inv(~k0), xmax = dkey_inv(k1);
+        const double ymin = dkey_inv(~k2), ymax = dkey_inv(k3);
         int c0 = (int)floor(fmax((xmin - I.x0) / I.dx, -4.0)) - 1;
         int c1 = (int)floor(fmin((xmax - I.x0) / I.dx, (double)I.nx + 4.0)) + 1;
         int r0 = (int)floor(fmax((ymin - I.y0) / I.dy, -4.0)) - 1;
@@ -183,7 +222,7 @@ __global__ void k_pose(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y, 
         if (c1 > I.nx - 1) c1 = I.nx - 1;
         if (r0 < 0) r0 = 0;
         if (r1 > I.ny - 1) r1 = I.ny - 1;
-        if (c1 - c0 + 1 > I.gcol_max) { c1 = c0 + I.gcol_max - 1; y.err |= ERR_EDGE_CAP; }
+        if (c1 - c0 + 1 > I.gcol_max) { c1 = c0 + I.gcol_max - 1; atomicOr(&y.err, ERR_EDGE_CAP); }
         y.col0 = c0;
         y.col1 = c1;
         y.row0 = r0;
@@ -1091,7 +1130,7 @@ __device__ __forceinline__ void geom_group(int gw, const InstDesc *__restrict__ 
             r.aM = cell_alpha_g(G, I, c, i, j, xl, xr, yb, yt, &nlx, &nly, &mov);
             r.nx = nlx;
             r.ny = nly;
-            r.pad = mov ? 1 : 0;
+            r.aux = mov ? 1 : 0;
         } else if (part == 1) {
             if (I.rotating) {
                 r.bown += wsimp_M * face_ap_g(G, I, dir, true, c, i, j, xl, xr, yb, yt);
@@ -1111,8 +1150,8 @@ __device__ __forceinline__ void geom_group(int gw, const InstDesc *__restrict__ 
         const int ri = I.rec_base + base + t;
         BandRec &r = R[ri];
         const double aM = r.aM, blo = r.d, bhi = r.wx, nlx = r.nx, nly = r.ny;
-        int fl = r.flags | (r.pad ? RF_MOVING : 0);
-        r.pad = 0;
+        int fl = r.flags | (r.aux ? RF_MOVING : 0);
+        r.aux = 0;
         const double db = fabs(blo - bhi);
         const double ahat = aM - dmin(blo, bhi);
         r.d = db > 0.0 ? clamp01(ahat / db) : 1.0;
@@ -1285,7 +1324,7 @@ void launch_nodes(const InstDesc *D, int n_inst, cudaStream_t st) {
 void launch_pose(const InstDesc *D, InstDyn *Y, const double *vx, const double *vy, const unsigned char *vmov,
                  const int *vnext, double *px, double *py, float *ebox, int total_v, int n_inst, int dir, int sidx,
                  double dt, cudaStream_t st) {
-    k_pose<<<n_inst, 256, 0, st>>>(D, Y, vx, vy, vmov, vnext, px, py, ebox, total_v, dir, sidx, dt);
+    k_pose<<<n_inst * POSE_PARTS, 256, 0, st>>>(D, Y, vx, vy, vmov, vnext, px, py, ebox, total_v, dir, sidx, dt);
 }
 
 void launch_geom(const InstDesc *D, InstDyn *Y, const int *ginst, const double *px, const double *py, const float *ebox,

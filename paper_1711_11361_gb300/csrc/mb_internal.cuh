@@ -59,7 +59,7 @@ struct BandRec {
     double C2[MAXC];     // content after covering / uncovering
     double den;          // event weight denominator
     int mix;             // safeguard cluster root (record index) or -1
-    int pad;
+    int aux;             // k_geom: moving flag of the mid pose (then 0); k_band_prep: next to an event
 };
 
 // list of the cell pairs whose bulk update waits for the band fluxes (FP32
@@ -124,6 +124,12 @@ struct InstDyn {
     int nbulk;                  // non-band cells found non-physical by the bulk update
     int bulkbad[NBULK];         // their cell indices (first NBULK)
     double wall_sum[MAXC];
+    // k_pose: body extent over the sweep's poses merged across its CTAs
+    // (order-preserving keys of xmin, xmax, ymin, ymax; the minima stored
+    // complemented), and the count of its CTAs done; both back to 0 after use
+    unsigned long long bbkey[4];
+    int pose_done;
+    int pad3;
 };
 
 // ---------------------------------------------------------------------------

@@ -267,6 +267,13 @@ __global__ void k_band_prep(const InstDesc *__restrict__ D, InstDyn *__restrict_
             if (use8) b.flags |= RF_USE8;
             b.den = (b.flags & RF_COVER) ? den : b.aB + den;
         }
+        // mark the band neighbours this event exchanges content with (all
+        // eight), so that k_events gathers only where an event is near
+        for (int dj = -1; dj <= 1; ++dj)
+            for (int di = -1; di <= 1; ++di) {
+                int c;
+                if ((di || dj) && nbr_cell(di, dj, &c) && (I.cls[c] & CLS_BAND)) atomicOr(&R[I.rec[c]].aux, 1);
+            }
     }
 }
 
@@ -1747,6 +1754,7 @@ void bulk_attr_t(int dir) {
 // ---------------------------------------------------------------------------
 // k_events: covering / uncovering, gathered by each band cell
 // ---------------------------------------------------------------------------
+template <class T>
 __global__ void k_events(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y, BandRec *__restrict__ R,
                          int n_inst, int total_rec) {
     int r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1762,7 +1770,10 @@ __global__ void k_events(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y
     double C[MAXC];
     for (int q = 0; q < MAXC; ++q) C[q] = x.C[q];
     double unc_sum[MAXC] = {0, 0, 0, 0};
-    for (int dj = -1; dj <= 1; ++dj)
+    // only a covered or donor-uncovered cell and the neighbours k_band_prep
+    // marked next to one exchange content
+    const bool near_event = (x.flags & RF_COVER) || x_donor_unc || x.aux;
+    for (int dj = near_event ? -1 : 2; dj <= 1; ++dj)
         for (int di = -1; di <= 1; ++di) {
             if (di == 0 && dj == 0) continue;
             int ii = x.i + di, jj = x.j + dj;
@@ -1796,11 +1807,12 @@ __global__ void k_events(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y
     }
     if (x.flags & RF_COVER) for (int q = 0; q < MAXC; ++q) C[q] = 0.0;
     for (int q = 0; q < MAXC; ++q) x.C2[q] = C[q];
-    // positivity check of the new state
+    // positivity check of the new state (in the path's type; the FP64 path
+    // in FP64)
     if (I.eq == 0 && x.aB > 0.0) {
-        double q0 = C[0] / x.aB, q1 = C[1] / x.aB, q2 = C[2] / x.aB, q3 = C[3] / x.aB;
-        double p = (I.gamma - 1.0) * (q3 - 0.5 * (q1 * q1 + q2 * q2) / q0);
-        bool ok = q0 > 0.0 && p > 0.0 && isfinite(q0) && isfinite(q1) && isfinite(q2) && isfinite(q3);
+        const T q0 = (T)(C[0] / x.aB), q1 = (T)(C[1] / x.aB), q2 = (T)(C[2] / x.aB), q3 = (T)(C[3] / x.aB);
+        const T p = ((T)I.gamma - T(1)) * (q3 - T(0.5) * (q1 * q1 + q2 * q2) / q0);
+        bool ok = q0 > T(0) && p > T(0) && isfinite(q0) && isfinite(q1) && isfinite(q2) && isfinite(q3);
         if (!ok) {
             x.flags |= RF_BAD;
             int k = atomicAdd(&y.nbad, 1);
@@ -1995,19 +2007,23 @@ __device__ __forceinline__ bool finalize_rec(const InstDesc *__restrict__ D, Ins
     const size_t plane = (size_t)I.pitch * I.ny;
     T *Qo = bufw<T>(I, dst);
     if (b.aB > 0.0) {
-        double q[MAXC];
+        // the state divides the content by the volume fraction in FP64; the
+        // positivity check and the wave speeds run in the path's type (on
+        // GB300 every FP64 instruction takes the narrow FP64 pipe)
+        T q[MAXC];
         for (int k = 0; k < I.nc; ++k) {
-            q[k] = b.C2[k] / b.aB;
-            Qo[k * plane + b.cell] = (T)q[k];
+            q[k] = (T)(b.C2[k] / b.aB);
+            Qo[k * plane + b.cell] = q[k];
         }
         if (I.eq == 0) {
-            double p = (I.gamma - 1.0) * (q[3] - 0.5 * (q[1] * q[1] + q[2] * q[2]) / q[0]);
-            bool ok = q[0] > 0.0 && p > 0.0 && isfinite(q[1]) && isfinite(q[2]) && isfinite(q[3]);
+            const T g = (T)I.gamma;
+            T p = (g - T(1)) * (q[3] - T(0.5) * (q[1] * q[1] + q[2] * q[2]) / q[0]);
+            bool ok = q[0] > T(0) && p > T(0) && isfinite(q[1]) && isfinite(q[2]) && isfinite(q[3]);
             if (!ok) atomicOr(&y.err, ERR_UNSTABLE | ERR_MIX_BAND);
             if (last) {
-                double c = sqrt(I.gamma * p / q[0]);
-                s0 = fabs(q[1] / q[0]) + c;
-                s1 = fabs(q[2] / q[0]) + c;
+                T c = tsqrt(g * p / q[0]);
+                s0 = (double)(fabs(q[1] / q[0]) + c);
+                s1 = (double)(fabs(q[2] / q[0]) + c);
                 // non-finite or negative speeds force the smallest step
                 if (!(s0 >= 0.0)) s0 = 1e300;
                 if (!(s1 >= 0.0)) s1 = 1e300;
@@ -2101,7 +2117,7 @@ void launch_band_stage(int stage, const InstDesc *D, InstDyn *Y, BandRec *R, con
     switch (stage) {
         case 0: if (blocks) k_band_prep<T><<<blocks, 128, 0, st>>>(D, Y, R, n_inst, total_rec, dir, src, qn); break;
         case 1: if (blocks) k_band_sweep<T><<<blocks, 128, 0, st>>>(D, Y, R, bnd, n_inst, total_rec, dir, src); break;
-        case 2: if (blocks) k_events<<<blocks, 128, 0, st>>>(D, Y, R, n_inst, total_rec); break;
+        case 2: if (blocks) k_events<T><<<blocks, 128, 0, st>>>(D, Y, R, n_inst, total_rec); break;
         case 3: k_mix<T><<<(n_inst + 63) / 64, 64, 0, st>>>(D, Y, R, scratch, n_inst, dst, sidx); break;
         case 4: if (blocks) k_finalize<T><<<blocks, 128, 0, st>>>(D, Y, R, n_inst, total_rec, dst, last); break;
     }
