@@ -43,9 +43,26 @@ struct GeoWarp {
     int wpre[MAXROWWORDS + 1];
 };
 
-__device__ __forceinline__ double dmin(double a, double b) { return a < b ? a : b; }
-__device__ __forceinline__ double dmax(double a, double b) { return a > b ? a : b; }
-__device__ __forceinline__ double clamp01(double a) { return a < 0.0 ? 0.0 : (a > 1.0 ? 1.0 : a); }
+// Comparisons of finite doubles on integer keys.  On GB300 every FP64
+// instruction, compares, min/max and selects included, takes the SM's narrow
+// FP64 pipe; the geometry's decisions run on the integer pipes instead, with
+// the same results (-0 and +0 compare equal, as in IEEE comparisons).  The
+// key of -0 is that of +0; other doubles keep their bits, negative ones with
+// the magnitude bits inverted, so that signed 64-bit order is double order.
+__device__ __forceinline__ long long dk(double v) {
+    long long b = __double_as_longlong(v);
+    b = (b == (long long)0x8000000000000000ull) ? 0ll : b;
+    return b ^ ((b >> 63) & 0x7fffffffffffffffll);
+}
+__device__ __forceinline__ bool dlt(double a, double b) { return dk(a) < dk(b); }
+__device__ __forceinline__ bool dle(double a, double b) { return dk(a) <= dk(b); }
+__device__ __forceinline__ bool deq(double a, double b) { return dk(a) == dk(b); }
+__device__ __forceinline__ bool dneg(double a) { return dk(a) < 0; }       // a < 0
+__device__ __forceinline__ bool dpos(double a) { return dk(a) > 0; }       // a > 0
+__device__ __forceinline__ bool dzero(double a) { return (__double_as_longlong(a) << 1) == 0; }   // a == 0
+__device__ __forceinline__ double dmin(double a, double b) { return dlt(a, b) ? a : b; }
+__device__ __forceinline__ double dmax(double a, double b) { return dlt(b, a) ? a : b; }
+__device__ __forceinline__ double clamp01(double a) { return dneg(a) ? 0.0 : (dlt(1.0, a) ? 1.0 : a); }
 
 // ---------------------------------------------------------------------------
 // K0: time step, poses of the sweep, posed vertices, conservative FP32 x
@@ -519,16 +536,21 @@ struct GeoWarpG {
 
 __device__ __forceinline__ bool edge_yrange_s(double xa, double ya, double xb, double yb, double slope, double xl,
                                               double xr, double *elo, double *ehi) {
-    double lo = dmin(xa, xb), hi = dmax(xa, xb);
-    if (hi < xl || lo > xr) return false;
+    const long long kxa = dk(xa), kxb = dk(xb), kxl = dk(xl), kxr = dk(xr);
+    const bool alo = kxa < kxb;
+    const double lo = alo ? xa : xb, hi = alo ? xb : xa;
+    const long long klo = alo ? kxa : kxb, khi = alo ? kxb : kxa;
+    if (khi < kxl || klo > kxr) return false;
     double e0, e1;
-    if (xa == xb) {
+    if (kxa == kxb) {
         e0 = ya; e1 = yb;
     } else {
-        double xc0 = lo > xl ? lo : xl;
-        double xc1 = hi < xr ? hi : xr;
-        e0 = (xc0 == xa) ? ya : ((xc0 == xb) ? yb : ya + (xc0 - xa) * slope);
-        e1 = (xc1 == xa) ? ya : ((xc1 == xb) ? yb : ya + (xc1 - xa) * slope);
+        const bool c0l = klo > kxl, c1h = khi < kxr;
+        const double xc0 = c0l ? lo : xl;
+        const double xc1 = c1h ? hi : xr;
+        const long long kc0 = c0l ? klo : kxl, kc1 = c1h ? khi : kxr;
+        e0 = (kc0 == kxa) ? ya : ((kc0 == kxb) ? yb : ya + (xc0 - xa) * slope);
+        e1 = (kc1 == kxa) ? ya : ((kc1 == kxb) ? yb : ya + (xc1 - xa) * slope);
     }
     *elo = dmin(e0, e1);
     *ehi = dmax(e0, e1);
@@ -700,7 +722,8 @@ __device__ void index_g(GeoBufG &G, const InstDesc &I, int i0, int ncol, int row
             for (; cand; cand &= cand - 1u) {
                 const int b = __ffs(cand) - 1, e = w * 32 + b;
                 const double xa = G.xa[e], xb = G.xb[e];
-                if (xa != xb && dmin(xa, xb) <= xs && xs <= dmax(xa, xb)) msk |= 1u << b;
+                const long long ka = dk(xa), kb = dk(xb), ks = dk(xs);
+                if (ka != kb && (ka < kb ? (ka <= ks && ks <= kb) : (kb <= ks && ks <= ka))) msk |= 1u << b;
             }
             G.lm[L][w] = msk;
         }
@@ -727,7 +750,7 @@ __device__ void index_g(GeoBufG &G, const InstDesc &I, int i0, int ncol, int row
             // rows jf0+1 .. jf1-1 lie strictly inside [elo, ehi] whatever the
             // rounding of the floors; the exact predicate decides the rest
             bool hit = j > jf0 && j < jf1;
-            if (!hit) hit = ehi >= I.yn[j] && elo <= I.yn[j + 1];
+            if (!hit) hit = dle(I.yn[j], ehi) && dle(elo, I.yn[j + 1]);
             if (hit) atomicOr(&bits[c][(j - row0) >> 5], 1u << ((j - row0) & 31));
         }
     }
@@ -796,11 +819,15 @@ __device__ __forceinline__ int col_iter_next(const GeoBufG &G, int c, ColIter &i
 __device__ __forceinline__ double line_solid_vg(const GeoBufG &G, int L, double y0r, double y1r, bool left_limit) {
     double s = 0.0;
     const unsigned char want = left_limit ? 1 : 2;
+    const long long k0 = dk(y0r), k1 = dk(y1r);
     for (int e = 0; e < G.lcnt[L]; ++e) {
         if (!(G.lf[L][e] & want)) continue;
-        double yc = G.lyc[L][e];
-        double cl = yc < y0r ? y0r : (yc > y1r ? y1r : yc);
-        s += (double)G.ls[L][e] * (y1r - cl);
+        const double yc = G.lyc[L][e];
+        const long long kc = dk(yc);
+        const double cl = kc < k0 ? y0r : (kc > k1 ? y1r : yc);
+        // crossing direction +-1: add or subtract the length (exact, as the product)
+        if (G.ls[L][e] > 0) s += y1r - cl;
+        else s -= y1r - cl;
     }
     return s;
 }
@@ -810,8 +837,9 @@ __device__ __forceinline__ double line_solid_vg(const GeoBufG &G, int L, double 
 // then the crossings of y_f inside the column, in order along x
 __device__ double line_solid_hg(const GeoBufG &G, int c, int i, double xl, double xr, double yf, int jf) {
     int w = 0;
+    const long long kyf = dk(yf), kxl = dk(xl), kxr = dk(xr);
     for (int e = 0; e < G.lcnt[c]; ++e)
-        if ((G.lf[c][e] & 2) && G.lyc[c][e] < yf) w += G.ls[c][e];
+        if ((G.lf[c][e] & 2) && dk(G.lyc[c][e]) < kyf) w += G.ls[c][e];
     double ex[8];
     int ed[8], ne = 0;
     bool overflow = false;
@@ -828,16 +856,18 @@ __device__ double line_solid_hg(const GeoBufG &G, int c, int i, double xl, doubl
         for (int q = 0; q < ns; ++q) {
             const int e = sv[q];
             const double xa = G.xa[e], xb = G.xb[e], ya = G.ya[e], yb = G.yb[e];
-            if (ya == yb) continue;
-            if ((ya < yf) == (yb < yf)) continue;
-            const double xs = xa == xb ? xa : xa + (yf - ya) * (xb - xa) * G.idy[e];
-            if (!(xs > xl && xs < xr)) continue;
+            const long long kya = dk(ya), kyb = dk(yb);
+            if (kya == kyb) continue;
+            if ((kya < kyf) == (kyb < kyf)) continue;
+            const double xs = deq(xa, xb) ? xa : xa + (yf - ya) * (xb - xa) * G.idy[e];
+            const long long kxs = dk(xs);
+            if (!(kxs > kxl && kxs < kxr)) continue;
             // crossing the boundary left to right: the interior of a
             // counter-clockwise polygon lies left of its edges
-            const int dw = yb > ya ? -1 : 1;
+            const int dw = kyb > kya ? -1 : 1;
             if (ne < 8) {
                 int p = ne++;
-                while (p > 0 && ex[p - 1] > xs) { ex[p] = ex[p - 1]; ed[p] = ed[p - 1]; --p; }
+                while (p > 0 && dlt(xs, ex[p - 1])) { ex[p] = ex[p - 1]; ed[p] = ed[p - 1]; --p; }
                 ex[p] = xs;
                 ed[p] = dw;
             } else {
@@ -880,6 +910,8 @@ __device__ double line_solid_hg(const GeoBufG &G, int c, int i, double xl, doubl
 __device__ double rect_edges_g(const GeoBufG &G, int c, int ja, int jb, double rx0, double rx1, double ry0,
                                double ry1, double xo, double xs, double *nlx, double *nly, bool *mov) {
     const double lx0 = rx0 - xo, lx1 = rx1 - xo, ly1 = ry1 - ry0;
+    const long long krx0 = dk(rx0), krx1 = dk(rx1), kry0 = dk(ry0), kry1 = dk(ry1);
+    const long long klx0 = dk(lx0), klx1 = dk(lx1), kly1 = dk(ly1), kxs = dk(xs);
     const float frx0 = __double2float_rd(rx0), frx1 = __double2float_ru(rx1);
     const float fry0 = __double2float_rd(ry0), fry1 = __double2float_ru(ry1);
     double A = 0.0;
@@ -895,31 +927,36 @@ __device__ double rect_edges_g(const GeoBufG &G, int c, int ja, int jb, double r
         for (int k = 0; k < ns; ++k) {
             const int e = sv[k];
             const double xa = G.xa[e], xb = G.xb[e], ya = G.ya[e], yb = G.yb[e];
-            if (dmax(ya, yb) < ry0 || dmin(ya, yb) > ry1 || dmax(xa, xb) < rx0 || dmin(xa, xb) > rx1) continue;
+            const long long kxa = dk(xa), kxb = dk(xb), kya = dk(ya), kyb = dk(yb);
+            if ((kya < kry0 && kyb < kry0) || (kya > kry1 && kyb > kry1) || (kxa < krx0 && kxb < krx0) ||
+                (kxa > krx1 && kxb > krx1))
+                continue;
             const double ax = xa - xo, ay = ya - ry0, bx = xb - xo, by = yb - ry0;
             const double ddx = bx - ax, ddy = by - ay;
             double t0 = 0.0, t1 = 1.0;
             bool ok = true;
-            if (ddx == 0.0) {
-                if (ax < lx0 || ax > lx1) ok = false;
+            if (dzero(ddx)) {
+                const long long kax = dk(ax);
+                if (kax < klx0 || kax > klx1) ok = false;
             } else {
                 const double inv = G.idx[e];
                 const double ra = (lx0 - ax) * inv, rb = (lx1 - ax) * inv;
                 t0 = dmax(t0, dmin(ra, rb));
                 t1 = dmin(t1, dmax(ra, rb));
             }
-            if (ddy == 0.0) {
-                if (ay < 0.0 || ay > ly1) ok = false;
+            if (dzero(ddy)) {
+                const long long kay = dk(ay);
+                if (kay < 0 || kay > kly1) ok = false;
             } else {
                 const double inv = G.idy[e];
                 const double ra = (0.0 - ay) * inv, rb = (ly1 - ay) * inv;
                 t0 = dmax(t0, dmin(ra, rb));
                 t1 = dmin(t1, dmax(ra, rb));
             }
-            if (!ok || t1 < t0) continue;
+            if (!ok || dlt(t1, t0)) continue;
             if (mov && G.mov[e]) *mov = true;
-            if (xa == xb && xa == xs) continue;   // vertical edge on the grid side
-            if (!(t1 > t0)) continue;
+            if (kxa == kxb && kxa == kxs) continue;   // vertical edge on the grid side
+            if (!dlt(t0, t1)) continue;
             const double xc0 = ax + t0 * ddx, xc1 = ax + t1 * ddx;
             A += ddy * (t1 - t0) * (0.5 * (xc0 + xc1));
             if (nlx) {
