@@ -1064,9 +1064,17 @@ __global__ void __launch_bounds__(128, MINB) k_bulk_x_p(const InstDesc *__restri
     // the previous chunk entirely plain
     bool prev_hi = !((rg.cls[XRN - 2] | rg.cls[XRN - 1]) & CLS_OFF);
     bool prev_all = false;
-    // touch masks of the two chunks before the current one
+    // touch masks of the two chunks before the current one.  Touched cells
+    // lie inside the body's extent over the sweep's poses (k_pose), so rows
+    // and chunks outside it skip the masks (not across a periodic side,
+    // whose ghost cells mirror the far end of the row)
     unsigned tp2_0 = 0u, tp2_1 = 0u, tp1_0 = 0u, tp1_1 = 0u;
-    if (!gen) touch_masks(-1, tp1_0, tp1_1);
+    const int ext_c0 = y.col0, ext_c1 = y.col1;
+    const bool row_near = I.bc[0] == 2 || (j >= y.row0 && j <= y.row1);
+    auto chunk_near = [&](int c) {
+        return row_near && (I.bc[0] == 2 || (64 * c - 2 <= ext_c1 && 64 * c + 65 >= ext_c0));
+    };
+    if (!gen && chunk_near(-1)) touch_masks(-1, tp1_0, tp1_1);
     const int rem = n + 1 - 2 * lane;
     float s0 = 0.0f, s1 = 0.0f;
     float2 Fprev[4];
@@ -1136,7 +1144,7 @@ __global__ void __launch_bounds__(128, MINB) k_bulk_x_p(const InstDesc *__restri
             plain = bal == 0xffffffffu && prev_hi && hclean;
         }
         unsigned tc_0 = 0u, tc_1 = 0u;
-        if (!gen) touch_masks(c, tc_0, tc_1);
+        if (!gen && chunk_near(c)) touch_masks(c, tc_0, tc_1);
         S2 Q0;
         float2 qm[4], qp[4];
 #pragma unroll
@@ -1356,7 +1364,12 @@ __global__ void __launch_bounds__(128, MINB) k_bulk_y_p(const InstDesc *__restri
     // history of touched bits per column (bit 0: the newest row); row j0-3
     // comes straight from global memory
     unsigned h0 = 0u, h1 = 0u;
-    if (!gen) {
+    // touched cells lie inside the body's extent over the sweep's poses
+    // (k_pose): a tile whose columns miss it, or whose rows are more than
+    // three rows away, holds no deferred cell (not across a periodic side)
+    const bool tile_near = !gen && (bclo == 2 || (col0 <= y.col1 && col0 + YCOLS_P - 1 >= y.col0 &&
+                                                 j1 + 3 >= y.row0 && j0 - 3 <= y.row1));
+    if (tile_near) {
         const int r = j0 - 3;
         if (r >= -2) {
             bool fl;
@@ -1396,7 +1409,7 @@ __global__ void __launch_bounds__(128, MINB) k_bulk_y_p(const InstDesc *__restri
         // cells of row f-1 this pass stores; mode 0 lists the deferred pairs
         // (touched cells in rows f-4 .. f+2) and keeps the others
         int sm = st0;
-        if (!gen) {
+        if (tile_near) {
             const int b = touch_bits(f + 2);
             h0 = (h0 << 1) | (b & 1);
             h1 = (h1 << 1) | (b >> 1);
