@@ -635,6 +635,7 @@ static mb_status do_sweep(mb_sim *s, int dir, double dt) {
         cudaEventRecord(s->ev_fork, st);
         cudaStreamWaitEvent(s->side, s->ev_fork, 0);
         geom_band(s->side, s->geom_ctas_per_sm * s->nsm);
+        band(2, s->side);   // covering / uncovering: band records only, no bulk cell
         cudaEventRecord(s->ev_join, s->side);
         bulk(0);
         cudaStreamWaitEvent(st, s->ev_join, 0);
@@ -654,7 +655,7 @@ static mb_status do_sweep(mb_sim *s, int dir, double dt) {
             s->evs.push_back({e0, e1});
         }
     }
-    band(2, st);
+    if (!(two_pass && !s->timing)) band(2, st);
     band(3, st);
     band(4, st);
     if (s->sidx == 1) {

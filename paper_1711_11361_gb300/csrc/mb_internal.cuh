@@ -60,6 +60,8 @@ struct BandRec {
     double den;          // event weight denominator
     int mix;             // safeguard cluster root (record index) or -1
     int aux;             // k_geom: moving flag of the mid pose (then 0); k_band_prep: next to an event
+    float Flof[MAXC];    // Flo and Fhi rounded to FP32, for the FP32 bulk kernels' band faces
+    float Fhif[MAXC];
 };
 
 // list of the cell pairs whose bulk update waits for the band fluxes (FP32

@@ -203,26 +203,24 @@ __global__ void k_band_prep(const InstDesc *__restrict__ D, InstDyn *__restrict_
     // moving-wall boundary state: advective part from the step-start state,
     // pressure from the sweep-start state
     if (b.flags & RF_FLUID_A) {
-        double qc[MAXC], qs[MAXC];
-        bool unc = (b.flags & RF_UNCOV) != 0;
-        
+        // the cell's states in the path's type (the FP32 path stays in FP32:
+        // on GB300 every FP64 conversion takes the narrow FP64 pipe)
+        T qcT[MAXC], qsT[MAXC];
+        const bool unc = (b.flags & RF_UNCOV) != 0;
 #pragma unroll
-        for (int q = 0; q < MAXC; ++q) qc[q] = q >= I.nc ? 0.0 : unc ? b.Qp[q] : (double)QA[q * plane + b.cell];
-        double n0 = (double)QN[b.cell];
-        bool fresh = n0 != n0;
-        
+        for (int q = 0; q < MAXC; ++q) qcT[q] = q >= I.nc ? T(0) : unc ? (T)b.Qp[q] : QA[q * plane + b.cell];
+        const T n0 = QN[b.cell];
+        const bool fresh = n0 != n0;
 #pragma unroll
-        for (int q = 0; q < MAXC; ++q) qs[q] = q >= I.nc ? 0.0 : fresh ? qc[q] : (double)QN[q * plane + b.cell];
+        for (int q = 0; q < MAXC; ++q) qsT[q] = q >= I.nc ? T(0) : fresh ? qcT[q] : QN[q * plane + b.cell];
         if (I.eq == 0) {
             // wall problem in the path's arithmetic type (FP64 path: double)
-            T qsT[4], qcT[4];
-            for (int q = 0; q < 4; ++q) { qsT[q] = (T)qs[q]; qcT[q] = (T)qc[q]; }
             const T g = (T)I.gamma;
             const T nx = (T)b.nx, ny = (T)b.ny, wx = (T)b.wx, wy = (T)b.wy;
             T rs, ps_step, usx, usy, rs2, ps_sw, u2x, u2y;
             wall_state<T>(g, qsT, nx, ny, wx, wy, &rs, &ps_step, &usx, &usy);
             bool same = true;
-            for (int q = 0; q < 4; ++q) same = same && qs[q] == qc[q];
+            for (int q = 0; q < 4; ++q) same = same && qsT[q] == qcT[q];
             if (same) ps_sw = ps_step;   // first sweep of a step: one state
             else wall_state<T>(g, qcT, nx, ny, wx, wy, &rs2, &ps_sw, &u2x, &u2y);
             T Eadv = ps_step / (g - T(1)) + T(0.5) * rs * (usx * usx + usy * usy);
@@ -233,8 +231,8 @@ __global__ void k_band_prep(const InstDesc *__restrict__ D, InstDyn *__restrict_
             b.FB[2] = rs * ud * usy + (dir == 1 ? ps_sw : T(0));
             b.FB[3] = ud * (Eadv + ps_step);
         } else {
-            b.QB[0] = qs[0];
-            b.FB[0] = I.adv[dir] * qs[0];
+            b.QB[0] = (double)qsT[0];
+            b.FB[0] = I.adv[dir] * (double)qsT[0];
         }
         b.flags |= RF_WALL;
     }
@@ -358,7 +356,12 @@ __device__ __forceinline__ bool band_sweep_rec(const InstDesc *__restrict__ D, I
     wall_of(w[2], &fi.hasL, &fi.dL, fi.FBL);
     wall_of(w[3], &fi.hasR, &fi.dR, fi.FBR);
     face_stab<T>(I.eq, g, dir, lamT, av0, av1, I.nc, &w[1], &fi, Fhi);
-    for (int q = 0; q < MAXC; ++q) { b.Flo[q] = Flo[q]; b.Fhi[q] = Fhi[q]; }
+    for (int q = 0; q < MAXC; ++q) {
+        b.Flo[q] = Flo[q];
+        b.Fhi[q] = Fhi[q];
+        b.Flof[q] = (float)Flo[q];
+        b.Fhif[q] = (float)Fhi[q];
+    }
     // content alpha_B Q' of this cell
     double C[MAXC] = {0, 0, 0, 0};
     if (b.flags & RF_FLUID_A) {
@@ -830,11 +833,11 @@ __device__ __forceinline__ void face_override(const InstDesc &I, const BandRec *
         if ((cr & CLS_BAND) && (b_real || !a_real || !(cl & CLS_BAND))) {
             const BandRec &rb = R[I.rec[cib]];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) v[k] = (float)rb.Flo[k];
+            for (int k = 0; k < 4; ++k) v[k] = rb.Flof[k];
         } else {
             const BandRec &ra = R[I.rec[cia]];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) v[k] = (float)ra.Fhi[k];
+            for (int k = 0; k < 4; ++k) v[k] = ra.Fhif[k];
         }
     }
 #pragma unroll

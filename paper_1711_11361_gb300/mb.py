@@ -353,5 +353,6 @@ BAND_DTYPE = np.dtype([("cell", "i4"), ("i", "i4"), ("j", "i4"), ("flags", "i4")
                        ("aA", "f8"), ("aB", "f8"), ("aM", "f8"), ("bown", "f8"), ("d", "f8"),
                        ("nx", "f8"), ("ny", "f8"), ("wx", "f8"), ("wy", "f8"),
                        ("FB", "f8", 4), ("QB", "f8", 4), ("Qp", "f8", 4), ("Flo", "f8", 4), ("Fhi", "f8", 4),
-                       ("C", "f8", 4), ("C2", "f8", 4), ("den", "f8"), ("mix", "i4"), ("aux", "i4")])
+                       ("C", "f8", 4), ("C2", "f8", 4), ("den", "f8"), ("mix", "i4"), ("aux", "i4"),
+                       ("Flof", "f4", 4), ("Fhif", "f4", 4)])
 assert BAND_DTYPE.itemsize == lib.mb_band_record_size(), "band record layout changed"
