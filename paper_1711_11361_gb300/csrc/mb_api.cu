@@ -27,7 +27,7 @@ void launch_nodes(const InstDesc *, int, cudaStream_t);
 void launch_pose(const InstDesc *, InstDyn *, const double *, const double *, const unsigned char *, const int *,
                  double *, double *, float *, int, int, int, int, double, cudaStream_t);
 void launch_geom(const InstDesc *, InstDyn *, const int *, const double *, const double *, const float *, const int *,
-                 const unsigned char *, int, int, int, int, BandRec *, double *, int, cudaStream_t);
+                 const unsigned char *, int, int, int, int, BandRec *, double *, cudaStream_t);
 void launch_classify(const InstDesc *, InstDyn *, const double *, const double *, const unsigned char *, double *,
                      double *, float *, const int *, int, int, int, double *, cudaStream_t);
 template <class T>
@@ -93,10 +93,6 @@ struct mb_sim {
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     bool overlap = true;          // mb_set_overlap
-    // geometry CTAs per SM while the bulk pass runs beside them (0: one CTA
-    // per geometry group, the fastest measured; n > 0: n CTAs per SM looping
-    // over the groups)
-    int geom_ctas_per_sm = 0;
     // launch shapes of the bulk kernels (mb_autotune): CTA size, register
     // budget and ring depth per direction of the FP32x2 kernels, rows per
     // thread of the y sweep
@@ -595,6 +591,8 @@ static mb_status do_sweep(mb_sim *s, int dir, double dt) {
     qn = s->qn;
     const int last = s->sidx == 1;
     cudaStream_t st = s->stream;
+    // the sweep's count of deferred bulk cell pairs
+    cudaMemsetAsync(s->dcount, 0, sizeof(int), st);
     launch_pose(s->dd, s->dy, s->vx, s->vy, s->vmov, s->vnext, s->px, s->py, s->ebox, s->total_v, s->n, dir, s->sidx,
                 dt, st);
     auto band = [&](int stage, cudaStream_t sx) {
@@ -605,9 +603,9 @@ static mb_status do_sweep(mb_sim *s, int dir, double dt) {
             launch_band_stage<double>(stage, s->dd, s->dy, s->rec, s->bnd, s->scratch, s->n, s->total_rec, dir, src,
                                       dst, qn, s->sidx, last, sx);
     };
-    auto geom_band = [&](cudaStream_t sx, int ctas) {
+    auto geom_band = [&](cudaStream_t sx) {
         launch_geom(s->dd, s->dy, s->ginst, s->px, s->py, s->ebox, s->vnext, s->vmov, s->total_v, s->n, s->total_cols,
-                    dir, s->rec, s->bnd, ctas, sx);
+                    dir, s->rec, s->bnd, sx);
         band(0, sx);
         band(1, sx);
     };
@@ -619,7 +617,7 @@ static mb_status do_sweep(mb_sim *s, int dir, double dt) {
     for (const auto &I : s->hd) any_dall = any_dall || I.rotating || I.cfl >= 0.9 || I.serial_bulk;
     const DeferList dl{s->ditem, s->dcount, (int)std::min<size_t>(s->cap_ditem, 0x7fffffff)};
     auto bulk = [&](int mode) {
-        if (mode == 0 && s->prec == MB_FP32 && eq == MB_EULER) cudaMemsetAsync(s->dcount, 0, sizeof(int), st);
+
         if (s->prec == MB_FP32)
             launch_bulk<float>(dir, eq, s->dd, s->dy, s->rec, s->n, s->total_tiles[dir], src, dst, last,
                                s->tune_cta[dir], mode, dl, any_dall ? 1 : 0, st);
@@ -634,14 +632,14 @@ static mb_status do_sweep(mb_sim *s, int dir, double dt) {
         // on the sim's stream; the deferred cells after both
         cudaEventRecord(s->ev_fork, st);
         cudaStreamWaitEvent(s->side, s->ev_fork, 0);
-        geom_band(s->side, s->geom_ctas_per_sm * s->nsm);
+        geom_band(s->side);
         band(2, s->side);   // covering / uncovering: band records only, no bulk cell
         cudaEventRecord(s->ev_join, s->side);
         bulk(0);
         cudaStreamWaitEvent(st, s->ev_join, 0);
         bulk(1);
     } else {
-        geom_band(st, 0);
+        geom_band(st);
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         if (s->timing) {
             cudaEventCreate(&e0);

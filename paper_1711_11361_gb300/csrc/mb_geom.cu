@@ -1237,9 +1237,8 @@ __device__ __forceinline__ void geom_group(int gw, const InstDesc *__restrict__ 
     if (err) atomicOr(&y.err, err);
 }
 
-// One CTA per geometry group, or (when the bulk pass runs concurrently) a
-// grid of fewer CTAs that loop over the groups, so that every SM keeps room
-// for bulk CTAs beside its geometry CTA.
+// One CTA per geometry group (a grid capped below the group count, looping
+// over the groups so that bulk CTAs find room beside it, measured slower).
 __global__ void __launch_bounds__(GEOMG_THREADS, 3) k_geom(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y,
                                                             const int *__restrict__ ginst,
                                                             const double *__restrict__ px, const double *__restrict__ py,
@@ -1249,10 +1248,8 @@ __global__ void __launch_bounds__(GEOMG_THREADS, 3) k_geom(const InstDesc *__res
                                                             int n_inst, int total_groups, int dir,
                                                             BandRec *__restrict__ R, double *__restrict__ bnd) {
     __shared__ int sh_base;
-    for (int gw = blockIdx.x; gw < total_groups; gw += gridDim.x) {
-        geom_group(gw, D, Y, ginst, px, py, ebox, vnext, vmov, total_v, n_inst, total_groups, dir, R, bnd, sh_base);
-        __syncthreads();
-    }
+    geom_group(blockIdx.x, D, Y, ginst, px, py, ebox, vnext, vmov, total_v, n_inst, total_groups, dir, R, bnd,
+               sh_base);
 }
 
 // ---------------------------------------------------------------------------
@@ -1366,8 +1363,8 @@ void launch_pose(const InstDesc *D, InstDyn *Y, const double *vx, const double *
 
 void launch_geom(const InstDesc *D, InstDyn *Y, const int *ginst, const double *px, const double *py, const float *ebox,
                  const int *vnext, const unsigned char *vmov, int total_v, int n_inst, int total_groups, int dir,
-                 BandRec *R, double *bnd, int ctas, cudaStream_t st) {
-    int blocks = (ctas > 0 && ctas < total_groups) ? ctas : total_groups;
+                 BandRec *R, double *bnd, cudaStream_t st) {
+    const int blocks = total_groups;
     if (blocks > 0)
         k_geom<<<blocks, GEOMG_THREADS, geomg_smem(), st>>>(D, Y, ginst, px, py, ebox, vnext, vmov, total_v, n_inst,
                                                              total_groups, dir, R, bnd);
