@@ -129,6 +129,20 @@ mb_status mb_write_state(mb_sim *sim, int inst, const double *Q, double t);
  * any kernel has flagged for this instance since the last write. */
 mb_status mb_read_state(mb_sim *sim, int inst, double *Q, double *alpha, double *clock);
 
+/* mb_write_state of every instance in one call: Q[k] is instance k's host
+ * array (layout as above), t[k] its time (t NULL: all 0).  Same result as n
+ * mb_write_state calls.  Arrays in page-locked host memory (cudaHostAlloc,
+ * cudaMallocHost, cudaHostRegister) are read by the kernels in place over
+ * the host link; pageable arrays are copied through a staging buffer.
+ * Synchronises: the arrays may be reused on return. */
+mb_status mb_write_states(mb_sim *sim, const double *const *Q, const double *t);
+
+/* mb_read_state of every instance in one call: Q[k] (NULL entries skipped)
+ * receives instance k's state, clocks (optional, 4n doubles) the clocks
+ * {t, X, Y, step}.  Page-locked arrays are written by the kernels in place.
+ * Synchronises; returns the first flagged error in instance order. */
+mb_status mb_read_states(mb_sim *sim, double *const *Q, double *clocks);
+
 /* One time step of every instance: two sweeps, x then y on even steps and
  * y then x on odd steps (Sec. II.A, II.C.4).  dt > 0: that step for all
  * instances; dt <= 0: each instance's own CFL step (Sec. III), computed on

@@ -29,7 +29,7 @@ void launch_pose(const InstDesc *, InstDyn *, const double *, const double *, co
 void launch_geom(const InstDesc *, InstDyn *, const int *, const double *, const double *, const float *, const int *,
                  const unsigned char *, int, int, int, int, BandRec *, double *, cudaStream_t);
 void launch_classify(const InstDesc *, InstDyn *, const double *, const double *, const unsigned char *, double *,
-                     double *, float *, const int *, int, int, int, double *, cudaStream_t);
+                     double *, float *, const int *, int, int, int, int, double *, cudaStream_t);
 template <class T>
 void launch_band_stage(int, const InstDesc *, InstDyn *, BandRec *, const double *, int *, int, int, int, int, int,
                        int, int, int, cudaStream_t);
@@ -39,9 +39,10 @@ void launch_bulk(int, int, const InstDesc *, InstDyn *, const BandRec *, int, in
 template <class T>
 int bulk_blocks_per_sm(int);
 template <class T>
-void launch_write_state(const InstDesc *, InstDyn *, const double *, int, int, cudaStream_t);
+void launch_write_state(const InstDesc *, InstDyn *, const double *const *, const double *, int, int, int, int,
+                        cudaStream_t);
 template <class T>
-void launch_read_state(const InstDesc *, double *, int, int, cudaStream_t);
+void launch_read_state(const InstDesc *, double *const *, double *, int, int, int, int, cudaStream_t);
 constexpr int MIXCAP_HOST = 1024;
 }  // namespace mb
 
@@ -80,6 +81,8 @@ struct mb_sim {
     int *scratch = nullptr;
     double *stage = nullptr;      // staging for state I/O (nc * max cells doubles)
     size_t stage_len = 0;
+    const double **iop = nullptr; // per-instance host-buffer aliases of the batched state I/O
+    size_t cap_iop = 0;
     int total_cols = 0;           // geometry groups
     int *ginst = nullptr;         // instance of each geometry group
     int total_tiles[2] = {0, 0};
@@ -163,7 +166,7 @@ static void free_all(mb_sim *s) {
         for (void *p : h.allocs) cudaFree(p);
     s->ih.clear();
     void *shared[] = {s->dd, s->dy, s->vx, s->vy, s->px, s->py, s->ebox, s->vmov, s->vnext,
-                      s->rec, s->bnd, s->scratch, s->stage, s->ginst, s->ditem, s->dcount};
+                      s->rec, s->bnd, s->scratch, s->stage, s->ginst, s->ditem, s->dcount, s->iop};
     for (void *p : shared)
         if (p) cudaFree(p);
     if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
@@ -379,6 +382,7 @@ static cudaError_t relayout(mb_sim *s, int old_n, const std::vector<int> &from) 
     if (e == cudaSuccess) e = ensure(&s->bnd, s->cap_bnd, std::max(1, rec_total), sizeof(double));
     if (e == cudaSuccess) e = ensure(&s->scratch, s->cap_scr, (size_t)std::max(1, n) * 3 * MIXCAP_HOST, sizeof(int));
     if (e == cudaSuccess) e = ensure(&s->stage, s->stage_len, max_cells * 4, sizeof(double));
+    if (e == cudaSuccess) e = ensure(&s->iop, s->cap_iop, std::max(1, n), sizeof(double *));
     if (e == cudaSuccess) e = ensure(&s->dd, s->cap_dd, std::max(1, n), sizeof(InstDesc));
     if (e == cudaSuccess) e = ensure(&s->dy, s->cap_dy, std::max(1, n), sizeof(InstDyn));
     if (e == cudaSuccess) e = ensure(&s->ginst, s->cap_ginst, std::max<size_t>(1, ginst.size()), sizeof(int));
@@ -410,9 +414,12 @@ static cudaError_t relayout(mb_sim *s, int old_n, const std::vector<int> &from) 
     return cudaSuccess;
 }
 
-// classes and volume fractions of instance k at its current pose
-static void classify_instance(mb_sim *s, int k, double *alpha_out) {
-    launch_classify(s->dd, s->dy, s->vx, s->vy, s->vmov, s->px, s->py, s->ebox, s->vnext, s->total_v, k, s->hd[k].nx,
+// classes and volume fractions of instances k .. k+cnt-1 at their current
+// poses (alpha_out: the volume fractions of a single instance, nx*ny)
+static void classify_instances(mb_sim *s, int k, int cnt, double *alpha_out) {
+    int max_nx = 0;
+    for (int q = k; q < k + cnt; ++q) max_nx = std::max(max_nx, s->hd[q].nx);
+    launch_classify(s->dd, s->dy, s->vx, s->vy, s->vmov, s->px, s->py, s->ebox, s->vnext, s->total_v, k, cnt, max_nx,
                     alpha_out, s->stream);
 }
 
@@ -464,7 +471,7 @@ mb_status mb_batch_create(int n, const mb_grid *grids, const double *gammas, con
         s->bulk_grid[d] = bps * s->nsm;
     }
     // initial classes at t = 0
-    for (int k = 0; k < n; ++k) classify_instance(s, k, nullptr);
+    classify_instances(s, 0, n, nullptr);
     CK(cudaStreamSynchronize(s->stream));
     CK(cudaGetLastError());
 #undef CK
@@ -497,7 +504,7 @@ mb_status mb_batch_add(mb_sim *sim, const mb_grid *grid, double gamma, const mb_
     e = relayout(sim, old_n, from);
     if (e == cudaSuccess) {
         launch_nodes(sim->dd, sim->n, sim->stream);
-        classify_instance(sim, old_n, nullptr);
+        classify_instances(sim, old_n, 1, nullptr);
         e = cudaStreamSynchronize(sim->stream);
         if (e == cudaSuccess) e = cudaGetLastError();
     }
@@ -753,67 +760,162 @@ mb_status mb_sync(mb_sim *sim) {
     return map_err(sim, err);
 }
 
-mb_status mb_write_state(mb_sim *sim, int inst, const double *Q, double t) {
-    if (!sim || !Q || inst < 0 || inst >= sim->n) return MB_E_INVAL;
+// Device alias of a page-locked host buffer: the state kernels read or write
+// it directly over the host link.  nullptr for pageable memory, which goes
+// through the staging buffer and a copy.
+static const double *host_alias(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost && a.devicePointer ? (const double *)a.devicePointer : nullptr;
+}
+
+// instances k0 .. k0+cnt-1 from host arrays Q[q] at times t[q]
+static mb_status write_states(mb_sim *sim, int k0, int cnt, const double *const *Q, const double *t) {
     if (sim->sidx != 0) {
         // abandon the half-done step: the written state starts a new one
         sim->cur = (sim->qn + 1) % 3;
         sim->sidx = 0;
     }
-    const InstDesc &I = sim->hd[inst];
-    size_t n = (size_t)I.nx * I.ny;
     cudaStream_t st = sim->stream;
-    InstDyn y;
-    memset(&y, 0, sizeof(y));
-    y.t = t;
-    y.X = I.U[0] * t;
-    y.Y = I.U[1] * t;
-    y.th = I.rotating ? I.a0 + I.a1 * std::sin(I.omega * t) : 0.0;
-    cudaError_t e = cudaMemcpyAsync(sim->dy + inst, &y, sizeof(y), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(sim->stage, Q, n * I.nc * sizeof(double), cudaMemcpyHostToDevice, st);
+    std::vector<InstDyn> ys(cnt);
+    for (int q = 0; q < cnt; ++q) {
+        const InstDesc &I = sim->hd[k0 + q];
+        InstDyn &y = ys[q];
+        memset(&y, 0, sizeof(y));
+        y.t = t[q];
+        y.X = I.U[0] * t[q];
+        y.Y = I.U[1] * t[q];
+        y.th = I.rotating ? I.a0 + I.a1 * std::sin(I.omega * t[q]) : 0.0;
+    }
+    cudaError_t e = cudaMemcpyAsync(sim->dy + k0, ys.data(), cnt * sizeof(InstDyn), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_check(sim, e, "write_state copy");
-    launch_classify(sim->dd, sim->dy, sim->vx, sim->vy, sim->vmov, sim->px, sim->py, sim->ebox, sim->vnext,
-                    sim->total_v, inst, I.nx, nullptr, st);
-    if (sim->prec == MB_FP32) launch_write_state<float>(sim->dd, sim->dy, sim->stage, inst, sim->cur, st);
-    else launch_write_state<double>(sim->dd, sim->dy, sim->stage, inst, sim->cur, st);
+    classify_instances(sim, k0, cnt, nullptr);
+    auto launch = [&](const double *const *ptrs, const double *p1, int i0, int ni, int max_ny) {
+        if (sim->prec == MB_FP32) launch_write_state<float>(sim->dd, sim->dy, ptrs, p1, i0, ni, max_ny, sim->cur, st);
+        else launch_write_state<double>(sim->dd, sim->dy, ptrs, p1, i0, ni, max_ny, sim->cur, st);
+    };
+    std::vector<const double *> alias(cnt);
+    int n_alias = 0, max_ny = 0;
+    for (int q = 0; q < cnt; ++q) {
+        alias[q] = host_alias(Q[q]);
+        if (alias[q]) {
+            ++n_alias;
+            max_ny = std::max(max_ny, sim->hd[k0 + q].ny);
+        }
+    }
+    if (n_alias) {
+        e = cudaMemcpyAsync(sim->iop, alias.data(), cnt * sizeof(double *), cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return cuda_check(sim, e, "write_state copy");
+        launch(sim->iop, nullptr, k0, cnt, max_ny);
+    }
+    for (int q = 0; q < cnt; ++q) {
+        if (alias[q]) continue;
+        const InstDesc &I = sim->hd[k0 + q];
+        e = cudaMemcpyAsync(sim->stage, Q[q], (size_t)I.nx * I.ny * I.nc * sizeof(double), cudaMemcpyHostToDevice,
+                            st);
+        if (e != cudaSuccess) return cuda_check(sim, e, "write_state copy");
+        launch(nullptr, sim->stage, k0 + q, 1, I.ny);
+    }
     e = cudaStreamSynchronize(st);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_check(sim, e, "write_state");
-    if (inst == 0) sim->nstep = 0;
+    if (k0 == 0) sim->nstep = 0;
     return MB_OK;
+}
+
+// states of instances k0 .. k0+cnt-1 into host arrays Q[q] (entries may be
+// NULL); their dynamic records into ys
+static mb_status read_states(mb_sim *sim, int k0, int cnt, double *const *Q, std::vector<InstDyn> &ys) {
+    cudaStream_t st = sim->stream;
+    const int buf = sim->sidx == 0 ? sim->cur : (sim->qn + 1) % 3;
+    auto launch = [&](double *const *ptrs, double *p1, int i0, int ni, int max_ny) {
+        if (sim->prec == MB_FP32) launch_read_state<float>(sim->dd, ptrs, p1, i0, ni, max_ny, buf, st);
+        else launch_read_state<double>(sim->dd, ptrs, p1, i0, ni, max_ny, buf, st);
+    };
+    cudaError_t e = cudaSuccess;
+    std::vector<double *> alias(cnt, nullptr);
+    int n_alias = 0, max_ny = 0;
+    for (int q = 0; q < cnt; ++q) {
+        if (!Q[q]) continue;
+        alias[q] = const_cast<double *>(host_alias(Q[q]));
+        if (alias[q]) {
+            ++n_alias;
+            max_ny = std::max(max_ny, sim->hd[k0 + q].ny);
+        }
+    }
+    if (n_alias) {
+        e = cudaMemcpyAsync(sim->iop, alias.data(), cnt * sizeof(double *), cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return cuda_check(sim, e, "read_state copy");
+        launch((double *const *)sim->iop, nullptr, k0, cnt, max_ny);
+    }
+    for (int q = 0; q < cnt; ++q) {
+        if (!Q[q] || alias[q]) continue;
+        const InstDesc &I = sim->hd[k0 + q];
+        launch(nullptr, sim->stage, k0 + q, 1, I.ny);
+        e = cudaMemcpyAsync(Q[q], sim->stage, (size_t)I.nx * I.ny * I.nc * sizeof(double), cudaMemcpyDeviceToHost,
+                            st);
+        if (e != cudaSuccess) return cuda_check(sim, e, "read_state copy");
+    }
+    ys.resize(cnt);
+    e = cudaMemcpyAsync(ys.data(), sim->dy + k0, cnt * sizeof(InstDyn), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_check(sim, e, "read_state");
+    return MB_OK;
+}
+
+static void clock_of(const InstDyn &y, double *clock) {
+    clock[0] = y.t;
+    clock[1] = y.X;
+    clock[2] = y.Y;
+    clock[3] = (double)y.step;
+}
+
+mb_status mb_write_state(mb_sim *sim, int inst, const double *Q, double t) {
+    if (!sim || !Q || inst < 0 || inst >= sim->n) return MB_E_INVAL;
+    return write_states(sim, inst, 1, &Q, &t);
+}
+
+mb_status mb_write_states(mb_sim *sim, const double *const *Q, const double *t) {
+    if (!sim || !Q) return MB_E_INVAL;
+    for (int k = 0; k < sim->n; ++k)
+        if (!Q[k]) return fail(sim, MB_E_INVAL, "write_states: NULL state array");
+    std::vector<double> tt(sim->n, 0.0);
+    if (t) tt.assign(t, t + sim->n);
+    return write_states(sim, 0, sim->n, Q, tt.data());
 }
 
 mb_status mb_read_state(mb_sim *sim, int inst, double *Q, double *alpha, double *clock) {
     if (!sim || inst < 0 || inst >= sim->n) return MB_E_INVAL;
     const InstDesc &I = sim->hd[inst];
-    size_t n = (size_t)I.nx * I.ny;
     cudaStream_t st = sim->stream;
-    cudaError_t e = cudaSuccess;
-    int buf = sim->sidx == 0 ? sim->cur : (sim->qn + 1) % 3;
-    if (Q) {
-        if (sim->prec == MB_FP32) launch_read_state<float>(sim->dd, sim->stage, inst, buf, st);
-        else launch_read_state<double>(sim->dd, sim->stage, inst, buf, st);
-        e = cudaMemcpyAsync(Q, sim->stage, n * I.nc * sizeof(double), cudaMemcpyDeviceToHost, st);
-        if (e != cudaSuccess) return cuda_check(sim, e, "read_state copy");
-    }
     if (alpha) {
-        launch_classify(sim->dd, sim->dy, sim->vx, sim->vy, sim->vmov, sim->px, sim->py, sim->ebox, sim->vnext,
-                        sim->total_v, inst, I.nx, sim->stage, st);
-        e = cudaMemcpyAsync(alpha, sim->stage, n * sizeof(double), cudaMemcpyDeviceToHost, st);
+        classify_instances(sim, inst, 1, sim->stage);
+        cudaError_t e = cudaMemcpyAsync(alpha, sim->stage, (size_t)I.nx * I.ny * sizeof(double),
+                                        cudaMemcpyDeviceToHost, st);
         if (e != cudaSuccess) return cuda_check(sim, e, "alpha copy");
     }
-    InstDyn y;
-    e = cudaMemcpyAsync(&y, sim->dy + inst, sizeof(y), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e == cudaSuccess) e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_check(sim, e, "read_state");
-    if (clock) {
-        clock[0] = y.t;
-        clock[1] = y.X;
-        clock[2] = y.Y;
-        clock[3] = (double)y.step;
+    std::vector<InstDyn> ys;
+    mb_status r = read_states(sim, inst, 1, &Q, ys);
+    if (r != MB_OK) return r;
+    if (clock) clock_of(ys[0], clock);
+    return map_err(sim, ys[0].err);
+}
+
+mb_status mb_read_states(mb_sim *sim, double *const *Q, double *clocks) {
+    if (!sim || !Q) return MB_E_INVAL;
+    std::vector<InstDyn> ys;
+    mb_status r = read_states(sim, 0, sim->n, Q, ys);
+    if (r != MB_OK) return r;
+    r = MB_OK;
+    for (int k = 0; k < sim->n; ++k) {
+        if (clocks) clock_of(ys[k], clocks + 4 * k);
+        if (r == MB_OK && ys[k].err) r = map_err(sim, ys[k].err);
     }
-    return map_err(sim, y.err);
+    return r;
 }
 
 mb_status mb_band_records(mb_sim *sim, int inst, void *out, int max_records, int *count) {

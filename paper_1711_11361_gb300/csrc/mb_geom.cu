@@ -1261,27 +1261,63 @@ __global__ void __launch_bounds__(GEOM_WARPS * 32) k_classify(const InstDesc *__
                                                             const float *__restrict__ ebox,
                                                             const int *__restrict__ vnext,
                                                             const unsigned char *__restrict__ vmov, int total_v,
-                                                            int inst, double *__restrict__ alpha_out) {
+                                                            int inst0, double *__restrict__ alpha_out) {
     extern __shared__ __align__(16) unsigned char gsm[];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     GeoWarp &W = ((GeoWarp *)gsm)[wib];
     GeoBuf &G = W.G;
+    const int inst = inst0 + blockIdx.y;
     const InstDesc &I = D[inst];
     const int i = blockIdx.x * GEOM_WARPS + wib;
     if (i >= I.nx) return;
     const double xl = node_coord(I.x0, i, I.dx), xr = node_coord(I.x0, i + 1, I.dx);
     const int nwords = (I.ny + 31) >> 5;
     int err = 0;
-    for (int w = lane; w < nwords; w += 32) W.bB[w] = 0u;
+    for (int w = lane; w < nwords; w += 32) W.bB[w] = W.bA[w] = 0u;
     __syncwarp();
     if (I.nv) gather(G, I, px, py, ebox, vnext, vmov, 0, total_v, xl, xr, xl, xr, W.bB, lane, &err);
     else if (lane == 0) { G.cnt = 0; G.lcnt[0] = G.lcnt[1] = 0; }
     __syncwarp();
+    // rows that rect_edges examines an edge for (jlo <= j <= jhi)
+    for (int e = lane; e < G.cnt; e += 32) {
+        const int a = max((int)G.jlo[e], 0), z = min((int)G.jhi[e], I.ny - 1);
+        for (int w = a >> 5; w <= (z >> 5) && a <= z; ++w) {
+            const int lo = max(a - 32 * w, 0), hi = min(z - 32 * w, 31);
+            const unsigned m = (hi == 31 ? 0xffffffffu : ((1u << (hi + 1)) - 1u)) & ~((1u << lo) - 1u);
+            atomicOr(&W.bA[w], m);
+        }
+    }
+    __syncwarp();
     for (int j = lane; j < I.ny; j += 32) {
-        const double yb = node_coord(I.y0, j, I.dy), yt = node_coord(I.y0, j + 1, I.dy);
+        const double yb = I.yn[j], yt = I.yn[j + 1];
         const bool touched = (W.bB[j >> 5] >> (j & 31)) & 1u;
         bool mov = false;
-        const double a = cell_alpha(G, I, j, xl, xr, yb, yt, nullptr, nullptr, &mov);
+        // A cell that no edge meets and whose rows rect_edges examines no edge
+        // for, with no crossing of x_r within [yb, yt]: rect_edges is 0 and
+        // x_r is solid over the whole cell or over none of it, S times its
+        // height (S: the signed crossings below the cell).  The same value as
+        // cell_alpha, without its FP64 work in the common case S = 0.
+        bool fast = !touched && !((W.bA[j >> 5] >> (j & 31)) & 1u);
+        int S = 0;
+        if (fast) {
+            const long long kb = dk(yb), kt = dk(yt);
+            for (int e = 0; e < G.lcnt[1]; ++e) {
+                if (!(G.lf[1][e] & 1)) continue;
+                const long long kc = dk(G.lyc[1][e]);
+                if (kc < kb) S += G.ls[1][e];
+                else if (kc <= kt) fast = false;
+            }
+        }
+        double a;
+        if (!fast) {
+            a = cell_alpha(G, I, j, xl, xr, yb, yt, nullptr, nullptr, &mov);
+        } else if (S == 0) {
+            a = 1.0;
+        } else {
+            const double A = (xr - xl) * ((double)S * (yt - yb));
+            a = clamp01(1.0 - A / (I.dx * I.dy));
+            if (a < ALPHA_MIN) a = 0.0;
+        }
         uint8_t c = touched ? CLS_TOUCH : 0;
         if (mov) c |= CLS_MOVT;
         if (a == 0.0) c |= CLS_SOLID;
@@ -1301,7 +1337,8 @@ __global__ void k_pose_current(const InstDesc *__restrict__ D, const InstDyn *__
                                const double *__restrict__ vx, const double *__restrict__ vy,
                                const unsigned char *__restrict__ vmov, const int *__restrict__ vnext,
                                double *__restrict__ px, double *__restrict__ py, float *__restrict__ ebox,
-                               int inst) {
+                               int inst0) {
+    const int inst = inst0 + blockIdx.x;
     const InstDesc &I = D[inst];
     const InstDyn &y = Y[inst];
     double th = I.rotating ? y.th : 0.0;
@@ -1371,12 +1408,13 @@ void launch_geom(const InstDesc *D, InstDyn *Y, const int *ginst, const double *
 }
 
 void launch_classify(const InstDesc *D, InstDyn *Y, const double *vx, const double *vy, const unsigned char *vmov,
-                     double *px, double *py, float *ebox, const int *vnext, int total_v, int inst, int nx,
-                     double *alpha_out, cudaStream_t st) {
-    k_pose_current<<<1, 256, 0, st>>>(D, Y, vx, vy, vmov, vnext, px, py, ebox, inst);
-    int blocks = (nx + GEOM_WARPS - 1) / GEOM_WARPS;
-    k_classify<<<blocks, GEOM_WARPS * 32, geom_smem(), st>>>(D, Y, px, py, ebox, vnext, vmov, total_v, inst,
-                                                           alpha_out);
+                     double *px, double *py, float *ebox, const int *vnext, int total_v, int inst0, int ninst,
+                     int max_nx, double *alpha_out, cudaStream_t st) {
+    if (ninst <= 0 || max_nx <= 0) return;
+    k_pose_current<<<ninst, 256, 0, st>>>(D, Y, vx, vy, vmov, vnext, px, py, ebox, inst0);
+    const dim3 grid((max_nx + GEOM_WARPS - 1) / GEOM_WARPS, ninst);
+    k_classify<<<grid, GEOM_WARPS * 32, geom_smem(), st>>>(D, Y, px, py, ebox, vnext, vmov, total_v, inst0,
+                                                         ninst == 1 ? alpha_out : nullptr);
 }
 
 }  // namespace mb

@@ -2070,56 +2070,88 @@ __global__ void k_finalize(const InstDesc *__restrict__ D, InstDyn *__restrict__
 }
 
 // ---------------------------------------------------------------------------
-// state initialisation and the CFL wave speeds of a state
+// state initialisation and the CFL wave speeds of a state; state read-back.
+// One CTA per STATE_ROWS rows of one instance (instance inst0 + blockIdx.y),
+// threads along the row.  A source / destination is either device memory
+// (the staging buffer) or a page-locked host buffer seen through its device
+// alias, which the kernel reads or writes directly over the host link.
 // ---------------------------------------------------------------------------
+constexpr int STATE_ROWS = 8;
+constexpr int STATE_THREADS = 128;
+
+// Sources: srcs[blockIdx.y] (srcs != nullptr; a null entry skips that
+// instance) or src1.  Wave speeds in T, the precision of the state (the
+// speeds of later steps come from the update kernels, also in T).
 template <class T>
-__global__ void k_write_state(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y, const double *__restrict__ Qh,
-                              int inst, int b) {
+__global__ void __launch_bounds__(STATE_THREADS) k_write_state(const InstDesc *__restrict__ D,
+                                                               InstDyn *__restrict__ Y,
+                                                               const double *const *__restrict__ srcs,
+                                                               const double *__restrict__ src1, int inst0, int b) {
+    const int inst = inst0 + blockIdx.y;
+    const double *__restrict__ Qh = srcs ? srcs[blockIdx.y] : src1;
+    if (!Qh) return;
     const InstDesc &I = D[inst];
-    size_t n = (size_t)I.nx * I.ny;
+    const int j0 = blockIdx.x * STATE_ROWS;
+    if (j0 >= I.ny) return;
+    const size_t n = (size_t)I.nx * I.ny;
     const size_t plane = (size_t)I.pitch * I.ny;
     T *Q = bufw<T>(I, b);
-    double s0 = 0.0, s1 = 0.0;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-        int i = (int)(e % I.nx), j = (int)(e / I.nx);
-        int c = j * I.pitch + i;
-        bool solid = I.cls[c] & CLS_SOLID;
-        double q[MAXC];
-        for (int k = 0; k < I.nc; ++k) {
-            q[k] = (double)(T)Qh[k * n + e];
-            Q[k * plane + c] = solid ? T(NAN) : (T)Qh[k * n + e];
-        }
-        if (solid) continue;
-        if (I.eq == 0) {
-            double p = (I.gamma - 1.0) * (q[3] - 0.5 * (q[1] * q[1] + q[2] * q[2]) / q[0]);
-            double c2 = sqrt(I.gamma * p / q[0]);
-            s0 = fmax(s0, fabs(q[1] / q[0]) + c2);
-            s1 = fmax(s1, fabs(q[2] / q[0]) + c2);
-        } else {
-            s0 = fabs(I.adv[0]);
-            s1 = fabs(I.adv[1]);
+    const T g = (T)I.gamma;
+    T s0 = T(0), s1 = T(0);
+    bool fluid = false;
+    const int j1 = min(j0 + STATE_ROWS, I.ny);
+    for (int j = j0; j < j1; ++j) {
+        for (int i = threadIdx.x; i < I.nx; i += STATE_THREADS) {
+            const int c = j * I.pitch + i;
+            const size_t e = (size_t)j * I.nx + i;
+            const bool solid = I.cls[c] & CLS_SOLID;
+            T q[MAXC] = {T(0), T(0), T(0), T(0)};
+            for (int k = 0; k < I.nc; ++k) {
+                q[k] = (T)Qh[k * n + e];
+                Q[k * plane + c] = solid ? T(NAN) : q[k];
+            }
+            if (solid) continue;
+            fluid = true;
+            if (I.eq == 0) {
+                T p = (g - T(1)) * (q[3] - T(0.5) * (q[1] * q[1] + q[2] * q[2]) / q[0]);
+                T c2 = tsqrt(g * p / q[0]);
+                s0 = fmax(s0, fabs(q[1] / q[0]) + c2);
+                s1 = fmax(s1, fabs(q[2] / q[0]) + c2);
+            }
         }
     }
     for (int o = 16; o > 0; o >>= 1) {
         s0 = fmax(s0, __shfl_xor_sync(0xffffffffu, s0, o));
         s1 = fmax(s1, __shfl_xor_sync(0xffffffffu, s1, o));
     }
-    if ((threadIdx.x & 31) == 0) {
-        atomic_max_pos(&Y[inst].S[0], s0);
-        atomic_max_pos(&Y[inst].S[1], s1);
+    fluid = __any_sync(0xffffffffu, fluid);
+    if ((threadIdx.x & 31) == 0 && fluid) {
+        // advection: the constant speeds, exactly
+        atomic_max_pos(&Y[inst].S[0], I.eq == 0 ? (double)s0 : fabs(I.adv[0]));
+        atomic_max_pos(&Y[inst].S[1], I.eq == 0 ? (double)s1 : fabs(I.adv[1]));
     }
 }
 
+// Destinations: dsts[blockIdx.y] (null entry: skip) or dst1; nc planes of
+// nx*ny doubles, solid cells NaN.
 template <class T>
-__global__ void k_read_state(const InstDesc *__restrict__ D, double *__restrict__ out, int inst, int b) {
+__global__ void __launch_bounds__(STATE_THREADS) k_read_state(const InstDesc *__restrict__ D,
+                                                              double *const *__restrict__ dsts,
+                                                              double *__restrict__ dst1, int inst0, int b) {
+    const int inst = inst0 + blockIdx.y;
+    double *__restrict__ out = dsts ? dsts[blockIdx.y] : dst1;
+    if (!out) return;
     const InstDesc &I = D[inst];
-    size_t n = (size_t)I.nx * I.ny;
+    const int j0 = blockIdx.x * STATE_ROWS;
+    if (j0 >= I.ny) return;
+    const size_t n = (size_t)I.nx * I.ny;
     const size_t plane = (size_t)I.pitch * I.ny;
     const T *Q = buf<T>(I, b);
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-        int i = (int)(e % I.nx), j = (int)(e / I.nx);
-        for (int k = 0; k < I.nc; ++k) out[k * n + e] = (double)Q[k * plane + (size_t)j * I.pitch + i];
-    }
+    const int j1 = min(j0 + STATE_ROWS, I.ny);
+    for (int j = j0; j < j1; ++j)
+        for (int i = threadIdx.x; i < I.nx; i += STATE_THREADS)
+            for (int k = 0; k < I.nc; ++k)
+                out[k * n + (size_t)j * I.nx + i] = (double)Q[k * plane + (size_t)j * I.pitch + i];
 }
 
 // ---------------------------------------------------------------------------
@@ -2205,13 +2237,19 @@ int bulk_blocks_per_sm(int dir) {
     return 1;
 }
 
+// instances inst0 .. inst0+ninst-1 (max_ny: their largest ny); per-instance
+// pointers in the device array ptrs, or one pointer p1 (ninst == 1)
 template <class T>
-void launch_write_state(const InstDesc *D, InstDyn *Y, const double *Qh, int inst, int b, cudaStream_t st) {
-    k_write_state<T><<<512, 256, 0, st>>>(D, Y, Qh, inst, b);
+void launch_write_state(const InstDesc *D, InstDyn *Y, const double *const *ptrs, const double *p1, int inst0,
+                        int ninst, int max_ny, int b, cudaStream_t st) {
+    const dim3 grid((max_ny + STATE_ROWS - 1) / STATE_ROWS, ninst);
+    if (ninst > 0 && max_ny > 0) k_write_state<T><<<grid, STATE_THREADS, 0, st>>>(D, Y, ptrs, p1, inst0, b);
 }
 template <class T>
-void launch_read_state(const InstDesc *D, double *out, int inst, int b, cudaStream_t st) {
-    k_read_state<T><<<512, 256, 0, st>>>(D, out, inst, b);
+void launch_read_state(const InstDesc *D, double *const *ptrs, double *p1, int inst0, int ninst, int max_ny, int b,
+                       cudaStream_t st) {
+    const dim3 grid((max_ny + STATE_ROWS - 1) / STATE_ROWS, ninst);
+    if (ninst > 0 && max_ny > 0) k_read_state<T><<<grid, STATE_THREADS, 0, st>>>(D, ptrs, p1, inst0, b);
 }
 
 #define MB_INST(T)                                                                                                \
@@ -2220,8 +2258,9 @@ void launch_read_state(const InstDesc *D, double *out, int inst, int b, cudaStre
     template void launch_bulk<T>(int, int, const InstDesc *, InstDyn *, const BandRec *, int, int, int, int, int,  \
                                  int, int, DeferList, int, cudaStream_t);                                               \
     template int bulk_blocks_per_sm<T>(int);                                                                       \
-    template void launch_write_state<T>(const InstDesc *, InstDyn *, const double *, int, int, cudaStream_t);      \
-    template void launch_read_state<T>(const InstDesc *, double *, int, int, cudaStream_t);
+    template void launch_write_state<T>(const InstDesc *, InstDyn *, const double *const *, const double *, int,  \
+                                        int, int, int, cudaStream_t);                                             \
+    template void launch_read_state<T>(const InstDesc *, double *const *, double *, int, int, int, int, cudaStream_t);
 MB_INST(float)
 MB_INST(double)
 

@@ -25,7 +25,8 @@ EXPORTS = ["mb_create", "mb_batch_create", "mb_destroy", "mb_last_error", "mb_se
            "mb_enable_timing", "mb_kernel_time", "mb_band_records", "mb_band_record_size",
            "mb_cut_cells_noalloc", "mb_noalloc_last_error", "mb_batch_add", "mb_batch_remove", "mb_instance_bytes",
            "mb_request_bytes", "mb_server_create", "mb_server_destroy", "mb_server_last_error", "mb_server_submit",
-           "mb_server_tick", "mb_server_query", "mb_server_request_error", "mb_autotune", "mb_set_overlap"]
+           "mb_server_tick", "mb_server_query", "mb_server_request_error", "mb_autotune", "mb_set_overlap",
+           "mb_write_states", "mb_read_states"]
 
 
 class Grid(ctypes.Structure):
@@ -100,6 +101,8 @@ def _load():
         "mb_server_request_error": ([P, I], ctypes.c_char_p),
         "mb_autotune": ([P, D], I),
         "mb_set_overlap": ([P, I], I),
+        "mb_write_states": ([P, ctypes.POINTER(D), D], I),
+        "mb_read_states": ([P, ctypes.POINTER(D), D], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -169,9 +172,12 @@ class Sim:
         self.n = n
         self.precision = precision
         if write_initial:
-            for k, p in enumerate(self.problems):
-                if p.Q0 is not None:
-                    self.write_state(k, p.Q0)
+            if all(p.Q0 is not None for p in self.problems):
+                self.write_states([p.Q0 for p in self.problems])
+            else:
+                for k, p in enumerate(self.problems):
+                    if p.Q0 is not None:
+                        self.write_state(k, p.Q0)
 
     def _check(self, r):
         if r != MB_OK:
@@ -193,6 +199,39 @@ class Sim:
         p = self.problems[inst]
         Q = np.ascontiguousarray(Q, dtype=np.float64).reshape(p.nc, p.ny, p.nx)
         self._check(lib.mb_write_state(self._h, inst, _dp(Q), t))
+
+    @staticmethod
+    def _ptrs(arrays):
+        # numpy arrays, or addresses (ints) of host buffers such as pinned
+        # torch tensors' data_ptr()
+        D = ctypes.POINTER(ctypes.c_double)
+        return (D * len(arrays))(*[ctypes.cast(a, D) if isinstance(a, int) else _dp(a) for a in arrays])
+
+    def write_states(self, Qs, t=None):
+        """Every instance's state in one call (mb_write_states).  Qs[k]: a
+        C-contiguous float64 array of shape (nc, ny, nx), or the address of
+        such a host buffer; t: times (default 0)."""
+        if len(Qs) != self.n:
+            raise ValueError("one state per instance")
+        keep = []
+        for k, Q in enumerate(Qs):
+            if not isinstance(Q, int):
+                p = self.problems[k]
+                Q = np.ascontiguousarray(Q, dtype=np.float64).reshape(p.nc, p.ny, p.nx)
+            keep.append(Q)
+        tt = None if t is None else np.ascontiguousarray(t, dtype=np.float64)
+        self._check(lib.mb_write_states(self._h, self._ptrs(keep), _dp(tt) if tt is not None else None))
+
+    def read_states(self, out=None, check=True):
+        """Every instance's state in one call (mb_read_states) into out (as
+        for write_states) or new arrays; returns (states, clocks (n, 4), status)."""
+        if out is None:
+            out = [np.empty((p.nc, p.ny, p.nx)) for p in self.problems]
+        clk = np.empty((self.n, 4))
+        r = lib.mb_read_states(self._h, self._ptrs(out), _dp(clk))
+        if check:
+            self._check(r)
+        return out, clk, r
 
     def read_state(self, inst=0, alpha=False, check=True):
         p = self.problems[inst]
