@@ -131,16 +131,19 @@ mb_status mb_read_state(mb_sim *sim, int inst, double *Q, double *alpha, double 
 
 /* mb_write_state of every instance in one call: Q[k] is instance k's host
  * array (layout as above), t[k] its time (t NULL: all 0).  Same result as n
- * mb_write_state calls.  Arrays in page-locked host memory (cudaHostAlloc,
- * cudaMallocHost, cudaHostRegister) are read by the kernels in place over
- * the host link; pageable arrays are copied through a staging buffer.
+ * mb_write_state calls.  The arrays are copied into a device buffer that
+ * holds every instance's FP64 state (allocated on the first batched call)
+ * while the classification of the new poses runs beside the copies; arrays
+ * in page-locked host memory (cudaHostAlloc, cudaMallocHost,
+ * cudaHostRegister) copy at the full speed of the host link.
  * Synchronises: the arrays may be reused on return. */
 mb_status mb_write_states(mb_sim *sim, const double *const *Q, const double *t);
 
 /* mb_read_state of every instance in one call: Q[k] (NULL entries skipped)
  * receives instance k's state, clocks (optional, 4n doubles) the clocks
- * {t, X, Y, step}.  Page-locked arrays are written by the kernels in place.
- * Synchronises; returns the first flagged error in instance order. */
+ * {t, X, Y, step}.  One conversion launch into the batch's device buffer,
+ * then one copy per instance.  Synchronises; returns the first flagged
+ * error in instance order. */
 mb_status mb_read_states(mb_sim *sim, double *const *Q, double *clocks);
 
 /* One time step of every instance: two sweeps, x then y on even steps and

@@ -81,7 +81,9 @@ struct mb_sim {
     int *scratch = nullptr;
     double *stage = nullptr;      // staging for state I/O (nc * max cells doubles)
     size_t stage_len = 0;
-    const double **iop = nullptr; // per-instance host-buffer aliases of the batched state I/O
+    double *bstage = nullptr;     // batched state I/O: every instance's FP64 state
+    size_t cap_bstage = 0;
+    const double **iop = nullptr; // batched state I/O: per-instance pointers into bstage
     size_t cap_iop = 0;
     int total_cols = 0;           // geometry groups
     int *ginst = nullptr;         // instance of each geometry group
@@ -166,7 +168,7 @@ static void free_all(mb_sim *s) {
         for (void *p : h.allocs) cudaFree(p);
     s->ih.clear();
     void *shared[] = {s->dd, s->dy, s->vx, s->vy, s->px, s->py, s->ebox, s->vmov, s->vnext,
-                      s->rec, s->bnd, s->scratch, s->stage, s->ginst, s->ditem, s->dcount, s->iop};
+                      s->rec, s->bnd, s->scratch, s->stage, s->ginst, s->ditem, s->dcount, s->iop, s->bstage};
     for (void *p : shared)
         if (p) cudaFree(p);
     if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
@@ -416,11 +418,11 @@ static cudaError_t relayout(mb_sim *s, int old_n, const std::vector<int> &from) 
 
 // classes and volume fractions of instances k .. k+cnt-1 at their current
 // poses (alpha_out: the volume fractions of a single instance, nx*ny)
-static void classify_instances(mb_sim *s, int k, int cnt, double *alpha_out) {
+static void classify_instances(mb_sim *s, int k, int cnt, double *alpha_out, cudaStream_t st) {
     int max_nx = 0;
     for (int q = k; q < k + cnt; ++q) max_nx = std::max(max_nx, s->hd[q].nx);
     launch_classify(s->dd, s->dy, s->vx, s->vy, s->vmov, s->px, s->py, s->ebox, s->vnext, s->total_v, k, cnt, max_nx,
-                    alpha_out, s->stream);
+                    alpha_out, st);
 }
 
 mb_status mb_batch_create(int n, const mb_grid *grids, const double *gammas, const mb_body *bodies,
@@ -471,7 +473,7 @@ mb_status mb_batch_create(int n, const mb_grid *grids, const double *gammas, con
         s->bulk_grid[d] = bps * s->nsm;
     }
     // initial classes at t = 0
-    classify_instances(s, 0, n, nullptr);
+    classify_instances(s, 0, n, nullptr, s->stream);
     CK(cudaStreamSynchronize(s->stream));
     CK(cudaGetLastError());
 #undef CK
@@ -504,7 +506,7 @@ mb_status mb_batch_add(mb_sim *sim, const mb_grid *grid, double gamma, const mb_
     e = relayout(sim, old_n, from);
     if (e == cudaSuccess) {
         launch_nodes(sim->dd, sim->n, sim->stream);
-        classify_instances(sim, old_n, 1, nullptr);
+        classify_instances(sim, old_n, 1, nullptr, sim->stream);
         e = cudaStreamSynchronize(sim->stream);
         if (e == cudaSuccess) e = cudaGetLastError();
     }
@@ -760,19 +762,24 @@ mb_status mb_sync(mb_sim *sim) {
     return map_err(sim, err);
 }
 
-// Device alias of a page-locked host buffer: the state kernels read or write
-// it directly over the host link.  nullptr for pageable memory, which goes
-// through the staging buffer and a copy.
-static const double *host_alias(const void *p) {
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return nullptr;
+// batch staging buffer: the FP64 states of all instances back to back
+// (allocated on the first batched state I/O call); off[k]: instance k's offset
+static cudaError_t batch_stage(mb_sim *sim, std::vector<size_t> &off) {
+    off.resize(sim->n + 1);
+    off[0] = 0;
+    for (int k = 0; k < sim->n; ++k) {
+        const InstDesc &I = sim->hd[k];
+        off[k + 1] = off[k] + (size_t)I.nx * I.ny * I.nc;
     }
-    return a.type == cudaMemoryTypeHost && a.devicePointer ? (const double *)a.devicePointer : nullptr;
+    return ensure(&sim->bstage, sim->cap_bstage, off[sim->n], sizeof(double));
 }
 
-// instances k0 .. k0+cnt-1 from host arrays Q[q] at times t[q]
+static size_t state_bytes(const InstDesc &I) { return (size_t)I.nx * I.ny * I.nc * sizeof(double); }
+
+// instances k0 .. k0+cnt-1 from host arrays Q[q] at times t[q].  A single
+// instance goes through the one-instance staging buffer; a batch is copied
+// whole into the batch staging buffer while its classification runs on the
+// side stream, then converted by one launch.
 static mb_status write_states(mb_sim *sim, int k0, int cnt, const double *const *Q, const double *t) {
     if (sim->sidx != 0) {
         // abandon the half-done step: the written state starts a new one
@@ -781,6 +788,7 @@ static mb_status write_states(mb_sim *sim, int k0, int cnt, const double *const 
     }
     cudaStream_t st = sim->stream;
     std::vector<InstDyn> ys(cnt);
+    int max_ny = 0;
     for (int q = 0; q < cnt; ++q) {
         const InstDesc &I = sim->hd[k0 + q];
         InstDyn &y = ys[q];
@@ -789,35 +797,39 @@ static mb_status write_states(mb_sim *sim, int k0, int cnt, const double *const 
         y.X = I.U[0] * t[q];
         y.Y = I.U[1] * t[q];
         y.th = I.rotating ? I.a0 + I.a1 * std::sin(I.omega * t[q]) : 0.0;
+        max_ny = std::max(max_ny, I.ny);
     }
     cudaError_t e = cudaMemcpyAsync(sim->dy + k0, ys.data(), cnt * sizeof(InstDyn), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_check(sim, e, "write_state copy");
-    classify_instances(sim, k0, cnt, nullptr);
-    auto launch = [&](const double *const *ptrs, const double *p1, int i0, int ni, int max_ny) {
-        if (sim->prec == MB_FP32) launch_write_state<float>(sim->dd, sim->dy, ptrs, p1, i0, ni, max_ny, sim->cur, st);
-        else launch_write_state<double>(sim->dd, sim->dy, ptrs, p1, i0, ni, max_ny, sim->cur, st);
+    auto launch = [&](const double *const *ptrs, const double *p1, int i0, int ni, int mny) {
+        if (sim->prec == MB_FP32) launch_write_state<float>(sim->dd, sim->dy, ptrs, p1, i0, ni, mny, sim->cur, st);
+        else launch_write_state<double>(sim->dd, sim->dy, ptrs, p1, i0, ni, mny, sim->cur, st);
     };
-    std::vector<const double *> alias(cnt);
-    int n_alias = 0, max_ny = 0;
-    for (int q = 0; q < cnt; ++q) {
-        alias[q] = host_alias(Q[q]);
-        if (alias[q]) {
-            ++n_alias;
-            max_ny = std::max(max_ny, sim->hd[k0 + q].ny);
+    if (cnt == 1) {
+        e = cudaMemcpyAsync(sim->stage, Q[0], state_bytes(sim->hd[k0]), cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return cuda_check(sim, e, "write_state copy");
+        classify_instances(sim, k0, 1, nullptr, st);
+        launch(nullptr, sim->stage, k0, 1, max_ny);
+    } else {
+        std::vector<size_t> off;
+        e = batch_stage(sim, off);
+        if (e != cudaSuccess) return cuda_check(sim, e, "write_states staging");
+        e = cudaEventRecord(sim->ev_fork, st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(sim->side, sim->ev_fork, 0);
+        if (e != cudaSuccess) return cuda_check(sim, e, "write_states fork");
+        classify_instances(sim, k0, cnt, nullptr, sim->side);
+        e = cudaEventRecord(sim->ev_join, sim->side);
+        std::vector<const double *> ptrs(cnt);
+        for (int q = 0; q < cnt && e == cudaSuccess; ++q) {
+            ptrs[q] = sim->bstage + off[k0 + q];
+            e = cudaMemcpyAsync(sim->bstage + off[k0 + q], Q[q], state_bytes(sim->hd[k0 + q]),
+                                cudaMemcpyHostToDevice, st);
         }
-    }
-    if (n_alias) {
-        e = cudaMemcpyAsync(sim->iop, alias.data(), cnt * sizeof(double *), cudaMemcpyHostToDevice, st);
-        if (e != cudaSuccess) return cuda_check(sim, e, "write_state copy");
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(sim->iop, ptrs.data(), cnt * sizeof(double *), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, sim->ev_join, 0);
+        if (e != cudaSuccess) return cuda_check(sim, e, "write_states copy");
         launch(sim->iop, nullptr, k0, cnt, max_ny);
-    }
-    for (int q = 0; q < cnt; ++q) {
-        if (alias[q]) continue;
-        const InstDesc &I = sim->hd[k0 + q];
-        e = cudaMemcpyAsync(sim->stage, Q[q], (size_t)I.nx * I.ny * I.nc * sizeof(double), cudaMemcpyHostToDevice,
-                            st);
-        if (e != cudaSuccess) return cuda_check(sim, e, "write_state copy");
-        launch(nullptr, sim->stage, k0 + q, 1, I.ny);
     }
     e = cudaStreamSynchronize(st);
     if (e == cudaSuccess) e = cudaGetLastError();
@@ -827,7 +839,8 @@ static mb_status write_states(mb_sim *sim, int k0, int cnt, const double *const 
 }
 
 // states of instances k0 .. k0+cnt-1 into host arrays Q[q] (entries may be
-// NULL); their dynamic records into ys
+// NULL); their dynamic records into ys.  A batch is converted by one launch
+// into the batch staging buffer, then copied out.
 static mb_status read_states(mb_sim *sim, int k0, int cnt, double *const *Q, std::vector<InstDyn> &ys) {
     cudaStream_t st = sim->stream;
     const int buf = sim->sidx == 0 ? sim->cur : (sim->qn + 1) % 3;
@@ -836,29 +849,29 @@ static mb_status read_states(mb_sim *sim, int k0, int cnt, double *const *Q, std
         else launch_read_state<double>(sim->dd, ptrs, p1, i0, ni, max_ny, buf, st);
     };
     cudaError_t e = cudaSuccess;
-    std::vector<double *> alias(cnt, nullptr);
-    int n_alias = 0, max_ny = 0;
-    for (int q = 0; q < cnt; ++q) {
-        if (!Q[q]) continue;
-        alias[q] = const_cast<double *>(host_alias(Q[q]));
-        if (alias[q]) {
-            ++n_alias;
+    if (cnt == 1) {
+        if (Q[0]) {
+            launch(nullptr, sim->stage, k0, 1, sim->hd[k0].ny);
+            e = cudaMemcpyAsync(Q[0], sim->stage, state_bytes(sim->hd[k0]), cudaMemcpyDeviceToHost, st);
+        }
+    } else {
+        std::vector<size_t> off;
+        e = batch_stage(sim, off);
+        if (e != cudaSuccess) return cuda_check(sim, e, "read_states staging");
+        std::vector<double *> ptrs(cnt, nullptr);
+        int max_ny = 0;
+        for (int q = 0; q < cnt; ++q) {
+            if (!Q[q]) continue;
+            ptrs[q] = sim->bstage + off[k0 + q];
             max_ny = std::max(max_ny, sim->hd[k0 + q].ny);
         }
+        e = cudaMemcpyAsync(sim->iop, ptrs.data(), cnt * sizeof(double *), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) launch((double *const *)sim->iop, nullptr, k0, cnt, max_ny);
+        for (int q = 0; q < cnt && e == cudaSuccess; ++q)
+            if (Q[q])
+                e = cudaMemcpyAsync(Q[q], ptrs[q], state_bytes(sim->hd[k0 + q]), cudaMemcpyDeviceToHost, st);
     }
-    if (n_alias) {
-        e = cudaMemcpyAsync(sim->iop, alias.data(), cnt * sizeof(double *), cudaMemcpyHostToDevice, st);
-        if (e != cudaSuccess) return cuda_check(sim, e, "read_state copy");
-        launch((double *const *)sim->iop, nullptr, k0, cnt, max_ny);
-    }
-    for (int q = 0; q < cnt; ++q) {
-        if (!Q[q] || alias[q]) continue;
-        const InstDesc &I = sim->hd[k0 + q];
-        launch(nullptr, sim->stage, k0 + q, 1, I.ny);
-        e = cudaMemcpyAsync(Q[q], sim->stage, (size_t)I.nx * I.ny * I.nc * sizeof(double), cudaMemcpyDeviceToHost,
-                            st);
-        if (e != cudaSuccess) return cuda_check(sim, e, "read_state copy");
-    }
+    if (e != cudaSuccess) return cuda_check(sim, e, "read_state copy");
     ys.resize(cnt);
     e = cudaMemcpyAsync(ys.data(), sim->dy + k0, cnt * sizeof(InstDyn), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -893,7 +906,7 @@ mb_status mb_read_state(mb_sim *sim, int inst, double *Q, double *alpha, double 
     const InstDesc &I = sim->hd[inst];
     cudaStream_t st = sim->stream;
     if (alpha) {
-        classify_instances(sim, inst, 1, sim->stage);
+        classify_instances(sim, inst, 1, sim->stage, st);
         cudaError_t e = cudaMemcpyAsync(alpha, sim->stage, (size_t)I.nx * I.ny * sizeof(double),
                                         cudaMemcpyDeviceToHost, st);
         if (e != cudaSuccess) return cuda_check(sim, e, "alpha copy");

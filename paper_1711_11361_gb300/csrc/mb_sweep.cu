@@ -2072,9 +2072,8 @@ __global__ void k_finalize(const InstDesc *__restrict__ D, InstDyn *__restrict__
 // ---------------------------------------------------------------------------
 // state initialisation and the CFL wave speeds of a state; state read-back.
 // One CTA per STATE_ROWS rows of one instance (instance inst0 + blockIdx.y),
-// threads along the row.  A source / destination is either device memory
-// (the staging buffer) or a page-locked host buffer seen through its device
-// alias, which the kernel reads or writes directly over the host link.
+// threads along the row; the FP64 host layout lives in a device staging
+// buffer (one per instance, or one per batch with a pointer per instance).
 // ---------------------------------------------------------------------------
 constexpr int STATE_ROWS = 8;
 constexpr int STATE_THREADS = 128;

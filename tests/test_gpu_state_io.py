@@ -1,7 +1,6 @@
 """Batched host state I/O (mb_write_states / mb_read_states): the same bits as
 one mb_write_state / mb_read_state call per instance, whether the host
-arrays are pageable (copied through the staging buffer) or page-locked (read
-and written by the kernels in place), in FP32 and FP64; a write followed by
+arrays are pageable or page-locked, in FP32 and FP64; a write followed by
 a read returns the state rounded to the batch's precision, NaN in solid
 cells."""
 import numpy as np
