@@ -31,8 +31,8 @@ void launch_geom(const InstDesc *, InstDyn *, const int *, const double *, const
 void launch_classify(const InstDesc *, InstDyn *, const double *, const double *, const unsigned char *, double *,
                      double *, float *, const int *, int, int, int, int, double *, cudaStream_t);
 template <class T>
-void launch_band_stage(int, const InstDesc *, InstDyn *, BandRec *, const double *, int *, int, int, int, int, int,
-                       int, int, int, cudaStream_t);
+void launch_band_stage(int, const InstDesc *, InstDyn *, BandRec *, const double *, int *, int *, int, int, int, int,
+                       int, int, int, int, cudaStream_t);
 template <class T>
 void launch_bulk(int, int, const InstDesc *, InstDyn *, const BandRec *, int, int, int, int, int, int, int, DeferList,
                  int, cudaStream_t);
@@ -79,6 +79,8 @@ struct mb_sim {
     double *bnd = nullptr;
     int total_rec = 0;
     int *scratch = nullptr;
+    int *boff = nullptr;          // used band records before each instance (n + 1), per sweep
+    size_t cap_boff = 0;
     double *stage = nullptr;      // staging for state I/O (nc * max cells doubles)
     size_t stage_len = 0;
     double *bstage = nullptr;     // batched state I/O: every instance's FP64 state
@@ -168,7 +170,7 @@ static void free_all(mb_sim *s) {
         for (void *p : h.allocs) cudaFree(p);
     s->ih.clear();
     void *shared[] = {s->dd, s->dy, s->vx, s->vy, s->px, s->py, s->ebox, s->vmov, s->vnext,
-                      s->rec, s->bnd, s->scratch, s->stage, s->ginst, s->ditem, s->dcount, s->iop, s->bstage};
+                      s->rec, s->bnd, s->scratch, s->stage, s->ginst, s->ditem, s->dcount, s->iop, s->bstage, s->boff};
     for (void *p : shared)
         if (p) cudaFree(p);
     if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
@@ -385,6 +387,7 @@ static cudaError_t relayout(mb_sim *s, int old_n, const std::vector<int> &from) 
     if (e == cudaSuccess) e = ensure(&s->scratch, s->cap_scr, (size_t)std::max(1, n) * 3 * MIXCAP_HOST, sizeof(int));
     if (e == cudaSuccess) e = ensure(&s->stage, s->stage_len, max_cells * 4, sizeof(double));
     if (e == cudaSuccess) e = ensure(&s->iop, s->cap_iop, std::max(1, n), sizeof(double *));
+    if (e == cudaSuccess) e = ensure(&s->boff, s->cap_boff, (size_t)n + 1, sizeof(int));
     if (e == cudaSuccess) e = ensure(&s->dd, s->cap_dd, std::max(1, n), sizeof(InstDesc));
     if (e == cudaSuccess) e = ensure(&s->dy, s->cap_dy, std::max(1, n), sizeof(InstDyn));
     if (e == cudaSuccess) e = ensure(&s->ginst, s->cap_ginst, std::max<size_t>(1, ginst.size()), sizeof(int));
@@ -606,11 +609,11 @@ static mb_status do_sweep(mb_sim *s, int dir, double dt) {
                 dt, st);
     auto band = [&](int stage, cudaStream_t sx) {
         if (s->prec == MB_FP32)
-            launch_band_stage<float>(stage, s->dd, s->dy, s->rec, s->bnd, s->scratch, s->n, s->total_rec, dir, src,
-                                     dst, qn, s->sidx, last, sx);
+            launch_band_stage<float>(stage, s->dd, s->dy, s->rec, s->bnd, s->scratch, s->boff, s->n, s->total_rec,
+                                     dir, src, dst, qn, s->sidx, last, sx);
         else
-            launch_band_stage<double>(stage, s->dd, s->dy, s->rec, s->bnd, s->scratch, s->n, s->total_rec, dir, src,
-                                      dst, qn, s->sidx, last, sx);
+            launch_band_stage<double>(stage, s->dd, s->dy, s->rec, s->bnd, s->scratch, s->boff, s->n, s->total_rec,
+                                      dir, src, dst, qn, s->sidx, last, sx);
     };
     auto geom_band = [&](cudaStream_t sx) {
         launch_geom(s->dd, s->dy, s->ginst, s->px, s->py, s->ebox, s->vnext, s->vmov, s->total_v, s->n, s->total_cols,

@@ -30,6 +30,55 @@ __device__ __forceinline__ int find_inst_rec(const InstDesc *D, int n_inst, int 
     return lo;
 }
 
+// The band kernels run over the used band records only: boff[k] counts the
+// used records of instances 0..k-1 (boff[n_inst]: all of them), and thread t
+// of a launch takes the t-th, instance by instance.  -1 past the last.
+__device__ __forceinline__ int band_rec_of(const InstDesc *D, const int *__restrict__ boff, int n_inst, int t) {
+    if (t >= boff[n_inst]) return -1;
+    int lo = 0, hi = n_inst - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (boff[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    return D[lo].rec_base + (t - boff[lo]);
+}
+
+// one CTA of 256 threads after the geometry: boff from each instance's
+// record count (capped at its capacity; an overflow is flagged elsewhere)
+__global__ void __launch_bounds__(256) k_band_offsets(const InstDesc *__restrict__ D, const InstDyn *__restrict__ Y,
+                                                      int n_inst, int *__restrict__ boff) {
+    __shared__ int wsum[8];
+    __shared__ int carry;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int k0 = 0; k0 < n_inst; k0 += 256) {
+        const int k = k0 + threadIdx.x;
+        const int c = k < n_inst ? min(Y[k].band_count, D[k].rec_cap) : 0;
+        int v = c;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += u;
+        }
+        if (lane == 31) wsum[warp] = v;
+        __syncthreads();
+        if (warp == 0) {
+            int w = lane < 8 ? wsum[lane] : 0;
+            for (int o = 1; o < 8; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += u;
+            }
+            if (lane < 8) wsum[lane] = w;
+        }
+        __syncthreads();
+        if (k < n_inst) boff[k] = carry + (warp ? wsum[warp - 1] : 0) + v - c;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += wsum[7];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) boff[n_inst] = carry;
+}
+
 template <class T>
 __device__ __forceinline__ const T *buf(const InstDesc &I, int b) { return (const T *)I.Q[b]; }
 template <class T>
@@ -150,10 +199,8 @@ __device__ __forceinline__ void warp_max_to(InstDyn *Y, bool act, int inst, doub
 // k_band_prep
 // ---------------------------------------------------------------------------
 template <class T>
-__global__ void k_band_prep(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y, BandRec *__restrict__ R,
-                            int n_inst, int total_rec, int dir, int src, int qn) {
-    int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= total_rec) return;
+__device__ __forceinline__ void band_prep_rec(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y,
+                                              BandRec *__restrict__ R, int n_inst, int r, int dir, int src, int qn) {
     int inst = find_inst_rec(D, n_inst, r);
     const InstDesc &I = D[inst];
     InstDyn &y = Y[inst];
@@ -275,6 +322,17 @@ __global__ void k_band_prep(const InstDesc *__restrict__ D, InstDyn *__restrict_
     }
 }
 
+template <class T>
+__global__ void k_band_prep(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y, BandRec *__restrict__ R,
+                            const int *__restrict__ boff, int n_inst, int dir, int src, int qn) {
+    const int stride = gridDim.x * blockDim.x;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x;; t += stride) {
+        const int r = band_rec_of(D, boff, n_inst, t);
+        if (r < 0) break;
+        band_prep_rec<T>(D, Y, R, n_inst, r, dir, src, qn);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // stabilised flux of one face: aperture times F2D (eqs. Klein2shieldedFluxMethod2
 // and Klein2DtotalfluxaMethod2 with the one- or two-sided shielded parts).
@@ -383,12 +441,17 @@ __device__ __forceinline__ bool band_sweep_rec(const InstDesc *__restrict__ D, I
 
 template <class T>
 __global__ void k_band_sweep(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y, BandRec *__restrict__ R,
-                             const double *__restrict__ bnd, int n_inst, int total_rec, int dir, int src) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    double ws[MAXC] = {0.0, 0.0, 0.0, 0.0};
-    int inst = -1;
-    const bool act = r < total_rec && band_sweep_rec<T>(D, Y, R, bnd, n_inst, r, dir, src, ws, inst);
-    warp_add_to(Y, act, inst, ws);
+                             const double *__restrict__ bnd, const int *__restrict__ boff, int n_inst, int dir,
+                             int src) {
+    const int total = boff[n_inst], stride = gridDim.x * blockDim.x;
+    // whole warps iterate together (the wall-flux sum is warp-wide)
+    for (int base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31; base < total; base += stride) {
+        const int r = band_rec_of(D, boff, n_inst, base + (threadIdx.x & 31));
+        double ws[MAXC] = {0.0, 0.0, 0.0, 0.0};
+        int inst = -1;
+        const bool act = r >= 0 && band_sweep_rec<T>(D, Y, R, bnd, n_inst, r, dir, src, ws, inst);
+        warp_add_to(Y, act, inst, ws);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1771,10 +1834,8 @@ void bulk_attr_t(int dir) {
 // k_events: covering / uncovering, gathered by each band cell
 // ---------------------------------------------------------------------------
 template <class T>
-__global__ void k_events(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y, BandRec *__restrict__ R,
-                         int n_inst, int total_rec) {
-    int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= total_rec) return;
+__device__ __forceinline__ void events_rec(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y,
+                                           BandRec *__restrict__ R, int n_inst, int r) {
     int inst = find_inst_rec(D, n_inst, r);
     const InstDesc &I = D[inst];
     InstDyn &y = Y[inst];
@@ -1834,6 +1895,17 @@ __global__ void k_events(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y
             int k = atomicAdd(&y.nbad, 1);
             if (k < 16) y.badlist[k] = r;
         }
+    }
+}
+
+template <class T>
+__global__ void k_events(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y, BandRec *__restrict__ R,
+                         const int *__restrict__ boff, int n_inst) {
+    const int stride = gridDim.x * blockDim.x;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x;; t += stride) {
+        const int r = band_rec_of(D, boff, n_inst, t);
+        if (r < 0) break;
+        events_rec<T>(D, Y, R, n_inst, r);
     }
 }
 
@@ -2061,12 +2133,16 @@ __device__ __forceinline__ bool finalize_rec(const InstDesc *__restrict__ D, Ins
 
 template <class T>
 __global__ void k_finalize(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y, BandRec *__restrict__ R,
-                           int n_inst, int total_rec, int dst, int last) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    double s0 = 0.0, s1 = 0.0;
-    int inst = -1;
-    const bool act = r < total_rec && finalize_rec<T>(D, Y, R, n_inst, r, dst, last, s0, s1, inst);
-    if (last) warp_max_to(Y, act, inst, s0, s1);
+                           const int *__restrict__ boff, int n_inst, int dst, int last) {
+    const int total = boff[n_inst], stride = gridDim.x * blockDim.x;
+    // whole warps iterate together (the wave-speed reduction is warp-wide)
+    for (int base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31; base < total; base += stride) {
+        const int r = band_rec_of(D, boff, n_inst, base + (threadIdx.x & 31));
+        double s0 = 0.0, s1 = 0.0;
+        int inst = -1;
+        const bool act = r >= 0 && finalize_rec<T>(D, Y, R, n_inst, r, dst, last, s0, s1, inst);
+        if (last) warp_max_to(Y, act, inst, s0, s1);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -2156,17 +2232,24 @@ __global__ void __launch_bounds__(STATE_THREADS) k_read_state(const InstDesc *__
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
+// stage 0 first counts the sweep's used band records (boff, n_inst + 1
+// ints); the record kernels then run grid-stride over those only
 template <class T>
 void launch_band_stage(int stage, const InstDesc *D, InstDyn *Y, BandRec *R, const double *bnd, int *scratch,
-                       int n_inst, int total_rec, int dir, int src, int dst, int qn, int sidx, int last,
+                       int *boff, int n_inst, int total_rec, int dir, int src, int dst, int qn, int sidx, int last,
                        cudaStream_t st) {
-    int blocks = (total_rec + 127) / 128;
+    constexpr int BAND_BLOCKS = 1216;   // 8 CTAs of 128 threads per SM
+    const int blocks = std::min((total_rec + 127) / 128, BAND_BLOCKS);
     switch (stage) {
-        case 0: if (blocks) k_band_prep<T><<<blocks, 128, 0, st>>>(D, Y, R, n_inst, total_rec, dir, src, qn); break;
-        case 1: if (blocks) k_band_sweep<T><<<blocks, 128, 0, st>>>(D, Y, R, bnd, n_inst, total_rec, dir, src); break;
-        case 2: if (blocks) k_events<T><<<blocks, 128, 0, st>>>(D, Y, R, n_inst, total_rec); break;
+        case 0:
+            if (!blocks) break;
+            k_band_offsets<<<1, 256, 0, st>>>(D, Y, n_inst, boff);
+            k_band_prep<T><<<blocks, 128, 0, st>>>(D, Y, R, boff, n_inst, dir, src, qn);
+            break;
+        case 1: if (blocks) k_band_sweep<T><<<blocks, 128, 0, st>>>(D, Y, R, bnd, boff, n_inst, dir, src); break;
+        case 2: if (blocks) k_events<T><<<blocks, 128, 0, st>>>(D, Y, R, boff, n_inst); break;
         case 3: k_mix<T><<<(n_inst + 63) / 64, 64, 0, st>>>(D, Y, R, scratch, n_inst, dst, sidx); break;
-        case 4: if (blocks) k_finalize<T><<<blocks, 128, 0, st>>>(D, Y, R, n_inst, total_rec, dst, last); break;
+        case 4: if (blocks) k_finalize<T><<<blocks, 128, 0, st>>>(D, Y, R, boff, n_inst, dst, last); break;
     }
 }
 
@@ -2252,8 +2335,8 @@ void launch_read_state(const InstDesc *D, double *const *ptrs, double *p1, int i
 }
 
 #define MB_INST(T)                                                                                                \
-    template void launch_band_stage<T>(int, const InstDesc *, InstDyn *, BandRec *, const double *, int *, int, int, \
-                                       int, int, int, int, int, int, cudaStream_t);                                \
+    template void launch_band_stage<T>(int, const InstDesc *, InstDyn *, BandRec *, const double *, int *, int *,   \
+                                       int, int, int, int, int, int, int, int, cudaStream_t);                     \
     template void launch_bulk<T>(int, int, const InstDesc *, InstDyn *, const BandRec *, int, int, int, int, int,  \
                                  int, int, DeferList, int, cudaStream_t);                                               \
     template int bulk_blocks_per_sm<T>(int);                                                                       \
