@@ -1638,7 +1638,7 @@ __device__ __forceinline__ void def_wave_speeds(InstDyn *__restrict__ Y, int ins
     }
 }
 
-__global__ void __launch_bounds__(128) k_bulk_def_x(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y,
+__global__ void __launch_bounds__(128, 5) k_bulk_def_x(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y,
                                                     const BandRec *__restrict__ R, int src, int dst, int last,
                                                     DeferList dl) {
     const int cnt = min(*dl.count, dl.cap);
@@ -1741,7 +1741,7 @@ __global__ void __launch_bounds__(128) k_bulk_def_x(const InstDesc *__restrict__
     }
 }
 
-__global__ void __launch_bounds__(128) k_bulk_def_y(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y,
+__global__ void __launch_bounds__(128, 5) k_bulk_def_y(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y,
                                                     const BandRec *__restrict__ R, int src, int dst, int last,
                                                     DeferList dl) {
     const int cnt = min(*dl.count, dl.cap);
@@ -2269,7 +2269,7 @@ void launch_bulk(int dir, int eq, const InstDesc *D, InstDyn *Y, const BandRec *
     if (!packed && mode != 0) return;
     const int pg = (total_warps + wpc - 1) / wpc;
     const bool m4 = (shape & SHAPE_MINB4) != 0, r8 = (shape & SHAPE_RING8) != 0;
-    constexpr int DEF_BLOCKS = 1216;   // 8 CTAs of 128 threads per SM, grid-stride over the list
+    constexpr int DEF_BLOCKS = 760;   // 5 resident CTAs of 128 threads per SM, grid-stride over the list
     if (dir == 0) {
         if (packed) {
             const size_t sm = wpc * (r8 ? sizeof(XRing<8>) : sizeof(XRing<4>));
