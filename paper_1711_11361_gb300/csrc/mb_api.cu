@@ -31,7 +31,7 @@ void launch_geom(const InstDesc *, InstDyn *, const int *, const double *, const
 void launch_classify(const InstDesc *, InstDyn *, const double *, const double *, const unsigned char *, double *,
                      double *, float *, const int *, int, int, int, int, double *, cudaStream_t);
 template <class T>
-void launch_band_stage(int, const InstDesc *, InstDyn *, BandRec *, const double *, int *, int *, int, int, int, int,
+void launch_band_stage(int, const InstDesc *, InstDyn *, BandRec *, const double *, int *, int, int, int, int,
                        int, int, int, int, cudaStream_t);
 template <class T>
 void launch_bulk(int, int, const InstDesc *, InstDyn *, const BandRec *, int, int, int, int, int, int, int, DeferList,
@@ -43,7 +43,6 @@ void launch_write_state(const InstDesc *, InstDyn *, const double *const *, cons
                         cudaStream_t);
 template <class T>
 void launch_read_state(const InstDesc *, double *const *, double *, int, int, int, int, cudaStream_t);
-constexpr int MIXCAP_HOST = 1024;
 }  // namespace mb
 
 using namespace mb;
@@ -67,7 +66,7 @@ struct mb_sim {
     std::vector<InstHost> ih;
     // capacities (elements) of the shared arrays below
     size_t cap_vx = 0, cap_vy = 0, cap_mov = 0, cap_next = 0, cap_px = 0, cap_py = 0, cap_ebox = 0;
-    size_t cap_rec = 0, cap_bnd = 0, cap_scr = 0, cap_dd = 0, cap_dy = 0, cap_ginst = 0;
+    size_t cap_rec = 0, cap_bnd = 0, cap_dd = 0, cap_dy = 0, cap_ginst = 0;
     InstDesc *dd = nullptr;
     InstDyn *dy = nullptr;
     double *vx = nullptr, *vy = nullptr, *px = nullptr, *py = nullptr;
@@ -78,7 +77,6 @@ struct mb_sim {
     BandRec *rec = nullptr;
     double *bnd = nullptr;
     int total_rec = 0;
-    int *scratch = nullptr;
     int *boff = nullptr;          // used band records before each instance (n + 1), per sweep
     size_t cap_boff = 0;
     double *stage = nullptr;      // staging for state I/O (nc * max cells doubles)
@@ -170,7 +168,7 @@ static void free_all(mb_sim *s) {
         for (void *p : h.allocs) cudaFree(p);
     s->ih.clear();
     void *shared[] = {s->dd, s->dy, s->vx, s->vy, s->px, s->py, s->ebox, s->vmov, s->vnext,
-                      s->rec, s->bnd, s->scratch, s->stage, s->ginst, s->ditem, s->dcount, s->iop, s->bstage, s->boff};
+                      s->rec, s->bnd, s->stage, s->ginst, s->ditem, s->dcount, s->iop, s->bstage, s->boff};
     for (void *p : shared)
         if (p) cudaFree(p);
     if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
@@ -322,7 +320,7 @@ static size_t instance_bytes(const InstDesc &I, int prec) {
     const size_t cells = (size_t)I.pitch * I.ny;
     return 3 * cells * I.nc * esz + cells * (1 + 4 + 8) + (size_t)(I.nx + I.ny + 2) * 8 +
            (size_t)I.rec_cap * (sizeof(BandRec) + 8) + (size_t)I.nv * 100 + sizeof(InstDesc) + sizeof(InstDyn) +
-           3 * MIXCAP_HOST * sizeof(int) + (size_t)I.nx * I.ny * I.nc * 8;
+           (size_t)I.nx * I.ny * I.nc * 8;
 }
 
 // offsets of every instance in the shared arrays, those arrays, the
@@ -384,7 +382,6 @@ static cudaError_t relayout(mb_sim *s, int old_n, const std::vector<int> &from) 
     if (e == cudaSuccess) e = ensure(&s->ebox, s->cap_ebox, 3 * tv * 2, sizeof(float));
     if (e == cudaSuccess) e = ensure(&s->rec, s->cap_rec, std::max(1, rec_total), sizeof(BandRec));
     if (e == cudaSuccess) e = ensure(&s->bnd, s->cap_bnd, std::max(1, rec_total), sizeof(double));
-    if (e == cudaSuccess) e = ensure(&s->scratch, s->cap_scr, (size_t)std::max(1, n) * 3 * MIXCAP_HOST, sizeof(int));
     if (e == cudaSuccess) e = ensure(&s->stage, s->stage_len, max_cells * 4, sizeof(double));
     if (e == cudaSuccess) e = ensure(&s->iop, s->cap_iop, std::max(1, n), sizeof(double *));
     if (e == cudaSuccess) e = ensure(&s->boff, s->cap_boff, (size_t)n + 1, sizeof(int));
@@ -609,10 +606,10 @@ static mb_status do_sweep(mb_sim *s, int dir, double dt) {
                 dt, st);
     auto band = [&](int stage, cudaStream_t sx) {
         if (s->prec == MB_FP32)
-            launch_band_stage<float>(stage, s->dd, s->dy, s->rec, s->bnd, s->scratch, s->boff, s->n, s->total_rec,
+            launch_band_stage<float>(stage, s->dd, s->dy, s->rec, s->bnd, s->boff, s->n, s->total_rec,
                                      dir, src, dst, qn, s->sidx, last, sx);
         else
-            launch_band_stage<double>(stage, s->dd, s->dy, s->rec, s->bnd, s->scratch, s->boff, s->n, s->total_rec,
+            launch_band_stage<double>(stage, s->dd, s->dy, s->rec, s->bnd, s->boff, s->n, s->total_rec,
                                       dir, src, dst, qn, s->sidx, last, sx);
     };
     auto geom_band = [&](cudaStream_t sx) {

@@ -1912,40 +1912,62 @@ __global__ void k_events(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y
 // ---------------------------------------------------------------------------
 // k_mix: positivity safeguard (a reading; the paper gives none): every cluster
 // of non-physical cells and their fluid face neighbours shares its total
-// content in proportion to volume.  One thread per instance; runs only when
-// the instance flagged a bad cell.  Also advances the instance's clock.
+// content in proportion to volume.  One warp per instance; runs only when the
+// instance flagged a bad cell.  Also advances the instance's clock.
+//
+// The cluster bookkeeping (union-find over the cells involved) lives in
+// shared memory.  Every lane follows the same control flow on the same data;
+// lane 0 writes the shared arrays, and the searches, the scans of the band
+// records and the loads of the cluster members are spread over the lanes.
+// Sums over a cluster run in cell order on every lane alike, so the result
+// does not depend on the lanes.
 // ---------------------------------------------------------------------------
 constexpr int MIXCAP = 1024;
 constexpr int MIX_LAYERS = 8;   // merges per sweep (cells still non-physical seed the next)
 
 template <class T>
-__global__ void k_mix(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y, BandRec *__restrict__ R,
-                      int *__restrict__ scratch, int n_inst, int dst, int sidx) {
-    int inst = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(32) k_mix(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y,
+                                            BandRec *__restrict__ R, int n_inst, int dst, int sidx) {
+    __shared__ int node[MIXCAP];   // cell of each node
+    __shared__ int par[MIXCAP];    // union-find parent (node index), later the root's cell
+    __shared__ int nxt[MIXCAP];    // seeds of the merge; scratch of the root pass
+    __shared__ unsigned char nbm[MIXCAP];   // each seed's fluid face neighbours (bit m: neighbour m)
+    const int inst = blockIdx.x, lane = threadIdx.x;
     if (inst >= n_inst) return;
     const InstDesc &I = D[inst];
     InstDyn &y = Y[inst];
-    // advance pose and clock
-    y.X = y.XB;
-    y.Y = y.YB;
-    y.th = y.thB;
-    if (sidx == 1) {
-        y.t += y.dt;
-        y.step += 1;
+    const int nbad = y.nbad, nbulk = y.nbulk;
+    __syncwarp();
+    if (lane == 0) {
+        // advance pose and clock
+        y.X = y.XB;
+        y.Y = y.YB;
+        y.th = y.thB;
+        if (sidx == 1) {
+            y.t += y.dt;
+            y.step += 1;
+        }
     }
-    if (y.nbad == 0 && y.nbulk == 0) return;
-    if (y.nbulk > NBULK) { y.err |= ERR_UNSTABLE | ERR_MIX_CAP; return; }
-    int *node = scratch + (size_t)inst * 3 * MIXCAP;     // cell index of node
-    int *par = node + MIXCAP;
-    int nn = 0;
+    if (nbad == 0 && nbulk == 0) return;
+    if (nbulk > NBULK) {
+        if (lane == 0) y.err |= ERR_UNSTABLE | ERR_MIX_CAP;
+        return;
+    }
+    int nn = 0;   // nodes (the same on every lane)
     const size_t plane = (size_t)I.pitch * I.ny;
     T *Qo = bufw<T>(I, dst);
     auto find_node = [&](int cell) -> int {
-        for (int k = 0; k < nn; ++k)
-            if (node[k] == cell) return k;
+        for (int k0 = 0; k0 < nn; k0 += 32) {
+            const int k = k0 + lane;
+            const unsigned m = __ballot_sync(0xffffffffu, k < nn && node[k] == cell);
+            if (m) return k0 + __ffs(m) - 1;
+        }
         if (nn >= MIXCAP) return -1;
-        node[nn] = cell;
-        par[nn] = nn;
+        if (lane == 0) {
+            node[nn] = cell;
+            par[nn] = nn;
+        }
+        __syncwarp();
         return nn++;
     };
     auto root = [&](int k) { while (par[k] != k) k = par[k]; return k; };
@@ -1953,23 +1975,51 @@ __global__ void k_mix(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y, B
         const uint8_t cl = I.cls[c];
         return (cl & CLS_BAND) ? R[I.rec[c]].aB : ((cl & CLS_SOLID) ? 0.0 : 1.0);
     };
+    const int dd[4][2] = {{-1, 0}, {1, 0}, {0, -1}, {0, 1}};
+    auto nbr = [&](int i, int j, int m, int &c) -> bool {
+        int ii = i + dd[m][0], jj = j + dd[m][1];
+        if (I.bc[0] == 2) { ii %= I.nx; if (ii < 0) ii += I.nx; }
+        if (I.bc[2] == 2) { jj %= I.ny; if (jj < 0) jj += I.ny; }
+        if (ii < 0 || ii >= I.nx || jj < 0 || jj >= I.ny) return false;
+        c = jj * I.pitch + ii;
+        return true;
+    };
     // a non-physical cell joins the clusters of its fluid face neighbours
-    auto seed = [&](int cell, int i, int j) -> bool {
+    // (msk: which of them are fluid, found beforehand)
+    auto seed = [&](int cell, unsigned msk) -> bool {
         const int kb = find_node(cell);
         if (kb < 0) return false;
-        const int dd[4][2] = {{-1, 0}, {1, 0}, {0, -1}, {0, 1}};
+        const int i = cell % I.pitch, j = cell / I.pitch;
         for (int m = 0; m < 4; ++m) {
-            int ii = i + dd[m][0], jj = j + dd[m][1];
-            if (I.bc[0] == 2) { ii %= I.nx; if (ii < 0) ii += I.nx; }
-            if (I.bc[2] == 2) { jj %= I.ny; if (jj < 0) jj += I.ny; }
-            if (ii < 0 || ii >= I.nx || jj < 0 || jj >= I.ny) continue;
-            const int c = jj * I.pitch + ii;
-            if (!(alpha_B(c) > 0.0)) continue;
+            int c;
+            if (!((msk >> m) & 1u) || !nbr(i, j, m, c)) continue;
             const int kn = find_node(c);
             if (kn < 0) return false;
             const int ra = root(kb), rb = root(kn);
-            if (ra != rb) { if (ra < rb) par[rb] = ra; else par[ra] = rb; }
+            if (ra != rb) {
+                if (lane == 0) {
+                    if (ra < rb) par[rb] = ra; else par[ra] = rb;
+                }
+                __syncwarp();
+            }
         }
+        return true;
+    };
+    // the ns seeds in nxt, in order; their neighbours' volume fractions are
+    // looked up by all lanes at once (classes and records do not change here)
+    auto seed_all = [&](int ns) -> bool {
+        for (int q = lane; q < ns; q += 32) {
+            const int c = nxt[q], i = c % I.pitch, j = c / I.pitch;
+            unsigned msk = 0u;
+            for (int m = 0; m < 4; ++m) {
+                int cn;
+                if (nbr(i, j, m, cn) && alpha_B(cn) > 0.0) msk |= 1u << m;
+            }
+            nbm[q] = (unsigned char)msk;
+        }
+        __syncwarp();
+        for (int q = 0; q < ns; ++q)
+            if (!seed(nxt[q], nbm[q])) return false;
         return true;
     };
     auto sort_int = [](int *v, int m) {
@@ -1993,72 +2043,94 @@ __global__ void k_mix(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y, B
         const double pm = (I.gamma - 1.0) * (q[3] - 0.5 * (q[1] * q[1] + q[2] * q[2]) / q[0]);
         return q[0] > 0.0 && pm > 0.0 && isfinite(q[1]) && isfinite(q[2]) && isfinite(q[3]);
     };
-    int *next = par + MIXCAP;   // seeds of the next merge
     int nnext = 0;
     bool overflow = false;
     for (int layer = 0; layer < MIX_LAYERS; ++layer) {
         nn = 0;
+        int ns = nnext;   // later merges: the cells still non-physical, in cell order
         if (layer == 0) {
             // flagged band records by cell, then listed bulk cells
             int seeds[16 + NBULK];
-            int ns = 0;
-            const bool listed = y.nbad <= 16;
-            if (listed) {
-                for (int q = 0; q < y.nbad; ++q) seeds[ns++] = R[y.badlist[q]].cell;
-                sort_int(seeds, ns);
-                for (int q = 0; q < ns && !overflow; ++q) {
-                    const int c = seeds[q];
-                    overflow = !seed(c, c % I.pitch, c / I.pitch);
-                }
-            } else {
-                for (int q = 0; q < y.band_count && !overflow; ++q) {
-                    const BandRec &bb = R[I.rec_base + q];
-                    if (bb.flags & RF_BAD) overflow = !seed(bb.cell, bb.i, bb.j);
-                }
-            }
+            int nl = 0;
             ns = 0;
-            for (int q = 0; q < y.nbulk; ++q) seeds[ns++] = y.bulkbad[q];
-            sort_int(seeds, ns);
-            for (int q = 0; q < ns && !overflow; ++q) {
-                const int c = seeds[q];
-                overflow = !seed(c, c % I.pitch, c / I.pitch);
+            if (nbad <= 16) {
+                for (int q = 0; q < nbad; ++q) seeds[nl++] = R[y.badlist[q]].cell;
+                sort_int(seeds, nl);
+                if (lane == 0)
+                    for (int q = 0; q < nl; ++q) nxt[q] = seeds[q];
+                ns = nl;
+            } else {
+                // every flagged record, in record order
+                const int nrec = min(y.band_count, I.rec_cap);
+                for (int q0 = 0; q0 < nrec; q0 += 32) {
+                    const int q = q0 + lane;
+                    const bool bad = q < nrec && (R[I.rec_base + q].flags & RF_BAD);
+                    const unsigned m = __ballot_sync(0xffffffffu, bad);
+                    const int at = ns + __popc(m & ((1u << lane) - 1u));
+                    if (bad && at < MIXCAP) nxt[at] = R[I.rec_base + q].cell;
+                    ns += __popc(m);
+                }
             }
-        } else {
-            // cells still non-physical after the last merge (in cell order)
-            for (int q = 0; q < nnext && !overflow; ++q) {
-                const int c = next[q];
-                overflow = !seed(c, c % I.pitch, c / I.pitch);
-            }
+            nl = 0;
+            for (int q = 0; q < nbulk; ++q) seeds[nl++] = y.bulkbad[q];
+            sort_int(seeds, nl);
+            if (lane == 0)
+                for (int q = 0; q < nl && ns + q < MIXCAP; ++q) nxt[ns + q] = seeds[q];
+            ns += nl;
+            __syncwarp();
         }
-        if (overflow) { y.err |= ERR_UNSTABLE | ERR_MIX_CAP; return; }
+        // more seeds than nodes fit: the merge would overflow
+        overflow = ns > MIXCAP || !seed_all(ns);
+        if (overflow) {
+            if (lane == 0) y.err |= ERR_UNSTABLE | ERR_MIX_CAP;
+            return;
+        }
+        __syncwarp();
         // nodes in cell order with the cell of their cluster root, so that the
         // cluster sums run in a fixed order
-        for (int k = 0; k < nn; ++k) par[k] = root(k);        // node indices of the roots
-        for (int k = 0; k < nn; ++k) par[k] = node[par[k]];   // then their cells
-        for (int x = 1; x < nn; ++x) {
-            const int c = node[x], r = par[x];
-            int z = x;
-            while (z > 0 && node[z - 1] > c) { node[z] = node[z - 1]; par[z] = par[z - 1]; --z; }
-            node[z] = c;
-            par[z] = r;
+        for (int k = lane; k < nn; k += 32) nxt[k] = node[root(k)];
+        __syncwarp();
+        for (int k = lane; k < nn; k += 32) par[k] = nxt[k];
+        __syncwarp();
+        if (lane == 0) {
+            for (int x = 1; x < nn; ++x) {
+                const int c = node[x], r = par[x];
+                int z = x;
+                while (z > 0 && node[z - 1] > c) { node[z] = node[z - 1]; par[z] = par[z - 1]; --z; }
+                node[z] = c;
+                par[z] = r;
+            }
         }
+        __syncwarp();
         for (int k = 0; k < nn; ++k) {
             const int rc = par[k];
             if (node[k] != rc) continue;   // one pass per cluster, at its root cell
             double tot[MAXC] = {0, 0, 0, 0}, vol = 0.0;
-            for (int m = 0; m < nn; ++m) {
-                if (par[m] != rc) continue;
-                const int c = node[m];
-                if (I.cls[c] & CLS_BAND) {
-                    const BandRec &bb = R[I.rec[c]];
-                    vol += bb.aB;
-                    for (int q = 0; q < I.nc; ++q) tot[q] += bb.C2[q];
-                } else {
-                    vol += 1.0;
-                    for (int q = 0; q < I.nc; ++q) tot[q] += (double)Qo[q * plane + c];
+            for (int m0 = 0; m0 < nn; m0 += 32) {
+                const int m = m0 + lane;
+                const bool mem = m < nn && par[m] == rc;
+                unsigned mask = __ballot_sync(0xffffffffu, mem);
+                if (!mask) continue;
+                double cv[MAXC] = {0, 0, 0, 0}, vv = 0.0;
+                if (mem) {
+                    const int c = node[m];
+                    if (I.cls[c] & CLS_BAND) {
+                        const BandRec &bb = R[I.rec[c]];
+                        vv = bb.aB;
+                        for (int q = 0; q < I.nc; ++q) cv[q] = bb.C2[q];
+                    } else {
+                        vv = 1.0;
+                        for (int q = 0; q < I.nc; ++q) cv[q] = (double)Qo[q * plane + c];
+                    }
+                }
+                // members in cell order, the same additions on every lane
+                for (; mask; mask &= mask - 1) {
+                    const int b = __ffs(mask) - 1;
+                    vol += __shfl_sync(0xffffffffu, vv, b);
+                    for (int q = 0; q < MAXC; ++q) tot[q] += __shfl_sync(0xffffffffu, cv[q], b);
                 }
             }
-            for (int m = 0; m < nn; ++m) {
+            for (int m = lane; m < nn; m += 32) {
                 if (par[m] != rc) continue;
                 const int c = node[m];
                 if (I.cls[c] & CLS_BAND) {
@@ -2068,15 +2140,23 @@ __global__ void k_mix(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y, B
                     for (int q = 0; q < I.nc; ++q) Qo[q * plane + c] = (T)(tot[q] / vol);
                 }
             }
+            __syncwarp();
         }
-        y.mixed += nn;
+        if (lane == 0) y.mixed += nn;
+        // cells still non-physical, in cell order
         nnext = 0;
-        for (int k = 0; k < nn; ++k)
-            if (!physical(node[k])) next[nnext++] = node[k];
+        for (int k0 = 0; k0 < nn; k0 += 32) {
+            const int k = k0 + lane;
+            const bool bad = k < nn && !physical(node[k]);
+            const unsigned m = __ballot_sync(0xffffffffu, bad);
+            if (bad) nxt[nnext + __popc(m & ((1u << lane) - 1u))] = node[k];
+            nnext += __popc(m);
+        }
+        __syncwarp();
         if (nnext == 0) return;
     }
     // still non-physical after the last merge
-    y.err |= ERR_UNSTABLE | ERR_MIX_BULK;
+    if (lane == 0) y.err |= ERR_UNSTABLE | ERR_MIX_BULK;
 }
 
 // ---------------------------------------------------------------------------
@@ -2235,9 +2315,8 @@ __global__ void __launch_bounds__(STATE_THREADS) k_read_state(const InstDesc *__
 // stage 0 first counts the sweep's used band records (boff, n_inst + 1
 // ints); the record kernels then run grid-stride over those only
 template <class T>
-void launch_band_stage(int stage, const InstDesc *D, InstDyn *Y, BandRec *R, const double *bnd, int *scratch,
-                       int *boff, int n_inst, int total_rec, int dir, int src, int dst, int qn, int sidx, int last,
-                       cudaStream_t st) {
+void launch_band_stage(int stage, const InstDesc *D, InstDyn *Y, BandRec *R, const double *bnd, int *boff, int n_inst,
+                       int total_rec, int dir, int src, int dst, int qn, int sidx, int last, cudaStream_t st) {
     constexpr int BAND_BLOCKS = 1216;   // 8 CTAs of 128 threads per SM
     const int blocks = std::min((total_rec + 127) / 128, BAND_BLOCKS);
     switch (stage) {
@@ -2248,7 +2327,7 @@ void launch_band_stage(int stage, const InstDesc *D, InstDyn *Y, BandRec *R, con
             break;
         case 1: if (blocks) k_band_sweep<T><<<blocks, 128, 0, st>>>(D, Y, R, bnd, boff, n_inst, dir, src); break;
         case 2: if (blocks) k_events<T><<<blocks, 128, 0, st>>>(D, Y, R, boff, n_inst); break;
-        case 3: k_mix<T><<<(n_inst + 63) / 64, 64, 0, st>>>(D, Y, R, scratch, n_inst, dst, sidx); break;
+        case 3: k_mix<T><<<n_inst, 32, 0, st>>>(D, Y, R, n_inst, dst, sidx); break;
         case 4: if (blocks) k_finalize<T><<<blocks, 128, 0, st>>>(D, Y, R, boff, n_inst, dst, last); break;
     }
 }
@@ -2335,7 +2414,7 @@ void launch_read_state(const InstDesc *D, double *const *ptrs, double *p1, int i
 }
 
 #define MB_INST(T)                                                                                                \
-    template void launch_band_stage<T>(int, const InstDesc *, InstDyn *, BandRec *, const double *, int *, int *,   \
+    template void launch_band_stage<T>(int, const InstDesc *, InstDyn *, BandRec *, const double *, int *,          \
                                        int, int, int, int, int, int, int, int, cudaStream_t);                     \
     template void launch_bulk<T>(int, int, const InstDesc *, InstDyn *, const BandRec *, int, int, int, int, int,  \
                                  int, int, DeferList, int, cudaStream_t);                                               \
