@@ -2235,8 +2235,15 @@ constexpr int STATE_ROWS = 8;
 constexpr int STATE_THREADS = 128;
 
 // Sources: srcs[blockIdx.y] (srcs != nullptr; a null entry skips that
-// instance) or src1.  Wave speeds in T, the precision of the state (the
-// speeds of later steps come from the update kernels, also in T).
+// instance) or src1.  The first step's wave speeds are the FP64 maxima over
+// the stored (T-rounded) states.  With T = float each cell's speeds are
+// first formed in FP32; a cell goes through the FP64 formula only if one of
+// its FP32 speeds comes within 1e-4 of the largest the thread has seen, or
+// if its pressure is small against its energy (p <= E/20, where the FP32
+// error could exceed 1e-5), and its state differs from the last state the
+// thread took through the FP64 formula.  Elsewhere the FP32 speeds are
+// within 1e-5 of the FP64 ones, so no skipped cell can hold the maximum,
+// and the result is that of the FP64 formula over every cell.
 template <class T>
 __global__ void __launch_bounds__(STATE_THREADS) k_write_state(const InstDesc *__restrict__ D,
                                                                InstDyn *__restrict__ Y,
@@ -2251,8 +2258,10 @@ __global__ void __launch_bounds__(STATE_THREADS) k_write_state(const InstDesc *_
     const size_t n = (size_t)I.nx * I.ny;
     const size_t plane = (size_t)I.pitch * I.ny;
     T *Q = bufw<T>(I, b);
-    const T g = (T)I.gamma;
-    T s0 = T(0), s1 = T(0);
+    const float gf = (float)I.gamma;
+    float m0 = -1.0f, m1 = -1.0f;   // FP32 maxima of the trusted cells (T = float)
+    unsigned lq[4] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu};   // last state taken in FP64
+    double s0 = 0.0, s1 = 0.0;
     bool fluid = false;
     const int j1 = min(j0 + STATE_ROWS, I.ny);
     for (int j = j0; j < j1; ++j) {
@@ -2268,10 +2277,32 @@ __global__ void __launch_bounds__(STATE_THREADS) k_write_state(const InstDesc *_
             if (solid) continue;
             fluid = true;
             if (I.eq == 0) {
-                T p = (g - T(1)) * (q[3] - T(0.5) * (q[1] * q[1] + q[2] * q[2]) / q[0]);
-                T c2 = tsqrt(g * p / q[0]);
-                s0 = fmax(s0, fabs(q[1] / q[0]) + c2);
-                s1 = fmax(s1, fabs(q[2] / q[0]) + c2);
+                bool exact = true;
+                if (sizeof(T) == 4) {
+                    const float r = (float)q[0], u = (float)q[1], v = (float)q[2], E = (float)q[3];
+                    const unsigned b[4] = {__float_as_uint(r), __float_as_uint(u), __float_as_uint(v),
+                                           __float_as_uint(E)};
+                    const bool same = b[0] == lq[0] && b[1] == lq[1] && b[2] == lq[2] && b[3] == lq[3];
+                    const float pf = (gf - 1.0f) * (E - 0.5f * (u * u + v * v) / r);
+                    const bool trusted = r > 0.0f && pf > 0.05f * E && isfinite(pf) && isfinite(u) && isfinite(v);
+                    if (trusted) {
+                        const float cf = sqrtf(gf * pf / r);
+                        const float f0 = fabsf(u / r) + cf, f1 = fabsf(v / r) + cf;
+                        exact = f0 >= m0 * (1.0f - 1e-4f) || f1 >= m1 * (1.0f - 1e-4f);
+                        m0 = fmaxf(m0, f0);
+                        m1 = fmaxf(m1, f1);
+                    }
+                    exact = exact && !same;
+                    if (exact)
+                        for (int k = 0; k < 4; ++k) lq[k] = b[k];
+                }
+                if (exact) {
+                    const double d0 = (double)q[0], d1 = (double)q[1], d2 = (double)q[2], d3 = (double)q[3];
+                    const double p = (I.gamma - 1.0) * (d3 - 0.5 * (d1 * d1 + d2 * d2) / d0);
+                    const double c2 = sqrt(I.gamma * p / d0);
+                    s0 = fmax(s0, fabs(d1 / d0) + c2);
+                    s1 = fmax(s1, fabs(d2 / d0) + c2);
+                }
             }
         }
     }
@@ -2281,9 +2312,9 @@ __global__ void __launch_bounds__(STATE_THREADS) k_write_state(const InstDesc *_
     }
     fluid = __any_sync(0xffffffffu, fluid);
     if ((threadIdx.x & 31) == 0 && fluid) {
-        // advection: the constant speeds, exactly
-        atomic_max_pos(&Y[inst].S[0], I.eq == 0 ? (double)s0 : fabs(I.adv[0]));
-        atomic_max_pos(&Y[inst].S[1], I.eq == 0 ? (double)s1 : fabs(I.adv[1]));
+        // advection: the constant speeds
+        atomic_max_pos(&Y[inst].S[0], I.eq == 0 ? s0 : fabs(I.adv[0]));
+        atomic_max_pos(&Y[inst].S[1], I.eq == 0 ? s1 : fabs(I.adv[1]));
     }
 }
 
