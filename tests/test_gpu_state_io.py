@@ -100,3 +100,19 @@ def test_write_read_round_trip(mb, prec):
         assert np.all(np.isnan(out[k][:, solid])), p.name
         assert np.array_equal(out[k][:, ~solid], want[:, ~solid]), p.name
     sim.close()
+
+
+def test_first_step_dt_is_the_fp64_one(mb):
+    """The first step's wave speeds of a written FP32 state are the FP64
+    maxima over the stored states, screened in FP32 without changing the
+    result: with initial states that FP32 holds exactly, the FP32 and FP64
+    batches take the same first CFL step, bit for bit."""
+    probs = _mix()
+    for p in probs:
+        p.Q0 = np.asarray(p.Q0, dtype=np.float32).astype(np.float64)
+    dts = []
+    for prec in (mb.FP32, mb.FP64):
+        sim = mb.Sim(probs, prec)
+        dts.append(sim.step(0.0, report=True))
+        sim.close()
+    assert np.array_equal(dts[0], dts[1]), (dts[0], dts[1])
