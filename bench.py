@@ -131,6 +131,31 @@ def bulk_traffic(precision, wname):
         return None
 
 
+# FP32 lane operations per clock: 152 SMs x 128 FP32 lanes x 2.07 GHz
+FP32_LANE_OPS_PEAK = 152 * 128 * 2.07e9
+
+
+def bulk_alu(precision, wname):
+    """FP32 lane operations per cell-sweep of the bulk update (mean over the
+    x and y sweeps) from the ncu instruction counts summarised in
+    profiles/bulk_alu.json, or None under the same conditions as
+    bulk_traffic."""
+    import hashlib
+    prof = os.path.join(ROOT, "profiles", "bulk_alu.json")
+    try:
+        d = json.load(open(prof))
+        if d["workload"] != wname or d["precision"] != precision:
+            return None
+        for f, sha in d["sources_sha256"].items():
+            with open(os.path.join(ROOT, "paper_1711_11361_gb300", "csrc", f), "rb") as fh:
+                if hashlib.sha256(fh.read()).hexdigest() != sha:
+                    return None
+        v = list(d["fp32_lane_ops_per_cell"].values())
+        return float(sum(v) / len(v))
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def accuracy_leg(mb, probs, steps=20):
     """FP32 batch against the FP64 GPU path (itself held to the oracle at
     1e-12 per step by the parity tests) on the same instances, the same
@@ -490,6 +515,7 @@ def main():
     achieved = cells * bpc / avg_bulk_s / 1e9
     peak, peak_kind = measured_peaks()
     traffic = bulk_traffic(args.precision, wname)
+    ops_per_cell = bulk_alu(args.precision, wname)
 
     # end to end through the C ABI with pinned host buffers
     pinned_in = [torch.empty((p.nc, p.ny, p.nx), dtype=torch.float64).pin_memory() for p in probs]
@@ -538,6 +564,12 @@ def main():
                      "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "peak_kind": peak_kind, "bytes_per_cell": bpc, "avg_launch_ms": avg_bulk_s * 1e3,
                      "launches_timed": launches},
+        # the same kernels against the FP32 lanes (context: they are issue-bound)
+        "alu": None if ops_per_cell is None else {
+            "fp32_lane_ops_per_cell": ops_per_cell, "achieved": ops_per_cell * cells / avg_bulk_s / 1e12,
+            "peak": FP32_LANE_OPS_PEAK / 1e12, "unit": "T FP32 lane-ops/s",
+            "frac": ops_per_cell * cells / avg_bulk_s / FP32_LANE_OPS_PEAK,
+            "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz"},
         "clocks": summarize_clocks(samples, local),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d,
                 "steps": e2e_steps},
