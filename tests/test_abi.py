@@ -14,7 +14,7 @@ def declared():
     return sorted(set(re.findall(r"^\s*(?:mb_status|void|int|size_t|const char \*)\s*(mb_\w+)\s*\(", src, re.M)))
 
 
-def test_header_declares_the_north_star_calls():
+def test_header_declares_the_sweep_calls():
     names = declared()
     for n in ("mb_create", "mb_step", "mb_sweep", "mb_read_state", "mb_write_state", "mb_destroy"):
         assert n in names
