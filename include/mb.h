@@ -129,21 +129,28 @@ mb_status mb_write_state(mb_sim *sim, int inst, const double *Q, double t);
  * any kernel has flagged for this instance since the last write. */
 mb_status mb_read_state(mb_sim *sim, int inst, double *Q, double *alpha, double *clock);
 
-/* mb_write_state of every instance in one call: Q[k] is instance k's host
- * array (layout as above), t[k] its time (t NULL: all 0).  Same result as n
- * mb_write_state calls.  The arrays are copied into a device buffer that
- * holds every instance's FP64 state (allocated on the first batched call)
+/* mb_write_state of every instance in one call (the initial data of the
+ * method's update, Sec. II): Q is an array of n host pointers, Q[k] instance
+ * k's state (nc*nx*ny doubles, layout as above, caller-owned); t (optional,
+ * n doubles) their times, all 0 when NULL.  Same result as n mb_write_state
+ * calls.  The arrays are copied into a device buffer that holds every
+ * instance's FP64 state (library-owned, allocated on the first batched call)
  * while the classification of the new poses runs beside the copies; arrays
  * in page-locked host memory (cudaHostAlloc, cudaMallocHost,
- * cudaHostRegister) copy at the full speed of the host link.
+ * cudaHostRegister) copy at the full speed of the host link.  Returns
+ * MB_E_INVAL (nothing written) if sim, Q or any Q[k] is NULL, MB_E_NOMEM if
+ * the buffer cannot be allocated, MB_E_CUDA on a failed copy or launch.
  * Synchronises: the arrays may be reused on return. */
 mb_status mb_write_states(mb_sim *sim, const double *const *Q, const double *t);
 
-/* mb_read_state of every instance in one call: Q[k] (NULL entries skipped)
- * receives instance k's state, clocks (optional, 4n doubles) the clocks
- * {t, X, Y, step}.  One conversion launch into the batch's device buffer,
- * then one copy per instance.  Synchronises; returns the first flagged
- * error in instance order. */
+/* mb_read_state of every instance in one call: Q is an array of n host
+ * pointers (caller-owned); Q[k] (NULL entries skipped) receives instance k's
+ * state (nc*nx*ny doubles, solid cells NaN), clocks (optional, 4n doubles)
+ * the clocks {t, X, Y, step} of each.  One conversion launch into the
+ * batch's device buffer, then one copy per instance.  Synchronises; returns
+ * MB_E_INVAL if sim or Q is NULL, MB_E_NOMEM / MB_E_CUDA as
+ * mb_write_states, else the first error a kernel has flagged, in instance
+ * order (the states are read either way). */
 mb_status mb_read_states(mb_sim *sim, double *const *Q, double *clocks);
 
 /* One time step of every instance: two sweeps, x then y on even steps and
