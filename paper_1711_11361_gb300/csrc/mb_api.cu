@@ -25,7 +25,7 @@ namespace mb {
 void geom_init();
 void launch_nodes(const InstDesc *, int, cudaStream_t);
 void launch_pose(const InstDesc *, InstDyn *, const double *, const double *, const unsigned char *, const int *,
-                 double *, double *, float *, int, int, int, int, double, cudaStream_t);
+                 double *, double *, float *, int, int, int, int, double, int *, cudaStream_t);
 void launch_geom(const InstDesc *, InstDyn *, const int *, const double *, const double *, const float *, const int *,
                  const unsigned char *, int, int, int, int, BandRec *, double *, cudaStream_t);
 void launch_classify(const InstDesc *, InstDyn *, const double *, const double *, const unsigned char *, double *,
@@ -600,10 +600,9 @@ static mb_status do_sweep(mb_sim *s, int dir, double dt) {
     qn = s->qn;
     const int last = s->sidx == 1;
     cudaStream_t st = s->stream;
-    // the sweep's count of deferred bulk cell pairs
-    cudaMemsetAsync(s->dcount, 0, sizeof(int), st);
+    // k_pose also empties the sweep's list of deferred bulk cell pairs
     launch_pose(s->dd, s->dy, s->vx, s->vy, s->vmov, s->vnext, s->px, s->py, s->ebox, s->total_v, s->n, dir, s->sidx,
-                dt, st);
+                dt, s->dcount, st);
     auto band = [&](int stage, cudaStream_t sx) {
         if (s->prec == MB_FP32)
             launch_band_stage<float>(stage, s->dd, s->dy, s->rec, s->bnd, s->boff, s->n, s->total_rec,

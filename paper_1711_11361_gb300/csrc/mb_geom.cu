@@ -86,8 +86,12 @@ __device__ __forceinline__ double dkey_inv(unsigned long long k) {
 __global__ void k_pose(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y, const double *__restrict__ vx,
                        const double *__restrict__ vy, const unsigned char *__restrict__ vmov,
                        const int *__restrict__ vnext, double *__restrict__ px, double *__restrict__ py,
-                       float *__restrict__ ebox, int total_v, int dir, int sidx, double dt_host) {
+                       float *__restrict__ ebox, int total_v, int dir, int sidx, double dt_host,
+                       int *__restrict__ defer_count) {
     const int inst = blockIdx.x / POSE_PARTS, part = blockIdx.x % POSE_PARTS;
+    // the sweep's list of deferred bulk cell pairs starts empty (its readers
+    // of the sweep before have finished; its writers of this sweep follow)
+    if (blockIdx.x == 0 && threadIdx.x == 0 && defer_count) *defer_count = 0;
     const InstDesc &I = D[inst];
     InstDyn &y = Y[inst];
     __shared__ double sh[16];
@@ -1394,8 +1398,9 @@ void launch_nodes(const InstDesc *D, int n_inst, cudaStream_t st) {
 
 void launch_pose(const InstDesc *D, InstDyn *Y, const double *vx, const double *vy, const unsigned char *vmov,
                  const int *vnext, double *px, double *py, float *ebox, int total_v, int n_inst, int dir, int sidx,
-                 double dt, cudaStream_t st) {
-    k_pose<<<n_inst * POSE_PARTS, 256, 0, st>>>(D, Y, vx, vy, vmov, vnext, px, py, ebox, total_v, dir, sidx, dt);
+                 double dt, int *defer_count, cudaStream_t st) {
+    k_pose<<<n_inst * POSE_PARTS, 256, 0, st>>>(D, Y, vx, vy, vmov, vnext, px, py, ebox, total_v, dir, sidx, dt,
+                                                 defer_count);
 }
 
 void launch_geom(const InstDesc *D, InstDyn *Y, const int *ginst, const double *px, const double *py, const float *ebox,
