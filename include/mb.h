@@ -280,16 +280,27 @@ const char *mb_server_request_error(const mb_server *srv, int id);
  *
  * Allocates nothing: its scratch is a fixed 0.7 MB device array inside the
  * library, held by every GPU that loads it until the process exits.  Limits:
- * at most 16384 polygon vertices, nx and ny at most 8192; larger requests
- * return MB_E_INVAL with a message from mb_noalloc_last_error().  The first
- * call on each device looks up that array's device address and should come
- * before any stream capture.  All calls share the array, so calls that
- * overlap on the GPU (for example on two streams) race: serialise them. */
+ * at most 16384 polygon vertices, nx and ny at most 8192 (larger requests
+ * return MB_E_INVAL); per grid column at most 192 polygon edges meeting the
+ * column and at most 32 edges crossing each of its two grid lines (a body
+ * sampled more finely than that on a coarse grid returns MB_E_CAPACITY, and
+ * the outputs are then not valid).  Polygons need at least 3 vertices and
+ * the domain a positive extent (MB_E_INVAL otherwise); every argument is
+ * checked before the first CUDA call.  mb_noalloc_last_error() gives the
+ * message of the calling host thread's last failure.
+ *
+ * The call blocks the host: it synchronises `stream` once its copies into
+ * the scratch array are queued, and again after the kernels to read their
+ * error word back.  The first call on each device looks up the scratch
+ * array's device address (once, safe from several host threads) and should
+ * come before any stream capture.  All calls share the array, so calls that
+ * overlap on the GPU (for example from two host threads on two streams of one
+ * device) race: serialise them. */
 mb_status mb_cut_cells_noalloc(const mb_grid *grid, const mb_body *body, const mb_motion *motion,
                                double X, double Y, double theta, double *alpha_dev,
                                unsigned char *class_dev, void *stream);
 
-/* Text of the last error of mb_cut_cells_noalloc. */
+/* Text of the calling host thread's last error of mb_cut_cells_noalloc. */
 const char *mb_noalloc_last_error(void);
 
 #ifdef __cplusplus

@@ -14,6 +14,7 @@
 #include "mb_internal.cuh"
 
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1458,9 +1459,13 @@ constexpr size_t NA_BYTES = NA_OFF_MOV + (size_t)NA_MAX_V;   // about 0.7 MB
 static __device__ __align__(256) unsigned char g_na_scratch[NA_BYTES];
 
 // host-side stand-in `g_na_scratch` is not a device address: kernels get the
-// address that cudaGetSymbolAddress returns for the current device
-static void *g_na_addr[64];
-static bool g_na_ready[64];
+// address that cudaGetSymbolAddress returns for the current device, looked up
+// once per device (std::call_once, so concurrent first calls from several
+// host threads are safe)
+constexpr int NA_MAX_DEV = 64;
+static void *g_na_addr[NA_MAX_DEV];
+static cudaError_t g_na_setup_err[NA_MAX_DEV];
+static std::once_flag g_na_once[NA_MAX_DEV];
 
 // variant of k_classify writing unpitched outputs and no record map
 __global__ void __launch_bounds__(GEOM_WARPS * 32) k_classify_na(const InstDesc *__restrict__ D,
@@ -1504,14 +1509,20 @@ __global__ void __launch_bounds__(GEOM_WARPS * 32) k_classify_na(const InstDesc 
 
 }  // namespace mb
 
-static std::string g_na_error;
+// per host thread, like the scratch vectors of the call below
+static thread_local std::string g_na_error;
 
 extern "C" mb_status mb_cut_cells_noalloc(const mb_grid *grid, const mb_body *body, const mb_motion *motion,
                                           double X, double Y, double theta, double *alpha_dev,
                                           unsigned char *class_dev, void *stream) {
     using namespace mb;
+    // every argument check comes before the first CUDA call
     if (!grid || !body || !motion || !alpha_dev || !class_dev) {
         g_na_error = "mb_cut_cells_noalloc: NULL argument";
+        return MB_E_INVAL;
+    }
+    if (body->npoly < 0 || (body->npoly > 0 && (!body->poly_start || !body->poly_moving || !body->vx || !body->vy))) {
+        g_na_error = "mb_cut_cells_noalloc: body arrays missing";
         return MB_E_INVAL;
     }
     const int nv = body->npoly > 0 ? body->poly_start[body->npoly] : 0;
@@ -1527,31 +1538,40 @@ extern "C" mb_status mb_cut_cells_noalloc(const mb_grid *grid, const mb_body *bo
         g_na_error = "mb_cut_cells_noalloc: empty domain";
         return MB_E_INVAL;
     }
+    if (body->npoly > 0 && body->poly_start[0] != 0) {
+        g_na_error = "mb_cut_cells_noalloc: poly_start[0] must be 0";
+        return MB_E_INVAL;
+    }
+    for (int p = 0; p < body->npoly; ++p) {
+        if (body->poly_start[p + 1] - body->poly_start[p] < 3) {
+            g_na_error = "mb_cut_cells_noalloc: polygon with fewer than 3 vertices";
+            return MB_E_INVAL;
+        }
+    }
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= 64) {
+    if (e != cudaSuccess || dev < 0 || dev >= NA_MAX_DEV) {
         g_na_error = std::string("mb_cut_cells_noalloc: no current device: ") + cudaGetErrorString(e);
         return MB_E_CUDA;
     }
+    cudaStream_t st = (cudaStream_t)stream;
     // one-time set-up on this device (the first call per device does it, and
     // should therefore come before any stream capture)
-    if (!g_na_ready[dev]) {
+    std::call_once(g_na_once[dev], [dev]() {
         void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_na_scratch);
-        if (e != cudaSuccess || !p) {
-            g_na_error = std::string("mb_cut_cells_noalloc: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e);
-            return MB_E_CUDA;
-        }
-        e = cudaFuncSetAttribute(k_classify_na, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)geom_smem());
-        if (e != cudaSuccess) {
-            g_na_error = std::string("mb_cut_cells_noalloc: kernel attribute: ") + cudaGetErrorString(e);
-            return MB_E_CUDA;
-        }
-        g_na_addr[dev] = p;
-        g_na_ready[dev] = true;
+        cudaError_t r = cudaGetSymbolAddress(&p, g_na_scratch);
+        if (r == cudaSuccess && !p) r = cudaErrorInvalidSymbol;
+        if (r == cudaSuccess)
+            r = cudaFuncSetAttribute(k_classify_na, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)geom_smem());
+        g_na_addr[dev] = r == cudaSuccess ? p : nullptr;
+        g_na_setup_err[dev] = r;
+    });
+    if (g_na_setup_err[dev] != cudaSuccess) {
+        g_na_error = std::string("mb_cut_cells_noalloc: set-up of the scratch array failed: ") +
+                     cudaGetErrorString(g_na_setup_err[dev]);
+        return MB_E_CUDA;
     }
     unsigned char *base = (unsigned char *)g_na_addr[dev];
-    cudaStream_t st = (cudaStream_t)stream;
     // descriptor of a one-instance, unpitched grid
     InstDesc I;
     memset(&I, 0, sizeof(I));
@@ -1576,10 +1596,6 @@ extern "C" mb_status mb_cut_cells_noalloc(const mb_grid *grid, const mb_body *bo
     hmov.assign(nv > 0 ? nv : 1, 0);
     for (int p = 0; p < body->npoly; ++p) {
         const int a = body->poly_start[p], z = body->poly_start[p + 1];
-        if (z - a < 3) {
-            g_na_error = "mb_cut_cells_noalloc: polygon with fewer than 3 vertices";
-            return MB_E_INVAL;
-        }
         for (int v = a; v < z; ++v) {
             hnext[v] = v + 1 < z ? v + 1 : a;
             hmov[v] = body->poly_moving[p] ? 1 : 0;
@@ -1611,6 +1627,25 @@ extern "C" mb_status mb_cut_cells_noalloc(const mb_grid *grid, const mb_body *bo
     e = cudaGetLastError();
     if (e != cudaSuccess) {
         g_na_error = std::string("mb_cut_cells_noalloc: launch failed: ") + cudaGetErrorString(e);
+        return MB_E_CUDA;
+    }
+    // the kernels' error word (a column whose edge or crossing lists would
+    // exceed their fixed capacity clips them and sets it): read back into
+    // host memory, so that truncated lists never pass as a result
+    int herr = 0;
+    e = cudaMemcpyAsync(&herr, &Yd->err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        g_na_error = std::string("mb_cut_cells_noalloc: ") + cudaGetErrorString(e);
+        return MB_E_CUDA;
+    }
+    if (herr & ERR_EDGE_CAP) {
+        g_na_error = "mb_cut_cells_noalloc: a grid column meets more than 192 polygon edges, or one of its grid "
+                     "lines more than 32 edges; the outputs are not valid (use a finer grid or fewer vertices)";
+        return MB_E_CAPACITY;
+    }
+    if (herr) {
+        g_na_error = "mb_cut_cells_noalloc: device error word " + std::to_string(herr);
         return MB_E_CUDA;
     }
     return MB_OK;

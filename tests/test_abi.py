@@ -31,3 +31,43 @@ def test_library_exports_every_declared_symbol():
 def test_binding_lists_every_export():
     from paper_1711_11361_gb300 import mb
     assert sorted(mb.EXPORTS) == declared()
+
+
+def _noalloc_call(prob):
+    """mb_cut_cells_noalloc on dummy output pointers: every case below fails
+    its argument checks, which come before the first CUDA call, so no device
+    is touched (and none is needed)."""
+    import numpy as np
+    from paper_1711_11361_gb300 import mb
+    out = np.zeros(8)
+    with pytest.raises(mb.MBError) as ei:
+        mb.cut_cells_noalloc(prob, 0.0, 0.0, 0.0, out.ctypes.data, out.ctypes.data)
+    return ei.value
+
+
+def _square(n=4):
+    import numpy as np
+    t = np.linspace(0.0, 2.0 * np.pi, n, endpoint=False)
+    return np.stack([0.5 + 0.2 * np.cos(t), 0.5 + 0.2 * np.sin(t)], axis=1)
+
+
+def test_noalloc_rejects_too_many_vertices():
+    from paper_1711_11361_gb300 import inputs, mb
+    prob = inputs.Problem("many", 16, 16, 0.0, 0.0, 1.0, 1.0, polygons=[_square(16385)], moving=[1])
+    e = _noalloc_call(prob)
+    assert e.code == mb.MB_E_INVAL and "16384" in str(e)
+
+
+def test_noalloc_rejects_degenerate_polygon():
+    from paper_1711_11361_gb300 import inputs, mb
+    prob = inputs.Problem("deg", 16, 16, 0.0, 0.0, 1.0, 1.0, polygons=[_square(2)], moving=[1])
+    e = _noalloc_call(prob)
+    assert e.code == mb.MB_E_INVAL and "fewer than 3" in str(e)
+
+
+@pytest.mark.parametrize("x1,y1", [(0.0, 1.0), (1.0, 0.0), (-1.0, 1.0)])
+def test_noalloc_rejects_empty_domain(x1, y1):
+    from paper_1711_11361_gb300 import inputs, mb
+    prob = inputs.Problem("empty", 16, 16, 0.0, 0.0, x1, y1, polygons=[_square(8)], moving=[1])
+    e = _noalloc_call(prob)
+    assert e.code == mb.MB_E_INVAL and "empty domain" in str(e)
