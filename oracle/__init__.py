@@ -88,6 +88,12 @@ def _load():
                                       ctypes.c_double, D, D, D, D]
         lib.or_status.argtypes = [P]
         lib.or_last_sweep.argtypes = [P, D]
+        lib.or_stab_face.argtypes = [ctypes.c_int, ctypes.c_double, D, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                     D, ctypes.c_int, ctypes.c_double, ctypes.c_double, D, D]
+        lib.or_cover_uncover.argtypes = [ctypes.c_int] * 6 + [D, D, D, D, B]
+        lib.or_safeguard.argtypes = [ctypes.c_int] * 4 + [ctypes.c_double, D, B, D]
+        lib.or_last_faces.argtypes = [P, D]
+        lib.or_last_wall.argtypes = [P, D]
         _lib = lib
     return _lib
 
@@ -114,6 +120,56 @@ def wall_state(gamma: float, q, n, w):
     lib.or_wall_state(gamma, _dp(q), float(n[0]), float(n[1]), float(w[0]), float(w[1]),
                       *[ctypes.byref(o) for o in out])
     return tuple(o.value for o in out)
+
+
+def stab_face(bf, F, left=None, right=None):
+    """Stabilised flux (times the face aperture bf) of one face with standard
+    flux F.  left / right: None, or (bfar, d, FB) of a neighbour with wall
+    data: the aperture of its far face, its shielded distance and its
+    boundary flux."""
+    lib = _load()
+    F = np.ascontiguousarray(F, dtype=np.float64)
+    nc = F.size
+    z = np.zeros(nc)
+    bl, dl, fbl = left if left is not None else (0.0, 0.0, z)
+    br, dr, fbr = right if right is not None else (0.0, 0.0, z)
+    fbl = np.ascontiguousarray(fbl, dtype=np.float64)
+    fbr = np.ascontiguousarray(fbr, dtype=np.float64)
+    out = np.zeros(nc)
+    lib.or_stab_face(nc, bf, _dp(F), 1 if left is not None else 0, bl, dl, _dp(fbl),
+                     1 if right is not None else 0, br, dr, _dp(fbr), _dp(out))
+    return out
+
+
+def cover_uncover(alphaA, alphaB, C, mode=UNCOVER_DONOR, periodic=(False, False)):
+    """Covering / uncovering redistribution of the contents C (nc, ny, nx)
+    between the poses with volume fractions alphaA and alphaB (ny, nx);
+    returns (new contents, status, updated flags)."""
+    lib = _load()
+    aA = np.ascontiguousarray(alphaA, dtype=np.float64)
+    aB = np.ascontiguousarray(alphaB, dtype=np.float64)
+    C = np.ascontiguousarray(C, dtype=np.float64)
+    if C.ndim == 2:
+        C = C[None]
+    nc, ny, nx = C.shape
+    Cn = np.empty_like(C)
+    upd = np.zeros((ny, nx), dtype=np.uint8)
+    r = lib.or_cover_uncover(nx, ny, int(periodic[0]), int(periodic[1]), nc, mode, _dp(aA), _dp(aB), _dp(C),
+                             _dp(Cn), upd.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)))
+    return Cn, r, upd
+
+
+def safeguard(alphaB, C, updated=None, gamma=1.4, periodic=(False, False)):
+    """Positivity safeguard on Euler contents C (4, ny, nx); returns (merged
+    contents, cells merged)."""
+    lib = _load()
+    aB = np.ascontiguousarray(alphaB, dtype=np.float64)
+    Cn = np.array(C, dtype=np.float64, order="C", copy=True)
+    _, ny, nx = Cn.shape
+    upd = np.ascontiguousarray(np.ones((ny, nx), dtype=np.uint8) if updated is None else updated, dtype=np.uint8)
+    m = lib.or_safeguard(nx, ny, int(periodic[0]), int(periodic[1]), gamma, _dp(aB),
+                         upd.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)), _dp(Cn))
+    return Cn, m
 
 
 class Oracle:
@@ -202,6 +258,22 @@ class Oracle:
         w = np.zeros(4)
         m = self._lib.or_last_sweep(self._h, _dp(w))
         return w[: self.nc], m
+
+    def last_faces(self):
+        """(direction, time-averaged apertures of the last sweep's faces)."""
+        nx, ny = self.nx, self.ny
+        buf = np.zeros(max((nx + 1) * ny, nx * (ny + 1)))
+        d = self._lib.or_last_faces(self._h, _dp(buf))
+        if d < 0:
+            return d, None
+        return d, (buf[: (nx + 1) * ny].reshape(ny, nx + 1) if d == 0 else buf[: nx * (ny + 1)].reshape(ny + 1, nx))
+
+    def last_wall(self):
+        """Wall data of the last sweep per cell: dict of (ny, nx) arrays has,
+        d, nx, ny (normal), wx, wy (wall velocity at the mid pose)."""
+        out = np.zeros((self.ny, self.nx, 6))
+        self._lib.or_last_wall(self._h, _dp(out))
+        return {k: out[..., i] for i, k in enumerate(("has", "d", "n_x", "n_y", "wx", "wy"))}
 
     def cfl_dt(self) -> float:
         return self._lib.or_cfl_dt(self._h)

@@ -95,6 +95,11 @@ typedef struct {
     double *px, *py;        /* posed vertices (scratch) */
     double wall_last[4];    /* sum over cells of the last sweep's wall terms (content units) */
     int mixed_last;         /* cells merged by the positivity safeguard in the last sweep */
+    /* last sweep, kept for diagnostics: direction, time-averaged apertures
+     * of its faces, and per cell the wall data (has, d, n_x, n_y, w_x, w_y) */
+    int last_dir;
+    double *bt_last;
+    double *wall_cell;
 } or_sim;
 
 /* ------------------------------------------------------------------------ */
@@ -555,6 +560,12 @@ or_sim *or_create(const or_config *cfg) {
     s->Q = (double *)malloc(sizeof(double) * s->nc * cfg->nx * cfg->ny);
     s->Qn = (double *)malloc(sizeof(double) * s->nc * cfg->nx * cfg->ny);
     for (int k = 0; k < s->nc * cfg->nx * cfg->ny; ++k) s->Q[k] = s->Qn[k] = NAN;
+    {
+        int nfmax = (cfg->nx + 1) * cfg->ny > cfg->nx * (cfg->ny + 1) ? (cfg->nx + 1) * cfg->ny : cfg->nx * (cfg->ny + 1);
+        s->bt_last = (double *)calloc((size_t)nfmax, sizeof(double));
+        s->wall_cell = (double *)calloc((size_t)6 * cfg->nx * cfg->ny, sizeof(double));
+        s->last_dir = -1;
+    }
     s->rmax = 0.0;
     for (int p = 0; p < np; ++p) {
         if (!s->pmoving[p]) continue;
@@ -569,7 +580,7 @@ or_sim *or_create(const or_config *cfg) {
 void or_destroy(or_sim *s) {
     if (!s) return;
     free(s->pstart); free(s->pmoving); free(s->vx); free(s->vy); free(s->px); free(s->py);
-    free(s->Q); free(s->Qn); free(s);
+    free(s->Q); free(s->Qn); free(s->bt_last); free(s->wall_cell); free(s);
 }
 
 int or_num_components(const or_sim *s) { return s->nc; }
@@ -672,6 +683,189 @@ typedef struct {
 
 static int wrapi(int k, int n) { k %= n; return k < 0 ? k + n : k; }
 
+/* Stabilised flux of one face (eqs. Klein2DtotalfluxaMethod2,
+ * Klein2shieldedFluxMethod2), times its time-averaged aperture bf:
+ *   bf F2D = (bf - sL - sR) F + sR [FB_R + d_R (F - FB_R)] + sL [FB_L + d_L (F - FB_L)],
+ * where the shielded part attached to the face by a neighbour with wall data
+ * is s = max(0, bf - bfar), bfar the aperture of that neighbour's far face.
+ * When both neighbours shield the face and sL + sR > bf, both parts are
+ * scaled by bf / (sL + sR) (a reading: the paper treats one side only).
+ * wL / wR are NULL when that neighbour has no wall data. */
+static void stab_face(int nc, double bf, const double *F, const wall_t *wL, double bfarL, const wall_t *wR,
+                      double bfarR, double *out) {
+    double sR = 0.0, sLv = 0.0;
+    if (wR) sR = dmax(0.0, bf - bfarR);
+    if (wL) sLv = dmax(0.0, bf - bfarL);
+    if (sR + sLv > bf) { double sc = bf / (sR + sLv); sR *= sc; sLv *= sc; }
+    for (int q = 0; q < nc; ++q) {
+        double v = (bf - sLv - sR) * F[q];
+        if (sR > 0.0) v += sR * (wR->FB[q] + wR->d * (F[q] - wR->FB[q]));
+        if (sLv > 0.0) v += sLv * (wL->FB[q] + wL->d * (F[q] - wL->FB[q]));
+        out[q] = v;
+    }
+}
+
+/* stab_face with plain arguments (has* = 0: that neighbour has no wall data) */
+void or_stab_face(int nc, double bf, const double *F, int hasL, double bfarL, double dL, const double *FBL,
+                  int hasR, double bfarR, double dR, const double *FBR, double *out) {
+    wall_t wl, wr;
+    memset(&wl, 0, sizeof(wl));
+    memset(&wr, 0, sizeof(wr));
+    wl.d = dL; wr.d = dR;
+    for (int q = 0; q < nc; ++q) { wl.FB[q] = hasL ? FBL[q] : 0.0; wr.FB[q] = hasR ? FBR[q] : 0.0; }
+    stab_face(nc, bf, F, hasL ? &wl : NULL, bfarL, hasR ? &wr : NULL, bfarR, out);
+}
+
+/* Covering / uncovering (Sec. II.C.5), applied simultaneously to all cells
+ * (Jacobi: every event reads the contents C from before any event, a
+ * reading; the paper is silent on simultaneous events).  C holds the new
+ * contents alpha^B Q' of the update; Cn receives the contents after the
+ * events.  A cell is covered when alphaA > 0 and alphaB = 0: its residual
+ * content (eq. massDeficitEquation: what the update left in it) goes to the
+ * fluid face neighbours at B in proportion to their volume fractions (eq.
+ * cutCellCoverDonation).  A cell is uncovered when alphaA = 0 and
+ * alphaB > 0; in donor mode it takes sigma * (sum of the donors' contents),
+ * sigma = alphaB / (alphaB + sum of the donors' alphaB) (eqs.
+ * volumeWeighting, cutCellInitialisation), and each donor loses sigma times
+ * its own content (eq. cutCellInitialisationDonorCellUpdate); donors are the
+ * fluid face neighbours at B that are not themselves uncovered.  With no
+ * such face neighbour the 8-neighbourhood is used (a reading).  updated[c]
+ * is set for donor-initialised cells.  Returns OR_E_UNSTABLE when a cell
+ * has no neighbour to exchange with. */
+static int cover_uncover(int nx, int ny, int perx, int pery, int nc, int mode, const double *alphaA,
+                         const double *alphaB, const double *C, double *Cn, unsigned char *updated) {
+    const int n = nx * ny;
+    int err = OR_OK;
+    memcpy(Cn, C, sizeof(double) * nc * n);
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            int c = j * nx + i;
+            int covered = alphaA[c] > 0.0 && alphaB[c] == 0.0;
+            int donor_unc = mode == OR_UNCOVER_DONOR && alphaA[c] == 0.0 && alphaB[c] > 0.0;
+            if (!covered && !donor_unc) continue;
+            /* neighbour sets: face neighbours first, then the 8-neighbourhood */
+            int nb[8], nnb = 0;
+            double asum = 0.0;
+            for (int pass = 0; pass < 2 && nnb == 0; ++pass) {
+                for (int dj = -1; dj <= 1; ++dj)
+                    for (int di = -1; di <= 1; ++di) {
+                        if (di == 0 && dj == 0) continue;
+                        if (pass == 0 && di != 0 && dj != 0) continue;
+                        int ii = i + di, jj = j + dj;
+                        if (perx) ii = wrapi(ii, nx);
+                        if (pery) jj = wrapi(jj, ny);
+                        if (ii < 0 || ii >= nx || jj < 0 || jj >= ny) continue;
+                        int cc = jj * nx + ii;
+                        if (!(alphaB[cc] > 0.0)) continue;
+                        if (mode == OR_UNCOVER_DONOR && alphaA[cc] == 0.0) continue; /* no content yet */
+                        nb[nnb++] = cc;
+                        asum += alphaB[cc];
+                    }
+            }
+            if (nnb == 0) { err = OR_E_UNSTABLE; continue; }
+            if (covered) {
+                for (int m = 0; m < nnb; ++m)
+                    for (int q = 0; q < nc; ++q) Cn[q * n + nb[m]] += alphaB[nb[m]] / asum * C[q * n + c];
+                for (int q = 0; q < nc; ++q) Cn[q * n + c] = 0.0;
+            } else {
+                double sigma = alphaB[c] / (alphaB[c] + asum);
+                for (int q = 0; q < nc; ++q) {
+                    double tot = 0.0;
+                    for (int m = 0; m < nnb; ++m) tot += C[q * n + nb[m]];
+                    Cn[q * n + c] = sigma * tot;
+                    for (int m = 0; m < nnb; ++m) Cn[q * n + nb[m]] -= sigma * C[q * n + nb[m]];
+                }
+                updated[c] = 1;
+            }
+        }
+    return err;
+}
+
+/* cover_uncover on caller arrays (updated may be NULL) */
+int or_cover_uncover(int nx, int ny, int perx, int pery, int nc, int mode, const double *alphaA,
+                     const double *alphaB, const double *C, double *Cn, unsigned char *updated) {
+    unsigned char *u = updated ? updated : (unsigned char *)calloc((size_t)nx * ny, 1);
+    int r = cover_uncover(nx, ny, perx, pery, nc, mode, alphaA, alphaB, C, Cn, u);
+    if (!updated) free(u);
+    return r;
+}
+
+/* Positivity safeguard (a reading; the paper gives none): a cell whose
+ * content is non-physical (rho <= 0, p <= 0 or non-finite, Euler only) is
+ * merged with its fluid, updated face neighbours; every connected cluster of
+ * such cells and their neighbours shares its total content in proportion to
+ * the volume fractions alphaB.  Cells still non-physical after a merge seed
+ * the next one, which reaches one layer of neighbours further, up to
+ * OR_MIX_LAYERS merges.  Exactly conservative.  Cn is updated in place;
+ * returns the number of cells merged (summed over the merges). */
+static int safeguard(int nx, int ny, int perx, int pery, double g, const double *alphaB,
+                     const unsigned char *updated, double *Cn) {
+    const int n = nx * ny;
+    int mixed = 0;
+    for (int layer = 0; layer < OR_MIX_LAYERS; ++layer) {
+        int *lab = (int *)malloc(sizeof(int) * n);
+        unsigned char *bad = (unsigned char *)calloc((size_t)n, 1);
+        int nbad = 0;
+        for (int c = 0; c < n; ++c) {
+            lab[c] = -1;
+            double aB = alphaB[c];
+            if (!(aB > 0.0) || !updated[c]) continue;
+            double q[4] = {Cn[c] / aB, Cn[n + c] / aB, Cn[2 * n + c] / aB, Cn[3 * n + c] / aB};
+            int b = !(q[0] > 0.0) || !(pressure(g, q) > 0.0);
+            for (int k = 0; k < 4; ++k) if (!isfinite(q[k])) b = 1;
+            if (b) { bad[c] = 1; nbad++; }
+        }
+        if (nbad) {
+            /* union-find over bad cells and their fluid face neighbours */
+            int *par = (int *)malloc(sizeof(int) * n);
+            for (int c = 0; c < n; ++c) par[c] = c;
+            for (int c = 0; c < n; ++c) {
+                if (!bad[c]) continue;
+                int i = c % nx, j = c / nx;
+                lab[c] = c;
+                int dd[4][2] = {{-1, 0}, {1, 0}, {0, -1}, {0, 1}};
+                for (int m = 0; m < 4; ++m) {
+                    int ii = i + dd[m][0], jj = j + dd[m][1];
+                    if (perx) ii = wrapi(ii, nx);
+                    if (pery) jj = wrapi(jj, ny);
+                    if (ii < 0 || ii >= nx || jj < 0 || jj >= ny) continue;
+                    int cc = jj * nx + ii;
+                    if (!(alphaB[cc] > 0.0) || !updated[cc]) continue;
+                    lab[cc] = cc;
+                    int ra = c, rb = cc;
+                    while (par[ra] != ra) ra = par[ra];
+                    while (par[rb] != rb) rb = par[rb];
+                    if (ra != rb) { if (ra < rb) par[rb] = ra; else par[ra] = rb; }
+                }
+            }
+            double *tot = (double *)calloc((size_t)n * 5, sizeof(double));
+            for (int c = 0; c < n; ++c) {
+                if (lab[c] < 0) continue;
+                int r = c; while (par[r] != r) r = par[r];
+                lab[c] = r;
+                tot[5 * r + 4] += alphaB[c];
+                for (int q = 0; q < 4; ++q) tot[5 * r + q] += Cn[q * n + c];
+            }
+            for (int c = 0; c < n; ++c) {
+                if (lab[c] < 0) continue;
+                mixed++;
+                int r = lab[c];
+                for (int q = 0; q < 4; ++q) Cn[q * n + c] = alphaB[c] * (tot[5 * r + q] / tot[5 * r + 4]);
+            }
+            free(tot); free(par);
+        }
+        free(lab); free(bad);
+        if (!nbad) break;
+    }
+    return mixed;
+}
+
+/* safeguard on caller arrays (Euler contents, 4 planes of nx*ny) */
+int or_safeguard(int nx, int ny, int perx, int pery, double g, const double *alphaB, const unsigned char *updated,
+                 double *Cn) {
+    return safeguard(nx, ny, perx, pery, g, alphaB, updated, Cn);
+}
+
 /* Sweep `d` with time step dt.  The body moves by U_d*dt along d (and by half
  * of the step's rotation) between the start pose A and the end pose B. */
 int or_sweep(or_sim *s, int d, double dt) {
@@ -760,6 +954,11 @@ int or_sweep(or_sim *s, int d, double dt) {
             }
     }
 
+    /* kept for diagnostics */
+    s->last_dir = d;
+    memcpy(s->bt_last, bt, sizeof(double) * nf);
+    memset(s->wall_cell, 0, sizeof(double) * 6 * n);
+
     /* wall data per band cell (Sec. II.B, II.C.3, II.C.4) */
     wall_t *W = (wall_t *)calloc((size_t)n, sizeof(wall_t));
     double Om = rot ? thetadot_at(s, tM) : 0.0;
@@ -791,6 +990,10 @@ int or_sweep(or_sim *s, int d, double dt) {
                 wy = s->c.U[1] + Om * (xc - pcx);
             }
             w->wd = d == 0 ? wx : wy;
+            {
+                double *wc = &s->wall_cell[6 * c];
+                wc[0] = 1.0; wc[1] = w->d; wc[2] = nxv; wc[3] = nyv; wc[4] = wx; wc[5] = wy;
+            }
             /* advective state from the step-start state (common to both sweeps),
              * pressure per sweep (eq. KleinAdvectivePressureSplitA and text after it) */
             double qn[4], qc[4];
@@ -883,30 +1086,22 @@ int or_sweep(or_sim *s, int d, double dt) {
             double qL[4], qR[4];
             for (int q = 0; q < nc; ++q) { qL[q] = QRb[q * len + a - 1]; qR[q] = QLb[q * len + a]; }
             riemann_flux(s, d, qL, qR, &Fst[4 * k]);
-            /* stabilised face flux (eqs. Klein2DtotalfluxaMethod2, Klein2shieldedFluxMethod2):
-             * beta_f F2D_f = (beta_f - sL - sR) F_f + sR Fsh_R + sL Fsh_L */
+            /* stabilised face flux (eqs. Klein2DtotalfluxaMethod2, Klein2shieldedFluxMethod2) */
             int kR = k < nal ? k : (periodic ? 0 : -1);
             int kL = k - 1 >= 0 ? k - 1 : (periodic ? nal - 1 : -1);
-            double sR = 0.0, sLv = 0.0;
             const wall_t *wR = NULL, *wL = NULL;
+            double bfarR = 0.0, bfarL = 0.0;
             if (kR >= 0) {
                 int cR = CELL(l, kR);
-                double bfar = bt[FACE(l, kR + 1 < nal || !periodic ? kR + 1 : 0)];
-                if (W[cR].has) { sR = dmax(0.0, bf - bfar); wR = &W[cR]; }
+                bfarR = bt[FACE(l, kR + 1 < nal || !periodic ? kR + 1 : 0)];
+                if (W[cR].has) wR = &W[cR];
             }
             if (kL >= 0) {
                 int cL = CELL(l, kL);
-                double bfar = bt[FACE(l, kL)];
-                if (W[cL].has) { sLv = dmax(0.0, bf - bfar); wL = &W[cL]; }
+                bfarL = bt[FACE(l, kL)];
+                if (W[cL].has) wL = &W[cL];
             }
-            if (sR + sLv > bf) { double sc = bf / (sR + sLv); sR *= sc; sLv *= sc; }
-            for (int q = 0; q < nc; ++q) {
-                double F = Fst[4 * k + q];
-                double v = (bf - sLv - sR) * F;
-                if (sR > 0.0) v += sR * (wR->FB[q] + wR->d * (F - wR->FB[q]));
-                if (sLv > 0.0) v += sLv * (wL->FB[q] + wL->d * (F - wL->FB[q]));
-                F2[4 * k + q] = v;
-            }
+            stab_face(nc, bf, &Fst[4 * k], wL, bfarL, wR, bfarR, &F2[4 * k]);
         }
         /* conservative update in alpha Q form (eqs. Klein2DcompleteMovingMethod2a-b) */
         for (int k = 0; k < nal; ++k) {
@@ -930,112 +1125,11 @@ int or_sweep(or_sim *s, int d, double dt) {
 
     /* covering / uncovering (Sec. II.C.5), applied simultaneously */
     double *Cn = (double *)malloc(sizeof(double) * nc * n);
-    memcpy(Cn, C, sizeof(double) * nc * n);
-    for (int j = 0; j < ny; ++j)
-        for (int i = 0; i < nx; ++i) {
-            int c = j * nx + i;
-            int covered = gA.alpha[c] > 0.0 && gB.alpha[c] == 0.0;
-            int donor_unc = ucov == OR_UNCOVER_DONOR && uncov[c];
-            if (!covered && !donor_unc) continue;
-            /* neighbour sets: face neighbours first, then the 8-neighbourhood */
-            int nb[8], nnb = 0;
-            double asum = 0.0;
-            for (int pass = 0; pass < 2 && nnb == 0; ++pass) {
-                for (int dj = -1; dj <= 1; ++dj)
-                    for (int di = -1; di <= 1; ++di) {
-                        if (di == 0 && dj == 0) continue;
-                        if (pass == 0 && di != 0 && dj != 0) continue;
-                        int ii = i + di, jj = j + dj;
-                        if (s->c.bc[0] == OR_BC_PERIODIC) ii = wrapi(ii, nx);
-                        if (s->c.bc[2] == OR_BC_PERIODIC) jj = wrapi(jj, ny);
-                        if (ii < 0 || ii >= nx || jj < 0 || jj >= ny) continue;
-                        int cc = jj * nx + ii;
-                        if (!(gB.alpha[cc] > 0.0)) continue;
-                        if (ucov == OR_UNCOVER_DONOR && uncov[cc]) continue; /* no content yet */
-                        nb[nnb++] = cc;
-                        asum += gB.alpha[cc];
-                    }
-            }
-            if (nnb == 0) { err = OR_E_UNSTABLE; continue; }
-            if (covered) {
-                /* residual (eq. massDeficitEquation) shared by volume (eq. cutCellCoverDonation) */
-                for (int m = 0; m < nnb; ++m)
-                    for (int q = 0; q < nc; ++q) Cn[q * n + nb[m]] += gB.alpha[nb[m]] / asum * C[q * n + c];
-                for (int q = 0; q < nc; ++q) Cn[q * n + c] = 0.0;
-            } else {
-                /* eqs. volumeWeighting, cutCellInitialisation, cutCellInitialisationDonorCellUpdate */
-                double sigma = gB.alpha[c] / (gB.alpha[c] + asum);
-                for (int q = 0; q < nc; ++q) {
-                    double tot = 0.0;
-                    for (int m = 0; m < nnb; ++m) tot += C[q * n + nb[m]];
-                    Cn[q * n + c] = sigma * tot;
-                    for (int m = 0; m < nnb; ++m) Cn[q * n + nb[m]] -= sigma * C[q * n + nb[m]];
-                }
-                updated[c] = 1;
-            }
-        }
+    const int perx = s->c.bc[0] == OR_BC_PERIODIC, pery = s->c.bc[2] == OR_BC_PERIODIC;
+    if (cover_uncover(nx, ny, perx, pery, nc, ucov, gA.alpha, gB.alpha, C, Cn, updated) != OR_OK) err = OR_E_UNSTABLE;
 
-    /* positivity safeguard (a reading; the paper gives none): a cell whose
-     * content is non-physical after the update is merged with its fluid face
-     * neighbours; every connected cluster of such cells and their neighbours
-     * shares its total content in proportion to volume.  Cells still
-     * non-physical after a merge seed the next one, which reaches one layer of
-     * neighbours further, up to OR_MIX_LAYERS merges.  Exactly conservative. */
-    for (int layer = 0; layer < OR_MIX_LAYERS && s->c.equation == OR_EULER; ++layer) {
-        int *lab = (int *)malloc(sizeof(int) * n);
-        unsigned char *bad = (unsigned char *)calloc((size_t)n, 1);
-        int nbad = 0;
-        for (int c = 0; c < n; ++c) {
-            lab[c] = -1;
-            double aB = gB.alpha[c];
-            if (!(aB > 0.0) || !updated[c]) continue;
-            double q[4] = {Cn[c] / aB, Cn[n + c] / aB, Cn[2 * n + c] / aB, Cn[3 * n + c] / aB};
-            int b = !(q[0] > 0.0) || !(pressure(g, q) > 0.0);
-            for (int k = 0; k < 4; ++k) if (!isfinite(q[k])) b = 1;
-            if (b) { bad[c] = 1; nbad++; }
-        }
-        if (nbad) {
-            /* union-find over bad cells and their fluid face neighbours */
-            int *par = (int *)malloc(sizeof(int) * n);
-            for (int c = 0; c < n; ++c) par[c] = c;
-            for (int c = 0; c < n; ++c) {
-                if (!bad[c]) continue;
-                int i = c % nx, j = c / nx;
-                lab[c] = c;
-                int dd[4][2] = {{-1, 0}, {1, 0}, {0, -1}, {0, 1}};
-                for (int m = 0; m < 4; ++m) {
-                    int ii = i + dd[m][0], jj = j + dd[m][1];
-                    if (s->c.bc[0] == OR_BC_PERIODIC) ii = wrapi(ii, nx);
-                    if (s->c.bc[2] == OR_BC_PERIODIC) jj = wrapi(jj, ny);
-                    if (ii < 0 || ii >= nx || jj < 0 || jj >= ny) continue;
-                    int cc = jj * nx + ii;
-                    if (!(gB.alpha[cc] > 0.0) || !updated[cc]) continue;
-                    lab[cc] = cc;
-                    int ra = c, rb = cc;
-                    while (par[ra] != ra) ra = par[ra];
-                    while (par[rb] != rb) rb = par[rb];
-                    if (ra != rb) { if (ra < rb) par[rb] = ra; else par[ra] = rb; }
-                }
-            }
-            double *tot = (double *)calloc((size_t)n * 5, sizeof(double));
-            for (int c = 0; c < n; ++c) {
-                if (lab[c] < 0) continue;
-                int r = c; while (par[r] != r) r = par[r];
-                lab[c] = r;
-                tot[5 * r + 4] += gB.alpha[c];
-                for (int q = 0; q < 4; ++q) tot[5 * r + q] += Cn[q * n + c];
-            }
-            for (int c = 0; c < n; ++c) {
-                if (lab[c] < 0) continue;
-                s->mixed_last++;
-                int r = lab[c];
-                for (int q = 0; q < 4; ++q) Cn[q * n + c] = gB.alpha[c] * (tot[5 * r + q] / tot[5 * r + 4]);
-            }
-            free(tot); free(par);
-        }
-        free(lab); free(bad);
-        if (!nbad) break;
-    }
+    /* positivity safeguard */
+    if (s->c.equation == OR_EULER) s->mixed_last = safeguard(nx, ny, perx, pery, g, gB.alpha, updated, Cn);
 
     /* new state Q' = content / alpha^B */
     for (int c = 0; c < n; ++c) {
@@ -1085,4 +1179,21 @@ int or_status(const or_sim *s) { return s->status; }
 int or_last_sweep(const or_sim *s, double *wall) {
     if (wall) for (int q = 0; q < 4; ++q) wall[q] = s->wall_last[q];
     return s->mixed_last;
+}
+
+/* Time-averaged apertures of the last sweep's faces (the layout of or_swept
+ * for its direction); returns that direction (-1 before the first sweep). */
+int or_last_faces(const or_sim *s, double *bt) {
+    if (s->last_dir < 0) return -1;
+    int nx = s->c.nx, ny = s->c.ny;
+    int nf = s->last_dir == 0 ? (nx + 1) * ny : nx * (ny + 1);
+    if (bt) memcpy(bt, s->bt_last, sizeof(double) * nf);
+    return s->last_dir;
+}
+
+/* Wall data of the last sweep per cell, 6 doubles each: 1 if the cell had
+ * wall data, the shielded distance d, the wall normal (n_x, n_y) and the
+ * wall velocity (w_x, w_y) at the mid pose; zeros elsewhere. */
+void or_last_wall(const or_sim *s, double *out) {
+    memcpy(out, s->wall_cell, sizeof(double) * 6 * s->c.nx * s->c.ny);
 }
