@@ -1023,6 +1023,174 @@ __device__ __forceinline__ int deferred_pair(int lane, unsigned p2_0, unsigned p
     return (d0 ? 1 : 0) | (d1 ? 2 : 0);
 }
 
+// Lines and tiles the body cannot reach (mode 0).  The body's extent over
+// the sweep's poses (k_pose: every polygon, fixed or moving, at poses A, mid
+// and B, widened by a cell) bounds every touched and every solid cell of the
+// sweep.  A row of the x sweep outside it, or a y-sweep tile whose columns
+// miss it or whose rows lie more than three rows away from it, holds only
+// fluid cells with plain five-cell stencils: no class byte is needed, no
+// cell is deferred and every real cell is stored.  These paths skip the
+// class bytes, touch masks and deferral bookkeeping of the general loops
+// below; each cell's arithmetic is the same function sequence on the same
+// inputs (evolve2 with slopes on, hllc2, the update, the positivity and
+// wave-speed checks), so the bits are the same.
+
+// positivity list and CFL wave speeds of a pair of new states (cells ci and
+// ci + 1; st: bit 0 first stored, bit 1 second stored)
+__device__ __forceinline__ void pair_checks(const float2 *qn, int st, int ci, bool last, float g1, float g, float &s0,
+                                            float &s1, InstDyn &y) {
+    float2 ir, p;
+    prim2(g1, qn, ir, p);
+    if ((st & 1) && !(qn[0].x > 0.0f && p.x > 0.0f)) list_bulk_bad(y, ci);
+    if ((st & 2) && !(qn[0].y > 0.0f && p.y > 0.0f)) list_bulk_bad(y, ci + 1);
+    if (last) {
+        const float2 cs = sqrt2(mul2(mul2(P2(g), p), ir));
+        const float2 w0 = add2(make_float2(fabsf(qn[1].x * ir.x), fabsf(qn[1].y * ir.y)), cs);
+        const float2 w1 = add2(make_float2(fabsf(qn[2].x * ir.x), fabsf(qn[2].y * ir.y)), cs);
+        if (st & 1) { s0 = fmaxf(s0, w0.x); s1 = fmaxf(s1, w1.x); }
+        if (st & 2) { s0 = fmaxf(s0, w0.y); s1 = fmaxf(s1, w1.y); }
+    }
+}
+
+// x sweep of row j (Q, Qo: the row's first cell) outside the body's extent,
+// in the layout of k_bulk_x_p: lane l holds cells 64c + 2l, 64c + 2l + 1 of
+// chunk c, the ring is filled by cp.async XC - 2 chunks ahead, the update
+// trails the fluxes by one chunk
+template <int XC>
+__device__ __forceinline__ void bulk_x_far(const InstDesc &I, InstDyn &y, XRing<XC> &rg,
+                                           const float *__restrict__ Q, float *__restrict__ Qo, int rowb, size_t plane,
+                                           float lam, float g, float g1, bool last, float &s0, float &s1) {
+    constexpr int XRN = 64 * XC;
+    const int lane = threadIdx.x & 31;
+    const int n = I.nx;
+    const int c_last = (n + 1) >> 6;   // chunk holding face n
+    // ghost cells of the boundary conditions: lane 0: -2, 1: -1, 2: n, 3: n+1
+    float gq[4] = {1.0f, 1.0f, 1.0f, 1.0f};
+    int gb = -1000000;
+    if (lane < 4) {
+        gb = lane < 2 ? lane - 2 : n + lane - 2;
+        bool fl;
+        const int p = ghost_map(gb, n, I.bc[0], I.bc[1], &fl);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) gq[k] = __ldg(Q + k * plane + p);
+        if (fl) gq[1] = -gq[1];
+    }
+    // ghosts of chunk c or c+1 into the ring, once those chunks' copies are
+    // complete (a copy cannot overwrite them then)
+    const int c_hi_ghost = (n >> 6) - 1;
+    auto put_ghost = [&](int c) {
+        const int gk = gb >> 6;
+        if (lane < 4 && (gk == c || gk == c + 1)) {
+            const int pos = gb & (XRN - 1);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) rg.q[k][pos] = gq[k];
+        }
+    };
+    auto prefetch = [&](int c) {
+        const int a0 = 64 * c;
+        if (c >= 0 && a0 < n) {
+            const int sl = a0 & (XRN - 1);
+            const int a = a0 + 2 * lane;
+            if (a + 1 < n) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) cp_async8(&rg.q[k][sl + 2 * lane], Q + k * plane + a);
+            } else if (a < n) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) cp_async4(&rg.q[k][sl + 2 * lane], Q + k * plane + a);
+            }
+        }
+        cp_async_commit();
+    };
+#pragma unroll
+    for (int c = 0; c < XC - 2; ++c) prefetch(c);
+    cp_async_wait<XC - 4>();   // chunks 0 and 1 complete
+    __syncwarp();
+    put_ghost(-1);
+    __syncwarp();
+    // evolved right state of cell -1 (all lanes alike)
+    E2 QRc;
+    {
+        float2 qm[4], q0[4], qp[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            qm[k] = P2(rg.q[k][XRN - 2]);
+            q0[k] = P2(rg.q[k][XRN - 1]);
+            qp[k] = P2(rg.q[k][0]);
+        }
+        E2 QL;
+        evolve2<0>(g1, lam, qm, q0, qp, true, true, QL, QRc);
+    }
+    float2 Fprev[4];
+    // new states of chunk c - 1 (F: this chunk's fluxes, whose lane 0 holds
+    // the high face of the previous chunk's lane 31; tail: none)
+    auto update = [&](int c, const float2 *F, bool tail) {
+        const int ap = 64 * (c - 1) + 2 * lane;
+        const int pp = ap & (XRN - 1);
+        float2 qn[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float dn = __shfl_down_sync(0xffffffffu, Fprev[k].x, 1);
+            const float nx0 = tail ? 0.0f : __shfl_sync(0xffffffffu, F[k].x, 0);
+            const float2 Fhi = make_float2(Fprev[k].y, lane == 31 ? nx0 : dn);
+            const float2 qo = *(const float2 *)&rg.q[k][pp];
+            qn[k] = fma2(P2(lam), sub2(Fprev[k], Fhi), qo);
+        }
+        const int st = (ap < n ? 1 : 0) | (ap + 1 < n ? 2 : 0);
+        if (st == 3) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) *(float2 *)(Qo + k * plane + ap) = qn[k];
+        } else if (st) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) Qo[k * plane + ap] = qn[k].x;
+        }
+        pair_checks(qn, st, rowb + ap, last, g1, g, s0, s1, y);
+    };
+    for (int c = 0; c <= c_last; ++c) {
+        __syncwarp();
+        prefetch(c + XC - 2);
+        cp_async_wait<XC - 3>();   // chunks up to c + 1 complete
+        __syncwarp();
+        if (c >= c_hi_ghost) {
+            put_ghost(c);
+            __syncwarp();
+        }
+        const int a = 64 * c + 2 * lane;
+        const int pa = a & (XRN - 1), pl = (a - 1) & (XRN - 1), pr = (a + 2) & (XRN - 1);
+        float2 q0[4], qm[4], qp[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            q0[k] = *(const float2 *)&rg.q[k][pa];
+            qm[k] = make_float2(rg.q[k][pl], q0[k].x);
+            qp[k] = make_float2(q0[k].y, rg.q[k][pr]);
+        }
+        E2 QL, QR;
+        evolve2<0>(g1, lam, qm, q0, qp, true, true, QL, QR);
+        // faces a (cells a-1 | a) and a+1 (cells a | a+1)
+        E2 Lf;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float up = __shfl_up_sync(0xffffffffu, QR.q[k].y, 1);
+            Lf.q[k] = make_float2(lane == 0 ? QRc.q[k].x : up, QR.q[k].x);
+        }
+        {
+            const float ui = __shfl_up_sync(0xffffffffu, QR.ir.y, 1), up = __shfl_up_sync(0xffffffffu, QR.p.y, 1);
+            Lf.ir = make_float2(lane == 0 ? QRc.ir.x : ui, QR.ir.x);
+            Lf.p = make_float2(lane == 0 ? QRc.p.x : up, QR.p.x);
+        }
+        float2 F[4];
+        hllc2<0>(g, Lf, QL, F);
+        if (c >= 1) update(c, F, false);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) QRc.q[k].x = __shfl_sync(0xffffffffu, QR.q[k].y, 31);
+        QRc.ir.x = __shfl_sync(0xffffffffu, QR.ir.y, 31);
+        QRc.p.x = __shfl_sync(0xffffffffu, QR.p.y, 31);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) Fprev[k] = F[k];
+    }
+    // the row's last chunk (the face past its lane 31 lies beyond face n)
+    update(c_last + 1, Fprev, true);
+}
+
 // x sweep, packed: one warp per row, lane l holds cells 64c + 2l and
 // 64c + 2l + 1 of chunk c; the update trails the fluxes by one chunk.
 // MODE 0: the cells that are not deferred (plain arithmetic throughout);
@@ -1056,6 +1224,13 @@ __global__ void __launch_bounds__(128, MINB) k_bulk_x_p(const InstDesc *__restri
     const float *__restrict__ Q = (const float *)I.Q[src] + rowb;
     float *__restrict__ Qb = (float *)I.Q[dst];
     float *__restrict__ Qo = Qb + rowb;
+    if (MODE == 0 && I.bc[0] != 2 && (j < y.row0 || j > y.row1)) {
+        // a row outside the body's extent: plain throughout
+        float s0 = 0.0f, s1 = 0.0f;
+        bulk_x_far<XC>(I, y, rg, Q, Qo, rowb, plane, lam, g, g1, last != 0, s0, s1);
+        finish_warp<float>(y, last != 0, s0, s1);
+        return;
+    }
     const unsigned char *__restrict__ cl = I.cls + rowb;
     // ghost cells of the boundary conditions: lane 0: -2, 1: -1, 2: n, 3: n+1
     float gq[4] = {1.0f, 1.0f, 1.0f, 1.0f};
@@ -1333,6 +1508,111 @@ struct YRing {
     unsigned char cls[YR][64];
 };
 
+// y sweep of a tile the body cannot reach (see bulk_x_far), in the layout
+// of k_bulk_y_p: columns i, i+1 of this thread (st0: which exist), rows
+// j0 .. j1-1 streamed through the warp's ring six rows ahead
+__device__ __forceinline__ void bulk_y_far(const InstDesc &I, InstDyn &y, YRing &rg, const float *__restrict__ Q,
+                                           float *__restrict__ Qo, int i, int st0, int j0, int j1, size_t plane,
+                                           float lam, float g, float g1, bool last, float &s0, float &s1) {
+    const int lane = threadIdx.x & 31;
+    const int n = I.ny, pitch = I.pitch;
+    const int bclo = I.bc[2], bchi = I.bc[3];
+    // copies of row r (a ghost row of the boundary condition outside [0, n))
+    // into its slot; rows past j1 + 2 are not needed (one commit group per call)
+    auto prefetch = [&](int r) {
+        if (r <= j1 + 2) {
+            const int sl = (r - j0 + 2) & (YR - 1);
+            int p = r;
+            if (r < 0 || r >= n) {
+                bool fl;
+                p = ghost_map(r, n, bclo, bchi, &fl);
+            }
+            const float *src_q = Q + (size_t)p * pitch + i;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (st0 == 3) cp_async8(&rg.q[sl][k][2 * lane], src_q + k * plane);
+                else if (st0 == 1) cp_async4(&rg.q[sl][k][2 * lane], src_q + k * plane);
+            }
+        }
+        cp_async_commit();
+    };
+    // the pair of row r from the ring; columns past the grid read as 1,
+    // ghost rows of a reflective side flip the normal momentum
+    auto row = [&](int r, float2 *v) {
+        const int sl = (r - j0 + 2) & (YR - 1);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] = *(const float2 *)&rg.q[sl][k][2 * lane];
+        if (st0 != 3) {
+            if (!(st0 & 1)) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) v[k].x = 1.0f;
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) v[k].y = 1.0f;
+        }
+        if ((r < 0 && bclo == 1) || (r >= n && bchi == 1)) {
+            v[2].x = -v[2].x;
+            v[2].y = -v[2].y;
+        }
+    };
+    for (int r = j0 - 2; r < j0 - 2 + YR; ++r) prefetch(r);
+    cp_async_wait<YR - 4>();   // rows j0-2 .. j0+1 complete
+    __syncwarp();
+    E2 QRc;
+    {
+        float2 qa[4], qm[4], qc[4];
+        row(j0 - 2, qa);
+        row(j0 - 1, qm);
+        row(j0, qc);
+        E2 QL;
+        evolve2<1>(g1, lam, qa, qm, qc, true, true, QL, QRc);
+    }
+    float2 Fprev[4];
+    float *__restrict__ wp = Qo + (size_t)(j0 - 1) * pitch + i;   // row f-1 of this thread's columns
+    for (int f = j0; f <= j1; ++f, wp += pitch) {
+        __syncwarp();
+        prefetch(f + YR - 2);
+        cp_async_wait<YR - 4>();   // rows up to f + 2 complete
+        __syncwarp();
+        float2 qm[4], qc[4], qp[4];
+        if (f >= 1 && f + 1 < n) {
+            // rows f-1, f, f+1 (lanes past the grid compute on values that
+            // are never stored)
+            const int sm_ = (f - j0 + 1) & (YR - 1), sc = (f - j0 + 2) & (YR - 1), sp = (f - j0 + 3) & (YR - 1);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                qm[k] = *(const float2 *)&rg.q[sm_][k][2 * lane];
+                qc[k] = *(const float2 *)&rg.q[sc][k][2 * lane];
+                qp[k] = *(const float2 *)&rg.q[sp][k][2 * lane];
+            }
+        } else {
+            row(f - 1, qm);
+            row(f, qc);
+            row(f + 1, qp);
+        }
+        E2 QL, QR;
+        evolve2<1>(g1, lam, qm, qc, qp, true, true, QL, QR);
+        float2 F[4];
+        hllc2<1>(g, QRc, QL, F);
+        if (f > j0) {
+            float2 qn[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) qn[k] = fma2(P2(lam), sub2(Fprev[k], F[k]), qm[k]);
+            if (st0 == 3) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) *(float2 *)(wp + k * plane) = qn[k];
+            } else if (st0) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) wp[k * plane] = qn[k].x;
+            }
+            pair_checks(qn, st0, (f - 1) * pitch + i, last, g1, g, s0, s1, y);
+        }
+        QRc = QR;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) Fprev[k] = F[k];
+    }
+}
+
 // y sweep, packed: one thread per pair of neighbouring columns and segment of
 // I.yseg rows, marching upward; a warp covers 64 consecutive columns and
 // streams its rows through a shared-memory ring filled by cp.async.  Passes
@@ -1370,8 +1650,16 @@ __global__ void __launch_bounds__(128, MINB) k_bulk_y_p(const InstDesc *__restri
     const size_t plane = (size_t)pitch * n;
     const float *__restrict__ Q = (const float *)I.Q[src];
     float *__restrict__ Qo = (float *)I.Q[dst];
-    const unsigned char *__restrict__ cl = I.cls;
     const int bclo = I.bc[2], bchi = I.bc[3];
+    if (MODE == 0 && bclo != 2 && !(col0 <= y.col1 && col0 + YCOLS_P - 1 >= y.col0 && j1 + 3 >= y.row0 &&
+                                    j0 - 3 <= y.row1)) {
+        // a tile the body cannot reach: plain throughout
+        float s0 = 0.0f, s1 = 0.0f;
+        bulk_y_far(I, y, rg, Q, Qo, i, st0, j0, j1, plane, lam, g, g1, last != 0, s0, s1);
+        finish_warp<float>(y, last != 0, s0, s1);
+        return;
+    }
+    const unsigned char *__restrict__ cl = I.cls;
     const bool cls_lane = lane < 16 && col0 + 4 * lane < pitch;
     // validity mask of this lane's class pair for the plain-path test
     const int vm = st0 == 3 ? 0x0505 : (st0 == 1 ? 0x0005 : 0);
