@@ -79,6 +79,25 @@ def summarize_clocks(samples, gpu_index):
             "reasons": sorted(reasons), "samples": len(rows)}
 
 
+def cpu_model():
+    """CPU model name of this host (lscpu, else /proc/cpuinfo)."""
+    try:
+        r = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=5)
+        for line in r.stdout.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -156,6 +175,54 @@ def bulk_alu(precision, wname):
         return None
 
 
+def fp64_pipe_per_cell(wname):
+    """FP64-pipe lane operations per cell-sweep of the FP64 bulk kernels
+    (every FP64 instruction -- add, multiply, FMA, compare, min/max,
+    conversion -- holds the pipe alike), mean over the x and y sweeps, from
+    the ncu capture summarised in profiles/fp64_ops.json; None when the
+    kernel sources have changed since."""
+    import hashlib
+    prof = os.path.join(ROOT, "profiles", "fp64_ops.json")
+    try:
+        d = json.load(open(prof))
+        for f, sha in d["sources_sha256"].items():
+            with open(os.path.join(ROOT, "paper_1711_11361_gb300", "csrc", f), "rb") as fh:
+                if hashlib.sha256(fh.read()).hexdigest() != sha:
+                    return None
+        v = list(d["fp64_pipe_lane_ops_per_cell"].values())
+        return float(sum(v) / len(v))
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def fp64_roofline_leg(mb, probs, wname, stream):
+    """The plain FP64 path on the same batch: its bulk kernels' time per sweep
+    (CUDA events around the bulk passes of 4 steps), cell-updates/s, and the
+    FP64-pipe roofline against the GPU's measured FP64 FMA rate."""
+    import torch
+    sim = mb.Sim(probs, mb.FP64)
+    sim.set_stream(stream.cuda_stream)
+    sim.run(2, 0.0)
+    sim.sync()
+    sim.enable_timing(True)
+    sim.run(4, 0.0)
+    ms, n = sim.kernel_time()
+    sim.enable_timing(False)
+    sim.close()
+    rate = mb.fp64_rate(stream.cuda_stream)
+    cells = sum(p.nx * p.ny for p in probs)
+    bulk_s = ms * 1e-3 / max(n, 1)
+    out = {"bulk_ms_per_sweep": bulk_s * 1e3, "bulk_cell_updates_per_s": cells / bulk_s, "unit": UNIT,
+           "peak_fp64_fma_per_s": rate, "peak_kind": "measured: mb_fp64_rate (independent FP64 FMA chains)"}
+    ops = fp64_pipe_per_cell(wname)
+    if ops is not None:
+        achieved = ops * cells / bulk_s
+        out["roofline"] = {"bound": "fp64", "achieved": achieved / 1e12, "peak": rate / 1e12,
+                           "unit": "T FP64-pipe lane-ops/s", "frac": achieved / rate,
+                           "fp64_pipe_lane_ops_per_cell": ops}
+    return out
+
+
 def accuracy_leg(mb, probs, steps=20):
     """FP32 batch against the FP64 GPU path (itself held to the oracle at
     1e-12 per step by the parity tests) on the same instances, the same
@@ -192,11 +259,19 @@ def accuracy_leg(mb, probs, steps=20):
             t32 = np.sum(w * b["Q"][q][fl])
             scale = mom if q in (1, 2) else np.sum(w * np.abs(a["Q"][q][fl]))
             drift[q] = max(drift[q], abs(t32 - t64) / scale if scale > 0 else 0.0)
+    m32 = [s32.merge_count(k) for k in range(len(probs))]
+    m64 = [s64.merge_count(k) for k in range(len(probs))]
     s64.close()
     s32.close()
     return {"l1_density_rel_max": max(l1), "l1_density_rel_mean": float(np.mean(l1)),
             "conservation_drift_rel_max": {"rho": drift[0], "rho_u": drift[1], "rho_v": drift[2], "E": drift[3]},
-            "against": "FP64 GPU path, same instances and states", "steps": steps, "dt": dt}
+            "against": "FP64 GPU path, same instances and states", "steps": steps, "dt": dt,
+            "safeguard_merged_cells": {
+                "fp32": {"total": int(sum(m32)), "instances_merging": int(sum(1 for m in m32 if m)),
+                         "max_instance": int(max(m32)), "per_step_mean": float(sum(m32)) / steps},
+                "fp64": {"total": int(sum(m64)), "instances_merging": int(sum(1 for m in m64 if m)),
+                         "max_instance": int(max(m64)), "per_step_mean": float(sum(m64)) / steps},
+                "cells_per_step": len(probs) and sum(p.nx * p.ny for p in probs) * 2}}
 
 
 def fp64_single_leg(mb, probs, steps=6):
@@ -328,6 +403,60 @@ def run_served(args):
     print(json.dumps(line))
 
 
+def run_period_accuracy(args):
+    """The pitching NACA 0012 workload (1024^2) over one full pitch period,
+    t = 2 pi / omega, in FP32 bulk arithmetic and in FP64, from the same
+    initial state at a common fixed step (0.9 times the FP64 CFL step at
+    t = 0): relative L1 density error (alpha-weighted over fluid cells) and
+    the drift of the conserved totals, FP32 against FP64, at t = T."""
+    import torch
+    from paper_1711_11361_gb300 import inputs, mb
+    torch.cuda.set_device(0)
+    prob = inputs.c3_naca(1024)
+    T = 2.0 * math.pi / prob.omega
+    s64 = mb.Sim(prob, mb.FP64)
+    dt0 = float(s64.step(0.0, report=True)[0])
+    s64.close()
+    nsteps = int(math.ceil(T / (0.9 * dt0)))
+    dt = T / nsteps
+    res = {}
+    for name, prec in (("fp64", mb.FP64), ("fp32", mb.FP32)):
+        sim = mb.Sim(prob, prec)
+        st = torch.cuda.Stream()
+        sim.set_stream(st.cuda_stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        sim.run(nsteps, dt)
+        e1.record(st)
+        torch.cuda.synchronize()
+        status = sim.sync()
+        res[name] = (sim.read_state(0, alpha=True), e0.elapsed_time(e1) * 1e-3, int(status))
+        sim.close()
+    a64, t64, st64 = res["fp64"]
+    a32, t32, st32 = res["fp32"]
+    al = a64["alpha"]
+    fl = al > 0
+    w = al[fl]
+    l1 = float(np.sum(w * np.abs(a32["Q"][0][fl] - a64["Q"][0][fl])) / np.sum(w * np.abs(a64["Q"][0][fl])))
+    drift = {}
+    for q, nm in enumerate(("rho", "rho_u", "rho_v", "E")):
+        t_64 = np.sum(w * a64["Q"][q][fl])
+        t_32 = np.sum(w * a32["Q"][q][fl])
+        scale = np.sum(w * np.abs(a64["Q"][q][fl])) if q in (0, 3) else np.sum(
+            w * np.hypot(a64["Q"][1][fl], a64["Q"][2][fl]))
+        drift[nm] = float(abs(t_32 - t_64) / scale)
+    cells = prob.nx * prob.ny * 2 * nsteps
+    print(json.dumps({
+        "metric": "FP32 bulk vs FP64 relative L1 density error after one pitch period (pitching NACA 0012)",
+        "value": l1, "unit": "relative L1", "higher_is_better": False, "dtype": "f32 vs f64", "data": "synthetic",
+        "config": {"workload": "c3_naca0012_1024_one_period", "T": T, "steps": nsteps, "dt": dt,
+                   "dt_rule": "0.9 x FP64 CFL step at t = 0, common to both runs"},
+        "t_end": {"fp64": a64["t"], "fp32": a32["t"]}, "status": {"fp64": st64, "fp32": st32},
+        "conservation_drift_rel": drift,
+        "throughput": {"fp64": cells / t64, "fp32": cells / t32, "unit": UNIT, "seconds": {"fp64": t64, "fp32": t32}},
+    }))
+
+
 def workload(rank, args):
     from paper_1711_11361_gb300 import inputs
     if args.workload == "c4":
@@ -357,7 +486,7 @@ def cpu_baseline(probs, budget_s=12.0):
         steps += 1
     el = time.perf_counter() - t0
     value = p.nx * p.ny * 2 * steps / el
-    return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "cpu_model": cpu_model(),
             "sample": f"{steps} full steps of instance {p.name} ({p.nx}x{p.ny}), {el:.1f} s, single-threaded"}
 
 
@@ -389,7 +518,7 @@ def cpu_baseline_all_cores(probs, budget_s=10.0):
     wall = time.perf_counter() - t0
     cells = sum(r[0] for r in res)
     span = max(r[1] for r in res)
-    return {"value": cells / span, "unit": UNIT, "cores": n, "kind": "oracle",
+    return {"value": cells / span, "unit": UNIT, "cores": n, "kind": "oracle", "cpu_model": cpu_model(),
             "sample": f"{n} processes, one instance each (smallest of the batch, {pick[0].nx}^2 to "
                       f"{pick[-1].nx}^2), full steps for {budget_s:.0f} s; wall {wall:.1f} s with start-up"}
 
@@ -425,13 +554,18 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="mb", choices=["mb", "reference"])
     ap.add_argument("--workload", default="c4")
     ap.add_argument("--instances", type=int, default=64)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--sweep-samples", type=int, default=100, help="steps sampled for the per-sweep p50/p99")
+    ap.add_argument("--c3-period", action="store_true",
+                    help="FP32 vs FP64 accuracy of the pitching NACA 0012 workload after one full pitch period")
+    ap.add_argument("--accuracy-steps", type=int, default=500,
+                    help="steps of the FP32-vs-FP64 accuracy leg (the 64-instance workload runs 500)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes of the bulk kernels")
     ap.add_argument("--no-accuracy", action="store_true", help="skip the FP32-vs-FP64 and FP64 single-instance legs")
@@ -449,6 +583,8 @@ def main():
         return run_reference(args)
     if args.workload == "c5":
         return run_served(args)
+    if args.c3_period:
+        return run_period_accuracy(args)
 
     import torch
     ws, rank, local = dist_env()
@@ -517,6 +653,26 @@ def main():
     traffic = bulk_traffic(args.precision, wname)
     ops_per_cell = bulk_alu(args.precision, wname)
 
+    # per-sweep times of the real path (step graph replay): an event recorded
+    # between a step's two sweeps, one step per sample
+    ev_mid = torch.cuda.Event(enable_timing=True)
+    ev_mid.record(stream)
+    torch.cuda.synchronize()
+    sim.set_sweep_event(ev_mid.cuda_event)
+    e_a, e_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sweeps = []
+    with torch.cuda.stream(stream):
+        sim.run(2, 0.0)
+        for k in range(args.sweep_samples):
+            e_a.record(stream)
+            sim.run(1, 0.0)
+            e_b.record(stream)
+            e_b.synchronize()
+            sweeps += [e_a.elapsed_time(ev_mid), ev_mid.elapsed_time(e_b)]
+    torch.cuda.synchronize()
+    sim.set_sweep_event(0)
+    kernels_per_step = sim.graph_kernels()
+
     # end to end through the C ABI with pinned host buffers
     pinned_in = [torch.empty((p.nc, p.ny, p.nx), dtype=torch.float64).pin_memory() for p in probs]
     pinned_out = [torch.empty((p.nc, p.ny, p.nx), dtype=torch.float64).pin_memory() for p in probs]
@@ -557,6 +713,9 @@ def main():
                    "autotuned": {k: tune.get(k) for k in ("x_cta", "y_cta", "y_rows", "x_min_ctas", "y_min_ctas",
                                                           "x_ring_chunks")}},
         "p50_ms_per_step": float(np.percentile(per, 50)), "p99_ms_per_step": float(np.percentile(per, 99)),
+        "per_sweep_ms": {"p50": float(np.percentile(sweeps, 50)), "p99": float(np.percentile(sweeps, 99)),
+                         "sweeps": len(sweeps),
+                         "how": "CUDA events around single step-graph replays with an event between the sweeps"},
         "ms_per_step_without_overlap": serial_ms,
         "status": int(status),
         "roofline": {"kernel": "bulk sweep update (MUSCL-Hancock + HLLC), x and y: the pass concurrent with the "
@@ -573,12 +732,14 @@ def main():
         "clocks": summarize_clocks(samples, local),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d,
                 "steps": e2e_steps},
-        "gpu_launches": 16 * args.steps,
+        "gpu_launches": kernels_per_step * args.steps,
+        "kernels_per_step": kernels_per_step,
     }
     if args.workload == "c4" and not args.no_accuracy:
-        line["accuracy"] = accuracy_leg(mb, probs)
+        line["accuracy"] = accuracy_leg(mb, probs, steps=args.accuracy_steps)
         f64 = fp64_single_leg(mb, probs)
         line["fp64_single_instance"] = f64
+        line["fp64_batch"] = fp64_roofline_leg(mb, probs, wname, stream)
         line["speedup_vs_fp64_single_instance"] = value / f64["value"]
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(probs)

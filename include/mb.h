@@ -41,7 +41,9 @@ typedef enum {
     MB_E_CUDA = -3,      /* CUDA runtime error (see mb_last_error) */
     MB_E_UNSTABLE = -4,  /* a fluid cell became non-finite or rho/p <= 0, or
                             a covered/uncovered cell had no fluid neighbour */
-    MB_E_TIMEOUT = -5,   /* reserved: a bounded device wait gave up */
+    MB_E_TIMEOUT = -5,   /* reserved for a bounded device wait that gives up;
+                            never returned: no kernel of this library waits
+                            on another kernel or on the host */
     MB_E_STATE = -6,     /* call order (e.g. second sweep with another dt) */
     MB_E_CAPACITY = -7   /* a fixed-size device work list overflowed */
 } mb_status;
@@ -95,6 +97,8 @@ mb_status mb_create(const mb_grid *grid, double gamma, const mb_body *body,
 mb_status mb_batch_create(int n, const mb_grid *grids, const double *gammas,
                           const mb_body *bodies, const mb_motion *motions, mb_sim **out);
 
+/* Free every device buffer, stream, event and cached graph of the sim
+ * (waits for its work first); NULL is a no-op.  No paper counterpart. */
 void mb_destroy(mb_sim *sim);
 
 /* Text of the last error on this sim (or of the last failed create if sim is
@@ -160,13 +164,31 @@ mb_status mb_read_states(mb_sim *sim, double *const *Q, double *clocks);
 mb_status mb_step(mb_sim *sim, double dt, double *dt_used);
 
 /* One directional sweep (dir 0: x, 1: y) of every instance with time step dt
- * (> 0).  Two calls make a step; the second must use the same dt.  The body
- * moves along dir by U_dir*dt and through half the step's rotation. */
+ * (> 0): the five stages of the split update along dir, Sec. II.C.4 (eqs.
+ * Klein2DcompleteMovingMethod2a-b with the stabilised fluxes of eqs.
+ * Klein2DtotalfluxaMethod2, Klein2shieldedFluxMethod2 and the wall term of
+ * eq. Klein2DMovingResultantFluxes) and Sec. II.C.5 (covering and
+ * uncovering).  Two calls make a step; the second must use the same dt
+ * (MB_E_STATE otherwise).  The body moves along dir by U_dir*dt and through
+ * half the step's rotation.  Asynchronous: errors flagged by the kernels are
+ * reported by mb_sync / mb_read_state. */
 mb_status mb_sweep(mb_sim *sim, int dir, double dt);
 
 /* Run nsteps steps (as mb_step with the same dt rule), replaying one CUDA
  * graph per step.  Does not synchronise. */
 mb_status mb_run(mb_sim *sim, int nsteps, double dt);
+
+/* Kernel launches of one step as captured by mb_run: the kernel nodes of the
+ * step graph captured last (0 before the first capture).  No paper
+ * counterpart: launch accounting for callers. */
+mb_status mb_graph_kernels(const mb_sim *sim, int *kernels_per_step);
+
+/* Record the caller's CUDA event (a cudaEvent_t; NULL: none) on the sim's
+ * stream between the two sweeps of every later step, so that the caller can
+ * time each sweep.  The caller owns the event and keeps it alive while it is
+ * set.  Drops the cached step graphs; not in the middle of a step.  No paper
+ * counterpart: measurement support. */
+mb_status mb_set_sweep_event(mb_sim *sim, void *event);
 
 /* Wait for the sim's stream and report flagged errors (any instance). */
 mb_status mb_sync(mb_sim *sim);
@@ -179,6 +201,19 @@ mb_status mb_info(const mb_sim *sim, int inst, int *n_inst, int *nx, int *ny, in
  * wall terms (content per unit cell area, eq. Klein2DcompleteMovingMethod2a),
  * out[4] = cells merged by the positivity safeguard, out[5] = band cells. */
 mb_status mb_diagnostics(mb_sim *sim, int inst, double *out);
+
+/* Measured FP64 rate of this GPU: fused multiply-adds per second of a plain
+ * kernel of independent FP64 FMA chains filling every SM (best of three
+ * launches, CUDA events on `stream`, a cudaStream_t or NULL), the peak the
+ * FP64 path's roofline is reported against.  Allocates a few KB of device
+ * memory for the duration of the call and synchronises `stream`.  No paper
+ * counterpart: measurement support. */
+mb_status mb_fp64_rate(void *stream, double *fma_per_s);
+
+/* Cells merged by the positivity safeguard (a reading; the paper has none)
+ * in all sweeps of instance inst since its state was last written, counted
+ * once per merge a cell takes part in.  Synchronises the sim's stream. */
+mb_status mb_merge_count(mb_sim *sim, int inst, long long *cells);
 
 /* Copy the band records (cells cut at the start or end pose) of instance
  * inst's last sweep into `out` (an array of max_records records of

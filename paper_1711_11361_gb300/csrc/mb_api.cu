@@ -38,6 +38,7 @@ void launch_bulk(int, int, const InstDesc *, InstDyn *, const BandRec *, int, in
                  int, cudaStream_t);
 template <class T>
 int bulk_blocks_per_sm(int);
+double fp64_probe_rate(cudaStream_t st);
 template <class T>
 void launch_write_state(const InstDesc *, InstDyn *, const double *const *, const double *, int, int, int, int,
                         cudaStream_t);
@@ -97,6 +98,8 @@ struct mb_sim {
     // concurrently with the bulk pass on the sim's stream (FP32 Euler)
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_mid = nullptr;   // caller's event recorded between a step's two sweeps (optional)
+    int graph_kernels = 0;          // kernel nodes of the step graph captured last
     bool overlap = true;          // mb_set_overlap
     // launch shapes of the bulk kernels (mb_autotune): CTA size, register
     // budget and ring depth per direction of the FP32x2 kernels, rows per
@@ -689,6 +692,12 @@ static mb_status issue_step(mb_sim *sim, double dt) {
     int d1 = (sim->nstep % 2 == 0) ? 0 : 1;
     mb_status r = do_sweep(sim, d1, dt);
     if (r != MB_OK) return r;
+    if (sim->ev_mid) {
+        // an external record: inside a stream capture a plain record would
+        // become a dependency edge and never time anything
+        cudaError_t e = cudaEventRecordWithFlags(sim->ev_mid, sim->stream, cudaEventRecordExternal);
+        if (e != cudaSuccess) return cuda_check(sim, e, "sweep event");
+    }
     return do_sweep(sim, 1 - d1, dt);
 }
 
@@ -733,6 +742,19 @@ mb_status mb_run(mb_sim *sim, int nsteps, double dt) {
             if (r != MB_OK) return r;
             if (e != cudaSuccess) return cuda_check(sim, e, "end capture");
             cudaGraphExec_t ex;
+            // kernel launches per step, for the caller's accounting
+            size_t nn = 0;
+            if (cudaGraphGetNodes(g, nullptr, &nn) == cudaSuccess) {
+                std::vector<cudaGraphNode_t> nodes(nn);
+                int kn = 0;
+                if (nn && cudaGraphGetNodes(g, nodes.data(), &nn) == cudaSuccess) {
+                    for (auto nd : nodes) {
+                        cudaGraphNodeType t;
+                        if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kn;
+                    }
+                }
+                sim->graph_kernels = kn;
+            }
             e = cudaGraphInstantiate(&ex, g, 0);
             cudaGraphDestroy(g);
             if (e != cudaSuccess) return cuda_check(sim, e, "instantiate");
@@ -971,6 +993,16 @@ mb_status mb_diagnostics(mb_sim *sim, int inst, double *out) {
     return MB_OK;
 }
 
+mb_status mb_merge_count(mb_sim *sim, int inst, long long *cells) {
+    if (!sim || !cells || inst < 0 || inst >= sim->n) return MB_E_INVAL;
+    InstDyn y;
+    cudaError_t e = cudaMemcpyAsync(&y, sim->dy + inst, sizeof(y), cudaMemcpyDeviceToHost, sim->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(sim->stream);
+    if (e != cudaSuccess) return cuda_check(sim, e, "merge count");
+    *cells = y.mixed_total;
+    return MB_OK;
+}
+
 // rows per thread of the y sweep for every instance (tile counts follow)
 static cudaError_t set_yseg(mb_sim *s, int yseg) {
     if (yseg == s->tune_yseg) return cudaSuccess;
@@ -1069,12 +1101,34 @@ mb_status mb_autotune(mb_sim *sim, double *report) {
     return MB_OK;
 }
 
+mb_status mb_fp64_rate(void *stream, double *fma_per_s) {
+    if (!fma_per_s) return MB_E_INVAL;
+    const double r = mb::fp64_probe_rate((cudaStream_t)stream);
+    if (!(r > 0.0)) return MB_E_CUDA;
+    *fma_per_s = r;
+    return MB_OK;
+}
+
 mb_status mb_enable_timing(mb_sim *sim, int enable) {
     if (!sim) return MB_E_INVAL;
     cudaStreamSynchronize(sim->stream);
     for (auto &ev : sim->evs) { cudaEventDestroy(ev.first); cudaEventDestroy(ev.second); }
     sim->evs.clear();
     sim->timing = enable != 0;
+    return MB_OK;
+}
+
+mb_status mb_graph_kernels(const mb_sim *sim, int *kernels_per_step) {
+    if (!sim || !kernels_per_step) return MB_E_INVAL;
+    *kernels_per_step = sim->graph_kernels;
+    return MB_OK;
+}
+
+mb_status mb_set_sweep_event(mb_sim *sim, void *event) {
+    if (!sim) return MB_E_INVAL;
+    if (sim->sidx != 0) return fail(sim, MB_E_STATE, "mb_set_sweep_event in the middle of a step");
+    sim->ev_mid = (cudaEvent_t)event;
+    drop_graphs(sim);   // the cached graphs hold the old sequence
     return MB_OK;
 }
 

@@ -121,6 +121,7 @@ struct InstDyn {
     int band_count;
     int nbad;
     int mixed;
+    long long mixed_total;      // cells merged by the safeguard in every sweep since the state was written
     int nbadlist;
     int badlist[16];            // first records flagged by the positivity check
     int nbulk;                  // non-band cells found non-physical by the bulk update

@@ -1880,6 +1880,57 @@ __global__ void __launch_bounds__(128, MINB) k_bulk_y_p(const InstDesc *__restri
 }
 
 // ---------------------------------------------------------------------------
+// FP64 rate probe (measurement support for the FP64 path's roofline): every
+// thread runs eight independent chains of FP64 fused multiply-adds, enough
+// warps resident to keep the FP64 pipe of every SM busy
+// ---------------------------------------------------------------------------
+constexpr int FP64_PROBE_CHAINS = 8;
+__global__ void __launch_bounds__(256) k_fp64_probe(double *out, int iters, double a, double b) {
+    double x[FP64_PROBE_CHAINS];
+#pragma unroll
+    for (int k = 0; k < FP64_PROBE_CHAINS; ++k) x[k] = 1.0 + 1e-3 * (threadIdx.x + k);
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int k = 0; k < FP64_PROBE_CHAINS; ++k) x[k] = fma(x[k], a, b);
+    }
+    double r = 0.0;
+#pragma unroll
+    for (int k = 0; k < FP64_PROBE_CHAINS; ++k) r += x[k];
+    if (r == 12345.678) out[blockIdx.x] = r;   // keeps the chains alive; never true for these inputs
+}
+
+// FP64 fused multiply-adds per second of k_fp64_probe on the current
+// device (best of three timed launches after one warm-up), or < 0 on error
+double fp64_probe_rate(cudaStream_t st) {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return -1.0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1.0;
+    const int blocks = sms * 8, threads = 256, iters = 4096;
+    double *out = nullptr;
+    if (cudaMallocAsync((void **)&out, sizeof(double) * blocks, st) != cudaSuccess) return -1.0;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    double best = 0.0;
+    k_fp64_probe<<<blocks, threads, 0, st>>>(out, iters, 0.999999, 1e-6);
+    for (int r = 0; r < 3; ++r) {
+        cudaEventRecord(e0, st);
+        k_fp64_probe<<<blocks, threads, 0, st>>>(out, iters, 0.999999, 1e-6);
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double rate = (double)blocks * threads * FP64_PROBE_CHAINS * iters / (ms * 1e-3);
+        if (rate > best) best = rate;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFreeAsync(out, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess) return -1.0;
+    return best;
+}
+
+// ---------------------------------------------------------------------------
 // deferred bulk cells (FP32 Euler, after the band fluxes): one thread per
 // listed cell pair, the general path of the streaming kernels for its two
 // cells (same functions on the same inputs, so the same bits): MUSCL-Hancock
@@ -2430,7 +2481,10 @@ __global__ void __launch_bounds__(32) k_mix(const InstDesc *__restrict__ D, Inst
             }
             __syncwarp();
         }
-        if (lane == 0) y.mixed += nn;
+        if (lane == 0) {
+            y.mixed += nn;
+            y.mixed_total += nn;
+        }
         // cells still non-physical, in cell order
         nnext = 0;
         for (int k0 = 0; k0 < nn; k0 += 32) {

@@ -26,7 +26,8 @@ EXPORTS = ["mb_create", "mb_batch_create", "mb_destroy", "mb_last_error", "mb_se
            "mb_cut_cells_noalloc", "mb_noalloc_last_error", "mb_batch_add", "mb_batch_remove", "mb_instance_bytes",
            "mb_request_bytes", "mb_server_create", "mb_server_destroy", "mb_server_last_error", "mb_server_submit",
            "mb_server_tick", "mb_server_query", "mb_server_request_error", "mb_autotune", "mb_set_overlap",
-           "mb_write_states", "mb_read_states"]
+           "mb_write_states", "mb_read_states", "mb_graph_kernels", "mb_set_sweep_event",
+           "mb_merge_count", "mb_fp64_rate"]
 
 
 class Grid(ctypes.Structure):
@@ -103,6 +104,10 @@ def _load():
         "mb_set_overlap": ([P, I], I),
         "mb_write_states": ([P, ctypes.POINTER(D), D], I),
         "mb_read_states": ([P, ctypes.POINTER(D), D], I),
+        "mb_graph_kernels": ([P, ctypes.POINTER(I)], I),
+        "mb_set_sweep_event": ([P, P], I),
+        "mb_merge_count": ([P, I, ctypes.POINTER(ctypes.c_longlong)], I),
+        "mb_fp64_rate": ([P, D], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -267,6 +272,12 @@ class Sim:
         self._check(lib.mb_diagnostics(self._h, inst, _dp(o)))
         return dict(wall=o[:4], mixed=int(o[4]), band=int(o[5]))
 
+    def merge_count(self, inst=0):
+        """Cells merged by the positivity safeguard since the instance's state was written (mb_merge_count)."""
+        c = ctypes.c_longlong()
+        self._check(lib.mb_merge_count(self._h, inst, ctypes.byref(c)))
+        return c.value
+
     def autotune(self):
         """Tune the bulk kernels' launch shapes (mb_autotune); returns the choice."""
         r = np.zeros(8)
@@ -277,6 +288,16 @@ class Sim:
     def set_overlap(self, on=True):
         """Overlap of the bulk pass with the geometry and band fluxes (mb_set_overlap)."""
         self._check(lib.mb_set_overlap(self._h, 1 if on else 0))
+
+    def graph_kernels(self):
+        """Kernel launches per step of the step graph captured last (mb_graph_kernels)."""
+        k = ctypes.c_int()
+        self._check(lib.mb_graph_kernels(self._h, ctypes.byref(k)))
+        return k.value
+
+    def set_sweep_event(self, event_handle: int):
+        """Record a CUDA event between the two sweeps of each step (mb_set_sweep_event; 0: none)."""
+        self._check(lib.mb_set_sweep_event(self._h, ctypes.c_void_p(event_handle)))
 
     def enable_timing(self, on=True):
         self._check(lib.mb_enable_timing(self._h, 1 if on else 0))
@@ -328,6 +349,15 @@ def cut_cells_noalloc(prob: inputs.Problem, X: float, Y: float, theta: float, al
                                  ctypes.c_void_p(alpha_ptr), ctypes.c_void_p(class_ptr), ctypes.c_void_p(stream))
     if r != MB_OK:
         raise MBError(r, lib.mb_noalloc_last_error().decode())
+
+
+def fp64_rate(stream: int = 0) -> float:
+    """Measured FP64 fused multiply-adds per second of this GPU (mb_fp64_rate)."""
+    r = ctypes.c_double()
+    rc = lib.mb_fp64_rate(ctypes.c_void_p(stream), ctypes.byref(r))
+    if rc != MB_OK:
+        raise MBError(rc, "mb_fp64_rate failed")
+    return r.value
 
 
 class Server:
