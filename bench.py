@@ -301,23 +301,27 @@ def fp64_single_leg(mb, probs, steps=6):
 
 
 def run_served(args):
-    """Served stream (continuous batching through mb_server_*): a bounded
-    prefix of the seeded request stream (grid sizes, step counts and count
-    set by the --c5-* options), Poisson arrivals at an offered load of
-    --c5-load times the batched throughput measured on the stream's own first
-    requests.  Reports aggregate cell-updates/s over the run, p50/p99
-    completion latency (submission to result on the host), and the serial
-    plain-FP64 time of the same stream extrapolated from a sample."""
+    """Served stream (continuous batching through mb_server_*): the seeded
+    request stream (count, grid sizes and step counts set by the --c5-*
+    options; the defaults are the full stream: 2000 requests, N log-uniform
+    in 256..2048, 500..5000 steps), Poisson arrivals at an offered load of
+    --c5-load times the batched throughput measured on the stream's own
+    first 16 requests.  Requests are built when they arrive and their final
+    states are not kept (host memory).  Reports aggregate cell-updates/s over
+    the run, p50/p99 completion latency (submission to result on the host),
+    and the serial plain-FP64 time of the same stream extrapolated from a
+    seeded subsample (each sampled request timed over a few steps, scaled by
+    its step count)."""
     import torch
     from paper_1711_11361_gb300 import inputs, mb
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
     specs = inputs.c5_requests(n=args.c5_requests, nmin=args.c5_nmin, nmax=args.c5_nmax, smin=args.c5_smin,
                                smax=args.c5_smax)
+    n = len(specs)
     work = np.array([sp["N"] ** 2 * 2.0 * sp["steps"] for sp in specs])
-    probs = [inputs.make_request(sp) for sp in specs]
     # batched throughput of the stream's own instances sets the offered rate
-    probe = probs[:16]
+    probe = [inputs.make_request(sp) for sp in specs[:16]]
     sim = mb.Sim(probe, mb.FP32)
     st = torch.cuda.Stream()
     sim.set_stream(st.cuda_stream)
@@ -330,20 +334,21 @@ def run_served(args):
     torch.cuda.synchronize()
     thr = sum(p.nx * p.ny for p in probe) * 2 * 5 / (e0.elapsed_time(e1) * 1e-3)
     sim.close()
+    del probe
     mean_gap = float(np.mean(work)) / (args.c5_load * thr)
-    arr = inputs.c5_arrivals(len(specs), mean_gap)
+    arr = inputs.c5_arrivals(n, mean_gap)
     srv = mb.Server(mb.FP32, 0, budget_bytes=args.c5_budget_gib * 2 ** 30, max_active=args.c5_max_active)
     stop = threading.Event()
     samples = []
     th = threading.Thread(target=sample_clocks, args=(stop, samples), daemon=True)
     th.start()
-    ids, k, n = [], 0, len(specs)
+    ids, k = [], 0
     t0 = time.perf_counter()
     peak = 0
     while True:
         now = time.perf_counter() - t0
         while k < n and arr[k] <= now:
-            ids.append(srv.submit(probs[k], specs[k]["steps"]))
+            ids.append(srv.submit(inputs.make_request(specs[k]), specs[k]["steps"], keep_result=False))
             k += 1
         a, q, d = srv.tick()
         peak = max(peak, a)
@@ -358,24 +363,29 @@ def run_served(args):
     lat = np.array([x["t_done"] - x["t_submit"] for x in info])
     span = max(x["t_done"] for x in info) - min(x["t_submit"] for x in info)
     value = float(work.sum() / span)
+    failures = [{"request": "c5_%04d_%s_N%d" % (specs[i]["k"], specs[i]["kind"], specs[i]["N"]),
+                 "state": info[i]["state"], "error": info[i]["error"]}
+                for i in range(n) if info[i]["state"] != mb.Server.DONE][:10]
     srv.close()
-    # serial plain FP64: one request at a time, FP64 throughout (sample)
-    sample = sorted(range(n), key=lambda i: specs[i]["N"])
-    sample = [sample[0], sample[n // 2], sample[-1]]
-    cells, ms = 0.0, 0.0
+    # serial plain FP64: one request at a time, FP64 throughout, on a seeded
+    # subsample; each sampled request's time = its per-step time x its steps
+    rng = np.random.default_rng(inputs.BASE_SEED + 5)
+    sample = sorted(rng.choice(n, size=min(args.c5_serial_sample, n), replace=False).tolist())
+    t_sample, w_sample = 0.0, 0.0
     for i in sample:
-        s64 = mb.Sim(probs[i], mb.FP64)
+        p = inputs.make_request(specs[i])
+        s64 = mb.Sim(p, mb.FP64)
         s64.set_stream(st.cuda_stream)
         s64.run(1, 0.0)
         s64.sync()
         e0.record(st)
-        s64.run(4, 0.0)
+        s64.run(args.c5_serial_steps, 0.0)
         e1.record(st)
         torch.cuda.synchronize()
-        ms += e0.elapsed_time(e1)
-        cells += probs[i].nx * probs[i].ny * 2 * 4
+        t_sample += e0.elapsed_time(e1) * 1e-3 / args.c5_serial_steps * specs[i]["steps"]
+        w_sample += work[i]
         s64.close()
-    rate64 = cells / (ms * 1e-3)
+    rate64 = w_sample / t_sample
     serial_s = float(work.sum() / rate64)
     if rank != 0:
         return
@@ -388,16 +398,16 @@ def run_served(args):
                                                                       args.c5_smax),
                    "arrivals": "Poisson, mean gap %.4g s = %.2f x batched throughput %.3g cell-updates/s"
                                % (mean_gap, args.c5_load, thr),
-                   "budget_gib": args.c5_budget_gib, "max_active": args.c5_max_active,
-                   "full_stream": "2000 requests, N 256-2048, 500-5000 steps (this run: the bounded prefix above)"},
+                   "budget_gib": args.c5_budget_gib, "max_active": args.c5_max_active},
         "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                       "mean": float(lat.mean())},
-        "requests": n, "failed": failed, "peak_active": peak, "makespan_s": span,
-        "failures": [{"request": probs[i].name, "state": info[i]["state"], "error": info[i]["error"]}
-                     for i in range(n) if info[i]["state"] != mb.Server.DONE][:10],
+        "requests": n, "failed": failed, "peak_active": peak, "makespan_s": span, "total_cell_updates": float(work.sum()),
+        "failures": failures,
         "clocks": summarize_clocks(samples, local),
         "serial_fp64": {"value": rate64, "unit": UNIT, "seconds_for_stream": serial_s,
-                        "extrapolated": "from %d-request sample (4 steps each), one instance at a time" % len(sample)},
+                        "extrapolated": "from a seeded %d-request subsample: each timed over %d steps after one "
+                                        "warm-up step, one instance at a time, scaled by its step count"
+                                        % (len(sample), args.c5_serial_steps)},
         "speedup_vs_serial_fp64": serial_s / span,
     }
     print(json.dumps(line))
@@ -455,6 +465,58 @@ def run_period_accuracy(args):
         "conservation_drift_rel": drift,
         "throughput": {"fp64": cells / t64, "fp32": cells / t32, "unit": UNIT, "seconds": {"fp64": t64, "fp32": t32}},
     }))
+
+
+def run_n1(args):
+    """The paper's sloped-channel validation (Sec. III.A) as read in
+    inputs.n1_channel, on the plain FP64 GPU path (held to the oracle per
+    sweep by tests/test_gpu_configs.py): density error norms against the exact
+    translated profile at t_end on the paper's five grids (160x32 ...
+    2560x512) for the static channel, the moving channel with the paper's
+    donor uncovering and with flux-GCL uncovering, and the paper's
+    CFL-halving study (eq. CFLvarying) on the finest three grids.  Each run
+    takes a fixed step: t_end split into equal steps no longer than the CFL
+    step at t = 0.  Norms over fluid cells, weighted by volume fraction
+    (L1, L2) or not (L_inf)."""
+    import torch
+    from paper_1711_11361_gb300 import inputs, mb
+    torch.cuda.set_device(0)
+
+    def run(level, moving, mode, cfl):
+        p = inputs.n1_channel(level, moving, cfl=cfl)
+        p.uncover_mode = mode
+        s = mb.Sim(p, mb.FP64)
+        dt0 = float(s.step(0.0, report=True)[0])
+        s.close()
+        n = int(math.ceil(p.t_end / dt0))
+        s = mb.Sim(p, mb.FP64)
+        s.run(n, p.t_end / n)
+        status = int(s.sync())
+        g = s.read_state(0, alpha=True)
+        merged = s.merge_count(0)
+        s.close()
+        X, Y = p.cell_centres()
+        a = g["alpha"]
+        fl = a > 0
+        e = np.abs(g["Q"][0][fl] - inputs.n1_exact_density(X, Y, g["t"], p.U[0])[fl])
+        w = a[fl]
+        return {"grid": f"{p.nx}x{p.ny}", "cfl": cfl, "steps": n, "status": status, "merged_cells": merged,
+                "L1": float(np.sum(w * e) / np.sum(w)), "L2": float(math.sqrt(np.sum(w * e * e) / np.sum(w))),
+                "Linf": float(e.max())}
+
+    def orders(rows):
+        for a, b in zip(rows, rows[1:]):
+            b["orders"] = {k: math.log2(a[k] / b[k]) for k in ("L1", "L2", "Linf")}
+        return rows
+
+    out = {"metric": "density error norms of the sloped-channel validation (reading of Sec. III.A)",
+           "dtype": "f64", "data": "synthetic", "config": {"workload": "n1_sloped_channel_5x1_160x32-2560x512"}}
+    out["static"] = orders([run(l, False, inputs.UNCOVER_DONOR, 0.5) for l in range(5)])
+    out["moving_donor"] = orders([run(l, True, inputs.UNCOVER_DONOR, 0.5) for l in range(5)])
+    out["moving_flux_gcl"] = orders([run(l, True, inputs.UNCOVER_FLUX_GCL, 0.5) for l in range(5)])
+    out["moving_donor_cfl_halving"] = orders([run(l, True, inputs.UNCOVER_DONOR, 0.5 / 2 ** (l - 2))
+                                              for l in (2, 3, 4)])
+    print(json.dumps(out))
 
 
 def workload(rank, args):
@@ -569,11 +631,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes of the bulk kernels")
     ap.add_argument("--no-accuracy", action="store_true", help="skip the FP32-vs-FP64 and FP64 single-instance legs")
-    ap.add_argument("--c5-requests", type=int, default=200)
+    ap.add_argument("--c5-requests", type=int, default=2000)
     ap.add_argument("--c5-nmin", type=int, default=256)
-    ap.add_argument("--c5-nmax", type=int, default=1024)
-    ap.add_argument("--c5-smin", type=int, default=50)
-    ap.add_argument("--c5-smax", type=int, default=200)
+    ap.add_argument("--c5-nmax", type=int, default=2048)
+    ap.add_argument("--c5-smin", type=int, default=500)
+    ap.add_argument("--c5-smax", type=int, default=5000)
+    ap.add_argument("--c5-serial-sample", type=int, default=50)
+    ap.add_argument("--c5-serial-steps", type=int, default=4)
     ap.add_argument("--c5-load", type=float, default=0.9)
     ap.add_argument("--c5-budget-gib", type=float, default=32.0)
     ap.add_argument("--c5-max-active", type=int, default=64)
@@ -585,6 +649,8 @@ def main():
         return run_served(args)
     if args.c3_period:
         return run_period_accuracy(args)
+    if args.workload == "n1":
+        return run_n1(args)
 
     import torch
     ws, rank, local = dist_env()

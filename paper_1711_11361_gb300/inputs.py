@@ -194,6 +194,73 @@ def c1_advection(N=100, steps=200):
     return prob
 
 
+# --------------------------------------------------------------------------
+# the paper's sloped-channel validation (Sec. III.A), as read here
+# --------------------------------------------------------------------------
+N1_ANGLE = math.radians(30.0)   # channel walls against the x-axis
+N1_HALF_WIDTH = 0.125           # channel width 0.02 m in a 0.08 m high box
+N1_CENTRE = (1.2, 0.5)          # point of the channel axis at mid-height (t = 0)
+N1_U_AXIAL = 0.5                # gas velocity along the channel, relative to the walls
+N1_AMPLITUDE, N1_WIDTH = 0.2, 0.1
+N1_S0 = -0.4                    # pulse centre on the channel axis at t = 0 (from N1_CENTRE)
+N1_TRAVEL = 0.8                 # distance the pulse travels along the channel by t_end
+
+
+def n1_axis():
+    return np.array([math.cos(N1_ANGLE), math.sin(N1_ANGLE)])
+
+
+def n1_exact_density(x, y, t, V):
+    """Exact density of the sloped-channel case at time t: the Gaussian
+    profile along the channel axis translated with the gas velocity (a
+    contact wave in a uniform flow at uniform pressure)."""
+    a = n1_axis()
+    ug = np.array([V + N1_U_AXIAL * a[0], N1_U_AXIAL * a[1]])
+    s = (x - N1_CENTRE[0]) * a[0] + (y - N1_CENTRE[1]) * a[1] - N1_S0 - float(ug @ a) * t
+    return 1.0 + N1_AMPLITUDE * np.exp(-(s / N1_WIDTH) ** 2)
+
+
+def n1_channel(level=0, moving=True, cfl=0.5):
+    """The paper's sloped-channel validation (Sec. III.A) as read here, in
+    units of the box height (0.08 m) and the sound speed (c = 1):
+    - box 5 x 1 (0.4 m x 0.08 m), grid 160x32 at level 0, doubled per level
+      (the paper's 160x32 ... 2560x512);
+    - two parallel walls at 30 degrees, channel width 0.25 (0.02 m); the solid
+      parts are two parallelograms reaching past the box;
+    - moving: the walls translate in +x at V = 0.3 (static: V = 0);
+    - gas at p = 1/gamma moving with the walls plus 0.5 along the channel, so
+      that it flows along the walls in their frame and their motion exerts no
+      force (the paper removes that force to compare with a static channel);
+    - a Gaussian density perturbation (amplitude 0.2, width 0.1) along the
+      axis, uniform across the channel; exact solution: its translation with
+      the gas velocity, by 0.8 along the channel at t_end;
+    - transmissive box sides, CFL 0.5 (the paper's), donor-mode uncovering."""
+    nx, ny = 160 * 2 ** level, 32 * 2 ** level
+    V = 0.3 if moving else 0.0
+    a = n1_axis()
+    nrm = np.array([-a[1], a[0]])
+    c = np.array(N1_CENTRE)
+    L = 8.0
+    polys = []
+    for side in (-1.0, 1.0):
+        o = c + side * N1_HALF_WIDTH * nrm
+        far = o + side * 3.0 * nrm
+        p0, p1 = o - L * a, o + L * a
+        q1, q0 = far + L * a, far - L * a
+        quad = np.array([p0, p1, q1, q0]) if side < 0 else np.array([p1, p0, q0, q1])
+        # counter-clockwise
+        area = 0.5 * np.sum(quad[:, 0] * np.roll(quad[:, 1], -1) - np.roll(quad[:, 0], -1) * quad[:, 1])
+        polys.append(quad if area > 0 else quad[::-1].copy())
+    ug = np.array([V + N1_U_AXIAL * a[0], N1_U_AXIAL * a[1]])
+    t_end = N1_TRAVEL / float(ug @ a)
+    prob = Problem(f"n1_channel_{'moving' if moving else 'static'}_{nx}x{ny}", nx, ny, 0.0, 0.0, 5.0, 1.0,
+                   bc=(TRANSMISSIVE,) * 4, cfl=cfl, polygons=polys, moving=[1, 1], U=(V, 0.0), t_end=t_end)
+    X, Y = prob.cell_centres()
+    rho = n1_exact_density(X, Y, 0.0, V)
+    prob.Q0 = conserved(rho, ug[0], ug[1], np.full_like(rho, 1.0 / GAMMA))
+    return prob
+
+
 def c2_cylinder(N=400, M=2.0, t_end=0.3, uncover_mode=UNCOVER_DONOR):
     """Cylinder r = 0.1 from (0.15, 0.5) at (0.5 c, 0) meeting a Mach-M shock at
     x = 0.3.  As in the paper's cylinder and wedge tests the body moves with
