@@ -519,6 +519,67 @@ def run_n1(args):
     print(json.dumps(out))
 
 
+def run_n2(args):
+    """The paper's axisymmetric open-ended tube (Sec. III.E) as read in
+    inputs.n2_open_tube, on the FP64 GPU path (held to the oracle per sweep by
+    tests/test_gpu_configs.py), at 94, 189 and 378 cells per diameter (the
+    paper's 1.6 mm and 0.8 mm single-level meshes and its finest AMR level,
+    here as a single-level mesh).  Pressure on the axis is probed after every
+    step at the exit plane and 1.5 D downstream; reported: the time the shock
+    reaches the exit (converted to the paper's start, the piston face at
+    5.5 D with no shock yet) and the peak overpressure at the probe with its
+    time after that, beside the paper's values in the same units (tau =
+    D / sqrt(p/rho) = 0.525 ms for its D = 0.151 m and air)."""
+    import torch
+    from paper_1711_11361_gb300 import inputs, mb
+    torch.cuda.set_device(0)
+    tau_ms = 0.1511 / math.sqrt(101325.0 / 1.225) * 1e3
+    paper = {"exit_time_tau": 1.388 / tau_ms, "peak_overpressure": 98544.0 / 101325.0,
+             "peak_t_ref_tau": 0.398 / tau_ms, "measured_peak_overpressure": 98341.0 / 101325.0,
+             "measured_peak_t_ref_tau": 0.394 / tau_ms, "tau_ms": tau_ms}
+    rows = []
+    for k in args.n2_resolutions:
+        p = inputs.n2_open_tube(k)
+        info = p.n2
+        r2, up, p2 = info["post_shock"]
+        sim = mb.Sim(p, mb.FP64)
+        cells = [info["exit_cell"], info["probe_cell"]]
+        hist = []
+        t = 0.0
+        t0 = time.perf_counter()
+        steps = 0
+        while t < p.t_end:
+            dt = float(sim.step(0.0, report=True)[0])
+            t += dt
+            steps += 1
+            q = sim.probe(0, cells)
+            pr = (p.gamma - 1.0) * (q[3] - 0.5 * (q[1] ** 2 + q[2] ** 2) / q[0])
+            hist.append((t, pr[0], pr[1]))
+        status = int(sim.sync())
+        merged = sim.merge_count(0)
+        sim.close()
+        h = np.array(hist)
+        half = 0.5 * (1.0 + p2)
+        k_exit = int(np.argmax(h[:, 1] > half))
+        ta, tb, pa, pb = h[k_exit - 1, 0], h[k_exit, 0], h[k_exit - 1, 1], h[k_exit, 1]
+        t_exit = ta + (half - pa) * (tb - ta) / (pb - pa)
+        # the start configuration has the shock (shock - face) ahead of a face
+        # at 5.5 D from the exit; the paper's shock starts at the face
+        d = 1.0 / k
+        lead = 3.0 * d * info["shock_speed"] / (info["shock_speed"] - up) / info["shock_speed"]
+        after = h[:, 0] >= t_exit
+        j = int(np.argmax(np.where(after, h[:, 2], -np.inf)))
+        rows.append({"cells_per_D": k, "grid": f"{p.nx}x{p.ny}", "steps": steps, "status": status,
+                     "merged_cells": merged, "seconds": time.perf_counter() - t0,
+                     "exit_time_tau": t_exit + lead, "peak_overpressure": float(h[j, 2] - 1.0),
+                     "peak_t_ref_tau": float(h[j, 0] - t_exit)})
+    print(json.dumps({"metric": "open-ended tube (reading of Sec. III.E): shock exit time and peak overpressure "
+                                "1.5 D downstream on the axis", "dtype": "f64", "data": "synthetic",
+                      "config": {"workload": "n2_axisymmetric_open_tube_10Dx4D"},
+                      "units": "time in tau = D / sqrt(p/rho); overpressure in units of the ambient pressure",
+                      "paper": paper, "runs": rows}))
+
+
 def workload(rank, args):
     from paper_1711_11361_gb300 import inputs
     if args.workload == "c4":
@@ -624,6 +685,8 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--sweep-samples", type=int, default=100, help="steps sampled for the per-sweep p50/p99")
+    ap.add_argument("--n2-resolutions", type=int, nargs="+", default=[94, 189, 378],
+                    help="cells per tube diameter of the open-tube runs")
     ap.add_argument("--c3-period", action="store_true",
                     help="FP32 vs FP64 accuracy of the pitching NACA 0012 workload after one full pitch period")
     ap.add_argument("--accuracy-steps", type=int, default=500,
@@ -651,6 +714,8 @@ def main():
         return run_period_accuracy(args)
     if args.workload == "n1":
         return run_n1(args)
+    if args.workload == "n2":
+        return run_n2(args)
 
     import torch
     ws, rank, local = dist_env()

@@ -49,7 +49,15 @@ typedef enum {
 } mb_status;
 
 enum { MB_BC_TRANSMISSIVE = 0, MB_BC_REFLECTIVE = 1, MB_BC_PERIODIC = 2 };
-enum { MB_EULER = 0, MB_ADVECTION = 1 };
+/* Equations.  MB_EULER_AXISYM: the Euler equations in axisymmetric form
+ * about the line y = y0 (x axial, y - y0 the radius; Sec. III.E models the
+ * open-ended tube this way): the planar sweeps of MB_EULER, and after every
+ * y sweep the geometric source -(1/r) [rho v, rho u v, rho v^2, v (E + p)]
+ * applied explicitly over the sweep's dt to every fluid cell, r at the cell
+ * centre (a reading: the paper does not state how it integrates the
+ * source).  Set y0 = 0 and a reflective y-low side for the axis.  It may
+ * share a batch with MB_EULER instances. */
+enum { MB_EULER = 0, MB_ADVECTION = 1, MB_EULER_AXISYM = 2 };
 enum { MB_UNCOVER_DONOR = 0, MB_UNCOVER_FLUX_GCL = 1 };
 enum { MB_FP64 = 0, MB_FP32 = 1 };
 
@@ -58,7 +66,7 @@ typedef struct {
     int nx, ny;                 /* cells; 8 <= nx, ny <= 16384 */
     double x0, y0, x1, y1;
     int bc[4];                  /* x-low, x-high, y-low, y-high; periodic in pairs */
-    int equation;               /* MB_EULER or MB_ADVECTION */
+    int equation;               /* MB_EULER, MB_ADVECTION or MB_EULER_AXISYM */
     double adv[2];              /* advection velocity (MB_ADVECTION) */
     double cfl;                 /* CFL number on regular cells (Sec. III) */
     int uncover_mode;           /* MB_UNCOVER_DONOR: volume-weighted donor
@@ -209,6 +217,13 @@ mb_status mb_diagnostics(mb_sim *sim, int inst, double *out);
  * memory for the duration of the call and synchronises `stream`.  No paper
  * counterpart: measurement support. */
 mb_status mb_fp64_rate(void *stream, double *fma_per_s);
+
+/* State of instance inst at n cells (ij: n pairs i, j) between steps: out
+ * receives nc planes of n doubles (solid cells NaN), in the batch's
+ * precision rounded to double.  Synchronises the sim's stream; MB_E_INVAL for
+ * a cell outside the grid.  No paper counterpart: probes such as the
+ * pressure history of Sec. III.E. */
+mb_status mb_probe(mb_sim *sim, int inst, int n, const int *ij, double *out);
 
 /* Cells merged by the positivity safeguard (a reading; the paper has none)
  * in all sweeps of instance inst since its state was last written, counted

@@ -58,6 +58,7 @@ class _Config(ctypes.Structure):
         ("vx", ctypes.POINTER(ctypes.c_double)), ("vy", ctypes.POINTER(ctypes.c_double)),
         ("U", ctypes.c_double * 2), ("pivot", ctypes.c_double * 2),
         ("a0", ctypes.c_double), ("a1", ctypes.c_double), ("omega", ctypes.c_double),
+        ("axisym", ctypes.c_int),
     ]
 
 
@@ -90,7 +91,7 @@ def _load():
         lib.or_last_sweep.argtypes = [P, D]
         lib.or_stab_face.argtypes = [ctypes.c_int, ctypes.c_double, D, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                      D, ctypes.c_int, ctypes.c_double, ctypes.c_double, D, D]
-        lib.or_cover_uncover.argtypes = [ctypes.c_int] * 6 + [D, D, D, D, B]
+        lib.or_cover_uncover.argtypes = [ctypes.c_int] * 7 + [D, D, D, D, B]
         lib.or_safeguard.argtypes = [ctypes.c_int] * 4 + [ctypes.c_double, D, B, D]
         lib.or_last_faces.argtypes = [P, D]
         lib.or_last_wall.argtypes = [P, D]
@@ -141,10 +142,11 @@ def stab_face(bf, F, left=None, right=None):
     return out
 
 
-def cover_uncover(alphaA, alphaB, C, mode=UNCOVER_DONOR, periodic=(False, False)):
+def cover_uncover(alphaA, alphaB, C, mode=UNCOVER_DONOR, periodic=(False, False), open_sides=0):
     """Covering / uncovering redistribution of the contents C (nc, ny, nx)
-    between the poses with volume fractions alphaA and alphaB (ny, nx);
-    returns (new contents, status, updated flags)."""
+    between the poses with volume fractions alphaA and alphaB (ny, nx)
+    (open_sides: bit mask of transmissive sides x-low, x-high, y-low,
+    y-high); returns (new contents, status, updated flags)."""
     lib = _load()
     aA = np.ascontiguousarray(alphaA, dtype=np.float64)
     aB = np.ascontiguousarray(alphaB, dtype=np.float64)
@@ -154,7 +156,8 @@ def cover_uncover(alphaA, alphaB, C, mode=UNCOVER_DONOR, periodic=(False, False)
     nc, ny, nx = C.shape
     Cn = np.empty_like(C)
     upd = np.zeros((ny, nx), dtype=np.uint8)
-    r = lib.or_cover_uncover(nx, ny, int(periodic[0]), int(periodic[1]), nc, mode, _dp(aA), _dp(aB), _dp(C),
+    r = lib.or_cover_uncover(nx, ny, int(periodic[0]), int(periodic[1]), int(open_sides), nc, mode, _dp(aA),
+                             _dp(aB), _dp(C),
                              _dp(Cn), upd.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)))
     return Cn, r, upd
 
@@ -207,6 +210,7 @@ class Oracle:
         c.U[0], c.U[1] = prob.U
         c.pivot[0], c.pivot[1] = prob.pivot
         c.a0, c.a1, c.omega = prob.a0, prob.a1, prob.omega
+        c.axisym = 1 if getattr(prob, "axisym", False) else 0
         self._cfg = c
         self._h = self._lib.or_create(ctypes.byref(c))
         if not self._h:

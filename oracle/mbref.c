@@ -23,8 +23,11 @@
  *              massDeficitEquation, cutCellCoverDonation)
  *   Sec. II.C.5 (last paragraph) standard fluxes: MUSCL-Hancock + HLLC + van Leer.
  *
- * Geometry is the plain definition: the body is a union of disjoint closed
- * polygons; cell volume fractions are areas from Sutherland-Hodgman clipping,
+ * Geometry is the plain definition: the body is a union of polygons with
+ * disjoint interiors (two may touch along an edge, as a piston rod sliding in
+ * its tube; areas and solid lengths add over the polygons, and the wall
+ * normal from aperture closure is zero where only such a contact is left in
+ * a cell); cell volume fractions are areas from Sutherland-Hodgman clipping,
  * face apertures are lengths from sorted line/polygon crossings, and the
  * swept (time-averaged) aperture of a face under translation is the fluid
  * fraction of the strip the face sweeps through the body, which is the exact
@@ -68,6 +71,7 @@ typedef struct {
     double U[2];            /* translation velocity */
     double pivot[2];        /* rotation centre at t = 0 */
     double a0, a1, omega;   /* theta(t) = a0 + a1 sin(omega t) */
+    int axisym;             /* Euler in axisymmetric form: y is the radius from the axis y = y0 */
 } or_config;
 
 typedef struct {
@@ -729,10 +733,13 @@ void or_stab_face(int nc, double bf, const double *F, int hasL, double bfarL, do
  * volumeWeighting, cutCellInitialisation), and each donor loses sigma times
  * its own content (eq. cutCellInitialisationDonorCellUpdate); donors are the
  * fluid face neighbours at B that are not themselves uncovered.  With no
- * such face neighbour the 8-neighbourhood is used (a reading).  updated[c]
- * is set for donor-initialised cells.  Returns OR_E_UNSTABLE when a cell
- * has no neighbour to exchange with. */
-static int cover_uncover(int nx, int ny, int perx, int pery, int nc, int mode, const double *alphaA,
+ * such face neighbour the 8-neighbourhood is used (a reading).  A covered
+ * cell on a transmissive side of the domain (open_sides: bit 0 x-low, 1
+ * x-high, 2 y-low, 3 y-high) with no fluid neighbour at all passes its
+ * residual out of the domain (a reading: a body leaving the domain).
+ * updated[c] is set for donor-initialised cells.  Returns OR_E_UNSTABLE when
+ * any other cell has no neighbour to exchange with. */
+static int cover_uncover(int nx, int ny, int perx, int pery, int open_sides, int nc, int mode, const double *alphaA,
                          const double *alphaB, const double *C, double *Cn, unsigned char *updated) {
     const int n = nx * ny;
     int err = OR_OK;
@@ -762,7 +769,16 @@ static int cover_uncover(int nx, int ny, int perx, int pery, int nc, int mode, c
                         asum += alphaB[cc];
                     }
             }
-            if (nnb == 0) { err = OR_E_UNSTABLE; continue; }
+            if (nnb == 0) {
+                const int open = ((open_sides & 1) && i == 0) || ((open_sides & 2) && i == nx - 1) ||
+                                 ((open_sides & 4) && j == 0) || ((open_sides & 8) && j == ny - 1);
+                if (covered && open) {
+                    for (int q = 0; q < nc; ++q) Cn[q * n + c] = 0.0;   /* leaves the domain */
+                } else {
+                    err = OR_E_UNSTABLE;
+                }
+                continue;
+            }
             if (covered) {
                 for (int m = 0; m < nnb; ++m)
                     for (int q = 0; q < nc; ++q) Cn[q * n + nb[m]] += alphaB[nb[m]] / asum * C[q * n + c];
@@ -782,10 +798,10 @@ static int cover_uncover(int nx, int ny, int perx, int pery, int nc, int mode, c
 }
 
 /* cover_uncover on caller arrays (updated may be NULL) */
-int or_cover_uncover(int nx, int ny, int perx, int pery, int nc, int mode, const double *alphaA,
+int or_cover_uncover(int nx, int ny, int perx, int pery, int open_sides, int nc, int mode, const double *alphaA,
                      const double *alphaB, const double *C, double *Cn, unsigned char *updated) {
     unsigned char *u = updated ? updated : (unsigned char *)calloc((size_t)nx * ny, 1);
-    int r = cover_uncover(nx, ny, perx, pery, nc, mode, alphaA, alphaB, C, Cn, u);
+    int r = cover_uncover(nx, ny, perx, pery, open_sides, nc, mode, alphaA, alphaB, C, Cn, u);
     if (!updated) free(u);
     return r;
 }
@@ -864,6 +880,37 @@ static int safeguard(int nx, int ny, int perx, int pery, double g, const double 
 int or_safeguard(int nx, int ny, int perx, int pery, double g, const double *alphaB, const unsigned char *updated,
                  double *Cn) {
     return safeguard(nx, ny, perx, pery, g, alphaB, updated, Cn);
+}
+
+/* Geometric source of the axisymmetric Euler equations (a reading: the
+ * paper models its open-ended tube, Sec. III.E, in axisymmetric form without
+ * stating how the source is integrated).  With x axial and y the radius r
+ * measured from the axis y = y0, the planar fluxes of the sweeps miss the
+ * term -(1/r) [rho v, rho u v, rho v^2, v (E + p)].  It is applied as a step
+ * of its own after every radial (y) sweep, explicitly over the sweep's dt,
+ * to the state of every fluid cell, r taken at the cell centre
+ * (j + 1/2) dy.  Returns OR_E_UNSTABLE when a state turns non-physical. */
+static int axisym_source(or_sim *s, double dt) {
+    const int nx = s->c.nx, ny = s->c.ny, n = nx * ny;
+    const double g = s->c.gamma;
+    int err = OR_OK;
+    for (int j = 0; j < ny; ++j) {
+        const double r = ((double)j + 0.5) * s->dy;
+        for (int i = 0; i < nx; ++i) {
+            const int c = j * nx + i;
+            if (s->Q[c] != s->Q[c]) continue;   /* solid */
+            double q[4] = {s->Q[c], s->Q[n + c], s->Q[2 * n + c], s->Q[3 * n + c]};
+            const double v = q[2] / q[0], p = pressure(g, q);
+            const double f = dt * v / r;
+            s->Q[c] = q[0] - f * q[0];
+            s->Q[n + c] = q[1] - f * q[1];
+            s->Q[2 * n + c] = q[2] - f * q[2];
+            s->Q[3 * n + c] = q[3] - f * (q[3] + p);
+            double qn[4] = {s->Q[c], s->Q[n + c], s->Q[2 * n + c], s->Q[3 * n + c]};
+            if (!(qn[0] > 0.0) || !(pressure(g, qn) > 0.0)) err = OR_E_UNSTABLE;
+        }
+    }
+    return err;
 }
 
 /* Sweep `d` with time step dt.  The body moves by U_d*dt along d (and by half
@@ -1126,7 +1173,11 @@ int or_sweep(or_sim *s, int d, double dt) {
     /* covering / uncovering (Sec. II.C.5), applied simultaneously */
     double *Cn = (double *)malloc(sizeof(double) * nc * n);
     const int perx = s->c.bc[0] == OR_BC_PERIODIC, pery = s->c.bc[2] == OR_BC_PERIODIC;
-    if (cover_uncover(nx, ny, perx, pery, nc, ucov, gA.alpha, gB.alpha, C, Cn, updated) != OR_OK) err = OR_E_UNSTABLE;
+    int open_sides = 0;
+    for (int side = 0; side < 4; ++side)
+        if (s->c.bc[side] == OR_BC_TRANSMISSIVE) open_sides |= 1 << side;
+    if (cover_uncover(nx, ny, perx, pery, open_sides, nc, ucov, gA.alpha, gB.alpha, C, Cn, updated) != OR_OK)
+        err = OR_E_UNSTABLE;
 
     /* positivity safeguard */
     if (s->c.equation == OR_EULER) s->mixed_last = safeguard(nx, ny, perx, pery, g, gB.alpha, updated, Cn);
@@ -1145,6 +1196,9 @@ int or_sweep(or_sim *s, int d, double dt) {
             } else if (!isfinite(s->Q[c])) err = OR_E_UNSTABLE;
         }
     }
+
+    /* geometric source of the axisymmetric form after the radial sweep */
+    if (s->c.axisym && d == 1 && s->c.equation == OR_EULER && axisym_source(s, dt) != OR_OK) err = OR_E_UNSTABLE;
 
     /* advance pose / time */
     s->X = XB; s->Y = YB;

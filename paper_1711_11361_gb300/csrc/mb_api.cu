@@ -40,6 +40,8 @@ template <class T>
 int bulk_blocks_per_sm(int);
 double fp64_probe_rate(cudaStream_t st);
 template <class T>
+void launch_axisym_source(const InstDesc *, InstDyn *, int, int, int, cudaStream_t);
+template <class T>
 void launch_write_state(const InstDesc *, InstDyn *, const double *const *, const double *, int, int, int, int,
                         cudaStream_t);
 template <class T>
@@ -208,6 +210,9 @@ extern "C" {
 
 const char *mb_last_error(const mb_sim *sim) { return sim ? sim->err.c_str() : g_create_error.c_str(); }
 
+// MB_EULER_AXISYM is MB_EULER plus the geometric source step
+static int base_equation(int eq) { return eq == MB_EULER_AXISYM ? MB_EULER : eq; }
+
 // checks of one instance against the batch's precision and equation
 static const char *check_instance(const mb_grid &g, const mb_body &b, int prec, int eq) {
     if (g.nx < 8 || g.ny < 8 || g.nx > 16384 || g.ny > 8192) return "grid size out of range";
@@ -215,9 +220,11 @@ static const char *check_instance(const mb_grid &g, const mb_body &b, int prec, 
     if ((g.bc[0] == MB_BC_PERIODIC) != (g.bc[1] == MB_BC_PERIODIC) ||
         (g.bc[2] == MB_BC_PERIODIC) != (g.bc[3] == MB_BC_PERIODIC))
         return "periodic boundaries must come in pairs";
-    if (g.equation != MB_EULER && g.equation != MB_ADVECTION) return "unknown equation";
+    if (g.equation != MB_EULER && g.equation != MB_ADVECTION && g.equation != MB_EULER_AXISYM)
+        return "unknown equation";
     if (g.precision != prec) return "all instances of a batch share one precision";
-    if (g.equation != eq) return "all instances of a batch share one equation";
+    if (base_equation(g.equation) != base_equation(eq)) return "all instances of a batch share one equation";
+    if (g.equation == MB_EULER_AXISYM && !(g.y0 == 0.0)) return "axisymmetric instances need y0 = 0 (the axis)";
     if (!(g.cfl > 0.0 && g.cfl <= 1.0)) return "cfl must be in (0, 1]";
     if (b.npoly < 0 || (b.npoly > 0 && (!b.poly_start || !b.poly_moving || !b.vx || !b.vy))) return "bad body";
     for (int p = 0; p < b.npoly; ++p)
@@ -232,7 +239,7 @@ static void describe_instance(int prec, int yseg, const mb_grid &g, double gamma
     memset(&I, 0, sizeof(I));
     I.nx = g.nx; I.ny = g.ny;
     I.pitch = (g.nx + 31) / 32 * 32;
-    I.nc = g.equation == MB_EULER ? 4 : 1;
+    I.nc = base_equation(g.equation) == MB_EULER ? 4 : 1;
     I.x0 = g.x0; I.y0 = g.y0;
     I.dx = (g.x1 - g.x0) / (double)g.nx;
     I.dy = (g.y1 - g.y0) / (double)g.ny;
@@ -241,7 +248,8 @@ static void describe_instance(int prec, int yseg, const mb_grid &g, double gamma
     I.rdxf = (float)I.rdx;
     I.rdyf = (float)I.rdy;
     for (int q = 0; q < 4; ++q) I.bc[q] = g.bc[q];
-    I.eq = g.equation;
+    I.eq = base_equation(g.equation);
+    I.axisym = g.equation == MB_EULER_AXISYM ? 1 : 0;
     I.ucov = g.uncover_mode;
     I.adv[0] = g.adv[0]; I.adv[1] = g.adv[1];
     I.gamma = gamma;
@@ -288,7 +296,7 @@ static void describe_instance(int prec, int yseg, const mb_grid &g, double gamma
     // thread) and 64-row segment
     I.tiles_x[0] = 1;
     I.ntiles[0] = g.ny;
-    const int ycols = (prec == MB_FP32 && g.equation == MB_EULER) ? 64 : 32;
+    const int ycols = (prec == MB_FP32 && base_equation(g.equation) == MB_EULER) ? 64 : 32;
     I.tiles_x[1] = (g.nx + ycols - 1) / ycols;
     I.yseg = yseg;
     I.ntiles[1] = I.tiles_x[1] * ((g.ny + yseg - 1) / yseg);
@@ -439,7 +447,7 @@ mb_status mb_batch_create(int n, const mb_grid *grids, const double *gammas, con
     }
     mb_sim *s = new mb_sim();
     s->prec = grids[0].precision;
-    s->eq = grids[0].equation;
+    s->eq = base_equation(grids[0].equation);
 #define CK(x)                                                     \
     do {                                                          \
         cudaError_t _e = (x);                                     \
@@ -667,6 +675,15 @@ static mb_status do_sweep(mb_sim *s, int dir, double dt) {
     if (!(two_pass && !s->timing)) band(2, st);
     band(3, st);
     band(4, st);
+    if (dir == 1 && s->eq == MB_EULER) {
+        // geometric source of the axisymmetric instances after the radial sweep
+        bool axi = false;
+        for (const auto &I : s->hd) axi = axi || I.axisym;
+        if (axi) {
+            if (s->prec == MB_FP32) launch_axisym_source<float>(s->dd, s->dy, s->n, s->total_tiles[0], dst, st);
+            else launch_axisym_source<double>(s->dd, s->dy, s->n, s->total_tiles[0], dst, st);
+        }
+    }
     if (s->sidx == 1) {
         s->cur = dst;
         s->sidx = 0;
@@ -990,6 +1007,36 @@ mb_status mb_diagnostics(mb_sim *sim, int inst, double *out) {
     for (int q = 0; q < 4; ++q) out[q] = y.wall_sum[q];
     out[4] = y.mixed;
     out[5] = y.band_count;
+    return MB_OK;
+}
+
+mb_status mb_probe(mb_sim *sim, int inst, int n, const int *ij, double *out) {
+    if (!sim || inst < 0 || inst >= sim->n || n < 0 || (n > 0 && (!ij || !out))) return MB_E_INVAL;
+    if (sim->sidx != 0) return fail(sim, MB_E_STATE, "mb_probe in the middle of a step");
+    const InstDesc &I = sim->hd[inst];
+    const size_t esz = sim->prec == MB_FP32 ? 4 : 8;
+    const size_t plane = (size_t)I.pitch * I.ny;
+    std::vector<unsigned char> raw((size_t)n * I.nc * 8);
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < n && e == cudaSuccess; ++k) {
+        const int i = ij[2 * k], j = ij[2 * k + 1];
+        if (i < 0 || i >= I.nx || j < 0 || j >= I.ny) return fail(sim, MB_E_INVAL, "mb_probe: cell outside the grid");
+        for (int q = 0; q < I.nc && e == cudaSuccess; ++q) {
+            const unsigned char *src = (const unsigned char *)I.Q[sim->cur] + ((size_t)q * plane + (size_t)j * I.pitch + i) * esz;
+            e = cudaMemcpyAsync(raw.data() + ((size_t)q * n + k) * 8, src, esz, cudaMemcpyDeviceToHost, sim->stream);
+        }
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(sim->stream);
+    if (e != cudaSuccess) return cuda_check(sim, e, "probe");
+    for (size_t m = 0; m < (size_t)n * I.nc; ++m) {
+        if (esz == 4) {
+            float f;
+            memcpy(&f, raw.data() + m * 8, 4);
+            out[m] = f;
+        } else {
+            memcpy(&out[m], raw.data() + m * 8, 8);
+        }
+    }
     return MB_OK;
 }
 

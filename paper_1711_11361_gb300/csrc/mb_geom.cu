@@ -1197,9 +1197,15 @@ __device__ __forceinline__ void geom_group(int gw, const InstDesc *__restrict__ 
         const double db = fabs(blo - bhi);
         const double ahat = aM - dmin(blo, bhi);
         r.d = db > 0.0 ? clamp01(ahat / db) : 1.0;
+        // Where two bodies touch along an edge (a piston sliding in a tube),
+        // their edges cancel in this sum and no fluid boundary is left; the
+        // sum keeps a rounding residual of about eps x the edge length, which
+        // must not be normalised into a unit normal.  A wall in a cell with
+        // alpha >= ALPHA_MIN is at least ~1e-5 of the cell size long.
         const double L = sqrt(nlx * nlx + nly * nly);
-        r.nx = L > 0.0 ? nlx / L : 0.0;
-        r.ny = L > 0.0 ? nly / L : 0.0;
+        const bool wall = L > 1e-9 * fmax(I.dx, I.dy);
+        r.nx = wall ? nlx / L : 0.0;
+        r.ny = wall ? nly / L : 0.0;
         double wx = 0.0, wy = 0.0;
         if (fl & RF_MOVING) {
             const double xc = I.x0 + ((double)i + 0.5) * I.dx, yc = I.y0 + ((double)j + 0.5) * I.dy;

@@ -80,6 +80,7 @@ struct InstDesc {
     const double *xn, *yn;      // grid-line coordinates x_0..x_nx, y_0..y_ny (device)
     int bc[4];
     int eq;
+    int axisym;          // Euler in axisymmetric form: geometric source after every y sweep
     int ucov;
     double adv[2];
     double gamma, cfl;

@@ -99,7 +99,8 @@ const char *mb_server_last_error(const mb_server *srv) { return srv ? srv->err.c
 
 mb_status mb_server_submit(mb_server *srv, const mb_request *r, int *id) {
     if (!srv || !r || !r->Q0 || r->nsteps < 0) return MB_E_INVAL;
-    if (r->grid.precision != srv->precision || r->grid.equation != srv->equation)
+    const int req_eq = r->grid.equation == MB_EULER_AXISYM ? MB_EULER : r->grid.equation;
+    if (r->grid.precision != srv->precision || req_eq != srv->equation)
         return srv_fail(srv, MB_E_INVAL, "request precision or equation differs from the server's");
     const mb_body &b = r->body;
     if (b.npoly < 0 || (b.npoly > 0 && (!b.poly_start || !b.poly_moving || !b.vx || !b.vy)))
@@ -119,7 +120,7 @@ mb_status mb_server_submit(mb_server *srv, const mb_request *r, int *id) {
         q.pstart.assign(1, 0);
         q.pmov.assign(1, 0);
     }
-    const int nc = r->grid.equation == MB_EULER ? 4 : 1;
+    const int nc = req_eq == MB_EULER ? 4 : 1;
     q.Q0.assign(r->Q0, r->Q0 + (size_t)nc * r->grid.nx * r->grid.ny);
     q.t0 = r->t0;
     q.nsteps = r->nsteps;

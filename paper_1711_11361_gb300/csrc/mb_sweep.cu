@@ -305,8 +305,13 @@ __device__ __forceinline__ void band_prep_rec(const InstDesc *__restrict__ D, In
             if (found) use8 = pass;
         }
         if (!found) {
+            // a covered cell on a transmissive side with no fluid neighbour
+            // (a body leaving the domain) passes its residual out of the
+            // domain: no recipient gathers it; any other such event fails
+            const bool open = (i == 0 && I.bc[0] == 0) || (i == I.nx - 1 && I.bc[1] == 0) ||
+                              (j == 0 && I.bc[2] == 0) || (j == I.ny - 1 && I.bc[3] == 0);
             b.flags |= RF_NONBR;
-            atomicOr(&y.err, ERR_NONBR);
+            if (!((b.flags & RF_COVER) && open)) atomicOr(&y.err, ERR_NONBR);
             b.den = 0.0;
         } else {
             if (use8) b.flags |= RF_USE8;
@@ -1121,19 +1126,18 @@ __device__ __forceinline__ void bulk_x_far(const InstDesc &I, InstDyn &y, XRing<
         evolve2<0>(g1, lam, qm, q0, qp, true, true, QL, QRc);
     }
     float2 Fprev[4];
+    float2 qprev[4];   // states of the previous chunk's two cells (as loaded there)
     // new states of chunk c - 1 (F: this chunk's fluxes, whose lane 0 holds
     // the high face of the previous chunk's lane 31; tail: none)
     auto update = [&](int c, const float2 *F, bool tail) {
         const int ap = 64 * (c - 1) + 2 * lane;
-        const int pp = ap & (XRN - 1);
         float2 qn[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const float dn = __shfl_down_sync(0xffffffffu, Fprev[k].x, 1);
             const float nx0 = tail ? 0.0f : __shfl_sync(0xffffffffu, F[k].x, 0);
             const float2 Fhi = make_float2(Fprev[k].y, lane == 31 ? nx0 : dn);
-            const float2 qo = *(const float2 *)&rg.q[k][pp];
-            qn[k] = fma2(P2(lam), sub2(Fprev[k], Fhi), qo);
+            qn[k] = fma2(P2(lam), sub2(Fprev[k], Fhi), qprev[k]);
         }
         const int st = (ap < n ? 1 : 0) | (ap + 1 < n ? 2 : 0);
         if (st == 3) {
@@ -1185,7 +1189,10 @@ __device__ __forceinline__ void bulk_x_far(const InstDesc &I, InstDyn &y, XRing<
         QRc.ir.x = __shfl_sync(0xffffffffu, QR.ir.y, 31);
         QRc.p.x = __shfl_sync(0xffffffffu, QR.p.y, 31);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) Fprev[k] = F[k];
+        for (int k = 0; k < 4; ++k) {
+            Fprev[k] = F[k];
+            qprev[k] = q0[k];
+        }
     }
     // the row's last chunk (the face past its lane 31 lies beyond face n)
     update(c_last + 1, Fprev, true);
@@ -1558,14 +1565,16 @@ __device__ __forceinline__ void bulk_y_far(const InstDesc &I, InstDyn &y, YRing 
     for (int r = j0 - 2; r < j0 - 2 + YR; ++r) prefetch(r);
     cp_async_wait<YR - 4>();   // rows j0-2 .. j0+1 complete
     __syncwarp();
+    // rows f and f+1 carry over to the next row step (as its rows f-1 and f)
+    float2 qm[4], qc[4], qp[4];
     E2 QRc;
     {
-        float2 qa[4], qm[4], qc[4];
+        float2 qa[4];
         row(j0 - 2, qa);
-        row(j0 - 1, qm);
-        row(j0, qc);
+        row(j0 - 1, qc);
+        row(j0, qp);
         E2 QL;
-        evolve2<1>(g1, lam, qa, qm, qc, true, true, QL, QRc);
+        evolve2<1>(g1, lam, qa, qc, qp, true, true, QL, QRc);
     }
     float2 Fprev[4];
     float *__restrict__ wp = Qo + (size_t)(j0 - 1) * pitch + i;   // row f-1 of this thread's columns
@@ -1574,20 +1583,18 @@ __device__ __forceinline__ void bulk_y_far(const InstDesc &I, InstDyn &y, YRing 
         prefetch(f + YR - 2);
         cp_async_wait<YR - 4>();   // rows up to f + 2 complete
         __syncwarp();
-        float2 qm[4], qc[4], qp[4];
-        if (f >= 1 && f + 1 < n) {
-            // rows f-1, f, f+1 (lanes past the grid compute on values that
-            // are never stored)
-            const int sm_ = (f - j0 + 1) & (YR - 1), sc = (f - j0 + 2) & (YR - 1), sp = (f - j0 + 3) & (YR - 1);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                qm[k] = *(const float2 *)&rg.q[sm_][k][2 * lane];
-                qc[k] = *(const float2 *)&rg.q[sc][k][2 * lane];
-                qp[k] = *(const float2 *)&rg.q[sp][k][2 * lane];
-            }
+        for (int k = 0; k < 4; ++k) {
+            qm[k] = qc[k];
+            qc[k] = qp[k];
+        }
+        if (f + 1 < n) {
+            // row f+1 (lanes past the grid compute on values that are never
+            // stored)
+            const int sp = (f - j0 + 3) & (YR - 1);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) qp[k] = *(const float2 *)&rg.q[sp][k][2 * lane];
         } else {
-            row(f - 1, qm);
-            row(f, qc);
             row(f + 1, qp);
         }
         E2 QL, QR;
@@ -1877,6 +1884,70 @@ __global__ void __launch_bounds__(128, MINB) k_bulk_y_p(const InstDesc *__restri
         for (int k = 0; k < 4; ++k) Fprev[k] = F[k];
     }
     finish_warp<float>(y, last != 0, s0, s1);
+}
+
+// ---------------------------------------------------------------------------
+// Geometric source of the axisymmetric Euler equations after a y sweep (a
+// reading; Sec. III.E models its open-ended tube in axisymmetric form): with
+// x axial and y the radius from the axis y = y0 = 0, every fluid cell gets
+// Q -= dt (v / r) [rho, rho u, rho v, E + p], r at the cell centre.  One warp
+// per grid row; instances of the batch without the flag return at once.  In
+// FP64 every operation is rounded on its own (no contraction), in the order
+// of the plain definition.
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void __launch_bounds__(256) k_axisym_source(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y,
+                                                       int n_inst, int total_warps, int buf) {
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (gw >= total_warps) return;
+    const int inst = find_inst_warp(D, n_inst, gw, 0);
+    const InstDesc &I = D[inst];
+    if (!I.axisym || I.eq != 0) return;
+    InstDyn &y = Y[inst];
+    const int j = gw - I.tile_off[0];
+    const size_t plane = (size_t)I.pitch * I.ny;
+    T *__restrict__ Q = (T *)I.Q[buf] + (size_t)j * I.pitch;
+    const double r = __dmul_rn(__dadd_rn((double)j, 0.5), I.dy);
+    const double dt = y.dt;
+    bool bad = false;
+    for (int i = lane; i < I.nx; i += 32) {
+        const T q0 = Q[i], q1 = Q[plane + i], q2 = Q[2 * plane + i], q3 = Q[3 * plane + i];
+        if (!(q0 == q0)) continue;   // solid
+        T n0, n1, n2, n3, pn;
+        if (sizeof(T) == 8) {
+            const double g1 = __dsub_rn(I.gamma, 1.0);
+            const double p = __dmul_rn(g1, __dsub_rn(q3, __ddiv_rn(__dmul_rn(0.5, __dadd_rn(__dmul_rn(q1, q1),
+                                                                                           __dmul_rn(q2, q2))), q0)));
+            const double f = __ddiv_rn(__dmul_rn(dt, __ddiv_rn(q2, q0)), r);
+            n0 = (T)__dsub_rn(q0, __dmul_rn(f, q0));
+            n1 = (T)__dsub_rn(q1, __dmul_rn(f, q1));
+            n2 = (T)__dsub_rn(q2, __dmul_rn(f, q2));
+            n3 = (T)__dsub_rn(q3, __dmul_rn(f, __dadd_rn(q3, p)));
+            pn = (T)__dmul_rn(g1, __dsub_rn(n3, __ddiv_rn(__dmul_rn(0.5, __dadd_rn(__dmul_rn(n1, n1),
+                                                                                  __dmul_rn(n2, n2))), n0)));
+        } else {
+            const float g1 = (float)I.gamma - 1.0f;
+            const float p = g1 * (q3 - 0.5f * (q1 * q1 + q2 * q2) / q0);
+            const float f = (float)dt * (q2 / q0) / (float)r;
+            n0 = q0 - f * q0;
+            n1 = q1 - f * q1;
+            n2 = q2 - f * q2;
+            n3 = q3 - f * (q3 + p);
+            pn = g1 * (n3 - 0.5f * (n1 * n1 + n2 * n2) / n0);
+        }
+        Q[i] = n0;
+        Q[plane + i] = n1;
+        Q[2 * plane + i] = n2;
+        Q[3 * plane + i] = n3;
+        if (!(n0 > (T)0) || !(pn > (T)0)) bad = true;
+    }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&y.err, ERR_UNSTABLE);
+}
+
+template <class T>
+void launch_axisym_source(const InstDesc *D, InstDyn *Y, int n_inst, int total_rows, int buf, cudaStream_t st) {
+    if (total_rows > 0) k_axisym_source<T><<<(total_rows + 7) / 8, 256, 0, st>>>(D, Y, n_inst, total_rows, buf);
 }
 
 // ---------------------------------------------------------------------------
@@ -2792,6 +2863,7 @@ void launch_read_state(const InstDesc *D, double *const *ptrs, double *p1, int i
     template void launch_bulk<T>(int, int, const InstDesc *, InstDyn *, const BandRec *, int, int, int, int, int,  \
                                  int, int, DeferList, int, cudaStream_t);                                               \
     template int bulk_blocks_per_sm<T>(int);                                                                       \
+    template void launch_axisym_source<T>(const InstDesc *, InstDyn *, int, int, int, cudaStream_t);               \
     template void launch_write_state<T>(const InstDesc *, InstDyn *, const double *const *, const double *, int,  \
                                         int, int, int, cudaStream_t);                                             \
     template void launch_read_state<T>(const InstDesc *, double *const *, double *, int, int, int, int, cudaStream_t);

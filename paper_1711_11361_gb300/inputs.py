@@ -50,6 +50,7 @@ class Problem:
     Q0: Optional[np.ndarray] = None           # (nc, ny, nx) conserved variables
     steps: int = 0
     t_end: float = 0.0
+    axisym: bool = False                      # Euler in axisymmetric form (y: radius from the axis y = y0)
 
     @property
     def nc(self) -> int:
@@ -258,6 +259,65 @@ def n1_channel(level=0, moving=True, cfl=0.5):
     X, Y = prob.cell_centres()
     rho = n1_exact_density(X, Y, 0.0, V)
     prob.Q0 = conserved(rho, ug[0], ug[1], np.full_like(rho, 1.0 / GAMMA))
+    return prob
+
+
+# --------------------------------------------------------------------------
+# the paper's axisymmetric open-ended tube (Sec. III.E), as read here
+# --------------------------------------------------------------------------
+N2_MACH = 1.76
+N2_EXIT = 6.0          # tube exit plane (the tube runs from the left side)
+N2_PISTON = 0.5        # piston face at t = 0 (5.5 D from the exit)
+N2_WALL = 0.1          # tube wall thickness (not given in the paper; a reading)
+N2_PROBE = 1.5         # pressure probe: on the axis, 1.5 D downstream of the exit
+
+
+def n2_piston_speed(M=N2_MACH, gamma=GAMMA):
+    """Piston speed that drives a Mach-M shock into gas at rest (rho = p = 1)."""
+    c1 = math.sqrt(gamma)
+    return 2.0 / (gamma + 1.0) * (M - 1.0 / M) * c1
+
+
+def n2_open_tube(cells_per_d=94, t_after_exit=1.2):
+    """The paper's axisymmetric open-ended tube (Sec. III.E) as read here, in
+    units of the tube diameter D and the pre-shock state (rho = p = 1):
+    - box 10 D x 4 D, x axial, y the radius (reflective axis at y = 0,
+      transmissive elsewhere), cells_per_d cells per D (the paper's 1.6 mm,
+      0.8 mm and 0.4 mm cells are about 94, 189 and 378 per D for the D that
+      its shock-exit time implies, 0.151 m);
+    - the tube: a fixed wall of thickness 0.1 D (not given) at radius 0.5 D
+      from outside the box to the exit plane x = 6 D;
+    - the piston: a rod filling the tube from outside the box to its face at
+      x = 0.5 D (5.5 D from the exit), moving at the speed that drives a
+      Mach 1.76 shock into gas at rest (0.993 c);
+    - gas at rest, started from the exact planar piston solution at the time
+      the shock is three cells ahead of the piston face (not impulsively);
+    - body sides kept off the grid lines by a fraction of a cell;
+    - run until t_after_exit after the planar shock reaches the exit."""
+    k = cells_per_d
+    if k < 25:
+        # the tube wall must span a few cells: content exchanges between face
+        # neighbours (covering, the safeguard) would otherwise cross it
+        raise ValueError("n2_open_tube needs at least 25 cells per diameter (tube wall >= 2.5 cells)")
+    nx, ny = 10 * k, 4 * k
+    d = 1.0 / k
+    off, ox = 0.3183 * d, 0.2718 * d
+    up = n2_piston_speed()
+    r_in = 0.5 + off
+    tube = rect_polygon(-0.5, r_in, N2_EXIT + ox, r_in + N2_WALL)
+    rod = rect_polygon(-20.0, -0.1, N2_PISTON + ox, r_in)
+    Ms, S, r2, p2 = piston_shock(up)
+    face = N2_PISTON + ox
+    shock = face + 3.0 * d * S / (S - up)
+    t_exit = (N2_EXIT + ox - shock) / S
+    prob = Problem(f"n2_open_tube_{k}perD", nx, ny, 0.0, 0.0, 10.0, 4.0,
+                   bc=(TRANSMISSIVE, TRANSMISSIVE, REFLECTIVE, TRANSMISSIVE), cfl=0.5, polygons=[tube, rod],
+                   moving=[0, 1], U=(up, 0.0), pivot=(0.0, 0.0), axisym=True, t_end=t_exit + t_after_exit)
+    X, Y = prob.cell_centres()
+    inside = (X + 0.5 * d > face) & (X < shock) & (Y < r_in)
+    prob.Q0 = conserved(np.where(inside, r2, 1.0), np.where(inside, up, 0.0), 0.0, np.where(inside, p2, 1.0))
+    prob.n2 = dict(t_exit=t_exit, shock_speed=S, post_shock=(r2, up, p2), mach=Ms,
+                   probe_cell=(int((N2_EXIT + ox + N2_PROBE) / d), 0), exit_cell=(int((N2_EXIT + ox) / d), 0))
     return prob
 
 

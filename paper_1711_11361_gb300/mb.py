@@ -27,7 +27,7 @@ EXPORTS = ["mb_create", "mb_batch_create", "mb_destroy", "mb_last_error", "mb_se
            "mb_request_bytes", "mb_server_create", "mb_server_destroy", "mb_server_last_error", "mb_server_submit",
            "mb_server_tick", "mb_server_query", "mb_server_request_error", "mb_autotune", "mb_set_overlap",
            "mb_write_states", "mb_read_states", "mb_graph_kernels", "mb_set_sweep_event",
-           "mb_merge_count", "mb_fp64_rate"]
+           "mb_merge_count", "mb_fp64_rate", "mb_probe"]
 
 
 class Grid(ctypes.Structure):
@@ -108,6 +108,7 @@ def _load():
         "mb_set_sweep_event": ([P, P], I),
         "mb_merge_count": ([P, I, ctypes.POINTER(ctypes.c_longlong)], I),
         "mb_fp64_rate": ([P, D], I),
+        "mb_probe": ([P, I, I, ctypes.POINTER(ctypes.c_int), D], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -129,7 +130,7 @@ def _marshal(prob: inputs.Problem, precision: int):
     g.x0, g.y0, g.x1, g.y1 = prob.x0, prob.y0, prob.x1, prob.y1
     for k in range(4):
         g.bc[k] = prob.bc[k]
-    g.equation = prob.equation
+    g.equation = 2 if getattr(prob, "axisym", False) else prob.equation   # MB_EULER_AXISYM
     g.adv[0], g.adv[1] = prob.adv
     g.cfl = prob.cfl
     g.uncover_mode = prob.uncover_mode
@@ -272,6 +273,14 @@ class Sim:
         self._check(lib.mb_diagnostics(self._h, inst, _dp(o)))
         return dict(wall=o[:4], mixed=int(o[4]), band=int(o[5]))
 
+    def probe(self, inst, cells):
+        """States at the given (i, j) cells between steps (mb_probe): array (nc, len(cells))."""
+        ij = np.ascontiguousarray(np.asarray(cells, dtype=np.int32).reshape(-1))
+        n = ij.size // 2
+        out = np.empty((self.problems[inst].nc, n))
+        self._check(lib.mb_probe(self._h, inst, n, ij.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(out)))
+        return out
+
     def merge_count(self, inst=0):
         """Cells merged by the positivity safeguard since the instance's state was written (mb_merge_count)."""
         c = ctypes.c_longlong()
@@ -387,14 +396,17 @@ class Server:
         if r != MB_OK:
             raise MBError(r, lib.mb_server_last_error(self._h).decode())
 
-    def submit(self, prob: inputs.Problem, nsteps: int, Q0=None, t0=0.0) -> int:
+    def submit(self, prob: inputs.Problem, nsteps: int, Q0=None, t0=0.0, keep_result=True) -> int:
+        """Queue a request (the library copies its description and initial
+        state).  keep_result=False: the final state is not returned."""
         g, b, m, keep = _marshal(prob, self.precision)
         Q0 = np.ascontiguousarray(prob.Q0 if Q0 is None else Q0, dtype=np.float64)
-        out = np.full((prob.nc, prob.ny, prob.nx), np.nan)
-        req = Request(g, prob.gamma, b, m, _dp(Q0), t0, nsteps, _dp(out))
+        out = np.full((prob.nc, prob.ny, prob.nx), np.nan) if keep_result else None
+        req = Request(g, prob.gamma, b, m, _dp(Q0), t0, nsteps, _dp(out) if keep_result else None)
         k = ctypes.c_int()
         self._check(lib.mb_server_submit(self._h, ctypes.byref(req), ctypes.byref(k)))
-        self.out[k.value] = out
+        if keep_result:
+            self.out[k.value] = out
         return k.value
 
     def tick(self):

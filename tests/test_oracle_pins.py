@@ -178,6 +178,21 @@ def test_flux_gcl_mode_leaves_uncovered_cells_to_the_update():
     assert abs(Cn[0, 0, 1] - 1.25) < 1e-15 and abs(Cn[0, 1, 0] - 1.25) < 1e-15
 
 
+def test_covered_cell_on_an_open_side_passes_its_residual_out():
+    """A body leaving through a transmissive side: the covered cell in the
+    last column has no fluid neighbour left, so its residual (0.7) leaves
+    the domain instead of failing the sweep; on a closed side it fails."""
+    aA = np.zeros((3, 3))
+    aA[1, 2] = 0.3
+    aB = np.zeros((3, 3))
+    C = np.zeros((1, 3, 3))
+    C[0, 1, 2] = 0.7
+    Cn, r, _ = oracle.cover_uncover(aA, aB, C, oracle.UNCOVER_DONOR, open_sides=2)
+    assert r == 0 and Cn[0, 1, 2] == 0.0 and Cn.sum() == 0.0
+    _, r, _ = oracle.cover_uncover(aA, aB, C, oracle.UNCOVER_DONOR, open_sides=1)
+    assert r == -4
+
+
 def test_event_without_any_fluid_neighbour_is_reported():
     aB = np.zeros((3, 3))
     aB[1, 1] = 0.5
