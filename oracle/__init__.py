@@ -92,7 +92,7 @@ def _load():
         lib.or_stab_face.argtypes = [ctypes.c_int, ctypes.c_double, D, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                      D, ctypes.c_int, ctypes.c_double, ctypes.c_double, D, D]
         lib.or_cover_uncover.argtypes = [ctypes.c_int] * 7 + [D, D, D, D, B]
-        lib.or_safeguard.argtypes = [ctypes.c_int] * 4 + [ctypes.c_double, D, B, D]
+        lib.or_safeguard.argtypes = [ctypes.c_int] * 4 + [ctypes.c_double, D, D, B, D]
         lib.or_last_faces.argtypes = [P, D]
         lib.or_last_wall.argtypes = [P, D]
         _lib = lib
@@ -162,15 +162,18 @@ def cover_uncover(alphaA, alphaB, C, mode=UNCOVER_DONOR, periodic=(False, False)
     return Cn, r, upd
 
 
-def safeguard(alphaB, C, updated=None, gamma=1.4, periodic=(False, False)):
+def safeguard(alphaB, C, updated=None, gamma=1.4, periodic=(False, False), alphaA=None):
     """Positivity safeguard on Euler contents C (4, ny, nx); returns (merged
-    contents, cells merged)."""
+    contents, cells merged).  With alphaA (the volume fractions at the start
+    of the sweep), cells that kept less than 1% of their volume also seed the
+    first merge."""
     lib = _load()
     aB = np.ascontiguousarray(alphaB, dtype=np.float64)
+    aA = None if alphaA is None else np.ascontiguousarray(alphaA, dtype=np.float64)
     Cn = np.array(C, dtype=np.float64, order="C", copy=True)
     _, ny, nx = Cn.shape
     upd = np.ascontiguousarray(np.ones((ny, nx), dtype=np.uint8) if updated is None else updated, dtype=np.uint8)
-    m = lib.or_safeguard(nx, ny, int(periodic[0]), int(periodic[1]), gamma, _dp(aB),
+    m = lib.or_safeguard(nx, ny, int(periodic[0]), int(periodic[1]), gamma, None if aA is None else _dp(aA), _dp(aB),
                          upd.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)), _dp(Cn))
     return Cn, m
 

@@ -41,6 +41,7 @@
 #include <string.h>
 
 #define OR_MIX_LAYERS 8   /* merges of the positivity safeguard per sweep */
+#define OR_COLLAPSE 0.01  /* a cell keeping less of its volume over a sweep seeds a merge */
 #define OR_EULER 0
 #define OR_ADVECTION 1
 #define OR_BC_TRANSMISSIVE 0
@@ -812,9 +813,16 @@ int or_cover_uncover(int nx, int ny, int perx, int pery, int open_sides, int nc,
  * such cells and their neighbours shares its total content in proportion to
  * the volume fractions alphaB.  Cells still non-physical after a merge seed
  * the next one, which reaches one layer of neighbours further, up to
- * OR_MIX_LAYERS merges.  Exactly conservative.  Cn is updated in place;
- * returns the number of cells merged (summed over the merges). */
-static int safeguard(int nx, int ny, int perx, int pery, double g, const double *alphaB,
+ * OR_MIX_LAYERS merges.  The first merge is also seeded by every cell that
+ * kept less than OR_COLLAPSE of its volume over the sweep (0 < alphaB <
+ * OR_COLLAPSE alphaA; alphaA may be NULL): the stabilised update leaves such
+ * a cell a content of the order of its shielded volume at the mid pose
+ * (Sec. II.C.4), so its state, content / alphaB, is amplified by up to
+ * alphaA / alphaB -- the growth of the state as the volume fraction
+ * vanishes that Sec. II.C.1 describes -- and can be physical but far out
+ * of range.  Exactly conservative.  Cn is updated in place; returns the
+ * number of cells merged (summed over the merges). */
+static int safeguard(int nx, int ny, int perx, int pery, double g, const double *alphaA, const double *alphaB,
                      const unsigned char *updated, double *Cn) {
     const int n = nx * ny;
     int mixed = 0;
@@ -829,6 +837,7 @@ static int safeguard(int nx, int ny, int perx, int pery, double g, const double 
             double q[4] = {Cn[c] / aB, Cn[n + c] / aB, Cn[2 * n + c] / aB, Cn[3 * n + c] / aB};
             int b = !(q[0] > 0.0) || !(pressure(g, q) > 0.0);
             for (int k = 0; k < 4; ++k) if (!isfinite(q[k])) b = 1;
+            if (layer == 0 && alphaA && aB < OR_COLLAPSE * alphaA[c]) b = 1;
             if (b) { bad[c] = 1; nbad++; }
         }
         if (nbad) {
@@ -877,9 +886,9 @@ static int safeguard(int nx, int ny, int perx, int pery, double g, const double 
 }
 
 /* safeguard on caller arrays (Euler contents, 4 planes of nx*ny) */
-int or_safeguard(int nx, int ny, int perx, int pery, double g, const double *alphaB, const unsigned char *updated,
-                 double *Cn) {
-    return safeguard(nx, ny, perx, pery, g, alphaB, updated, Cn);
+int or_safeguard(int nx, int ny, int perx, int pery, double g, const double *alphaA, const double *alphaB,
+                 const unsigned char *updated, double *Cn) {
+    return safeguard(nx, ny, perx, pery, g, alphaA, alphaB, updated, Cn);
 }
 
 /* Geometric source of the axisymmetric Euler equations (a reading: the
@@ -1180,7 +1189,7 @@ int or_sweep(or_sim *s, int d, double dt) {
         err = OR_E_UNSTABLE;
 
     /* positivity safeguard */
-    if (s->c.equation == OR_EULER) s->mixed_last = safeguard(nx, ny, perx, pery, g, gB.alpha, updated, Cn);
+    if (s->c.equation == OR_EULER) s->mixed_last = safeguard(nx, ny, perx, pery, g, gA.alpha, gB.alpha, updated, Cn);
 
     /* new state Q' = content / alpha^B */
     for (int c = 0; c < n; ++c) {

@@ -31,6 +31,9 @@ constexpr int RF_COVER = 128;         // alpha_A > 0, alpha_B == 0
 constexpr int RF_WALL = 256;          // wall data valid
 constexpr int RF_USE8 = 512;          // event uses the 8-neighbourhood
 constexpr int RF_BAD = 1024;          // positivity safeguard triggered
+// a cell that keeps less than this fraction of its volume over a sweep seeds
+// the positivity safeguard's first merge (its state is content / alpha_B)
+constexpr double MIX_COLLAPSE = 0.01;
 constexpr int RF_NONBR = 2048;        // event without fluid neighbour
 constexpr int RF_MOV_B = 4096;        // a moving edge meets the cell at the end pose
 

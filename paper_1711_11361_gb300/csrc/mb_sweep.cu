@@ -2295,11 +2295,14 @@ __device__ __forceinline__ void events_rec(const InstDesc *__restrict__ D, InstD
     if (x.flags & RF_COVER) for (int q = 0; q < MAXC; ++q) C[q] = 0.0;
     for (int q = 0; q < MAXC; ++q) x.C2[q] = C[q];
     // positivity check of the new state (in the path's type; the FP64 path
-    // in FP64)
+    // in FP64); a cell that kept less than MIX_COLLAPSE of its volume over
+    // the sweep seeds the first merge as well (its state, content / alpha_B,
+    // carries residuals of the order of its mid-pose volume)
     if (I.eq == 0 && x.aB > 0.0) {
         const T q0 = (T)(C[0] / x.aB), q1 = (T)(C[1] / x.aB), q2 = (T)(C[2] / x.aB), q3 = (T)(C[3] / x.aB);
         const T p = ((T)I.gamma - T(1)) * (q3 - T(0.5) * (q1 * q1 + q2 * q2) / q0);
         bool ok = q0 > T(0) && p > T(0) && isfinite(q0) && isfinite(q1) && isfinite(q2) && isfinite(q3);
+        if (x.aB < MIX_COLLAPSE * x.aA) ok = false;
         if (!ok) {
             x.flags |= RF_BAD;
             int k = atomicAdd(&y.nbad, 1);
@@ -2333,6 +2336,7 @@ __global__ void k_events(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y
 // does not depend on the lanes.
 // ---------------------------------------------------------------------------
 constexpr int MIXCAP = 1024;
+constexpr int MIX_SMEM = 2 * (1 + MAXC) * MIXCAP * (int)sizeof(double);   // k_mix's node cache and sums
 constexpr int MIX_LAYERS = 8;   // merges per sweep (cells still non-physical seed the next)
 
 template <class T>
@@ -2342,6 +2346,11 @@ __global__ void __launch_bounds__(32) k_mix(const InstDesc *__restrict__ D, Inst
     __shared__ int par[MIXCAP];    // union-find parent (node index), later the root's cell
     __shared__ int nxt[MIXCAP];    // seeds of the merge; scratch of the root pass
     __shared__ unsigned char nbm[MIXCAP];   // each seed's fluid face neighbours (bit m: neighbour m)
+    // each node's volume fraction and content, read once per merge and
+    // replaced by the merged content as it is written (dynamic, MIX_SMEM bytes)
+    extern __shared__ double mixc[];
+    double *vol_s = mixc, *cont_s = mixc + MIXCAP;   // cont_s[q * MIXCAP + node]
+    double *acc_s = mixc + (1 + MAXC) * MIXCAP;      // cluster sums by slot: volume, then the components
     const int inst = blockIdx.x, lane = threadIdx.x;
     if (inst >= n_inst) return;
     const InstDesc &I = D[inst];
@@ -2440,15 +2449,17 @@ __global__ void __launch_bounds__(32) k_mix(const InstDesc *__restrict__ D, Inst
             v[z] = t;
         }
     };
-    // physical state of a cell's content after the update (or a merge)
-    auto physical = [&](int c) -> bool {
+    // physical state of node k's content after a merge (the cached values
+    // are those written: a band cell's content, a bulk cell's state in the
+    // path's type)
+    auto physical = [&](int k) -> bool {
         double q[MAXC];
-        if (I.cls[c] & CLS_BAND) {
-            const BandRec &bb = R[I.rec[c]];
-            if (!(bb.aB > 0.0)) return true;
-            for (int k = 0; k < I.nc; ++k) q[k] = bb.C2[k] / bb.aB;
+        if (I.cls[node[k]] & CLS_BAND) {
+            const double aB = vol_s[k];
+            if (!(aB > 0.0)) return true;
+            for (int m = 0; m < I.nc; ++m) q[m] = cont_s[m * MIXCAP + k] / aB;
         } else {
-            for (int k = 0; k < I.nc; ++k) q[k] = (double)Qo[k * plane + c];
+            for (int m = 0; m < I.nc; ++m) q[m] = cont_s[m * MIXCAP + k];
         }
         const double pm = (I.gamma - 1.0) * (q[3] - 0.5 * (q[1] * q[1] + q[2] * q[2]) / q[0]);
         return q[0] > 0.0 && pm > 0.0 && isfinite(q[1]) && isfinite(q[2]) && isfinite(q[3]);
@@ -2512,46 +2523,63 @@ __global__ void __launch_bounds__(32) k_mix(const InstDesc *__restrict__ D, Inst
             }
         }
         __syncwarp();
-        for (int k = 0; k < nn; ++k) {
-            const int rc = par[k];
-            if (node[k] != rc) continue;   // one pass per cluster, at its root cell
-            double tot[MAXC] = {0, 0, 0, 0}, vol = 0.0;
-            for (int m0 = 0; m0 < nn; m0 += 32) {
-                const int m = m0 + lane;
-                const bool mem = m < nn && par[m] == rc;
-                unsigned mask = __ballot_sync(0xffffffffu, mem);
-                if (!mask) continue;
-                double cv[MAXC] = {0, 0, 0, 0}, vv = 0.0;
-                if (mem) {
-                    const int c = node[m];
-                    if (I.cls[c] & CLS_BAND) {
-                        const BandRec &bb = R[I.rec[c]];
-                        vv = bb.aB;
-                        for (int q = 0; q < I.nc; ++q) cv[q] = bb.C2[q];
-                    } else {
-                        vv = 1.0;
-                        for (int q = 0; q < I.nc; ++q) cv[q] = (double)Qo[q * plane + c];
-                    }
-                }
-                // members in cell order, the same additions on every lane
-                for (; mask; mask &= mask - 1) {
-                    const int b = __ffs(mask) - 1;
-                    vol += __shfl_sync(0xffffffffu, vv, b);
-                    for (int q = 0; q < MAXC; ++q) tot[q] += __shfl_sync(0xffffffffu, cv[q], b);
-                }
+        // every node's volume fraction and content, one read each
+        for (int m = lane; m < nn; m += 32) {
+            const int c = node[m];
+            double vv = 1.0, cv[MAXC] = {0, 0, 0, 0};
+            if (I.cls[c] & CLS_BAND) {
+                const BandRec &bb = R[I.rec[c]];
+                vv = bb.aB;
+                for (int q = 0; q < I.nc; ++q) cv[q] = bb.C2[q];
+            } else {
+                for (int q = 0; q < I.nc; ++q) cv[q] = (double)Qo[q * plane + c];
             }
-            for (int m = lane; m < nn; m += 32) {
-                if (par[m] != rc) continue;
-                const int c = node[m];
-                if (I.cls[c] & CLS_BAND) {
-                    BandRec &bb = R[I.rec[c]];
-                    for (int q = 0; q < I.nc; ++q) bb.C2[q] = bb.aB * (tot[q] / vol);
-                } else {
-                    for (int q = 0; q < I.nc; ++q) Qo[q * plane + c] = (T)(tot[q] / vol);
-                }
-            }
-            __syncwarp();
+            vol_s[m] = vv;
+            for (int q = 0; q < MAXC; ++q) cont_s[q * MIXCAP + m] = cv[q];
         }
+        __syncwarp();
+        // each node's cluster slot: the position of its root cell among the
+        // nodes (sorted by cell); the slots' sums start at zero
+        for (int m = lane; m < nn; m += 32) {
+            const int rc = par[m];
+            int lo = 0, hi = nn - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (node[mid] < rc) lo = mid + 1; else hi = mid;
+            }
+            nxt[m] = lo;
+            for (int q = 0; q <= MAXC; ++q) acc_s[q * MIXCAP + m] = 0.0;
+        }
+        __syncwarp();
+        // the cluster sums: every cluster's members added in cell order
+        if (lane == 0) {
+            for (int m = 0; m < nn; ++m) {
+                const int r = nxt[m];
+                acc_s[r] += vol_s[m];
+                for (int q = 0; q < MAXC; ++q) acc_s[(q + 1) * MIXCAP + r] += cont_s[q * MIXCAP + m];
+            }
+        }
+        __syncwarp();
+        // each member's share, in proportion to its volume
+        for (int m = lane; m < nn; m += 32) {
+            const int r = nxt[m], c = node[m];
+            const double vol = acc_s[r];
+            if (I.cls[c] & CLS_BAND) {
+                BandRec &bb = R[I.rec[c]];
+                for (int q = 0; q < I.nc; ++q) {
+                    const double v = bb.aB * (acc_s[(q + 1) * MIXCAP + r] / vol);
+                    bb.C2[q] = v;
+                    cont_s[q * MIXCAP + m] = v;
+                }
+            } else {
+                for (int q = 0; q < I.nc; ++q) {
+                    const T v = (T)(acc_s[(q + 1) * MIXCAP + r] / vol);
+                    Qo[q * plane + c] = v;
+                    cont_s[q * MIXCAP + m] = (double)v;
+                }
+            }
+        }
+        __syncwarp();
         if (lane == 0) {
             y.mixed += nn;
             y.mixed_total += nn;
@@ -2560,7 +2588,7 @@ __global__ void __launch_bounds__(32) k_mix(const InstDesc *__restrict__ D, Inst
         nnext = 0;
         for (int k0 = 0; k0 < nn; k0 += 32) {
             const int k = k0 + lane;
-            const bool bad = k < nn && !physical(node[k]);
+            const bool bad = k < nn && !physical(k);
             const unsigned m = __ballot_sync(0xffffffffu, bad);
             if (bad) nxt[nnext + __popc(m & ((1u << lane) - 1u))] = node[k];
             nnext += __popc(m);
@@ -2771,7 +2799,7 @@ void launch_band_stage(int stage, const InstDesc *D, InstDyn *Y, BandRec *R, con
             break;
         case 1: if (blocks) k_band_sweep<T><<<blocks, 128, 0, st>>>(D, Y, R, bnd, boff, n_inst, dir, src); break;
         case 2: if (blocks) k_events<T><<<blocks, 128, 0, st>>>(D, Y, R, boff, n_inst); break;
-        case 3: k_mix<T><<<n_inst, 32, 0, st>>>(D, Y, R, n_inst, dst, sidx); break;
+        case 3: k_mix<T><<<n_inst, 32, MIX_SMEM, st>>>(D, Y, R, n_inst, dst, sidx); break;
         case 4: if (blocks) k_finalize<T><<<blocks, 128, 0, st>>>(D, Y, R, boff, n_inst, dst, last); break;
     }
 }
@@ -2822,6 +2850,7 @@ void launch_bulk(int dir, int eq, const InstDesc *D, InstDyn *Y, const BandRec *
 
 template <class T>
 int bulk_blocks_per_sm(int dir) {
+    cudaFuncSetAttribute(k_mix<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, MIX_SMEM);
     bulk_attr_t<T, 0>(dir);
     bulk_attr_t<T, 1>(dir);
     if (sizeof(T) == 4) {   // the FP32x2 kernels' shared-memory rings (4 warps per CTA at most)

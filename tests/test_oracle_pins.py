@@ -253,6 +253,46 @@ def test_safeguard_leaves_physical_contents_alone():
     assert m == 0 and np.array_equal(Cn, C)
 
 
+def _collapsed(aA_c, aB_c):
+    """3x3, the centre's volume fraction goes from aA_c to aB_c in the sweep
+    and it holds a physical but far out-of-range state (rho 50, E 125); the
+    others alpha 1, rho 1, E 2.5."""
+    aA, aB = np.ones((3, 3)), np.ones((3, 3))
+    aA[1, 1], aB[1, 1] = aA_c, aB_c
+    C = _euler(3, 3)
+    C[:, 1, 1] = [50.0 * aB_c, 0.0, 0.0, 125.0 * aB_c]
+    return aA, aB, C
+
+
+def test_safeguard_collapsed_cell_merges_by_hand():
+    """alpha 0.5 -> 0.004 keeps 0.8% of the volume: the centre seeds the
+    first merge although its state is physical.  Cluster: centre + 4 face
+    neighbours, rho total 0.2 + 4, E total 0.5 + 10, volume 4.004."""
+    aA, aB, C = _collapsed(0.5, 0.004)
+    Cn, m = oracle.safeguard(aB, C, alphaA=aA)
+    assert m == 5
+    for (j, i) in [(1, 0), (1, 2), (0, 1), (2, 1)]:
+        assert abs(Cn[0, j, i] - 4.2 / 4.004) < 1e-15 and abs(Cn[3, j, i] - 10.5 / 4.004) < 1e-14
+    assert abs(Cn[0, 1, 1] - 0.004 * 4.2 / 4.004) < 1e-17
+    assert Cn[0, 0, 0] == 1.0
+    assert abs(Cn[0].sum() - C[0].sum()) < 1e-14 and abs(Cn[3].sum() - C[3].sum()) < 1e-14
+
+
+def test_safeguard_collapse_threshold_and_exclusions():
+    """1% of the start volume is the boundary: alpha 0.5 -> 0.0051 is left
+    alone; without the start fractions, or for a cell uncovered in the
+    sweep (alpha 0 -> 0.001), nothing is seeded; a physical collapsed cell
+    seeds the first merge only (one merge of 5 cells, not one per layer)."""
+    aA, aB, C = _collapsed(0.5, 0.0051)
+    assert oracle.safeguard(aB, C, alphaA=aA)[1] == 0
+    aA, aB, C = _collapsed(0.5, 0.004)
+    assert oracle.safeguard(aB, C)[1] == 0
+    aA, aB, C = _collapsed(0.0, 0.001)
+    assert oracle.safeguard(aB, C, alphaA=aA)[1] == 0
+    aA, aB, C = _collapsed(0.9, 0.0001)
+    assert oracle.safeguard(aB, C, alphaA=aA)[1] == 5
+
+
 # ---------------------------------------------------------------------------
 # CFL step, Euler branch (regular-cell wave speeds, raised to the wall speed)
 # ---------------------------------------------------------------------------
