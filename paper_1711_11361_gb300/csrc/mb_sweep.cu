@@ -796,6 +796,17 @@ __device__ __forceinline__ void prim2(float g1, const float2 *q, float2 &ir, flo
     p = mul2(P2(g1), fma2(mul2(P2(-0.5f), ke), ir, q[3]));
 }
 
+// prim2 of two states a, b of the same cells from one reciprocal,
+// 1 / (rho_a rho_b) (the MUFU pipe is the kernels' second stall)
+__device__ __forceinline__ void prim2x2(float g1, const float2 *a, const float2 *b, float2 &ira, float2 &pa,
+                                        float2 &irb, float2 &pb) {
+    const float2 r = rcp2(mul2(a[0], b[0]));
+    ira = mul2(b[0], r);
+    irb = mul2(a[0], r);
+    pa = mul2(P2(g1), fma2(mul2(P2(-0.5f), fma2(a[1], a[1], mul2(a[2], a[2]))), ira, a[3]));
+    pb = mul2(P2(g1), fma2(mul2(P2(-0.5f), fma2(b[1], b[1], mul2(b[2], b[2]))), irb, b[3]));
+}
+
 // physical flux along D of states q with normal velocity un and pressure p
 template <int D>
 __device__ __forceinline__ void flux2(const float2 *q, float2 un, float2 p, float2 *f) {
@@ -826,11 +837,12 @@ __device__ __forceinline__ void evolve2(float g1, float lam, const float2 *qm, c
         qL[k] = fma2(P2(-0.5f), sl, q0[k]);
         qR[k] = fma2(P2(0.5f), sl, q0[k]);
     }
-    float2 ir, p;
-    prim2(g1, qL, ir, p);
-    flux2<D>(qL, mul2(qL[in], ir), p, fL);
-    prim2(g1, qR, ir, p);
-    flux2<D>(qR, mul2(qR[in], ir), p, fR);
+    {
+        float2 irL, pL, irR, pR;
+        prim2x2(g1, qL, qR, irL, pL, irR, pR);
+        flux2<D>(qL, mul2(qL[in], irL), pL, fL);
+        flux2<D>(qR, mul2(qR[in], irR), pR, fR);
+    }
     const float2 hl = P2(0.5f * lam);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -838,8 +850,7 @@ __device__ __forceinline__ void evolve2(float g1, float lam, const float2 *qm, c
         QL.q[k] = add2(qL[k], dfl);
         QR.q[k] = add2(qR[k], dfl);
     }
-    prim2(g1, QL.q, QL.ir, QL.p);
-    prim2(g1, QR.q, QR.ir, QR.p);
+    prim2x2(g1, QL.q, QR.q, QL.ir, QL.p, QR.ir, QR.p);
     const bool okx = QL.q[0].x > 0.0f && QR.q[0].x > 0.0f && QL.p.x > 0.0f && QR.p.x > 0.0f;
     const bool oky = QL.q[0].y > 0.0f && QR.q[0].y > 0.0f && QL.p.y > 0.0f && QR.p.y > 0.0f;
     if (!(okx && oky)) {
@@ -873,12 +884,17 @@ __device__ __forceinline__ void hllc2(float g, const E2 &L, const E2 &R, float2 
     const float2 S = sel2(kx, ky, SL, SR), a = sel2(kx, ky, aL, aR);
     float2 f[4];
     flux2<D>(q, u, p, f);
-    const float2 fac = mul2(a, rcp2(sub2(S, Ss)));
+    // a / (S - S*) and p / a from one reciprocal, 1 / (a (S - S*)) (both
+    // factors are non-zero where the star state is used)
+    const float2 dS = sub2(S, Ss);
+    const float2 rr = rcp2(mul2(a, dS));
+    const float2 fac = mul2(mul2(a, a), rr);
+    const float2 pa = mul2(mul2(p, dS), rr);
     float2 qs[4];
     qs[0] = fac;
     qs[in] = mul2(fac, Ss);
     qs[it] = mul2(fac, mul2(q[it], iv));
-    qs[3] = mul2(fac, fma2(sub2(Ss, u), fma2(p, rcp2(a), Ss), mul2(q[3], iv)));
+    qs[3] = mul2(fac, fma2(sub2(Ss, u), add2(pa, Ss), mul2(q[3], iv)));
     const bool sx = SL.x >= 0.0f || SR.x <= 0.0f, sy = SL.y >= 0.0f || SR.y <= 0.0f;
 #pragma unroll
     for (int k = 0; k < 4; ++k) F[k] = sel2(sx, sy, f[k], fma2(S, sub2(qs[k], q[k]), f[k]));
@@ -915,6 +931,30 @@ __device__ __forceinline__ void face_override(const InstDesc &I, const BandRec *
     }
 }
 
+// positivity list and CFL wave speeds of a pair of new states (cells ci and
+// ci + 1; st: bit 0 first stored, bit 1 second stored).  Outside the last
+// sweep only the signs are needed: rho > 0 and p > 0, i.e. 2 rho E > |m|^2,
+// with no division
+__device__ __forceinline__ void pair_checks(const float2 *qn, int st, int ci, bool last, float g1, float g, float &s0,
+                                            float &s1, InstDyn &y) {
+    if (!last) {
+        const float2 m2 = fma2(qn[1], qn[1], mul2(qn[2], qn[2]));
+        const float2 e2 = mul2(add2(qn[0], qn[0]), qn[3]);
+        if ((st & 1) && !(qn[0].x > 0.0f && e2.x > m2.x)) list_bulk_bad(y, ci);
+        if ((st & 2) && !(qn[0].y > 0.0f && e2.y > m2.y)) list_bulk_bad(y, ci + 1);
+        return;
+    }
+    float2 ir, p;
+    prim2(g1, qn, ir, p);
+    if ((st & 1) && !(qn[0].x > 0.0f && p.x > 0.0f)) list_bulk_bad(y, ci);
+    if ((st & 2) && !(qn[0].y > 0.0f && p.y > 0.0f)) list_bulk_bad(y, ci + 1);
+    const float2 cs = sqrt2(mul2(mul2(P2(g), p), ir));
+    const float2 w0 = add2(make_float2(fabsf(qn[1].x * ir.x), fabsf(qn[1].y * ir.y)), cs);
+    const float2 w1 = add2(make_float2(fabsf(qn[2].x * ir.x), fabsf(qn[2].y * ir.y)), cs);
+    if (st & 1) { s0 = fmaxf(s0, w0.x); s1 = fmaxf(s1, w1.x); }
+    if (st & 2) { s0 = fmaxf(s0, w0.y); s1 = fmaxf(s1, w1.y); }
+}
+
 // new states of the two cells (q, fluxes Flo / Fhi through their low / high
 // faces); stores the cells flagged in st (bit 0: first, bit 1: second);
 // wave speeds and positivity for the CFL step
@@ -934,17 +974,7 @@ __device__ __forceinline__ void update2(float *__restrict__ Qo, size_t plane, in
             if (st & 2) Qo[k * plane + ci + 1] = qn[k].y;
         }
     }
-    float2 ir, p;
-    prim2(g1, qn, ir, p);
-    if ((st & 1) && !(qn[0].x > 0.0f && p.x > 0.0f)) list_bulk_bad(y, ci);
-    if ((st & 2) && !(qn[0].y > 0.0f && p.y > 0.0f)) list_bulk_bad(y, ci + 1);
-    if (last) {
-        const float2 c = sqrt2(mul2(mul2(P2(g), p), ir));
-        const float2 w0 = add2(make_float2(fabsf(qn[1].x * ir.x), fabsf(qn[1].y * ir.y)), c);
-        const float2 w1 = add2(make_float2(fabsf(qn[2].x * ir.x), fabsf(qn[2].y * ir.y)), c);
-        if (st & 1) { s0 = fmaxf(s0, w0.x); s1 = fmaxf(s1, w1.x); }
-        if (st & 2) { s0 = fmaxf(s0, w0.y); s1 = fmaxf(s1, w1.y); }
-    }
+    pair_checks(qn, st, ci, last, g1, g, s0, s1, y);
 }
 
 // asynchronous global -> shared copies of 4 or 8 bytes (completion through
@@ -1040,22 +1070,6 @@ __device__ __forceinline__ int deferred_pair(int lane, unsigned p2_0, unsigned p
 // inputs (evolve2 with slopes on, hllc2, the update, the positivity and
 // wave-speed checks), so the bits are the same.
 
-// positivity list and CFL wave speeds of a pair of new states (cells ci and
-// ci + 1; st: bit 0 first stored, bit 1 second stored)
-__device__ __forceinline__ void pair_checks(const float2 *qn, int st, int ci, bool last, float g1, float g, float &s0,
-                                            float &s1, InstDyn &y) {
-    float2 ir, p;
-    prim2(g1, qn, ir, p);
-    if ((st & 1) && !(qn[0].x > 0.0f && p.x > 0.0f)) list_bulk_bad(y, ci);
-    if ((st & 2) && !(qn[0].y > 0.0f && p.y > 0.0f)) list_bulk_bad(y, ci + 1);
-    if (last) {
-        const float2 cs = sqrt2(mul2(mul2(P2(g), p), ir));
-        const float2 w0 = add2(make_float2(fabsf(qn[1].x * ir.x), fabsf(qn[1].y * ir.y)), cs);
-        const float2 w1 = add2(make_float2(fabsf(qn[2].x * ir.x), fabsf(qn[2].y * ir.y)), cs);
-        if (st & 1) { s0 = fmaxf(s0, w0.x); s1 = fmaxf(s1, w1.x); }
-        if (st & 2) { s0 = fmaxf(s0, w0.y); s1 = fmaxf(s1, w1.y); }
-    }
-}
 
 // x sweep of row j (Q, Qo: the row's first cell) outside the body's extent,
 // in the layout of k_bulk_x_p: lane l holds cells 64c + 2l, 64c + 2l + 1 of
@@ -1469,17 +1483,7 @@ __global__ void __launch_bounds__(128, MINB) k_bulk_x_p(const InstDesc *__restri
                     }
                 }
                 const int st = sm & ~sol;
-                float2 ir, p;
-                prim2(g1, qn, ir, p);
-                if ((st & 1) && !(qn[0].x > 0.0f && p.x > 0.0f)) list_bulk_bad(y, rowb + ap);
-                if ((st & 2) && !(qn[0].y > 0.0f && p.y > 0.0f)) list_bulk_bad(y, rowb + ap + 1);
-                if (last) {
-                    const float2 cs = sqrt2(mul2(mul2(P2(g), p), ir));
-                    const float2 w0 = add2(make_float2(fabsf(qn[1].x * ir.x), fabsf(qn[1].y * ir.y)), cs);
-                    const float2 w1 = add2(make_float2(fabsf(qn[2].x * ir.x), fabsf(qn[2].y * ir.y)), cs);
-                    if (st & 1) { s0 = fmaxf(s0, w0.x); s1 = fmaxf(s1, w1.x); }
-                    if (st & 2) { s0 = fmaxf(s0, w0.y); s1 = fmaxf(s1, w1.y); }
-                }
+                pair_checks(qn, st, rowb + ap, last != 0, g1, g, s0, s1, y);
             } else {
                 update_general(c, F, false, sm, cm);
             }
@@ -1837,18 +1841,7 @@ __global__ void __launch_bounds__(128, MINB) k_bulk_y_p(const InstDesc *__restri
                     }
                 }
                 const int st = sm & ~sol;
-                float2 ir, p;
-                prim2(g1, qn, ir, p);
-                const int ci = (f - 1) * pitch + i;
-                if ((st & 1) && !(qn[0].x > 0.0f && p.x > 0.0f)) list_bulk_bad(y, ci);
-                if ((st & 2) && !(qn[0].y > 0.0f && p.y > 0.0f)) list_bulk_bad(y, ci + 1);
-                if (last) {
-                    const float2 cs = sqrt2(mul2(mul2(P2(g), p), ir));
-                    const float2 w0 = add2(make_float2(fabsf(qn[1].x * ir.x), fabsf(qn[1].y * ir.y)), cs);
-                    const float2 w1 = add2(make_float2(fabsf(qn[2].x * ir.x), fabsf(qn[2].y * ir.y)), cs);
-                    if (st & 1) { s0 = fmaxf(s0, w0.x); s1 = fmaxf(s1, w1.x); }
-                    if (st & 2) { s0 = fmaxf(s0, w0.y); s1 = fmaxf(s1, w1.y); }
-                }
+                pair_checks(qn, st, (f - 1) * pitch + i, last != 0, g1, g, s0, s1, y);
             }
         } else {
             // rows f-1, f, f+1
