@@ -321,6 +321,30 @@ def n2_open_tube(cells_per_d=94, t_after_exit=1.2):
     return prob
 
 
+# a column covered from 0.3 to 0.002 of its volume in one x sweep
+COLLAPSE_SLAB_DT = 0.298 / 32.0
+
+
+def collapse_slab(uniform=True):
+    """32^2 unit box, transmissive sides; a slab x < 19.7/32 (rows 9.32 ..
+    22.32 of 32) moving at (1, 0).  In one x sweep of COLLAPSE_SLAB_DT its
+    front face moves 0.298 of a cell, so the cells of column 19 the slab
+    spans go from volume fraction 0.3 to 0.002.  Gas moving with the slab at
+    rho = p = 1 (uniform), or a smooth non-uniform state."""
+    d = 1.0 / 32.0
+    slab = rect_polygon(-1.0, (9 + 0.3183) * d, 19.7 * d, (22 + 0.3183) * d)
+    prob = Problem("collapse_slab", 32, 32, 0.0, 0.0, 1.0, 1.0, bc=(TRANSMISSIVE,) * 4, cfl=0.5, polygons=[slab],
+                   moving=[1], U=(1.0, 0.0))
+    X, Y = prob.cell_centres()
+    if uniform:
+        prob.Q0 = conserved(np.ones_like(X), 1.0, 0.0, np.ones_like(X))
+    else:
+        tp = 2.0 * math.pi
+        prob.Q0 = conserved(1.0 + 0.2 * np.sin(tp * Y) + 0.1 * np.cos(tp * X), 1.0 + 0.1 * np.sin(tp * (X + Y)),
+                            0.1 * np.cos(tp * X), 1.0 + 0.1 * np.sin(tp * X))
+    return prob
+
+
 def c2_cylinder(N=400, M=2.0, t_end=0.3, uncover_mode=UNCOVER_DONOR):
     """Cylinder r = 0.1 from (0.15, 0.5) at (0.5 c, 0) meeting a Mach-M shock at
     x = 0.3.  As in the paper's cylinder and wedge tests the body moves with

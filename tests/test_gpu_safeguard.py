@@ -1,9 +1,11 @@
 """The positivity safeguard on the GPU (cluster mixing of non-physical cells
-with their fluid face neighbours, a reading: the paper gives none) against
-the oracle, on an instance whose first non-physical cells appear in the bulk
-next to the body: triangle on 751^2, shock Mach 1.918, from the seeded
-64-instance batch.  The oracle first merges cells in step 56 (x sweep, 4
-cells) and again in step 57 (y sweep, 4 cells)."""
+and of cells that keep less than 1% of their volume over a sweep with their
+fluid face neighbours, a reading: the paper gives none) against the oracle:
+- a triangle on 751^2, shock Mach 1.918, from the seeded 64-instance batch,
+  whose corners leave slivers in most x sweeps (the oracle merges cells in
+  the x sweeps of steps 56 and 57);
+- a slab whose front face covers a column from 0.3 to 0.002 of its volume in
+  one x sweep (every cell of that column seeds a merge)."""
 import numpy as np
 import pytest
 
@@ -59,3 +61,21 @@ def test_fp32_batch_long_run_stays_physical(mb):
     assert sim.sync() == 0
     for k in range(len(probs)):
         assert sim.read_state(k)["step"] == 120
+
+
+def test_collapse_merges_like_oracle(mb):
+    """One x sweep of the collapsing slab (see tests/test_oracle_pins.py) from
+    a non-uniform state: the GPU's FP64 contents equal the oracle's to 1e-12
+    and both merge the same cells."""
+    prob = inputs.collapse_slab(uniform=False)
+    orc = oracle.Oracle(prob)
+    sim = mb.Sim(prob, mb.FP64)
+    sim.write_state(0, orc.state(), 0.0)
+    dt = inputs.COLLAPSE_SLAB_DT
+    assert orc.sweep(0, dt) == 0
+    sim.sweep(0, dt)
+    mo, mg = orc.last_sweep()[1], sim.diagnostics()["mixed"]
+    assert mo > 0 and mg == mo, (mg, mo)
+    r = compare(sim, orc)
+    assert r["cls"] == 0
+    assert r["contents"] <= 1e-12, r["contents"]

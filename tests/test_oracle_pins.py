@@ -293,6 +293,25 @@ def test_safeguard_collapse_threshold_and_exclusions():
     assert oracle.safeguard(aB, C, alphaA=aA)[1] == 5
 
 
+def test_collapse_sweep_keeps_uniform_flow_uniform():
+    """A whole column goes from alpha 0.3 to 0.002 in one x sweep (the slab
+    of inputs.collapse_slab): its cells seed merges, and gas moving with the
+    slab stays uniform (the stabilised update keeps uniform flow, and merging
+    equal states changes nothing)."""
+    prob = inputs.collapse_slab(uniform=True)
+    o = oracle.Oracle(prob)
+    a0 = o.alpha()
+    assert np.all(np.abs(a0[10:22, 19] - 0.3) < 1e-12)
+    assert o.sweep(0, inputs.COLLAPSE_SLAB_DT) == 0
+    a1 = o.alpha()
+    assert np.all(np.abs(a1[10:22, 19] - 0.002) < 1e-12)
+    assert o.last_sweep()[1] >= 12
+    Q = o.state()
+    fl = a1 > 0
+    for q, v in enumerate((1.0, 1.0, 0.0, 1.0 / 0.4 + 0.5)):
+        assert np.max(np.abs(Q[q][fl] - v)) < 1e-12, q
+
+
 # ---------------------------------------------------------------------------
 # CFL step, Euler branch (regular-cell wave speeds, raised to the wall speed)
 # ---------------------------------------------------------------------------
