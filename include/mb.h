@@ -165,6 +165,17 @@ mb_status mb_write_states(mb_sim *sim, const double *const *Q, const double *t);
  * order (the states are read either way). */
 mb_status mb_read_states(mb_sim *sim, double *const *Q, double *clocks);
 
+/* mb_write_states and mb_read_states with FP32 host states (nc*nx*ny floats
+ * per instance, same layout): half the bytes on the host link.  On an FP32
+ * batch the device state written from FP32 host values has the same bits as
+ * the one written from the FP64 values they were rounded from (the device
+ * rounds FP64 input to FP32 the same way), and mb_read_states_f32 returns
+ * the device values exactly; on an FP64 batch the FP32 values are widened
+ * on writing and rounded on reading.  Same arguments, errors, staging and
+ * synchronisation as the FP64 calls. */
+mb_status mb_write_states_f32(mb_sim *sim, const float *const *Q, const double *t);
+mb_status mb_read_states_f32(mb_sim *sim, float *const *Q, double *clocks);
+
 /* One time step of every instance: two sweeps, x then y on even steps and
  * y then x on odd steps (Sec. II.A, II.C.4).  dt > 0: that step for all
  * instances; dt <= 0: each instance's own CFL step (Sec. III), computed on

@@ -41,11 +41,10 @@ int bulk_blocks_per_sm(int);
 double fp64_probe_rate(cudaStream_t st);
 template <class T>
 void launch_axisym_source(const InstDesc *, InstDyn *, int, int, int, cudaStream_t);
-template <class T>
-void launch_write_state(const InstDesc *, InstDyn *, const double *const *, const double *, int, int, int, int,
-                        cudaStream_t);
-template <class T>
-void launch_read_state(const InstDesc *, double *const *, double *, int, int, int, int, cudaStream_t);
+template <class T, class H>
+void launch_write_state(const InstDesc *, InstDyn *, const H *const *, const H *, int, int, int, int, cudaStream_t);
+template <class T, class H>
+void launch_read_state(const InstDesc *, H *const *, H *, int, int, int, int, cudaStream_t);
 }  // namespace mb
 
 using namespace mb;
@@ -812,13 +811,17 @@ static cudaError_t batch_stage(mb_sim *sim, std::vector<size_t> &off) {
     return ensure(&sim->bstage, sim->cap_bstage, off[sim->n], sizeof(double));
 }
 
-static size_t state_bytes(const InstDesc &I) { return (size_t)I.nx * I.ny * I.nc * sizeof(double); }
+static size_t state_elems(const InstDesc &I) { return (size_t)I.nx * I.ny * I.nc; }
 
 // instances k0 .. k0+cnt-1 from host arrays Q[q] at times t[q].  A single
 // instance goes through the one-instance staging buffer; a batch is copied
 // whole into the batch staging buffer while its classification runs on the
 // side stream, then converted by one launch.
-static mb_status write_states(mb_sim *sim, int k0, int cnt, const double *const *Q, const double *t) {
+// H: the element type of the host states (FP64 or FP32); the staging buffers
+// hold them in that type
+extern "C++" {
+template <class H>
+static mb_status write_states(mb_sim *sim, int k0, int cnt, const H *const *Q, const double *t) {
     if (sim->sidx != 0) {
         // abandon the half-done step: the written state starts a new one
         sim->cur = (sim->qn + 1) % 3;
@@ -839,35 +842,37 @@ static mb_status write_states(mb_sim *sim, int k0, int cnt, const double *const 
     }
     cudaError_t e = cudaMemcpyAsync(sim->dy + k0, ys.data(), cnt * sizeof(InstDyn), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_check(sim, e, "write_state copy");
-    auto launch = [&](const double *const *ptrs, const double *p1, int i0, int ni, int mny) {
-        if (sim->prec == MB_FP32) launch_write_state<float>(sim->dd, sim->dy, ptrs, p1, i0, ni, mny, sim->cur, st);
-        else launch_write_state<double>(sim->dd, sim->dy, ptrs, p1, i0, ni, mny, sim->cur, st);
+    auto launch = [&](const H *const *ptrs, const H *p1, int i0, int ni, int mny) {
+        if (sim->prec == MB_FP32) launch_write_state<float, H>(sim->dd, sim->dy, ptrs, p1, i0, ni, mny, sim->cur, st);
+        else launch_write_state<double, H>(sim->dd, sim->dy, ptrs, p1, i0, ni, mny, sim->cur, st);
     };
+    H *const stage1 = (H *)sim->stage;   // the batch buffer is taken after batch_stage (it may allocate)
     if (cnt == 1) {
-        e = cudaMemcpyAsync(sim->stage, Q[0], state_bytes(sim->hd[k0]), cudaMemcpyHostToDevice, st);
+        e = cudaMemcpyAsync(stage1, Q[0], state_elems(sim->hd[k0]) * sizeof(H), cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) return cuda_check(sim, e, "write_state copy");
         classify_instances(sim, k0, 1, nullptr, st);
-        launch(nullptr, sim->stage, k0, 1, max_ny);
+        launch(nullptr, stage1, k0, 1, max_ny);
     } else {
         std::vector<size_t> off;
         e = batch_stage(sim, off);
         if (e != cudaSuccess) return cuda_check(sim, e, "write_states staging");
+        H *const bst = (H *)sim->bstage;
         e = cudaEventRecord(sim->ev_fork, st);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(sim->side, sim->ev_fork, 0);
         if (e != cudaSuccess) return cuda_check(sim, e, "write_states fork");
         classify_instances(sim, k0, cnt, nullptr, sim->side);
         e = cudaEventRecord(sim->ev_join, sim->side);
-        std::vector<const double *> ptrs(cnt);
+        std::vector<const H *> ptrs(cnt);
         for (int q = 0; q < cnt && e == cudaSuccess; ++q) {
-            ptrs[q] = sim->bstage + off[k0 + q];
-            e = cudaMemcpyAsync(sim->bstage + off[k0 + q], Q[q], state_bytes(sim->hd[k0 + q]),
+            ptrs[q] = bst + off[k0 + q];
+            e = cudaMemcpyAsync(bst + off[k0 + q], Q[q], state_elems(sim->hd[k0 + q]) * sizeof(H),
                                 cudaMemcpyHostToDevice, st);
         }
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(sim->iop, ptrs.data(), cnt * sizeof(double *), cudaMemcpyHostToDevice, st);
+            e = cudaMemcpyAsync(sim->iop, ptrs.data(), cnt * sizeof(H *), cudaMemcpyHostToDevice, st);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(st, sim->ev_join, 0);
         if (e != cudaSuccess) return cuda_check(sim, e, "write_states copy");
-        launch(sim->iop, nullptr, k0, cnt, max_ny);
+        launch((const H *const *)sim->iop, nullptr, k0, cnt, max_ny);
     }
     e = cudaStreamSynchronize(st);
     if (e == cudaSuccess) e = cudaGetLastError();
@@ -875,39 +880,45 @@ static mb_status write_states(mb_sim *sim, int k0, int cnt, const double *const 
     if (k0 == 0) sim->nstep = 0;
     return MB_OK;
 }
+}  // extern "C++"
 
 // states of instances k0 .. k0+cnt-1 into host arrays Q[q] (entries may be
 // NULL); their dynamic records into ys.  A batch is converted by one launch
 // into the batch staging buffer, then copied out.
-static mb_status read_states(mb_sim *sim, int k0, int cnt, double *const *Q, std::vector<InstDyn> &ys) {
+extern "C++" {
+template <class H>
+static mb_status read_states(mb_sim *sim, int k0, int cnt, H *const *Q, std::vector<InstDyn> &ys) {
     cudaStream_t st = sim->stream;
     const int buf = sim->sidx == 0 ? sim->cur : (sim->qn + 1) % 3;
-    auto launch = [&](double *const *ptrs, double *p1, int i0, int ni, int max_ny) {
-        if (sim->prec == MB_FP32) launch_read_state<float>(sim->dd, ptrs, p1, i0, ni, max_ny, buf, st);
-        else launch_read_state<double>(sim->dd, ptrs, p1, i0, ni, max_ny, buf, st);
+    auto launch = [&](H *const *ptrs, H *p1, int i0, int ni, int max_ny) {
+        if (sim->prec == MB_FP32) launch_read_state<float, H>(sim->dd, ptrs, p1, i0, ni, max_ny, buf, st);
+        else launch_read_state<double, H>(sim->dd, ptrs, p1, i0, ni, max_ny, buf, st);
     };
+    H *const stage1 = (H *)sim->stage;   // the batch buffer is taken after batch_stage (it may allocate)
     cudaError_t e = cudaSuccess;
     if (cnt == 1) {
         if (Q[0]) {
-            launch(nullptr, sim->stage, k0, 1, sim->hd[k0].ny);
-            e = cudaMemcpyAsync(Q[0], sim->stage, state_bytes(sim->hd[k0]), cudaMemcpyDeviceToHost, st);
+            launch(nullptr, stage1, k0, 1, sim->hd[k0].ny);
+            e = cudaMemcpyAsync(Q[0], stage1, state_elems(sim->hd[k0]) * sizeof(H), cudaMemcpyDeviceToHost, st);
         }
     } else {
         std::vector<size_t> off;
         e = batch_stage(sim, off);
         if (e != cudaSuccess) return cuda_check(sim, e, "read_states staging");
-        std::vector<double *> ptrs(cnt, nullptr);
+        H *const bst = (H *)sim->bstage;
+        std::vector<H *> ptrs(cnt, nullptr);
         int max_ny = 0;
         for (int q = 0; q < cnt; ++q) {
             if (!Q[q]) continue;
-            ptrs[q] = sim->bstage + off[k0 + q];
+            ptrs[q] = bst + off[k0 + q];
             max_ny = std::max(max_ny, sim->hd[k0 + q].ny);
         }
-        e = cudaMemcpyAsync(sim->iop, ptrs.data(), cnt * sizeof(double *), cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess) launch((double *const *)sim->iop, nullptr, k0, cnt, max_ny);
+        e = cudaMemcpyAsync(sim->iop, ptrs.data(), cnt * sizeof(H *), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) launch((H *const *)sim->iop, nullptr, k0, cnt, max_ny);
         for (int q = 0; q < cnt && e == cudaSuccess; ++q)
             if (Q[q])
-                e = cudaMemcpyAsync(Q[q], ptrs[q], state_bytes(sim->hd[k0 + q]), cudaMemcpyDeviceToHost, st);
+                e = cudaMemcpyAsync(Q[q], ptrs[q], state_elems(sim->hd[k0 + q]) * sizeof(H), cudaMemcpyDeviceToHost,
+                                    st);
     }
     if (e != cudaSuccess) return cuda_check(sim, e, "read_state copy");
     ys.resize(cnt);
@@ -917,6 +928,7 @@ static mb_status read_states(mb_sim *sim, int k0, int cnt, double *const *Q, std
     if (e != cudaSuccess) return cuda_check(sim, e, "read_state");
     return MB_OK;
 }
+}  // extern "C++"
 
 static void clock_of(const InstDyn &y, double *clock) {
     clock[0] = y.t;
@@ -930,7 +942,9 @@ mb_status mb_write_state(mb_sim *sim, int inst, const double *Q, double t) {
     return write_states(sim, inst, 1, &Q, &t);
 }
 
-mb_status mb_write_states(mb_sim *sim, const double *const *Q, const double *t) {
+extern "C++" {
+template <class H>
+static mb_status write_all(mb_sim *sim, const H *const *Q, const double *t) {
     if (!sim || !Q) return MB_E_INVAL;
     for (int k = 0; k < sim->n; ++k)
         if (!Q[k]) return fail(sim, MB_E_INVAL, "write_states: NULL state array");
@@ -938,6 +952,11 @@ mb_status mb_write_states(mb_sim *sim, const double *const *Q, const double *t) 
     if (t) tt.assign(t, t + sim->n);
     return write_states(sim, 0, sim->n, Q, tt.data());
 }
+}  // extern "C++"
+
+mb_status mb_write_states(mb_sim *sim, const double *const *Q, const double *t) { return write_all(sim, Q, t); }
+
+mb_status mb_write_states_f32(mb_sim *sim, const float *const *Q, const double *t) { return write_all(sim, Q, t); }
 
 mb_status mb_read_state(mb_sim *sim, int inst, double *Q, double *alpha, double *clock) {
     if (!sim || inst < 0 || inst >= sim->n) return MB_E_INVAL;
@@ -956,7 +975,9 @@ mb_status mb_read_state(mb_sim *sim, int inst, double *Q, double *alpha, double 
     return map_err(sim, ys[0].err);
 }
 
-mb_status mb_read_states(mb_sim *sim, double *const *Q, double *clocks) {
+extern "C++" {
+template <class H>
+static mb_status read_all(mb_sim *sim, H *const *Q, double *clocks) {
     if (!sim || !Q) return MB_E_INVAL;
     std::vector<InstDyn> ys;
     mb_status r = read_states(sim, 0, sim->n, Q, ys);
@@ -968,6 +989,11 @@ mb_status mb_read_states(mb_sim *sim, double *const *Q, double *clocks) {
     }
     return r;
 }
+}  // extern "C++"
+
+mb_status mb_read_states(mb_sim *sim, double *const *Q, double *clocks) { return read_all(sim, Q, clocks); }
+
+mb_status mb_read_states_f32(mb_sim *sim, float *const *Q, double *clocks) { return read_all(sim, Q, clocks); }
 
 mb_status mb_band_records(mb_sim *sim, int inst, void *out, int max_records, int *count) {
     if (!sim || inst < 0 || inst >= sim->n) return MB_E_INVAL;

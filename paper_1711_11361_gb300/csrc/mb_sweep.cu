@@ -2677,14 +2677,15 @@ constexpr int STATE_THREADS = 128;
 // error could exceed 1e-5), and its state differs from the last state the
 // thread took through the FP64 formula.  Elsewhere the FP32 speeds are
 // within 1e-5 of the FP64 ones, so no skipped cell can hold the maximum,
-// and the result is that of the FP64 formula over every cell.
-template <class T>
+// and the result is that of the FP64 formula over every cell.  H: the
+// element type of the host layout (FP64 or FP32 states).
+template <class T, class H>
 __global__ void __launch_bounds__(STATE_THREADS) k_write_state(const InstDesc *__restrict__ D,
                                                                InstDyn *__restrict__ Y,
-                                                               const double *const *__restrict__ srcs,
-                                                               const double *__restrict__ src1, int inst0, int b) {
+                                                               const H *const *__restrict__ srcs,
+                                                               const H *__restrict__ src1, int inst0, int b) {
     const int inst = inst0 + blockIdx.y;
-    const double *__restrict__ Qh = srcs ? srcs[blockIdx.y] : src1;
+    const H *__restrict__ Qh = srcs ? srcs[blockIdx.y] : src1;
     if (!Qh) return;
     const InstDesc &I = D[inst];
     const int j0 = blockIdx.x * STATE_ROWS;
@@ -2753,13 +2754,13 @@ __global__ void __launch_bounds__(STATE_THREADS) k_write_state(const InstDesc *_
 }
 
 // Destinations: dsts[blockIdx.y] (null entry: skip) or dst1; nc planes of
-// nx*ny doubles, solid cells NaN.
-template <class T>
+// nx*ny values of type H (FP64 or FP32), solid cells NaN.
+template <class T, class H>
 __global__ void __launch_bounds__(STATE_THREADS) k_read_state(const InstDesc *__restrict__ D,
-                                                              double *const *__restrict__ dsts,
-                                                              double *__restrict__ dst1, int inst0, int b) {
+                                                              H *const *__restrict__ dsts,
+                                                              H *__restrict__ dst1, int inst0, int b) {
     const int inst = inst0 + blockIdx.y;
-    double *__restrict__ out = dsts ? dsts[blockIdx.y] : dst1;
+    H *__restrict__ out = dsts ? dsts[blockIdx.y] : dst1;
     if (!out) return;
     const InstDesc &I = D[inst];
     const int j0 = blockIdx.x * STATE_ROWS;
@@ -2771,7 +2772,7 @@ __global__ void __launch_bounds__(STATE_THREADS) k_read_state(const InstDesc *__
     for (int j = j0; j < j1; ++j)
         for (int i = threadIdx.x; i < I.nx; i += STATE_THREADS)
             for (int k = 0; k < I.nc; ++k)
-                out[k * n + (size_t)j * I.nx + i] = (double)Q[k * plane + (size_t)j * I.pitch + i];
+                out[k * n + (size_t)j * I.nx + i] = (H)Q[k * plane + (size_t)j * I.pitch + i];
 }
 
 // ---------------------------------------------------------------------------
@@ -2866,17 +2867,17 @@ int bulk_blocks_per_sm(int dir) {
 
 // instances inst0 .. inst0+ninst-1 (max_ny: their largest ny); per-instance
 // pointers in the device array ptrs, or one pointer p1 (ninst == 1)
-template <class T>
-void launch_write_state(const InstDesc *D, InstDyn *Y, const double *const *ptrs, const double *p1, int inst0,
-                        int ninst, int max_ny, int b, cudaStream_t st) {
+template <class T, class H>
+void launch_write_state(const InstDesc *D, InstDyn *Y, const H *const *ptrs, const H *p1, int inst0, int ninst,
+                        int max_ny, int b, cudaStream_t st) {
     const dim3 grid((max_ny + STATE_ROWS - 1) / STATE_ROWS, ninst);
-    if (ninst > 0 && max_ny > 0) k_write_state<T><<<grid, STATE_THREADS, 0, st>>>(D, Y, ptrs, p1, inst0, b);
+    if (ninst > 0 && max_ny > 0) k_write_state<T, H><<<grid, STATE_THREADS, 0, st>>>(D, Y, ptrs, p1, inst0, b);
 }
-template <class T>
-void launch_read_state(const InstDesc *D, double *const *ptrs, double *p1, int inst0, int ninst, int max_ny, int b,
+template <class T, class H>
+void launch_read_state(const InstDesc *D, H *const *ptrs, H *p1, int inst0, int ninst, int max_ny, int b,
                        cudaStream_t st) {
     const dim3 grid((max_ny + STATE_ROWS - 1) / STATE_ROWS, ninst);
-    if (ninst > 0 && max_ny > 0) k_read_state<T><<<grid, STATE_THREADS, 0, st>>>(D, ptrs, p1, inst0, b);
+    if (ninst > 0 && max_ny > 0) k_read_state<T, H><<<grid, STATE_THREADS, 0, st>>>(D, ptrs, p1, inst0, b);
 }
 
 #define MB_INST(T)                                                                                                \
@@ -2886,9 +2887,14 @@ void launch_read_state(const InstDesc *D, double *const *ptrs, double *p1, int i
                                  int, int, DeferList, int, cudaStream_t);                                               \
     template int bulk_blocks_per_sm<T>(int);                                                                       \
     template void launch_axisym_source<T>(const InstDesc *, InstDyn *, int, int, int, cudaStream_t);               \
-    template void launch_write_state<T>(const InstDesc *, InstDyn *, const double *const *, const double *, int,  \
-                                        int, int, int, cudaStream_t);                                             \
-    template void launch_read_state<T>(const InstDesc *, double *const *, double *, int, int, int, int, cudaStream_t);
+    template void launch_write_state<T, double>(const InstDesc *, InstDyn *, const double *const *, const double *, \
+                                                int, int, int, int, cudaStream_t);                                 \
+    template void launch_write_state<T, float>(const InstDesc *, InstDyn *, const float *const *, const float *,    \
+                                               int, int, int, int, cudaStream_t);                                  \
+    template void launch_read_state<T, double>(const InstDesc *, double *const *, double *, int, int, int, int,    \
+                                               cudaStream_t);                                                      \
+    template void launch_read_state<T, float>(const InstDesc *, float *const *, float *, int, int, int, int,       \
+                                              cudaStream_t);
 MB_INST(float)
 MB_INST(double)
 

@@ -27,7 +27,7 @@ EXPORTS = ["mb_create", "mb_batch_create", "mb_destroy", "mb_last_error", "mb_se
            "mb_request_bytes", "mb_server_create", "mb_server_destroy", "mb_server_last_error", "mb_server_submit",
            "mb_server_tick", "mb_server_query", "mb_server_request_error", "mb_autotune", "mb_set_overlap",
            "mb_write_states", "mb_read_states", "mb_graph_kernels", "mb_set_sweep_event",
-           "mb_merge_count", "mb_fp64_rate", "mb_probe"]
+           "mb_merge_count", "mb_fp64_rate", "mb_probe", "mb_write_states_f32", "mb_read_states_f32"]
 
 
 class Grid(ctypes.Structure):
@@ -104,6 +104,8 @@ def _load():
         "mb_set_overlap": ([P, I], I),
         "mb_write_states": ([P, ctypes.POINTER(D), D], I),
         "mb_read_states": ([P, ctypes.POINTER(D), D], I),
+        "mb_write_states_f32": ([P, ctypes.POINTER(ctypes.POINTER(ctypes.c_float)), D], I),
+        "mb_read_states_f32": ([P, ctypes.POINTER(ctypes.POINTER(ctypes.c_float)), D], I),
         "mb_graph_kernels": ([P, ctypes.POINTER(I)], I),
         "mb_set_sweep_event": ([P, P], I),
         "mb_merge_count": ([P, I, ctypes.POINTER(ctypes.c_longlong)], I),
@@ -207,34 +209,42 @@ class Sim:
         self._check(lib.mb_write_state(self._h, inst, _dp(Q), t))
 
     @staticmethod
-    def _ptrs(arrays):
+    def _ptrs(arrays, ctype=ctypes.c_double):
         # numpy arrays, or addresses (ints) of host buffers such as pinned
         # torch tensors' data_ptr()
-        D = ctypes.POINTER(ctypes.c_double)
-        return (D * len(arrays))(*[ctypes.cast(a, D) if isinstance(a, int) else _dp(a) for a in arrays])
+        T = ctypes.POINTER(ctype)
+        return (T * len(arrays))(*[ctypes.cast(a, T) if isinstance(a, int) else a.ctypes.data_as(T)
+                                   for a in arrays])
 
-    def write_states(self, Qs, t=None):
-        """Every instance's state in one call (mb_write_states).  Qs[k]: a
-        C-contiguous float64 array of shape (nc, ny, nx), or the address of
-        such a host buffer; t: times (default 0)."""
+    def write_states(self, Qs, t=None, dtype=np.float64):
+        """Every instance's state in one call (mb_write_states, or
+        mb_write_states_f32 for dtype float32).  Qs[k]: a C-contiguous array
+        of shape (nc, ny, nx), or the address of such a host buffer of that
+        dtype; t: times (default 0)."""
         if len(Qs) != self.n:
             raise ValueError("one state per instance")
+        f32 = np.dtype(dtype) == np.float32
         keep = []
         for k, Q in enumerate(Qs):
             if not isinstance(Q, int):
                 p = self.problems[k]
-                Q = np.ascontiguousarray(Q, dtype=np.float64).reshape(p.nc, p.ny, p.nx)
+                Q = np.ascontiguousarray(Q, dtype=np.float32 if f32 else np.float64).reshape(p.nc, p.ny, p.nx)
             keep.append(Q)
         tt = None if t is None else np.ascontiguousarray(t, dtype=np.float64)
-        self._check(lib.mb_write_states(self._h, self._ptrs(keep), _dp(tt) if tt is not None else None))
+        fn = lib.mb_write_states_f32 if f32 else lib.mb_write_states
+        ptrs = self._ptrs(keep, ctypes.c_float if f32 else ctypes.c_double)
+        self._check(fn(self._h, ptrs, _dp(tt) if tt is not None else None))
 
-    def read_states(self, out=None, check=True):
-        """Every instance's state in one call (mb_read_states) into out (as
-        for write_states) or new arrays; returns (states, clocks (n, 4), status)."""
+    def read_states(self, out=None, check=True, dtype=np.float64):
+        """Every instance's state in one call (mb_read_states, or
+        mb_read_states_f32 for dtype float32) into out (as for write_states)
+        or new arrays; returns (states, clocks (n, 4), status)."""
+        f32 = np.dtype(dtype) == np.float32
         if out is None:
-            out = [np.empty((p.nc, p.ny, p.nx)) for p in self.problems]
+            out = [np.empty((p.nc, p.ny, p.nx), dtype=np.float32 if f32 else np.float64) for p in self.problems]
         clk = np.empty((self.n, 4))
-        r = lib.mb_read_states(self._h, self._ptrs(out), _dp(clk))
+        fn = lib.mb_read_states_f32 if f32 else lib.mb_read_states
+        r = fn(self._h, self._ptrs(out, ctypes.c_float if f32 else ctypes.c_double), _dp(clk))
         if check:
             self._check(r)
         return out, clk, r

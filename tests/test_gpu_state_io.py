@@ -116,3 +116,47 @@ def test_first_step_dt_is_the_fp64_one(mb):
         dts.append(sim.step(0.0, report=True))
         sim.close()
     assert np.array_equal(dts[0], dts[1]), (dts[0], dts[1])
+
+
+def test_fp32_host_io_matches_fp64_host_io(mb):
+    """mb_write_states_f32 / mb_read_states_f32 on an FP32 batch: writing the
+    FP32 roundings of the FP64 states gives the same device bits (and so the
+    same steps) as writing the FP64 states, and the FP32 read returns the
+    device values exactly (the FP64 read's values, rounded)."""
+    probs = _mix()
+    ts = _times(probs)
+    a = mb.Sim(probs, mb.FP32, write_initial=False)
+    a.write_states([p.Q0 for p in probs], ts)
+    b = mb.Sim(probs, mb.FP32, write_initial=False)
+    b.write_states([p.Q0.astype(np.float32) for p in probs], ts, dtype=np.float32)
+    c = mb.Sim(probs, mb.FP32, write_initial=False)
+    pin = _pinned([p.Q0.astype(np.float32) for p in probs])
+    c.write_states([t.data_ptr() for t in pin], ts, dtype=np.float32)
+    for s in (a, b, c):
+        s.run(5, 0.0)
+    qa, ca, _ = a.read_states()
+    qb, cb, _ = b.read_states(dtype=np.float32)
+    qc, cc, _ = c.read_states(dtype=np.float32)
+    assert np.array_equal(ca, cb) and np.array_equal(ca, cc)
+    for k, p in enumerate(probs):
+        assert qb[k].dtype == np.float32
+        assert np.array_equal(qa[k].astype(np.float32), qb[k], equal_nan=True), p.name
+        assert np.array_equal(qb[k], qc[k], equal_nan=True), p.name
+    for s in (a, b, c):
+        s.close()
+
+
+def test_fp32_host_io_on_fp64_batch(mb):
+    """On an FP64 batch the FP32 host values are widened exactly on writing
+    and rounded on reading."""
+    probs = _mix()[:3]
+    q32 = [p.Q0.astype(np.float32) for p in probs]
+    s = mb.Sim(probs, mb.FP64, write_initial=False)
+    s.write_states(q32, dtype=np.float32)
+    q64, _, _ = s.read_states()
+    q32b, _, _ = s.read_states(dtype=np.float32)
+    for k in range(len(probs)):
+        fl = np.isfinite(q64[k][0])
+        assert np.array_equal(q64[k][:, fl], q32[k][:, fl].astype(np.float64))
+        assert np.array_equal(q32b[k], q64[k].astype(np.float32), equal_nan=True)
+    s.close()
