@@ -1026,12 +1026,15 @@ int or_sweep(or_sim *s, int d, double dt) {
             wall_t *w = &W[c];
             w->has = 1;
             /* shielded distance at the mid pose: alpha_hat = alpha - min(beta),
-             * d = alpha_hat / |delta beta| (eqs. Klein2DalphaHat, timeAveragedAlpha) */
+             * d = alpha_hat / |delta beta| (eqs. Klein2DalphaHat, timeAveragedAlpha);
+             * d = 1 when the two apertures differ by 1e-12 or less, where
+             * both alpha_hat and |delta beta| are round-off and their ratio
+             * means nothing (the limit of equally open faces) */
             double blo = d == 0 ? gM.bx[j * (nx + 1) + i] : gM.by[j * nx + i];
             double bhi = d == 0 ? gM.bx[j * (nx + 1) + i + 1] : gM.by[(j + 1) * nx + i];
             double db = fabs(blo - bhi);
             double ahat = gM.alpha[c] - dmin(blo, bhi);
-            w->d = db > 0.0 ? clamp01(ahat / db) : 1.0;
+            w->d = db > 1e-12 ? clamp01(ahat / db) : 1.0;
             /* wall normal from aperture closure at the mid pose, pointing into the body */
             double bW = gM.bx[j * (nx + 1) + i], bE = gM.bx[j * (nx + 1) + i + 1];
             double bS = gM.by[j * nx + i], bN = gM.by[(j + 1) * nx + i];

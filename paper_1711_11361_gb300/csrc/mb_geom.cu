@@ -1196,7 +1196,9 @@ __device__ __forceinline__ void geom_group(int gw, const InstDesc *__restrict__ 
         r.aux = 0;
         const double db = fabs(blo - bhi);
         const double ahat = aM - dmin(blo, bhi);
-        r.d = db > 0.0 ? clamp01(ahat / db) : 1.0;
+        // equally open faces (|delta beta| <= 1e-12, where both terms are
+        // round-off): d = 1
+        r.d = db > 1e-12 ? clamp01(ahat / db) : 1.0;
         // Where two bodies touch along an edge (a piston sliding in a tube),
         // their edges cancel in this sum and no fluid boundary is left; the
         // sum keeps a rounding residual of about eps x the edge length, which

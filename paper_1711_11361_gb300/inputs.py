@@ -470,3 +470,87 @@ def small_case(kind="cylinder", N=48, M=2.0, uncover_mode=UNCOVER_DONOR):
 
 def with_state(prob: Problem, Q) -> Problem:
     return replace(prob, Q0=np.asarray(Q, dtype=np.float64))
+
+
+# ---------------------------------------------------------------------------
+# three dimensions: one convex polyhedral body (half-spaces n . x <= c in body
+# coordinates) translating at U; Euler with 5 conserved variables
+# (rho, rho u, rho v, rho w, E), planes of (nz, ny, nx) cells, x fastest
+# ---------------------------------------------------------------------------
+@dataclass
+class Problem3:
+    """One three-dimensional simulation instance."""
+    name: str
+    nx: int
+    ny: int
+    nz: int
+    lo: tuple = (0.0, 0.0, 0.0)
+    hi: tuple = (1.0, 1.0, 1.0)
+    bc: tuple = (TRANSMISSIVE,) * 6          # x-low, x-high, y-low, y-high, z-low, z-high
+    gamma: float = GAMMA
+    cfl: float = 0.5
+    normals: Optional[np.ndarray] = None     # (nplane, 3) outward unit normals
+    offsets: Optional[np.ndarray] = None     # (nplane,)
+    bbox: tuple = (0.0, 0.0, 0.0, 0.0, 0.0, 0.0)   # body bounding box, body coordinates
+    U: tuple = (0.0, 0.0, 0.0)
+    uncover_mode: int = UNCOVER_DONOR
+    Q0: Optional[np.ndarray] = None          # (5, nz, ny, nx)
+    info: dict = field(default_factory=dict)
+
+    nc = 5
+
+    @property
+    def h(self):
+        return tuple((self.hi[a] - self.lo[a]) / (self.nx, self.ny, self.nz)[a] for a in range(3))
+
+    def cell_centres(self):
+        c = [self.lo[a] + (np.arange((self.nx, self.ny, self.nz)[a]) + 0.5) * self.h[a] for a in range(3)]
+        Z, Y, X = np.meshgrid(c[2], c[1], c[0], indexing="ij")
+        return X, Y, Z
+
+
+def conserved3(rho, u, v, w, p, gamma=GAMMA):
+    rho = np.asarray(rho, dtype=np.float64)
+    shape = rho.shape
+    u, v, w, p = (np.broadcast_to(np.asarray(a, dtype=np.float64), shape) for a in (u, v, w, p))
+    E = p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v + w * w)
+    return np.stack([rho, rho * u, rho * v, rho * w, E])
+
+
+def prism_planes(poly2d):
+    """Planes of the z-invariant prism over a convex CCW polygon (n, 2): one
+    per edge, normal (ey, -ex, 0) / |e|, offset n . vertex."""
+    P = np.asarray(poly2d, dtype=np.float64)
+    nrm, off = [], []
+    for k in range(len(P)):
+        a, b = P[k], P[(k + 1) % len(P)]
+        e = b - a
+        n = np.array([e[1], -e[0], 0.0]) / math.hypot(e[0], e[1])
+        nrm.append(n)
+        off.append(float(n[0] * a[0] + n[1] * a[1]))
+    return np.array(nrm), np.array(off)
+
+
+def cone_planes(apex, height, radius, k_sides=24):
+    """A cone along +x (apex forward) as a right pyramid over the regular
+    k_sides-gon inscribed in its base circle: one lateral plane per base edge
+    through the apex, and the base plane.  Returns (normals, offsets,
+    bounding box)."""
+    ax, ay, az = apex
+    xb = ax - height
+    A = np.array([ax, ay, az])
+    th = 2.0 * math.pi * np.arange(k_sides) / k_sides
+    V = np.stack([np.full(k_sides, xb), ay + radius * np.cos(th), az + radius * np.sin(th)], axis=1)
+    nrm, off = [], []
+    for m in range(k_sides):
+        n = np.cross(V[m] - A, V[(m + 1) % k_sides] - A)
+        mid = 0.5 * (V[m] + V[(m + 1) % k_sides])
+        if np.dot(n, mid - np.array([xb, ay, az])) < 0.0:   # outward: away from the axis
+            n = -n
+        n = n / np.linalg.norm(n)
+        nrm.append(n)
+        off.append(float(np.dot(n, A)))
+    nrm.append(np.array([-1.0, 0.0, 0.0]))
+    off.append(-xb)
+    bbox = (xb, ax, ay - radius, ay + radius, az - radius, az + radius)
+    return np.array(nrm), np.array(off), bbox
