@@ -919,6 +919,9 @@ double o3_cfl_dt(const o3_sim *s) {
 /* ------------------------------------------------------------------------ */
 o3_sim *o3_create(const o3_config *cfg, const double *bb) {
     if (!cfg || cfg->nx < 1 || cfg->ny < 1 || cfg->nz < 1 || cfg->nplane < 0 || cfg->nplane > O3_MAXP) return NULL;
+    /* the stencil's two ghost cells mirror two cells of a non-periodic axis */
+    const int nax[3] = {cfg->nx, cfg->ny, cfg->nz};
+    for (int a = 0; a < 3; ++a) if (nax[a] < 2 && cfg->bc[2 * a] != O3_BC_PERIODIC) return NULL;
     o3_sim *s = (o3_sim *)calloc(1, sizeof(o3_sim));
     s->c = *cfg;
     memcpy(s->bb, bb, sizeof(s->bb));

@@ -25,6 +25,7 @@ UNITS = {
     "mb_sweep.cu": ["--ftz=true", "--prec-div=false", "--prec-sqrt=false"],
     "mb_api.cu": [],
     "mb_server.cu": [],
+    "mb3.cu": ["-fmad=false"],
 }
 
 
@@ -36,7 +37,9 @@ def nvcc() -> str:
 
 
 def _sources_mtime() -> float:
-    paths = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(ROOT, "include", "mb.h"), __file__]
+    inc = os.path.join(ROOT, "include")
+    paths = ([os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(inc, f) for f in os.listdir(inc)] +
+             [__file__])
     return max(os.path.getmtime(p) for p in paths)
 
 

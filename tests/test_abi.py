@@ -1,5 +1,5 @@
 """The C-ABI library builds, loads without a GPU and exports every entry
-point declared in include/mb.h (no compute calls)."""
+point declared in include/mb.h and include/mb3.h (no compute calls)."""
 import ctypes
 import os
 import re
@@ -9,9 +9,9 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def declared():
-    src = open(os.path.join(ROOT, "include", "mb.h")).read()
-    return sorted(set(re.findall(r"^\s*(?:mb_status|void|int|size_t|const char \*)\s*(mb_\w+)\s*\(", src, re.M)))
+def declared(header="mb.h"):
+    src = open(os.path.join(ROOT, "include", header)).read()
+    return sorted(set(re.findall(r"^\s*(?:mb_status|void|int|size_t|const char \*)\s*(mb3?_\w+)\s*\(", src, re.M)))
 
 
 def test_header_declares_the_sweep_calls():
@@ -20,17 +20,21 @@ def test_header_declares_the_sweep_calls():
         assert n in names
 
 
-def test_library_exports_every_declared_symbol():
+@pytest.mark.parametrize("header", ["mb.h", "mb3.h"])
+def test_library_exports_every_declared_symbol(header):
     from paper_1711_11361_gb300 import build
     path = build.build()
     lib = ctypes.CDLL(path)
-    for n in declared():
+    names = declared(header)
+    assert names
+    for n in names:
         assert hasattr(lib, n), n
 
 
 def test_binding_lists_every_export():
-    from paper_1711_11361_gb300 import mb
-    assert sorted(mb.EXPORTS) == declared()
+    from paper_1711_11361_gb300 import mb, mb3
+    assert sorted(mb.EXPORTS) == declared("mb.h")
+    assert sorted(mb3.EXPORTS) == declared("mb3.h")
 
 
 def _noalloc_call(prob):
