@@ -580,6 +580,105 @@ def run_n2(args):
                       "paper": paper, "runs": rows}))
 
 
+def n3_flux_ops_per_face():
+    """FP64-pipe lane operations per face of the three-dimensional flux
+    kernel k3_flux, from the ncu capture summarised in
+    profiles/n3_flux_ops.json; None when mb3.cu has changed since."""
+    import hashlib
+    try:
+        d = json.load(open(os.path.join(ROOT, "profiles", "n3_flux_ops.json")))
+        for f, sha in d["sources_sha256"].items():
+            with open(os.path.join(ROOT, "paper_1711_11361_gb300", "csrc", f), "rb") as fh:
+                if hashlib.sha256(fh.read()).hexdigest() != sha:
+                    return None
+        return float(d["fp64_pipe_lane_ops_per_face"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def n3_flux_roofline(mb3, p, rate):
+    """k3_flux, the three-dimensional path's dominant kernel, against the
+    FP64 pipe: its device time per sweep (CUDA events around each launch on
+    the simulation's stream, two steps' sweeps from the initial state),
+    faces per second, and FP64-pipe lane operations per second against the
+    measured FP64 rate."""
+    from paper_1711_11361_gb300 import inputs
+    sim = mb3.Sim3(p)
+    dt = sim.cfl_dt()
+    n = p.nx * p.ny * p.nz
+    nn = (p.nx, p.ny, p.nz)
+    per = []
+    for s in range(3):
+        for d in ((0, 1, 2) if s % 2 == 0 else (2, 1, 0)):
+            sim.sweep(d, dt)
+            nfl = nn[d] + (0 if p.bc[2 * d] == inputs.PERIODIC else 1)
+            if s > 0:   # the first step warms up
+                per.append((nfl * (n // nn[d]), sim.flux_time_ms() * 1e-3))
+    sim.close()
+    faces = sum(f for f, _ in per)
+    secs = sum(t for _, t in per)
+    out = {"kernel": "k3_flux", "ms_per_sweep": secs / len(per) * 1e3, "faces_per_s": faces / secs}
+    ops = n3_flux_ops_per_face()
+    if ops is not None:
+        achieved = ops * faces / secs
+        out.update({"bound": "fp64", "achieved": achieved / 1e12, "peak": rate / 1e12,
+                    "unit": "T FP64-pipe lane-ops/s", "frac": achieved / rate, "fp64_pipe_lane_ops_per_face": ops,
+                    "peak_kind": "measured: mb_fp64_rate (independent FP64 FMA chains)"})
+    return out
+
+
+def run_n3(args):
+    """The paper's three-dimensional Schardin test (Sec. III.F) as read in
+    inputs.n3_schardin_cone: a 60-degree cone moving with the gas into a
+    stationary Mach-1.34 shock in the 10 D x 10 D x 5 D half domain, on the
+    FP64 three-dimensional GPU path (held to the three-dimensional oracle by
+    tests/test_gpu_3d.py), until 1.48 tau after contact (the paper's 102 us
+    for its 20 mm cone), at each of --n3-resolutions cells per diameter.
+    Reports cell-sweeps/s (cells x 3 sweeps per step), the steps, the cells
+    merged by the safeguard and the status; the 3-D oracle on a bounded
+    sample (one step of the 10-per-D case) is the CPU baseline."""
+    import torch
+    from paper_1711_11361_gb300 import inputs, mb3
+    torch.cuda.set_device(0)
+    rows = []
+    for k in args.n3_resolutions:
+        p = inputs.n3_schardin_cone(k)
+        sim = mb3.Sim3(p)
+        sim.step()                       # untimed warm-up step (buffers, first launch)
+        sim.write_state(p.Q0)
+        t, steps, merged = 0.0, 0, 0
+        t0 = time.perf_counter()
+        while t < p.info["t_end"]:
+            t += sim.step()
+            steps += 1
+            merged += sim.last_sweep()[1]
+        el = time.perf_counter() - t0
+        st = sim.read_state(check=False)
+        sim.close()
+        rows.append({"cells_per_D": k, "grid": f"{p.nx}x{p.ny}x{p.nz}", "cells": p.info["cells"], "steps": steps,
+                     "seconds": el, "cell_sweeps_per_s": p.info["cells"] * 3 * steps / el,
+                     "ms_per_step": el / steps * 1e3, "status": int(st["status"]), "t_end": t,
+                     "merged_cells_last_sweeps": merged})
+    line = {"metric": "cell-sweeps/s, three-dimensional FP64 path (x, y, z sweeps), Schardin cone",
+            "value": rows[-1]["cell_sweeps_per_s"], "unit": "cell-sweeps/s", "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "n3_schardin_cone_10Dx10Dx5D", "mach": inputs.N3_MACH,
+                       "t_after_contact_tau": inputs.N3_T_AFTER, "cone": "24-sided pyramid, apex angle 60 deg"},
+            "runs": rows}
+    from paper_1711_11361_gb300 import mb
+    rate = mb.fp64_rate(torch.cuda.current_stream().cuda_stream)
+    line["roofline"] = n3_flux_roofline(mb3, inputs.n3_schardin_cone(args.n3_resolutions[-1]), rate)
+    if not args.no_cpu_baseline:
+        from oracle import o3
+        p = inputs.n3_schardin_cone(10)
+        o = o3.Oracle3(p)
+        t0 = time.perf_counter()
+        r, dt = o.step()
+        el = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": p.info["cells"] * 3 / el, "unit": "cell-sweeps/s", "cores": 1,
+                                "kind": "oracle", "sample": f"one step of the {p.nx}x{p.ny}x{p.nz} case, {el:.1f} s"}
+    print(json.dumps(line))
+
+
 def workload(rank, args):
     from paper_1711_11361_gb300 import inputs
     if args.workload == "c4":
@@ -748,6 +847,8 @@ def main():
     ap.add_argument("--sweep-samples", type=int, default=100, help="steps sampled for the per-sweep p50/p99")
     ap.add_argument("--n2-resolutions", type=int, nargs="+", default=[94, 189, 378],
                     help="cells per tube diameter of the open-tube runs")
+    ap.add_argument("--n3-resolutions", type=int, nargs="+", default=[10, 20],
+                    help="cells per cone diameter of the three-dimensional Schardin runs")
     ap.add_argument("--c3-period", action="store_true",
                     help="FP32 vs FP64 accuracy of the pitching NACA 0012 workload after one full pitch period")
     ap.add_argument("--accuracy-steps", type=int, default=500,
@@ -781,6 +882,8 @@ def main():
         return run_n1(args)
     if args.workload == "n2":
         return run_n2(args)
+    if args.workload == "n3":
+        return run_n3(args)
 
     import torch
     ws, rank, local = dist_env()

@@ -76,6 +76,10 @@ mb_status mb3_cfl_dt(mb3_sim *sim, double *dt);
 /* the last sweep's summed wall terms (5 doubles, optional) and cells merged
  * by the safeguard (optional) */
 mb_status mb3_last_sweep(mb3_sim *sim, double *wall, int *merged);
+/* device time (ms) of the last sweep's face-flux kernel (MUSCL-Hancock +
+ * HLLC + stabilised flux of every face along the sweep), from CUDA events
+ * recorded around it on the simulation's stream */
+mb_status mb3_flux_time(mb3_sim *sim, double *ms);
 
 #ifdef __cplusplus
 }

@@ -9,7 +9,8 @@
 //             apertures of the sweep's faces (R)
 //   k3_wall   flux-GCL provisional states, shielded distance, wall normal,
 //             wall state and flux of the band cells (R)
-//   k3_flux   MUSCL-Hancock + HLLC + stabilised flux of every d-face
+//   k3_evolve MUSCL-Hancock evolved boundary states of every cell along d
+//   k3_flux   HLLC + stabilised flux of every d-face
 //   k3_update the conservative update alpha_B Q' of every cell
 //   k3_events covering / uncovering, gathered per cell in cell order (R)
 //   k3_bad / k3_mix  the positivity safeguard (one thread merges)
@@ -33,6 +34,7 @@ namespace mb3 {
 
 constexpr int NC = 5;
 constexpr int MAXP = MB3_MAX_PLANES;
+static_assert(MAXP <= 32, "one plane per lane and per mask bit");
 constexpr int MAXH = 6 + MAXP;          // half-spaces of a box inside the body
 constexpr int MAXPV = MAXH + 4;         // polygon vertices
 constexpr double ALPHA_MIN = 1e-10;
@@ -85,8 +87,11 @@ __device__ double clipped_area(const double *a, const double *b, const double *r
 
 // volume of the box [lo, lo + h] inside the body; *touch: the body
 // boundary cuts the box.  Coordinates relative to lo.  V = (1/3) sum over
-// the faces of box ∩ body of offset x area (divergence theorem).
+// the faces of box ∩ body of offset x area (divergence theorem).  Called by
+// all 32 lanes of a warp for the same box: lane l takes faces l, l + 32;
+// the sums are reduced over the warp (every exit depends on the box only).
 __device__ double box_solid_volume(const Body3 &B, const double *lo, const double *h, bool *touch) {
+    const int lane = threadIdx.x & 31;
     double hn[MAXH][3], hc[MAXH];
     int nh = 0;
     for (int a = 0; a < 3; ++a) {   // the box: -x_a <= 0, x_a <= h_a
@@ -98,20 +103,27 @@ __device__ double box_solid_volume(const Body3 &B, const double *lo, const doubl
         }
     }
     const int nbox = nh;
-    for (int f = 0; f < B.np; ++f) {
+    // the body's planes against the box, lane f taking plane f: over the
+    // box's vertices v, n . v is least at v_a = h_a where n_a < 0 (else 0)
+    // and greatest at v_a = h_a where n_a > 0, and the rounded sums keep
+    // that order; the box lies outside plane f when its lowest vertex does,
+    // and plane f cuts it when its highest vertex lies outside
+    bool outside = false, cuts = false;
+    if (lane < B.np) {
+        const double *n = &B.n[3 * lane];
+        const double c = B.c[lane] - dot3(n, lo);
+        const double vl[3] = {n[0] < 0.0 ? h[0] : 0.0, n[1] < 0.0 ? h[1] : 0.0, n[2] < 0.0 ? h[2] : 0.0};
+        const double vh[3] = {n[0] > 0.0 ? h[0] : 0.0, n[1] > 0.0 ? h[1] : 0.0, n[2] > 0.0 ? h[2] : 0.0};
+        outside = !(dot3(n, vl) <= c);
+        cuts = !outside && !(dot3(n, vh) <= c);
+    }
+    if (__ballot_sync(0xffffffffu, outside)) { *touch = false; return 0.0; }
+    for (unsigned m = __ballot_sync(0xffffffffu, cuts); m; m &= m - 1) {   // the cutting planes in order
+        const int f = __ffs(m) - 1;
         const double *n = &B.n[3 * f];
-        const double c = B.c[f] - dot3(n, lo);
-        int nin = 0;
-        for (int k = 0; k < 8; ++k) {
-            const double v[3] = {(k & 1) ? h[0] : 0.0, (k & 2) ? h[1] : 0.0, (k & 4) ? h[2] : 0.0};
-            if (dot3(n, v) <= c) ++nin;
-        }
-        if (nin == 0) { *touch = false; return 0.0; }   // the box lies outside this plane
-        if (nin < 8) {
-            hn[nh][0] = n[0]; hn[nh][1] = n[1]; hn[nh][2] = n[2];
-            hc[nh] = c;
-            ++nh;
-        }
+        hn[nh][0] = n[0]; hn[nh][1] = n[1]; hn[nh][2] = n[2];
+        hc[nh] = B.c[f] - dot3(n, lo);
+        ++nh;
     }
     const double vol = h[0] * h[1] * h[2];
     if (nh == nbox) { *touch = false; return vol; }
@@ -119,7 +131,7 @@ __device__ double box_solid_volume(const Body3 &B, const double *lo, const doubl
     // within |h| + |c| of the plane's origin c n
     const double L = 2.0 * sqrt(h[0] * h[0] + h[1] * h[1] + h[2] * h[2]);
     double V = 0.0, body_area = 0.0;
-    for (int f = 0; f < nh; ++f) {
+    for (int f = lane; f < nh; f += 32) {
         // in-plane basis e1, e2 (e1 x e2 = n), origin o = c n
         const double *n = hn[f];
         double t[3] = {1.0, 0.0, 0.0};
@@ -142,6 +154,10 @@ __device__ double box_solid_volume(const Body3 &B, const double *lo, const doubl
         V += hc[f] * A;
         if (f >= nbox) body_area += A;
     }
+    for (int o = 16; o > 0; o >>= 1) {
+        V += __shfl_xor_sync(0xffffffffu, V, o);
+        body_area += __shfl_xor_sync(0xffffffffu, body_area, o);
+    }
     *touch = body_area > 0.0;
     return fmin(vol, fmax(0.0, V / 3.0));
 }
@@ -151,10 +167,22 @@ __device__ double box_solid_volume(const Body3 &B, const double *lo, const doubl
 // planes, in coordinates relative to (lb, lc)
 __device__ double rect_solid_area(const Body3 &B, int a, double v, double lb, double wb, double lc, double wc) {
     const int b = (a + 1) % 3, c = (a + 2) % 3;
+    // the planes against the rectangle's corners first: none inside one
+    // plane leaves no solid, all inside one leaves that plane out
+    unsigned cut = 0;
+    for (int f = 0; f < B.np; ++f) {
+        const double *nn = &B.n[3 * f];
+        const double cc = B.c[f] - nn[a] * v - nn[b] * lb - nn[c] * lc;
+        const double lo_ = (nn[b] < 0.0 ? nn[b] * wb : 0.0) + (nn[c] < 0.0 ? nn[c] * wc : 0.0) - cc;
+        const double hi_ = (nn[b] > 0.0 ? nn[b] * wb : 0.0) + (nn[c] > 0.0 ? nn[c] * wc : 0.0) - cc;
+        if (lo_ > 0.0) return 0.0;
+        if (hi_ > 0.0) cut |= 1u << f;
+    }
     double px[MAXPV], py[MAXPV], qx[MAXPV], qy[MAXPV];
     int n = 4;
     px[0] = 0.0; py[0] = 0.0; px[1] = wb; py[1] = 0.0; px[2] = wb; py[2] = wc; px[3] = 0.0; py[3] = wc;
-    for (int f = 0; f < B.np && n > 0; ++f) {
+    for (; cut && n > 0; cut &= cut - 1) {
+        const int f = __ffs(cut) - 1;
         const double *nn = &B.n[3 * f];
         const double cc = B.c[f] - nn[a] * v - nn[b] * lb - nn[c] * lc;
         int k2 = 0;
@@ -195,6 +223,7 @@ struct Desc {
     double lam;             // dt / h_d
     int r0[3], rn[3];       // region R: first cell and extent per axis
     double *Q, *Qn, *C, *Cn, *F;
+    double *E;              // evolved boundary states along d, 2 NC planes
     double *aA, *aM, *aB;   // over R
     unsigned char *tA, *tB; // over R
     double *bM[3];          // mid-pose apertures of R's faces, per axis
@@ -270,9 +299,10 @@ __device__ __forceinline__ void r_cell(const Desc &D, int t, int *i, int *j, int
     *k = D.r0[2] + t / (D.rn[0] * D.rn[1]);
 }
 
-// volume fractions at the three poses and the touch flags of R's cells
+// volume fractions at the three poses and the touch flags of R's cells,
+// one warp per cell
 __global__ void k3_cells(Desc D, Body3 BA, Body3 BM, Body3 BB) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (t >= D.rn[0] * D.rn[1] * D.rn[2]) return;
     int i, j, k;
     r_cell(D, t, &i, &j, &k);
@@ -284,14 +314,17 @@ __global__ void k3_cells(Desc D, Body3 BA, Body3 BM, Body3 BB) {
     const double VA = box_solid_volume(BA, lo, h, &ta);
     const double VM = box_solid_volume(BM, lo, h, &tm);
     const double VB = box_solid_volume(BB, lo, h, &tb);
+    const bool l0 = (threadIdx.x & 31) == 0;
     double a = fmin(1.0, fmax(0.0, 1.0 - VA / vol));
-    D.aA[t] = a < ALPHA_MIN ? 0.0 : a;
+    if (l0) D.aA[t] = a < ALPHA_MIN ? 0.0 : a;
     a = fmin(1.0, fmax(0.0, 1.0 - VM / vol));
-    D.aM[t] = a < ALPHA_MIN ? 0.0 : a;
+    if (l0) D.aM[t] = a < ALPHA_MIN ? 0.0 : a;
     a = fmin(1.0, fmax(0.0, 1.0 - VB / vol));
-    D.aB[t] = a < ALPHA_MIN ? 0.0 : a;
-    D.tA[t] = ta;
-    D.tB[t] = tb;
+    if ((threadIdx.x & 31) == 0) {
+        D.aB[t] = a < ALPHA_MIN ? 0.0 : a;
+        D.tA[t] = ta;
+        D.tB[t] = tb;
+    }
 }
 
 // apertures at M of R's x-, y- and z-faces, then the time-averaged
@@ -311,26 +344,33 @@ __global__ void k3_faces(Desc D, Body3 BM, Body3 BA, double delta) {
             const double lc = node(D, c, ijk[c]), wc = node(D, c, ijk[c] + 1) - lc;
             const double A = rect_solid_area(BM, ax, node(D, ax, ijk[ax]), lb, wb, lc, wc);
             D.bM[ax][t] = fmin(1.0, fmax(0.0, 1.0 - A / (wb * wc)));
-        } else {
-            if (delta == 0.0) {
-                const double lb = node(D, b, ijk[b]), wb = node(D, b, ijk[b] + 1) - lb;
-                const double lc = node(D, c, ijk[c]), wc = node(D, c, ijk[c] + 1) - lc;
-                const double A = rect_solid_area(BA, ax, node(D, ax, ijk[ax]), lb, wb, lc, wc);
-                D.bt[t] = fmin(1.0, fmax(0.0, 1.0 - A / (wb * wc)));
-            } else {
-                double lo[3], h[3];
-                for (int q = 0; q < 3; ++q) { lo[q] = node(D, q, ijk[q]); h[q] = node(D, q, ijk[q] + 1) - lo[q]; }
-                const double xf = node(D, ax, ijk[ax]);
-                const double s0 = delta > 0.0 ? xf - delta : xf, s1 = delta > 0.0 ? xf : xf - delta;
-                lo[ax] = s0;
-                h[ax] = s1 - s0;
-                bool tch;
-                const double V = box_solid_volume(BA, lo, h, &tch);
-                D.bt[t] = fmin(1.0, fmax(0.0, 1.0 - V / (h[0] * h[1] * h[2])));
-            }
+        } else if (delta == 0.0) {
+            const double lb = node(D, b, ijk[b]), wb = node(D, b, ijk[b] + 1) - lb;
+            const double lc = node(D, c, ijk[c]), wc = node(D, c, ijk[c] + 1) - lc;
+            const double A = rect_solid_area(BA, ax, node(D, ax, ijk[ax]), lb, wb, lc, wc);
+            D.bt[t] = fmin(1.0, fmax(0.0, 1.0 - A / (wb * wc)));
         }
         return;
     }
+}
+
+// time-averaged apertures of R's d-faces for delta != 0: the fluid fraction
+// of [x_f - delta, x_f] with the body at A, one warp per face
+__global__ void k3_swept(Desc D, Body3 BA, double delta) {
+    const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int ax = D.d;
+    const int m0 = D.rn[0] + (ax == 0), m1 = D.rn[1] + (ax == 1), m2 = D.rn[2] + (ax == 2);
+    if (t >= m0 * m1 * m2) return;
+    const int ijk[3] = {D.r0[0] + t % m0, D.r0[1] + (t / m0) % m1, D.r0[2] + t / (m0 * m1)};
+    double lo[3], h[3];
+    for (int q = 0; q < 3; ++q) { lo[q] = node(D, q, ijk[q]); h[q] = node(D, q, ijk[q] + 1) - lo[q]; }
+    const double xf = node(D, ax, ijk[ax]);
+    const double s0 = delta > 0.0 ? xf - delta : xf, s1 = delta > 0.0 ? xf : xf - delta;
+    lo[ax] = s0;
+    h[ax] = s1 - s0;
+    bool tch;
+    const double V = box_solid_volume(BA, lo, h, &tch);
+    if ((threadIdx.x & 31) == 0) D.bt[t] = fmin(1.0, fmax(0.0, 1.0 - V / (h[0] * h[1] * h[2])));
 }
 
 // exact wall Riemann problem (eq. riemann_wallvel), normal n into the body
@@ -439,19 +479,23 @@ __global__ void k3_wall(Desc D) {
 __device__ __forceinline__ double pressure5(double g, const double *q) {
     return (g - 1.0) * (q[4] - 0.5 * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) / q[0]);
 }
-__device__ void flux5(double g, int d, const double *q, double *f) {
-    const double rho = q[0], un = q[1 + d] / rho, p = pressure5(g, q);
+// (GB300's FP64 pipe is narrow: each quotient costs a Newton sequence, so
+// the kernels share one reciprocal of rho where they can)
+__device__ __forceinline__ void flux5(double g, int d, const double *q, double *f) {
+    const double rho = q[0], ir = 1.0 / rho, un = q[1 + d] * ir;
+    const double p = (g - 1.0) * (q[4] - 0.5 * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) * ir);
     f[0] = rho * un;
     for (int m = 0; m < 3; ++m) f[1 + m] = q[1 + m] * un + (m == d ? p : 0.0);
     f[4] = un * (q[4] + p);
 }
 // HLLC, Davis wave speeds (Toro, Riemann Solvers ch. 10)
-__device__ void hllc5(double g, int d, const double *qL, const double *qR, double *F) {
+__device__ __forceinline__ void hllc5(double g, int d, const double *qL, const double *qR, double *F) {
     const int in = 1 + d;
-    const double rL = qL[0], rR = qR[0];
-    const double uL = qL[in] / rL, uR = qR[in] / rR;
-    const double pL = pressure5(g, qL), pR = pressure5(g, qR);
-    const double cL = sqrt(g * pL / rL), cR = sqrt(g * pR / rR);
+    const double rL = qL[0], rR = qR[0], iL = 1.0 / rL, iR = 1.0 / rR;
+    const double uL = qL[in] * iL, uR = qR[in] * iR;
+    const double pL = (g - 1.0) * (qL[4] - 0.5 * (qL[1] * qL[1] + qL[2] * qL[2] + qL[3] * qL[3]) * iL);
+    const double pR = (g - 1.0) * (qR[4] - 0.5 * (qR[1] * qR[1] + qR[2] * qR[2] + qR[3] * qR[3]) * iR);
+    const double cL = sqrt(g * pL * iL), cR = sqrt(g * pR * iR);
     const double SL = fmin(uL - cL, uR - cR), SR = fmax(uL + cL, uR + cR);
     if (SL >= 0.0) { flux5(g, d, qL, F); return; }
     if (SR <= 0.0) { flux5(g, d, qR, F); return; }
@@ -460,13 +504,19 @@ __device__ void hllc5(double g, int d, const double *qL, const double *qR, doubl
     const double Ss = num / den;
     const bool left = Ss >= 0.0;
     const double *q = left ? qL : qR;
-    const double r = left ? rL : rR, u = left ? uL : uR, p = left ? pL : pR, S = left ? SL : SR;
+    const double r = left ? rL : rR, ir = left ? iL : iR, u = left ? uL : uR, p = left ? pL : pR;
+    const double S = left ? SL : SR;
     double f[NC], qs[NC];
-    flux5(g, d, q, f);
-    const double fac = r * (S - u) / (S - Ss);
+    f[0] = r * u;
+    for (int m = 0; m < 3; ++m) f[1 + m] = q[1 + m] * u + (m == d ? p : 0.0);
+    f[4] = u * (q[4] + p);
+    // fac = a / dS and p / a with a = rho (S - u), dS = S - S*, from one
+    // reciprocal of a dS
+    const double a = r * (S - u), dS = S - Ss, rr = 1.0 / (a * dS);
+    const double fac = a * a * rr;
     qs[0] = fac;
-    for (int m = 0; m < 3; ++m) qs[1 + m] = m == d ? fac * Ss : fac * (q[1 + m] / r);
-    qs[4] = fac * (q[4] / r + (Ss - u) * (Ss + p / (r * (S - u))));
+    for (int m = 0; m < 3; ++m) qs[1 + m] = m == d ? fac * Ss : fac * (q[1 + m] * ir);
+    qs[4] = fac * (q[4] * ir + (Ss - u) * (Ss + p * dS * rr));
     for (int k = 0; k < NC; ++k) F[k] = f[k] + S * (qs[k] - q[k]);
 }
 __device__ __forceinline__ double vanleer(double dm, double dp) {
@@ -494,7 +544,8 @@ __device__ __forceinline__ int line_cell(const Desc &D, int d, const int *base, 
 // MUSCL-Hancock evolved boundary states QL, QR of the cell at position m
 // along the line (conserved variables, van Leer, zero slope next to a solid
 // cell, first order where an evolved state is not physical)
-__device__ void evolve5(const Desc &D, int d, const int *base, int m, int nal, double *QL, double *QR) {
+__device__ __forceinline__ void evolve5(const Desc &D, int d, const int *base, int m, int nal, double *QL,
+                                        double *QR) {
     double q[3][NC];
     bool fl[3];
     for (int s = 0; s < 3; ++s) {
@@ -520,39 +571,67 @@ __device__ void evolve5(const Desc &D, int d, const int *base, int m, int nal, d
         QL[k] = qL[k] + dfl;
         QR[k] = qR[k] + dfl;
     }
-    if (!(QL[0] > 0.0) || !(QR[0] > 0.0) || !(pressure5(g, QL) > 0.0) || !(pressure5(g, QR) > 0.0))
+    // physical: rho > 0 and p > 0, i.e. 2 rho E > |m|^2
+    const bool okL = QL[0] > 0.0 && 2.0 * QL[0] * QL[4] > QL[1] * QL[1] + QL[2] * QL[2] + QL[3] * QL[3];
+    const bool okR = QR[0] > 0.0 && 2.0 * QR[0] * QR[4] > QR[1] * QR[1] + QR[2] * QR[2] + QR[3] * QR[3];
+    if (!okL || !okR)
         for (int k = 0; k < NC; ++k) { QL[k] = q[1][k]; QR[k] = q[1][k]; }
 }
 
+// the d-faces form a grid like the cells' with nfl faces along d (x
+// fastest): the index of the face at (i, j, k), the low d-face of cell
+// (i, j, k) (its d-index may be nal: the high face of the last cell)
+__device__ __forceinline__ int fidx(const Desc &D, int nfl, int i, int j, int k) {
+    const int m0 = D.d == 0 ? nfl : D.nx, m1 = D.d == 1 ? nfl : D.ny;
+    return (k * m1 + j) * m0 + i;
+}
+
+// (the kernels of the sweep's line work take the direction d as a template
+// argument, so that the per-direction indexing is static)
+// the evolved boundary states of every fluid cell along d, once per cell:
+// E holds QL in planes 0..NC-1 and QR in planes NC..2NC-1
+template <int d>
+__global__ void k3_evolve(Desc D, int nal) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= D.n) return;
+    const int base[3] = {c % D.nx, (c / D.nx) % D.ny, c / (D.nx * D.ny)};
+    if (!fluid_a(D, base[0], base[1], base[2])) return;
+    double QL[NC], QR[NC];
+    evolve5(D, d, base, base[d], nal, QL, QR);
+    for (int q = 0; q < NC; ++q) {
+        D.E[(size_t)q * D.n + c] = QL[q];
+        D.E[(size_t)(NC + q) * D.n + c] = QR[q];
+    }
+}
+
 // the stabilised flux bf F2D of every d-face (eqs. Klein2DtotalfluxaMethod2,
-// Klein2shieldedFluxMethod2, with the two-sided shielded parts): F holds
-// NC planes of (faces per line) x (lines), face m of a line between its
-// cells m-1 and m
+// Klein2shieldedFluxMethod2, with the two-sided shielded parts) into the
+// NC planes of F, face m of a line between its cells m-1 and m; the
+// evolved states of the cells come from E, those of a boundary's ghost
+// cells (a periodic ghost is the cell it wraps to) are evolved here
+template <int d>
 __global__ void k3_flux(Desc D, int nal, int nfl, int nlines) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (long long)nfl * nlines) return;
-    const int m = (int)(t % nfl), l = (int)(t / nfl);
-    const int d = D.d;
-    int base[3];
-    if (d == 0) { base[0] = 0; base[1] = l % D.ny; base[2] = l / D.ny; }
-    else if (d == 1) { base[0] = l % D.nx; base[1] = 0; base[2] = l / D.nx; }
-    else { base[0] = l % D.nx; base[1] = l / D.nx; base[2] = 0; }
     const int faces = nfl * nlines;
+    if (t >= faces) return;
+    const int m0 = d == 0 ? nfl : D.nx, m1 = d == 1 ? nfl : D.ny;
+    const int base[3] = {(int)(t % m0), (int)((t / m0) % m1), (int)(t / ((long long)m0 * m1))};
+    const int m = base[d];
     const bool periodic = D.bc[2 * d] == MB_BC_PERIODIC;
     double out[NC] = {0, 0, 0, 0, 0};
     bool flipL, flipR;
     int pL[3], pR[3];
-    line_cell(D, d, base, m - 1, nal, &flipL, pL);
-    line_cell(D, d, base, m, nal, &flipR, pR);
+    const int cL = line_cell(D, d, base, m - 1, nal, &flipL, pL);
+    const int cR = line_cell(D, d, base, m, nal, &flipR, pR);
     // face m's time-averaged aperture (the low face of cell m; m = nal: the
     // high face of the last cell)
-    int fpos[3] = {base[0], base[1], base[2]};
-    fpos[d] = m;
-    const double bf = swept(D, fpos[0], fpos[1], fpos[2]);
+    const double bf = swept(D, base[0], base[1], base[2]);
     if (fluid_a(D, pL[0], pL[1], pL[2]) && fluid_a(D, pR[0], pR[1], pR[2]) && bf > 0.0) {
-        double QLa[NC], QRa[NC], QLb[NC], QRb[NC], F[NC];
-        evolve5(D, d, base, m - 1, nal, QLa, QRa);
-        evolve5(D, d, base, m, nal, QLb, QRb);
+        double QRa[NC], QLb[NC], G[NC], F[NC];
+        if (m >= 1 || periodic) for (int q = 0; q < NC; ++q) QRa[q] = D.E[(size_t)(NC + q) * D.n + cL];
+        else evolve5(D, d, base, m - 1, nal, G, QRa);
+        if (m < nal) for (int q = 0; q < NC; ++q) QLb[q] = D.E[(size_t)q * D.n + cR];
+        else evolve5(D, d, base, m, nal, QLb, G);
         hllc5(D.gamma, d, QRa, QLb, F);
         const int mR = m < nal ? m : (periodic ? 0 : -1);
         const int mL = m - 1 >= 0 ? m - 1 : (periodic ? nal - 1 : -1);
@@ -601,23 +680,21 @@ __global__ void k3_flux(Desc D, int nal, int nfl, int nlines) {
 
 // alpha_B Q' = alpha_A Q + lam (F_lo - F_hi) + lam (beta_hi - beta_lo)(F^B -
 // w_d Q^B) (eqs. Klein2DcompleteMovingMethod2a-c); C and Cn both receive it
+template <int d>
 __global__ void k3_update(Desc D, int nal, int nfl) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= D.n) return;
     const int i = c % D.nx, j = (c / D.nx) % D.ny, k = c / (D.nx * D.ny);
-    const int d = D.d;
     const bool periodic = D.bc[2 * d] == MB_BC_PERIODIC;
     double v[NC] = {0, 0, 0, 0, 0};
     unsigned char u = 0;
     if (fluid_a(D, i, j, k)) {
         const int ijk[3] = {i, j, k};
         const int m = ijk[d];
-        const int l = d == 0 ? k * D.ny + j : (d == 1 ? k * D.nx + i : j * D.nx + i);
         const int faces = nfl * (D.n / nal);
-        const long long flo = (long long)l * nfl + m;
-        const long long fhi = (long long)l * nfl + (m + 1 < nal || !periodic ? m + 1 : 0);
         int hi3[3] = {i, j, k};
         hi3[d] = m + 1 < nal || !periodic ? m + 1 : 0;
+        const int flo = fidx(D, nfl, i, j, k), fhi = fidx(D, nfl, hi3[0], hi3[1], hi3[2]);
         const double blo = swept(D, i, j, k), bhi = swept(D, hi3[0], hi3[1], hi3[2]);
         const double aA = alphaA(D, i, j, k);
         const bool w = in_r(D, i, j, k) && D.whas[ridx(D, i, j, k)] && blo != bhi;
@@ -753,13 +830,15 @@ __global__ void k3_bad(Desc D) {
     const int i = c % D.nx, j = (c / D.nx) % D.ny, k = c / (D.nx * D.ny);
     const double aB = alphaB(D, i, j, k);
     if (!(aB > 0.0)) return;
+    // the state content / alpha_B is physical iff the content is (alpha_B > 0):
+    // rho > 0 and 2 rho E > |m|^2, no division
     double q[NC];
     bool bad = false;
     for (int m = 0; m < NC; ++m) {
-        q[m] = D.Cn[(size_t)m * D.n + c] / aB;
-        if (!isfinite(q[m])) bad = true;
+        q[m] = D.Cn[(size_t)m * D.n + c];
+        if (!isfinite(q[m])) bad = true;   // alpha_B >= 1e-10: the quotient is finite with it
     }
-    if (!(q[0] > 0.0) || !(pressure5(D.gamma, q) > 0.0)) bad = true;
+    if (!(q[0] > 0.0) || !(2.0 * q[0] * q[4] > q[1] * q[1] + q[2] * q[2] + q[3] * q[3])) bad = true;
     if (aB < COLLAPSE * alphaA(D, i, j, k)) bad = true;
     if (!bad) return;
     const int s = atomicAdd(D.nseed, 1);
@@ -882,14 +961,15 @@ __global__ void k3_final(Desc D) {
     const int i = c % D.nx, j = (c / D.nx) % D.ny, k = c / (D.nx * D.ny);
     const double aB = alphaB(D, i, j, k);
     const bool ok = aB > 0.0 && D.upd[c];
+    const double ia = ok ? 1.0 / aB : 0.0;
     double q[NC];
     for (int m = 0; m < NC; ++m) {
-        q[m] = ok ? D.Cn[(size_t)m * D.n + c] / aB : NAN;
+        q[m] = ok ? D.Cn[(size_t)m * D.n + c] * ia : NAN;
         D.Q[(size_t)m * D.n + c] = q[m];
     }
     if (aB > 0.0 && !D.upd[c]) atomicOr(D.err, E_UNSTABLE);
     if (ok) {
-        bool bad = !(q[0] > 0.0) || !(pressure5(D.gamma, q) > 0.0);
+        bool bad = !(q[0] > 0.0) || !(2.0 * q[0] * q[4] > q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
         for (int m = 0; m < NC; ++m) if (!isfinite(q[m])) bad = true;
         if (bad) atomicOr(D.err, E_UNSTABLE);
     }
@@ -903,8 +983,10 @@ __global__ void k3_speeds(Desc D) {
     if (c < D.n && !isnan(D.Q[c])) {
         double q[NC];
         for (int m = 0; m < NC; ++m) q[m] = D.Q[(size_t)m * D.n + c];
-        const double cs = sqrt(D.gamma * pressure5(D.gamma, q) / q[0]);
-        for (int a = 0; a < 3; ++a) s[a] = fabs(q[1 + a] / q[0]) + cs;
+        const double ir = 1.0 / q[0];
+        const double p = (D.gamma - 1.0) * (q[4] - 0.5 * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) * ir);
+        const double cs = sqrt(D.gamma * p * ir);
+        for (int a = 0; a < 3; ++a) s[a] = fabs(q[1 + a] * ir) + cs;
     }
     for (int a = 0; a < 3; ++a) {
         double v = s[a];
@@ -946,6 +1028,8 @@ struct mb3_sim {
     size_t rcap = 0, rfcap = 0;
     double wall_host[NC] = {0, 0, 0, 0, 0};
     int merged = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;   // around the last sweep's k3_flux
+    float flux_ms = 0.0f;
     std::vector<void *> owned;
 };
 
@@ -1053,7 +1137,7 @@ static cudaError_t pose_alpha(mb3_sim *s, const double *T, Desc &D) {
     D = s->D, region(s, T, T, D.r0, D.rn);
     if (rc > 0) {
         const mb3::Body3 B = posed(s, T);
-        mb3::k3_cells<<<nblk((long long)rc), 256, 0, s->st>>>(D, B, B, B);
+        mb3::k3_cells<<<nblk(32LL * (long long)rc), 256, 0, s->st>>>(D, B, B, B);
     }
     return cudaGetLastError();
 }
@@ -1096,6 +1180,8 @@ mb_status mb3_create(const mb3_grid *g, double gamma, double cfl, const mb3_body
     }
     for (int q = 0; q < 6; ++q) s->bb[q] = b->bbox[q];
     cudaError_t e = cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&s->ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&s->ev1);
     const size_t n = D.n;
     size_t fmax_ = 0;
     for (int a = 0; a < 3; ++a) fmax_ = std::max(fmax_, (size_t)(nn[a] + 1) * (n / nn[a]));
@@ -1104,6 +1190,7 @@ mb_status mb3_create(const mb3_grid *g, double gamma, double cfl, const mb3_body
     if (e == cudaSuccess) e = dalloc(s, &D.C, NC * n);
     if (e == cudaSuccess) e = dalloc(s, &D.Cn, NC * n);
     if (e == cudaSuccess) e = dalloc(s, &D.F, NC * fmax_);
+    if (e == cudaSuccess) e = dalloc(s, &D.E, 2 * NC * n);
     if (e == cudaSuccess) e = dalloc(s, &D.upd, n);
     if (e == cudaSuccess) e = dalloc(s, &D.err, 1);
     if (e == cudaSuccess) e = dalloc(s, &D.wall, NC);
@@ -1132,6 +1219,8 @@ void mb3_destroy(mb3_sim *s) {
     if (!s) return;
     if (s->st) cudaStreamSynchronize(s->st);
     for (void *p : s->owned) cudaFree(p);
+    if (s->ev0) cudaEventDestroy(s->ev0);
+    if (s->ev1) cudaEventDestroy(s->ev1);
     if (s->st) cudaStreamDestroy(s->st);
     delete s;
 }
@@ -1219,17 +1308,27 @@ mb_status mb3_sweep(mb3_sim *s, int d, double dt) {
     if (e != cudaSuccess) return cuda3(s, e, "mb3_sweep");
     const mb3::Body3 BA = posed(s, TA), BM = posed(s, TM), BB = posed(s, TB);
     if (rc > 0) {
-        mb3::k3_cells<<<nblk((long long)rc), 256, 0, s->st>>>(D, BA, BM, BB);
+        mb3::k3_cells<<<nblk(32LL * (long long)rc), 256, 0, s->st>>>(D, BA, BM, BB);
         long long nfaces = 0;
         for (int a = 0; a < 4; ++a) {
             const int ax = a < 3 ? a : d;
             nfaces += (long long)(rn[0] + (ax == 0)) * (rn[1] + (ax == 1)) * (rn[2] + (ax == 2));
         }
         mb3::k3_faces<<<nblk(nfaces), 256, 0, s->st>>>(D, BM, BA, delta);
+        if (delta != 0.0) {
+            const long long nsw = (long long)(rn[0] + (d == 0)) * (rn[1] + (d == 1)) * (rn[2] + (d == 2));
+            mb3::k3_swept<<<nblk(32LL * nsw), 256, 0, s->st>>>(D, BA, delta);
+        }
         mb3::k3_wall<<<nblk((long long)rc), 256, 0, s->st>>>(D);
     }
-    mb3::k3_flux<<<nblk((long long)nfl * nlines), 256, 0, s->st>>>(D, nal, nfl, nlines);
-    mb3::k3_update<<<nblk(D.n), 256, 0, s->st>>>(D, nal, nfl);
+    const auto evolve = d == 0 ? mb3::k3_evolve<0> : d == 1 ? mb3::k3_evolve<1> : mb3::k3_evolve<2>;
+    const auto flux = d == 0 ? mb3::k3_flux<0> : d == 1 ? mb3::k3_flux<1> : mb3::k3_flux<2>;
+    const auto update = d == 0 ? mb3::k3_update<0> : d == 1 ? mb3::k3_update<1> : mb3::k3_update<2>;
+    evolve<<<nblk(D.n), 256, 0, s->st>>>(D, nal);
+    cudaEventRecord(s->ev0, s->st);
+    flux<<<nblk((long long)nfl * nlines), 256, 0, s->st>>>(D, nal, nfl, nlines);
+    cudaEventRecord(s->ev1, s->st);
+    update<<<nblk(D.n), 256, 0, s->st>>>(D, nal, nfl);
     if (rc > 0) {
         mb3::k3_evprep<<<nblk((long long)rc), 256, 0, s->st>>>(D);
         mb3::k3_events<<<nblk((long long)rc), 256, 0, s->st>>>(D);
@@ -1244,6 +1343,7 @@ mb_status mb3_sweep(mb3_sim *s, int d, double dt) {
     if (e == cudaSuccess) e = cudaMemcpyAsync(&w, D.err, sizeof(int), cudaMemcpyDeviceToHost, s->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
     if (e != cudaSuccess) return cuda3(s, e, "mb3_sweep");
+    cudaEventElapsedTime(&s->flux_ms, s->ev0, s->ev1);
     s->T[d] = TB[d];
     if (++s->sidx == 3) {
         s->sidx = 0;
@@ -1295,6 +1395,12 @@ mb_status mb3_last_sweep(mb3_sim *s, double *wall, int *merged) {
     if (!s) return MB_E_INVAL;
     if (wall) for (int q = 0; q < NC; ++q) wall[q] = s->wall_host[q];
     if (merged) *merged = s->merged;
+    return MB_OK;
+}
+
+mb_status mb3_flux_time(mb3_sim *s, double *ms) {
+    if (!s || !ms) return MB_E_INVAL;
+    *ms = s->flux_ms;
     return MB_OK;
 }
 

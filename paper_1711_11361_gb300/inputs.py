@@ -531,15 +531,15 @@ def prism_planes(poly2d):
     return np.array(nrm), np.array(off)
 
 
-def cone_planes(apex, height, radius, k_sides=24):
+def cone_planes(apex, height, radius, k_sides=24, phase=0.0):
     """A cone along +x (apex forward) as a right pyramid over the regular
-    k_sides-gon inscribed in its base circle: one lateral plane per base edge
-    through the apex, and the base plane.  Returns (normals, offsets,
-    bounding box)."""
+    k_sides-gon inscribed in its base circle (vertices at angles 2 pi (m +
+    phase) / k_sides): one lateral plane per base edge through the apex, and
+    the base plane.  Returns (normals, offsets, bounding box)."""
     ax, ay, az = apex
     xb = ax - height
     A = np.array([ax, ay, az])
-    th = 2.0 * math.pi * np.arange(k_sides) / k_sides
+    th = 2.0 * math.pi * (np.arange(k_sides) + phase) / k_sides
     V = np.stack([np.full(k_sides, xb), ay + radius * np.cos(th), az + radius * np.sin(th)], axis=1)
     nrm, off = [], []
     for m in range(k_sides):
@@ -554,3 +554,42 @@ def cone_planes(apex, height, radius, k_sides=24):
     off.append(-xb)
     bbox = (xb, ax, ay - radius, ay + radius, az - radius, az + radius)
     return np.array(nrm), np.array(off), bbox
+
+
+N3_MACH = 1.34        # the stationary shock (matches a moving Mach-1.34 shock's jumps)
+N3_T_AFTER = 1.48     # 102 us after contact, in tau = D / sqrt(p/rho) of the paper's 20 mm cone
+
+
+def n3_schardin_cone(cells_per_d=20, k_sides=24, t_after=N3_T_AFTER):
+    """The paper's three-dimensional Schardin test (Sec. III.F) as read here,
+    in units of the cone's base diameter D and the pre-shock state (rho =
+    p = 1): a cone of apex angle 60 deg (an equilateral triangle in
+    cross-section), base diameter D, as a right pyramid on a regular
+    k_sides-gon, apex along +x, moving with the pre-shock gas at u1 = M c1
+    into a stationary Mach-1.34 shock at x = 4 D (the post-shock state from
+    the Rankine-Hugoniot relations in the shock's frame); the domain 10 D x
+    10 D x 5 D (the paper's 0.2 x 0.2 x 0.1 m), the cone's centre-line on the
+    reflective side z = 0 (the paper's half domain), transmissive elsewhere;
+    the apex two cells before the shock at t = 0; run until t_after."""
+    h = 1.0 / cells_per_d
+    g = GAMMA
+    c1 = math.sqrt(g)
+    u1 = N3_MACH * c1
+    r2 = (g + 1.0) * N3_MACH ** 2 / ((g - 1.0) * N3_MACH ** 2 + 2.0)
+    p2 = 1.0 + 2.0 * g / (g + 1.0) * (N3_MACH ** 2 - 1.0)
+    u2 = u1 / r2
+    xs = 4.0 + 0.3183 * h
+    H = math.sqrt(3.0) / 2.0
+    apex = (xs - 2.0 * h, 0.0 + 0.2718 * h, 0.0)
+    # half-step phase: the symmetry plane z = 0 cuts faces through their
+    # middles, not along an edge
+    n, c, bb = cone_planes(apex, H, 0.5, k_sides, phase=0.5)
+    nx, ny, nz = 10 * cells_per_d, 10 * cells_per_d, 5 * cells_per_d
+    p = Problem3(f"n3_schardin_cone_{cells_per_d}perD", nx, ny, nz, lo=(0.0, -5.0, 0.0), hi=(10.0, 5.0, 5.0),
+                 bc=(TRANSMISSIVE, TRANSMISSIVE, TRANSMISSIVE, TRANSMISSIVE, REFLECTIVE, TRANSMISSIVE),
+                 normals=n, offsets=c, bbox=bb, U=(u1, 0.0, 0.0))
+    X, Y, Z = p.cell_centres()
+    right = X > xs
+    p.Q0 = conserved3(np.where(right, r2, 1.0), np.where(right, u2, u1), 0.0, 0.0, np.where(right, p2, 1.0))
+    p.info = dict(t_end=t_after, shock_x=xs, post_shock=(r2, u2, p2), u1=u1, cells=nx * ny * nz)
+    return p

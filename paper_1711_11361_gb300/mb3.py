@@ -11,7 +11,7 @@ from . import mb
 from .mb import MBError, MB_OK
 
 EXPORTS = ["mb3_create", "mb3_destroy", "mb3_last_error", "mb3_write_state", "mb3_read_state", "mb3_sweep",
-           "mb3_step", "mb3_cfl_dt", "mb3_last_sweep"]
+           "mb3_step", "mb3_cfl_dt", "mb3_last_sweep", "mb3_flux_time"]
 
 
 class Grid3(ctypes.Structure):
@@ -38,6 +38,7 @@ for _name, (_args, _res) in {
     "mb3_step": ([_P, ctypes.c_double, _D], _I),
     "mb3_cfl_dt": ([_P, _D], _I),
     "mb3_last_sweep": ([_P, _D, ctypes.POINTER(_I)], _I),
+    "mb3_flux_time": ([_P, _D], _I),
 }.items():
     _f = getattr(lib, _name)
     _f.argtypes, _f.restype = _args, _res
@@ -121,6 +122,12 @@ class Sim3:
         dt = ctypes.c_double()
         self._check(lib.mb3_cfl_dt(self._h, ctypes.byref(dt)))
         return dt.value
+
+    def flux_time_ms(self):
+        """Device time of the last sweep's face-flux kernel (CUDA events)."""
+        ms = ctypes.c_double()
+        self._check(lib.mb3_flux_time(self._h, ctypes.byref(ms)))
+        return ms.value
 
     def last_sweep(self):
         w = np.zeros(5)
