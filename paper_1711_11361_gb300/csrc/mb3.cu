@@ -226,6 +226,9 @@ struct Desc {
     double *E;              // evolved boundary states along d, 2 NC planes
     double *aA, *aM, *aB;   // over R
     unsigned char *tA, *tB; // over R
+    double *aP;             // alpha at the sweep's pose A over the region P
+    unsigned char *tP;      // (the previous sweep's R), with its touch flags
+    int p0[3], pn[3];
     double *bM[3];          // mid-pose apertures of R's faces, per axis
     double *bt;             // time-averaged apertures of R's d-faces
     unsigned char *whas;    // wall data over R
@@ -300,30 +303,51 @@ __device__ __forceinline__ void r_cell(const Desc &D, int t, int *i, int *j, int
 }
 
 // volume fractions at the three poses and the touch flags of R's cells,
-// one warp per cell
-__global__ void k3_cells(Desc D, Body3 BA, Body3 BM, Body3 BB) {
-    const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (t >= D.rn[0] * D.rn[1] * D.rn[2]) return;
+// one warp per cell and pose (pose B first, then M, then A, so that a
+// costly cell's poses run side by side).  CELLS_ALL: poses A, M and B;
+// CELLS_REUSE_A: pose A is the previous sweep's pose B, whose values P
+// holds (a cell outside P lies two cells or more from the body's bounding
+// box: alpha 1, no touch, as computing it gives), copied by the pose-B
+// warp; CELLS_ONE: pose B only, into all three
+enum { CELLS_ALL = 0, CELLS_REUSE_A = 1, CELLS_ONE = 2 };
+__device__ __forceinline__ double fraction(double V, double vol) {
+    const double a = fmin(1.0, fmax(0.0, 1.0 - V / vol));
+    return a < ALPHA_MIN ? 0.0 : a;
+}
+__global__ void k3_cells(Desc D, Body3 BA, Body3 BM, Body3 BB, int mode) {
+    const int rc = D.rn[0] * D.rn[1] * D.rn[2];
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int npose = mode == CELLS_ALL ? 3 : mode == CELLS_REUSE_A ? 2 : 1;
+    if (w >= npose * rc) return;
+    const int t = w % rc, pose = w / rc;   // 0: B, 1: M, 2: A
     int i, j, k;
     r_cell(D, t, &i, &j, &k);
     const double lo[3] = {node(D, 0, i), node(D, 1, j), node(D, 2, k)};
     const double hi[3] = {node(D, 0, i + 1), node(D, 1, j + 1), node(D, 2, k + 1)};
     const double h[3] = {hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2]};
     const double vol = h[0] * h[1] * h[2];
-    bool ta, tm, tb;
-    const double VA = box_solid_volume(BA, lo, h, &ta);
-    const double VM = box_solid_volume(BM, lo, h, &tm);
-    const double VB = box_solid_volume(BB, lo, h, &tb);
-    const bool l0 = (threadIdx.x & 31) == 0;
-    double a = fmin(1.0, fmax(0.0, 1.0 - VA / vol));
-    if (l0) D.aA[t] = a < ALPHA_MIN ? 0.0 : a;
-    a = fmin(1.0, fmax(0.0, 1.0 - VM / vol));
-    if (l0) D.aM[t] = a < ALPHA_MIN ? 0.0 : a;
-    a = fmin(1.0, fmax(0.0, 1.0 - VB / vol));
-    if ((threadIdx.x & 31) == 0) {
-        D.aB[t] = a < ALPHA_MIN ? 0.0 : a;
-        D.tA[t] = ta;
-        D.tB[t] = tb;
+    bool touch;
+    const double a = fraction(box_solid_volume(pose == 0 ? BB : pose == 1 ? BM : BA, lo, h, &touch), vol);
+    if ((threadIdx.x & 31) != 0) return;
+    if (pose == 0) {
+        D.aB[t] = a;
+        D.tB[t] = touch;
+        if (mode == CELLS_ONE) {
+            D.aM[t] = a;
+            D.aA[t] = a;
+            D.tA[t] = touch;
+        } else if (mode == CELLS_REUSE_A) {
+            const bool inP = i >= D.p0[0] && i < D.p0[0] + D.pn[0] && j >= D.p0[1] && j < D.p0[1] + D.pn[1] &&
+                             k >= D.p0[2] && k < D.p0[2] + D.pn[2];
+            const int q = inP ? ((k - D.p0[2]) * D.pn[1] + (j - D.p0[1])) * D.pn[0] + (i - D.p0[0]) : 0;
+            D.aA[t] = inP ? D.aP[q] : 1.0;
+            D.tA[t] = inP ? D.tP[q] : 0;
+        }
+    } else if (pose == 1) {
+        D.aM[t] = a;
+    } else {
+        D.aA[t] = a;
+        D.tA[t] = touch;
     }
 }
 
@@ -961,7 +985,7 @@ __global__ void k3_final(Desc D) {
     const int i = c % D.nx, j = (c / D.nx) % D.ny, k = c / (D.nx * D.ny);
     const double aB = alphaB(D, i, j, k);
     const bool ok = aB > 0.0 && D.upd[c];
-    const double ia = ok ? 1.0 / aB : 0.0;
+    const double ia = ok ? (aB == 1.0 ? 1.0 : 1.0 / aB) : 0.0;
     double q[NC];
     for (int m = 0; m < NC; ++m) {
         q[m] = ok ? D.Cn[(size_t)m * D.n + c] * ia : NAN;
@@ -977,22 +1001,30 @@ __global__ void k3_final(Desc D) {
 
 // maxima of |u_d| + c over the fluid cells (positive doubles compare as
 // their bit patterns)
+// (a grid-stride loop, 256-thread blocks: one atomic per block and axis)
 __global__ void k3_speeds(Desc D) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ double red[3][8];
     double s[3] = {0.0, 0.0, 0.0};
-    if (c < D.n && !isnan(D.Q[c])) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < D.n; c += gridDim.x * blockDim.x) {
+        if (isnan(D.Q[c])) continue;
         double q[NC];
         for (int m = 0; m < NC; ++m) q[m] = D.Q[(size_t)m * D.n + c];
         const double ir = 1.0 / q[0];
         const double p = (D.gamma - 1.0) * (q[4] - 0.5 * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) * ir);
         const double cs = sqrt(D.gamma * p * ir);
-        for (int a = 0; a < 3; ++a) s[a] = fabs(q[1 + a] * ir) + cs;
+        for (int a = 0; a < 3; ++a) s[a] = fmax(s[a], fabs(q[1 + a] * ir) + cs);
     }
+    const int w = threadIdx.x >> 5;
     for (int a = 0; a < 3; ++a) {
         double v = s[a];
         for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-        if ((threadIdx.x & 31) == 0 && v > 0.0)
-            atomicMax((unsigned long long *)&D.smax[a], (unsigned long long)__double_as_longlong(v));
+        if ((threadIdx.x & 31) == 0) red[a][w] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        double v = 0.0;
+        for (int q = 0; q < 8; ++q) v = fmax(v, red[threadIdx.x][q]);
+        if (v > 0.0) atomicMax((unsigned long long *)&D.smax[threadIdx.x], (unsigned long long)__double_as_longlong(v));
     }
 }
 
@@ -1026,6 +1058,8 @@ struct mb3_sim {
     cudaStream_t st = nullptr;
     std::string err;
     size_t rcap = 0, rfcap = 0;
+    bool prev_ok = false;        // aB / tB hold the current pose over the region q0, qn
+    int q0[3] = {0, 0, 0}, qn[3] = {0, 0, 0};
     double wall_host[NC] = {0, 0, 0, 0, 0};
     int merged = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;   // around the last sweep's k3_flux
@@ -1097,6 +1131,8 @@ static cudaError_t ensure_r(mb3_sim *s, size_t rc, size_t rf) {
     if (rc > s->rcap) {
         cudaStreamSynchronize(s->st);
         dfree(s, D.aA); dfree(s, D.aM); dfree(s, D.aB); dfree(s, D.tA); dfree(s, D.tB); dfree(s, D.whas);
+        dfree(s, D.aP); dfree(s, D.tP);
+        s->prev_ok = false;
         dfree(s, D.wdist); dfree(s, D.wFB); dfree(s, D.wQB); dfree(s, D.evt); dfree(s, D.emask); dfree(s, D.easum);
         const size_t c = rc + rc / 4;
         if (e == cudaSuccess) e = dalloc(s, &D.aA, c);
@@ -1104,6 +1140,8 @@ static cudaError_t ensure_r(mb3_sim *s, size_t rc, size_t rf) {
         if (e == cudaSuccess) e = dalloc(s, &D.aB, c);
         if (e == cudaSuccess) e = dalloc(s, &D.tA, c);
         if (e == cudaSuccess) e = dalloc(s, &D.tB, c);
+        if (e == cudaSuccess) e = dalloc(s, &D.aP, c);
+        if (e == cudaSuccess) e = dalloc(s, &D.tP, c);
         if (e == cudaSuccess) e = dalloc(s, &D.whas, c);
         if (e == cudaSuccess) e = dalloc(s, &D.wdist, c);
         if (e == cudaSuccess) e = dalloc(s, &D.wFB, NC * c);
@@ -1137,9 +1175,12 @@ static cudaError_t pose_alpha(mb3_sim *s, const double *T, Desc &D) {
     D = s->D, region(s, T, T, D.r0, D.rn);
     if (rc > 0) {
         const mb3::Body3 B = posed(s, T);
-        mb3::k3_cells<<<nblk(32LL * (long long)rc), 256, 0, s->st>>>(D, B, B, B);
+        mb3::k3_cells<<<nblk(32LL * (long long)rc), 256, 0, s->st>>>(D, B, B, B, mb3::CELLS_ONE);   // one pose
     }
-    return cudaGetLastError();
+    e = cudaGetLastError();
+    s->prev_ok = e == cudaSuccess;
+    for (int a = 0; a < 3; ++a) { s->q0[a] = D.r0[a]; s->qn[a] = D.rn[a]; }
+    return e;
 }
 
 extern "C" {
@@ -1294,6 +1335,15 @@ mb_status mb3_sweep(mb3_sim *s, int d, double dt) {
     const size_t rf = (size_t)(rn[0] + 1) * (rn[1] + 1) * (rn[2] + 1);
     if (e == cudaSuccess) e = ensure_r(s, rc, rf);
     if (e != cudaSuccess) return cuda3(s, e, "mb3_sweep buffers");
+    // pose A is the last pose computed (the previous sweep's B, or the pose
+    // of the last state write or read): its fractions move to aP
+    const bool reuse = s->prev_ok;
+    if (reuse) {
+        std::swap(s->D.aB, s->D.aP);
+        std::swap(s->D.tB, s->D.tP);
+        for (int a = 0; a < 3; ++a) { s->D.p0[a] = s->q0[a]; s->D.pn[a] = s->qn[a]; }
+    }
+    s->prev_ok = false;
     Desc D = s->D;
     for (int a = 0; a < 3; ++a) { D.r0[a] = r0[a]; D.rn[a] = rn[a]; }
     D.d = d;
@@ -1308,7 +1358,8 @@ mb_status mb3_sweep(mb3_sim *s, int d, double dt) {
     if (e != cudaSuccess) return cuda3(s, e, "mb3_sweep");
     const mb3::Body3 BA = posed(s, TA), BM = posed(s, TM), BB = posed(s, TB);
     if (rc > 0) {
-        mb3::k3_cells<<<nblk(32LL * (long long)rc), 256, 0, s->st>>>(D, BA, BM, BB);
+        mb3::k3_cells<<<nblk(32LL * (reuse ? 2 : 3) * (long long)rc), 256, 0, s->st>>>(
+            D, BA, BM, BB, reuse ? mb3::CELLS_REUSE_A : mb3::CELLS_ALL);
         long long nfaces = 0;
         for (int a = 0; a < 4; ++a) {
             const int ax = a < 3 ? a : d;
@@ -1343,6 +1394,8 @@ mb_status mb3_sweep(mb3_sim *s, int d, double dt) {
     if (e == cudaSuccess) e = cudaMemcpyAsync(&w, D.err, sizeof(int), cudaMemcpyDeviceToHost, s->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
     if (e != cudaSuccess) return cuda3(s, e, "mb3_sweep");
+    s->prev_ok = true;
+    for (int a = 0; a < 3; ++a) { s->q0[a] = r0[a]; s->qn[a] = rn[a]; }
     cudaEventElapsedTime(&s->flux_ms, s->ev0, s->ev1);
     s->T[d] = TB[d];
     if (++s->sidx == 3) {
@@ -1357,7 +1410,7 @@ mb_status mb3_cfl_dt(mb3_sim *s, double *dt) {
     if (!s || !dt) return MB_E_INVAL;
     double sm[3] = {0, 0, 0};
     cudaError_t e = cudaMemsetAsync(s->D.smax, 0, 3 * sizeof(double), s->st);
-    if (e == cudaSuccess) mb3::k3_speeds<<<nblk(s->D.n), 256, 0, s->st>>>(s->D);
+    if (e == cudaSuccess) mb3::k3_speeds<<<std::min(nblk(s->D.n), 152u * 8u), 256, 0, s->st>>>(s->D);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(sm, s->D.smax, 3 * sizeof(double), cudaMemcpyDeviceToHost, s->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
