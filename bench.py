@@ -581,8 +581,8 @@ def run_n2(args):
 
 
 def n3_flux_ops_per_face():
-    """FP64-pipe lane operations per face of the three-dimensional flux
-    kernel k3_flux, from the ncu capture summarised in
+    """(FP64-pipe lane operations, DRAM bytes) per face of the three-
+    dimensional flux kernel k3_flux, from the ncu capture summarised in
     profiles/n3_flux_ops.json; None when mb3.cu has changed since."""
     import hashlib
     try:
@@ -591,7 +591,7 @@ def n3_flux_ops_per_face():
             with open(os.path.join(ROOT, "paper_1711_11361_gb300", "csrc", f), "rb") as fh:
                 if hashlib.sha256(fh.read()).hexdigest() != sha:
                     return None
-        return float(d["fp64_pipe_lane_ops_per_face"])
+        return float(d["fp64_pipe_lane_ops_per_face"]), float(d["dram_bytes_per_face"])
     except (OSError, KeyError, ValueError):
         return None
 
@@ -618,11 +618,14 @@ def n3_flux_roofline(mb3, p, rate):
     faces = sum(f for f, _ in per)
     secs = sum(t for _, t in per)
     out = {"kernel": "k3_flux", "ms_per_sweep": secs / len(per) * 1e3, "faces_per_s": faces / secs}
-    ops = n3_flux_ops_per_face()
-    if ops is not None:
+    prof = n3_flux_ops_per_face()
+    if prof is not None:
+        ops, dram = prof
         achieved = ops * faces / secs
         out.update({"bound": "fp64", "achieved": achieved / 1e12, "peak": rate / 1e12,
                     "unit": "T FP64-pipe lane-ops/s", "frac": achieved / rate, "fp64_pipe_lane_ops_per_face": ops,
+                    "traffic": dram * faces / len(per), "traffic_note": "DRAM bytes per launch, ncu bytes per "
+                    "face at 20 cells per D scaled by the faces of one launch here",
                     "peak_kind": "measured: mb_fp64_rate (independent FP64 FMA chains)"})
     return out
 

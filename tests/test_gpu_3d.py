@@ -3,7 +3,8 @@ dimensional oracle (itself pinned to closed forms and to the two-dimensional
 oracle in tests/test_oracle_3d.py), through the C ABI: volume fractions at a
 pose, one sweep along each axis from identical input in both uncovering
 modes, whole steps re-seeded from the oracle, the CFL step, uniform flow, a
-cone meeting a shock free running, and a body leaving through an open side.
+cone meeting a shock free running, and the Schardin workload itself (a small
+mesh free running, and the bench's 20-cells-per-D mesh sweep by sweep).
 Tolerances: contents alpha*Q to 1e-12 relative per sweep from identical
 input; after a second and third sweep, round-off in a cut cell's content
 divided by its volume fraction enters the fluxes, as in two dimensions."""
@@ -144,4 +145,53 @@ def test_cone_meets_a_shock_free_running(mb3):
         assert orc.step(dt)[0] == 0
     assert _rel(sim.contents(), orc.contents()) <= 1e-9
     assert sim.read_state()["step"] == 10
+    sim.close()
+
+
+def test_schardin_cone_small_mesh_free_running(mb3):
+    """The Schardin workload (inputs.n3_schardin_cone) at 4 cells per D (40 x
+    40 x 20): the cone on the reflective side z = 0, the stationary shock,
+    transmissive sides; 12 free-running steps at the device's dt, each
+    oracle step at that dt; contents to 1e-9 relative."""
+    p = inputs.n3_schardin_cone(4)
+    orc = o3.Oracle3(p)
+    sim = mb3.Sim3(p)
+    for _ in range(12):
+        dt = sim.step()
+        assert orc.step(dt)[0] == 0
+    assert _rel(sim.contents(), orc.contents()) <= 1e-9
+    assert sim.last_sweep()[1] == orc.last_sweep()[1]
+    assert sim.read_state()["status"] == 0
+    sim.close()
+
+
+def test_schardin_cone_bench_mesh_sweeps(mb3):
+    """The bench's 20-cells-per-D mesh (200 x 200 x 100, 4 M cells, the
+    launch configuration bench.py times), the shock moved 0.4 D behind the
+    apex so that it crosses the cone's surface: two steps, each started from
+    the oracle's state, every sweep compared as in the re-seeded test."""
+    p = inputs.n3_schardin_cone(20)
+    X, Y, Z = p.cell_centres()
+    r2, u2, p2 = p.info["post_shock"]
+    xs = p.info["shock_x"] - 2.0 / 20 - 0.4
+    right = X > xs
+    p.Q0 = inputs.conserved3(np.where(right, r2, 1.0), np.where(right, u2, p.info["u1"]), 0.0, 0.0,
+                             np.where(right, p2, 1.0))
+    orc = o3.Oracle3(p)
+    sim = mb3.Sim3(p)
+    for s in range(2):
+        clk = orc.clock()
+        sim.write_state(orc.state(), clk["t"], clk["T"])
+        orc.set_state(orc.state(), clk["t"], clk["T"], s)
+        dt = orc.cfl_dt()
+        assert abs(sim.cfl_dt() - dt) <= 1e-14 * dt
+        amp = 1.0
+        for m, d in enumerate((0, 1, 2) if s % 2 == 0 else (2, 1, 0)):
+            assert orc.sweep(d, dt) == 0
+            sim.sweep(d, dt)
+            tol = 1e-11 if m == 0 else max(1e-11, 1e-15 / amp)
+            assert _rel(sim.contents(), orc.contents()) <= tol, (s, d)
+            assert sim.last_sweep()[1] == orc.last_sweep()[1]
+            a = orc.alpha()
+            amp *= a[a > 0].min()
     sim.close()
