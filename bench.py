@@ -580,10 +580,11 @@ def run_n2(args):
                       "paper": paper, "runs": rows}))
 
 
-def n3_flux_ops_per_face():
+def n3_flux_profile(precision):
     """(FP64-pipe lane operations, DRAM bytes) per face of the three-
-    dimensional flux kernel k3_flux, from the ncu capture summarised in
-    profiles/n3_flux_ops.json; None when mb3.cu has changed since."""
+    dimensional flux kernel k3_flux in the given precision ("fp64" or
+    "fp32"), from the ncu captures summarised in profiles/n3_flux_ops.json;
+    None when mb3.cu has changed since."""
     import hashlib
     try:
         d = json.load(open(os.path.join(ROOT, "profiles", "n3_flux_ops.json")))
@@ -591,19 +592,24 @@ def n3_flux_ops_per_face():
             with open(os.path.join(ROOT, "paper_1711_11361_gb300", "csrc", f), "rb") as fh:
                 if hashlib.sha256(fh.read()).hexdigest() != sha:
                     return None
-        return float(d["fp64_pipe_lane_ops_per_face"]), float(d["dram_bytes_per_face"])
+        e = d[precision]
+        return float(e["fp64_pipe_lane_ops_per_face"]), float(e["dram_bytes_per_face"])
     except (OSError, KeyError, ValueError):
         return None
 
 
-def n3_flux_roofline(mb3, p, rate):
-    """k3_flux, the three-dimensional path's dominant kernel, against the
-    FP64 pipe: its device time per sweep (CUDA events around each launch on
-    the simulation's stream, two steps' sweeps from the initial state),
-    faces per second, and FP64-pipe lane operations per second against the
-    measured FP64 rate."""
-    from paper_1711_11361_gb300 import inputs
-    sim = mb3.Sim3(p)
+N3_FLUX_F32_BYTES = 80   # per face: two cells' FP32 evolved states (2 x 20 B) read, the FP64 flux (40 B) written
+
+
+def n3_flux_roofline(mb3, p, rate, precision="fp64"):
+    """k3_flux, the three-dimensional path's dominant kernel: its device time
+    per sweep (CUDA events around each launch on the simulation's stream,
+    two steps' sweeps from the initial state) and faces per second.  FP64:
+    FP64-pipe lane operations per second against the measured FP64 rate.
+    FP32 flux option: algorithmic bytes per second against the measured HBM
+    copy bandwidth.  `rate` is the FP64 FMA rate."""
+    from paper_1711_11361_gb300 import inputs, mb
+    sim = mb3.Sim3(p, precision=mb.FP32 if precision == "fp32" else mb.FP64)
     dt = sim.cfl_dt()
     n = p.nx * p.ny * p.nz
     nn = (p.nx, p.ny, p.nz)
@@ -617,9 +623,16 @@ def n3_flux_roofline(mb3, p, rate):
     sim.close()
     faces = sum(f for f, _ in per)
     secs = sum(t for _, t in per)
-    out = {"kernel": "k3_flux", "ms_per_sweep": secs / len(per) * 1e3, "faces_per_s": faces / secs}
-    prof = n3_flux_ops_per_face()
-    if prof is not None:
+    out = {"kernel": "k3_flux", "precision": precision, "ms_per_sweep": secs / len(per) * 1e3,
+           "faces_per_s": faces / secs}
+    prof = n3_flux_profile(precision)
+    if precision == "fp32":
+        hbm, kind = measured_peaks()
+        achieved = N3_FLUX_F32_BYTES * faces / secs / 1e9
+        out.update({"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                    "algorithmic_bytes_per_face": N3_FLUX_F32_BYTES, "peak_kind": f"{kind} (MEASURED_PEAKS hbm_gbs)",
+                    "traffic": None if prof is None else prof[1] * faces / len(per)})
+    elif prof is not None:
         ops, dram = prof
         achieved = ops * faces / secs
         out.update({"bound": "fp64", "achieved": achieved / 1e12, "peak": rate / 1e12,
@@ -639,14 +652,17 @@ def run_n3(args):
     for its 20 mm cone), at each of --n3-resolutions cells per diameter.
     Reports cell-sweeps/s (cells x 3 sweeps per step), the steps, the cells
     merged by the safeguard and the status; the 3-D oracle on a bounded
-    sample (one step of the 10-per-D case) is the CPU baseline."""
+    sample (one step of the 10-per-D case) is the CPU baseline.  The FP32
+    flux option (mb3_set_precision) runs the finest mesh too, with its
+    alpha-weighted L1 density difference from the FP64 path over 40 steps
+    at the FP64 path's dt on the 10-per-D mesh."""
     import torch
-    from paper_1711_11361_gb300 import inputs, mb3
+    from paper_1711_11361_gb300 import inputs, mb, mb3
     torch.cuda.set_device(0)
-    rows = []
-    for k in args.n3_resolutions:
+
+    def run(k, precision):
         p = inputs.n3_schardin_cone(k)
-        sim = mb3.Sim3(p)
+        sim = mb3.Sim3(p, precision=precision)
         sim.step()                       # untimed warm-up step (buffers, first launch)
         sim.write_state(p.Q0)
         t, steps, merged = 0.0, 0, 0
@@ -658,18 +674,46 @@ def run_n3(args):
         el = time.perf_counter() - t0
         st = sim.read_state(check=False)
         sim.close()
-        rows.append({"cells_per_D": k, "grid": f"{p.nx}x{p.ny}x{p.nz}", "cells": p.info["cells"], "steps": steps,
-                     "seconds": el, "cell_sweeps_per_s": p.info["cells"] * 3 * steps / el,
-                     "ms_per_step": el / steps * 1e3, "status": int(st["status"]), "t_end": t,
-                     "merged_cells_last_sweeps": merged})
-    line = {"metric": "cell-sweeps/s, three-dimensional FP64 path (x, y, z sweeps), Schardin cone",
-            "value": rows[-1]["cell_sweeps_per_s"], "unit": "cell-sweeps/s", "dtype": "f64", "data": "synthetic",
+        return {"cells_per_D": k, "grid": f"{p.nx}x{p.ny}x{p.nz}", "cells": p.info["cells"], "steps": steps,
+                "seconds": el, "cell_sweeps_per_s": p.info["cells"] * 3 * steps / el,
+                "ms_per_step": el / steps * 1e3, "status": int(st["status"]), "t_end": t,
+                "merged_cells_last_sweeps": merged, "precision": "fp32" if precision == mb.FP32 else "fp64"}
+
+    main = mb.FP32 if args.n3_precision == "fp32" else mb.FP64
+    rows = [run(k, main) for k in args.n3_resolutions]
+    fp32 = None
+    if args.n3_precision != "fp64":
+        fp32 = run(args.n3_resolutions[-1], mb.FP32) if args.n3_precision == "both" else rows[-1]
+        p = inputs.n3_schardin_cone(args.n3_resolutions[0])
+        s64, s32 = mb3.Sim3(p), mb3.Sim3(p, precision=mb.FP32)
+        for _ in range(40):
+            dt = s64.step()
+            s32.step(dt)
+        a, b = s64.read_state(alpha=True, check=False), s32.read_state(alpha=True, check=False)
+        s64.close()
+        s32.close()
+        fl = a["alpha"] > 0
+        w = a["alpha"][fl]
+        fp32["l1_density_rel_vs_fp64"] = float(np.sum(w * np.abs(b["Q"][0][fl] - a["Q"][0][fl])) /
+                                               np.sum(w * np.abs(a["Q"][0][fl])))
+        fp32["accuracy_sample"] = f"{args.n3_resolutions[0]} cells per D, 40 steps at the FP64 path's dt"
+        if args.n3_precision == "both":
+            fp32["speedup_vs_fp64"] = fp32["cell_sweeps_per_s"] / rows[-1]["cell_sweeps_per_s"]
+    f32 = main == mb.FP32
+    line = {"metric": "cell-sweeps/s, three-dimensional " + ("path, FP32 flux option" if f32 else "FP64 path") +
+                      " (x, y, z sweeps), Schardin cone",
+            "value": rows[-1]["cell_sweeps_per_s"], "unit": "cell-sweeps/s", "dtype": "f32 flux, f64 state" if f32
+            else "f64", "data": "synthetic",
             "config": {"workload": "n3_schardin_cone_10Dx10Dx5D", "mach": inputs.N3_MACH,
                        "t_after_contact_tau": inputs.N3_T_AFTER, "cone": "24-sided pyramid, apex angle 60 deg"},
             "runs": rows}
-    from paper_1711_11361_gb300 import mb
+    if args.n3_precision != "fp64":
+        line["fp32_flux_option"] = fp32
     rate = mb.fp64_rate(torch.cuda.current_stream().cuda_stream)
-    line["roofline"] = n3_flux_roofline(mb3, inputs.n3_schardin_cone(args.n3_resolutions[-1]), rate)
+    finest = inputs.n3_schardin_cone(args.n3_resolutions[-1])
+    line["roofline"] = n3_flux_roofline(mb3, finest, rate, "fp32" if f32 else "fp64")
+    if args.n3_precision == "both":
+        line["roofline_fp32_flux_option"] = n3_flux_roofline(mb3, finest, rate, "fp32")
     if not args.no_cpu_baseline:
         from oracle import o3
         p = inputs.n3_schardin_cone(10)
@@ -852,6 +896,8 @@ def main():
                     help="cells per tube diameter of the open-tube runs")
     ap.add_argument("--n3-resolutions", type=int, nargs="+", default=[10, 20],
                     help="cells per cone diameter of the three-dimensional Schardin runs")
+    ap.add_argument("--n3-precision", choices=["both", "fp64", "fp32"], default="both",
+                    help="three-dimensional runs: the FP64 path with the FP32 flux option beside it, or one of them")
     ap.add_argument("--c3-period", action="store_true",
                     help="FP32 vs FP64 accuracy of the pitching NACA 0012 workload after one full pitch period")
     ap.add_argument("--accuracy-steps", type=int, default=500,

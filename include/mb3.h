@@ -76,6 +76,16 @@ mb_status mb3_cfl_dt(mb3_sim *sim, double *dt);
 /* the last sweep's summed wall terms (5 doubles, optional) and cells merged
  * by the safeguard (optional) */
 mb_status mb3_last_sweep(mb3_sim *sim, double *wall, int *merged);
+/* the flow arithmetic's precision: MB_FP64 (the default; every kernel in
+ * FP64, the path the parity tests hold to the oracle) or MB_FP32 (the
+ * MUSCL-Hancock evolved states, the HLLC fluxes of faces without a wall
+ * part and the CFL wave speeds in FP32, from an FP32 copy of the state kept
+ * beside it).  Geometry, wall states and shielded fluxes, the update of the
+ * contents, covering and uncovering, the safeguard and the state stay FP64,
+ * and fluxes are stored in FP64, so the update stays conservative to FP64
+ * rounding.  Allocates the copy (4 bytes x 5 per cell) on first use;
+ * MB_E_STATE in the middle of a step, MB_E_INVAL for another value. */
+mb_status mb3_set_precision(mb3_sim *sim, int precision);
 /* device time (ms) of the last sweep's face-flux kernel (MUSCL-Hancock +
  * HLLC + stabilised flux of every face along the sweep), from CUDA events
  * recorded around it on the simulation's stream */

@@ -13,7 +13,7 @@
 //   k3_flux   HLLC + stabilised flux of every d-face
 //   k3_update the conservative update alpha_B Q' of every cell
 //   k3_events covering / uncovering, gathered per cell in cell order (R)
-//   k3_bad / k3_mix  the positivity safeguard (one thread merges)
+//   k3_bad / k3_mix  the positivity safeguard (one block merges in shared memory)
 //   k3_final  Q = content / alpha_B, solid cells NaN, error checks
 // Geometry: the volume of a box inside the body by the divergence theorem
 // over the faces of box ∩ body, each face the plane's polygon clipped by all
@@ -22,6 +22,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -224,6 +225,9 @@ struct Desc {
     int r0[3], rn[3];       // region R: first cell and extent per axis
     double *Q, *Qn, *C, *Cn, *F;
     double *E;              // evolved boundary states along d, 2 NC planes
+    int f32;                // FP32 flux option: Qf, and E read as floats
+    float *Qf;              // the state in FP32 (FP32 flux option)
+    float gammaf, hlamf;    // gamma and lam / 2 in FP32 (no conversion per thread)
     double *aA, *aM, *aB;   // over R
     unsigned char *tA, *tB; // over R
     double *aP;             // alpha at the sweep's pose A over the region P
@@ -278,12 +282,56 @@ __device__ __forceinline__ double alphaB(const Desc &D, int i, int j, int k) {
 __device__ __forceinline__ double swept(const Desc &D, int i, int j, int k) {
     return in_rf(D, D.d, i, j, k) ? D.bt[rfidx(D, D.d, i, j, k)] : 1.0;
 }
+// (outside R without a floating-point test: alpha_A = 1 there)
 __device__ __forceinline__ bool fluid_a(const Desc &D, int i, int j, int k) {
-    const double a = alphaA(D, i, j, k);
-    return a > 0.0 || (D.gcl && a == 0.0 && alphaB(D, i, j, k) > 0.0);
+    if (!in_r(D, i, j, k)) return true;
+    const int r = ridx(D, i, j, k);
+    const double a = D.aA[r];
+    return a > 0.0 || (D.gcl && a == 0.0 && D.aB[r] > 0.0);
 }
+// float to double exactly by moving the bit fields: integer work, off
+// GB300's narrow FP64 pipe, which takes conversions too.  Normal numbers
+// rebias the exponent (127 -> 1023); a subnormal m 2^-149 is normalised
+// at its highest set bit p; infinities and NaN keep an all-ones exponent
+// and the shifted payload
+__device__ __forceinline__ double widen(float x) {
+    const unsigned u = __float_as_uint(x), e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+    const unsigned long long s = (unsigned long long)(u >> 31) << 63;
+    unsigned long long b;
+    if (e == 0u) {
+        if (m == 0u) {
+            b = s;
+        } else {
+            const int p = 31 - __clz((int)m);
+            b = s | ((unsigned long long)(p + 874) << 52) | (((unsigned long long)m << (52 - p)) & 0xfffffffffffffULL);
+        }
+    } else if (e == 0xffu) {
+        b = s | (0x7ffULL << 52) | ((unsigned long long)m << 29);
+    } else {
+        b = s | ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)m << 29);
+    }
+    return __longlong_as_double((long long)b);
+}
+__device__ __forceinline__ double widen(double x) { return x; }
 __device__ __forceinline__ double node(const Desc &D, int a, int i) { return D.lo[a] + (double)i * D.h[a]; }
+// x is neither infinite nor NaN: its exponent field is not all ones (an
+// integer test, off GB300's narrow FP64 pipe)
+__device__ __forceinline__ bool finite64(double x) {
+    return (__double_as_longlong(x) & 0x7ff0000000000000LL) != 0x7ff0000000000000LL;
+}
 
+// the state content / alpha_B is physical iff the content is (alpha_B > 0):
+// rho > 0 and 2 rho E > |m|^2, no division
+__device__ __forceinline__ bool content_bad(const double *q) {
+    bool bad = false;
+    for (int m = 0; m < NC; ++m) if (!finite64(q[m])) bad = true;   // alpha_B >= 1e-10: the quotient is finite with it
+    return bad || !(q[0] > 0.0) || !(2.0 * q[0] * q[4] > q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+}
+__device__ __forceinline__ void add_seed(const Desc &D, int c) {
+    const int s = atomicAdd(D.nseed, 1);
+    if (s < SEEDCAP) D.seeds[s] = c;
+    else atomicOr(D.err, E_SEEDCAP);
+}
 // neighbour (i+di, j+dj, k+dk) under the periodic sides, -1 outside
 __device__ __forceinline__ int nbr(const Desc &D, int i, int j, int k, int di, int dj, int dk, int *ii, int *jj,
                                    int *kk) {
@@ -453,7 +501,10 @@ __global__ void k3_wall(Desc D) {
                         for (int q = 0; q < NC; ++q) acc[q] += w * D.Q[(size_t)q * D.n + cc];
                     }
         if (wsum == 0.0) atomicOr(D.err, E_NONBR);
-        else for (int q = 0; q < NC; ++q) D.Q[(size_t)q * D.n + c] = acc[q] / wsum;
+        else for (int q = 0; q < NC; ++q) {
+            D.Q[(size_t)q * D.n + c] = acc[q] / wsum;
+            if (D.f32) D.Qf[(size_t)q * D.n + c] = float(acc[q] / wsum);
+        }
     }
     const bool fl = aA > 0.0 || (D.gcl && aA == 0.0 && aB > 0.0);
     D.whas[t] = 0;
@@ -504,49 +555,70 @@ __device__ __forceinline__ double pressure5(double g, const double *q) {
     return (g - 1.0) * (q[4] - 0.5 * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) / q[0]);
 }
 // (GB300's FP64 pipe is narrow: each quotient costs a Newton sequence, so
-// the kernels share one reciprocal of rho where they can)
-__device__ __forceinline__ void flux5(double g, int d, const double *q, double *f) {
-    const double rho = q[0], ir = 1.0 / rho, un = q[1 + d] * ir;
-    const double p = (g - 1.0) * (q[4] - 0.5 * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) * ir);
+// the kernels share one reciprocal of rho where they can.  The flow
+// arithmetic below takes its type T as a template argument: double for the
+// FP64 path, float for the FP32 flux option; every literal is a T, so the
+// float instances stay in float and the double ones are the FP64 path's
+// arithmetic unchanged)
+template <typename T>
+__device__ __forceinline__ void flux5(T g, int d, const T *q, T *f) {
+    const T rho = q[0], ir = T(1) / rho, un = q[1 + d] * ir;
+    const T p = (g - T(1)) * (q[4] - T(0.5) * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) * ir);
     f[0] = rho * un;
-    for (int m = 0; m < 3; ++m) f[1 + m] = q[1 + m] * un + (m == d ? p : 0.0);
+    for (int m = 0; m < 3; ++m) f[1 + m] = q[1 + m] * un + (m == d ? p : T(0));
     f[4] = un * (q[4] + p);
 }
 // HLLC, Davis wave speeds (Toro, Riemann Solvers ch. 10)
-__device__ __forceinline__ void hllc5(double g, int d, const double *qL, const double *qR, double *F) {
+template <typename T>
+__device__ __forceinline__ void hllc5(T g, int d, const T *qL, const T *qR, T *F) {
     const int in = 1 + d;
-    const double rL = qL[0], rR = qR[0], iL = 1.0 / rL, iR = 1.0 / rR;
-    const double uL = qL[in] * iL, uR = qR[in] * iR;
-    const double pL = (g - 1.0) * (qL[4] - 0.5 * (qL[1] * qL[1] + qL[2] * qL[2] + qL[3] * qL[3]) * iL);
-    const double pR = (g - 1.0) * (qR[4] - 0.5 * (qR[1] * qR[1] + qR[2] * qR[2] + qR[3] * qR[3]) * iR);
-    const double cL = sqrt(g * pL * iL), cR = sqrt(g * pR * iR);
-    const double SL = fmin(uL - cL, uR - cR), SR = fmax(uL + cL, uR + cR);
-    if (SL >= 0.0) { flux5(g, d, qL, F); return; }
-    if (SR <= 0.0) { flux5(g, d, qR, F); return; }
-    const double num = pR - pL + rL * uL * (SL - uL) - rR * uR * (SR - uR);
-    const double den = rL * (SL - uL) - rR * (SR - uR);
-    const double Ss = num / den;
-    const bool left = Ss >= 0.0;
-    const double *q = left ? qL : qR;
-    const double r = left ? rL : rR, ir = left ? iL : iR, u = left ? uL : uR, p = left ? pL : pR;
-    const double S = left ? SL : SR;
-    double f[NC], qs[NC];
+    const T rL = qL[0], rR = qR[0], iL = T(1) / rL, iR = T(1) / rR;
+    const T uL = qL[in] * iL, uR = qR[in] * iR;
+    const T pL = (g - T(1)) * (qL[4] - T(0.5) * (qL[1] * qL[1] + qL[2] * qL[2] + qL[3] * qL[3]) * iL);
+    const T pR = (g - T(1)) * (qR[4] - T(0.5) * (qR[1] * qR[1] + qR[2] * qR[2] + qR[3] * qR[3]) * iR);
+    const T cL = sqrt(g * pL * iL), cR = sqrt(g * pR * iR);
+    const T SL = fmin(uL - cL, uR - cR), SR = fmax(uL + cL, uR + cR);
+    if (SL >= T(0)) { flux5(g, d, qL, F); return; }
+    if (SR <= T(0)) { flux5(g, d, qR, F); return; }
+    const T num = pR - pL + rL * uL * (SL - uL) - rR * uR * (SR - uR);
+    const T den = rL * (SL - uL) - rR * (SR - uR);
+    const T Ss = num / den;
+    const bool left = Ss >= T(0);
+    const T *q = left ? qL : qR;
+    const T r = left ? rL : rR, ir = left ? iL : iR, u = left ? uL : uR, p = left ? pL : pR;
+    const T S = left ? SL : SR;
+    T f[NC], qs[NC];
     f[0] = r * u;
-    for (int m = 0; m < 3; ++m) f[1 + m] = q[1 + m] * u + (m == d ? p : 0.0);
+    for (int m = 0; m < 3; ++m) f[1 + m] = q[1 + m] * u + (m == d ? p : T(0));
     f[4] = u * (q[4] + p);
     // fac = a / dS and p / a with a = rho (S - u), dS = S - S*, from one
     // reciprocal of a dS
-    const double a = r * (S - u), dS = S - Ss, rr = 1.0 / (a * dS);
-    const double fac = a * a * rr;
+    const T a = r * (S - u), dS = S - Ss, rr = T(1) / (a * dS);
+    const T fac = a * a * rr;
     qs[0] = fac;
     for (int m = 0; m < 3; ++m) qs[1 + m] = m == d ? fac * Ss : fac * (q[1 + m] * ir);
     qs[4] = fac * (q[4] * ir + (Ss - u) * (Ss + p * dS * rr));
     for (int k = 0; k < NC; ++k) F[k] = f[k] + S * (qs[k] - q[k]);
 }
-__device__ __forceinline__ double vanleer(double dm, double dp) {
-    const double pr = dm * dp;
-    return pr > 0.0 ? 2.0 * pr / (dm + dp) : 0.0;
+template <typename T>
+__device__ __forceinline__ T vanleer(T dm, T dp) {
+    const T pr = dm * dp;
+    return pr > T(0) ? T(2) * pr / (dm + dp) : T(0);
 }
+// gamma and lam / 2 in the type T
+template <typename T> __device__ __forceinline__ T gam(const Desc &D);
+template <> __device__ __forceinline__ double gam<double>(const Desc &D) { return D.gamma; }
+template <> __device__ __forceinline__ float gam<float>(const Desc &D) { return D.gammaf; }
+template <typename T> __device__ __forceinline__ T halflam(const Desc &D);
+template <> __device__ __forceinline__ double halflam<double>(const Desc &D) { return 0.5 * D.lam; }
+template <> __device__ __forceinline__ float halflam<float>(const Desc &D) { return D.hlamf; }
+// the state and evolved-state arrays of the type T
+template <typename T> __device__ __forceinline__ const T *qsrc(const Desc &D);
+template <> __device__ __forceinline__ const double *qsrc<double>(const Desc &D) { return D.Q; }
+template <> __device__ __forceinline__ const float *qsrc<float>(const Desc &D) { return D.Qf; }
+template <typename T> __device__ __forceinline__ T *esrc(const Desc &D);
+template <> __device__ __forceinline__ double *esrc<double>(const Desc &D) { return D.E; }
+template <> __device__ __forceinline__ float *esrc<float>(const Desc &D) { return reinterpret_cast<float *>(D.E); }
 
 // the cell at position m along d of the line through (i, j, k) (the
 // coordinate along d replaced), with the boundary conditions' ghosts:
@@ -568,36 +640,37 @@ __device__ __forceinline__ int line_cell(const Desc &D, int d, const int *base, 
 // MUSCL-Hancock evolved boundary states QL, QR of the cell at position m
 // along the line (conserved variables, van Leer, zero slope next to a solid
 // cell, first order where an evolved state is not physical)
-__device__ __forceinline__ void evolve5(const Desc &D, int d, const int *base, int m, int nal, double *QL,
-                                        double *QR) {
-    double q[3][NC];
+template <typename T>
+__device__ __forceinline__ void evolve5(const Desc &D, int d, const int *base, int m, int nal, T *QL, T *QR) {
+    const T *Q = qsrc<T>(D);
+    T q[3][NC];
     bool fl[3];
     for (int s = 0; s < 3; ++s) {
         bool flip;
         int pos[3];
         const int c = line_cell(D, d, base, m - 1 + s, nal, &flip, pos);
         fl[s] = fluid_a(D, pos[0], pos[1], pos[2]);
-        for (int k = 0; k < NC; ++k) q[s][k] = D.Q[(size_t)k * D.n + c];
+        for (int k = 0; k < NC; ++k) q[s][k] = Q[(size_t)k * D.n + c];
         if (flip) q[s][1 + d] = -q[s][1 + d];
     }
     const bool lim = fl[0] && fl[2];
-    const double g = D.gamma;
-    double qL[NC], qR[NC], fL[NC], fR[NC];
+    const T g = gam<T>(D), hl = halflam<T>(D);
+    T qL[NC], qR[NC], fL[NC], fR[NC];
     for (int k = 0; k < NC; ++k) {
-        const double sl = lim ? vanleer(q[1][k] - q[0][k], q[2][k] - q[1][k]) : 0.0;
-        qL[k] = q[1][k] - 0.5 * sl;
-        qR[k] = q[1][k] + 0.5 * sl;
+        const T sl = lim ? vanleer(q[1][k] - q[0][k], q[2][k] - q[1][k]) : T(0);
+        qL[k] = q[1][k] - T(0.5) * sl;
+        qR[k] = q[1][k] + T(0.5) * sl;
     }
     flux5(g, d, qL, fL);
     flux5(g, d, qR, fR);
     for (int k = 0; k < NC; ++k) {
-        const double dfl = 0.5 * D.lam * (fL[k] - fR[k]);
+        const T dfl = hl * (fL[k] - fR[k]);
         QL[k] = qL[k] + dfl;
         QR[k] = qR[k] + dfl;
     }
     // physical: rho > 0 and p > 0, i.e. 2 rho E > |m|^2
-    const bool okL = QL[0] > 0.0 && 2.0 * QL[0] * QL[4] > QL[1] * QL[1] + QL[2] * QL[2] + QL[3] * QL[3];
-    const bool okR = QR[0] > 0.0 && 2.0 * QR[0] * QR[4] > QR[1] * QR[1] + QR[2] * QR[2] + QR[3] * QR[3];
+    const bool okL = QL[0] > T(0) && T(2) * QL[0] * QL[4] > QL[1] * QL[1] + QL[2] * QL[2] + QL[3] * QL[3];
+    const bool okR = QR[0] > T(0) && T(2) * QR[0] * QR[4] > QR[1] * QR[1] + QR[2] * QR[2] + QR[3] * QR[3];
     if (!okL || !okR)
         for (int k = 0; k < NC; ++k) { QL[k] = q[1][k]; QR[k] = q[1][k]; }
 }
@@ -614,17 +687,18 @@ __device__ __forceinline__ int fidx(const Desc &D, int nfl, int i, int j, int k)
 // argument, so that the per-direction indexing is static)
 // the evolved boundary states of every fluid cell along d, once per cell:
 // E holds QL in planes 0..NC-1 and QR in planes NC..2NC-1
-template <int d>
+template <int d, typename T>
 __global__ void k3_evolve(Desc D, int nal) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= D.n) return;
     const int base[3] = {c % D.nx, (c / D.nx) % D.ny, c / (D.nx * D.ny)};
     if (!fluid_a(D, base[0], base[1], base[2])) return;
-    double QL[NC], QR[NC];
+    T QL[NC], QR[NC];
     evolve5(D, d, base, base[d], nal, QL, QR);
+    T *E = esrc<T>(D);
     for (int q = 0; q < NC; ++q) {
-        D.E[(size_t)q * D.n + c] = QL[q];
-        D.E[(size_t)(NC + q) * D.n + c] = QR[q];
+        E[(size_t)q * D.n + c] = QL[q];
+        E[(size_t)(NC + q) * D.n + c] = QR[q];
     }
 }
 
@@ -633,7 +707,7 @@ __global__ void k3_evolve(Desc D, int nal) {
 // NC planes of F, face m of a line between its cells m-1 and m; the
 // evolved states of the cells come from E, those of a boundary's ghost
 // cells (a periodic ghost is the cell it wraps to) are evolved here
-template <int d>
+template <int d, typename T>
 __global__ void k3_flux(Desc D, int nal, int nfl, int nlines) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int faces = nfl * nlines;
@@ -648,19 +722,22 @@ __global__ void k3_flux(Desc D, int nal, int nfl, int nlines) {
     const int cL = line_cell(D, d, base, m - 1, nal, &flipL, pL);
     const int cR = line_cell(D, d, base, m, nal, &flipR, pR);
     // face m's time-averaged aperture (the low face of cell m; m = nal: the
-    // high face of the last cell)
-    const double bf = swept(D, base[0], base[1], base[2]);
-    if (fluid_a(D, pL[0], pL[1], pL[2]) && fluid_a(D, pR[0], pR[1], pR[2]) && bf > 0.0) {
-        double QRa[NC], QLb[NC], G[NC], F[NC];
-        if (m >= 1 || periodic) for (int q = 0; q < NC; ++q) QRa[q] = D.E[(size_t)(NC + q) * D.n + cL];
+    // high face of the last cell): 1 outside R
+    const bool fin = in_rf(D, d, base[0], base[1], base[2]);
+    const double bf = fin ? D.bt[rfidx(D, d, base[0], base[1], base[2])] : 1.0;
+    if (fluid_a(D, pL[0], pL[1], pL[2]) && fluid_a(D, pR[0], pR[1], pR[2]) && (!fin || bf > 0.0)) {
+        const T *E = esrc<T>(D);
+        T QRa[NC], QLb[NC], G[NC], F[NC];
+        if (m >= 1 || periodic) for (int q = 0; q < NC; ++q) QRa[q] = E[(size_t)(NC + q) * D.n + cL];
         else evolve5(D, d, base, m - 1, nal, G, QRa);
-        if (m < nal) for (int q = 0; q < NC; ++q) QLb[q] = D.E[(size_t)q * D.n + cR];
+        if (m < nal) for (int q = 0; q < NC; ++q) QLb[q] = E[(size_t)q * D.n + cR];
         else evolve5(D, d, base, m, nal, QLb, G);
-        hllc5(D.gamma, d, QRa, QLb, F);
+        hllc5(gam<T>(D), d, QRa, QLb, F);
         const int mR = m < nal ? m : (periodic ? 0 : -1);
         const int mL = m - 1 >= 0 ? m - 1 : (periodic ? nal - 1 : -1);
         double sR = 0.0, sL = 0.0, dR = 0.0, dL = 0.0;
         const double *FBR = nullptr, *FBL = nullptr;
+        bool wall = false;   // a neighbour has wall data (else sR = sL = 0, no test needed)
         if (mR >= 0) {
             int c3[3] = {base[0], base[1], base[2]};
             c3[d] = mR;
@@ -669,6 +746,7 @@ __global__ void k3_flux(Desc D, int nal, int nfl, int nlines) {
             if (in_r(D, c3[0], c3[1], c3[2])) {
                 const int r = ridx(D, c3[0], c3[1], c3[2]);
                 if (D.whas[r]) {
+                    wall = true;
                     sR = fmax(0.0, bf - swept(D, f3[0], f3[1], f3[2]));
                     dR = D.wdist[r];
                     FBR = &D.wFB[(size_t)NC * r];
@@ -681,29 +759,38 @@ __global__ void k3_flux(Desc D, int nal, int nfl, int nlines) {
             if (in_r(D, c3[0], c3[1], c3[2])) {
                 const int r = ridx(D, c3[0], c3[1], c3[2]);
                 if (D.whas[r]) {
+                    wall = true;
                     sL = fmax(0.0, bf - swept(D, c3[0], c3[1], c3[2]));
                     dL = D.wdist[r];
                     FBL = &D.wFB[(size_t)NC * r];
                 }
             }
         }
-        if (sR + sL > bf) {
+        if (wall && sR + sL > bf) {
             const double sc = bf / (sR + sL);
             sR *= sc;
             sL *= sc;
         }
-        for (int q = 0; q < NC; ++q) {
-            double v = (bf - sL - sR) * F[q];
-            if (sR > 0.0) v += sR * (FBR[q] + dR * (F[q] - FBR[q]));
-            if (sL > 0.0) v += sL * (FBL[q] + dL * (F[q] - FBL[q]));
-            out[q] = v;
+        if (wall && (sR > 0.0 || sL > 0.0)) {   // the shielded parts, in FP64
+            for (int q = 0; q < NC; ++q) {
+                const double Fq = F[q];
+                double v = (bf - sL - sR) * Fq;
+                if (sR > 0.0) v += sR * (FBR[q] + dR * (Fq - FBR[q]));
+                if (sL > 0.0) v += sL * (FBL[q] + dL * (Fq - FBL[q]));
+                out[q] = v;
+            }
+        } else {                                // (bf - 0 - 0) F
+            const T b = fin ? T(bf) : T(1);
+            for (int q = 0; q < NC; ++q) out[q] = widen(b * F[q]);
         }
     }
+    // fluxes are stored in FP64 either way, so that the update's
+    // differences F_lo - F_hi telescope as in the FP64 path
     for (int q = 0; q < NC; ++q) D.F[(size_t)q * faces + t] = out[q];
 }
 
 // alpha_B Q' = alpha_A Q + lam (F_lo - F_hi) + lam (beta_hi - beta_lo)(F^B -
-// w_d Q^B) (eqs. Klein2DcompleteMovingMethod2a-c); C and Cn both receive it
+// w_d Q^B) (eqs. Klein2DcompleteMovingMethod2a-c) into Cn (and C in R)
 template <int d>
 __global__ void k3_update(Desc D, int nal, int nfl) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -720,11 +807,13 @@ __global__ void k3_update(Desc D, int nal, int nfl) {
         hi3[d] = m + 1 < nal || !periodic ? m + 1 : 0;
         const int flo = fidx(D, nfl, i, j, k), fhi = fidx(D, nfl, hi3[0], hi3[1], hi3[2]);
         const double blo = swept(D, i, j, k), bhi = swept(D, hi3[0], hi3[1], hi3[2]);
-        const double aA = alphaA(D, i, j, k);
-        const bool w = in_r(D, i, j, k) && D.whas[ridx(D, i, j, k)] && blo != bhi;
+        const bool cin = in_r(D, i, j, k);
+        const double aA = cin ? D.aA[ridx(D, i, j, k)] : 1.0;
+        const bool w = cin && D.whas[ridx(D, i, j, k)] && blo != bhi;
         const int r = w ? ridx(D, i, j, k) : 0;
         for (int q = 0; q < NC; ++q) {
-            double x = aA * D.Q[(size_t)q * D.n + c] + D.lam * (D.F[(size_t)q * faces + flo] - D.F[(size_t)q * faces + fhi]);
+            const double Qq = D.Q[(size_t)q * D.n + c];   // alpha_A Q, which is Q outside R
+            double x = (cin ? aA * Qq : Qq) + D.lam * (D.F[(size_t)q * faces + flo] - D.F[(size_t)q * faces + fhi]);
             if (w) {
                 const double wt = D.lam * (bhi - blo) * (D.wFB[(size_t)NC * r + q] - D.U[d] * D.wQB[(size_t)NC * r + q]);
                 x += wt;
@@ -734,11 +823,17 @@ __global__ void k3_update(Desc D, int nal, int nfl) {
         }
         u = 1;
     }
+    // C keeps the content for the events, which read it in R only (event
+    // cells are cut at pose A or B, their neighbours within R)
+    const bool inr = in_r(D, i, j, k);
     for (int q = 0; q < NC; ++q) {
-        D.C[(size_t)q * D.n + c] = v[q];
+        if (inr) D.C[(size_t)q * D.n + c] = v[q];
         D.Cn[(size_t)q * D.n + c] = v[q];
     }
     D.upd[c] = u;
+    // a safeguard seed outside R (alpha_A = alpha_B = 1 there, no event
+    // changes the content): a non-physical content
+    if (u && !inr && content_bad(v)) add_seed(D, c);
 }
 
 // covering / uncovering (Sec. II.C.5): each event cell of R finds its
@@ -848,26 +943,20 @@ __global__ void k3_events(Desc D) {
 
 // safeguard seeds: non-physical new contents, and cells keeping less than
 // COLLAPSE of their volume over the sweep, in the list (cell indices)
+// (cells outside R are tested by k3_update, whose contents no later step
+// before the safeguard changes; this kernel runs over R, after the events)
 __global__ void k3_bad(Desc D) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= D.n || !D.upd[c]) return;
-    const int i = c % D.nx, j = (c / D.nx) % D.ny, k = c / (D.nx * D.ny);
-    const double aB = alphaB(D, i, j, k);
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= D.rn[0] * D.rn[1] * D.rn[2]) return;
+    int i, j, k;
+    r_cell(D, t, &i, &j, &k);
+    const int c = cidx(D, i, j, k);
+    if (!D.upd[c]) return;
+    const double aB = D.aB[t];
     if (!(aB > 0.0)) return;
-    // the state content / alpha_B is physical iff the content is (alpha_B > 0):
-    // rho > 0 and 2 rho E > |m|^2, no division
     double q[NC];
-    bool bad = false;
-    for (int m = 0; m < NC; ++m) {
-        q[m] = D.Cn[(size_t)m * D.n + c];
-        if (!isfinite(q[m])) bad = true;   // alpha_B >= 1e-10: the quotient is finite with it
-    }
-    if (!(q[0] > 0.0) || !(2.0 * q[0] * q[4] > q[1] * q[1] + q[2] * q[2] + q[3] * q[3])) bad = true;
-    if (aB < COLLAPSE * alphaA(D, i, j, k)) bad = true;
-    if (!bad) return;
-    const int s = atomicAdd(D.nseed, 1);
-    if (s < SEEDCAP) D.seeds[s] = c;
-    else atomicOr(D.err, E_SEEDCAP);
+    for (int m = 0; m < NC; ++m) q[m] = D.Cn[(size_t)m * D.n + c];
+    if (content_bad(q) || aB < COLLAPSE * D.aA[t]) add_seed(D, c);
 }
 
 // the merges (one thread): each cluster of seeds and their fluid, updated
@@ -883,13 +972,12 @@ __device__ bool physical5(const Desc &D, int c) {
     }
     return q[0] > 0.0 && pressure5(D.gamma, q) > 0.0;
 }
-__global__ void k3_mix(Desc D) {
-    if (blockIdx.x != 0 || threadIdx.x != 0) return;
-    int ns = *D.nseed;
-    if (ns > SEEDCAP) { *D.err |= E_SEEDCAP; ns = SEEDCAP; }
+// (one thread, over global lists: the form for clusters too large for the
+// shared-memory form in k3_mix; it continues from layer layer0 with the ns
+// seeds in D.seeds and the mixed count so far)
+__device__ void mix_serial(const Desc &D, int ns, int layer0, int mixed) {
     int *seed = D.seeds;
-    int mixed = 0;
-    for (int layer = 0; layer < MIX_LAYERS && ns > 0; ++layer) {
+    for (int layer = layer0; layer < MIX_LAYERS && ns > 0; ++layer) {
         // seeds in cell order
         for (int x = 1; x < ns; ++x) {
             const int v = seed[x];
@@ -974,49 +1062,218 @@ __global__ void k3_mix(Desc D) {
         for (int x = 0; x < nn; ++x) D.lab[D.nodes[x]] = -1;
         ns = nb;
     }
+    if (ns > 0) atomicOr(D.err, E_UNSTABLE);   // cells left non-physical after the last merge
     *D.mixed = mixed;
+}
+
+// The merges in one 256-thread block over shared memory, while a layer's
+// seeds and nodes fit (MIXS_SEEDS seeds, MIXS_NODES nodes); else the
+// remaining layers in mix_serial.  The same clusters, sums and write-back
+// as mix_serial: the candidate cells (the seeds and their fluid, updated
+// face neighbours) are sorted and made unique (the nodes, in cell order);
+// the clusters are the connected components of the seed-neighbour edges,
+// labelled by their smallest node (repeated minimum over the edges until
+// no label changes); each cluster's smallest node's thread sums its
+// members in node order, i.e. in cell order.
+constexpr int MIXS_THREADS = 256, MIXS_SORT = 1024, MIXS_SEEDS = MIXS_SORT / 7, MIXS_NODES = 320;
+__device__ __forceinline__ int node_of(const int *nodes, int nn, int c) {
+    int lo = 0, hi = nn - 1;
+    while (lo < hi) { const int mid = (lo + hi) >> 1; if (nodes[mid] < c) lo = mid + 1; else hi = mid; }
+    return lo;
+}
+__global__ void __launch_bounds__(MIXS_THREADS) k3_mix(Desc D) {
+    __shared__ int cand[MIXS_SORT];
+    __shared__ int enode[MIXS_SEEDS * 6];   // per (seed, direction): the neighbour's cell, then its node; -1 none
+    __shared__ int snode[MIXS_SEEDS];       // the seed's node
+    __shared__ int nodes[MIXS_NODES], lbl[MIXS_NODES];
+    __shared__ double cache[MIXS_NODES][NC + 1], sums[MIXS_NODES][NC + 1];
+    __shared__ int s_wsum[MIXS_THREADS / 32], s_nn, s_changed, s_nb;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    int ns = *D.nseed;
+    if (ns > SEEDCAP) {
+        if (tid == 0) atomicOr(D.err, E_SEEDCAP);
+        ns = SEEDCAP;
+    }
+    int mixed = 0, layer = 0;
+    for (; layer < MIX_LAYERS && ns > 0; ++layer) {
+        if (ns > MIXS_SEEDS) break;
+        int P = 2;
+        while (P < 7 * ns) P <<= 1;
+        // candidates: seed s at 7s, its neighbours after it
+        for (int x = tid; x < P; x += MIXS_THREADS) cand[x] = INT_MAX;
+        __syncthreads();
+        for (int s = tid; s < ns; s += MIXS_THREADS) {
+            const int c = D.seeds[s];
+            const int i = c % D.nx, j = (c / D.nx) % D.ny, k = c / (D.nx * D.ny);
+            cand[7 * s] = c;
+            const int off[6][3] = {{-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}, {0, 0, -1}, {0, 0, 1}};
+            for (int m = 0; m < 6; ++m) {
+                int ii, jj, kk;
+                const int cc = nbr(D, i, j, k, off[m][0], off[m][1], off[m][2], &ii, &jj, &kk);
+                const bool ok = cc >= 0 && alphaB(D, ii, jj, kk) > 0.0 && D.upd[cc];
+                cand[7 * s + 1 + m] = ok ? cc : INT_MAX;
+                enode[6 * s + m] = ok ? cc : -1;
+            }
+        }
+        __syncthreads();
+        // bitonic sort of cand[0, P)
+        for (int k2 = 2; k2 <= P; k2 <<= 1)
+            for (int j2 = k2 >> 1; j2 > 0; j2 >>= 1) {
+                for (int x = tid; x < P; x += MIXS_THREADS) {
+                    const int y = x ^ j2;
+                    if (y > x) {
+                        const int a = cand[x], b = cand[y];
+                        if ((a > b) == ((x & k2) == 0)) { cand[x] = b; cand[y] = a; }
+                    }
+                }
+                __syncthreads();
+            }
+        // the distinct cells, in order: a contiguous chunk per thread and a
+        // block-wide exclusive scan of the chunks' counts
+        const int per = (P + MIXS_THREADS - 1) / MIXS_THREADS, x0 = min(P, tid * per), x1 = min(P, x0 + per);
+        int cnt = 0;
+        for (int x = x0; x < x1; ++x) cnt += cand[x] != INT_MAX && (x == 0 || cand[x - 1] != cand[x]);
+        int inc = cnt;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += v;
+        }
+        if (lane == 31) s_wsum[wid] = inc;
+        __syncthreads();
+        int pos = inc - cnt, tot = 0;
+        for (int w = 0; w < MIXS_THREADS / 32; ++w) {
+            if (w < wid) pos += s_wsum[w];
+            tot += s_wsum[w];
+        }
+        for (int x = x0; x < x1; ++x)
+            if (cand[x] != INT_MAX && (x == 0 || cand[x - 1] != cand[x])) {
+                if (pos < MIXS_NODES) nodes[pos] = cand[x];
+                ++pos;
+            }
+        __syncthreads();
+        const int nn = tot;
+        if (nn > MIXS_NODES) break;
+        // edges as node pairs, labels, the nodes' contents and alpha_B
+        for (int x = tid; x < 6 * ns; x += MIXS_THREADS)
+            if (enode[x] >= 0) enode[x] = node_of(nodes, nn, enode[x]);
+        for (int s = tid; s < ns; s += MIXS_THREADS) snode[s] = node_of(nodes, nn, D.seeds[s]);
+        for (int x = tid; x < nn; x += MIXS_THREADS) {
+            const int c = nodes[x];
+            const int i = c % D.nx, j = (c / D.nx) % D.ny, k = c / (D.nx * D.ny);
+            lbl[x] = x;
+            for (int q = 0; q < NC; ++q) cache[x][q] = D.Cn[(size_t)q * D.n + c];
+            cache[x][NC] = alphaB(D, i, j, k);
+        }
+        for (;;) {
+            __syncthreads();
+            if (tid == 0) s_changed = 0;
+            __syncthreads();
+            for (int x = tid; x < 6 * ns; x += MIXS_THREADS) {
+                const int b = enode[x];
+                if (b < 0) continue;
+                const int a = snode[x / 6];
+                const int la = lbl[a], lb = lbl[b];
+                if (la != lb) {
+                    const int mn = min(la, lb);
+                    atomicMin(&lbl[a], mn);
+                    atomicMin(&lbl[b], mn);
+                    s_changed = 1;
+                }
+            }
+            __syncthreads();
+            const int ch = s_changed;
+            if (!ch) break;
+        }
+        // each cluster's sums (alpha_B and contents) in node order
+        for (int r = tid; r < nn; r += MIXS_THREADS) {
+            if (lbl[r] != r) continue;
+            double acc[NC + 1] = {0, 0, 0, 0, 0, 0};
+            for (int x = r; x < nn; ++x) {
+                if (lbl[x] != r) continue;
+                acc[NC] += cache[x][NC];
+                for (int q = 0; q < NC; ++q) acc[q] += cache[x][q];
+            }
+            for (int q = 0; q <= NC; ++q) sums[r][q] = acc[q];
+        }
+        if (tid == 0) s_nb = 0;
+        __syncthreads();
+        // shares in proportion to alpha_B; cells still non-physical seed
+        // the next layer (its candidates are sorted, so order is free)
+        for (int x = tid; x < nn; x += MIXS_THREADS) {
+            const int c = nodes[x], r = lbl[x];
+            const double aB = cache[x][NC];
+            for (int q = 0; q < NC; ++q) D.Cn[(size_t)q * D.n + c] = aB * (sums[r][q] / sums[r][NC]);
+            if (!physical5(D, c)) D.seeds[atomicAdd(&s_nb, 1)] = c;
+        }
+        mixed += nn;
+        __syncthreads();
+        ns = s_nb;
+        __syncthreads();
+    }
+    if (layer < MIX_LAYERS && ns > 0) {   // too large for shared memory: the serial form goes on
+        if (tid == 0) mix_serial(D, ns, layer, mixed);
+        return;
+    }
+    if (tid == 0 && ns > 0) atomicOr(D.err, E_UNSTABLE);   // cells left non-physical after the last merge
+    if (tid == 0) *D.mixed = mixed;
 }
 
 // Q = content / alpha_B (NaN where alpha_B = 0 or the cell was not
 // updated), with the checks of the new state
+// (outside R alpha_B = 1 and the state is the content: its test was the
+// seed test, and the safeguard flags cells it leaves non-physical)
 __global__ void k3_final(Desc D) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= D.n) return;
     const int i = c % D.nx, j = (c / D.nx) % D.ny, k = c / (D.nx * D.ny);
+    if (!in_r(D, i, j, k)) {
+        for (int m = 0; m < NC; ++m) {
+            const double cn = D.Cn[(size_t)m * D.n + c];
+            D.Q[(size_t)m * D.n + c] = cn;
+            if (D.f32) D.Qf[(size_t)m * D.n + c] = float(cn);
+        }
+        return;
+    }
     const double aB = alphaB(D, i, j, k);
     const bool ok = aB > 0.0 && D.upd[c];
     const double ia = ok ? (aB == 1.0 ? 1.0 : 1.0 / aB) : 0.0;
     double q[NC];
     for (int m = 0; m < NC; ++m) {
-        q[m] = ok ? D.Cn[(size_t)m * D.n + c] * ia : NAN;
+        const double cn = D.Cn[(size_t)m * D.n + c];
+        q[m] = ok ? (ia == 1.0 ? cn : cn * ia) : NAN;
         D.Q[(size_t)m * D.n + c] = q[m];
+        if (D.f32) D.Qf[(size_t)m * D.n + c] = float(q[m]);
     }
     if (aB > 0.0 && !D.upd[c]) atomicOr(D.err, E_UNSTABLE);
     if (ok) {
         bool bad = !(q[0] > 0.0) || !(2.0 * q[0] * q[4] > q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
-        for (int m = 0; m < NC; ++m) if (!isfinite(q[m])) bad = true;
+        for (int m = 0; m < NC; ++m) if (!finite64(q[m])) bad = true;
         if (bad) atomicOr(D.err, E_UNSTABLE);
     }
 }
 
 // maxima of |u_d| + c over the fluid cells (positive doubles compare as
 // their bit patterns)
-// (a grid-stride loop, 256-thread blocks: one atomic per block and axis)
+// (a grid-stride loop, 256-thread blocks: one atomic per block and axis;
+// in the type T of the flow arithmetic)
+template <typename T>
 __global__ void k3_speeds(Desc D) {
     __shared__ double red[3][8];
-    double s[3] = {0.0, 0.0, 0.0};
+    const T *Q = qsrc<T>(D);
+    const T g = gam<T>(D);
+    T s[3] = {T(0), T(0), T(0)};
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < D.n; c += gridDim.x * blockDim.x) {
-        if (isnan(D.Q[c])) continue;
-        double q[NC];
-        for (int m = 0; m < NC; ++m) q[m] = D.Q[(size_t)m * D.n + c];
-        const double ir = 1.0 / q[0];
-        const double p = (D.gamma - 1.0) * (q[4] - 0.5 * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) * ir);
-        const double cs = sqrt(D.gamma * p * ir);
+        if (isnan(Q[c])) continue;
+        T q[NC];
+        for (int m = 0; m < NC; ++m) q[m] = Q[(size_t)m * D.n + c];
+        const T ir = T(1) / q[0];
+        const T p = (g - T(1)) * (q[4] - T(0.5) * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) * ir);
+        const T cs = sqrt(g * p * ir);
         for (int a = 0; a < 3; ++a) s[a] = fmax(s[a], fabs(q[1 + a] * ir) + cs);
     }
     const int w = threadIdx.x >> 5;
     for (int a = 0; a < 3; ++a) {
-        double v = s[a];
+        double v = double(s[a]);
         for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
         if ((threadIdx.x & 31) == 0) red[a][w] = v;
     }
@@ -1039,6 +1296,13 @@ __global__ void k3_classify(Desc D, double *alpha_out) {
     else if (!(a > 0.0)) for (int m = 0; m < NC; ++m) D.Q[(size_t)m * D.n + c] = NAN;
 }
 
+// the FP32 copy of the state (FP32 flux option)
+__global__ void k3_to_f32(Desc D) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= D.n) return;
+    for (int m = 0; m < NC; ++m) D.Qf[(size_t)m * D.n + c] = float(D.Q[(size_t)m * D.n + c]);
+}
+
 }  // namespace mb3
 
 // ---------------------------------------------------------------------------
@@ -1056,6 +1320,8 @@ struct mb3_sim {
     int sidx = 0;
     double dt_step = 0.0, cfl = 0.5;
     cudaStream_t st = nullptr;
+    cudaStream_t gs[2] = {nullptr, nullptr};      // face apertures and swept apertures beside k3_cells
+    cudaEvent_t fork = nullptr, join[2] = {nullptr, nullptr};
     std::string err;
     size_t rcap = 0, rfcap = 0;
     bool prev_ok = false;        // aB / tB hold the current pose over the region q0, qn
@@ -1212,6 +1478,7 @@ mb_status mb3_create(const mb3_grid *g, double gamma, double cfl, const mb3_body
     }
     for (int q = 0; q < 6; ++q) D.bc[q] = g->bc[q];
     D.gamma = gamma;
+    D.gammaf = (float)gamma;
     D.gcl = uncover_mode == MB_UNCOVER_FLUX_GCL;
     s->cfl = cfl;
     s->nplane = b->nplane;
@@ -1223,6 +1490,11 @@ mb_status mb3_create(const mb3_grid *g, double gamma, double cfl, const mb3_body
     cudaError_t e = cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreate(&s->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&s->ev1);
+    for (int q = 0; q < 2 && e == cudaSuccess; ++q) {
+        e = cudaStreamCreateWithFlags(&s->gs[q], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->join[q], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->fork, cudaEventDisableTiming);
     const size_t n = D.n;
     size_t fmax_ = 0;
     for (int a = 0; a < 3; ++a) fmax_ = std::max(fmax_, (size_t)(nn[a] + 1) * (n / nn[a]));
@@ -1259,9 +1531,15 @@ mb_status mb3_create(const mb3_grid *g, double gamma, double cfl, const mb3_body
 void mb3_destroy(mb3_sim *s) {
     if (!s) return;
     if (s->st) cudaStreamSynchronize(s->st);
+    for (int q = 0; q < 2; ++q) if (s->gs[q]) cudaStreamSynchronize(s->gs[q]);
     for (void *p : s->owned) cudaFree(p);
     if (s->ev0) cudaEventDestroy(s->ev0);
     if (s->ev1) cudaEventDestroy(s->ev1);
+    if (s->fork) cudaEventDestroy(s->fork);
+    for (int q = 0; q < 2; ++q) {
+        if (s->join[q]) cudaEventDestroy(s->join[q]);
+        if (s->gs[q]) cudaStreamDestroy(s->gs[q]);
+    }
     if (s->st) cudaStreamDestroy(s->st);
     delete s;
 }
@@ -1283,6 +1561,7 @@ mb_status mb3_write_state(mb3_sim *s, const double *Q, double t, const double *T
     Desc D = s->D;
     if (e == cudaSuccess) e = pose_alpha(s, T, D);
     if (e == cudaSuccess) mb3::k3_classify<<<nblk(s->D.n), 256, 0, s->st>>>(D, nullptr);
+    if (e == cudaSuccess && D.f32) mb3::k3_to_f32<<<nblk(s->D.n), 256, 0, s->st>>>(D);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
     if (e != cudaSuccess) return cuda3(s, e, "mb3_write_state");
@@ -1348,6 +1627,7 @@ mb_status mb3_sweep(mb3_sim *s, int d, double dt) {
     for (int a = 0; a < 3; ++a) { D.r0[a] = r0[a]; D.rn[a] = rn[a]; }
     D.d = d;
     D.lam = dt / D.h[d];
+    D.hlamf = 0.5f * (float)D.lam;
     const int nn[3] = {D.nx, D.ny, D.nz};
     const int nal = nn[d], nlines = D.n / nal;
     const bool periodic = D.bc[2 * d] == MB_BC_PERIODIC;
@@ -1358,6 +1638,12 @@ mb_status mb3_sweep(mb3_sim *s, int d, double dt) {
     if (e != cudaSuccess) return cuda3(s, e, "mb3_sweep");
     const mb3::Body3 BA = posed(s, TA), BM = posed(s, TM), BB = posed(s, TB);
     if (rc > 0) {
+        // the three geometry kernels are independent (each writes its own
+        // arrays); the cut cells near a body's corners make each of them a
+        // long tail on few SMs, so they run side by side on three streams
+        cudaEventRecord(s->fork, s->st);
+        cudaStreamWaitEvent(s->gs[0], s->fork, 0);
+        cudaStreamWaitEvent(s->gs[1], s->fork, 0);
         mb3::k3_cells<<<nblk(32LL * (reuse ? 2 : 3) * (long long)rc), 256, 0, s->st>>>(
             D, BA, BM, BB, reuse ? mb3::CELLS_REUSE_A : mb3::CELLS_ALL);
         long long nfaces = 0;
@@ -1365,15 +1651,24 @@ mb_status mb3_sweep(mb3_sim *s, int d, double dt) {
             const int ax = a < 3 ? a : d;
             nfaces += (long long)(rn[0] + (ax == 0)) * (rn[1] + (ax == 1)) * (rn[2] + (ax == 2));
         }
-        mb3::k3_faces<<<nblk(nfaces), 256, 0, s->st>>>(D, BM, BA, delta);
+        mb3::k3_faces<<<nblk(nfaces), 256, 0, s->gs[0]>>>(D, BM, BA, delta);
         if (delta != 0.0) {
             const long long nsw = (long long)(rn[0] + (d == 0)) * (rn[1] + (d == 1)) * (rn[2] + (d == 2));
-            mb3::k3_swept<<<nblk(32LL * nsw), 256, 0, s->st>>>(D, BA, delta);
+            mb3::k3_swept<<<nblk(32LL * nsw), 256, 0, s->gs[1]>>>(D, BA, delta);
+        }
+        for (int q = 0; q < 2; ++q) {
+            cudaEventRecord(s->join[q], s->gs[q]);
+            cudaStreamWaitEvent(s->st, s->join[q], 0);
         }
         mb3::k3_wall<<<nblk((long long)rc), 256, 0, s->st>>>(D);
     }
-    const auto evolve = d == 0 ? mb3::k3_evolve<0> : d == 1 ? mb3::k3_evolve<1> : mb3::k3_evolve<2>;
-    const auto flux = d == 0 ? mb3::k3_flux<0> : d == 1 ? mb3::k3_flux<1> : mb3::k3_flux<2>;
+    const bool f = D.f32;
+    const auto evolve = d == 0 ? (f ? mb3::k3_evolve<0, float> : mb3::k3_evolve<0, double>)
+                      : d == 1 ? (f ? mb3::k3_evolve<1, float> : mb3::k3_evolve<1, double>)
+                               : (f ? mb3::k3_evolve<2, float> : mb3::k3_evolve<2, double>);
+    const auto flux = d == 0 ? (f ? mb3::k3_flux<0, float> : mb3::k3_flux<0, double>)
+                    : d == 1 ? (f ? mb3::k3_flux<1, float> : mb3::k3_flux<1, double>)
+                             : (f ? mb3::k3_flux<2, float> : mb3::k3_flux<2, double>);
     const auto update = d == 0 ? mb3::k3_update<0> : d == 1 ? mb3::k3_update<1> : mb3::k3_update<2>;
     evolve<<<nblk(D.n), 256, 0, s->st>>>(D, nal);
     cudaEventRecord(s->ev0, s->st);
@@ -1384,8 +1679,8 @@ mb_status mb3_sweep(mb3_sim *s, int d, double dt) {
         mb3::k3_evprep<<<nblk((long long)rc), 256, 0, s->st>>>(D);
         mb3::k3_events<<<nblk((long long)rc), 256, 0, s->st>>>(D);
     }
-    mb3::k3_bad<<<nblk(D.n), 256, 0, s->st>>>(D);
-    mb3::k3_mix<<<1, 32, 0, s->st>>>(D);
+    if (rc > 0) mb3::k3_bad<<<nblk((long long)rc), 256, 0, s->st>>>(D);
+    mb3::k3_mix<<<1, mb3::MIXS_THREADS, 0, s->st>>>(D);
     mb3::k3_final<<<nblk(D.n), 256, 0, s->st>>>(D);
     int w = 0;
     e = cudaGetLastError();
@@ -1410,7 +1705,9 @@ mb_status mb3_cfl_dt(mb3_sim *s, double *dt) {
     if (!s || !dt) return MB_E_INVAL;
     double sm[3] = {0, 0, 0};
     cudaError_t e = cudaMemsetAsync(s->D.smax, 0, 3 * sizeof(double), s->st);
-    if (e == cudaSuccess) mb3::k3_speeds<<<std::min(nblk(s->D.n), 152u * 8u), 256, 0, s->st>>>(s->D);
+    const unsigned nb = std::min(nblk(s->D.n), 152u * 8u);
+    if (e == cudaSuccess && s->D.f32) mb3::k3_speeds<float><<<nb, 256, 0, s->st>>>(s->D);
+    else if (e == cudaSuccess) mb3::k3_speeds<double><<<nb, 256, 0, s->st>>>(s->D);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(sm, s->D.smax, 3 * sizeof(double), cudaMemcpyDeviceToHost, s->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
@@ -1449,6 +1746,19 @@ mb_status mb3_last_sweep(mb3_sim *s, double *wall, int *merged) {
     if (wall) for (int q = 0; q < NC; ++q) wall[q] = s->wall_host[q];
     if (merged) *merged = s->merged;
     return MB_OK;
+}
+
+mb_status mb3_set_precision(mb3_sim *s, int precision) {
+    if (!s || (precision != MB_FP64 && precision != MB_FP32)) return MB_E_INVAL;
+    if (s->sidx != 0) return fail3(s, MB_E_STATE, "mb3_set_precision in the middle of a step");
+    cudaError_t e = cudaSuccess;
+    if (precision == MB_FP32 && !s->D.Qf) e = dalloc(s, &s->D.Qf, NC * (size_t)s->D.n);
+    if (e != cudaSuccess) return cuda3(s, e, "mb3_set_precision");
+    s->D.f32 = precision == MB_FP32;
+    if (s->D.f32) mb3::k3_to_f32<<<nblk(s->D.n), 256, 0, s->st>>>(s->D);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+    return cuda3(s, e, "mb3_set_precision");
 }
 
 mb_status mb3_flux_time(mb3_sim *s, double *ms) {

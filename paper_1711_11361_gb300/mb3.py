@@ -11,7 +11,7 @@ from . import mb
 from .mb import MBError, MB_OK
 
 EXPORTS = ["mb3_create", "mb3_destroy", "mb3_last_error", "mb3_write_state", "mb3_read_state", "mb3_sweep",
-           "mb3_step", "mb3_cfl_dt", "mb3_last_sweep", "mb3_flux_time"]
+           "mb3_step", "mb3_cfl_dt", "mb3_last_sweep", "mb3_flux_time", "mb3_set_precision"]
 
 
 class Grid3(ctypes.Structure):
@@ -39,6 +39,7 @@ for _name, (_args, _res) in {
     "mb3_cfl_dt": ([_P, _D], _I),
     "mb3_last_sweep": ([_P, _D, ctypes.POINTER(_I)], _I),
     "mb3_flux_time": ([_P, _D], _I),
+    "mb3_set_precision": ([_P, _I], _I),
 }.items():
     _f = getattr(lib, _name)
     _f.argtypes, _f.restype = _args, _res
@@ -50,9 +51,10 @@ def _dp(a):
 
 class Sim3:
     """One three-dimensional simulation from a
-    :class:`paper_1711_11361_gb300.inputs.Problem3` (FP64)."""
+    :class:`paper_1711_11361_gb300.inputs.Problem3`; ``precision`` the flow
+    arithmetic's (mb.FP64, the default, or mb.FP32: see set_precision)."""
 
-    def __init__(self, prob, write_initial=True):
+    def __init__(self, prob, write_initial=True, precision=mb.FP64):
         g = Grid3()
         g.nx, g.ny, g.nz = prob.nx, prob.ny, prob.nz
         for a in range(3):
@@ -76,6 +78,8 @@ class Sim3:
         self._h = h
         self.prob = prob
         self.shape = (5, prob.nz, prob.ny, prob.nx)
+        if precision != mb.FP64:
+            self.set_precision(precision)
         if write_initial and prob.Q0 is not None:
             self.write_state(prob.Q0)
 
@@ -122,6 +126,10 @@ class Sim3:
         dt = ctypes.c_double()
         self._check(lib.mb3_cfl_dt(self._h, ctypes.byref(dt)))
         return dt.value
+
+    def set_precision(self, precision):
+        """MB_FP64 (0, default) or MB_FP32 (1) flow arithmetic (mb3_set_precision)."""
+        self._check(lib.mb3_set_precision(self._h, int(precision)))
 
     def flux_time_ms(self):
         """Device time of the last sweep's face-flux kernel (CUDA events)."""
