@@ -1009,6 +1009,14 @@ int o3_swept(o3_sim *s, int d, const double *T, double delta, double *out) {
 /* the last sweep's wall data per cell (5 n doubles: has, d, n_x, n_y, n_z) */
 void o3_last_wall(const o3_sim *s, double *out) { memcpy(out, s->wall_cell, sizeof(double) * 5 * s->n); }
 
+/* the covering / uncovering step alone on given fields (alpha at poses A
+ * and B, the contents C after the flux update; Cn and the updated flags out),
+ * for tests of its neighbour passes and shares */
+int o3_cover_uncover(o3_sim *s, const double *alphaA, const double *alphaB, const double *C, double *Cn,
+                     unsigned char *updated) {
+    return cover_uncover3(s, alphaA, alphaB, C, Cn, updated);
+}
+
 /* the last sweep's summed wall terms (O3_NC) and cells merged */
 int o3_last_sweep(const o3_sim *s, double *wall) {
     if (wall) memcpy(wall, s->wall_last, sizeof(double) * O3_NC);

@@ -76,6 +76,7 @@ def _load():
         lib.o3_last_wall.argtypes = [P, D]
         lib.o3_solid_volume.argtypes = [P, D, D, D]
         lib.o3_solid_volume.restype = ctypes.c_double
+        lib.o3_cover_uncover.argtypes = [P, D, D, D, D, B]
         lib.o3_hllc.argtypes = [ctypes.c_double, ctypes.c_int, D, D, D]
         lib.o3_wall_state.argtypes = [ctypes.c_double, D, D, D, D, D, D]
         _lib = lib
@@ -205,6 +206,18 @@ class Oracle3:
         out = np.empty(shape)
         _lib.o3_swept(self._h, d, _dp(_vec(T)), delta, _dp(out))
         return out
+
+    def cover_uncover(self, alphaA, alphaB, C):
+        """The covering / uncovering step alone (Sec. II.C.5) on given fields
+        of shape (nz, ny, nx) and contents (5, nz, ny, nx): (status, Cn,
+        updated flags)."""
+        aA, aB = _vec(alphaA).reshape(-1), _vec(alphaB).reshape(-1)
+        Cc = _vec(C).reshape(-1)
+        Cn = np.empty_like(Cc)
+        upd = np.zeros(self.n, dtype=np.uint8)
+        r = _lib.o3_cover_uncover(self._h, _dp(aA), _dp(aB), _dp(Cc), _dp(Cn),
+                                  upd.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)))
+        return r, Cn.reshape(5, self.nz, self.ny, self.nx), upd.reshape(self.nz, self.ny, self.nx)
 
     def solid_volume(self, lo, hi, T=(0.0, 0.0, 0.0)):
         return _lib.o3_solid_volume(self._h, _dp(_vec(T)), _dp(_vec(lo)), _dp(_vec(hi)))

@@ -244,3 +244,133 @@ def test_x_invariant_prism_reduces_to_two_dimensions(mode):
             for q2, q3 in ((0, 0), (1, 2), (2, 3), (3, 4)):
                 scale = np.max(np.abs(c2[q2])) + 1e-300
                 assert np.max(np.abs(c3[q3, :, :, i] - c2[q2])) <= 1e-12 * scale, (s, i, q2)
+
+
+# --- covering / uncovering (Sec. II.C.5, eqs. volumeWeighting,
+# cutCellInitialisation, cutCellInitialisationDonorCellUpdate,
+# cutCellCoverDonation), the neighbour passes of the three-dimensional
+# reading: the six face neighbours, else the twelve sharing an edge, else the
+# eight sharing a vertex; expected values written out per case
+
+def _cu_case(mode, bc=(inputs.PERIODIC,) * 6):
+    p = inputs.Problem3("cu", 5, 5, 5, bc=bc, uncover_mode=mode)
+    o = o3.Oracle3(p)
+    aA = np.ones((5, 5, 5))
+    aB = np.ones((5, 5, 5))
+    C = np.random.default_rng(7).uniform(0.5, 2.0, (5, 5, 5, 5))
+    return o, aA, aB, C
+
+
+FACES = [(-1, 0, 0), (1, 0, 0), (0, -1, 0), (0, 1, 0), (0, 0, -1), (0, 0, 1)]
+EDGES = [(a, b, 0) for a in (-1, 1) for b in (-1, 1)] + [(a, 0, b) for a in (-1, 1) for b in (-1, 1)] + \
+        [(0, a, b) for a in (-1, 1) for b in (-1, 1)]
+CORNERS = [(a, b, c) for a in (-1, 1) for b in (-1, 1) for c in (-1, 1)]
+
+
+def _at(arr, off, centre=(2, 2, 2)):
+    """index (k, j, i) of the cell at offset (di, dj, dk) from the centre"""
+    return (centre[2] + off[2], centre[1] + off[1], centre[0] + off[0])
+
+
+def _covered_shares(pass_offsets, solid_offsets, mode):
+    o, aA, aB, C = _cu_case(mode)
+    c = _at(aA, (0, 0, 0))
+    aA[c], aB[c] = 0.4, 0.0
+    for off in solid_offsets:
+        aA[_at(aA, off)] = aB[_at(aA, off)] = 0.0
+    w = [0.05 + 0.07 * m for m in range(len(pass_offsets))]
+    for off, v in zip(pass_offsets, w):
+        aB[_at(aA, off)] = v
+    r, Cn, upd = o.cover_uncover(aA, aB, C)
+    assert r == 0
+    expect = C.copy()
+    expect[(slice(None),) + c] = 0.0
+    for off, v in zip(pass_offsets, w):
+        expect[(slice(None),) + _at(aA, off)] += v / sum(w) * C[(slice(None),) + c]
+    assert np.max(np.abs(Cn - expect)) < 1e-14
+
+
+@pytest.mark.parametrize("mode", [inputs.UNCOVER_DONOR, inputs.UNCOVER_FLUX_GCL])
+def test_covered_cell_gives_to_its_face_neighbours(mode):
+    """a covered cell's content goes to its face neighbours in proportion to
+    their alpha_B (the edge and vertex neighbours, fluid too, get none)"""
+    _covered_shares(FACES, [], mode)
+
+
+@pytest.mark.parametrize("mode", [inputs.UNCOVER_DONOR, inputs.UNCOVER_FLUX_GCL])
+def test_covered_cell_gives_to_its_edge_neighbours_when_no_face_neighbour_is_fluid(mode):
+    _covered_shares(EDGES, FACES, mode)
+
+
+@pytest.mark.parametrize("mode", [inputs.UNCOVER_DONOR, inputs.UNCOVER_FLUX_GCL])
+def test_covered_cell_gives_to_its_vertex_neighbours_when_no_face_or_edge_neighbour_is_fluid(mode):
+    _covered_shares(CORNERS, FACES + EDGES, mode)
+
+
+def test_uncovered_cell_takes_sigma_of_its_donors_contents():
+    """donor mode: an uncovered cell (alpha_A = 0 < alpha_B) takes sigma =
+    alpha_B / (alpha_B + sum of the donors' alpha_B) of each face donor's
+    content, and each donor keeps 1 - sigma of its own"""
+    o, aA, aB, C = _cu_case(inputs.UNCOVER_DONOR)
+    c = _at(aA, (0, 0, 0))
+    aA[c], aB[c] = 0.0, 0.3
+    w = [0.2, 0.9, 0.5, 1.0, 0.7, 0.35]
+    for off, v in zip(FACES, w):
+        aB[_at(aA, off)] = v
+    r, Cn, upd = o.cover_uncover(aA, aB, C)
+    assert r == 0 and upd[c] == 1 and upd.sum() == 1
+    sigma = 0.3 / (0.3 + sum(w))
+    expect = C.copy()
+    expect[(slice(None),) + c] = sigma * sum(C[(slice(None),) + _at(aA, off)] for off in FACES)
+    for off in FACES:
+        expect[(slice(None),) + _at(aA, off)] = (1.0 - sigma) * C[(slice(None),) + _at(aA, off)]
+    assert np.max(np.abs(Cn - expect)) < 1e-14
+
+
+def test_uncovered_cell_takes_no_donor_that_is_itself_uncovered():
+    """donor mode: a face neighbour with alpha_A = 0 is no donor (it is
+    uncovered itself and takes from its own fluid neighbours)"""
+    o, aA, aB, C = _cu_case(inputs.UNCOVER_DONOR)
+    c, n1 = _at(aA, (0, 0, 0)), _at(aA, (1, 0, 0))
+    aA[c], aB[c] = 0.0, 0.3
+    aA[n1], aB[n1] = 0.0, 0.6
+    r, Cn, upd = o.cover_uncover(aA, aB, C)
+    assert r == 0
+    don_c = [off for off in FACES if off != (1, 0, 0)]                     # alpha_B = 1 each
+    don_n1 = [(2, 0, 0), (1, -1, 0), (1, 1, 0), (1, 0, -1), (1, 0, 1)]     # c is not one of them
+    s_c, s_n1 = 0.3 / (0.3 + 5.0), 0.6 / (0.6 + 5.0)
+    expect = C.copy()
+    expect[(slice(None),) + c] = s_c * sum(C[(slice(None),) + _at(aA, off)] for off in don_c)
+    expect[(slice(None),) + n1] = s_n1 * sum(C[(slice(None),) + _at(aA, off)] for off in don_n1)
+    for off in don_c:
+        expect[(slice(None),) + _at(aA, off)] = (1.0 - s_c) * C[(slice(None),) + _at(aA, off)]
+    for off in don_n1:
+        expect[(slice(None),) + _at(aA, off)] = (1.0 - s_n1) * C[(slice(None),) + _at(aA, off)]
+    assert np.max(np.abs(Cn - expect)) < 1e-14
+
+
+@pytest.mark.parametrize("open_side", [True, False])
+def test_covered_cell_without_a_fluid_neighbour(open_side):
+    """a covered cell with no fluid neighbour at all: on a transmissive side
+    its content leaves the domain; elsewhere the step reports an error"""
+    bc = (inputs.TRANSMISSIVE,) * 6 if open_side else (inputs.PERIODIC,) * 6
+    o, aA, aB, C = _cu_case(inputs.UNCOVER_FLUX_GCL, bc)
+    centre = (0, 2, 2)
+    c = _at(aA, (0, 0, 0), centre)
+    aA[c], aB[c] = 0.5, 0.0
+    for off in FACES + EDGES + CORNERS:
+        k, j, i = _at(aA, off, centre)
+        if 0 <= i < 5:
+            aA[k, j, i] = aB[k, j, i] = 0.0
+    if not open_side:   # the periodic images at i = 4 as well
+        for off in FACES + EDGES + CORNERS:
+            if off[0] == -1:
+                aA[_at(aA, (4, off[1], off[2]), centre)] = aB[_at(aA, (4, off[1], off[2]), centre)] = 0.0
+    r, Cn, upd = o.cover_uncover(aA, aB, C)
+    if open_side:
+        assert r == 0
+        expect = C.copy()
+        expect[(slice(None),) + c] = 0.0
+        assert np.max(np.abs(Cn - expect)) < 1e-14
+    else:
+        assert r == -4
