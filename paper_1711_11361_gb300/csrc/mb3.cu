@@ -350,6 +350,11 @@ __device__ __forceinline__ void r_cell(const Desc &D, int t, int *i, int *j, int
     *k = D.r0[2] + t / (D.rn[0] * D.rn[1]);
 }
 
+// the item of a warp-per-item kernel: item v * gridDim.x + b for warp v of
+// block b, so that neighbouring items (cut cells cluster along the body's
+// surface) land on different blocks, and so on different SMs
+__device__ __forceinline__ int warp_item() { return (int)(threadIdx.x >> 5) * (int)gridDim.x + (int)blockIdx.x; }
+
 // volume fractions at the three poses and the touch flags of R's cells,
 // one warp per cell and pose (pose B first, then M, then A, so that a
 // costly cell's poses run side by side).  CELLS_ALL: poses A, M and B;
@@ -364,7 +369,7 @@ __device__ __forceinline__ double fraction(double V, double vol) {
 }
 __global__ void k3_cells(Desc D, Body3 BA, Body3 BM, Body3 BB, int mode) {
     const int rc = D.rn[0] * D.rn[1] * D.rn[2];
-    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int w = warp_item();
     const int npose = mode == CELLS_ALL ? 3 : mode == CELLS_REUSE_A ? 2 : 1;
     if (w >= npose * rc) return;
     const int t = w % rc, pose = w / rc;   // 0: B, 1: M, 2: A
@@ -403,7 +408,7 @@ __global__ void k3_cells(Desc D, Body3 BA, Body3 BM, Body3 BB, int mode) {
 // apertures of R's d-faces (the fluid fraction of [x_f - delta, x_f] with
 // the body at A), one face per thread over the four index ranges
 __global__ void k3_faces(Desc D, Body3 BM, Body3 BA, double delta) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    int t = warp_item() * 32 + (int)(threadIdx.x & 31);   // whole warps spread over blocks
     for (int a = 0; a < 4; ++a) {
         const int ax = a < 3 ? a : D.d;
         const int m0 = D.rn[0] + (ax == 0), m1 = D.rn[1] + (ax == 1), m2 = D.rn[2] + (ax == 2);
@@ -429,7 +434,7 @@ __global__ void k3_faces(Desc D, Body3 BM, Body3 BA, double delta) {
 // time-averaged apertures of R's d-faces for delta != 0: the fluid fraction
 // of [x_f - delta, x_f] with the body at A, one warp per face
 __global__ void k3_swept(Desc D, Body3 BA, double delta) {
-    const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int t = warp_item();
     const int ax = D.d;
     const int m0 = D.rn[0] + (ax == 0), m1 = D.rn[1] + (ax == 1), m2 = D.rn[2] + (ax == 2);
     if (t >= m0 * m1 * m2) return;
