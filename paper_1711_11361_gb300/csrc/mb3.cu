@@ -565,12 +565,17 @@ __device__ __forceinline__ double pressure5(double g, const double *q) {
 // FP64 path, float for the FP32 flux option; every literal is a T, so the
 // float instances stay in float and the double ones are the FP64 path's
 // arithmetic unchanged)
+// a b + c with one rounding (the file is built without contraction, so
+// the flow arithmetic fuses where it says so)
+__device__ __forceinline__ double fmad(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float fmad(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+template <typename T> __device__ __forceinline__ T sq3(const T *m) { return fmad(m[0], m[0], fmad(m[1], m[1], m[2] * m[2])); }
 template <typename T>
 __device__ __forceinline__ void flux5(T g, int d, const T *q, T *f) {
     const T rho = q[0], ir = T(1) / rho, un = q[1 + d] * ir;
-    const T p = (g - T(1)) * (q[4] - T(0.5) * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) * ir);
+    const T p = (g - T(1)) * fmad(T(-0.5) * sq3(q + 1), ir, q[4]);
     f[0] = rho * un;
-    for (int m = 0; m < 3; ++m) f[1 + m] = q[1 + m] * un + (m == d ? p : T(0));
+    for (int m = 0; m < 3; ++m) f[1 + m] = m == d ? fmad(q[1 + m], un, p) : q[1 + m] * un;
     f[4] = un * (q[4] + p);
 }
 // HLLC, Davis wave speeds (Toro, Riemann Solvers ch. 10)
@@ -579,14 +584,14 @@ __device__ __forceinline__ void hllc5(T g, int d, const T *qL, const T *qR, T *F
     const int in = 1 + d;
     const T rL = qL[0], rR = qR[0], iL = T(1) / rL, iR = T(1) / rR;
     const T uL = qL[in] * iL, uR = qR[in] * iR;
-    const T pL = (g - T(1)) * (qL[4] - T(0.5) * (qL[1] * qL[1] + qL[2] * qL[2] + qL[3] * qL[3]) * iL);
-    const T pR = (g - T(1)) * (qR[4] - T(0.5) * (qR[1] * qR[1] + qR[2] * qR[2] + qR[3] * qR[3]) * iR);
+    const T pL = (g - T(1)) * fmad(T(-0.5) * sq3(qL + 1), iL, qL[4]);
+    const T pR = (g - T(1)) * fmad(T(-0.5) * sq3(qR + 1), iR, qR[4]);
     const T cL = sqrt(g * pL * iL), cR = sqrt(g * pR * iR);
     const T SL = fmin(uL - cL, uR - cR), SR = fmax(uL + cL, uR + cR);
     if (SL >= T(0)) { flux5(g, d, qL, F); return; }
     if (SR <= T(0)) { flux5(g, d, qR, F); return; }
-    const T num = pR - pL + rL * uL * (SL - uL) - rR * uR * (SR - uR);
-    const T den = rL * (SL - uL) - rR * (SR - uR);
+    const T num = fmad(-(rR * uR), SR - uR, fmad(rL * uL, SL - uL, pR - pL));
+    const T den = fmad(rL, SL - uL, -(rR * (SR - uR)));
     const T Ss = num / den;
     const bool left = Ss >= T(0);
     const T *q = left ? qL : qR;
@@ -594,7 +599,7 @@ __device__ __forceinline__ void hllc5(T g, int d, const T *qL, const T *qR, T *F
     const T S = left ? SL : SR;
     T f[NC], qs[NC];
     f[0] = r * u;
-    for (int m = 0; m < 3; ++m) f[1 + m] = q[1 + m] * u + (m == d ? p : T(0));
+    for (int m = 0; m < 3; ++m) f[1 + m] = m == d ? fmad(q[1 + m], u, p) : q[1 + m] * u;
     f[4] = u * (q[4] + p);
     // fac = a / dS and p / a with a = rho (S - u), dS = S - S*, from one
     // reciprocal of a dS
@@ -602,8 +607,8 @@ __device__ __forceinline__ void hllc5(T g, int d, const T *qL, const T *qR, T *F
     const T fac = a * a * rr;
     qs[0] = fac;
     for (int m = 0; m < 3; ++m) qs[1 + m] = m == d ? fac * Ss : fac * (q[1 + m] * ir);
-    qs[4] = fac * (q[4] * ir + (Ss - u) * (Ss + p * dS * rr));
-    for (int k = 0; k < NC; ++k) F[k] = f[k] + S * (qs[k] - q[k]);
+    qs[4] = fac * fmad(q[4], ir, (Ss - u) * fmad(p * dS, rr, Ss));
+    for (int k = 0; k < NC; ++k) F[k] = fmad(S, qs[k] - q[k], f[k]);
 }
 template <typename T>
 __device__ __forceinline__ T vanleer(T dm, T dp) {
@@ -663,15 +668,15 @@ __device__ __forceinline__ void evolve5(const Desc &D, int d, const int *base, i
     T qL[NC], qR[NC], fL[NC], fR[NC];
     for (int k = 0; k < NC; ++k) {
         const T sl = lim ? vanleer(q[1][k] - q[0][k], q[2][k] - q[1][k]) : T(0);
-        qL[k] = q[1][k] - T(0.5) * sl;
-        qR[k] = q[1][k] + T(0.5) * sl;
+        qL[k] = fmad(T(-0.5), sl, q[1][k]);
+        qR[k] = fmad(T(0.5), sl, q[1][k]);
     }
     flux5(g, d, qL, fL);
     flux5(g, d, qR, fR);
     for (int k = 0; k < NC; ++k) {
-        const T dfl = hl * (fL[k] - fR[k]);
-        QL[k] = qL[k] + dfl;
-        QR[k] = qR[k] + dfl;
+        const T df = fL[k] - fR[k];
+        QL[k] = fmad(hl, df, qL[k]);
+        QR[k] = fmad(hl, df, qR[k]);
     }
     // physical: rho > 0 and p > 0, i.e. 2 rho E > |m|^2
     const bool okL = QL[0] > T(0) && T(2) * QL[0] * QL[4] > QL[1] * QL[1] + QL[2] * QL[2] + QL[3] * QL[3];
