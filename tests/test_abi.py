@@ -75,3 +75,50 @@ def test_noalloc_rejects_empty_domain(x1, y1):
     prob = inputs.Problem("empty", 16, 16, 0.0, 0.0, x1, y1, polygons=[_square(8)], moving=[1])
     e = _noalloc_call(prob)
     assert e.code == mb.MB_E_INVAL and "empty domain" in str(e)
+
+
+# mb3_create checks every argument before its first CUDA call, so these
+# run without a device: each must come back as MB_E_INVAL (-1)
+def _mb3_invalid(**kw):
+    import numpy as np
+    from paper_1711_11361_gb300 import inputs, mb, mb3
+    n, c, bb = inputs.cone_planes((0.5, 0.5, 0.5), 0.3, 0.2, 8)
+    args = dict(normals=n, offsets=c, bbox=bb, U=(0.1, 0.0, 0.0))
+    args.update(kw)
+    dims = args.pop("dims", (8, 8, 8))
+    p = inputs.Problem3("bad", *dims, **args)
+    with pytest.raises(mb.MBError) as ei:
+        mb3.Sim3(p, write_initial=False)
+    return ei.value.code
+
+
+@pytest.mark.parametrize("kw", [
+    dict(dims=(1, 8, 8)),                                                   # one cell on an open axis
+    dict(dims=(0, 8, 8)),
+    dict(bc=(2, 0, 0, 0, 0, 0)),                                            # periodic on one side only
+    dict(bc=(0, 0, 0, 0, 0, 3)),
+    dict(gamma=1.0),
+    dict(cfl=1.5),
+    dict(cfl=0.0),
+    dict(uncover_mode=5),
+    dict(hi=(0.0, 1.0, 1.0)),                                               # hi <= lo
+])
+def test_mb3_create_rejects_bad_arguments(kw):
+    assert _mb3_invalid(**kw) == -1
+
+
+def test_mb3_create_rejects_too_many_planes():
+    import numpy as np
+    from paper_1711_11361_gb300 import inputs
+    n, c, bb = inputs.cone_planes((0.5, 0.5, 0.5), 0.3, 0.2, 40)   # 41 planes > MB3_MAX_PLANES
+    assert _mb3_invalid(normals=n, offsets=c, bbox=bb) == -1
+
+
+def test_mb3_calls_reject_a_null_simulation():
+    from paper_1711_11361_gb300 import mb3
+    lib = mb3.lib
+    assert lib.mb3_sweep(None, 0, 0.1) == -1
+    assert lib.mb3_step(None, 0.1, None) == -1
+    assert lib.mb3_set_precision(None, 1) == -1
+    assert lib.mb3_flux_time(None, None) == -1
+    assert lib.mb3_last_sweep(None, None, None) == -1
