@@ -278,12 +278,23 @@ def test_schardin_cone_finest_mesh_conserves(mb3, precision):
     one exception is the z momentum in a z sweep, which also takes the
     pressure on the symmetry plane z = 0 where the cone's section covers it
     (the three-dimensional oracle shows the same at 4 and 8 cells per D).
-    To 1e-11 of the largest total, in both precisions (fluxes are stored and
-    the update runs in FP64 either way)."""
+    To 1e-11 of the largest total (fluxes are stored and the update runs in
+    FP64 in both precisions).  With the FP32 flux option the two x-side
+    fluxes are FP32 values of states whose exact fluxes are equal, so an x
+    sweep may also differ by their rounding, the same at every face pair:
+    at most 16 roundings of 2^-24 each (the flux's chain of operations) of
+    the largest flux component on either side, times dt/h and the ny nz
+    face pairs."""
     from paper_1711_11361_gb300 import mb
     p = inputs.n3_schardin_cone(40)
     sim = mb3.Sim3(p, precision=mb.FP32 if precision == "fp32" else mb.FP64)
     dt = sim.cfl_dt()
+    r2, u2, p2 = p.info["post_shock"]
+    u1, g = p.info["u1"], p.gamma
+
+    def fx(r, u, pr):   # the x flux of a uniform state at rest in y and z
+        return max(abs(r * u), abs(r * u * u + pr), abs(u * (pr / (g - 1.0) + 0.5 * r * u * u + pr)))
+    fmax = max(fx(1.0, u1, 1.0), fx(r2, u2, p2))
     c0 = sim.contents().sum(axis=(1, 2, 3))
     scale = np.abs(c0).max()
     for d in (0, 1, 2, 2, 1, 0):
@@ -291,7 +302,10 @@ def test_schardin_cone_finest_mesh_conserves(mb3, precision):
         c1 = sim.contents().sum(axis=(1, 2, 3))
         w, _ = sim.last_sweep()
         q = [0, 1, 2, 4] if d == 2 else [0, 1, 2, 3, 4]
-        assert np.max(np.abs((c1 - c0 - w)[q])) <= 1e-11 * scale, (d, c1 - c0 - w)
+        tol = 1e-11 * scale
+        if precision == "fp32" and d == 0:
+            tol += 2.0 * 16 * 2.0 ** -24 * fmax * dt / p.h[0] * p.ny * p.nz
+        assert np.max(np.abs((c1 - c0 - w)[q])) <= tol, (d, c1 - c0 - w)
         c0 = c1
     assert sim.read_state()["status"] == 0
     sim.close()
