@@ -652,7 +652,7 @@ def run_n3(args):
     for its 20 mm cone), at each of --n3-resolutions cells per diameter.
     Reports cell-sweeps/s (cells x 3 sweeps per step), the steps, the cells
     merged by the safeguard and the status; the 3-D oracle on a bounded
-    sample (one step of the 10-per-D case) is the CPU baseline.  The FP32
+    sample (the 10-per-D case's first steps, about 10 s) is the CPU baseline.  The FP32
     flux option (mb3_set_precision) runs the finest mesh too, with its
     alpha-weighted L1 density difference from the FP64 path over 40 steps
     at the FP64 path's dt on the 10-per-D mesh."""
@@ -719,10 +719,15 @@ def run_n3(args):
         p = inputs.n3_schardin_cone(10)
         o = o3.Oracle3(p)
         t0 = time.perf_counter()
-        r, dt = o.step()
+        nst = 0
+        while time.perf_counter() - t0 < 10.0:   # a bounded sample: whole steps for about 10 s
+            o.step()
+            nst += 1
         el = time.perf_counter() - t0
-        line["cpu_baseline"] = {"value": p.info["cells"] * 3 / el, "unit": "cell-sweeps/s", "cores": 1,
-                                "kind": "oracle", "sample": f"one step of the {p.nx}x{p.ny}x{p.nz} case, {el:.1f} s"}
+        line["cpu_baseline"] = {"value": p.info["cells"] * 3 * nst / el, "unit": "cell-sweeps/s", "cores": 1,
+                                "kind": "oracle",
+                                "sample": f"the first {nst} steps of the {p.nx}x{p.ny}x{p.nz} case from its initial "
+                                          f"state, {el:.1f} s, single-threaded"}
     print(json.dumps(line))
 
 
