@@ -570,9 +570,10 @@ __device__ __forceinline__ double pressure5(double g, const double *q) {
 __device__ __forceinline__ double fmad(double a, double b, double c) { return __fma_rn(a, b, c); }
 __device__ __forceinline__ float fmad(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 template <typename T> __device__ __forceinline__ T sq3(const T *m) { return fmad(m[0], m[0], fmad(m[1], m[1], m[2] * m[2])); }
+// the physical flux along d of a state with 1/rho given
 template <typename T>
-__device__ __forceinline__ void flux5(T g, int d, const T *q, T *f) {
-    const T rho = q[0], ir = T(1) / rho, un = q[1 + d] * ir;
+__device__ __forceinline__ void flux5(T g, int d, const T *q, T ir, T *f) {
+    const T rho = q[0], un = q[1 + d] * ir;
     const T p = (g - T(1)) * fmad(T(-0.5) * sq3(q + 1), ir, q[4]);
     f[0] = rho * un;
     for (int m = 0; m < 3; ++m) f[1 + m] = m == d ? fmad(q[1 + m], un, p) : q[1 + m] * un;
@@ -582,14 +583,15 @@ __device__ __forceinline__ void flux5(T g, int d, const T *q, T *f) {
 template <typename T>
 __device__ __forceinline__ void hllc5(T g, int d, const T *qL, const T *qR, T *F) {
     const int in = 1 + d;
-    const T rL = qL[0], rR = qR[0], iL = T(1) / rL, iR = T(1) / rR;
+    // 1/rho of both states from one reciprocal of their product
+    const T rL = qL[0], rR = qR[0], rr2 = T(1) / (rL * rR), iL = rR * rr2, iR = rL * rr2;
     const T uL = qL[in] * iL, uR = qR[in] * iR;
     const T pL = (g - T(1)) * fmad(T(-0.5) * sq3(qL + 1), iL, qL[4]);
     const T pR = (g - T(1)) * fmad(T(-0.5) * sq3(qR + 1), iR, qR[4]);
     const T cL = sqrt(g * pL * iL), cR = sqrt(g * pR * iR);
     const T SL = fmin(uL - cL, uR - cR), SR = fmax(uL + cL, uR + cR);
-    if (SL >= T(0)) { flux5(g, d, qL, F); return; }
-    if (SR <= T(0)) { flux5(g, d, qR, F); return; }
+    if (SL >= T(0)) { flux5(g, d, qL, iL, F); return; }
+    if (SR <= T(0)) { flux5(g, d, qR, iR, F); return; }
     const T num = fmad(-(rR * uR), SR - uR, fmad(rL * uL, SL - uL, pR - pL));
     const T den = fmad(rL, SL - uL, -(rR * (SR - uR)));
     const T Ss = num / den;
@@ -671,8 +673,9 @@ __device__ __forceinline__ void evolve5(const Desc &D, int d, const int *base, i
         qL[k] = fmad(T(-0.5), sl, q[1][k]);
         qR[k] = fmad(T(0.5), sl, q[1][k]);
     }
-    flux5(g, d, qL, fL);
-    flux5(g, d, qR, fR);
+    const T rr2 = T(1) / (qL[0] * qR[0]);   // 1/rho of both extrapolated states
+    flux5(g, d, qL, qR[0] * rr2, fL);
+    flux5(g, d, qR, qL[0] * rr2, fR);
     for (int k = 0; k < NC; ++k) {
         const T df = fL[k] - fR[k];
         QL[k] = fmad(hl, df, qL[k]);
