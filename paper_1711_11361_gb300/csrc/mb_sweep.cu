@@ -338,6 +338,61 @@ __global__ void k_band_prep(const InstDesc *__restrict__ D, InstDyn *__restrict_
     }
 }
 
+// the band offsets of k_band_offsets, computed by every CTA into shared
+// memory (n_inst + 1 ints; the same integer sums), CTA 0 also writing them
+// to boff for the later band kernels; then k_band_prep's loop over them.
+// One launch fewer per sweep than k_band_offsets + k_band_prep.
+template <class T>
+__global__ void k_band_prep_o(const InstDesc *__restrict__ D, InstDyn *__restrict__ Y, BandRec *__restrict__ R,
+                              int *__restrict__ boff, int n_inst, int dir, int src, int qn) {
+    extern __shared__ int s_boff[];
+    __shared__ int wsum[32];
+    __shared__ int carry;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const bool w0 = blockIdx.x == 0;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int k0 = 0; k0 < n_inst; k0 += blockDim.x) {
+        const int k = k0 + threadIdx.x;
+        const int c = k < n_inst ? min(Y[k].band_count, D[k].rec_cap) : 0;
+        int v = c;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += u;
+        }
+        if (lane == 31) wsum[warp] = v;
+        __syncthreads();
+        if (warp == 0) {
+            int w = lane < nw ? wsum[lane] : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += u;
+            }
+            if (lane < nw) wsum[lane] = w;
+        }
+        __syncthreads();
+        if (k < n_inst) {
+            const int ex = carry + (warp ? wsum[warp - 1] : 0) + v - c;
+            s_boff[k] = ex;
+            if (w0) boff[k] = ex;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) carry += wsum[nw - 1];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        s_boff[n_inst] = carry;
+        if (w0) boff[n_inst] = carry;
+    }
+    __syncthreads();
+    const int stride = gridDim.x * blockDim.x;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x;; t += stride) {
+        const int r = band_rec_of(D, s_boff, n_inst, t);
+        if (r < 0) break;
+        band_prep_rec<T>(D, Y, R, n_inst, r, dir, src, qn);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // stabilised flux of one face: aperture times F2D (eqs. Klein2shieldedFluxMethod2
 // and Klein2DtotalfluxaMethod2 with the one- or two-sided shielded parts).
@@ -2788,8 +2843,12 @@ void launch_band_stage(int stage, const InstDesc *D, InstDyn *Y, BandRec *R, con
     switch (stage) {
         case 0:
             if (!blocks) break;
-            k_band_offsets<<<1, 256, 0, st>>>(D, Y, n_inst, boff);
-            k_band_prep<T><<<blocks, 128, 0, st>>>(D, Y, R, boff, n_inst, dir, src, qn);
+            if ((size_t)(n_inst + 1) * sizeof(int) <= 32768) {
+                k_band_prep_o<T><<<blocks, 128, (n_inst + 1) * sizeof(int), st>>>(D, Y, R, boff, n_inst, dir, src, qn);
+            } else {
+                k_band_offsets<<<1, 256, 0, st>>>(D, Y, n_inst, boff);
+                k_band_prep<T><<<blocks, 128, 0, st>>>(D, Y, R, boff, n_inst, dir, src, qn);
+            }
             break;
         case 1: if (blocks) k_band_sweep<T><<<blocks, 128, 0, st>>>(D, Y, R, bnd, boff, n_inst, dir, src); break;
         case 2: if (blocks) k_events<T><<<blocks, 128, 0, st>>>(D, Y, R, boff, n_inst); break;
