@@ -56,15 +56,23 @@ __host__ __device__ inline double dot3(const double *a, const double *b) { retur
 
 // area of {p : p = o + s e1 + t e2} clipped by the half-spaces a_m s + b_m t
 // <= r_m, starting from the square [-L, L]^2 (a 2-D Sutherland-Hodgman)
+// (each vertex's signed distance is evaluated once per half-plane, and a
+// half-plane holding every vertex leaves the polygon as it is)
 __device__ double clipped_area(const double *a, const double *b, const double *r, int nh, double L) {
-    double px[MAXPV], py[MAXPV], qx[MAXPV], qy[MAXPV];
+    double px[MAXPV], py[MAXPV], qx[MAXPV], qy[MAXPV], s[MAXPV];
     int n = 4;
     px[0] = -L; py[0] = -L; px[1] = L; py[1] = -L; px[2] = L; py[2] = L; px[3] = -L; py[3] = L;
     for (int m = 0; m < nh && n > 0; ++m) {
+        bool out = false;
+        for (int k = 0; k < n; ++k) {
+            s[k] = a[m] * px[k] + b[m] * py[k] - r[m];
+            if (!(s[k] <= 0.0)) out = true;
+        }
+        if (!out) continue;
         int k2 = 0;
         for (int k = 0; k < n; ++k) {
             const int k1 = k + 1 < n ? k + 1 : 0;
-            const double sa = a[m] * px[k] + b[m] * py[k] - r[m], sb = a[m] * px[k1] + b[m] * py[k1] - r[m];
+            const double sa = s[k], sb = s[k1];
             const bool ina = sa <= 0.0, inb = sb <= 0.0;
             if (ina && k2 < MAXPV) { qx[k2] = px[k]; qy[k2] = py[k]; ++k2; }
             if (ina != inb && k2 < MAXPV) {
@@ -179,17 +187,23 @@ __device__ double rect_solid_area(const Body3 &B, int a, double v, double lb, do
         if (lo_ > 0.0) return 0.0;
         if (hi_ > 0.0) cut |= 1u << f;
     }
-    double px[MAXPV], py[MAXPV], qx[MAXPV], qy[MAXPV];
+    double px[MAXPV], py[MAXPV], qx[MAXPV], qy[MAXPV], s[MAXPV];
     int n = 4;
     px[0] = 0.0; py[0] = 0.0; px[1] = wb; py[1] = 0.0; px[2] = wb; py[2] = wc; px[3] = 0.0; py[3] = wc;
     for (; cut && n > 0; cut &= cut - 1) {
         const int f = __ffs(cut) - 1;
         const double *nn = &B.n[3 * f];
         const double cc = B.c[f] - nn[a] * v - nn[b] * lb - nn[c] * lc;
+        bool out = false;   // (as in clipped_area)
+        for (int k = 0; k < n; ++k) {
+            s[k] = nn[b] * px[k] + nn[c] * py[k] - cc;
+            if (!(s[k] <= 0.0)) out = true;
+        }
+        if (!out) continue;
         int k2 = 0;
         for (int k = 0; k < n; ++k) {
             const int k1 = k + 1 < n ? k + 1 : 0;
-            const double sa = nn[b] * px[k] + nn[c] * py[k] - cc, sb = nn[b] * px[k1] + nn[c] * py[k1] - cc;
+            const double sa = s[k], sb = s[k1];
             const bool ina = sa <= 0.0, inb = sb <= 0.0;
             if (ina && k2 < MAXPV) { qx[k2] = px[k]; qy[k2] = py[k]; ++k2; }
             if (ina != inb && k2 < MAXPV) {
