@@ -374,3 +374,94 @@ def test_covered_cell_without_a_fluid_neighbour(open_side):
         assert np.max(np.abs(Cn - expect)) < 1e-14
     else:
         assert r == -4
+
+
+# --- the three-dimensional HLLC and wall state (eq. riemann_wallvel) -------
+
+from exact_riemann import sample as _sample, star as _star   # noqa: E402
+
+
+def _cons3(r, u, p):
+    u = np.asarray(u, float)
+    return np.array([r, r * u[0], r * u[1], r * u[2], p / (G - 1.0) + 0.5 * r * u.dot(u)])
+
+
+def _flux3(q, d):
+    r = q[0]
+    u = q[1:4] / r
+    p = (G - 1.0) * (q[4] - 0.5 * r * u.dot(u))
+    f = np.array([r * u[d], q[1] * u[d], q[2] * u[d], q[3] * u[d], u[d] * (q[4] + p)])
+    f[1 + d] += p
+    return f
+
+
+@pytest.mark.parametrize("d", [0, 1, 2])
+def test_hllc3_consistency_and_stationary_contact(d):
+    """HLLC of a state with itself is the physical flux; an isolated
+    stationary contact (equal pressure, zero normal velocity) passes only the
+    pressure, whatever the tangential velocities"""
+    q = _cons3(1.3, [0.4, -0.25, 0.17], 0.8)
+    assert np.max(np.abs(o3.hllc(G, d, q, q) - _flux3(q, d))) < 1e-14
+    uL = np.array([0.3, -0.2, 0.5]); uL[d] = 0.0
+    uR = np.array([-0.1, 0.6, 0.2]); uR[d] = 0.0
+    F = o3.hllc(G, d, _cons3(1.0, uL, 0.7), _cons3(0.4, uR, 0.7))
+    expect = np.zeros(5)
+    expect[1 + d] = 0.7
+    assert np.max(np.abs(F - expect)) < 1e-14
+
+
+@pytest.mark.parametrize("d", [0, 1, 2])
+@pytest.mark.parametrize("case", [0, 1, 2])
+def test_hllc3_carries_the_upwind_tangential_velocities(d, case):
+    """In HLLC the star states keep their side's tangential velocities, so
+    the flux of each tangential momentum is the mass flux times the
+    tangential velocity of the side the contact leaves behind (left if S* >=
+    0, which the sign of the mass flux gives here)"""
+    rng = np.random.default_rng(40 + 3 * d + case)
+    uL, uR = rng.uniform(-0.6, 0.6, 3), rng.uniform(-0.6, 0.6, 3)
+    qL = _cons3(rng.uniform(0.5, 2.0), uL, rng.uniform(0.5, 2.0))
+    qR = _cons3(rng.uniform(0.5, 2.0), uR, rng.uniform(0.5, 2.0))
+    F = o3.hllc(G, d, qL, qR)
+    side = uL if F[0] >= 0.0 else uR
+    for t in range(3):
+        if t != d:
+            assert abs(F[1 + t] - F[0] * side[t]) < 1e-13 * max(1.0, abs(F[0]))
+
+
+def test_hllc3_directions_agree_on_permuted_states():
+    """the flux along z of a state equals the flux along x of the state with
+    its x and z components exchanged, exchanged back (and likewise y)"""
+    qL = _cons3(1.2, [0.3, -0.4, 0.25], 1.1)
+    qR = _cons3(0.7, [-0.2, 0.1, -0.35], 0.6)
+    for d, perm in ((2, [0, 3, 2, 1, 4]), (1, [0, 2, 1, 3, 4])):
+        Fd = o3.hllc(G, d, qL, qR)
+        Fx = o3.hllc(G, 0, qL[perm], qR[perm])
+        assert np.max(np.abs(Fd - Fx[perm])) < 1e-14
+
+
+@pytest.mark.parametrize("un,wn", [(0.3, 0.3), (0.0, 0.5), (0.4, -0.1), (-0.6, 0.2), (-0.2, -0.5)])
+def test_wall_state3(un, wn):
+    """The moving-wall Riemann problem with a three-dimensional normal:
+    u*.n = w.n; the tangential velocity (both components) is kept; a wall
+    moving with the gas leaves rho and p as they are; otherwise p* is the
+    exact star pressure of the reflected Riemann problem (the independent
+    Newton solution) and rho* the shock or isentropic density next to the
+    wall."""
+    n = np.array([0.36, 0.48, 0.8])
+    t1 = np.array([0.8, -0.6, 0.0])
+    t2 = np.cross(n, t1)
+    u = un * n + 0.37 * t1 - 0.21 * t2
+    w = wn * n + 1.3 * t1 + 0.5 * t2
+    q = _cons3(1.1, u, 0.9)
+    rs, ps, us = o3.wall_state(G, q, n, w)
+    assert abs(us.dot(n) - wn) < 1e-15
+    assert abs(us.dot(t1) - 0.37) < 1e-15 and abs(us.dot(t2) + 0.21) < 1e-15
+    if un == wn:
+        assert abs(rs - 1.1) < 1e-15 and abs(ps - 0.9) < 1e-15
+    else:
+        pex, uex = _star(1.1, un, 0.9, 1.1, 2 * wn - un, 0.9)
+        assert abs(uex - wn) < 1e-12
+        assert abs(ps - pex) / pex < 1e-10
+        rex = _sample(1.1, un, 0.9, 1.1, 2 * wn - un, 0.9, wn - 1e-9)[0]
+        assert abs(rs - rex) / rex < 1e-6
+        assert (ps > 0.9) == (un > wn)
