@@ -1017,6 +1017,12 @@ int o3_cover_uncover(o3_sim *s, const double *alphaA, const double *alphaB, cons
     return cover_uncover3(s, alphaA, alphaB, C, Cn, updated);
 }
 
+/* the positivity safeguard alone on given fields (Cn in place), for tests
+ * of its clusters and shares; returns the cells merged */
+int o3_safeguard(o3_sim *s, const double *alphaA, const double *alphaB, const unsigned char *updated, double *Cn) {
+    return safeguard3(s, s->c.gamma, alphaA, alphaB, updated, Cn);
+}
+
 /* the last sweep's summed wall terms (O3_NC) and cells merged */
 int o3_last_sweep(const o3_sim *s, double *wall) {
     if (wall) memcpy(wall, s->wall_last, sizeof(double) * O3_NC);

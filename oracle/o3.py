@@ -77,6 +77,7 @@ def _load():
         lib.o3_solid_volume.argtypes = [P, D, D, D]
         lib.o3_solid_volume.restype = ctypes.c_double
         lib.o3_cover_uncover.argtypes = [P, D, D, D, D, B]
+        lib.o3_safeguard.argtypes = [P, D, D, B, D]
         lib.o3_hllc.argtypes = [ctypes.c_double, ctypes.c_int, D, D, D]
         lib.o3_wall_state.argtypes = [ctypes.c_double, D, D, D, D, D, D]
         _lib = lib
@@ -218,6 +219,14 @@ class Oracle3:
         r = _lib.o3_cover_uncover(self._h, _dp(aA), _dp(aB), _dp(Cc), _dp(Cn),
                                   upd.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)))
         return r, Cn.reshape(5, self.nz, self.ny, self.nx), upd.reshape(self.nz, self.ny, self.nx)
+
+    def safeguard(self, alphaA, alphaB, updated, Cn):
+        """The positivity safeguard alone on given fields: (cells merged, Cn)."""
+        aA, aB = _vec(alphaA).reshape(-1), _vec(alphaB).reshape(-1)
+        up = np.ascontiguousarray(updated, dtype=np.uint8).reshape(-1)
+        C = _vec(Cn).reshape(-1).copy()
+        m = _lib.o3_safeguard(self._h, _dp(aA), _dp(aB), up.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)), _dp(C))
+        return m, C.reshape(5, self.nz, self.ny, self.nx)
 
     def solid_volume(self, lo, hi, T=(0.0, 0.0, 0.0)):
         return _lib.o3_solid_volume(self._h, _dp(_vec(T)), _dp(_vec(lo)), _dp(_vec(hi)))

@@ -498,3 +498,63 @@ def test_wall_normal_of_a_tilted_plane_is_the_plane_normal():
         assert np.max(np.abs(nn[well] + n)) < 1e-12
         assert np.max(np.abs(nn[keep] + n)) < 1e-6
         assert np.all(np.linalg.norm(nn[has & ~keep], axis=-1) == 0.0)
+
+
+# --- the positivity safeguard (R22): clusters over the six face neighbours,
+# shares in proportion to alpha_B; expected values written out per case
+
+def _sg_case(seed=5):
+    p = inputs.Problem3("sg", 5, 5, 5, bc=(inputs.PERIODIC,) * 6)
+    o = o3.Oracle3(p)
+    rng = np.random.default_rng(seed)
+    aB = rng.uniform(0.3, 1.0, (5, 5, 5))
+    aA = np.ones((5, 5, 5))
+    Q = inputs.conserved3(rng.uniform(0.8, 1.2, (5, 5, 5)), rng.uniform(-0.2, 0.2, (5, 5, 5)), 0.1, -0.1,
+                          rng.uniform(0.8, 1.2, (5, 5, 5)))
+    C = Q * aB[None]
+    up = np.ones((5, 5, 5), dtype=np.uint8)
+    return o, aA, aB, C, up
+
+
+def _shares(C, aB, cells):
+    tot = sum(C[(slice(None),) + c] for c in cells)
+    atot = sum(aB[c] for c in cells)
+    expect = C.copy()
+    for c in cells:
+        expect[(slice(None),) + c] = aB[c] * (tot / atot)
+    return expect
+
+
+def test_safeguard_merges_a_non_physical_cell_with_its_face_neighbours():
+    o, aA, aB, C, up = _sg_case()
+    c = _at(aA, (0, 0, 0))
+    C[(slice(None),) + c] = [-0.02, 0.0, 0.0, 0.0, 0.1]     # negative density
+    m, Cn = o.safeguard(aA, aB, up, C)
+    cells = [c] + [_at(aA, off) for off in FACES]
+    assert m == 7
+    assert np.max(np.abs(Cn - _shares(C, aB, cells))) < 1e-14
+
+
+def test_safeguard_seeds_a_collapsing_cell_and_skips_cells_not_updated():
+    """a physical cell keeping under 1% of its volume over the sweep seeds a
+    merge; a face neighbour that was not updated stays out of it"""
+    o, aA, aB, C, up = _sg_case(6)
+    c = _at(aA, (0, 0, 0))
+    aB[c] = 0.005
+    C[(slice(None),) + c] *= 0.005 / 0.6
+    up[_at(aA, (0, 1, 0))] = 0
+    m, Cn = o.safeguard(aA, aB, up, C)
+    cells = [c] + [_at(aA, off) for off in FACES if off != (0, 1, 0)]
+    assert m == 6
+    assert np.max(np.abs(Cn - _shares(C, aB, cells))) < 1e-14
+
+
+def test_safeguard_joins_neighbouring_seeds_into_one_cluster():
+    o, aA, aB, C, up = _sg_case(7)
+    c, c2 = _at(aA, (0, 0, 0)), _at(aA, (1, 0, 0))
+    for x in (c, c2):
+        C[(slice(None),) + x] = [0.3, 0.0, 0.0, 0.0, -0.05]   # negative energy
+    m, Cn = o.safeguard(aA, aB, up, C)
+    cells = sorted({c, c2} | {_at(aA, off) for off in FACES} | {_at(aA, (1 + a, b, z)) for a, b, z in FACES})
+    assert m == 12 and len(cells) == 12
+    assert np.max(np.abs(Cn - _shares(C, aB, cells))) < 1e-14
