@@ -558,3 +558,26 @@ def test_safeguard_joins_neighbouring_seeds_into_one_cluster():
     cells = sorted({c, c2} | {_at(aA, off) for off in FACES} | {_at(aA, (1 + a, b, z)) for a, b, z in FACES})
     assert m == 12 and len(cells) == 12
     assert np.max(np.abs(Cn - _shares(C, aB, cells))) < 1e-14
+
+
+@pytest.mark.parametrize("d", [0, 1, 2])
+def test_stationary_contacts_stay_put(d):
+    """No body: the density varies along d, the normal velocity is 0, the
+    tangential velocities and the pressure are uniform, so every face holds
+    a stationary contact.  Van Leer slopes are homogeneous, so the
+    conserved-variable extrapolation keeps the pressure and the tangential
+    velocities at every face, and HLLC passes only the pressure: a sweep
+    along d leaves the state as it was, to round-off"""
+    p = inputs.Problem3("contact", 16, 16, 16, bc=(inputs.PERIODIC,) * 6)
+    c = p.cell_centres()[d]
+    tp = 2 * math.pi
+    vel = [0.3 * np.ones_like(c), -0.2 * np.ones_like(c), 0.15 * np.ones_like(c)]
+    vel[d] = np.zeros_like(c)
+    tang = [a for a in range(3) if a != d]
+    p.Q0 = inputs.conserved3(1.0 + 0.5 * np.sin(tp * c), vel[0], vel[1], vel[2], np.ones_like(c))
+    o = o3.Oracle3(p)
+    before = o.contents()
+    assert o.sweep(d, 0.8 * o.cfl_dt()) == 0
+    after = o.contents()
+    assert np.max(np.abs(after - before)) < 1e-13
+    assert np.max(np.abs(before[1 + tang[0]])) > 0.1 and np.max(np.abs(before[1 + tang[1]])) > 0.1
