@@ -581,3 +581,20 @@ def test_stationary_contacts_stay_put(d):
     after = o.contents()
     assert np.max(np.abs(after - before)) < 1e-13
     assert np.max(np.abs(before[1 + tang[0]])) > 0.1 and np.max(np.abs(before[1 + tang[1]])) > 0.1
+
+
+def test_schardin_cone_states_are_the_papers():
+    """The Schardin workload's post-shock state (Rankine-Hugoniot of a
+    Mach-1.34 shock, in units of the pre-shock state) against the states
+    Sec. III.F prints (tests/golden/paper_states.txt), within the rounding of
+    the printed digits"""
+    import os
+    st = {}
+    for line in open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "paper_states.txt")):
+        if line.strip() and not line.startswith("#"):
+            k, r, u, pr = line.split()
+            st[k] = (float(r), float(pr))
+    (r1, p1), (r2p, p2p) = st["shock134_3d_left"], st["shock134_3d_right"]
+    r2, u2, p2 = inputs.n3_schardin_cone(4).info["post_shock"]
+    assert abs(r2 - r2p / r1) <= (0.0005 / r2p + 0.0005 / r1) * r2
+    assert abs(p2 - p2p / p1) <= (50.0 / p2p + 50.0 / p1) * p2
