@@ -309,3 +309,27 @@ def test_schardin_cone_finest_mesh_conserves(mb3, precision):
         c0 = c1
     assert sim.read_state()["status"] == 0
     sim.close()
+
+
+def test_no_body_shock_tube_along_each_axis(mb3):
+    """No body (an empty region R: the geometry, wall and event kernels do
+    not run): a shock tube along x, y and z in turn, with the tangential
+    velocities nonzero, 8 free-running steps against the oracle at the
+    device's dt; contents to 1e-11 relative (no cut cells, so no 1/alpha
+    growth of round-off)"""
+    for d in range(3):
+        p = inputs.Problem3("tube", 24, 20, 16, hi=(1.2, 1.0, 0.8))
+        c = p.cell_centres()[d]
+        hi = (1.2, 1.0, 0.8)[d]
+        left = c < 0.45 * hi
+        vel = [np.full_like(c, 0.2), np.full_like(c, -0.1), np.full_like(c, 0.05)]
+        vel[d] = np.zeros_like(c)
+        p.Q0 = inputs.conserved3(np.where(left, 1.0, 0.125), vel[0], vel[1], vel[2], np.where(left, 1.0, 0.1))
+        orc = o3.Oracle3(p)
+        sim = mb3.Sim3(p)
+        for _ in range(8):
+            dt = sim.step()
+            assert orc.step(dt)[0] == 0
+        assert _rel(sim.contents(), orc.contents()) <= 1e-11, d
+        assert sim.read_state()["status"] == 0
+        sim.close()
