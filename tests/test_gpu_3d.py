@@ -333,3 +333,31 @@ def test_no_body_shock_tube_along_each_axis(mb3):
         assert _rel(sim.contents(), orc.contents()) <= 1e-11, d
         assert sim.read_state()["status"] == 0
         sim.close()
+
+
+def test_many_collapse_seeds_take_the_one_thread_merge(mb3):
+    """A box body whose front face crosses a layer of identical cells: in
+    the first x sweep every cell of that layer keeps under 1% of its volume
+    (alpha 0.5 -> 0.004), so several hundred collapse seeds merge at once,
+    more than the block-wide merge holds (146 seeds), and the one-thread
+    form runs.  Contents to 1e-12 and the same merged-cell count as the
+    oracle (940 cells)."""
+    h = 1.0 / 32
+    N = np.array([[-1, 0, 0], [1, 0, 0], [0, -1, 0], [0, 1, 0], [0, 0, -1], [0, 0, 1]], float)
+    lo, hi = (0.2, 0.2031, 0.2017), (16.5 * h, 0.7969, 0.7983)
+    C = np.array([-lo[0], hi[0], -lo[1], hi[1], -lo[2], hi[2]])
+    U = 2.0
+    p = inputs.Problem3("slab3", 32, 32, 32, normals=N, offsets=C, bbox=(lo[0], hi[0], lo[1], hi[1], lo[2], hi[2]),
+                        U=(U, 0.0, 0.0), bc=(inputs.PERIODIC,) * 6)
+    X, Y, Z = p.cell_centres()
+    p.Q0 = inputs.conserved3(np.ones_like(X), 0.0, 0.0, 0.0, np.ones_like(X))
+    orc = o3.Oracle3(p)
+    sim = mb3.Sim3(p)
+    dt = 0.496 * h / U
+    assert orc.sweep(0, dt) == 0
+    sim.sweep(0, dt)
+    _, mo = orc.last_sweep()
+    _, mg = sim.last_sweep()
+    assert mo > 146 and mg == mo
+    assert _rel(sim.contents(), orc.contents()) <= 1e-12
+    sim.close()
