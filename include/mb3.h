@@ -2,7 +2,8 @@
  * Sec. II.C.4, eqs. Klein2DcompleteMovingMethod2a-c): x, y and z sweeps of
  * the compressible Euler equations (5 conserved variables) around one
  * convex polyhedral body translating at constant velocity, in FP64 on the
- * GPU.  The same readings as the two-dimensional library (mb.h), extended
+ * GPU (with an FP32 option for the flow arithmetic, mb3_set_precision).
+ * The same readings as the two-dimensional library (mb.h), extended
  * to three dimensions:
  *   - volume fractions, face apertures and the time-averaged apertures of a
  *     sweep's faces (the fluid fraction of the box a face sweeps through the
